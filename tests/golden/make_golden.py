@@ -1,0 +1,80 @@
+"""Write the stored expectations for the full-size workloads.
+
+Calls only the CPU oracle (``oracle/``) and the seeded generators
+(``synth/``); nothing here touches the CUDA path.  Each output file records
+the workload, the SHA-256 of the generated arc list (so a test can tell that
+it regenerated the same graph), N_k and every nonzero class count.
+
+    python tests/golden/make_golden.py [--threads T] [--only NAME ...]
+"""
+import argparse
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+WORKLOADS = {
+    "er_n1000_m5000_k3": (synth.er_k3, 3),
+    "chung_lu_n20000_m100000_k4": (synth.chung_lu_k4, 4),
+    "regulatory_n5000_m15000_k5": (synth.regulatory_k5, 5),
+}
+
+
+def write_counts(path, name, g, k, counts, seconds, threads):
+    with open(path, "w") as f:
+        f.write(f"# workload {name}\n")
+        f.write(f"# graph {g.name} n={g.n} m={g.m} sha256={synth.graph_digest(g)}\n")
+        f.write(f"# k {k}\n")
+        f.write(f"# classes {len(counts)}\n")
+        f.write(f"# total {int(counts.sum())}\n")
+        f.write(f"# oracle ESU, {threads} threads, {seconds:.1f} s\n")
+        for c, v in enumerate(counts):
+            if v:
+                f.write(f"{c} {int(v)}\n")
+
+
+def read_counts(path):
+    """(header dict, int64 counts) of a file written by write_counts."""
+    hdr = {}
+    rows = []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("# "):
+                key, _, val = line[2:].strip().partition(" ")
+                hdr[key] = val
+            elif line.strip():
+                c, v = line.split()
+                rows.append((int(c), int(v)))
+    counts = np.zeros(int(hdr["classes"]), dtype=np.int64)
+    for c, v in rows:
+        counts[c] = v
+    assert int(counts.sum()) == int(hdr["total"])
+    return hdr, counts
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--threads", type=int, default=oracle.max_threads())
+    ap.add_argument("--only", nargs="*")
+    args = ap.parse_args()
+    for name, (make, k) in WORKLOADS.items():
+        if args.only and name not in args.only:
+            continue
+        g = make()
+        t = time.time()
+        counts = oracle.count(g.n, g.src, g.dst, k, threads=args.threads)
+        dt = time.time() - t
+        write_counts(os.path.join(HERE, f"{name}.txt"), name, g, k, counts, dt, args.threads)
+        print(f"{name}: N_{k} = {int(counts.sum())} in {dt:.1f} s", flush=True)
+
+
+if __name__ == "__main__":
+    main()
