@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Benchmark: connected induced k-subgraphs classified per second.
+
+One step = one pass of the whole counting path over one graph already in HBM:
+graph ingest (pair-state matrix, G* neighbour lists), the two enumeration
+launches and the histogram flush, through the C ABI acc_motif_count.  The
+default workload is the directed Chung-Lu graph n=20000, m=100000 (Pareto
+exponent 2.2, degrees capped at 500, 10% reciprocal arcs) at k=4.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME]
+
+N>1 runs one independent replica per GPU (rank), each counting its own copy
+of the workload ("replicas only": the count has no exchange step), and
+reports the units all ranks processed over the slowest rank's time.
+``--impl reference`` times the CPU oracle on a bounded sample of the same
+workload on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "connected induced k-subgraphs classified/sec (k=3,4,5) and graphs/sec batched, bit-exact"
+UNIT = "subgraphs/s"
+
+WORKLOADS = {
+    "chung_lu_n20000_m100000_k4": (synth.chung_lu_k4, 4),
+    "er_n1000_m5000_k3": (synth.er_k3, 3),
+    "regulatory_n5000_m15000_k5": (synth.regulatory_k5, 5),
+}
+DEFAULT_WORKLOAD = "chung_lu_n20000_m100000_k4"
+
+# Algorithmic integer operations per classified subgraph (the method's minimum
+# at the leaf): k-1 pair states, each an address, a load and a 2-bit extract
+# (4 ops) placed into the code (2 ops), then one table load and one histogram
+# increment: 6(k-1) + 2.
+def ops_per_subgraph(k: int) -> int:
+    return 6 * (k - 1) + 2
+
+
+L2_FLUSH_BYTES = 256 << 20
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+REASON_BITS = {
+    0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+    0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+    0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting",
+}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    def __init__(self, gpu_index: int, period_ms: int = 50):
+        self.gpu = gpu_index
+        self.period = period_ms
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "-i", str(self.gpu),
+               "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active",
+               "--format=csv,noheader,nounits", "-lms", str(self.period)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 3:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                bits = int(parts[2], 16) if parts[2].startswith("0x") else int(parts[2])
+            except ValueError:
+                continue
+            for b, name in REASON_BITS.items():
+                if bits & b:
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (one process per GPU; replicas)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_max(dist, value: float, device=None) -> float:
+    """Maximum of value over all ranks (identity without a process group)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_rate(units_all_ranks: float, max_seconds: float) -> float:
+    return units_all_ranks / max_seconds if max_seconds > 0 else float("nan")
+
+
+# ---------------------------------------------------------------------------
+# profiles: ncu DRAM traffic of the enumeration kernel, if captured for this source
+# ---------------------------------------------------------------------------
+
+def kernel_source_digest() -> str:
+    h = hashlib.sha256()
+    for f in ("enum.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1203_3415_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """Bytes per enumeration stage from profiles/<workload>_traffic.txt, when it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"enum_{workload}_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            key, _, val = line.partition(":")
+            kv[key.strip()] = val.strip()
+    if kv.get("source_digest") != kernel_source_digest():
+        return None
+    try:
+        return float(kv["dram_bytes_per_stage"])
+    except (KeyError, ValueError):
+        return None
+
+
+def golden_counts(workload: str):
+    path = os.path.join(ROOT, "tests", "golden", workload + ".txt")
+    if not os.path.exists(path):
+        return None
+    from tests.golden.golden_io import read_counts
+    return read_counts(path)
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle timed on this host (cpu_baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+
+def time_oracle(g, k: int, roots):
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    oracle.table(k)
+    t = time.perf_counter()
+    c = oracle.count(g.n, g.src, g.dst, k, threads=threads, roots=roots)
+    dt = time.perf_counter() - t
+    return int(c.sum()), dt, threads
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    make, k = WORKLOADS[args.workload]
+    g = make()
+    roots = (0, min(g.n, args.reference_roots))
+    times, units = [], 0
+    threads = 1
+    for i in range(args.warmup + args.steps):
+        units, dt, threads = time_oracle(g, k, roots)
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = units * len(times) / total
+    sample = f"ESU roots {roots[0]}..{roots[1] - 1} of {g.n} ({units} subgraphs per step)"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * total / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "k": k, "n": g.n, "m": g.m},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+
+    from paper_1203_3415_gb300 import build as lib_build
+    if rank == 0 or world == 1:
+        lib_build.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_1203_3415_gb300 as acc
+
+    make, k = WORKLOADS[args.workload]
+    g = make()
+    rowptr_np, col_np = g.csr()
+    rowptr = torch.from_numpy(rowptr_np).to(dev)
+    col = torch.from_numpy(col_np).to(dev)
+    counts = torch.zeros(acc.NUM_CLASSES[k], dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    counter = acc.Counter(local)
+    counter.prepare(k)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        counter.count(rowptr, col, g.n, k, counts=counts, status=status, stream=stream)
+    torch.cuda.synchronize(dev)
+    if int(status.item()) != 0:
+        raise RuntimeError(f"count failed: {acc.acc_strerror(int(status.item()))}")
+    stats = counter.last_stats()
+    n_k = int(counts.sum().item())
+    gold = golden_counts(args.workload)
+    parity = None
+    if gold is not None:
+        parity = bool(np.array_equal(counts.cpu().numpy(), gold[1]))
+
+    # timed region: K steps, each bracketed by events on the launching stream;
+    # L2 flushed (256 MiB write) between steps, outside the events
+    counter.set_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    build_ms, enum_ms = [], []
+    sampler = ClockSampler(local) if rank == 0 else None
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.start()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        counter.count(rowptr, col, g.n, k, counts=counts, status=status, stream=stream)
+        ev[i][1].record(stream)
+        b, e = counter.last_timing()
+        build_ms.append(b)
+        enum_ms.append(e)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    counter.set_timing(False)
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    local_s = sum(step_ms) / 1000.0
+    if int(status.item()) != 0 or int(counts.sum().item()) != n_k:
+        raise RuntimeError("timed steps disagree with the warm-up result")
+
+    max_s = reduce_max(dist, local_s, dev)
+    units = reduce_sum(dist, float(n_k) * args.steps, dev)
+    value = whole_job_rate(units, max_s)
+
+    # end to end through the public host-buffer entry point: pinned host
+    # arrays in, int64 counts out, copies inside the timed region
+    h_rowptr = torch.from_numpy(rowptr_np).pin_memory()
+    h_col = torch.from_numpy(col_np).pin_memory()
+    h_counts = torch.zeros(acc.NUM_CLASSES[k], dtype=torch.int64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+    counter.count_host(h_rowptr, h_col, g.n, k, counts=h_counts)
+    e2e_t = 0.0
+    for _ in range(e2e_steps):
+        flush.fill_(3)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        counter.count_host(h_rowptr, h_col, g.n, k, counts=h_counts)
+        e2e_t += time.perf_counter() - t0
+    if int(h_counts.sum().item()) != n_k:
+        raise RuntimeError("host-buffer count differs from the device count")
+    e2e_max = reduce_max(dist, e2e_t, dev)
+    e2e_units = reduce_sum(dist, float(n_k) * e2e_steps, dev)
+
+    if rank != 0:
+        counter.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    props = torch.cuda.get_device_properties(dev)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    sm_max = 2070.0
+    peak_src = "recipe nominal max SM clock 2070 MHz"
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as f:
+            sm_max = float(json.load(f).get("sm_max_mhz", sm_max))
+        peak_src = "SM clock from MEASURED_PEAKS.json"
+    # issue peak: SMs x 4 schedulers x 32 lanes per clock
+    peak_gops = props.multi_processor_count * 4 * 32 * sm_max * 1e6 / 1e9
+    enum_s = statistics.mean(enum_ms) / 1000.0
+    achieved = ops_per_subgraph(k) * n_k / enum_s / 1e9
+    traffic = profiled_traffic(args.workload)
+
+    # CPU baseline: the oracle on this host's cores, the whole workload
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        units_cpu, dt, threads = time_oracle(g, k, (0, g.n))
+        cpu = {"value": units_cpu / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"the whole workload, all {g.n} ESU roots ({units_cpu} subgraphs), one pass, "
+                         f"{dt:.2f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * max_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "k": k, "n": g.n, "m": g.m, "subgraphs_per_step": n_k,
+                   "l2": "flushed between timed steps (256 MiB device write)",
+                   "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
+                     "frac": achieved / peak_gops, "traffic": traffic,
+                     "kernel": f"k_enum<{k}> (phase 1 + phase 2)",
+                     "ops_per_subgraph": ops_per_subgraph(k), "peak_source": peak_src},
+        "cpu_baseline": cpu,
+        "e2e": {"value": whole_job_rate(e2e_units, e2e_max), "unit": UNIT,
+                "h2d_bytes_per_step": int(rowptr_np.nbytes + col_np.nbytes),
+                "d2h_bytes_per_step": int(acc.NUM_CLASSES[k] * 8)},
+        "gpu_launches": int(stats["launches"]) * args.steps,
+        "clocks": clocks,
+        "stages_ms": {"build": statistics.mean(build_ms), "enumerate": enum_ms and statistics.mean(enum_ms),
+                      "step_median": statistics.median(step_ms)},
+        "parity_vs_stored_oracle_counts": parity,
+        "work": {"chunks": stats["chunks"], "undirected_edges": stats["undirected_edges"],
+                 "max_degree": stats["max_degree"], "blocks": stats["blocks"]},
+    }
+    print(json.dumps(line), flush=True)
+    counter.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--reference-roots", type=int, default=1000,
+                    help="reference arm: ESU roots per step (bounded CPU sample)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,169 @@
+/*
+ * acc_motif.h — C ABI of a GB300 (sm_103a) library that counts the connected
+ * induced k-vertex subgraphs of a directed graph, k = 3, 4, 5, grouped by
+ * isomorphism class.
+ *
+ * The operation is the one the paper states as Problems Motifs-3, Motifs-4
+ * and Motifs-5 (Background section, "Problem statement"): given a directed
+ * graph G(V,E), count the connected induced subgraphs of size k, grouped by
+ * the 13, 199 or 9364 isomorphism classes of connected k-vertex digraphs.
+ * "Connected" is taken in the undirected version G* of G (Notation section:
+ * {u,v} is an edge of G* iff (u,v) or (v,u) is an arc of G), i.e. weak
+ * connectivity.  Counts are exact int64.
+ *
+ * Class numbering (the paper's histogram positions are arbitrary): the
+ * adjacency code of an ordered vertex tuple (w_0..w_{k-1}) sets bit
+ * i*(k-1) + (j - [j > i]) iff the arc w_i -> w_j exists; the canonical code
+ * of a digraph is the minimum code over its k! vertex orders; class c is the
+ * c-th smallest canonical code among connected k-vertex digraphs.
+ * acc_motif_class_code() returns that code so callers can name classes.
+ *
+ * Conventions for every entry point:
+ *  - Return value: ACC_OK (0) or a negative ACC_ERR_* code.  No C++
+ *    exception crosses this interface.
+ *  - "device" pointers are CUDA device (or managed) memory of the context's
+ *    device; "host" pointers are ordinary (preferably pinned) host memory.
+ *    The caller owns every pointer it passes; the library never frees or
+ *    keeps one after the call returns.
+ *  - stream is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is stream-ordered: results are valid once the caller
+ *    synchronises the stream, unless the entry point says it synchronises.
+ *  - A context is not thread-safe: use one per host thread, or lock around it.
+ *    Calls on one context must not overlap on the GPU (they share its
+ *    workspace); issue them on one stream or synchronise in between.
+ */
+#ifndef ACC_MOTIF_H
+#define ACC_MOTIF_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ACC_API __attribute__((visibility("default")))
+#else
+#define ACC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define ACC_OK 0
+#define ACC_ERR_K (-1)        /* k is not 3, 4 or 5 */
+#define ACC_ERR_INPUT (-2)    /* malformed graph: bad rowptr, column out of range, self-loop, bad size */
+#define ACC_ERR_NOMEM (-3)    /* a device or pinned-host allocation failed */
+#define ACC_ERR_TIMEOUT (-4)  /* a bounded device wait gave up */
+#define ACC_ERR_OVERFLOW (-5) /* a count or an index would not fit its type */
+#define ACC_ERR_CUDA (-6)     /* a CUDA runtime call failed */
+#define ACC_ERR_ARG (-7)      /* null pointer, bad handle or bad option */
+#define ACC_ERR_TOO_LARGE (-8) /* n above ACC_MAX_N (dense pair-state matrix limit) */
+#define ACC_ERR_INTERNAL (-9)  /* an internal consistency check failed (a library bug) */
+
+/* Largest vertex count the dense n x n pair-state matrix is built for
+ * (n^2/4 bytes: 4 GiB at this limit). */
+#define ACC_MAX_N 131072
+
+typedef struct acc_ctx acc_ctx;
+
+/* Message for an error code (static string, never NULL). */
+ACC_API const char *acc_strerror(int code);
+
+/* 13, 199 or 9364 for k = 3, 4, 5 (Problems Motifs-3/4/5); ACC_ERR_K otherwise. */
+ACC_API int acc_motif_num_classes(int k);
+
+/*
+ * Create a context on CUDA device `device` (the device is made current for
+ * the calling thread).  The context owns the code -> class tables (built on
+ * the device on first use of each k) and a grow-only workspace.
+ * *out receives the handle.  Errors: ACC_ERR_ARG (out NULL), ACC_ERR_CUDA.
+ */
+ACC_API int acc_ctx_create(acc_ctx **out, int device);
+
+/* Release a context and all its device memory (NULL is a no-op).  Waits
+ * for the context's outstanding work. */
+ACC_API void acc_ctx_destroy(acc_ctx *ctx);
+
+/*
+ * Build (once) and cache the code -> class table for k on the context's
+ * device, stream-ordered on `stream`, then wait for it.  Counting calls do
+ * this themselves on first use; call it ahead to keep the one-time cost
+ * (largest for k = 5: 2^20 codes x 120 relabellings) out of a timed region.
+ * Errors: ACC_ERR_ARG, ACC_ERR_K, ACC_ERR_NOMEM, ACC_ERR_CUDA.
+ */
+ACC_API int acc_motif_prepare(acc_ctx *ctx, int k, void *stream);
+
+/*
+ * Count the connected induced k-subgraphs of one directed graph by class
+ * (Problems Motifs-3/4/5).
+ *
+ *  d_rowptr  device int64[n+1]: out-CSR row offsets, d_rowptr[0] = 0,
+ *            non-decreasing, d_rowptr[n] = m.
+ *  d_col     device int32[m]: arc targets; row v lists the heads of arcs
+ *            v -> u.  Any order within a row; repeated arcs count once
+ *            (E is a set).  A self-loop or a target outside [0, n) is an
+ *            input error.
+ *  n, m      vertex and arc counts, 0 <= n <= ACC_MAX_N, 0 <= m < 2^31.
+ *  k         3, 4 or 5.
+ *  stream    cudaStream_t (void*), see above.
+ *  d_counts  device int64[acc_motif_num_classes(k)], overwritten.
+ *  d_status  device int32[1] or NULL.  When non-NULL the call is fully
+ *            asynchronous: it returns after enqueueing, and *d_status
+ *            receives ACC_OK or the error the device found (ACC_ERR_INPUT for
+ *            a malformed graph, in which case d_counts is unspecified).  When
+ *            NULL the call waits for its own work and returns that status.
+ *
+ * Host-checked errors (returned before anything is enqueued): ACC_ERR_ARG,
+ * ACC_ERR_K, ACC_ERR_INPUT (negative sizes), ACC_ERR_TOO_LARGE,
+ * ACC_ERR_NOMEM, ACC_ERR_CUDA.
+ */
+ACC_API int acc_motif_count(acc_ctx *ctx, const int64_t *d_rowptr, const int32_t *d_col, int32_t n,
+                    int64_t m, int k, void *stream, int64_t *d_counts, int32_t *d_status);
+
+/*
+ * The same count with host arrays: copies h_rowptr (int64[n+1]) and h_col
+ * (int32[m]) to the device on the context's own stream, counts, copies the
+ * int64[num_classes(k)] result to h_counts and waits.  Pinned host memory
+ * gives the fastest copies.  Returns the status of the whole call.
+ */
+ACC_API int acc_motif_count_host(acc_ctx *ctx, const int64_t *h_rowptr, const int32_t *h_col, int32_t n,
+                         int64_t m, int k, int64_t *h_counts);
+
+/* Canonical adjacency code of class cls (0 <= cls < num_classes(k)). */
+ACC_API int acc_motif_class_code(acc_ctx *ctx, int k, int32_t cls, uint32_t *code);
+
+/* Class of an adjacency code (< 2^(k(k-1))); *cls = -1 for a code whose
+ * digraph is not weakly connected. */
+ACC_API int acc_motif_classify_code(acc_ctx *ctx, int k, uint32_t code, int32_t *cls);
+
+/* Copy the whole code -> class table for k to host int16[2^(k(k-1))]
+ * (-1 = disconnected). */
+ACC_API int acc_motif_copy_table(acc_ctx *ctx, int k, int16_t *h_table);
+
+/*
+ * Copy the launch and workload statistics of the context's last
+ * acc_motif_count call to host int64[ACC_STATS_LEN]; waits for the device
+ * (call it after that count has completed):
+ *   [0] kernels the call launched, [1] base work units (vertices for k = 3,
+ *   neighbour-list positions for k = 4, 5), [2] chunks heavy units were split
+ *   into, [3] undirected edges |E*|, [4] largest degree in G*, [5] blocks of
+ *   each enumeration launch.
+ */
+#define ACC_STATS_LEN 6
+ACC_API int acc_motif_last_stats(acc_ctx *ctx, int64_t *h_stats);
+
+/*
+ * Stage timing.  With timing on (on != 0), every acc_motif_count records CUDA
+ * events on its stream before the graph build, between build and
+ * enumeration, and after the enumeration.  acc_motif_last_timing waits for
+ * the last call's end event and writes h_ms[0] = graph-build stage,
+ * h_ms[1] = enumeration stage (both launches), in milliseconds.
+ * Errors: ACC_ERR_ARG (timing off or no count yet), ACC_ERR_CUDA.
+ */
+ACC_API int acc_ctx_set_timing(acc_ctx *ctx, int on);
+ACC_API int acc_motif_last_timing(acc_ctx *ctx, float *h_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACC_MOTIF_H */

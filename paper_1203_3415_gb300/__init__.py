@@ -1,0 +1,237 @@
+"""Python binding of libaccmotif.so, the GB300 connected-k-subgraph counter.
+
+Argument marshalling only: every function below forwards to the C ABI entry
+point of the same name (declared in include/acc_motif.h); all the work runs in
+the library's CUDA kernels.  There is no CPU fallback: if the library is not
+built, the first call raises ImportError.
+
+The ``Counter`` class is a convenience around one context for callers holding
+PyTorch CUDA tensors (PyTorch provides device memory and streams only).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaccmotif.so")
+
+ACC_OK = 0
+ACC_ERR_K = -1
+ACC_ERR_INPUT = -2
+ACC_ERR_NOMEM = -3
+ACC_ERR_TIMEOUT = -4
+ACC_ERR_OVERFLOW = -5
+ACC_ERR_CUDA = -6
+ACC_ERR_ARG = -7
+ACC_ERR_TOO_LARGE = -8
+ACC_ERR_INTERNAL = -9
+ACC_MAX_N = 131072
+ACC_STATS_LEN = 6
+
+NUM_CLASSES = {3: 13, 4: 199, 5: 9364}
+
+# every symbol include/acc_motif.h declares, in declaration order
+EXPORTS = (
+    "acc_strerror", "acc_motif_num_classes", "acc_ctx_create", "acc_ctx_destroy", "acc_motif_prepare",
+    "acc_motif_count", "acc_motif_count_host", "acc_motif_class_code", "acc_motif_classify_code",
+    "acc_motif_copy_table", "acc_motif_last_stats", "acc_ctx_set_timing", "acc_motif_last_timing",
+)
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built: run paper_1203_3415_gb300.build.build() "
+                          f"(the counter has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.acc_strerror.argtypes = [ctypes.c_int]
+    lib.acc_strerror.restype = ctypes.c_char_p
+    lib.acc_motif_num_classes.argtypes = [ctypes.c_int]
+    lib.acc_ctx_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+    lib.acc_ctx_destroy.argtypes = [vp]
+    lib.acc_ctx_destroy.restype = None
+    lib.acc_motif_prepare.argtypes = [vp, ctypes.c_int, vp]
+    lib.acc_motif_count.argtypes = [vp, vp, vp, i32, i64, ctypes.c_int, vp, vp, vp]
+    lib.acc_motif_count_host.argtypes = [vp, vp, vp, i32, i64, ctypes.c_int, vp]
+    lib.acc_motif_class_code.argtypes = [vp, ctypes.c_int, i32, ctypes.POINTER(ctypes.c_uint32)]
+    lib.acc_motif_classify_code.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(i32)]
+    lib.acc_motif_copy_table.argtypes = [vp, ctypes.c_int, vp]
+    lib.acc_motif_last_stats.argtypes = [vp, vp]
+    lib.acc_ctx_set_timing.argtypes = [vp, ctypes.c_int]
+    lib.acc_motif_last_timing.argtypes = [vp, vp]
+    return lib
+
+
+_lib_handle = None
+
+
+def _L():
+    """The loaded library; raises ImportError when it is not built."""
+    global _lib_handle
+    if _lib_handle is None:
+        _lib_handle = _load()
+    return _lib_handle
+
+
+class MotifError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {acc_strerror(code)} ({code})" if what else f"{acc_strerror(code)} ({code})")
+
+
+def _check(rc: int, what: str) -> int:
+    if rc != ACC_OK:
+        raise MotifError(rc, what)
+    return rc
+
+
+# ---------------------------------------------------------------------------
+# C ABI, one function per entry point (pointers as Python ints)
+# ---------------------------------------------------------------------------
+
+def acc_strerror(code: int) -> str:
+    return _L().acc_strerror(code).decode()
+
+
+def acc_motif_num_classes(k: int) -> int:
+    return _L().acc_motif_num_classes(k)
+
+
+def acc_ctx_create(device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(_L().acc_ctx_create(ctypes.byref(h), device), "acc_ctx_create")
+    return h.value
+
+
+def acc_ctx_destroy(ctx: int) -> None:
+    _L().acc_ctx_destroy(ctx)
+
+
+def acc_motif_prepare(ctx: int, k: int, stream: int = 0) -> int:
+    return _L().acc_motif_prepare(ctx, k, stream)
+
+
+def acc_motif_count(ctx: int, d_rowptr: int, d_col: int, n: int, m: int, k: int, stream: int,
+                    d_counts: int, d_status: int | None) -> int:
+    return _L().acc_motif_count(ctx, d_rowptr, d_col, n, m, k, stream, d_counts, d_status)
+
+
+def acc_motif_count_host(ctx: int, h_rowptr: int, h_col: int, n: int, m: int, k: int, h_counts: int) -> int:
+    return _L().acc_motif_count_host(ctx, h_rowptr, h_col, n, m, k, h_counts)
+
+
+def acc_motif_class_code(ctx: int, k: int, cls: int) -> int:
+    out = ctypes.c_uint32()
+    _check(_L().acc_motif_class_code(ctx, k, cls, ctypes.byref(out)), "acc_motif_class_code")
+    return out.value
+
+
+def acc_motif_classify_code(ctx: int, k: int, code: int) -> int:
+    out = ctypes.c_int32()
+    _check(_L().acc_motif_classify_code(ctx, k, code, ctypes.byref(out)), "acc_motif_classify_code")
+    return out.value
+
+
+def acc_motif_copy_table(ctx: int, k: int, h_table: int) -> int:
+    return _L().acc_motif_copy_table(ctx, k, h_table)
+
+
+def acc_motif_last_stats(ctx: int, h_stats: int) -> int:
+    return _L().acc_motif_last_stats(ctx, h_stats)
+
+
+def acc_ctx_set_timing(ctx: int, on: int) -> int:
+    return _L().acc_ctx_set_timing(ctx, on)
+
+
+def acc_motif_last_timing(ctx: int, h_ms: int) -> int:
+    return _L().acc_motif_last_timing(ctx, h_ms)
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper for PyTorch tensors
+# ---------------------------------------------------------------------------
+
+class Counter:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self.ctx = acc_ctx_create(device)
+
+    def close(self):
+        if self.ctx:
+            acc_ctx_destroy(self.ctx)
+            self.ctx = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def prepare(self, k: int, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        _check(acc_motif_prepare(self.ctx, k, s.cuda_stream), "acc_motif_prepare")
+
+    def count(self, rowptr, col, n: int, k: int, counts=None, status=None, stream=None):
+        """Counts of the graph given as CUDA tensors rowptr (int64[n+1]) and col
+        (int32[m]).  Returns the int64 counts tensor.  With ``status`` (a CUDA
+        int32 tensor of one element) the call does not wait; else it waits and
+        raises MotifError on any error."""
+        import torch
+        assert rowptr.dtype == torch.int64 and col.dtype == torch.int32
+        assert rowptr.is_cuda and col.is_cuda and rowptr.is_contiguous() and col.is_contiguous()
+        s = stream if stream is not None else torch.cuda.current_stream(rowptr.device)
+        if counts is None:
+            counts = torch.empty(NUM_CLASSES[k], dtype=torch.int64, device=rowptr.device)
+        rc = acc_motif_count(self.ctx, rowptr.data_ptr(), col.data_ptr() if col.numel() else 0, n,
+                             col.numel(), k, s.cuda_stream, counts.data_ptr(),
+                             status.data_ptr() if status is not None else None)
+        _check(rc, "acc_motif_count")
+        return counts
+
+    def count_host(self, rowptr, col, n: int, k: int, counts=None):
+        """Counts from host arrays (numpy or CPU tensors; pinned is fastest)."""
+        import numpy as np
+        rowptr_np = np.ascontiguousarray(rowptr, dtype=np.int64) if not hasattr(rowptr, "data_ptr") else None
+        col_np = np.ascontiguousarray(col, dtype=np.int32) if not hasattr(col, "data_ptr") else None
+        rp = rowptr_np.ctypes.data if rowptr_np is not None else rowptr.data_ptr()
+        cp = col_np.ctypes.data if col_np is not None else col.data_ptr()
+        m = len(col_np) if col_np is not None else col.numel()
+        if counts is None:
+            counts = np.zeros(NUM_CLASSES[k], dtype=np.int64)
+        hp = counts.ctypes.data if isinstance(counts, np.ndarray) else counts.data_ptr()
+        _check(acc_motif_count_host(self.ctx, rp, cp if m else 0, n, m, k, hp), "acc_motif_count_host")
+        return counts
+
+    def table(self, k: int):
+        import numpy as np
+        out = np.empty(1 << (k * (k - 1)), dtype=np.int16)
+        _check(acc_motif_copy_table(self.ctx, k, out.ctypes.data), "acc_motif_copy_table")
+        return out
+
+    def class_code(self, k: int, cls: int) -> int:
+        return acc_motif_class_code(self.ctx, k, cls)
+
+    def classify_code(self, k: int, code: int) -> int:
+        return acc_motif_classify_code(self.ctx, k, code)
+
+    def set_timing(self, on: bool = True):
+        _check(acc_ctx_set_timing(self.ctx, 1 if on else 0), "acc_ctx_set_timing")
+
+    def last_timing(self):
+        """(build_ms, enumerate_ms) of the last count (timing must be on)."""
+        import numpy as np
+        out = np.zeros(2, dtype=np.float32)
+        _check(acc_motif_last_timing(self.ctx, out.ctypes.data), "acc_motif_last_timing")
+        return float(out[0]), float(out[1])
+
+    def last_stats(self):
+        import numpy as np
+        out = np.zeros(ACC_STATS_LEN, dtype=np.int64)
+        _check(acc_motif_last_stats(self.ctx, out.ctypes.data), "acc_motif_last_stats")
+        return {"launches": int(out[0]), "units": int(out[1]), "chunks": int(out[2]),
+                "undirected_edges": int(out[3]), "max_degree": int(out[4]), "blocks": int(out[5])}

@@ -1,0 +1,406 @@
+// C ABI: context, workspace and the counting entry points.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+
+using namespace acc;
+
+struct acc_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t own = nullptr;  // stream of the host-buffer entry points
+
+    // code -> class tables per k
+    int16_t *lut[6] = {};
+    uint32_t *class_code_dev[6] = {};
+    int16_t *lut_host[6] = {};
+    uint32_t *class_code_host[6] = {};
+
+    // per-graph workspace (grow-only)
+    uint32_t *state = nullptr;
+    size_t state_words = 0;
+    int *deg = nullptr, *lo = nullptr;
+    long long *nptr = nullptr;
+    size_t n_cap = 0;
+    uint32_t *nbr = nullptr;
+    size_t nbr_cap = 0;
+    GraphInfo *info = nullptr;
+    uint4 *queue = nullptr;
+    unsigned long long queue_cap = 0;
+    uint32_t *scratch = nullptr;
+    size_t scratch_cap = 0;
+    int *status_dev = nullptr;
+    int *status_host = nullptr;  // pinned
+
+    // host-buffer entry point
+    long long *h2d_rowptr = nullptr;
+    size_t h2d_rowptr_cap = 0;
+    int *h2d_col = nullptr;
+    size_t h2d_col_cap = 0;
+    unsigned long long *h2d_counts = nullptr;
+
+    // stage timing
+    bool timing = false;
+    bool timed_call = false;
+    cudaEvent_t ev[3] = {};
+
+    // statistics of the last count
+    int last_launches = 0;
+    int last_k = 0;
+    long long last_units = 0;
+    int last_blocks = 0;
+};
+
+namespace {
+
+constexpr unsigned long long kQueueCap = 1ull << 22;
+
+bool ok(cudaError_t e) { return e == cudaSuccess; }
+
+template <typename T>
+int grow(T **p, size_t *cap, size_t need) {
+    if (need <= *cap && *p) return ACC_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    const size_t alloc = need + need / 4 + 64;
+    if (!ok(cudaMalloc((void **)p, alloc * sizeof(T)))) {
+        cudaGetLastError();
+        *p = nullptr;
+        return ACC_ERR_NOMEM;
+    }
+    *cap = alloc;
+    return ACC_OK;
+}
+
+bool valid_k(int k) { return k >= 3 && k <= 5; }
+
+int ensure_lut(acc_ctx *c, int k, cudaStream_t s) {
+    if (c->lut[k]) return ACC_OK;
+    const size_t ncodes = size_t(1) << code_bits(k);
+    const int ncls = num_classes(k);
+    uint32_t *canon = nullptr;
+    int *rank = nullptr;
+    int16_t *lut = nullptr;
+    uint32_t *cc = nullptr;
+    int rc = ACC_ERR_NOMEM;
+    c->lut_host[k] = new (std::nothrow) int16_t[ncodes];
+    c->class_code_host[k] = new (std::nothrow) uint32_t[ncls];
+    if (!c->lut_host[k] || !c->class_code_host[k]) goto fail;
+    if (!ok(cudaMalloc(&canon, ncodes * 4)) || !ok(cudaMalloc(&rank, ncodes * 4)) ||
+        !ok(cudaMalloc(&lut, ncodes * 2)) || !ok(cudaMalloc(&cc, ncls * 4)))
+        goto fail;
+    rc = launch_build_lut(k, canon, rank, lut, cc, s);
+    if (rc < 0) goto fail;
+    rc = ACC_ERR_CUDA;
+    if (!ok(cudaMemcpyAsync(c->lut_host[k], lut, ncodes * 2, cudaMemcpyDeviceToHost, s))) goto fail;
+    if (!ok(cudaMemcpyAsync(c->class_code_host[k], cc, ncls * 4, cudaMemcpyDeviceToHost, s))) goto fail;
+    if (!ok(cudaStreamSynchronize(s))) goto fail;
+    {
+        // the table must use every class index exactly up to ncls - 1
+        int mx = -1;
+        for (size_t i = 0; i < ncodes; i++) {
+            if (c->lut_host[k][i] < -1) mx = 1 << 20;
+            if (c->lut_host[k][i] > mx) mx = c->lut_host[k][i];
+        }
+        if (mx != ncls - 1) {
+            rc = ACC_ERR_INTERNAL;
+            goto fail;
+        }
+    }
+    cudaFree(canon);
+    cudaFree(rank);
+    c->lut[k] = lut;
+    c->class_code_dev[k] = cc;
+    return ACC_OK;
+fail:
+    cudaGetLastError();
+    cudaFree(canon);
+    cudaFree(rank);
+    cudaFree(lut);
+    cudaFree(cc);
+    delete[] c->lut_host[k];
+    delete[] c->class_code_host[k];
+    c->lut_host[k] = nullptr;
+    c->class_code_host[k] = nullptr;
+    return rc;
+}
+
+int ensure_workspace(acc_ctx *c, int n, long long m, int k) {
+    const long long pitch = state_pitch(n);
+    int rc;
+    if ((rc = grow(&c->state, &c->state_words, (size_t)n * pitch + 4))) return rc;
+    if ((size_t)n + 1 > c->n_cap || !c->deg) {
+        size_t a = 0, b = 0, d = 0;
+        cudaFree(c->deg);
+        cudaFree(c->lo);
+        cudaFree(c->nptr);
+        c->deg = c->lo = nullptr;
+        c->nptr = nullptr;
+        c->n_cap = 0;
+        if ((rc = grow(&c->deg, &a, (size_t)n + 1))) return rc;
+        if ((rc = grow(&c->lo, &b, (size_t)n + 1))) return rc;
+        if ((rc = grow(&c->nptr, &d, (size_t)n + 1))) return rc;
+        c->n_cap = a;
+    }
+    if ((rc = grow(&c->nbr, &c->nbr_cap, (size_t)(2 * m) + 1))) return rc;
+    if (!c->info) {
+        if (!ok(cudaMalloc(&c->info, sizeof(GraphInfo)))) return ACC_ERR_NOMEM;
+        if (!ok(cudaMemset(c->info, 0, sizeof(GraphInfo)))) return ACC_ERR_CUDA;
+    }
+    if (!c->queue) {
+        if (!ok(cudaMalloc(&c->queue, kQueueCap * sizeof(uint4)))) return ACC_ERR_NOMEM;
+        c->queue_cap = kQueueCap;
+    }
+    if (!c->status_dev) {
+        if (!ok(cudaMalloc(&c->status_dev, sizeof(int)))) return ACC_ERR_NOMEM;
+    }
+    const int warps = enum_grid_warps(k, c->num_sms);
+    if (warps < 0) return warps;
+    const size_t per_warp = 2 * (((size_t)n + 32 + 31) & ~size_t(31));
+    if ((rc = grow(&c->scratch, &c->scratch_cap, per_warp * (size_t)warps))) return rc;
+    return ACC_OK;
+}
+
+int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n, int64_t m, int k,
+               cudaStream_t s, int64_t *counts, int32_t *status_user) {
+    if (!c || !rowptr || !counts || (m > 0 && !col)) return ACC_ERR_ARG;
+    if (!valid_k(k)) return ACC_ERR_K;
+    if (n < 0 || m < 0 || m >= (1ll << 31)) return ACC_ERR_INPUT;
+    if (n > ACC_MAX_N) return ACC_ERR_TOO_LARGE;
+    if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
+    int rc = ensure_lut(c, k, s);
+    if (rc) return rc;
+    if ((rc = ensure_workspace(c, n, m, k))) return rc;
+    int *status = status_user ? status_user : c->status_dev;
+    const long long pitch = state_pitch(n);
+    int launches = 0;
+    c->timed_call = c->timing;
+    if (c->timing && !ok(cudaEventRecord(c->ev[0], s))) return ACC_ERR_CUDA;
+    rc = launch_build_graph(reinterpret_cast<const long long *>(rowptr), col, n, m, c->state, pitch, c->deg, c->lo,
+                            c->nptr, c->nbr, c->info, status, reinterpret_cast<unsigned long long *>(counts),
+                            num_classes(k), c->num_sms, s);
+    if (rc < 0) return rc;
+    launches += rc;
+    if (c->timing && !ok(cudaEventRecord(c->ev[1], s))) return ACC_ERR_CUDA;
+    EnumArgs a;
+    a.state = c->state;
+    a.pitch = pitch;
+    a.deg = c->deg;
+    a.lo = c->lo;
+    a.nptr = c->nptr;
+    a.nbr = c->nbr;
+    a.lut = c->lut[k];
+    a.n = n;
+    a.info = c->info;
+    a.queue = c->queue;
+    a.queue_cap = c->queue_cap;
+    a.scratch = c->scratch;
+    a.scratch_per_warp = 2 * (((long long)n + 32 + 31) & ~31LL);
+    a.counts = reinterpret_cast<unsigned long long *>(counts);
+    a.status = status;
+    if (n > 0) {
+        rc = launch_enumerate(k, a, c->num_sms, s);
+        if (rc < 0) return rc;
+        launches += rc;
+    }
+    if (c->timing && !ok(cudaEventRecord(c->ev[2], s))) return ACC_ERR_CUDA;
+    c->last_launches = launches;
+    c->last_k = k;
+    c->last_units = n;
+    c->last_blocks = enum_grid_warps(k, c->num_sms) / kWarpsPerBlock;
+    if (status_user) return ACC_OK;
+    if (!ok(cudaMemcpyAsync(c->status_host, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost, s)))
+        return ACC_ERR_CUDA;
+    if (!ok(cudaStreamSynchronize(s))) return ACC_ERR_CUDA;
+    return *c->status_host;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *acc_strerror(int code) {
+    switch (code) {
+    case ACC_OK: return "ok";
+    case ACC_ERR_K: return "k must be 3, 4 or 5";
+    case ACC_ERR_INPUT: return "malformed graph (rowptr, column range, self-loop or size)";
+    case ACC_ERR_NOMEM: return "device or pinned-host allocation failed";
+    case ACC_ERR_TIMEOUT: return "a bounded device wait gave up";
+    case ACC_ERR_OVERFLOW: return "a count or an index would not fit its type";
+    case ACC_ERR_CUDA: return "a CUDA runtime call failed";
+    case ACC_ERR_ARG: return "null pointer, bad handle or bad option";
+    case ACC_ERR_TOO_LARGE: return "n above ACC_MAX_N";
+    case ACC_ERR_INTERNAL: return "internal consistency check failed";
+    default: return "unknown error";
+    }
+}
+
+int acc_motif_num_classes(int k) { return valid_k(k) ? num_classes(k) : ACC_ERR_K; }
+
+int acc_ctx_create(acc_ctx **out, int device) {
+    if (!out) return ACC_ERR_ARG;
+    *out = nullptr;
+    acc_ctx *c = new (std::nothrow) acc_ctx();
+    if (!c) return ACC_ERR_NOMEM;
+    c->device = device;
+    if (!ok(cudaSetDevice(device)) ||
+        !ok(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device)) ||
+        !ok(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking)) ||
+        !ok(cudaMallocHost(&c->status_host, sizeof(int)))) {
+        cudaGetLastError();
+        acc_ctx_destroy(c);
+        return ACC_ERR_CUDA;
+    }
+    *out = c;
+    return ACC_OK;
+}
+
+void acc_ctx_destroy(acc_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (int k = 0; k < 6; k++) {
+        cudaFree(c->lut[k]);
+        cudaFree(c->class_code_dev[k]);
+        delete[] c->lut_host[k];
+        delete[] c->class_code_host[k];
+    }
+    cudaFree(c->state);
+    cudaFree(c->deg);
+    cudaFree(c->lo);
+    cudaFree(c->nptr);
+    cudaFree(c->nbr);
+    cudaFree(c->info);
+    cudaFree(c->queue);
+    cudaFree(c->scratch);
+    cudaFree(c->status_dev);
+    cudaFree(c->h2d_rowptr);
+    cudaFree(c->h2d_col);
+    cudaFree(c->h2d_counts);
+    for (int i = 0; i < 3; i++)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->status_host) cudaFreeHost(c->status_host);
+    if (c->own) cudaStreamDestroy(c->own);
+    cudaGetLastError();
+    delete c;
+}
+
+int acc_motif_prepare(acc_ctx *c, int k, void *stream) {
+    if (!c) return ACC_ERR_ARG;
+    if (!valid_k(k)) return ACC_ERR_K;
+    if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_lut(c, k, s);
+    if (rc) return rc;
+    return ok(cudaStreamSynchronize(s)) ? ACC_OK : ACC_ERR_CUDA;
+}
+
+int acc_motif_count(acc_ctx *c, const int64_t *d_rowptr, const int32_t *d_col, int32_t n, int64_t m, int k,
+                    void *stream, int64_t *d_counts, int32_t *d_status) {
+    return count_impl(c, d_rowptr, d_col, n, m, k, (cudaStream_t)stream, d_counts, d_status);
+}
+
+int acc_motif_count_host(acc_ctx *c, const int64_t *h_rowptr, const int32_t *h_col, int32_t n, int64_t m, int k,
+                         int64_t *h_counts) {
+    if (!c || !h_rowptr || !h_counts || (m > 0 && !h_col)) return ACC_ERR_ARG;
+    if (!valid_k(k)) return ACC_ERR_K;
+    if (n < 0 || m < 0 || m >= (1ll << 31)) return ACC_ERR_INPUT;
+    if (n > ACC_MAX_N) return ACC_ERR_TOO_LARGE;
+    if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
+    int rc;
+    size_t cnt_cap = c->h2d_counts ? 9364 : 0;
+    if ((rc = grow(&c->h2d_rowptr, &c->h2d_rowptr_cap, (size_t)n + 1))) return rc;
+    if ((rc = grow(&c->h2d_col, &c->h2d_col_cap, (size_t)m + 1))) return rc;
+    if ((rc = grow(&c->h2d_counts, &cnt_cap, 9364))) return rc;
+    cudaStream_t s = c->own;
+    if (!ok(cudaMemcpyAsync(c->h2d_rowptr, h_rowptr, ((size_t)n + 1) * 8, cudaMemcpyHostToDevice, s)))
+        return ACC_ERR_CUDA;
+    if (m > 0 && !ok(cudaMemcpyAsync(c->h2d_col, h_col, (size_t)m * 4, cudaMemcpyHostToDevice, s)))
+        return ACC_ERR_CUDA;
+    rc = count_impl(c, reinterpret_cast<const int64_t *>(c->h2d_rowptr), c->h2d_col, n, m, k, s,
+                    reinterpret_cast<int64_t *>(c->h2d_counts), c->status_dev);
+    if (rc) return rc;
+    if (!ok(cudaMemcpyAsync(h_counts, c->h2d_counts, (size_t)num_classes(k) * 8, cudaMemcpyDeviceToHost, s)))
+        return ACC_ERR_CUDA;
+    if (!ok(cudaMemcpyAsync(c->status_host, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost, s)))
+        return ACC_ERR_CUDA;
+    if (!ok(cudaStreamSynchronize(s))) return ACC_ERR_CUDA;
+    return *c->status_host;
+}
+
+int acc_motif_class_code(acc_ctx *c, int k, int32_t cls, uint32_t *code) {
+    if (!c || !code) return ACC_ERR_ARG;
+    if (!valid_k(k)) return ACC_ERR_K;
+    if (cls < 0 || cls >= num_classes(k)) return ACC_ERR_ARG;
+    if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
+    int rc = ensure_lut(c, k, c->own);
+    if (rc) return rc;
+    *code = c->class_code_host[k][cls];
+    return ACC_OK;
+}
+
+int acc_motif_classify_code(acc_ctx *c, int k, uint32_t code, int32_t *cls) {
+    if (!c || !cls) return ACC_ERR_ARG;
+    if (!valid_k(k)) return ACC_ERR_K;
+    if (code >= (1u << code_bits(k))) return ACC_ERR_ARG;
+    if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
+    int rc = ensure_lut(c, k, c->own);
+    if (rc) return rc;
+    *cls = c->lut_host[k][code];
+    return ACC_OK;
+}
+
+int acc_motif_copy_table(acc_ctx *c, int k, int16_t *h_table) {
+    if (!c || !h_table) return ACC_ERR_ARG;
+    if (!valid_k(k)) return ACC_ERR_K;
+    if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
+    int rc = ensure_lut(c, k, c->own);
+    if (rc) return rc;
+    memcpy(h_table, c->lut_host[k], (size_t(1) << code_bits(k)) * 2);
+    return ACC_OK;
+}
+
+int acc_motif_last_stats(acc_ctx *c, int64_t *h_stats) {
+    if (!c || !h_stats) return ACC_ERR_ARG;
+    if (!c->info) return ACC_ERR_ARG;
+    if (!ok(cudaSetDevice(c->device)) || !ok(cudaDeviceSynchronize())) return ACC_ERR_CUDA;
+    GraphInfo gi;
+    if (!ok(cudaMemcpy(&gi, c->info, sizeof(gi), cudaMemcpyDeviceToHost))) return ACC_ERR_CUDA;
+    h_stats[0] = c->last_launches;
+    h_stats[1] = c->last_k == 3 ? (int64_t)c->last_units : (int64_t)gi.nnz;
+    h_stats[2] = (int64_t)gi.queue_tail;
+    h_stats[3] = (int64_t)(gi.nnz / 2);
+    h_stats[4] = gi.maxdeg;
+    h_stats[5] = c->last_blocks;
+    return ACC_OK;
+}
+
+int acc_ctx_set_timing(acc_ctx *c, int on) {
+    if (!c) return ACC_ERR_ARG;
+    if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
+    if (on && !c->ev[0]) {
+        for (int i = 0; i < 3; i++)
+            if (!ok(cudaEventCreate(&c->ev[i]))) {
+                cudaGetLastError();
+                return ACC_ERR_CUDA;
+            }
+    }
+    c->timing = on != 0;
+    return ACC_OK;
+}
+
+int acc_motif_last_timing(acc_ctx *c, float *h_ms) {
+    if (!c || !h_ms || !c->timed_call) return ACC_ERR_ARG;
+    if (!ok(cudaSetDevice(c->device)) || !ok(cudaEventSynchronize(c->ev[2]))) return ACC_ERR_CUDA;
+    if (!ok(cudaEventElapsedTime(&h_ms[0], c->ev[0], c->ev[1])) ||
+        !ok(cudaEventElapsedTime(&h_ms[1], c->ev[1], c->ev[2])))
+        return ACC_ERR_CUDA;
+    return ACC_OK;
+}
+
+}  // extern "C"

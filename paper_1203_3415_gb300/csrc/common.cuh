@@ -1,0 +1,105 @@
+// Internal declarations shared by the library's CUDA translation units.
+//
+// Data layout on the device for one graph (all owned by the context's
+// workspace):
+//   state   uint32[n * pitch]   dense pair-state matrix, 2 bits per ordered
+//                               pair: bits of (a, b) = [arc a->b] | [arc b->a] << 1,
+//                               16 pairs per word, rows padded to 16 bytes.
+//                               The paper's neighbour partition (Notation
+//                               section): state 3 = bidirected (delta*),
+//                               1 = out only (delta+), 2 = in only (delta-).
+//   deg     int32[n]            degree of v in G*
+//   lo      int32[n]            neighbours of v below v (N*(v) is sorted, so
+//                               the neighbours above v start at lo[v])
+//   nptr    int64[n+1]          CSR offsets of the G* neighbour lists
+//   nbr     uint32[2|E*|]       neighbour entries (u << 2) | state(v, u),
+//                               sorted by u
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/acc_motif.h"
+
+namespace acc {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Block shape of the enumeration kernels.
+constexpr int kWarpsPerBlock = 8;
+constexpr int kThreads = kWarpsPerBlock * kWarp;
+
+// Per-graph scalars the builder leaves on the device.
+struct GraphInfo {
+    long long nnz;     // entries of nbr = 2 |E*|
+    int maxdeg;        // largest degree in G*
+    int pad;
+    unsigned long long queue_tail;  // heavy-unit chunks pushed by phase 1
+    unsigned long long queue_head;  // chunks taken by phase 2
+    unsigned long long unit_ctr;    // base units taken by phase 1
+    unsigned long long chunks_pushed;
+};
+
+// Bit of the adjacency code for the arc from tuple slot i to slot j.
+__host__ __device__ constexpr int code_bit(int k, int i, int j) {
+    return i * (k - 1) + (j - (j > i ? 1 : 0));
+}
+
+__host__ __device__ constexpr int num_classes(int k) {
+    return k == 3 ? 13 : (k == 4 ? 199 : (k == 5 ? 9364 : 0));
+}
+
+__host__ __device__ constexpr int code_bits(int k) { return k * (k - 1); }
+
+// Pitch (32-bit words per row) of the pair-state matrix for n vertices.
+inline long long state_pitch(int n) {
+    long long w = (n + 15) / 16;
+    return (w + 3) & ~3LL;
+}
+
+// First-error-wins status update.
+__device__ inline void set_status(int *status, int err) {
+    if (status) atomicCAS(status, 0, err);
+}
+
+// --------------------------------------------------------------------------
+// Launchers (each enqueues on `s` and returns the number of kernels it
+// launched, or a negative ACC_ERR_* code).
+// --------------------------------------------------------------------------
+
+// graph.cu
+int launch_build_graph(const long long *rowptr, const int *col, int n, long long m,
+                       uint32_t *state, long long pitch, int *deg, int *lo, long long *nptr,
+                       uint32_t *nbr, GraphInfo *info, int *status, unsigned long long *counts, int ncounts,
+                       int num_sms, cudaStream_t s);
+// Zero `bytes` at p, plus counts[0..ncounts) and *status when not NULL.
+int launch_zero(void *p, size_t bytes, int num_sms, cudaStream_t s, int *status = nullptr,
+                unsigned long long *counts = nullptr, int ncounts = 0);
+
+// lut.cu
+int launch_build_lut(int k, uint32_t *scratch_canon, int *scratch_rank, int16_t *lut,
+                     uint32_t *class_code, cudaStream_t s);
+
+// enum.cu
+struct EnumArgs {
+    const uint32_t *state;
+    long long pitch;
+    const int *deg;
+    const int *lo;
+    const long long *nptr;
+    const uint32_t *nbr;
+    const int16_t *lut;
+    int n;
+    GraphInfo *info;
+    uint4 *queue;               // heavy-unit chunks (unit, jlo, jhi, 0)
+    unsigned long long queue_cap;
+    uint32_t *scratch;          // per-warp overflow buffers for the extension sets
+    long long scratch_per_warp; // entries per warp
+    unsigned long long *counts; // int64[num_classes] (as unsigned for atomics)
+    int *status;
+};
+int launch_enumerate(int k, const EnumArgs &a, int num_sms, cudaStream_t s);
+int enum_grid_warps(int k, int num_sms);
+
+}  // namespace acc

@@ -1,0 +1,148 @@
+// Code -> class table, built on the device once per k.
+//
+// The paper classifies without isomorphism tests by hard-coding, per local
+// structure, which histogram slot each configuration feeds (pattern
+// matrices of the k=4 and k=5 sections, "precomputed" once and reused).
+// Here the same role is played by one table over all 2^(k(k-1)) adjacency
+// codes: code -> class of the digraph it describes, -1 if that digraph is not
+// weakly connected.  A code's class is the rank (ascending) of its canonical
+// code (minimum over the k! vertex orders) among the canonical codes of
+// connected digraphs.  k = 5: 2^20 codes x 120 orders, a few ms on the GPU.
+#include "common.cuh"
+
+namespace acc {
+
+namespace {
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+template <int K>
+struct Fact { static constexpr int v = K * Fact<K - 1>::v; };
+template <>
+struct Fact<0> { static constexpr int v = 1; };
+
+// Thread per code: weak connectivity, then the minimum code over all vertex
+// orders.  dest[p][b] is where order p sends code bit b.
+template <int K>
+__global__ void k_canon(uint32_t *canon) {
+    constexpr int NB = K * (K - 1);
+    constexpr int NP = Fact<K>::v;
+    __shared__ uint8_t dest[NP][NB];
+    for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+        // decode order p from the factorial number system
+        int pool[K], pi[K], r = p;
+        for (int i = 0; i < K; i++) pool[i] = i;
+        int left = K;
+        for (int i = 0; i < K; i++) {
+            int f = 1;
+            for (int j = 2; j < left; j++) f *= j;
+            const int q = r / f;
+            r -= q * f;
+            pi[i] = pool[q];
+            for (int j = q; j < left - 1; j++) pool[j] = pool[j + 1];
+            left--;
+        }
+        for (int i = 0; i < K; i++)
+            for (int j = 0; j < K; j++)
+                if (i != j) dest[p][code_bit(K, i, j)] = (uint8_t)code_bit(K, pi[i], pi[j]);
+    }
+    __syncthreads();
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (1u << NB)) return;
+    uint32_t adj[K];
+    for (int i = 0; i < K; i++) adj[i] = 0;
+    for (int i = 0; i < K; i++)
+        for (int j = 0; j < K; j++)
+            if (i != j && ((c >> code_bit(K, i, j)) & 1u)) {
+                adj[i] |= 1u << j;
+                adj[j] |= 1u << i;
+            }
+    uint32_t reach = 1;
+    for (int it = 0; it < K; it++) {
+        uint32_t nxt = reach;
+        for (int i = 0; i < K; i++)
+            if ((reach >> i) & 1u) nxt |= adj[i];
+        reach = nxt;
+    }
+    if (reach != (1u << K) - 1u) {
+        canon[c] = kNone;
+        return;
+    }
+    uint32_t best = c;
+    for (int p = 0; p < NP; p++) {
+        uint32_t out = 0, rest = c;
+        while (rest) {
+            const int b = __ffs(rest) - 1;
+            out |= 1u << dest[p][b];
+            rest &= rest - 1;
+        }
+        best = min(best, out);
+    }
+    canon[c] = best;
+}
+
+// One block: rank[c] = number of canonical codes below c.
+__global__ void k_rank(const uint32_t *__restrict__ canon, uint32_t ncodes, int *rank) {
+    __shared__ int warp_sum[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const uint32_t chunk = (ncodes + blockDim.x - 1) / blockDim.x;
+    const uint32_t b = min(ncodes, t * chunk), e = min(ncodes, b + chunk);
+    int s = 0;
+    for (uint32_t c = b; c < e; c++) s += canon[c] == c;
+    int incl = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) warp_sum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        int ws = lane < nw ? warp_sum[lane] : 0;
+        int wi = ws;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int y = __shfl_up_sync(kFull, wi, d);
+            if (lane >= d) wi += y;
+        }
+        if (lane < nw) warp_sum[lane] = wi - ws;
+    }
+    __syncthreads();
+    int run = warp_sum[wid] + (incl - s);
+    for (uint32_t c = b; c < e; c++) {
+        rank[c] = run;
+        run += canon[c] == c;
+    }
+}
+
+__global__ void k_finish(const uint32_t *__restrict__ canon, const int *__restrict__ rank, uint32_t ncodes,
+                         int ncls, int16_t *lut, uint32_t *class_code) {
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncodes) return;
+    const uint32_t cc = canon[c];
+    // a rank at or above the class count would be a canonicalisation bug:
+    // mark it (-2) for the host check instead of writing out of range
+    const int r = cc == kNone ? -1 : rank[cc];
+    lut[c] = (int16_t)(r >= ncls ? -2 : r);
+    if (cc == c && r < ncls) class_code[r] = c;
+}
+
+}  // namespace
+
+int launch_build_lut(int k, uint32_t *canon, int *rank, int16_t *lut, uint32_t *class_code, cudaStream_t s) {
+    const uint32_t ncodes = 1u << code_bits(k);
+    const int threads = 256;
+    const int grid = (int)((ncodes + threads - 1) / threads);
+    switch (k) {
+    case 3: k_canon<3><<<grid, threads, 0, s>>>(canon); break;
+    case 4: k_canon<4><<<grid, threads, 0, s>>>(canon); break;
+    case 5: k_canon<5><<<grid, threads, 0, s>>>(canon); break;
+    default: return ACC_ERR_K;
+    }
+    k_rank<<<1, 1024, 0, s>>>(canon, ncodes, rank);
+    k_finish<<<grid, threads, 0, s>>>(canon, rank, ncodes, num_classes(k), lut, class_code);
+    return cudaGetLastError() == cudaSuccess ? 3 : ACC_ERR_CUDA;
+}
+
+}  // namespace acc

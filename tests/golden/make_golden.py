@@ -20,6 +20,7 @@ import numpy as np  # noqa: E402
 
 import oracle  # noqa: E402
 import synth  # noqa: E402
+from tests.golden.golden_io import read_counts  # noqa: E402,F401
 
 WORKLOADS = {
     "er_n1000_m5000_k3": (synth.er_k3, 3),
@@ -39,25 +40,6 @@ def write_counts(path, name, g, k, counts, seconds, threads):
         for c, v in enumerate(counts):
             if v:
                 f.write(f"{c} {int(v)}\n")
-
-
-def read_counts(path):
-    """(header dict, int64 counts) of a file written by write_counts."""
-    hdr = {}
-    rows = []
-    with open(path) as f:
-        for line in f:
-            if line.startswith("# "):
-                key, _, val = line[2:].strip().partition(" ")
-                hdr[key] = val
-            elif line.strip():
-                c, v = line.split()
-                rows.append((int(c), int(v)))
-    counts = np.zeros(int(hdr["classes"]), dtype=np.int64)
-    for c, v in rows:
-        counts[c] = v
-    assert int(counts.sum()) == int(hdr["total"])
-    return hdr, counts
 
 
 def main():
