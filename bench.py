@@ -298,7 +298,7 @@ def run_ours(args):
     # L2 flushed (256 MiB write) between steps, outside the events
     counter.set_timing(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    build_ms, enum_ms = [], []
+    build_ms, enum_ms, p1_ms, p2_ms = [], [], [], []
     sampler = ClockSampler(local) if rank == 0 else None
     if dist is not None:
         dist.barrier()
@@ -310,9 +310,11 @@ def run_ours(args):
         ev[i][0].record(stream)
         counter.count(rowptr, col, g.n, k, counts=counts, status=status, stream=stream)
         ev[i][1].record(stream)
-        b, e = counter.last_timing()
+        b, e, e1, e2 = counter.last_timing()
         build_ms.append(b)
         enum_ms.append(e)
+        p1_ms.append(e1)
+        p2_ms.append(e2)
     torch.cuda.synchronize(dev)
     if dist is not None:
         dist.barrier()
@@ -391,7 +393,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(acc.NUM_CLASSES[k] * 8)},
         "gpu_launches": int(stats["launches"]) * args.steps,
         "clocks": clocks,
-        "stages_ms": {"build": statistics.mean(build_ms), "enumerate": enum_ms and statistics.mean(enum_ms),
+        "stages_ms": {"build": statistics.mean(build_ms), "enumerate": statistics.mean(enum_ms),
+                      "enumerate_phase1": statistics.mean(p1_ms), "enumerate_phase2": statistics.mean(p2_ms),
                       "step_median": statistics.median(step_ms)},
         "parity_vs_stored_oracle_counts": parity,
         "work": {"chunks": stats["chunks"], "undirected_edges": stats["undirected_edges"],

@@ -153,10 +153,10 @@ ACC_API int acc_motif_last_stats(acc_ctx *ctx, int64_t *h_stats);
 
 /*
  * Stage timing.  With timing on (on != 0), every acc_motif_count records CUDA
- * events on its stream before the graph build, between build and
- * enumeration, and after the enumeration.  acc_motif_last_timing waits for
- * the last call's end event and writes h_ms[0] = graph-build stage,
- * h_ms[1] = enumeration stage (both launches), in milliseconds.
+ * events on its stream around its stages.  acc_motif_last_timing waits for
+ * the last call's end event and writes float h_ms[4], in milliseconds:
+ * [0] graph build, [1] enumeration (both launches), [2] enumeration phase 1
+ * (light units run, heavy units queued), [3] phase 2 (queue drained).
  * Errors: ACC_ERR_ARG (timing off or no count yet), ACC_ERR_CUDA.
  */
 ACC_API int acc_ctx_set_timing(acc_ctx *ctx, int on);

@@ -223,11 +223,12 @@ class Counter:
         _check(acc_ctx_set_timing(self.ctx, 1 if on else 0), "acc_ctx_set_timing")
 
     def last_timing(self):
-        """(build_ms, enumerate_ms) of the last count (timing must be on)."""
+        """(build_ms, enumerate_ms, phase1_ms, phase2_ms) of the last count
+        (timing must be on)."""
         import numpy as np
-        out = np.zeros(2, dtype=np.float32)
+        out = np.zeros(4, dtype=np.float32)
         _check(acc_motif_last_timing(self.ctx, out.ctypes.data), "acc_motif_last_timing")
-        return float(out[0]), float(out[1])
+        return tuple(float(x) for x in out)
 
     def last_stats(self):
         import numpy as np

@@ -16,6 +16,7 @@ struct acc_ctx {
 
     // code -> class tables per k
     int16_t *lut[6] = {};
+    int16_t *lut_sv[6] = {};
     uint32_t *class_code_dev[6] = {};
     int16_t *lut_host[6] = {};
     uint32_t *class_code_host[6] = {};
@@ -23,7 +24,7 @@ struct acc_ctx {
     // per-graph workspace (grow-only)
     uint32_t *state = nullptr;
     size_t state_words = 0;
-    int *deg = nullptr, *lo = nullptr;
+    int *deg = nullptr, *lo = nullptr, *label = nullptr;
     long long *nptr = nullptr;
     size_t n_cap = 0;
     uint32_t *nbr = nullptr;
@@ -46,7 +47,7 @@ struct acc_ctx {
     // stage timing
     bool timing = false;
     bool timed_call = false;
-    cudaEvent_t ev[3] = {};
+    cudaEvent_t ev[4] = {};
 
     // statistics of the last count
     int last_launches = 0;
@@ -58,6 +59,8 @@ struct acc_ctx {
 namespace {
 
 constexpr unsigned long long kQueueCap = 1ull << 22;
+// Below this many vertices the renumbering pass costs more than it saves.
+constexpr int kRelabelMinN = 1024;
 
 bool ok(cudaError_t e) { return e == cudaSuccess; }
 
@@ -85,16 +88,17 @@ int ensure_lut(acc_ctx *c, int k, cudaStream_t s) {
     const int ncls = num_classes(k);
     uint32_t *canon = nullptr;
     int *rank = nullptr;
-    int16_t *lut = nullptr;
+    int16_t *lut = nullptr, *lut_sv = nullptr;
     uint32_t *cc = nullptr;
     int rc = ACC_ERR_NOMEM;
     c->lut_host[k] = new (std::nothrow) int16_t[ncodes];
     c->class_code_host[k] = new (std::nothrow) uint32_t[ncls];
     if (!c->lut_host[k] || !c->class_code_host[k]) goto fail;
     if (!ok(cudaMalloc(&canon, ncodes * 4)) || !ok(cudaMalloc(&rank, ncodes * 4)) ||
-        !ok(cudaMalloc(&lut, ncodes * 2)) || !ok(cudaMalloc(&cc, ncls * 4)))
+        !ok(cudaMalloc(&lut, ncodes * 2)) || !ok(cudaMalloc(&lut_sv, ncodes * 2)) ||
+        !ok(cudaMalloc(&cc, ncls * 4)))
         goto fail;
-    rc = launch_build_lut(k, canon, rank, lut, cc, s);
+    rc = launch_build_lut(k, canon, rank, lut, cc, lut_sv, s);
     if (rc < 0) goto fail;
     rc = ACC_ERR_CUDA;
     if (!ok(cudaMemcpyAsync(c->lut_host[k], lut, ncodes * 2, cudaMemcpyDeviceToHost, s))) goto fail;
@@ -115,6 +119,7 @@ int ensure_lut(acc_ctx *c, int k, cudaStream_t s) {
     cudaFree(canon);
     cudaFree(rank);
     c->lut[k] = lut;
+    c->lut_sv[k] = lut_sv;
     c->class_code_dev[k] = cc;
     return ACC_OK;
 fail:
@@ -122,6 +127,7 @@ fail:
     cudaFree(canon);
     cudaFree(rank);
     cudaFree(lut);
+    cudaFree(lut_sv);
     cudaFree(cc);
     delete[] c->lut_host[k];
     delete[] c->class_code_host[k];
@@ -136,15 +142,18 @@ int ensure_workspace(acc_ctx *c, int n, long long m, int k) {
     if ((rc = grow(&c->state, &c->state_words, (size_t)n * pitch + 4))) return rc;
     if ((size_t)n + 1 > c->n_cap || !c->deg) {
         size_t a = 0, b = 0, d = 0;
+        size_t e = 0;
         cudaFree(c->deg);
         cudaFree(c->lo);
         cudaFree(c->nptr);
-        c->deg = c->lo = nullptr;
+        cudaFree(c->label);
+        c->deg = c->lo = c->label = nullptr;
         c->nptr = nullptr;
         c->n_cap = 0;
         if ((rc = grow(&c->deg, &a, (size_t)n + 1))) return rc;
         if ((rc = grow(&c->lo, &b, (size_t)n + 1))) return rc;
         if ((rc = grow(&c->nptr, &d, (size_t)n + 1))) return rc;
+        if ((rc = grow(&c->label, &e, (size_t)n + 1))) return rc;
         c->n_cap = a;
     }
     if ((rc = grow(&c->nbr, &c->nbr_cap, (size_t)(2 * m) + 1))) return rc;
@@ -182,8 +191,9 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
     c->timed_call = c->timing;
     if (c->timing && !ok(cudaEventRecord(c->ev[0], s))) return ACC_ERR_CUDA;
     rc = launch_build_graph(reinterpret_cast<const long long *>(rowptr), col, n, m, c->state, pitch, c->deg, c->lo,
-                            c->nptr, c->nbr, c->info, status, reinterpret_cast<unsigned long long *>(counts),
-                            num_classes(k), c->num_sms, s);
+                            c->nptr, c->nbr, c->label, c->info, status,
+                            reinterpret_cast<unsigned long long *>(counts), num_classes(k), n >= kRelabelMinN,
+                            c->num_sms, s);
     if (rc < 0) return rc;
     launches += rc;
     if (c->timing && !ok(cudaEventRecord(c->ev[1], s))) return ACC_ERR_CUDA;
@@ -194,7 +204,7 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
     a.lo = c->lo;
     a.nptr = c->nptr;
     a.nbr = c->nbr;
-    a.lut = c->lut[k];
+    a.lut = c->lut_sv[k];
     a.n = n;
     a.info = c->info;
     a.queue = c->queue;
@@ -204,7 +214,13 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
     a.counts = reinterpret_cast<unsigned long long *>(counts);
     a.status = status;
     if (n > 0) {
-        rc = launch_enumerate(k, a, c->num_sms, s);
+        rc = launch_enumerate(k, a, c->num_sms, 1, s);
+        if (rc < 0) return rc;
+        launches += rc;
+    }
+    if (c->timing && !ok(cudaEventRecord(c->ev[3], s))) return ACC_ERR_CUDA;
+    if (n > 0) {
+        rc = launch_enumerate(k, a, c->num_sms, 2, s);
         if (rc < 0) return rc;
         launches += rc;
     }
@@ -266,6 +282,7 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaDeviceSynchronize();
     for (int k = 0; k < 6; k++) {
         cudaFree(c->lut[k]);
+        cudaFree(c->lut_sv[k]);
         cudaFree(c->class_code_dev[k]);
         delete[] c->lut_host[k];
         delete[] c->class_code_host[k];
@@ -274,6 +291,7 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaFree(c->deg);
     cudaFree(c->lo);
     cudaFree(c->nptr);
+    cudaFree(c->label);
     cudaFree(c->nbr);
     cudaFree(c->info);
     cudaFree(c->queue);
@@ -282,7 +300,7 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaFree(c->h2d_rowptr);
     cudaFree(c->h2d_col);
     cudaFree(c->h2d_counts);
-    for (int i = 0; i < 3; i++)
+    for (int i = 0; i < 4; i++)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->status_host) cudaFreeHost(c->status_host);
     if (c->own) cudaStreamDestroy(c->own);
@@ -384,7 +402,7 @@ int acc_ctx_set_timing(acc_ctx *c, int on) {
     if (!c) return ACC_ERR_ARG;
     if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
     if (on && !c->ev[0]) {
-        for (int i = 0; i < 3; i++)
+        for (int i = 0; i < 4; i++)
             if (!ok(cudaEventCreate(&c->ev[i]))) {
                 cudaGetLastError();
                 return ACC_ERR_CUDA;
@@ -398,7 +416,9 @@ int acc_motif_last_timing(acc_ctx *c, float *h_ms) {
     if (!c || !h_ms || !c->timed_call) return ACC_ERR_ARG;
     if (!ok(cudaSetDevice(c->device)) || !ok(cudaEventSynchronize(c->ev[2]))) return ACC_ERR_CUDA;
     if (!ok(cudaEventElapsedTime(&h_ms[0], c->ev[0], c->ev[1])) ||
-        !ok(cudaEventElapsedTime(&h_ms[1], c->ev[1], c->ev[2])))
+        !ok(cudaEventElapsedTime(&h_ms[1], c->ev[1], c->ev[2])) ||
+        !ok(cudaEventElapsedTime(&h_ms[2], c->ev[1], c->ev[3])) ||
+        !ok(cudaEventElapsedTime(&h_ms[3], c->ev[3], c->ev[2])))
         return ACC_ERR_CUDA;
     return ACC_OK;
 }

@@ -14,6 +14,10 @@
 //   nptr    int64[n+1]          CSR offsets of the G* neighbour lists
 //   nbr     uint32[2|E*|]       neighbour entries (u << 2) | state(v, u),
 //                               sorted by u
+//   label   int32[n]            new number of each input vertex (vertices
+//                               are renumbered by descending G* degree, so
+//                               hubs become the roots of their subsets)
+// All of the above except label are in the renumbered ids.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -69,17 +73,22 @@ __device__ inline void set_status(int *status, int err) {
 // --------------------------------------------------------------------------
 
 // graph.cu
+// Builds the pair-state matrix and the G* neighbour lists; with `relabel`
+// the vertices are first renumbered by descending G* degree (label[v] = new
+// number of input vertex v), which leaves the counts unchanged.
 int launch_build_graph(const long long *rowptr, const int *col, int n, long long m,
                        uint32_t *state, long long pitch, int *deg, int *lo, long long *nptr,
-                       uint32_t *nbr, GraphInfo *info, int *status, unsigned long long *counts, int ncounts,
-                       int num_sms, cudaStream_t s);
-// Zero `bytes` at p, plus counts[0..ncounts) and *status when not NULL.
+                       uint32_t *nbr, int *label, GraphInfo *info, int *status, unsigned long long *counts,
+                       int ncounts, bool relabel, int num_sms, cudaStream_t s);
+// Zero `bytes` at p, plus counts[0..ncounts), ints[0..nints) and *status
+// when not NULL.
 int launch_zero(void *p, size_t bytes, int num_sms, cudaStream_t s, int *status = nullptr,
-                unsigned long long *counts = nullptr, int ncounts = 0);
+                unsigned long long *counts = nullptr, int ncounts = 0, int *ints = nullptr, int nints = 0);
 
-// lut.cu
+// lut.cu: lut = code -> class in the canonical code layout (public API),
+// lut_sv = the same classes indexed in the state-vector layout (kernels).
 int launch_build_lut(int k, uint32_t *scratch_canon, int *scratch_rank, int16_t *lut,
-                     uint32_t *class_code, cudaStream_t s);
+                     uint32_t *class_code, int16_t *lut_sv, cudaStream_t s);
 
 // enum.cu
 struct EnumArgs {
@@ -89,7 +98,7 @@ struct EnumArgs {
     const int *lo;
     const long long *nptr;
     const uint32_t *nbr;
-    const int16_t *lut;
+    const int16_t *lut;         // class table in the state-vector layout
     int n;
     GraphInfo *info;
     uint4 *queue;               // heavy-unit chunks (unit, jlo, jhi, 0)
@@ -99,7 +108,8 @@ struct EnumArgs {
     unsigned long long *counts; // int64[num_classes] (as unsigned for atomics)
     int *status;
 };
-int launch_enumerate(int k, const EnumArgs &a, int num_sms, cudaStream_t s);
+// phase 1: light units run, heavy units queued; phase 2: the queue drained.
+int launch_enumerate(int k, const EnumArgs &a, int num_sms, int phase, cudaStream_t s);
 int enum_grid_warps(int k, int num_sms);
 
 }  // namespace acc

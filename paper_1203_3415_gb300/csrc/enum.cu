@@ -20,34 +20,55 @@
 //   leaves are  (a) P + {E[j], E[l]}  for j < l          ("pair leaves")
 //               (b) P + {E[j], u}     for u an exclusive neighbour of E[j]
 //
-// A leaf's code is the prefix code OR two table entries (the states of E[j]
-// and of the last vertex to the prefix, kept in each E entry) OR the state
-// of the last pair, found with one probe of the pair-state matrix (a) or read
-// from the neighbour entry (b).
+// Codes in the kernels use the state-vector layout: for tuple slot t >= 1 the
+// field f_t = sum_{i<t} state(w_i, w_t) << 2i (state bit 0 = arc w_i -> w_t,
+// bit 1 = arc w_t -> w_i), fields stored from the last slot (lowest bits) up
+// to slot 1.  Every piece of a leaf's code is then a shifted state vector, and
+// the bits that change along one extension row are the lowest ones, so the
+// codes of one row hit distinct shared-memory banks of the class table.  The
+// table the kernels read is the canonical-layout table with its index bits
+// permuted accordingly (lut.cu), so classes are the same.
 //
 // Work units: k=3 one unit per root v; k=4 and k=5 one unit per arc position
-// of the G* CSR, i.e. per (v, w1) with w1 > v.  Phase 1 runs every unit whose
-// estimated work is small and splits the others into row ranges of their
-// extension list, pushed to a queue that phase 2 (a second launch) drains.
+// of the G* CSR, i.e. per (v, w1) with w1 > v.  Phase 1 runs every light unit
+// and queues the heavy ones as row ranges of their extension list; phase 2
+// (a second launch) drains the queue.
+#include <math.h>
+
 #include "common.cuh"
 
 namespace acc {
 
 namespace {
 
-constexpr int kCap34 = 1024;           // per-warp shared extension entries, k = 3, 4
-constexpr int kCap5 = 512;             // per-warp shared entries per list, k = 5
-constexpr int kGrab = 16;              // base units per atomic grab
-constexpr long long kTarget = 1 << 15; // work per pushed chunk
+// Tuning knobs (compile-time; -D overrides for sweeps).
+#ifndef ACC_CAP34
+#define ACC_CAP34 1024
+#endif
+#ifndef ACC_GRAB
+#define ACC_GRAB 1
+#endif
+#ifndef ACC_LIGHT
+#define ACC_LIGHT (1 << 12)
+#endif
+#ifndef ACC_TARGET
+#define ACC_TARGET (1 << 14)
+#endif
+#ifndef ACC_UNROLL
+#define ACC_UNROLL 4
+#endif
+#ifndef ACC_HIST_MATCH
+#define ACC_HIST_MATCH 0  // 1: warp-aggregate increments with __match_any_sync
+#endif
+#ifndef ACC_MINB34
+#define ACC_MINB34 4  // resident blocks per SM the k = 3, 4 kernels are compiled for
+#endif
+constexpr int kCap34 = ACC_CAP34;         // per-warp shared extension entries, k = 3, 4
+constexpr int kCap5 = 512;                // per-warp shared entries per list, k = 5
+constexpr int kGrab = ACC_GRAB;           // base units per atomic grab
+constexpr long long kLight = ACC_LIGHT;   // phase 1 runs units up to this much work
+constexpr long long kTarget = ACC_TARGET; // work per queued chunk
 constexpr uint32_t kDrainAt = 1u << 30;
-
-struct Tables {
-    uint32_t t2[64];   // code bits of slot k-2 from its states to the prefix slots
-    uint32_t t3[64];   // code bits of slot k-1 from its states to the prefix slots
-    uint32_t s2[16];   // k = 5: code bits of slot 2 from its states to slots 0, 1
-    uint32_t tp[4];    // code bits of the pair (k-2, k-1) from state(x_{k-2}, x_{k-1})
-    uint32_t p01[4];   // code bits of the pair (0, 1) from state(v, w1)
-};
 
 template <int K>
 struct Layout {
@@ -56,31 +77,23 @@ struct Layout {
     static constexpr bool SMEM_LUT = K <= 4;
     static constexpr int CAP = K == 5 ? kCap5 : kCap34;
     static constexpr int LISTS = K == 5 ? 2 : 1;
-    static constexpr size_t tables = (sizeof(Tables) + 15) & ~size_t(15);
+    static constexpr int SH_PAIR = 2 * (K - 2);  // state(E[j], leaf) within the last field
+    static constexpr int SH_ROW = 2 * (K - 1);   // field of slot k-2
     static constexpr size_t lut = SMEM_LUT ? (((size_t(1) << NB) * 2 + 15) & ~size_t(15)) : 0;
     static constexpr size_t pending = 16;
     static constexpr size_t hist = (K == 5 ? size_t(NCLS) * 4 : size_t(kWarpsPerBlock) * NCLS * 4 + 15) & ~size_t(15);
     static constexpr size_t ebuf = size_t(kWarpsPerBlock) * LISTS * CAP * 4;
-    static constexpr size_t total = tables + lut + pending + hist + ebuf;
+    static constexpr size_t total = lut + pending + hist + ebuf;
 };
-
-__device__ __forceinline__ uint32_t slot_bits(int K, int slot, uint32_t svec, int nprefix) {
-    uint32_t out = 0;
-    for (int i = 0; i < nprefix; i++) {
-        const uint32_t s = (svec >> (2 * i)) & 3u;
-        if (s & 1u) out |= 1u << code_bit(K, i, slot);
-        if (s & 2u) out |= 1u << code_bit(K, slot, i);
-    }
-    return out;
-}
-
-__device__ __forceinline__ uint32_t pair_bits(int K, int a, int b, uint32_t s) {
-    return ((s & 1u) << code_bit(K, a, b)) | (((s >> 1) & 1u) << code_bit(K, b, a));
-}
 
 __device__ __forceinline__ uint32_t probe(const uint32_t *__restrict__ st, long long pitch, uint32_t a, uint32_t b) {
     return (__ldg(st + (long long)a * pitch + (b >> 4)) >> ((b & 15u) << 1)) & 3u;
 }
+
+// Extension-list entry: (x << 6) | states of x to the prefix vertices, two
+// bits each in prefix order (at most 3 prefix vertices).
+__device__ __forceinline__ uint32_t e_id(uint32_t e) { return e >> 6; }
+__device__ __forceinline__ uint32_t e_sv(uint32_t e) { return e & 63u; }
 
 // First position of N*(x) (entries (u << 2) | s, sorted) with u > root.
 __device__ __forceinline__ int first_above(const uint32_t *__restrict__ nbr, long long base, int d, uint32_t root) {
@@ -127,26 +140,58 @@ __device__ __forceinline__ int lb_search(int pre, int t) {
 }
 
 // Histogram sink: k <= 4 one private histogram per warp, k = 5 one per block.
+// Each lane keeps a run of equal classes in registers (consecutive leaves of
+// one extension row mostly share a class) and adds a run to shared memory
+// only when the class changes.
 template <int K>
 struct Sink {
     uint32_t *hist;
     const int16_t *lut;
     unsigned long long *counts;
     uint32_t *pending;  // k = 5: block-wide increments since the last drain
-    uint32_t since;     // k <= 4: this warp's increments since its last drain
+    uint32_t since;     // increments of this warp not yet accounted
     int *status;
+    int run_cls;        // this lane's current run
+    uint32_t run_len;
 
-    __device__ __forceinline__ void bump(uint32_t code) {
-        const int cls = Layout<K>::SMEM_LUT ? (int)lut[code] : (int)__ldg(lut + code);
-        if (cls >= 0) atomicAdd(&hist[cls], 1u);
-        else set_status(status, ACC_ERR_INTERNAL);
+    __device__ __forceinline__ void flush() {
+        if (run_len) {
+            if (run_cls >= 0) atomicAdd(&hist[run_cls], run_len);
+            else set_status(status, ACC_ERR_INTERNAL);
+            run_len = 0;
+        }
     }
 
-    // Called by the whole warp after each batch of at most `tot` bumps.
+    // Called by all lanes of the warp together; `valid` lanes count one leaf
+    // with adjacency code `code`.
+    __device__ __forceinline__ void bump(uint32_t code, bool valid) {
+#if ACC_HIST_MATCH
+        const int cls = valid ? (Layout<K>::SMEM_LUT ? (int)lut[code] : (int)__ldg(lut + code)) : -2;
+        const unsigned peers = __match_any_sync(kFull, cls);
+        if (valid && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) {
+            if (cls >= 0) atomicAdd(&hist[cls], (uint32_t)__popc(peers));
+            else set_status(status, ACC_ERR_INTERNAL);
+        }
+#else
+        if (!valid) return;
+        const int cls = Layout<K>::SMEM_LUT ? (int)lut[code] : (int)__ldg(lut + code);
+        if (cls == run_cls) {
+            ++run_len;
+        } else {
+            flush();
+            run_cls = cls;
+            run_len = 1;
+        }
+#endif
+    }
+
+    // Called by the whole warp after each batch of at most `tot` bumps: keeps
+    // every 32-bit shared counter below 2^32 by draining to the int64 counts.
     __device__ __forceinline__ void after_batch(uint32_t tot, int lane) {
+        since += tot;
         if (K <= 4) {
-            since += tot;
             if (since >= kDrainAt) {
+                flush();
                 __syncwarp();
                 for (int c = lane; c < Layout<K>::NCLS; c += kWarp) {
                     const uint32_t v = hist[c];
@@ -159,18 +204,23 @@ struct Sink {
                 since = 0;
             }
         } else {
+            if (since < (1u << 20)) return;
+            // account in the block-wide counter every 2^20 increments; the
+            // warp that crosses 2^30 drains the block histogram (atomicExch
+            // per bin, so concurrent increments are never lost)
             uint32_t old = 0;
             __threadfence_block();
-            if (lane == 0) old = atomicAdd(pending, tot);
+            if (lane == 0) old = atomicAdd(pending, since);
             old = __shfl_sync(kFull, old, 0);
-            if (old < kDrainAt && old + tot >= kDrainAt) {
+            if (old < kDrainAt && old + since >= kDrainAt) {
                 for (int c = lane; c < Layout<K>::NCLS; c += kWarp) {
                     const uint32_t v = atomicExch(&hist[c], 0u);
                     if (v) atomicAdd(&counts[c], (unsigned long long)v);
                 }
                 __syncwarp();
-                if (lane == 0) atomicSub(pending, old + tot);
+                if (lane == 0) atomicSub(pending, old + since);
             }
+            since = 0;
         }
     }
 };
@@ -181,89 +231,118 @@ struct Scratch {
     int cap;
 };
 
-// The last two ESU levels over extension list E[0..B) for rows [jlo, jend).
+// The last two ESU levels over extension list E[0..B), virtual rows
+// [plo, phi).  Virtual row p joins row p and row B-1-p of the pair triangle:
+// their pair counts (B-1-p and p) add up to B-1 for every p, so all virtual
+// rows have the same length and a flat position maps to (row, column) with one
+// comparison.  For odd B the middle row (p = B-1-p) stands alone.  pcode holds
+// the code fields of the prefix slots 1..k-3.
 template <int K>
-__device__ __forceinline__ void leaves(const EnumArgs &a, const Tables &tb, Sink<K> &sink, const uint32_t *E,
-                                       int B, int jlo, int jend, const uint32_t *pm, uint32_t pcode,
-                                       uint32_t root, int lane) {
-    // (a) pair leaves P + {E[j], E[l]}, j < l
-    for (int jb = jlo; jb < jend; jb += kWarp) {
-        const int j = jb + lane;
-        const bool ok = j < jend;
-        const uint32_t ej = ok ? E[j] : 0u;
-        const int cnt = ok ? (B - 1 - j) : 0;
-        int tot;
-        const int pre = excl_scan(cnt, lane, &tot);
-        const uint32_t cj = pcode | tb.t2[ej & 63u];
-        for (int t0 = 0; t0 < tot; t0 += kWarp) {
-            const int t = t0 + lane;
-            const int r = lb_search(pre, t);
-            const uint32_t cr = __shfl_sync(kFull, cj, r);
-            const uint32_t xr = __shfl_sync(kFull, ej, r) >> 6;
-            const int pr = __shfl_sync(kFull, pre, r);
-            if (t < tot) {
-                const uint32_t ey = E[jb + r + 1 + (t - pr)];
-                const uint32_t s = probe(a.state, a.pitch, xr, ey >> 6);
-                sink.bump(cr | tb.t3[ey & 63u] | tb.tp[s]);
+__device__ __forceinline__ void leaves(const EnumArgs &a, Sink<K> &sink, const uint32_t *E, int B, int plo,
+                                       int phi, const uint32_t *pm, uint32_t pcode, uint32_t root, int lane) {
+    using L = Layout<K>;
+    const int P = (B + 1) >> 1;
+    phi = min(phi, P);
+    if (plo >= phi) return;
+    // (a) pair leaves P + {E[row], E[col]}, row < col.  Virtual row p,
+    //     position q < B-1-p: (p, p+1+q); q >= B-1-p: (B-1-p, q+1).
+    const int Lv = B - 1;
+    if (Lv > 0) {
+        constexpr int U = ACC_UNROLL;  // positions each lane keeps in flight
+        const long long t_begin = (long long)plo * Lv, t_end = (long long)phi * Lv;
+        // this lane's cursor: virtual row p, position q of flat position t0 + lane
+        int p = (int)((t_begin + lane) / Lv), q = (int)((t_begin + lane) % Lv);
+        for (long long t0 = t_begin; t0 < t_end; t0 += U * kWarp) {
+            const long long t = t0 + lane;
+            uint32_t er[U], ec[U], w[U];
+            bool ok[U];
+            int pu = p, qu = q;
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int Lp = Lv - pu;
+                const bool first = qu < Lp;
+                const int row = first ? pu : Lv - pu;
+                const int col = first ? pu + 1 + qu : qu + 1;
+                ok[u] = t + u * kWarp < t_end && (first || 2 * pu + 1 != B);
+                er[u] = ok[u] ? E[row] : 0u;
+                ec[u] = ok[u] ? E[col] : 0u;
+                qu += kWarp;
+                while (qu >= Lv) {
+                    qu -= Lv;
+                    pu++;
+                }
             }
+            p = pu;
+            q = qu;
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                w[u] = ok[u] ? __ldg(a.state + (long long)e_id(er[u]) * a.pitch + (e_id(ec[u]) >> 4)) : 0u;
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const uint32_t s = (w[u] >> ((e_id(ec[u]) & 15u) << 1)) & 3u;
+                sink.bump(pcode | (e_sv(er[u]) << L::SH_ROW) | e_sv(ec[u]) | (s << L::SH_PAIR), ok[u]);
+            }
+            sink.after_batch((uint32_t)(U * kWarp), lane);
         }
-        sink.after_batch((uint32_t)tot, lane);
     }
     // (b) exclusive leaves P + {E[j], u}, u a neighbour of E[j] above the
-    //     root and adjacent to no prefix vertex
-    for (int jb = jlo; jb < jend; jb += kWarp) {
-        const int j = jb + lane;
-        uint32_t ej = 0;
-        long long base = 0;
+    //     root and adjacent to no prefix vertex (its states to the prefix
+    //     are 0).  Rows of virtual rows [plo, phi): [plo, phi) in the first
+    //     half, [B-phi, B-plo) in the second.  Neighbour-list positions fit
+    //     32 bits (2 |E*| < 2^32).
+    const int r1lo = plo, n1 = phi - plo;
+    const int r2lo = max(B - phi, P), n2 = max(0, (B - plo) - r2lo);
+    const int nr = n1 + n2;
+    for (int ib = 0; ib < nr; ib += kWarp) {
+        const int i = ib + lane;
+        uint32_t ej = 0, first = 0;
         int cnt = 0;
-        if (j < jend) {
+        if (i < nr) {
+            const int j = i < n1 ? r1lo + i : r2lo + (i - n1);
             ej = E[j];
-            const uint32_t x = ej >> 6;
+            const uint32_t x = e_id(ej);
             const long long nb = a.nptr[x];
             const int d = a.deg[x];
             const int st = first_above(a.nbr, nb, d, root);
-            base = nb + st;
+            first = (uint32_t)(nb + st);
             cnt = d - st;
         }
         int tot;
         const int pre = excl_scan(cnt, lane, &tot);
-        const uint32_t cj = pcode | tb.t2[ej & 63u];
+        const uint32_t cj = pcode | (e_sv(ej) << L::SH_ROW);
+        const uint32_t off = first - (uint32_t)pre;  // position of leaf t is off + t
         for (int t0 = 0; t0 < tot; t0 += kWarp) {
             const int t = t0 + lane;
             const int r = lb_search(pre, t);
             const uint32_t cr = __shfl_sync(kFull, cj, r);
-            const long long br = __shfl_sync(kFull, base, r);
-            const int pr = __shfl_sync(kFull, pre, r);
+            const uint32_t orow = __shfl_sync(kFull, off, r);
+            bool leaf = false;
+            uint32_t ue = 0;
             if (t < tot) {
-                const uint32_t ue = __ldg(a.nbr + br + (t - pr));
+                ue = __ldg(a.nbr + (orow + (uint32_t)t));
                 const uint32_t u = ue >> 2;
-                bool excl = true;
+                leaf = true;
 #pragma unroll
-                for (int i = 0; i < K - 2; i++) excl = excl && probe(a.state, a.pitch, pm[i], u) == 0u;
-                if (excl) sink.bump(cr | tb.tp[ue & 3u]);
+                for (int k2 = 0; k2 < K - 2; k2++) leaf = leaf && probe(a.state, a.pitch, pm[k2], u) == 0u;
             }
+            sink.bump(cr | ((ue & 3u) << L::SH_PAIR), leaf);
         }
         sink.after_batch((uint32_t)tot, lane);
     }
 }
 
-// Build the list of (prefix, extension) for k >= 4 from arc position p:
-// v = row of p, w1 = N*(v)[p - nptr[v]] > v; E = N*(v) after w1, then the
-// exclusive neighbours of w1 (above v, not adjacent to v).  Entry:
-// (x << 6) | state(v, x) | state(w1, x) << 2.  Returns B, or -1 if p is not
-// a unit (its neighbour is below v).
-__device__ __forceinline__ int build_level2(const EnumArgs &a, long long p, int v, uint32_t *out_w1,
-                                            uint32_t *out_s01, const Scratch &sc, int which, uint32_t **E_out,
-                                            int lane) {
+// Extension list of the prefix {v, w1} for k >= 4 (unit = arc position p in
+// row v, w1 = N*(v)[p - nptr[v]] > v): N*(v) after w1, then the exclusive
+// neighbours of w1 (above v, not adjacent to v).  Entry states:
+// state(v, x) | state(w1, x) << 2.  Returns B.
+__device__ __forceinline__ int build_level2(const EnumArgs &a, long long p, int v, uint32_t w1, const Scratch &sc,
+                                            uint32_t **E_out, int lane) {
     const long long rb = a.nptr[v];
     const int t = (int)(p - rb);
-    if (t < a.lo[v]) return -1;
-    const uint32_t e = __ldg(a.nbr + p);
-    const uint32_t w1 = e >> 2;
     const int dv = a.deg[v], dw = a.deg[w1];
     const int A = dv - t - 1;
     const long long ub = (long long)A + dw;
-    uint32_t *E = ub <= sc.cap ? sc.buf[which] : sc.ovf[which];
+    uint32_t *E = ub <= sc.cap ? sc.buf[0] : sc.ovf[0];
     for (int q = lane; q < A; q += kWarp) {
         const uint32_t xe = __ldg(a.nbr + rb + t + 1 + q);
         const uint32_t x = xe >> 2;
@@ -284,71 +363,104 @@ __device__ __forceinline__ int build_level2(const EnumArgs &a, long long p, int 
         pos += __popc(ball);
     }
     __syncwarp();
-    *out_w1 = w1;
-    *out_s01 = e & 3u;
     *E_out = E;
     return pos;
 }
 
-// Split rows [0, B) with per-row work work(j) into chunks of about kTarget;
-// push every chunk but the first to the queue.  Returns the end of the first
-// chunk; *rest_lo is where rows the full queue could not take begin (B if
-// none).
+// Reserve n queue slots; returns the first.
+__device__ __forceinline__ unsigned long long reserve(const EnumArgs &a, unsigned long long n, int lane) {
+    unsigned long long idx = 0;
+    if (lane == 0) idx = atomicAdd(&a.info->queue_tail, n);
+    return __shfl_sync(kFull, idx, 0);
+}
+
+// Queue a heavy unit whose extension list has at most Bu entries as chunks
+// of about kTarget work: its Pu = ceil(Bu/2) virtual rows all carry Bu-1
+// pairs (plus an allowance D per list row for exclusive leaves), so equal
+// ranges of virtual rows are equal work.  Returns the first virtual row whose
+// chunk did not fit the queue (Pu when all fit); the caller runs the rest.
+__device__ int queue_closed_form(const EnumArgs &a, uint32_t unit, int v, long long Bu, long long D, int lane) {
+    const long long Pu = (Bu + 1) / 2;
+    const long long W = Pu * (Bu - 1) + Bu * D;
+    long long C = (W + kTarget - 1) / kTarget;
+    if (C > Pu) C = Pu;
+    if (C < 1) C = 1;
+    const unsigned long long base = reserve(a, (unsigned long long)C, lane);
+    int rest = (int)Pu;
+    for (long long c0 = 0; c0 < C; c0 += kWarp) {
+        const long long c = c0 + lane;
+        bool lost = false;
+        if (c < C) {
+            const uint32_t plo = (uint32_t)(c * Pu / C), phi = (uint32_t)((c + 1) * Pu / C);
+            if (base + c < a.queue_cap) a.queue[base + c] = make_uint4(unit, plo, phi, (uint32_t)v);
+            else lost = true;
+        }
+        const unsigned ball = __ballot_sync(kFull, lost);
+        if (ball) {
+            rest = (int)((c0 + __ffs(ball) - 1) * Pu / C);
+            break;
+        }
+    }
+    return rest;
+}
+
+// Queue rows [0, B) with per-row work work(j) as chunks of about kTarget
+// (two passes over the rows: count, then write).  Returns the first row the
+// queue could not take (B when all fit).
 template <typename WorkFn>
-__device__ int split_rows(const EnumArgs &a, uint32_t unit, int B, WorkFn work, int *rest_lo, int lane) {
-    int cur = 0, first_end = -1;
-    long long acc = 0;
-    *rest_lo = B;
-    bool full = false;
-    for (int jb = 0; jb < B && !full; jb += kWarp) {
-        const int j = jb + lane;
-        const long long w = j < B ? work(j) : 0;
-        const long long incl = incl_scan64(w, lane);
-        const long long btot = __shfl_sync(kFull, incl, kWarp - 1);
-        long long used = 0;
-        for (;;) {
-            const unsigned ball = __ballot_sync(kFull, j < B && acc + incl - used >= kTarget);
-            if (!ball) {
-                acc += btot - used;
-                break;
-            }
-            const int r = __ffs(ball) - 1;
-            const int end = jb + r + 1;
-            if (first_end < 0) {
-                first_end = end;
-            } else {
-                unsigned long long idx = 0;
-                if (lane == 0) idx = atomicAdd(&a.info->queue_tail, 1ull);
-                idx = __shfl_sync(kFull, idx, 0);
-                if (idx < a.queue_cap) {
-                    if (lane == 0) a.queue[idx] = make_uint4(unit, (uint32_t)cur, (uint32_t)end, 0u);
-                } else {
-                    *rest_lo = cur;
-                    full = true;
+__device__ int queue_rows(const EnumArgs &a, uint32_t unit, int v, int B, WorkFn work, int lane) {
+    unsigned long long base = 0, lim = 0;
+    for (int pass = 0; pass < 2; pass++) {
+        int cur = 0;
+        long long acc = 0;
+        unsigned long long nchunk = 0;
+        for (int jb = 0; jb < B; jb += kWarp) {
+            const int j = jb + lane;
+            const long long w = j < B ? work(j) : 0;
+            const long long incl = incl_scan64(w, lane);
+            const long long btot = __shfl_sync(kFull, incl, kWarp - 1);
+            long long used = 0;
+            for (;;) {
+                const unsigned ball = __ballot_sync(kFull, j < B && acc + incl - used >= kTarget);
+                if (!ball) {
+                    acc += btot - used;
                     break;
                 }
-            }
-            cur = end;
-            used = __shfl_sync(kFull, incl, r);
-            acc = 0;
-        }
-    }
-    if (!full && cur < B) {
-        if (first_end < 0) {
-            first_end = B;
-        } else {
-            unsigned long long idx = 0;
-            if (lane == 0) idx = atomicAdd(&a.info->queue_tail, 1ull);
-            idx = __shfl_sync(kFull, idx, 0);
-            if (idx < a.queue_cap) {
-                if (lane == 0) a.queue[idx] = make_uint4(unit, (uint32_t)cur, (uint32_t)B, 0u);
-            } else {
-                *rest_lo = cur;
+                const int r = __ffs(ball) - 1;
+                const int end = jb + r + 1;
+                if (pass == 1) {
+                    if (base + nchunk >= lim) return cur;
+                    if (lane == 0) a.queue[base + nchunk] = make_uint4(unit, (uint32_t)cur, (uint32_t)end, (uint32_t)v);
+                }
+                nchunk++;
+                cur = end;
+                used = __shfl_sync(kFull, incl, r);
+                acc = 0;
             }
         }
+        if (cur < B) {
+            if (pass == 1) {
+                if (base + nchunk >= lim) return cur;
+                if (lane == 0) a.queue[base + nchunk] = make_uint4(unit, (uint32_t)cur, (uint32_t)B, (uint32_t)v);
+            }
+            nchunk++;
+        }
+        if (pass == 0) {
+            base = reserve(a, nchunk, lane);
+            lim = min(base + nchunk, a.queue_cap);
+        }
     }
-    if (first_end < 0) first_end = B;
-    return first_end;
+    return B;
+}
+
+// Sum of work(j) over rows [0, B), warp-reduced.
+template <typename WorkFn>
+__device__ __forceinline__ long long total_work(int B, WorkFn work, int lane) {
+    long long s = 0;
+    for (int j = lane; j < B; j += kWarp) s += work(j);
+#pragma unroll
+    for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(kFull, s, d);
+    return s;
 }
 
 __device__ __forceinline__ int row_of(const long long *__restrict__ nptr, int n, long long p) {
@@ -361,14 +473,27 @@ __device__ __forceinline__ int row_of(const long long *__restrict__ nptr, int n,
     return lo;
 }
 
+// Run part [jlo, jhi) of one unit: virtual rows of its extension list for
+// k = 3, 4, rows of the level-2 list E2 for k = 5.  In phase 1 (jlo = 0,
+// jhi = all) a unit with more than kLight estimated work is queued in chunks
+// instead.  D is the per-row allowance for exclusive neighbours (mean degree
+// + 1).
 template <int K>
-__device__ void process_unit(const EnumArgs &a, const Tables &tb, Sink<K> &sink, const Scratch &sc,
-                             uint32_t unit, int v, int jlo, int jhi, bool phase1, int lane) {
+__device__ void process_unit(const EnumArgs &a, Sink<K> &sink, const Scratch &sc, uint32_t unit, int v, int jlo,
+                             int jhi, bool phase1, long long D, int lane) {
+    using L = Layout<K>;
     if (K == 3) {
-        // prefix {v}; E = neighbours of v above v, entry (x << 6) | state(v, x)
+        // prefix {v}; E = neighbours of v above v
         const int dv = a.deg[v], l = a.lo[v];
         const int B = dv - l;
         if (B <= 0) return;
+        const int P = (B + 1) / 2;
+        int hi = min(jhi, P), rest = P;
+        if (phase1 && (long long)P * (B - 1) + (long long)B * D > kLight) {
+            rest = queue_closed_form(a, unit, v, B, D, lane);
+            if (rest >= P) return;
+            hi = 0;
+        }
         uint32_t *E = B <= sc.cap ? sc.buf[0] : sc.ovf[0];
         const long long rb = a.nptr[v] + l;
         for (int q = lane; q < B; q += kWarp) {
@@ -376,61 +501,76 @@ __device__ void process_unit(const EnumArgs &a, const Tables &tb, Sink<K> &sink,
             E[q] = ((xe >> 2) << 6) | (xe & 3u);
         }
         __syncwarp();
-        int rest = B;
-        if (phase1) {
-            const long long ub = (long long)B * (B - 1) / 2 + (long long)B * a.info->maxdeg;
-            if (ub > kTarget)
-                jhi = split_rows(a, unit, B, [&](int j) { return (long long)(B - 1 - j) + a.deg[E[j] >> 6] + 1; },
-                                 &rest, lane);
-        }
         const uint32_t pm[1] = {(uint32_t)v};
-        leaves<K>(a, tb, sink, E, B, jlo, min(jhi, B), pm, 0u, (uint32_t)v, lane);
-        if (rest < B) leaves<K>(a, tb, sink, E, B, rest, B, pm, 0u, (uint32_t)v, lane);
+        leaves<K>(a, sink, E, B, jlo, hi, pm, 0u, (uint32_t)v, lane);
+        if (rest < P) leaves<K>(a, sink, E, B, rest, P, pm, 0u, (uint32_t)v, lane);
+        sink.flush();
         __syncwarp();
         return;
     }
-    uint32_t w1, s01, *E2;
-    const int B2 = build_level2(a, unit, v, &w1, &s01, sc, 0, &E2, lane);
-    if (B2 <= 0) return;
-    int rest = B2;
-    if (K == 4) {
-        if (phase1) {
-            const long long ub = (long long)B2 * (B2 - 1) / 2 + (long long)B2 * a.info->maxdeg;
-            if (ub > kTarget)
-                jhi = split_rows(a, unit, B2, [&](int j) { return (long long)(B2 - 1 - j) + a.deg[E2[j] >> 6] + 1; },
-                                 &rest, lane);
+    const long long rb = a.nptr[v];
+    const int t = (int)(unit - rb);
+    if (t < a.lo[v]) return;  // neighbour below v: not a unit
+    const uint32_t e = __ldg(a.nbr + unit);
+    const uint32_t w1 = e >> 2, s01 = e & 3u;
+    int hi = jhi, rest = 0x7FFFFFFF;
+    if (K == 4 && phase1) {
+        long long Bu = (long long)(a.deg[v] - t - 1) + a.deg[w1];
+        if (Bu > a.n - 2) Bu = a.n - 2;
+        if (Bu <= 0) return;
+        const long long Pu = (Bu + 1) / 2;
+        if (Pu * (Bu - 1) + Bu * D > kLight) {
+            rest = queue_closed_form(a, unit, v, Bu, D, lane);
+            if (rest >= Pu) return;
+            hi = 0;
         }
+    }
+    uint32_t *E2;
+    const int B2 = build_level2(a, unit, v, w1, sc, &E2, lane);
+    if (B2 <= 0) return;
+    if (K == 4) {
+        // rows of E2 are paired into virtual rows
+        const int P2 = (B2 + 1) / 2;
+        hi = min(hi, P2);
+        rest = min(rest, P2);
         const uint32_t pm[2] = {(uint32_t)v, w1};
-        const uint32_t pcode = tb.p01[s01];
-        leaves<K>(a, tb, sink, E2, B2, jlo, min(jhi, B2), pm, pcode, (uint32_t)v, lane);
-        if (rest < B2) leaves<K>(a, tb, sink, E2, B2, rest, B2, pm, pcode, (uint32_t)v, lane);
+        const uint32_t pcode = s01 << (L::SH_ROW + 4);  // field of slot 1 sits above slot 2's
+        leaves<K>(a, sink, E2, B2, jlo, hi, pm, pcode, (uint32_t)v, lane);
+        if (rest < P2) leaves<K>(a, sink, E2, B2, rest, P2, pm, pcode, (uint32_t)v, lane);
+        sink.flush();
         __syncwarp();
         return;
     }
+    hi = min(hi, B2);
+    rest = min(rest, B2);
     // K == 5: one more level.  Row j2 of E2 gives w2 and the list E3.
     if (phase1) {
-        jhi = split_rows(a, unit, B2,
-                         [&](int j) {
-                             const long long b = (long long)(B2 - 1 - j) + a.deg[E2[j] >> 6];
-                             return b * (b - 1) / 2 + 4 * b + 1;
-                         },
-                         &rest, lane);
+        auto work = [&](int j) {
+            const long long b = (long long)(B2 - 1 - j) + a.deg[e_id(E2[j])];
+            return b * (b - 1) / 2 + b * D + 1;
+        };
+        if (total_work(B2, work, lane) > kLight) {
+            rest = queue_rows(a, unit, v, B2, work, lane);
+            hi = 0;
+        }
     }
-    const uint32_t pc01 = tb.p01[s01];
+    // fields: slot 1 at bit 18 (state(v, w1)), slot 2 at bit 14 (w2's states
+    // to v and w1)
+    const uint32_t pc01 = s01 << 18;
     for (int pass = 0; pass < 2; pass++) {
         const int r0 = pass == 0 ? jlo : rest;
-        const int r1 = pass == 0 ? min(jhi, B2) : B2;
+        const int r1 = pass == 0 ? hi : B2;
         for (int j2 = r0; j2 < r1; j2++) {
             const uint32_t e2 = E2[j2];
-            const uint32_t w2 = e2 >> 6;
-            const uint32_t pcode = pc01 | tb.s2[e2 & 15u];
+            const uint32_t w2 = e_id(e2);
+            const uint32_t pcode = pc01 | ((e2 & 15u) << 14);
             const int A3 = B2 - 1 - j2;
             const int dw = a.deg[w2];
             const long long ub = (long long)A3 + dw;
             uint32_t *E3 = ub <= sc.cap ? sc.buf[1] : sc.ovf[1];
             for (int q = lane; q < A3; q += kWarp) {
                 const uint32_t xe = E2[j2 + 1 + q];
-                const uint32_t x = xe >> 6;
+                const uint32_t x = e_id(xe);
                 E3[q] = (x << 6) | (xe & 15u) | (probe(a.state, a.pitch, w2, x) << 4);
             }
             const long long wb = a.nptr[w2];
@@ -450,34 +590,25 @@ __device__ void process_unit(const EnumArgs &a, const Tables &tb, Sink<K> &sink,
             }
             __syncwarp();
             const uint32_t pm[3] = {(uint32_t)v, w1, w2};
-            leaves<K>(a, tb, sink, E3, pos, 0, pos, pm, pcode, (uint32_t)v, lane);
+            leaves<K>(a, sink, E3, pos, 0, (pos + 1) / 2, pm, pcode, (uint32_t)v, lane);
             __syncwarp();
         }
         if (rest >= B2) break;
     }
+    sink.flush();
+    __syncwarp();
 }
 
 template <int K>
-__global__ void __launch_bounds__(kThreads, K == 5 ? 3 : 4) k_enum(EnumArgs a, int phase) {
+__global__ void __launch_bounds__(kThreads, K == 5 ? 3 : ACC_MINB34) k_enum(EnumArgs a, int phase) {
     using L = Layout<K>;
     extern __shared__ __align__(16) unsigned char smem[];
-    Tables &tb = *reinterpret_cast<Tables *>(smem);
-    int16_t *lut_s = reinterpret_cast<int16_t *>(smem + L::tables);
-    uint32_t *pending = reinterpret_cast<uint32_t *>(smem + L::tables + L::lut);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + L::tables + L::lut + L::pending);
-    uint32_t *ebuf = reinterpret_cast<uint32_t *>(smem + L::tables + L::lut + L::pending + L::hist);
+    int16_t *lut_s = reinterpret_cast<int16_t *>(smem);
+    uint32_t *pending = reinterpret_cast<uint32_t *>(smem + L::lut);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + L::lut + L::pending);
+    uint32_t *ebuf = reinterpret_cast<uint32_t *>(smem + L::lut + L::pending + L::hist);
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
 
-    // tables: slot codes for every state vector, pair codes
-    for (int i = tid; i < 64; i += blockDim.x) {
-        tb.t2[i] = slot_bits(K, K - 2, (uint32_t)i, K - 2);
-        tb.t3[i] = slot_bits(K, K - 1, (uint32_t)i, K - 2);
-        if (i < 16) tb.s2[i] = K == 5 ? slot_bits(K, 2, (uint32_t)i, 2) : 0u;
-        if (i < 4) {
-            tb.tp[i] = pair_bits(K, K - 2, K - 1, (uint32_t)i);
-            tb.p01[i] = pair_bits(K, 0, 1, (uint32_t)i);
-        }
-    }
     if (L::SMEM_LUT)
         for (int i = tid; i < (1 << L::NB); i += blockDim.x) lut_s[i] = a.lut[i];
     const int hist_words = K == 5 ? L::NCLS : kWarpsPerBlock * L::NCLS;
@@ -492,6 +623,8 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : 4) k_enum(EnumArgs a, i
     sink.pending = pending;
     sink.since = 0;
     sink.status = a.status;
+    sink.run_cls = -1;
+    sink.run_len = 0;
 
     Scratch sc;
     const long long gw = (long long)blockIdx.x * kWarpsPerBlock + wib;
@@ -500,9 +633,11 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : 4) k_enum(EnumArgs a, i
     sc.ovf[0] = a.scratch + gw * a.scratch_per_warp;
     sc.ovf[1] = sc.ovf[0] + a.scratch_per_warp / 2;
     sc.cap = L::CAP;
+    const long long nnz = a.info->nnz;
+    const long long D = (a.n > 0 ? nnz / a.n : 0) + 1;
 
     if (phase == 1) {
-        const long long nunits = K == 3 ? (long long)a.n : a.info->nnz;
+        const long long nunits = K == 3 ? (long long)a.n : nnz;
         for (;;) {
             unsigned long long u0 = 0;
             if (lane == 0) u0 = atomicAdd(&a.info->unit_ctr, (unsigned long long)kGrab);
@@ -516,7 +651,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : 4) k_enum(EnumArgs a, i
                 } else {
                     while (a.nptr[v + 1] <= u) v++;
                 }
-                process_unit<K>(a, tb, sink, sc, (uint32_t)u, v, 0, 0x7FFFFFFF, true, lane);
+                process_unit<K>(a, sink, sc, (uint32_t)u, v, 0, 0x7FFFFFFF, true, D, lane);
             }
         }
     } else {
@@ -527,8 +662,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : 4) k_enum(EnumArgs a, i
             idx = __shfl_sync(kFull, idx, 0);
             if (idx >= tail) break;
             const uint4 it = a.queue[idx];
-            const int v = K == 3 ? (int)it.x : row_of(a.nptr, a.n, (long long)it.x);
-            process_unit<K>(a, tb, sink, sc, it.x, v, (int)it.y, (int)it.z, false, lane);
+            process_unit<K>(a, sink, sc, it.x, (int)it.w, (int)it.y, (int)it.z, false, D, lane);
         }
     }
 
@@ -563,13 +697,12 @@ int blocks_per_sm() {
 }
 
 template <int K>
-int launch_k(const EnumArgs &a, int num_sms, cudaStream_t s) {
+int launch_k(const EnumArgs &a, int num_sms, int phase, cudaStream_t s) {
     const int bps = blocks_per_sm<K>();
     if (bps < 1) return ACC_ERR_CUDA;
     const int grid = num_sms * bps;
-    k_enum<K><<<grid, kThreads, Layout<K>::total, s>>>(a, 1);
-    k_enum<K><<<grid, kThreads, Layout<K>::total, s>>>(a, 2);
-    return cudaGetLastError() == cudaSuccess ? 2 : ACC_ERR_CUDA;
+    k_enum<K><<<grid, kThreads, Layout<K>::total, s>>>(a, phase);
+    return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
 
 }  // namespace
@@ -580,11 +713,11 @@ int enum_grid_warps(int k, int num_sms) {
     return num_sms * bps * kWarpsPerBlock;
 }
 
-int launch_enumerate(int k, const EnumArgs &a, int num_sms, cudaStream_t s) {
+int launch_enumerate(int k, const EnumArgs &a, int num_sms, int phase, cudaStream_t s) {
     switch (k) {
-    case 3: return launch_k<3>(a, num_sms, s);
-    case 4: return launch_k<4>(a, num_sms, s);
-    case 5: return launch_k<5>(a, num_sms, s);
+    case 3: return launch_k<3>(a, num_sms, phase, s);
+    case 4: return launch_k<4>(a, num_sms, phase, s);
+    case 5: return launch_k<5>(a, num_sms, phase, s);
     default: return ACC_ERR_K;
     }
 }

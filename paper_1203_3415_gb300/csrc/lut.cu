@@ -128,9 +128,32 @@ __global__ void k_finish(const uint32_t *__restrict__ canon, const int *__restri
     if (cc == c && r < ncls) class_code[r] = c;
 }
 
+// The same table indexed in the state-vector layout the enumeration kernels
+// use: field f_t = sum_{i<t} state(w_i, w_t) << 2i for slots t = k-1 (lowest
+// bits) down to 1 (highest), state bit 0 = arc w_i -> w_t, bit 1 = arc
+// w_t -> w_i.  Thread per layout code: map it to the canonical code, copy
+// that code's class.
+template <int K>
+__global__ void k_relayout(const int16_t *__restrict__ lut, int16_t *lut_sv) {
+    const uint32_t cp = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cp >= (1u << (K * (K - 1)))) return;
+    uint32_t c = 0;
+    int off = 0;
+    for (int t = K - 1; t >= 1; t--) {
+        for (int i = 0; i < t; i++) {
+            const uint32_t st = (cp >> (off + 2 * i)) & 3u;
+            if (st & 1u) c |= 1u << code_bit(K, i, t);
+            if (st & 2u) c |= 1u << code_bit(K, t, i);
+        }
+        off += 2 * t;
+    }
+    lut_sv[cp] = lut[c];
+}
+
 }  // namespace
 
-int launch_build_lut(int k, uint32_t *canon, int *rank, int16_t *lut, uint32_t *class_code, cudaStream_t s) {
+int launch_build_lut(int k, uint32_t *canon, int *rank, int16_t *lut, uint32_t *class_code, int16_t *lut_sv,
+                     cudaStream_t s) {
     const uint32_t ncodes = 1u << code_bits(k);
     const int threads = 256;
     const int grid = (int)((ncodes + threads - 1) / threads);
@@ -142,7 +165,12 @@ int launch_build_lut(int k, uint32_t *canon, int *rank, int16_t *lut, uint32_t *
     }
     k_rank<<<1, 1024, 0, s>>>(canon, ncodes, rank);
     k_finish<<<grid, threads, 0, s>>>(canon, rank, ncodes, num_classes(k), lut, class_code);
-    return cudaGetLastError() == cudaSuccess ? 3 : ACC_ERR_CUDA;
+    switch (k) {
+    case 3: k_relayout<3><<<grid, threads, 0, s>>>(lut, lut_sv); break;
+    case 4: k_relayout<4><<<grid, threads, 0, s>>>(lut, lut_sv); break;
+    default: k_relayout<5><<<grid, threads, 0, s>>>(lut, lut_sv); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? 4 : ACC_ERR_CUDA;
 }
 
 }  // namespace acc
