@@ -162,6 +162,34 @@ ACC_API int acc_motif_last_stats(acc_ctx *ctx, int64_t *h_stats);
 ACC_API int acc_ctx_set_timing(acc_ctx *ctx, int on);
 ACC_API int acc_motif_last_timing(acc_ctx *ctx, float *h_ms);
 
+/*
+ * Build the code -> class table for k without allocating anything.
+ *
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory where they need the table -- code under a fixed
+ * memory budget handed out up front, a framework that owns the device
+ * allocator, or work being captured into a CUDA graph.  It needs no context
+ * and calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ *  k             3, 4 or 5 (ACC_ERR_K otherwise).
+ *  stream        cudaStream_t (void*); the call only enqueues work.
+ *  d_table       device int16[2^(k(k-1))]: receives the same table as
+ *                acc_motif_copy_table (-1 = not weakly connected).
+ *  d_class_code  device uint32[num_classes(k)]: canonical code of each class,
+ *                as acc_motif_class_code.
+ *
+ * Working memory: a fixed 8 MiB array inside the library (room for the
+ * 2^20 codes of k = 5; anything larger is rejected with ACC_ERR_TOO_LARGE).
+ * Every GPU that loads the library holds those 8 MiB until the process
+ * exits.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array: each call writes
+ * every word of it that it reads, so no state carries over, but calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.
+ */
+ACC_API int acc_motif_build_table_static(int k, void *stream, int16_t *d_table, uint32_t *d_class_code);
+
 #ifdef __cplusplus
 }
 #endif

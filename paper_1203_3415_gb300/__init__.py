@@ -36,6 +36,7 @@ EXPORTS = (
     "acc_strerror", "acc_motif_num_classes", "acc_ctx_create", "acc_ctx_destroy", "acc_motif_prepare",
     "acc_motif_count", "acc_motif_count_host", "acc_motif_class_code", "acc_motif_classify_code",
     "acc_motif_copy_table", "acc_motif_last_stats", "acc_ctx_set_timing", "acc_motif_last_timing",
+    "acc_motif_build_table_static",
 )
 
 
@@ -60,6 +61,7 @@ def _load():
     lib.acc_motif_last_stats.argtypes = [vp, vp]
     lib.acc_ctx_set_timing.argtypes = [vp, ctypes.c_int]
     lib.acc_motif_last_timing.argtypes = [vp, vp]
+    lib.acc_motif_build_table_static.argtypes = [ctypes.c_int, vp, vp, vp]
     return lib
 
 
@@ -147,6 +149,12 @@ def acc_ctx_set_timing(ctx: int, on: int) -> int:
 
 def acc_motif_last_timing(ctx: int, h_ms: int) -> int:
     return _L().acc_motif_last_timing(ctx, h_ms)
+
+
+def acc_motif_build_table_static(k: int, stream: int, d_table: int, d_class_code: int) -> int:
+    """Table build that allocates nothing (working memory is a fixed array in
+    the library); for callers that cannot allocate device memory."""
+    return _L().acc_motif_build_table_static(k, stream, d_table, d_class_code)
 
 
 # ---------------------------------------------------------------------------

@@ -174,3 +174,79 @@ int launch_build_lut(int k, uint32_t *canon, int *rank, int16_t *lut, uint32_t *
 }
 
 }  // namespace acc
+
+// ---------------------------------------------------------------------------
+// Allocation-free table build.
+//
+// Some callers cannot allocate device memory at the point where they need the
+// table: code running under a strict memory budget that hands out every byte
+// up front, a framework that owns the device allocator, or a stream being
+// captured into a CUDA graph (where a cudaMalloc would break the capture).
+// acc_motif_build_table_static serves them: the caller passes the output
+// buffers, and the working memory comes from the fixed array below, which is
+// part of the library image (every GPU that loads the library holds these
+// 8 MiB until the process exits).
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace acc {
+namespace {
+
+// Canonical code (first half) and rank (second half) of every adjacency code
+// of the largest supported k (5: 2^20 codes).
+constexpr size_t kStaticCodes = size_t(1) << 20;
+static __device__ __align__(256) uint32_t g_table_scratch[2 * kStaticCodes];
+
+constexpr int kMaxDevices = 64;
+uint32_t *g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mu;
+
+// Device address of g_table_scratch on the current device, looked up once per
+// device (in host code the symbol name is only a stand-in, not an address).
+int static_scratch(uint32_t **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ACC_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_table_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return ACC_ERR_CUDA;
+        }
+        g_scratch_addr[dev] = static_cast<uint32_t *>(p);
+    }
+    *out = g_scratch_addr[dev];
+    return ACC_OK;
+}
+
+}  // namespace
+}  // namespace acc
+
+extern "C" ACC_API int acc_motif_build_table_static(int k, void *stream, int16_t *d_table,
+                                                    uint32_t *d_class_code) {
+    using namespace acc;
+    if (k < 3 || k > 5) return ACC_ERR_K;
+    if (!d_table || !d_class_code) return ACC_ERR_ARG;
+    const uint32_t ncodes = 1u << code_bits(k);
+    if (ncodes > kStaticCodes) return ACC_ERR_TOO_LARGE;
+    uint32_t *scratch = nullptr;
+    const int rc = static_scratch(&scratch);
+    if (rc) return rc;
+    // every scratch word the kernels read is written earlier in the same
+    // call, so nothing carries over from the previous call and nothing has to
+    // be cleared
+    uint32_t *canon = scratch;
+    int *rank = reinterpret_cast<int *>(scratch + kStaticCodes);
+    const int threads = 256;
+    const int grid = (int)((ncodes + threads - 1) / threads);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (k) {
+    case 3: k_canon<3><<<grid, threads, 0, s>>>(canon); break;
+    case 4: k_canon<4><<<grid, threads, 0, s>>>(canon); break;
+    default: k_canon<5><<<grid, threads, 0, s>>>(canon); break;
+    }
+    k_rank<<<1, 1024, 0, s>>>(canon, ncodes, rank);
+    k_finish<<<grid, threads, 0, s>>>(canon, rank, ncodes, num_classes(k), d_table, d_class_code);
+    return cudaGetLastError() == cudaSuccess ? ACC_OK : ACC_ERR_CUDA;
+}
