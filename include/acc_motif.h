@@ -128,6 +128,63 @@ ACC_API int acc_motif_count(acc_ctx *ctx, const int64_t *d_rowptr, const int32_t
 ACC_API int acc_motif_count_host(acc_ctx *ctx, const int64_t *h_rowptr, const int32_t *h_col, int32_t n,
                          int64_t m, int k, int64_t *h_counts);
 
+/*
+ * Batched form: many graphs counted by one sequence of launches (the
+ * significance step of the motif pipeline counts a real graph and an ensemble
+ * of randomised copies, Implementation section, steps i-iii; the paper counts
+ * each graph separately).
+ *
+ * acc_graph_desc describes one graph in device memory, with the same layout
+ * and rules as acc_motif_count's arguments.
+ */
+typedef struct {
+    const int64_t *rowptr; /* device int64[n+1] */
+    const int32_t *col;    /* device int32[m] */
+    int32_t n;
+    int64_t m;
+} acc_graph_desc;
+
+/*
+ * Prepare a batch of B graphs (h_graphs: host array of B descriptors) for
+ * k: validates sizes, lays out every graph's buffers in the context's
+ * workspace, uploads the descriptors and builds the table for k; waits.  The
+ * graphs' device arrays must stay valid and unchanged until the batch's last
+ * acc_motif_batch_run.  Preparing replaces the previous batch.  Errors:
+ * ACC_ERR_ARG, ACC_ERR_K, ACC_ERR_INPUT, ACC_ERR_TOO_LARGE (some n above
+ * ACC_MAX_N), ACC_ERR_OVERFLOW (more than 2^31-1 vertices or arcs in total),
+ * ACC_ERR_NOMEM, ACC_ERR_CUDA.
+ */
+ACC_API int acc_motif_batch_prepare(acc_ctx *ctx, const acc_graph_desc *h_graphs, int32_t B, int k, void *stream);
+
+/*
+ * Count every graph of the prepared batch: d_counts is device
+ * int64[B * num_classes(k)], row g = graph g, overwritten.  d_status as in
+ * acc_motif_count.  With d_status non-NULL the call only enqueues kernels
+ * (no allocation, no copy, no wait), so it can be captured into a CUDA graph
+ * and replayed; a captured run stays valid while no later call on the
+ * context grows its workspace (prepare the largest batch first).
+ */
+ACC_API int acc_motif_batch_run(acc_ctx *ctx, void *stream, int64_t *d_counts, int32_t *d_status);
+
+/* acc_motif_batch_prepare followed by acc_motif_batch_run. */
+ACC_API int acc_motif_count_batch(acc_ctx *ctx, const acc_graph_desc *h_graphs, int32_t B, int k, void *stream,
+                                  int64_t *d_counts, int32_t *d_status);
+
+/*
+ * Z-scores of class counts against randomised copies (significance step of
+ * the motif pipeline; the paper gives no formula).  d_counts is device
+ * int64[groups][group_size][num_classes(k)]: entry 0 of each group is the
+ * real graph, entries 1..R (R = group_size - 1 >= 1) its randomisations.
+ * d_z is device double[groups][num_classes(k)]:
+ *   Z_c = (N_c - mu_c) / sigma_c,  mu_c = (sum_i N_ic) / R,
+ *   sigma_c = sqrt(sum_i (N_ic - mu_c)^2 / R) (population deviation,
+ *   accumulated in increasing i), NaN when sigma_c = 0,
+ * every step an IEEE round-to-nearest double operation (no fused
+ * multiply-add).  Stream-ordered; no context needed.
+ */
+ACC_API int acc_motif_zscores(const int64_t *d_counts, int32_t groups, int32_t group_size, int k, void *stream,
+                              double *d_z);
+
 /* Canonical adjacency code of class cls (0 <= cls < num_classes(k)). */
 ACC_API int acc_motif_class_code(acc_ctx *ctx, int k, int32_t cls, uint32_t *code);
 

@@ -34,7 +34,8 @@ NUM_CLASSES = {3: 13, 4: 199, 5: 9364}
 # every symbol include/acc_motif.h declares, in declaration order
 EXPORTS = (
     "acc_strerror", "acc_motif_num_classes", "acc_ctx_create", "acc_ctx_destroy", "acc_motif_prepare",
-    "acc_motif_count", "acc_motif_count_host", "acc_motif_class_code", "acc_motif_classify_code",
+    "acc_motif_count", "acc_motif_count_host", "acc_motif_batch_prepare", "acc_motif_batch_run",
+    "acc_motif_count_batch", "acc_motif_zscores", "acc_motif_class_code", "acc_motif_classify_code",
     "acc_motif_copy_table", "acc_motif_last_stats", "acc_ctx_set_timing", "acc_motif_last_timing",
     "acc_motif_build_table_static",
 )
@@ -55,6 +56,10 @@ def _load():
     lib.acc_motif_prepare.argtypes = [vp, ctypes.c_int, vp]
     lib.acc_motif_count.argtypes = [vp, vp, vp, i32, i64, ctypes.c_int, vp, vp, vp]
     lib.acc_motif_count_host.argtypes = [vp, vp, vp, i32, i64, ctypes.c_int, vp]
+    lib.acc_motif_batch_prepare.argtypes = [vp, vp, i32, ctypes.c_int, vp]
+    lib.acc_motif_batch_run.argtypes = [vp, vp, vp, vp]
+    lib.acc_motif_count_batch.argtypes = [vp, vp, i32, ctypes.c_int, vp, vp, vp]
+    lib.acc_motif_zscores.argtypes = [vp, i32, i32, ctypes.c_int, vp, vp]
     lib.acc_motif_class_code.argtypes = [vp, ctypes.c_int, i32, ctypes.POINTER(ctypes.c_uint32)]
     lib.acc_motif_classify_code.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(i32)]
     lib.acc_motif_copy_table.argtypes = [vp, ctypes.c_int, vp]
@@ -121,6 +126,30 @@ def acc_motif_count(ctx: int, d_rowptr: int, d_col: int, n: int, m: int, k: int,
 
 def acc_motif_count_host(ctx: int, h_rowptr: int, h_col: int, n: int, m: int, k: int, h_counts: int) -> int:
     return _L().acc_motif_count_host(ctx, h_rowptr, h_col, n, m, k, h_counts)
+
+
+class acc_graph_desc(ctypes.Structure):
+    """One graph of a batch: device rowptr (int64[n+1]) and col (int32[m])."""
+    _fields_ = [("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("n", ctypes.c_int32),
+                ("m", ctypes.c_int64)]
+
+
+def acc_motif_batch_prepare(ctx: int, h_graphs, B: int, k: int, stream: int) -> int:
+    return _L().acc_motif_batch_prepare(ctx, ctypes.cast(h_graphs, ctypes.c_void_p), B, k, stream)
+
+
+def acc_motif_batch_run(ctx: int, stream: int, d_counts: int, d_status: int | None) -> int:
+    return _L().acc_motif_batch_run(ctx, stream, d_counts, d_status)
+
+
+def acc_motif_count_batch(ctx: int, h_graphs, B: int, k: int, stream: int, d_counts: int,
+                          d_status: int | None) -> int:
+    return _L().acc_motif_count_batch(ctx, ctypes.cast(h_graphs, ctypes.c_void_p), B, k, stream, d_counts,
+                                      d_status)
+
+
+def acc_motif_zscores(d_counts: int, groups: int, group_size: int, k: int, stream: int, d_z: int) -> int:
+    return _L().acc_motif_zscores(d_counts, groups, group_size, k, stream, d_z)
 
 
 def acc_motif_class_code(ctx: int, k: int, cls: int) -> int:
@@ -214,6 +243,41 @@ class Counter:
         hp = counts.ctypes.data if isinstance(counts, np.ndarray) else counts.data_ptr()
         _check(acc_motif_count_host(self.ctx, rp, cp if m else 0, n, m, k, hp), "acc_motif_count_host")
         return counts
+
+    def prepare_batch(self, graphs, k: int, stream=None):
+        """Prepare a batch from a list of (rowptr, col, n) CUDA tensors; the
+        tensors must stay alive until the last run_batch."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        descs = (acc_graph_desc * max(1, len(graphs)))()
+        for i, (rowptr, col, n) in enumerate(graphs):
+            assert rowptr.dtype == torch.int64 and col.dtype == torch.int32 and rowptr.is_cuda and col.is_cuda
+            descs[i].rowptr = rowptr.data_ptr()
+            descs[i].col = col.data_ptr() if col.numel() else 0
+            descs[i].n = n
+            descs[i].m = col.numel()
+        self._batch = (len(graphs), k, descs)
+        _check(acc_motif_batch_prepare(self.ctx, descs, len(graphs), k, s.cuda_stream), "acc_motif_batch_prepare")
+
+    def run_batch(self, counts=None, status=None, stream=None):
+        """Counts of the prepared batch as an int64 [B, num_classes] tensor."""
+        import torch
+        B, k, _ = self._batch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if counts is None:
+            counts = torch.empty((B, NUM_CLASSES[k]), dtype=torch.int64, device=f"cuda:{self.device}")
+        _check(acc_motif_batch_run(self.ctx, s.cuda_stream, counts.data_ptr(),
+                                   status.data_ptr() if status is not None else None), "acc_motif_batch_run")
+        return counts
+
+    def zscores(self, counts, groups: int, group_size: int, k: int, stream=None):
+        """Z-scores [groups, num_classes] of counts [groups * group_size, num_classes]."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        z = torch.empty((groups, NUM_CLASSES[k]), dtype=torch.float64, device=counts.device)
+        _check(acc_motif_zscores(counts.data_ptr(), groups, group_size, k, s.cuda_stream, z.data_ptr()),
+               "acc_motif_zscores")
+        return z
 
     def table(self, k: int):
         import numpy as np

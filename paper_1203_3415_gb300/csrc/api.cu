@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -21,12 +22,14 @@ struct acc_ctx {
     int16_t *lut_host[6] = {};
     uint32_t *class_code_host[6] = {};
 
-    // per-graph workspace (grow-only)
+    // workspace (grow-only)
     uint32_t *state = nullptr;
-    size_t state_words = 0;
+    size_t state_cap = 0;
     int *deg = nullptr, *lo = nullptr, *label = nullptr;
     long long *nptr = nullptr;
     size_t n_cap = 0;
+    long long *tiles = nullptr;
+    size_t tiles_cap = 0;
     uint32_t *nbr = nullptr;
     size_t nbr_cap = 0;
     GraphInfo *info = nullptr;
@@ -36,6 +39,17 @@ struct acc_ctx {
     size_t scratch_cap = 0;
     int *status_dev = nullptr;
     int *status_host = nullptr;  // pinned
+
+    // prepared batch
+    GMeta *meta_dev = nullptr;
+    size_t meta_cap = 0;
+    int *gid = nullptr;
+    size_t gid_cap = 0;
+    bool batch_ready = false;
+    int batch_k = 0;
+    GSet batch_set = {};
+    long long batch_words = 0, batch_arcs = 0;
+    int batch_max_n = 0;
 
     // host-buffer entry point
     long long *h2d_rowptr = nullptr;
@@ -136,13 +150,15 @@ fail:
     return rc;
 }
 
-int ensure_workspace(acc_ctx *c, int n, long long m, int k) {
-    const long long pitch = state_pitch(n);
+long long scratch_per_warp(int max_n) { return 2 * (((long long)max_n + 32 + 31) & ~31LL); }
+
+// Workspace for a set of NV vertices in blocks of state_words words, with at
+// most `arcs` arcs and graphs of at most max_n vertices.
+int ensure_workspace(acc_ctx *c, long long NV, long long state_words, long long arcs, int max_n, int k) {
     int rc;
-    if ((rc = grow(&c->state, &c->state_words, (size_t)n * pitch + 4))) return rc;
-    if ((size_t)n + 1 > c->n_cap || !c->deg) {
-        size_t a = 0, b = 0, d = 0;
-        size_t e = 0;
+    if ((rc = grow(&c->state, &c->state_cap, (size_t)state_words + 4))) return rc;
+    if ((size_t)NV + 1 > c->n_cap || !c->deg) {
+        size_t a = 0, b = 0, d = 0, e = 0;
         cudaFree(c->deg);
         cudaFree(c->lo);
         cudaFree(c->nptr);
@@ -150,13 +166,14 @@ int ensure_workspace(acc_ctx *c, int n, long long m, int k) {
         c->deg = c->lo = c->label = nullptr;
         c->nptr = nullptr;
         c->n_cap = 0;
-        if ((rc = grow(&c->deg, &a, (size_t)n + 1))) return rc;
-        if ((rc = grow(&c->lo, &b, (size_t)n + 1))) return rc;
-        if ((rc = grow(&c->nptr, &d, (size_t)n + 1))) return rc;
-        if ((rc = grow(&c->label, &e, (size_t)n + 1))) return rc;
+        if ((rc = grow(&c->deg, &a, (size_t)NV + 1))) return rc;
+        if ((rc = grow(&c->lo, &b, (size_t)NV + 1))) return rc;
+        if ((rc = grow(&c->nptr, &d, (size_t)NV + 1))) return rc;
+        if ((rc = grow(&c->label, &e, (size_t)NV + 1))) return rc;
         c->n_cap = a;
     }
-    if ((rc = grow(&c->nbr, &c->nbr_cap, (size_t)(2 * m) + 1))) return rc;
+    if ((rc = grow(&c->tiles, &c->tiles_cap, (size_t)scan_tiles_needed(NV) + 1))) return rc;
+    if ((rc = grow(&c->nbr, &c->nbr_cap, (size_t)(2 * arcs) + 1))) return rc;
     if (!c->info) {
         if (!ok(cudaMalloc(&c->info, sizeof(GraphInfo)))) return ACC_ERR_NOMEM;
         if (!ok(cudaMemset(c->info, 0, sizeof(GraphInfo)))) return ACC_ERR_CUDA;
@@ -170,9 +187,65 @@ int ensure_workspace(acc_ctx *c, int n, long long m, int k) {
     }
     const int warps = enum_grid_warps(k, c->num_sms);
     if (warps < 0) return warps;
-    const size_t per_warp = 2 * (((size_t)n + 32 + 31) & ~size_t(31));
-    if ((rc = grow(&c->scratch, &c->scratch_cap, per_warp * (size_t)warps))) return rc;
+    if ((rc = grow(&c->scratch, &c->scratch_cap, (size_t)scratch_per_warp(max_n) * (size_t)warps))) return rc;
     return ACC_OK;
+}
+
+// Build + enumerate one graph set into counts[B * num_classes(k)].
+int run_set(acc_ctx *c, const GSet &gs, long long state_words, int max_n, int k, bool relabel, cudaStream_t s,
+            int64_t *counts, int *status) {
+    int launches = 0;
+    c->timed_call = c->timing;
+    if (c->timing && !ok(cudaEventRecord(c->ev[0], s))) return ACC_ERR_CUDA;
+    int rc = launch_build_graph(gs, state_words, c->state, c->deg, c->lo, c->nptr, c->tiles, c->nbr, c->label,
+                                c->info, status, reinterpret_cast<unsigned long long *>(counts),
+                                (long long)gs.B * num_classes(k), relabel, c->num_sms, s);
+    if (rc < 0) return rc;
+    launches += rc;
+    if (c->timing && !ok(cudaEventRecord(c->ev[1], s))) return ACC_ERR_CUDA;
+    EnumArgs a;
+    a.state = c->state;
+    a.deg = c->deg;
+    a.lo = c->lo;
+    a.nptr = c->nptr;
+    a.nbr = c->nbr;
+    a.lut = c->lut_sv[k];
+    a.gs = gs;
+    a.max_n = max_n;
+    a.info = c->info;
+    a.queue = c->queue;
+    a.queue_cap = c->queue_cap;
+    a.scratch = c->scratch;
+    a.scratch_per_warp = scratch_per_warp(max_n);
+    a.counts = reinterpret_cast<unsigned long long *>(counts);
+    a.status = status;
+    const bool any = gs.NV > 0;
+    if (any) {
+        rc = launch_enumerate(k, a, c->num_sms, 1, s);
+        if (rc < 0) return rc;
+        launches += rc;
+    }
+    if (c->timing && !ok(cudaEventRecord(c->ev[3], s))) return ACC_ERR_CUDA;
+    if (any) {
+        rc = launch_enumerate(k, a, c->num_sms, 2, s);
+        if (rc < 0) return rc;
+        launches += rc;
+    }
+    if (c->timing && !ok(cudaEventRecord(c->ev[2], s))) return ACC_ERR_CUDA;
+    c->last_launches = launches;
+    c->last_k = k;
+    c->last_units = gs.NV;
+    c->last_blocks = enum_grid_warps(k, c->num_sms) / kWarpsPerBlock;
+    return ACC_OK;
+}
+
+// Wait for the call's device status when the caller gave no status word.
+int finish(acc_ctx *c, cudaStream_t s, int32_t *status_user) {
+    if (status_user) return ACC_OK;
+    if (!ok(cudaMemcpyAsync(c->status_host, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost, s)))
+        return ACC_ERR_CUDA;
+    if (!ok(cudaStreamSynchronize(s))) return ACC_ERR_CUDA;
+    return *c->status_host;
 }
 
 int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n, int64_t m, int k,
@@ -184,56 +257,22 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
     if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
     int rc = ensure_lut(c, k, s);
     if (rc) return rc;
-    if ((rc = ensure_workspace(c, n, m, k))) return rc;
-    int *status = status_user ? status_user : c->status_dev;
     const long long pitch = state_pitch(n);
-    int launches = 0;
-    c->timed_call = c->timing;
-    if (c->timing && !ok(cudaEventRecord(c->ev[0], s))) return ACC_ERR_CUDA;
-    rc = launch_build_graph(reinterpret_cast<const long long *>(rowptr), col, n, m, c->state, pitch, c->deg, c->lo,
-                            c->nptr, c->nbr, c->label, c->info, status,
-                            reinterpret_cast<unsigned long long *>(counts), num_classes(k), n >= kRelabelMinN,
-                            c->num_sms, s);
-    if (rc < 0) return rc;
-    launches += rc;
-    if (c->timing && !ok(cudaEventRecord(c->ev[1], s))) return ACC_ERR_CUDA;
-    EnumArgs a;
-    a.state = c->state;
-    a.pitch = pitch;
-    a.deg = c->deg;
-    a.lo = c->lo;
-    a.nptr = c->nptr;
-    a.nbr = c->nbr;
-    a.lut = c->lut_sv[k];
-    a.n = n;
-    a.info = c->info;
-    a.queue = c->queue;
-    a.queue_cap = c->queue_cap;
-    a.scratch = c->scratch;
-    a.scratch_per_warp = 2 * (((long long)n + 32 + 31) & ~31LL);
-    a.counts = reinterpret_cast<unsigned long long *>(counts);
-    a.status = status;
-    if (n > 0) {
-        rc = launch_enumerate(k, a, c->num_sms, 1, s);
-        if (rc < 0) return rc;
-        launches += rc;
-    }
-    if (c->timing && !ok(cudaEventRecord(c->ev[3], s))) return ACC_ERR_CUDA;
-    if (n > 0) {
-        rc = launch_enumerate(k, a, c->num_sms, 2, s);
-        if (rc < 0) return rc;
-        launches += rc;
-    }
-    if (c->timing && !ok(cudaEventRecord(c->ev[2], s))) return ACC_ERR_CUDA;
-    c->last_launches = launches;
-    c->last_k = k;
-    c->last_units = n;
-    c->last_blocks = enum_grid_warps(k, c->num_sms) / kWarpsPerBlock;
-    if (status_user) return ACC_OK;
-    if (!ok(cudaMemcpyAsync(c->status_host, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost, s)))
-        return ACC_ERR_CUDA;
-    if (!ok(cudaStreamSynchronize(s))) return ACC_ERR_CUDA;
-    return *c->status_host;
+    if ((rc = ensure_workspace(c, n, (long long)n * pitch, m, n, k))) return rc;
+    GSet gs = {};
+    gs.one.rowptr = reinterpret_cast<const long long *>(rowptr);
+    gs.one.col = col;
+    gs.one.m = m;
+    gs.one.soff = 0;
+    gs.one.pitch = pitch;
+    gs.one.n = n;
+    gs.one.voff = 0;
+    gs.B = 1;
+    gs.NV = n;
+    int *status = status_user ? status_user : c->status_dev;
+    rc = run_set(c, gs, (long long)n * pitch, n, k, n >= kRelabelMinN, s, counts, status);
+    if (rc) return rc;
+    return finish(c, s, status_user);
 }
 
 }  // namespace
@@ -292,11 +331,14 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaFree(c->lo);
     cudaFree(c->nptr);
     cudaFree(c->label);
+    cudaFree(c->tiles);
     cudaFree(c->nbr);
     cudaFree(c->info);
     cudaFree(c->queue);
     cudaFree(c->scratch);
     cudaFree(c->status_dev);
+    cudaFree(c->meta_dev);
+    cudaFree(c->gid);
     cudaFree(c->h2d_rowptr);
     cudaFree(c->h2d_col);
     cudaFree(c->h2d_counts);
@@ -349,6 +391,86 @@ int acc_motif_count_host(acc_ctx *c, const int64_t *h_rowptr, const int32_t *h_c
         return ACC_ERR_CUDA;
     if (!ok(cudaStreamSynchronize(s))) return ACC_ERR_CUDA;
     return *c->status_host;
+}
+
+int acc_motif_batch_prepare(acc_ctx *c, const acc_graph_desc *graphs, int32_t B, int k, void *stream) {
+    if (!c || (B > 0 && !graphs) || B < 0) return ACC_ERR_ARG;
+    if (!valid_k(k)) return ACC_ERR_K;
+    if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
+    c->batch_ready = false;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<GMeta> metas((size_t)B);
+    long long NV = 0, words = 0, arcs = 0;
+    int max_n = 0;
+    for (int g = 0; g < B; g++) {
+        const acc_graph_desc &d = graphs[g];
+        if (!d.rowptr || (d.m > 0 && !d.col)) return ACC_ERR_ARG;
+        if (d.n < 0 || d.m < 0 || d.m >= (1ll << 31)) return ACC_ERR_INPUT;
+        if (d.n > ACC_MAX_N) return ACC_ERR_TOO_LARGE;
+        GMeta &mt = metas[(size_t)g];
+        mt.rowptr = reinterpret_cast<const long long *>(d.rowptr);
+        mt.col = d.col;
+        mt.m = d.m;
+        mt.n = d.n;
+        mt.pitch = state_pitch(d.n);
+        mt.soff = words;
+        mt.voff = (int)NV;
+        words += (long long)d.n * mt.pitch;
+        NV += d.n;
+        arcs += d.m;
+        if (d.n > max_n) max_n = d.n;
+        if (NV >= (1ll << 31) || arcs >= (1ll << 31)) return ACC_ERR_OVERFLOW;
+    }
+    int rc = ensure_lut(c, k, s);
+    if (rc) return rc;
+    if ((rc = ensure_workspace(c, NV, words, arcs, max_n, k))) return rc;
+    if ((rc = grow(&c->meta_dev, &c->meta_cap, (size_t)B + 1))) return rc;
+    if ((rc = grow(&c->gid, &c->gid_cap, (size_t)NV + 1))) return rc;
+    if (B > 0 && !ok(cudaMemcpy(c->meta_dev, metas.data(), sizeof(GMeta) * (size_t)B, cudaMemcpyHostToDevice)))
+        return ACC_ERR_CUDA;
+    GSet gs = {};
+    if (B == 1) gs.one = metas[0];
+    gs.many = c->meta_dev;
+    gs.gid = c->gid;
+    gs.B = B;
+    gs.NV = NV;
+    if ((rc = launch_graph_ids(gs, c->gid, s)) < 0) return rc;
+    if (!ok(cudaStreamSynchronize(s))) return ACC_ERR_CUDA;
+    c->batch_set = gs;
+    c->batch_k = k;
+    c->batch_words = words;
+    c->batch_arcs = arcs;
+    c->batch_max_n = max_n;
+    c->batch_ready = true;
+    return ACC_OK;
+}
+
+int acc_motif_batch_run(acc_ctx *c, void *stream, int64_t *d_counts, int32_t *d_status) {
+    if (!c || !d_counts || !c->batch_ready) return ACC_ERR_ARG;
+    if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->batch_set.B == 0) return ACC_OK;
+    int *status = d_status ? d_status : c->status_dev;
+    const int rc = run_set(c, c->batch_set, c->batch_words, c->batch_max_n, c->batch_k, true, s, d_counts, status);
+    if (rc) return rc;
+    return finish(c, s, d_status);
+}
+
+int acc_motif_count_batch(acc_ctx *c, const acc_graph_desc *graphs, int32_t B, int k, void *stream,
+                          int64_t *d_counts, int32_t *d_status) {
+    const int rc = acc_motif_batch_prepare(c, graphs, B, k, stream);
+    if (rc) return rc;
+    return acc_motif_batch_run(c, stream, d_counts, d_status);
+}
+
+int acc_motif_zscores(const int64_t *d_counts, int32_t groups, int32_t group_size, int k, void *stream,
+                      double *d_z) {
+    if (!valid_k(k)) return ACC_ERR_K;
+    if (groups < 0 || group_size < 2) return ACC_ERR_ARG;
+    if (groups > 0 && (!d_counts || !d_z)) return ACC_ERR_ARG;
+    const int rc = launch_zscores(reinterpret_cast<const long long *>(d_counts), groups, group_size, num_classes(k),
+                                  d_z, (cudaStream_t)stream);
+    return rc < 0 ? rc : ACC_OK;
 }
 
 int acc_motif_class_code(acc_ctx *c, int k, int32_t cls, uint32_t *code) {

@@ -34,9 +34,9 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kWarpsPerBlock = 8;
 constexpr int kThreads = kWarpsPerBlock * kWarp;
 
-// Per-graph scalars the builder leaves on the device.
+// Per-call scalars the builder leaves on the device.
 struct GraphInfo {
-    long long nnz;     // entries of nbr = 2 |E*|
+    long long nnz;     // entries of nbr = sum over graphs of 2 |E*|
     int maxdeg;        // largest degree in G*
     int pad;
     unsigned long long queue_tail;  // heavy-unit chunks pushed by phase 1
@@ -44,6 +44,32 @@ struct GraphInfo {
     unsigned long long unit_ctr;    // base units taken by phase 1
     unsigned long long chunks_pushed;
 };
+
+// One graph of a set.  Its vertices are the global ids [voff, voff + n); its
+// pair-state block is n rows of `pitch` words starting at word soff.
+struct GMeta {
+    const long long *rowptr;  // input out-CSR (device)
+    const int *col;
+    long long m;
+    long long soff;
+    long long pitch;
+    int n;
+    int voff;
+};
+
+// A set of graphs counted together (B == 1: a single graph, held by value).
+struct GSet {
+    GMeta one;            // the graph when B == 1
+    const GMeta *many;    // device array of B entries when B > 1
+    const int *gid;       // graph of each global vertex when B > 1
+    int B;
+    long long NV;         // total vertices
+    __device__ __forceinline__ GMeta meta(int g) const { return B == 1 ? one : many[g]; }
+    __device__ __forceinline__ int graph_of(int v) const { return B == 1 ? 0 : gid[v]; }
+};
+
+// Sets with at most this many vertices scan their degrees in one block.
+constexpr long long kScanSingleMax = 1 << 17;
 
 // Bit of the adjacency code for the arc from tuple slot i to slot j.
 __host__ __device__ constexpr int code_bit(int k, int i, int j) {
@@ -72,18 +98,22 @@ __device__ inline void set_status(int *status, int err) {
 // launched, or a negative ACC_ERR_* code).
 // --------------------------------------------------------------------------
 
-// graph.cu
-// Builds the pair-state matrix and the G* neighbour lists; with `relabel`
-// the vertices are first renumbered by descending G* degree (label[v] = new
-// number of input vertex v), which leaves the counts unchanged.
-int launch_build_graph(const long long *rowptr, const int *col, int n, long long m,
-                       uint32_t *state, long long pitch, int *deg, int *lo, long long *nptr,
-                       uint32_t *nbr, int *label, GraphInfo *info, int *status, unsigned long long *counts,
-                       int ncounts, bool relabel, int num_sms, cudaStream_t s);
+// graph.cu.  Builds the pair-state blocks and the G* neighbour lists of a
+// graph set; with `relabel` each graph's vertices are first renumbered by
+// descending G* degree (label[v] = new global id of input vertex v), which
+// leaves the counts unchanged.  tile_scratch holds scan_tiles_needed(NV)
+// values.
+int launch_build_graph(const GSet &gs, long long state_words, uint32_t *state, int *deg, int *lo, long long *nptr,
+                       long long *tile_scratch, uint32_t *nbr, int *label, GraphInfo *info, int *status,
+                       unsigned long long *counts, long long ncounts, bool relabel, int num_sms, cudaStream_t s);
+long long scan_tiles_needed(long long NV);
+// gid[v] for a set of several graphs (no launch for one graph).
+int launch_graph_ids(const GSet &gs, int *gid, cudaStream_t s);
 // Zero `bytes` at p, plus counts[0..ncounts), ints[0..nints) and *status
 // when not NULL.
 int launch_zero(void *p, size_t bytes, int num_sms, cudaStream_t s, int *status = nullptr,
-                unsigned long long *counts = nullptr, int ncounts = 0, int *ints = nullptr, int nints = 0);
+                unsigned long long *counts = nullptr, long long ncounts = 0, int *ints = nullptr,
+                long long nints = 0);
 
 // lut.cu: lut = code -> class in the canonical code layout (public API),
 // lut_sv = the same classes indexed in the state-vector layout (kernels).
@@ -92,22 +122,25 @@ int launch_build_lut(int k, uint32_t *scratch_canon, int *scratch_rank, int16_t 
 
 // enum.cu
 struct EnumArgs {
-    const uint32_t *state;
-    long long pitch;
-    const int *deg;
+    const uint32_t *state;      // pair-state blocks of all graphs
+    const int *deg;             // by global vertex
     const int *lo;
     const long long *nptr;
-    const uint32_t *nbr;
+    const uint32_t *nbr;        // entries hold local ids
     const int16_t *lut;         // class table in the state-vector layout
-    int n;
+    GSet gs;
+    int max_n;                  // largest graph of the set
     GraphInfo *info;
-    uint4 *queue;               // heavy-unit chunks (unit, jlo, jhi, 0)
+    uint4 *queue;               // heavy-unit chunks (unit, lo, hi, global root)
     unsigned long long queue_cap;
     uint32_t *scratch;          // per-warp overflow buffers for the extension sets
     long long scratch_per_warp; // entries per warp
-    unsigned long long *counts; // int64[num_classes] (as unsigned for atomics)
+    unsigned long long *counts; // int64[B * num_classes]
     int *status;
 };
+// batch.cu: Z-scores of each group's real graph against its randomisations.
+int launch_zscores(const long long *counts, int groups, int group_size, int K, double *z, cudaStream_t s);
+
 // phase 1: light units run, heavy units queued; phase 2: the queue drained.
 int launch_enumerate(int k, const EnumArgs &a, int num_sms, int phase, cudaStream_t s);
 int enum_grid_warps(int k, int num_sms);

@@ -95,6 +95,29 @@ __device__ __forceinline__ uint32_t probe(const uint32_t *__restrict__ st, long 
 __device__ __forceinline__ uint32_t e_id(uint32_t e) { return e >> 6; }
 __device__ __forceinline__ uint32_t e_sv(uint32_t e) { return e & 63u; }
 
+// One graph of the set seen with local vertex ids.
+struct GView {
+    const uint32_t *state;  // the graph's pair-state block
+    long long pitch;
+    const long long *nptr;  // by local vertex (positions are global)
+    const int *deg;
+    const int *lo;
+    const uint32_t *nbr;
+    int n;
+};
+
+__device__ __forceinline__ GView view_of(const EnumArgs &a, const GMeta &mt) {
+    GView g;
+    g.state = a.state + mt.soff;
+    g.pitch = mt.pitch;
+    g.nptr = a.nptr + mt.voff;
+    g.deg = a.deg + mt.voff;
+    g.lo = a.lo + mt.voff;
+    g.nbr = a.nbr;
+    g.n = mt.n;
+    return g;
+}
+
 // First position of N*(x) (entries (u << 2) | s, sorted) with u > root.
 __device__ __forceinline__ int first_above(const uint32_t *__restrict__ nbr, long long base, int d, uint32_t root) {
     const uint32_t key = (root + 1u) << 2;
@@ -153,13 +176,37 @@ struct Sink {
     int *status;
     int run_cls;        // this lane's current run
     uint32_t run_len;
+    unsigned long long *counts_base;  // int64[B * NCLS]
+    int gcur;           // graph whose counts this warp accumulates
+    bool direct;        // k = 5 with several graphs: runs go straight to the int64 counts
 
     __device__ __forceinline__ void flush() {
         if (run_len) {
-            if (run_cls >= 0) atomicAdd(&hist[run_cls], run_len);
-            else set_status(status, ACC_ERR_INTERNAL);
+            if (run_cls < 0) set_status(status, ACC_ERR_INTERNAL);
+            else if (direct) atomicAdd(&counts[run_cls], (unsigned long long)run_len);
+            else atomicAdd(&hist[run_cls], run_len);
             run_len = 0;
         }
+    }
+
+    // Whole warp, between units: move to graph g (k <= 4: the warp's private
+    // histogram is drained to the previous graph's counts first).
+    __device__ __forceinline__ void switch_graph(int g, int lane) {
+        if (g == gcur) return;
+        if (K <= 4 && gcur >= 0) {
+            __syncwarp();
+            for (int c = lane; c < Layout<K>::NCLS; c += kWarp) {
+                const uint32_t v = hist[c];
+                if (v) {
+                    hist[c] = 0;
+                    atomicAdd(&counts[c], (unsigned long long)v);
+                }
+            }
+            __syncwarp();
+            since = 0;
+        }
+        gcur = g;
+        counts = counts_base + (size_t)g * Layout<K>::NCLS;
     }
 
     // Called by all lanes of the warp together; `valid` lanes count one leaf
@@ -204,7 +251,7 @@ struct Sink {
                 since = 0;
             }
         } else {
-            if (since < (1u << 20)) return;
+            if (direct || since < (1u << 20)) return;
             // account in the block-wide counter every 2^20 increments; the
             // warp that crosses 2^30 drains the block histogram (atomicExch
             // per bin, so concurrent increments are never lost)
@@ -238,7 +285,7 @@ struct Scratch {
 // comparison.  For odd B the middle row (p = B-1-p) stands alone.  pcode holds
 // the code fields of the prefix slots 1..k-3.
 template <int K>
-__device__ __forceinline__ void leaves(const EnumArgs &a, Sink<K> &sink, const uint32_t *E, int B, int plo,
+__device__ __forceinline__ void leaves(const GView &g, Sink<K> &sink, const uint32_t *E, int B, int plo,
                                        int phi, const uint32_t *pm, uint32_t pcode, uint32_t root, int lane) {
     using L = Layout<K>;
     const int P = (B + 1) >> 1;
@@ -276,7 +323,7 @@ __device__ __forceinline__ void leaves(const EnumArgs &a, Sink<K> &sink, const u
             q = qu;
 #pragma unroll
             for (int u = 0; u < U; u++)
-                w[u] = ok[u] ? __ldg(a.state + (long long)e_id(er[u]) * a.pitch + (e_id(ec[u]) >> 4)) : 0u;
+                w[u] = ok[u] ? __ldg(g.state + (long long)e_id(er[u]) * g.pitch + (e_id(ec[u]) >> 4)) : 0u;
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 const uint32_t s = (w[u] >> ((e_id(ec[u]) & 15u) << 1)) & 3u;
@@ -301,9 +348,9 @@ __device__ __forceinline__ void leaves(const EnumArgs &a, Sink<K> &sink, const u
             const int j = i < n1 ? r1lo + i : r2lo + (i - n1);
             ej = E[j];
             const uint32_t x = e_id(ej);
-            const long long nb = a.nptr[x];
-            const int d = a.deg[x];
-            const int st = first_above(a.nbr, nb, d, root);
+            const long long nb = g.nptr[x];
+            const int d = g.deg[x];
+            const int st = first_above(g.nbr, nb, d, root);
             first = (uint32_t)(nb + st);
             cnt = d - st;
         }
@@ -319,11 +366,11 @@ __device__ __forceinline__ void leaves(const EnumArgs &a, Sink<K> &sink, const u
             bool leaf = false;
             uint32_t ue = 0;
             if (t < tot) {
-                ue = __ldg(a.nbr + (orow + (uint32_t)t));
+                ue = __ldg(g.nbr + (orow + (uint32_t)t));
                 const uint32_t u = ue >> 2;
                 leaf = true;
 #pragma unroll
-                for (int k2 = 0; k2 < K - 2; k2++) leaf = leaf && probe(a.state, a.pitch, pm[k2], u) == 0u;
+                for (int k2 = 0; k2 < K - 2; k2++) leaf = leaf && probe(g.state, g.pitch, pm[k2], u) == 0u;
             }
             sink.bump(cr | ((ue & 3u) << L::SH_PAIR), leaf);
         }
@@ -335,7 +382,7 @@ __device__ __forceinline__ void leaves(const EnumArgs &a, Sink<K> &sink, const u
 // row v, w1 = N*(v)[p - nptr[v]] > v): N*(v) after w1, then the exclusive
 // neighbours of w1 (above v, not adjacent to v).  Entry states:
 // state(v, x) | state(w1, x) << 2.  Returns B.
-__device__ __forceinline__ int build_level2(const EnumArgs &a, long long p, int v, uint32_t w1, const Scratch &sc,
+__device__ __forceinline__ int build_level2(const GView &a, long long p, int v, uint32_t w1, const Scratch &sc,
                                             uint32_t **E_out, int lane) {
     const long long rb = a.nptr[v];
     const int t = (int)(p - rb);
@@ -479,54 +526,54 @@ __device__ __forceinline__ int row_of(const long long *__restrict__ nptr, int n,
 // instead.  D is the per-row allowance for exclusive neighbours (mean degree
 // + 1).
 template <int K>
-__device__ void process_unit(const EnumArgs &a, Sink<K> &sink, const Scratch &sc, uint32_t unit, int v, int jlo,
-                             int jhi, bool phase1, long long D, int lane) {
+__device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, const Scratch &sc, uint32_t unit,
+                             int v, int vglob, int jlo, int jhi, bool phase1, long long D, int lane) {
     using L = Layout<K>;
     if (K == 3) {
         // prefix {v}; E = neighbours of v above v
-        const int dv = a.deg[v], l = a.lo[v];
+        const int dv = g.deg[v], l = g.lo[v];
         const int B = dv - l;
         if (B <= 0) return;
         const int P = (B + 1) / 2;
         int hi = min(jhi, P), rest = P;
         if (phase1 && (long long)P * (B - 1) + (long long)B * D > kLight) {
-            rest = queue_closed_form(a, unit, v, B, D, lane);
+            rest = queue_closed_form(a, unit, vglob, B, D, lane);
             if (rest >= P) return;
             hi = 0;
         }
         uint32_t *E = B <= sc.cap ? sc.buf[0] : sc.ovf[0];
-        const long long rb = a.nptr[v] + l;
+        const long long rb = g.nptr[v] + l;
         for (int q = lane; q < B; q += kWarp) {
-            const uint32_t xe = __ldg(a.nbr + rb + q);
+            const uint32_t xe = __ldg(g.nbr + rb + q);
             E[q] = ((xe >> 2) << 6) | (xe & 3u);
         }
         __syncwarp();
         const uint32_t pm[1] = {(uint32_t)v};
-        leaves<K>(a, sink, E, B, jlo, hi, pm, 0u, (uint32_t)v, lane);
-        if (rest < P) leaves<K>(a, sink, E, B, rest, P, pm, 0u, (uint32_t)v, lane);
+        leaves<K>(g, sink, E, B, jlo, hi, pm, 0u, (uint32_t)v, lane);
+        if (rest < P) leaves<K>(g, sink, E, B, rest, P, pm, 0u, (uint32_t)v, lane);
         sink.flush();
         __syncwarp();
         return;
     }
-    const long long rb = a.nptr[v];
+    const long long rb = g.nptr[v];
     const int t = (int)(unit - rb);
-    if (t < a.lo[v]) return;  // neighbour below v: not a unit
-    const uint32_t e = __ldg(a.nbr + unit);
+    if (t < g.lo[v]) return;  // neighbour below v: not a unit
+    const uint32_t e = __ldg(g.nbr + unit);
     const uint32_t w1 = e >> 2, s01 = e & 3u;
     int hi = jhi, rest = 0x7FFFFFFF;
     if (K == 4 && phase1) {
-        long long Bu = (long long)(a.deg[v] - t - 1) + a.deg[w1];
-        if (Bu > a.n - 2) Bu = a.n - 2;
+        long long Bu = (long long)(g.deg[v] - t - 1) + g.deg[w1];
+        if (Bu > g.n - 2) Bu = g.n - 2;
         if (Bu <= 0) return;
         const long long Pu = (Bu + 1) / 2;
         if (Pu * (Bu - 1) + Bu * D > kLight) {
-            rest = queue_closed_form(a, unit, v, Bu, D, lane);
+            rest = queue_closed_form(a, unit, vglob, Bu, D, lane);
             if (rest >= Pu) return;
             hi = 0;
         }
     }
     uint32_t *E2;
-    const int B2 = build_level2(a, unit, v, w1, sc, &E2, lane);
+    const int B2 = build_level2(g, unit, v, w1, sc, &E2, lane);
     if (B2 <= 0) return;
     if (K == 4) {
         // rows of E2 are paired into virtual rows
@@ -535,8 +582,8 @@ __device__ void process_unit(const EnumArgs &a, Sink<K> &sink, const Scratch &sc
         rest = min(rest, P2);
         const uint32_t pm[2] = {(uint32_t)v, w1};
         const uint32_t pcode = s01 << (L::SH_ROW + 4);  // field of slot 1 sits above slot 2's
-        leaves<K>(a, sink, E2, B2, jlo, hi, pm, pcode, (uint32_t)v, lane);
-        if (rest < P2) leaves<K>(a, sink, E2, B2, rest, P2, pm, pcode, (uint32_t)v, lane);
+        leaves<K>(g, sink, E2, B2, jlo, hi, pm, pcode, (uint32_t)v, lane);
+        if (rest < P2) leaves<K>(g, sink, E2, B2, rest, P2, pm, pcode, (uint32_t)v, lane);
         sink.flush();
         __syncwarp();
         return;
@@ -546,11 +593,11 @@ __device__ void process_unit(const EnumArgs &a, Sink<K> &sink, const Scratch &sc
     // K == 5: one more level.  Row j2 of E2 gives w2 and the list E3.
     if (phase1) {
         auto work = [&](int j) {
-            const long long b = (long long)(B2 - 1 - j) + a.deg[e_id(E2[j])];
+            const long long b = (long long)(B2 - 1 - j) + g.deg[e_id(E2[j])];
             return b * (b - 1) / 2 + b * D + 1;
         };
         if (total_work(B2, work, lane) > kLight) {
-            rest = queue_rows(a, unit, v, B2, work, lane);
+            rest = queue_rows(a, unit, vglob, B2, work, lane);
             hi = 0;
         }
     }
@@ -565,24 +612,24 @@ __device__ void process_unit(const EnumArgs &a, Sink<K> &sink, const Scratch &sc
             const uint32_t w2 = e_id(e2);
             const uint32_t pcode = pc01 | ((e2 & 15u) << 14);
             const int A3 = B2 - 1 - j2;
-            const int dw = a.deg[w2];
+            const int dw = g.deg[w2];
             const long long ub = (long long)A3 + dw;
             uint32_t *E3 = ub <= sc.cap ? sc.buf[1] : sc.ovf[1];
             for (int q = lane; q < A3; q += kWarp) {
                 const uint32_t xe = E2[j2 + 1 + q];
                 const uint32_t x = e_id(xe);
-                E3[q] = (x << 6) | (xe & 15u) | (probe(a.state, a.pitch, w2, x) << 4);
+                E3[q] = (x << 6) | (xe & 15u) | (probe(g.state, g.pitch, w2, x) << 4);
             }
-            const long long wb = a.nptr[w2];
+            const long long wb = g.nptr[w2];
             int pos = A3;
-            for (int q0 = first_above(a.nbr, wb, dw, (uint32_t)v); q0 < dw; q0 += kWarp) {
+            for (int q0 = first_above(g.nbr, wb, dw, (uint32_t)v); q0 < dw; q0 += kWarp) {
                 const int q = q0 + lane;
                 uint32_t ue = 0;
                 bool keep = false;
                 if (q < dw) {
-                    ue = __ldg(a.nbr + wb + q);
+                    ue = __ldg(g.nbr + wb + q);
                     const uint32_t u = ue >> 2;
-                    keep = probe(a.state, a.pitch, (uint32_t)v, u) == 0u && probe(a.state, a.pitch, w1, u) == 0u;
+                    keep = probe(g.state, g.pitch, (uint32_t)v, u) == 0u && probe(g.state, g.pitch, w1, u) == 0u;
                 }
                 const unsigned ball = __ballot_sync(kFull, keep);
                 if (keep) E3[pos + __popc(ball & ((1u << lane) - 1u))] = ((ue >> 2) << 6) | ((ue & 3u) << 4);
@@ -590,7 +637,7 @@ __device__ void process_unit(const EnumArgs &a, Sink<K> &sink, const Scratch &sc
             }
             __syncwarp();
             const uint32_t pm[3] = {(uint32_t)v, w1, w2};
-            leaves<K>(a, sink, E3, pos, 0, (pos + 1) / 2, pm, pcode, (uint32_t)v, lane);
+            leaves<K>(g, sink, E3, pos, 0, (pos + 1) / 2, pm, pcode, (uint32_t)v, lane);
             __syncwarp();
         }
         if (rest >= B2) break;
@@ -608,6 +655,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : ACC_MINB34) k_enum(Enum
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem + L::lut + L::pending);
     uint32_t *ebuf = reinterpret_cast<uint32_t *>(smem + L::lut + L::pending + L::hist);
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    const bool several = a.gs.B > 1;
 
     if (L::SMEM_LUT)
         for (int i = tid; i < (1 << L::NB); i += blockDim.x) lut_s[i] = a.lut[i];
@@ -619,7 +667,10 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : ACC_MINB34) k_enum(Enum
     Sink<K> sink;
     sink.hist = K == 5 ? hist : hist + wib * L::NCLS;
     sink.lut = L::SMEM_LUT ? lut_s : a.lut;
+    sink.counts_base = a.counts;
     sink.counts = a.counts;
+    sink.gcur = several ? -1 : 0;
+    sink.direct = K == 5 && several;
     sink.pending = pending;
     sink.since = 0;
     sink.status = a.status;
@@ -634,24 +685,29 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : ACC_MINB34) k_enum(Enum
     sc.ovf[1] = sc.ovf[0] + a.scratch_per_warp / 2;
     sc.cap = L::CAP;
     const long long nnz = a.info->nnz;
-    const long long D = (a.n > 0 ? nnz / a.n : 0) + 1;
+    const long long NV = a.gs.NV;
+    const long long D = (NV > 0 ? nnz / NV : 0) + 1;
 
     if (phase == 1) {
-        const long long nunits = K == 3 ? (long long)a.n : nnz;
+        const long long nunits = K == 3 ? NV : nnz;
         for (;;) {
             unsigned long long u0 = 0;
             if (lane == 0) u0 = atomicAdd(&a.info->unit_ctr, (unsigned long long)kGrab);
             u0 = __shfl_sync(kFull, u0, 0);
             if ((long long)u0 >= nunits) break;
             const long long u1 = min((long long)u0 + kGrab, nunits);
-            int v = K == 3 ? 0 : row_of(a.nptr, a.n, (long long)u0);
+            int vg = K == 3 ? 0 : row_of(a.nptr, (int)NV, (long long)u0);
             for (long long u = (long long)u0; u < u1; u++) {
                 if (K == 3) {
-                    v = (int)u;
+                    vg = (int)u;
                 } else {
-                    while (a.nptr[v + 1] <= u) v++;
+                    while (a.nptr[vg + 1] <= u) vg++;
                 }
-                process_unit<K>(a, sink, sc, (uint32_t)u, v, 0, 0x7FFFFFFF, true, D, lane);
+                const int gi = a.gs.graph_of(vg);
+                const GMeta mt = a.gs.meta(gi);
+                sink.switch_graph(gi, lane);
+                process_unit<K>(a, view_of(a, mt), sink, sc, (uint32_t)u, vg - mt.voff, vg, 0, 0x7FFFFFFF, true, D,
+                                lane);
             }
         }
     } else {
@@ -662,12 +718,26 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : ACC_MINB34) k_enum(Enum
             idx = __shfl_sync(kFull, idx, 0);
             if (idx >= tail) break;
             const uint4 it = a.queue[idx];
-            process_unit<K>(a, sink, sc, it.x, (int)it.w, (int)it.y, (int)it.z, false, D, lane);
+            const int vg = (int)it.w;
+            const int gi = a.gs.graph_of(vg);
+            const GMeta mt = a.gs.meta(gi);
+            sink.switch_graph(gi, lane);
+            process_unit<K>(a, view_of(a, mt), sink, sc, it.x, vg - mt.voff, vg, (int)it.y, (int)it.z, false, D,
+                            lane);
         }
     }
 
     __syncthreads();
-    if (K == 5) {
+    if (several) {
+        // each warp drains its own histogram to the graph it ended on
+        // (k = 5 with several graphs counted straight into int64)
+        if (K <= 4 && sink.gcur >= 0) {
+            for (int c = lane; c < L::NCLS; c += kWarp) {
+                const uint32_t v = sink.hist[c];
+                if (v) atomicAdd(&sink.counts[c], (unsigned long long)v);
+            }
+        }
+    } else if (K == 5) {
         for (int c = tid; c < L::NCLS; c += blockDim.x) {
             const uint32_t v = hist[c];
             if (v) atomicAdd(&a.counts[c], (unsigned long long)v);

@@ -1,12 +1,17 @@
-// Graph ingest: out-CSR -> dense pair-state matrix -> sorted G* neighbour
-// lists with the 2-bit pair state attached to every entry.
+// Graph ingest for a set of graphs (one graph is a set of one): out-CSR ->
+// dense pair-state block per graph -> sorted G* neighbour lists with the
+// 2-bit pair state attached to every entry.
 //
 // The pair state is the paper's three-way neighbour partition (Notation
 // section; Algorithm table1a builds the same sets A, B, C by bucketing arcs):
 // a neighbour u of v is bidirected (state 3), out-only (state 1) or in-only
-// (state 2).  Here the partition is a 2-bit field of an n x n matrix, which
-// also answers every "are a and b adjacent, and how" question of the
+// (state 2).  Here the partition is a 2-bit field of an n x n block per graph,
+// which also answers every "are a and b adjacent, and how" question of the
 // enumeration in one 4-byte load.
+//
+// Vertices of graph g occupy the global range [voff_g, voff_g + n_g); its
+// pair-state block starts at word soff_g.  deg, lo, label, nptr are indexed
+// by global vertex; neighbour entries and block rows/columns use local ids.
 #include "common.cuh"
 
 namespace acc {
@@ -25,7 +30,7 @@ __device__ __forceinline__ int warp_excl_scan(int x, int lane, int *total) {
 }
 
 __global__ void k_zero(uint4 *p, size_t n16, unsigned char *tail, size_t ntail, int *status,
-                       unsigned long long *counts, int ncounts, int *ints, int nints) {
+                       unsigned long long *counts, long long ncounts, int *ints, long long nints) {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t j = i; j < n16; j += stride) p[j] = make_uint4(0, 0, 0, 0);
@@ -35,93 +40,52 @@ __global__ void k_zero(uint4 *p, size_t n16, unsigned char *tail, size_t ntail, 
     if (i == 0 && status) *status = 0;
 }
 
-// Warp per source row: set the pair-state bits of every arc, validating the
+// Warp per global row: set the pair-state bits of every arc, validating the
 // CSR on the way.  Invalid rows and arcs are skipped (never read out of
 // range) and reported through *status.  With `label` non-null, vertex x is
-// written as label[x] (the relabelled matrix).
-__global__ void k_ingest(const long long *__restrict__ rowptr, const int *__restrict__ col, int n,
-                         long long m, uint32_t *state, long long pitch, const int *__restrict__ label,
-                         int *status) {
+// written as label[x] (the renumbered block).
+__global__ void k_ingest(GSet gs, uint32_t *state, const int *__restrict__ label, int *status) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    if (warp == 0 && lane == 0) {
-        if (rowptr[0] != 0 || rowptr[n] != m) set_status(status, ACC_ERR_INPUT);
-    }
-    for (long long v = warp; v < n; v += nwarps) {
-        const long long b = rowptr[v], e = rowptr[v + 1];
-        if (b < 0 || e < b || e > m) {
+    for (long long v = warp; v < gs.NV; v += nwarps) {
+        const GMeta mt = gs.meta(gs.graph_of((int)v));
+        const int lv = (int)v - mt.voff;
+        if (lv == 0 && lane == 0 && (mt.rowptr[0] != 0 || mt.rowptr[mt.n] != mt.m))
+            set_status(status, ACC_ERR_INPUT);
+        const long long b = mt.rowptr[lv], e = mt.rowptr[lv + 1];
+        if (b < 0 || e < b || e > mt.m) {
             if (lane == 0) set_status(status, ACC_ERR_INPUT);
             continue;
         }
-        const long long a = label ? label[v] : v;
+        const long long a = label ? label[v] - mt.voff : lv;
+        uint32_t *blk = state + mt.soff;
         for (long long p = b + lane; p < e; p += kWarp) {
-            const int u0 = col[p];
-            if (u0 < 0 || u0 >= n || u0 == (int)v) {
+            const int u0 = mt.col[p];
+            if (u0 < 0 || u0 >= mt.n || u0 == lv) {
                 set_status(status, ACC_ERR_INPUT);
                 continue;
             }
-            const int u = label ? label[u0] : u0;
-            atomicOr(&state[a * pitch + (u >> 4)], 1u << ((u & 15) * 2));
-            atomicOr(&state[(long long)u * pitch + (a >> 4)], 2u << ((a & 15) * 2));
+            const int u = label ? label[mt.voff + u0] - mt.voff : u0;
+            atomicOr(&blk[a * mt.pitch + (u >> 4)], 1u << ((u & 15) * 2));
+            atomicOr(&blk[(long long)u * mt.pitch + (a >> 4)], 2u << ((a & 15) * 2));
         }
     }
 }
 
-// Degree-descending relabelling: start[d] = vertices of degree above d.
-// One block; dhist[d] = vertices of degree d, d < n.
-__global__ void k_desc_starts(const int *__restrict__ dhist, int n, int *start) {
-    __shared__ int warp_sum[32];
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int chunk = (n + blockDim.x - 1) / blockDim.x;
-    // position i of the scan is degree n - 1 - i
-    const int b = min(n, t * chunk), e = min(n, b + chunk);
-    int s = 0;
-    for (int i = b; i < e; i++) s += dhist[n - 1 - i];
-    int incl = s;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(kFull, incl, d);
-        if (lane >= d) incl += y;
-    }
-    if (lane == 31) warp_sum[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = blockDim.x >> 5;
-        const int ws = lane < nw ? warp_sum[lane] : 0;
-        int wi = ws;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(kFull, wi, d);
-            if (lane >= d) wi += y;
-        }
-        if (lane < nw) warp_sum[lane] = wi - ws;
-    }
-    __syncthreads();
-    int run = warp_sum[wid] + (incl - s);
-    for (int i = b; i < e; i++) {
-        start[n - 1 - i] = run;
-        run += dhist[n - 1 - i];
-    }
-}
-
-// label[v] = the next free position of v's degree class (ties in any order).
-__global__ void k_desc_scatter(const int *__restrict__ deg, int n, int *start, int *label) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        label[v] = atomicAdd(&start[deg[v]], 1);
-}
-
-// Warp per row: degree of v in G* and the number of its neighbours below v.
-__global__ void k_degrees(const uint32_t *__restrict__ state, long long pitch, int n, int *deg, int *lo,
-                          int *dhist) {
+// Warp per global row: degree of v in G*, neighbours below v, and (for the
+// renumbering) the per-graph degree histogram dhist[voff + degree].
+__global__ void k_degrees(GSet gs, const uint32_t *__restrict__ state, int *deg, int *lo, int *dhist) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const int words = (n + 15) >> 4;
-    for (long long v = warp; v < n; v += nwarps) {
-        const uint4 *row4 = reinterpret_cast<const uint4 *>(state + v * pitch);
-        const int vw = (int)(v >> 4);
-        const uint32_t below_mask = (1u << ((v & 15) * 2)) - 1u;
+    for (long long v = warp; v < gs.NV; v += nwarps) {
+        const GMeta mt = gs.meta(gs.graph_of((int)v));
+        const int lv = (int)v - mt.voff;
+        const int words = (mt.n + 15) >> 4;
+        const uint4 *row4 = reinterpret_cast<const uint4 *>(state + mt.soff + (long long)lv * mt.pitch);
+        const int vw = lv >> 4;
+        const uint32_t below_mask = (1u << ((lv & 15) * 2)) - 1u;
         int cnt = 0, below = 0;
         for (int w4 = lane; w4 * 4 < words; w4 += kWarp) {
             uint4 q = row4[w4];
@@ -144,13 +108,63 @@ __global__ void k_degrees(const uint32_t *__restrict__ state, long long pitch, i
         if (lane == 0) {
             deg[v] = cnt;
             if (lo) lo[v] = below;
-            if (dhist) atomicAdd(&dhist[cnt], 1);
+            if (dhist) atomicAdd(&dhist[mt.voff + cnt], 1);
         }
     }
 }
 
-// One block: exclusive scan of the degrees into nptr, the largest degree,
-// and the reset of the per-graph work counters.
+// Block per graph: start[voff + d] = vertices of the graph with degree above d.
+__global__ void k_desc_starts(GSet gs, const int *__restrict__ dhist, int *start) {
+    __shared__ int warp_sum[32];
+    const GMeta mt = gs.meta(blockIdx.x);
+    const int n = mt.n;
+    const int *h = dhist + mt.voff;
+    int *st = start + mt.voff;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int chunk = (n + blockDim.x - 1) / blockDim.x;
+    // position i of the scan is degree n - 1 - i
+    const int b = min(n, t * chunk), e = min(n, b + chunk);
+    int s = 0;
+    for (int i = b; i < e; i++) s += h[n - 1 - i];
+    int incl = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) warp_sum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        const int ws = lane < nw ? warp_sum[lane] : 0;
+        int wi = ws;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(kFull, wi, d);
+            if (lane >= d) wi += y;
+        }
+        if (lane < nw) warp_sum[lane] = wi - ws;
+    }
+    __syncthreads();
+    int run = warp_sum[wid] + (incl - s);
+    for (int i = b; i < e; i++) {
+        st[n - 1 - i] = run;
+        run += h[n - 1 - i];
+    }
+}
+
+// label[v] = voff + the next free position of v's degree class in its graph
+// (ties in any order).
+__global__ void k_desc_scatter(GSet gs, const int *__restrict__ deg, int *start, int *label) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < gs.NV;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int voff = gs.meta(gs.graph_of((int)v)).voff;
+        label[v] = voff + atomicAdd(&start[voff + deg[v]], 1);
+    }
+}
+
+// Exclusive scan of the degrees into nptr, with the largest degree and the
+// reset of the work counters.  Small sets: one block.
 __global__ void k_scan_degrees(const int *__restrict__ deg, int n, long long *nptr, GraphInfo *info) {
     __shared__ long long warp_sum[32];
     __shared__ int warp_max[32];
@@ -209,15 +223,144 @@ __global__ void k_scan_degrees(const int *__restrict__ deg, int n, long long *np
     }
 }
 
-// Warp per row: write the sorted neighbour entries (u << 2) | state(v, u).
-__global__ void k_fill(const uint32_t *__restrict__ state, long long pitch, int n,
-                       const long long *__restrict__ nptr, uint32_t *nbr) {
+// Large sets, three passes over tiles of kScanTile degrees: tile sums (and
+// the largest degree), a one-block scan of the tile sums, then each tile's
+// own scan plus its offset.  The caller zeroes info->maxdeg first.
+constexpr int kScanTile = 4096;
+
+__global__ void k_scan_tiles(const int *__restrict__ deg, int n, long long *tile_sum, GraphInfo *info) {
+    __shared__ long long ws[32];
+    __shared__ int wm[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long base = (long long)blockIdx.x * kScanTile;
+    long long s = 0;
+    int mx = 0;
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+        const long long j = base + i;
+        if (j < n) {
+            s += deg[j];
+            mx = max(mx, deg[j]);
+        }
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        s += __shfl_xor_sync(kFull, s, d);
+        mx = max(mx, __shfl_xor_sync(kFull, mx, d));
+    }
+    if (lane == 0) {
+        ws[wid] = s;
+        wm[wid] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        int m = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            t += ws[w];
+            m = max(m, wm[w]);
+        }
+        tile_sum[blockIdx.x] = t;
+        atomicMax(&info->maxdeg, m);
+    }
+}
+
+__global__ void k_scan_top(long long *tile_sum, int ntiles, long long *nptr, int n, GraphInfo *info) {
+    __shared__ long long warp_sum[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int chunk = (ntiles + blockDim.x - 1) / blockDim.x;
+    const int b = min(ntiles, t * chunk), e = min(ntiles, b + chunk);
+    long long s = 0;
+    for (int i = b; i < e; i++) s += tile_sum[i];
+    long long incl = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        long long y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) warp_sum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        long long w0 = lane < nw ? warp_sum[lane] : 0;
+        long long wi = w0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            long long y = __shfl_up_sync(kFull, wi, d);
+            if (lane >= d) wi += y;
+        }
+        if (lane < nw) warp_sum[lane] = wi - w0;
+        if (lane == nw - 1) {
+            info->nnz = wi;
+            nptr[n] = wi;
+        }
+    }
+    __syncthreads();
+    long long run = warp_sum[wid] + (incl - s);
+    for (int i = b; i < e; i++) {
+        const long long v = tile_sum[i];
+        tile_sum[i] = run;
+        run += v;
+    }
+    if (t == 0) {
+        info->queue_tail = 0;
+        info->queue_head = 0;
+        info->unit_ctr = 0;
+        info->chunks_pushed = 0;
+    }
+}
+
+__global__ void k_scan_apply(const int *__restrict__ deg, int n, const long long *__restrict__ tile_off,
+                             long long *nptr) {
+    __shared__ long long warp_sum[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int per = kScanTile / 1024;  // elements per thread (blockDim 1024)
+    const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * per;
+    int vals[per];
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < per; i++) {
+        vals[i] = base + i < n ? deg[base + i] : 0;
+        s += vals[i];
+    }
+    long long incl = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        long long y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) warp_sum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        long long w0 = warp_sum[lane];
+        long long wi = w0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            long long y = __shfl_up_sync(kFull, wi, d);
+            if (lane >= d) wi += y;
+        }
+        warp_sum[lane] = wi - w0;
+    }
+    __syncthreads();
+    long long run = tile_off[blockIdx.x] + warp_sum[wid] + (incl - s);
+#pragma unroll
+    for (int i = 0; i < per; i++) {
+        if (base + i < n) nptr[base + i] = run;
+        run += vals[i];
+    }
+}
+
+// Warp per global row: write the sorted neighbour entries (u << 2) | state(v, u)
+// with local u.
+__global__ void k_fill(GSet gs, const uint32_t *__restrict__ state, const long long *__restrict__ nptr,
+                       uint32_t *nbr) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const int words = (n + 15) >> 4;
-    for (long long v = warp; v < n; v += nwarps) {
-        const uint32_t *row = state + v * pitch;
+    for (long long v = warp; v < gs.NV; v += nwarps) {
+        const GMeta mt = gs.meta(gs.graph_of((int)v));
+        const int lv = (int)v - mt.voff;
+        const int words = (mt.n + 15) >> 4;
+        const uint32_t *row = state + mt.soff + (long long)lv * mt.pitch;
         long long base = nptr[v];
         for (int w0 = 0; w0 < words; w0 += kWarp) {
             const int w = w0 + lane;
@@ -237,6 +380,14 @@ __global__ void k_fill(const uint32_t *__restrict__ state, long long pitch, int 
     }
 }
 
+// gid[v] = graph of global vertex v (block per graph).
+__global__ void k_graph_ids(GSet gs, int *gid) {
+    const GMeta mt = gs.meta(blockIdx.x);
+    for (int i = threadIdx.x; i < mt.n; i += blockDim.x) gid[mt.voff + i] = blockIdx.x;
+}
+
+__global__ void k_reset_maxdeg(GraphInfo *info) { info->maxdeg = 0; }
+
 int grid_for(long long work_items, int per_block, int num_sms) {
     long long b = (work_items + per_block - 1) / per_block;
     long long cap = (long long)num_sms * 8;
@@ -247,8 +398,8 @@ int grid_for(long long work_items, int per_block, int num_sms) {
 
 }  // namespace
 
-int launch_zero(void *p, size_t bytes, int num_sms, cudaStream_t s, int *status,
-                unsigned long long *counts, int ncounts, int *ints, int nints) {
+int launch_zero(void *p, size_t bytes, int num_sms, cudaStream_t s, int *status, unsigned long long *counts,
+                long long ncounts, int *ints, long long nints) {
     const size_t n16 = bytes / 16, ntail = bytes % 16;
     const int grid = grid_for((long long)(n16 > 0 ? n16 : 1), 256 * 4, num_sms);
     k_zero<<<grid, 256, 0, s>>>(reinterpret_cast<uint4 *>(p), n16,
@@ -257,40 +408,59 @@ int launch_zero(void *p, size_t bytes, int num_sms, cudaStream_t s, int *status,
     return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
 
-int launch_build_graph(const long long *rowptr, const int *col, int n, long long m,
-                       uint32_t *state, long long pitch, int *deg, int *lo, long long *nptr,
-                       uint32_t *nbr, int *label, GraphInfo *info, int *status, unsigned long long *counts,
-                       int ncounts, bool relabel, int num_sms, cudaStream_t s) {
+int launch_graph_ids(const GSet &gs, int *gid, cudaStream_t s) {
+    if (gs.B <= 1) return 0;
+    k_graph_ids<<<gs.B, 256, 0, s>>>(gs, gid);
+    return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
+}
+
+long long scan_tiles_needed(long long NV) { return NV <= kScanSingleMax ? 0 : (NV + kScanTile - 1) / kScanTile; }
+
+int launch_build_graph(const GSet &gs, long long state_words, uint32_t *state, int *deg, int *lo, long long *nptr,
+                       long long *tile_scratch, uint32_t *nbr, int *label, GraphInfo *info, int *status,
+                       unsigned long long *counts, long long ncounts, bool relabel, int num_sms, cudaStream_t s) {
     int launches = 0;
-    const size_t state_bytes = (size_t)n * (size_t)pitch * 4;
-    const int rows_grid = grid_for((long long)n * kWarp, 256, num_sms);
-    // zero the pair-state matrix, the counts, the status word and (for the
-    // relabelling) the degree histogram kept in lo[]
+    const size_t state_bytes = (size_t)state_words * 4;
+    const long long NV = gs.NV;
+    const int rows_grid = grid_for(NV * kWarp, 256, num_sms);
+    // zero the pair-state blocks, the counts, the status word and (for the
+    // renumbering) the degree histograms kept in lo[]
     int r = launch_zero(state, state_bytes, num_sms, s, status, counts, ncounts, relabel ? lo : nullptr,
-                        relabel ? n + 1 : 0);
+                        relabel ? NV + 1 : 0);
     if (r < 0) return r;
     launches += r;
-    k_ingest<<<rows_grid, 256, 0, s>>>(rowptr, col, n, m, state, pitch, nullptr, status);
+    k_ingest<<<rows_grid, 256, 0, s>>>(gs, state, nullptr, status);
     launches++;
     if (relabel) {
-        // G* degrees under the input labels, then vertices renumbered by
-        // descending degree and the matrix rebuilt under the new numbers
+        // G* degrees under the input labels, then each graph's vertices
+        // renumbered by descending degree and its block rebuilt
         int *dhist = lo;
         int *start = reinterpret_cast<int *>(nptr);
-        k_degrees<<<rows_grid, 256, 0, s>>>(state, pitch, n, deg, nullptr, dhist);
-        k_desc_starts<<<1, 1024, 0, s>>>(dhist, n, start);
-        k_desc_scatter<<<grid_for(n, 256, num_sms), 256, 0, s>>>(deg, n, start, label);
+        k_degrees<<<rows_grid, 256, 0, s>>>(gs, state, deg, nullptr, dhist);
+        k_desc_starts<<<gs.B, 1024, 0, s>>>(gs, dhist, start);
+        k_desc_scatter<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, deg, start, label);
         launches += 3;
         r = launch_zero(state, state_bytes, num_sms, s);
         if (r < 0) return r;
         launches += r;
-        k_ingest<<<rows_grid, 256, 0, s>>>(rowptr, col, n, m, state, pitch, label, nullptr);
+        k_ingest<<<rows_grid, 256, 0, s>>>(gs, state, label, nullptr);
         launches++;
     }
-    k_degrees<<<rows_grid, 256, 0, s>>>(state, pitch, n, deg, lo, nullptr);
-    k_scan_degrees<<<1, 1024, 0, s>>>(deg, n, nptr, info);
-    k_fill<<<rows_grid, 256, 0, s>>>(state, pitch, n, nptr, nbr);
-    launches += 3;
+    k_degrees<<<rows_grid, 256, 0, s>>>(gs, state, deg, lo, nullptr);
+    launches++;
+    if (NV <= kScanSingleMax) {
+        k_scan_degrees<<<1, 1024, 0, s>>>(deg, (int)NV, nptr, info);
+        launches++;
+    } else {
+        const int ntiles = (int)scan_tiles_needed(NV);
+        k_reset_maxdeg<<<1, 1, 0, s>>>(info);
+        k_scan_tiles<<<ntiles, 1024, 0, s>>>(deg, (int)NV, tile_scratch, info);
+        k_scan_top<<<1, 1024, 0, s>>>(tile_scratch, ntiles, nptr, (int)NV, info);
+        k_scan_apply<<<ntiles, 1024, 0, s>>>(deg, (int)NV, tile_scratch, nptr);
+        launches += 4;
+    }
+    k_fill<<<rows_grid, 256, 0, s>>>(gs, state, nptr, nbr);
+    launches++;
     return cudaGetLastError() == cudaSuccess ? launches : ACC_ERR_CUDA;
 }
 

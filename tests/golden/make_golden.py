@@ -8,6 +8,7 @@ it regenerated the same graph), N_k and every nonzero class count.
     python tests/golden/make_golden.py [--threads T] [--only NAME ...]
 """
 import argparse
+import hashlib
 import os
 import sys
 import time
@@ -42,11 +43,47 @@ def write_counts(path, name, g, k, counts, seconds, threads):
                 f.write(f"{c} {int(v)}\n")
 
 
+def counts_digest(counts):
+    """SHA-256 of an int64 count block (little-endian, row-major)."""
+    return hashlib.sha256(np.ascontiguousarray(counts, dtype="<i8").tobytes()).hexdigest()
+
+
+def graphs_digest(graphs):
+    h = hashlib.sha256()
+    for g in graphs:
+        h.update(synth.graph_digest(g).encode())
+    return h.hexdigest()
+
+
+def make_batch_golden(path, threads, n_rand=synth.BATCH_RANDOMISATIONS):
+    """Batched k=4 workload: per base graph, the digest of its 1 + n_rand
+    graphs, the digest and total of their int64 counts [1 + n_rand, 199] and
+    the Z-scores of the base against its randomisations (hex doubles)."""
+    with open(path, "w") as f:
+        f.write("# workload batch_k4: 8 directed Chung-Lu bases (exponent 2.3, m = 4n) x "
+                f"(1 + {n_rand} degree-preserving randomisations, 3m swap attempts)\n")
+        f.write(f"# oracle ESU, {threads} threads; one line per base:\n")
+        f.write("# base n m graphs_sha256 counts_sha256 total z_hex[199]\n")
+        for b in range(synth.BATCH_BASES):
+            base = synth.batch_base(b)
+            graphs = [base] + [synth.batch_randomisation(base, b, i) for i in range(n_rand)]
+            t = time.time()
+            counts = np.stack([oracle.count(g.n, g.src, g.dst, 4, threads=threads) for g in graphs])
+            z = oracle.zscores(counts[0], counts[1:])
+            f.write(f"{b} {base.n} {base.m} {graphs_digest(graphs)} {counts_digest(counts)} "
+                    f"{int(counts.sum())} {' '.join(float(x).hex() for x in z)}\n")
+            f.flush()
+            print(f"batch base {b}: n={base.n} total={int(counts.sum())} in {time.time() - t:.1f} s", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--threads", type=int, default=oracle.max_threads())
     ap.add_argument("--only", nargs="*")
+    ap.add_argument("--batch", action="store_true", help="also write the batched k=4 expectations")
     args = ap.parse_args()
+    if args.batch:
+        make_batch_golden(os.path.join(HERE, "batch_k4.txt"), args.threads)
     for name, (make, k) in WORKLOADS.items():
         if args.only and name not in args.only:
             continue
