@@ -46,6 +46,7 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "chung_lu_n20000_m100000_k4"
 BATCH_WORKLOAD = "batch_k4"
+SERVING_WORKLOAD = "serving"
 
 # Algorithmic integer operations per classified subgraph (the method's minimum
 # at the leaf): k-1 pair states, each an address, a load and a 2-bit extract
@@ -532,24 +533,124 @@ def run_batch_bench(args):
     return 0
 
 
+def run_serving_bench(args):
+    """Serving workload: 64 resident directed Chung-Lu graphs (n log-uniform
+    in [100, 50000], mean out-degree 4-10), a Poisson stream of requests at
+    200/s with k in {3: 50%, 4: 35%, 5: 15%}, replayed in real time against
+    the request server; latency = completion - scheduled arrival."""
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    from paper_1203_3415_gb300 import build as lib_build
+    if rank == 0 or world == 1:
+        lib_build.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_1203_3415_gb300 as acc
+
+    specs = synth.serving_pool_specs()
+    graphs = [synth.serving_graph(sp) for sp in specs]
+    reqs = synth.serving_requests(duration_s=args.serve_seconds)
+    srv = acc.Server(local, slots=args.slots, mem_budget_bytes=int(args.mem_budget_gb * (1 << 30)))
+    tens = []
+    for g in graphs:
+        r, c = g.csr()
+        tens.append((torch.from_numpy(r).to(dev), torch.from_numpy(c).to(dev)))
+    ids = [srv.add_graph(r, c, g.n) for (r, c), g in zip(tens, graphs)]
+    srv.reserve()
+    # warm-up: one request per k on the smallest graph
+    for k in (3, 4, 5):
+        srv.submit(ids[int(np.argmin([g.n for g in graphs]))], k)
+    srv.drain()
+    if dist is not None:
+        dist.barrier()
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    t0 = time.perf_counter()
+    rids, arrivals = [], []
+    i = 0
+    while i < len(reqs):
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i][0] <= now:
+            t_arr, gid, k = reqs[i]
+            rids.append(srv.submit(ids[gid], k))
+            arrivals.append((t_arr, now, gid, k))
+            i += 1
+        srv.progress()
+        if i < len(reqs):
+            wait = reqs[i][0] - (time.perf_counter() - t0)
+            if wait > 0.0005:
+                time.sleep(min(wait, 0.001))
+    srv.drain()
+    t_end = time.perf_counter() - t0
+    clocks = sampler.stop() if sampler else None
+    lat, units, by_k = [], 0, {3: [], 4: [], 5: []}
+    failed = 0
+    for rid, (t_arr, t_sub, gid, k) in zip(rids, arrivals):
+        st, counts, l = srv.poll(rid)
+        if st != acc.ACC_REQ_DONE:
+            failed += 1
+            continue
+        total_l = l + (t_sub - t_arr)  # server latency plus the submission lag
+        lat.append(total_l)
+        by_k[k].append(total_l)
+        units += int(counts.sum())
+    srv.close()
+    lat = np.array(lat)
+    local_rate = units / t_end
+    value = reduce_sum(dist, local_rate, dev) if dist is not None else local_rate
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    pct = lambda a, q: float(np.percentile(a, q) * 1000.0) if len(a) else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(rids),
+        "warmup": 3, "ms_per_step": 1000.0 * t_end / max(1, len(rids)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": SERVING_WORKLOAD, "graphs": len(graphs), "requests": len(rids),
+                   "arrival_rate_per_s": 200, "window_s": args.serve_seconds, "slots": args.slots,
+                   "mem_budget_gb": args.mem_budget_gb, "parallelism": f"replicas{world}"},
+        "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": pct(lat, 100),
+                       "by_k_p50": {str(k): pct(np.array(v), 50) for k, v in by_k.items()},
+                       "by_k_p99": {str(k): pct(np.array(v), 99) for k, v in by_k.items()}},
+        "completed_per_s": len(lat) / t_end, "failed": failed, "wall_s": t_end,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD], default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD, SERVING_WORKLOAD],
+                    default=DEFAULT_WORKLOAD)
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="serving: arrival window")
+    ap.add_argument("--slots", type=int, default=4, help="serving: concurrent requests")
+    ap.add_argument("--mem-budget-gb", type=float, default=96.0, help="serving: workspace budget")
     ap.add_argument("--reference-roots", type=int, default=1000,
                     help="reference arm: ESU roots per step (bounded CPU sample)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":
-        if args.workload == BATCH_WORKLOAD:
+        if args.workload in (BATCH_WORKLOAD, SERVING_WORKLOAD):
             args.workload = DEFAULT_WORKLOAD
         return run_reference(args)
     if args.workload == BATCH_WORKLOAD:
         return run_batch_bench(args)
+    if args.workload == SERVING_WORKLOAD:
+        return run_serving_bench(args)
     return run_ours(args)
 
 

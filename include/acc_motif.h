@@ -185,6 +185,52 @@ ACC_API int acc_motif_count_batch(acc_ctx *ctx, const acc_graph_desc *h_graphs, 
 ACC_API int acc_motif_zscores(const int64_t *d_counts, int32_t groups, int32_t group_size, int k, void *stream,
                               double *d_z);
 
+/*
+ * Serving form: a request server with continuous batching on one GPU.
+ *
+ * Requests (resident graph, k) are submitted at any time.  A request is
+ * admitted as soon as one of the server's slots is free and the slot's device
+ * workspace for it fits the memory budget (FIFO; a request that cannot fit
+ * even with every slot idle fails with ACC_ERR_NOMEM).  Each slot has its own
+ * context and CUDA stream, so admitted requests overlap on the device; a
+ * request's enumeration grid is capped (1/8 of the GPU for graphs of at most
+ * 4096 vertices, 5/8 above) so that one large request cannot hold every SM.
+ * Results are the same as acc_motif_count's for the same graph and k.  The
+ * server does its host work only inside these calls (no threads), so call
+ * acc_server_progress or acc_server_poll regularly.  A server is not
+ * thread-safe.
+ */
+typedef struct acc_server acc_server;
+#define ACC_REQ_QUEUED 0
+#define ACC_REQ_RUNNING 1
+#define ACC_REQ_DONE 2
+
+/* Server on `device` with `slots` (1..64) concurrent requests and a device
+ * memory budget for the slots' workspaces in bytes. */
+ACC_API int acc_server_create(acc_server **out, int device, int32_t slots, int64_t mem_budget_bytes);
+/* Waits for running requests, releases everything (NULL is a no-op). */
+ACC_API void acc_server_destroy(acc_server *srv);
+/* Register a resident graph (device arrays as in acc_motif_count; they must
+ * stay valid while the server may count it).  *graph_id receives its id. */
+ACC_API int acc_server_add_graph(acc_server *srv, const int64_t *d_rowptr, const int32_t *d_col, int32_t n,
+                                 int64_t m, int32_t *graph_id);
+/* Pre-size every slot (within the budget) for the largest registered graph
+ * and build the class tables of every k, so serving allocates nothing; waits. */
+ACC_API int acc_server_reserve(acc_server *srv);
+/* Queue a request; *request_id receives its id.  Admits what fits. */
+ACC_API int acc_server_submit(acc_server *srv, int32_t graph_id, int k, int64_t *request_id);
+/* Retire finished requests and admit queued ones; *running / *queued
+ * (nullable) receive the current numbers. */
+ACC_API int acc_server_progress(acc_server *srv, int32_t *running, int32_t *queued);
+/* Progress, then report request_id: *state = ACC_REQ_QUEUED, _RUNNING,
+ * _DONE or a negative error code; when done, h_counts (nullable, host
+ * int64[num_classes(k)]) receives the counts and *latency_s (nullable) the
+ * seconds from submission to completion (-1 while not finished). */
+ACC_API int acc_server_poll(acc_server *srv, int64_t request_id, int32_t *state, int64_t *h_counts,
+                            double *latency_s);
+/* Run until no request is queued or running. */
+ACC_API int acc_server_drain(acc_server *srv);
+
 /* Canonical adjacency code of class cls (0 <= cls < num_classes(k)). */
 ACC_API int acc_motif_class_code(acc_ctx *ctx, int k, int32_t cls, uint32_t *code);
 

@@ -37,8 +37,10 @@ EXPORTS = (
     "acc_motif_count", "acc_motif_count_host", "acc_motif_batch_prepare", "acc_motif_batch_run",
     "acc_motif_count_batch", "acc_motif_zscores", "acc_motif_class_code", "acc_motif_classify_code",
     "acc_motif_copy_table", "acc_motif_last_stats", "acc_ctx_set_timing", "acc_motif_last_timing",
-    "acc_motif_build_table_static",
+    "acc_motif_build_table_static", "acc_server_create", "acc_server_destroy", "acc_server_add_graph",
+    "acc_server_reserve", "acc_server_submit", "acc_server_progress", "acc_server_poll", "acc_server_drain",
 )
+ACC_REQ_QUEUED, ACC_REQ_RUNNING, ACC_REQ_DONE = 0, 1, 2
 
 
 def _load():
@@ -67,6 +69,15 @@ def _load():
     lib.acc_ctx_set_timing.argtypes = [vp, ctypes.c_int]
     lib.acc_motif_last_timing.argtypes = [vp, vp]
     lib.acc_motif_build_table_static.argtypes = [ctypes.c_int, vp, vp, vp]
+    lib.acc_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, i32, i64]
+    lib.acc_server_destroy.argtypes = [vp]
+    lib.acc_server_destroy.restype = None
+    lib.acc_server_add_graph.argtypes = [vp, vp, vp, i32, i64, ctypes.POINTER(i32)]
+    lib.acc_server_reserve.argtypes = [vp]
+    lib.acc_server_submit.argtypes = [vp, i32, ctypes.c_int, ctypes.POINTER(i64)]
+    lib.acc_server_progress.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.acc_server_poll.argtypes = [vp, i64, ctypes.POINTER(i32), vp, ctypes.POINTER(ctypes.c_double)]
+    lib.acc_server_drain.argtypes = [vp]
     return lib
 
 
@@ -184,6 +195,95 @@ def acc_motif_build_table_static(k: int, stream: int, d_table: int, d_class_code
     """Table build that allocates nothing (working memory is a fixed array in
     the library); for callers that cannot allocate device memory."""
     return _L().acc_motif_build_table_static(k, stream, d_table, d_class_code)
+
+
+def acc_server_create(device: int, slots: int, mem_budget_bytes: int) -> int:
+    h = ctypes.c_void_p()
+    _check(_L().acc_server_create(ctypes.byref(h), device, slots, mem_budget_bytes), "acc_server_create")
+    return h.value
+
+
+def acc_server_destroy(srv: int) -> None:
+    _L().acc_server_destroy(srv)
+
+
+def acc_server_add_graph(srv: int, d_rowptr: int, d_col: int, n: int, m: int) -> int:
+    gid = ctypes.c_int32()
+    _check(_L().acc_server_add_graph(srv, d_rowptr, d_col, n, m, ctypes.byref(gid)), "acc_server_add_graph")
+    return gid.value
+
+
+def acc_server_reserve(srv: int) -> int:
+    return _L().acc_server_reserve(srv)
+
+
+def acc_server_submit(srv: int, graph_id: int, k: int) -> int:
+    rid = ctypes.c_int64()
+    _check(_L().acc_server_submit(srv, graph_id, k, ctypes.byref(rid)), "acc_server_submit")
+    return rid.value
+
+
+def acc_server_progress(srv: int):
+    run, q = ctypes.c_int32(), ctypes.c_int32()
+    _check(_L().acc_server_progress(srv, ctypes.byref(run), ctypes.byref(q)), "acc_server_progress")
+    return run.value, q.value
+
+
+def acc_server_poll(srv: int, request_id: int, h_counts: int | None = None):
+    """(state, latency_s) of a request; h_counts receives the counts when done."""
+    st, lat = ctypes.c_int32(), ctypes.c_double()
+    _check(_L().acc_server_poll(srv, request_id, ctypes.byref(st), h_counts, ctypes.byref(lat)), "acc_server_poll")
+    return st.value, lat.value
+
+
+def acc_server_drain(srv: int) -> int:
+    return _L().acc_server_drain(srv)
+
+
+class Server:
+    """Request server with continuous batching (see include/acc_motif.h)."""
+
+    def __init__(self, device: int = 0, slots: int = 4, mem_budget_bytes: int = 64 << 30):
+        self.srv = acc_server_create(device, slots, mem_budget_bytes)
+        self._graphs = []  # keeps the device tensors alive
+        self._k = {}
+
+    def add_graph(self, rowptr, col, n: int) -> int:
+        self._graphs.append((rowptr, col))
+        return acc_server_add_graph(self.srv, rowptr.data_ptr(), col.data_ptr() if col.numel() else 0, n,
+                                    col.numel())
+
+    def reserve(self):
+        _check(acc_server_reserve(self.srv), "acc_server_reserve")
+
+    def submit(self, graph_id: int, k: int) -> int:
+        rid = acc_server_submit(self.srv, graph_id, k)
+        self._k[rid] = k
+        return rid
+
+    def progress(self):
+        return acc_server_progress(self.srv)
+
+    def poll(self, rid: int):
+        """(state, counts or None, latency_s)."""
+        import numpy as np
+        out = np.zeros(NUM_CLASSES[self._k[rid]], dtype=np.int64)
+        st, lat = acc_server_poll(self.srv, rid, out.ctypes.data)
+        return st, (out if st == ACC_REQ_DONE else None), lat
+
+    def drain(self):
+        _check(acc_server_drain(self.srv), "acc_server_drain")
+
+    def close(self):
+        if self.srv:
+            acc_server_destroy(self.srv)
+            self.srv = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------------------

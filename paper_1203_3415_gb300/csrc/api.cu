@@ -7,68 +7,9 @@
 #include <vector>
 
 #include "common.cuh"
+#include "context.cuh"
 
 using namespace acc;
-
-struct acc_ctx {
-    int device = 0;
-    int num_sms = 0;
-    cudaStream_t own = nullptr;  // stream of the host-buffer entry points
-
-    // code -> class tables per k
-    int16_t *lut[6] = {};
-    int16_t *lut_sv[6] = {};
-    uint32_t *class_code_dev[6] = {};
-    int16_t *lut_host[6] = {};
-    uint32_t *class_code_host[6] = {};
-
-    // workspace (grow-only)
-    uint32_t *state = nullptr;
-    size_t state_cap = 0;
-    int *deg = nullptr, *lo = nullptr, *label = nullptr;
-    long long *nptr = nullptr;
-    size_t n_cap = 0;
-    long long *tiles = nullptr;
-    size_t tiles_cap = 0;
-    uint32_t *nbr = nullptr;
-    size_t nbr_cap = 0;
-    GraphInfo *info = nullptr;
-    uint4 *queue = nullptr;
-    unsigned long long queue_cap = 0;
-    uint32_t *scratch = nullptr;
-    size_t scratch_cap = 0;
-    int *status_dev = nullptr;
-    int *status_host = nullptr;  // pinned
-
-    // prepared batch
-    GMeta *meta_dev = nullptr;
-    size_t meta_cap = 0;
-    int *gid = nullptr;
-    size_t gid_cap = 0;
-    bool batch_ready = false;
-    int batch_k = 0;
-    GSet batch_set = {};
-    long long batch_words = 0, batch_arcs = 0;
-    int batch_max_n = 0;
-
-    // host-buffer entry point
-    long long *h2d_rowptr = nullptr;
-    size_t h2d_rowptr_cap = 0;
-    int *h2d_col = nullptr;
-    size_t h2d_col_cap = 0;
-    unsigned long long *h2d_counts = nullptr;
-
-    // stage timing
-    bool timing = false;
-    bool timed_call = false;
-    cudaEvent_t ev[4] = {};
-
-    // statistics of the last count
-    int last_launches = 0;
-    int last_k = 0;
-    long long last_units = 0;
-    int last_blocks = 0;
-};
 
 namespace {
 
@@ -221,13 +162,13 @@ int run_set(acc_ctx *c, const GSet &gs, long long state_words, int max_n, int k,
     a.status = status;
     const bool any = gs.NV > 0;
     if (any) {
-        rc = launch_enumerate(k, a, c->num_sms, 1, s);
+        rc = launch_enumerate(k, a, c->num_sms, 1, s, c->grid_num, c->grid_den);
         if (rc < 0) return rc;
         launches += rc;
     }
     if (c->timing && !ok(cudaEventRecord(c->ev[3], s))) return ACC_ERR_CUDA;
     if (any) {
-        rc = launch_enumerate(k, a, c->num_sms, 2, s);
+        rc = launch_enumerate(k, a, c->num_sms, 2, s, c->grid_num, c->grid_den);
         if (rc < 0) return rc;
         launches += rc;
     }
@@ -235,7 +176,7 @@ int run_set(acc_ctx *c, const GSet &gs, long long state_words, int max_n, int k,
     c->last_launches = launches;
     c->last_k = k;
     c->last_units = gs.NV;
-    c->last_blocks = enum_grid_warps(k, c->num_sms) / kWarpsPerBlock;
+    c->last_blocks = enum_grid_warps(k, c->num_sms) / kWarpsPerBlock * c->grid_num / c->grid_den;
     return ACC_OK;
 }
 
@@ -276,6 +217,27 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
 }
 
 }  // namespace
+
+namespace acc {
+
+long long ctx_footprint(const acc_ctx *c, long long n, long long m, int k) {
+    const long long pitch = state_pitch((int)n);
+    const long long warps = enum_grid_warps(k, c->num_sms);
+    const long long bytes = n * pitch * 4 + 4 * 4 * (n + 1) + 8 * (n + 1) + 4 * (2 * m + 1) +
+                            (long long)kQueueCap * 16 + scratch_per_warp((int)n) * (warps > 0 ? warps : 0) * 4;
+    return bytes + bytes / 4;
+}
+
+int ctx_reserve(acc_ctx *c, long long n, long long m, int k) {
+    if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
+    for (int kk = 3; kk <= 5; kk++) {
+        const int rc = ensure_lut(c, kk, c->own);
+        if (rc) return rc;
+    }
+    return ensure_workspace(c, n, n * state_pitch((int)n), m, (int)n, k);
+}
+
+}  // namespace acc
 
 extern "C" {
 

@@ -142,7 +142,10 @@ struct EnumArgs {
 int launch_zscores(const long long *counts, int groups, int group_size, int K, double *z, cudaStream_t s);
 
 // phase 1: light units run, heavy units queued; phase 2: the queue drained.
-int launch_enumerate(int k, const EnumArgs &a, int num_sms, int phase, cudaStream_t s);
+// The grid is the full persistent grid times grid_num / grid_den (at least
+// one block per SM).
+int launch_enumerate(int k, const EnumArgs &a, int num_sms, int phase, cudaStream_t s, int grid_num = 1,
+                     int grid_den = 1);
 int enum_grid_warps(int k, int num_sms);
 
 }  // namespace acc

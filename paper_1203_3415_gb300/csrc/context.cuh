@@ -1,0 +1,84 @@
+// The library context (private to the library's translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+using acc::GMeta;
+using acc::GSet;
+using acc::GraphInfo;
+
+struct acc_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t own = nullptr;  // stream of the host-buffer entry points
+
+    // code -> class tables per k
+    int16_t *lut[6] = {};
+    int16_t *lut_sv[6] = {};
+    uint32_t *class_code_dev[6] = {};
+    int16_t *lut_host[6] = {};
+    uint32_t *class_code_host[6] = {};
+
+    // workspace (grow-only)
+    uint32_t *state = nullptr;
+    size_t state_cap = 0;
+    int *deg = nullptr, *lo = nullptr, *label = nullptr;
+    long long *nptr = nullptr;
+    size_t n_cap = 0;
+    long long *tiles = nullptr;
+    size_t tiles_cap = 0;
+    uint32_t *nbr = nullptr;
+    size_t nbr_cap = 0;
+    GraphInfo *info = nullptr;
+    uint4 *queue = nullptr;
+    unsigned long long queue_cap = 0;
+    uint32_t *scratch = nullptr;
+    size_t scratch_cap = 0;
+    int *status_dev = nullptr;
+    int *status_host = nullptr;  // pinned
+
+    // prepared batch
+    GMeta *meta_dev = nullptr;
+    size_t meta_cap = 0;
+    int *gid = nullptr;
+    size_t gid_cap = 0;
+    bool batch_ready = false;
+    int batch_k = 0;
+    GSet batch_set = {};
+    long long batch_words = 0, batch_arcs = 0;
+    int batch_max_n = 0;
+
+    // host-buffer entry point
+    long long *h2d_rowptr = nullptr;
+    size_t h2d_rowptr_cap = 0;
+    int *h2d_col = nullptr;
+    size_t h2d_col_cap = 0;
+    unsigned long long *h2d_counts = nullptr;
+
+    // stage timing
+    bool timing = false;
+    bool timed_call = false;
+    cudaEvent_t ev[4] = {};
+
+    // statistics of the last count
+    int last_launches = 0;
+    int last_k = 0;
+    long long last_units = 0;
+    int last_blocks = 0;
+
+    // enumeration grid cap as a fraction of the full persistent grid
+    // (1 = whole GPU); the request server lowers it so requests overlap
+    int grid_num = 1, grid_den = 1;
+};
+
+
+namespace acc {
+// Device bytes a context's workspace needs for one graph of n vertices and m
+// arcs at k (with the growth margin), and pre-sizing it (plus the tables of
+// every k) so later counts of graphs up to that size allocate nothing.
+long long ctx_footprint(const acc_ctx *c, long long n, long long m, int k);
+int ctx_reserve(acc_ctx *c, long long n, long long m, int k);
+}  // namespace acc

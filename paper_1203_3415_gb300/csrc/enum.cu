@@ -767,10 +767,12 @@ int blocks_per_sm() {
 }
 
 template <int K>
-int launch_k(const EnumArgs &a, int num_sms, int phase, cudaStream_t s) {
+int launch_k(const EnumArgs &a, int num_sms, int phase, cudaStream_t s, int grid_num, int grid_den) {
     const int bps = blocks_per_sm<K>();
     if (bps < 1) return ACC_ERR_CUDA;
-    const int grid = num_sms * bps;
+    int grid = (int)((long long)num_sms * bps * grid_num / grid_den);
+    if (grid < num_sms) grid = num_sms;
+    if (grid > num_sms * bps) grid = num_sms * bps;
     k_enum<K><<<grid, kThreads, Layout<K>::total, s>>>(a, phase);
     return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
@@ -783,11 +785,11 @@ int enum_grid_warps(int k, int num_sms) {
     return num_sms * bps * kWarpsPerBlock;
 }
 
-int launch_enumerate(int k, const EnumArgs &a, int num_sms, int phase, cudaStream_t s) {
+int launch_enumerate(int k, const EnumArgs &a, int num_sms, int phase, cudaStream_t s, int grid_num, int grid_den) {
     switch (k) {
-    case 3: return launch_k<3>(a, num_sms, phase, s);
-    case 4: return launch_k<4>(a, num_sms, phase, s);
-    case 5: return launch_k<5>(a, num_sms, phase, s);
+    case 3: return launch_k<3>(a, num_sms, phase, s, grid_num, grid_den);
+    case 4: return launch_k<4>(a, num_sms, phase, s, grid_num, grid_den);
+    case 5: return launch_k<5>(a, num_sms, phase, s, grid_num, grid_den);
     default: return ACC_ERR_K;
     }
 }

@@ -1,0 +1,111 @@
+"""Serving form: requests admitted by free slots and device memory, running
+concurrently on the GPU, give exactly the counts they give alone (tolerance
+0: int64 histograms)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_helpers import csr_arrays
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def acc():
+    import torch  # noqa: F401
+    from paper_1203_3415_gb300 import build
+    build.build()
+    import paper_1203_3415_gb300 as p
+    return p
+
+
+def pool():
+    specs = [(300, 1200, 1), (800, 3200, 2), (2500, 12000, 3), (6000, 30000, 4), (150, 600, 5),
+             (4000, 16000, 6), (1200, 9000, 7), (9000, 40000, 8)]
+    return [synth.chung_lu(n, m, 2.2, 120, 10, 7000 + s) for n, m, s in specs]
+
+
+def to_dev(g):
+    import torch
+    r, c = g.csr()
+    return torch.from_numpy(r).cuda(), torch.from_numpy(c).cuda()
+
+
+def requests(n_graphs, count, seed):
+    rng = np.random.default_rng(seed)
+    return [(int(rng.integers(0, n_graphs)), int(rng.choice([3, 3, 4, 4, 5]))) for _ in range(count)]
+
+
+def test_mix_equals_alone(acc):
+    graphs = pool()
+    dev = [to_dev(g) for g in graphs]
+    reqs = requests(len(graphs), 48, 11)
+    counter = acc.Counter(0)
+    alone = {}
+    for gi, k in set(reqs):
+        alone[(gi, k)] = counter.count(dev[gi][0], dev[gi][1], graphs[gi].n, k).cpu().numpy()
+    counter.close()
+    # the oracle agrees on the small ones
+    for gi, k in alone:
+        if graphs[gi].n <= 1200 and k < 5:
+            g = graphs[gi]
+            assert alone[(gi, k)].tolist() == oracle.count(g.n, g.src, g.dst, k).tolist()
+    srv = acc.Server(0, slots=4, mem_budget_bytes=48 << 30)
+    ids = [srv.add_graph(r, c, g.n) for (r, c), g in zip(dev, graphs)]
+    srv.reserve()
+    rids = [srv.submit(ids[gi], k) for gi, k in reqs]  # all at once: they queue and overlap
+    most = 0
+    while True:
+        running, queued = srv.progress()
+        most = max(most, running)
+        if running == 0 and queued == 0:
+            break
+    assert most >= 2  # several requests were on the device together
+    srv.drain()
+    for rid, (gi, k) in zip(rids, reqs):
+        st, counts, lat = srv.poll(rid)
+        assert st == acc.ACC_REQ_DONE and lat >= 0.0
+        assert counts.tolist() == alone[(gi, k)].tolist(), (gi, k)
+    srv.close()
+
+
+def test_memory_admission_serialises(acc):
+    graphs = [synth.chung_lu(n, 4 * n, 2.2, 120, 10, 7100 + n) for n in (6000, 5600, 5800, 6000)]
+    dev = [to_dev(g) for g in graphs]
+    counter = acc.Counter(0)
+    want = [counter.count(r, c, g.n, 4).cpu().numpy() for (r, c), g in zip(dev, graphs)]
+    counter.close()
+    # a budget that holds one such workspace (~0.4 GB) but not two
+    srv = acc.Server(0, slots=4, mem_budget_bytes=int(0.6e9))
+    ids = [srv.add_graph(r, c, g.n) for (r, c), g in zip(dev, graphs)]
+    rids = [srv.submit(i, 4) for i in ids]
+    while True:
+        running, queued = srv.progress()
+        assert running <= 1
+        if running == 0 and queued == 0:
+            break
+    for rid, w in zip(rids, want):
+        st, counts, _ = srv.poll(rid)
+        assert st == acc.ACC_REQ_DONE and counts.tolist() == w.tolist()
+    srv.close()
+
+
+def test_request_errors(acc):
+    import torch
+    srv = acc.Server(0, slots=2, mem_budget_bytes=8 << 30)
+    r, c = csr_arrays(4, [0, 1], [1, 1])  # self-loop 1 -> 1
+    bad = srv.add_graph(torch.from_numpy(r).cuda(), torch.from_numpy(c).cuda(), 4)
+    rid = srv.submit(bad, 3)
+    srv.drain()
+    assert srv.poll(rid)[0] == acc.ACC_ERR_INPUT
+    srv.close()
+    # a graph whose workspace can never fit the budget
+    g = synth.chung_lu(20000, 80000, 2.2, 200, 10, 3)
+    rr, cc = to_dev(g)
+    srv = acc.Server(0, slots=1, mem_budget_bytes=1 << 20)
+    gid = srv.add_graph(rr, cc, g.n)
+    rid = srv.submit(gid, 4)
+    srv.drain()
+    assert srv.poll(rid)[0] == acc.ACC_ERR_NOMEM
+    srv.close()
