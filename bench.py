@@ -279,6 +279,7 @@ def run_ours(args):
     counts = torch.zeros(acc.NUM_CLASSES[k], dtype=torch.int64, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     counter = acc.Counter(local)
+    counter.set_mode(acc.ACC_MODE_ENUMERATE if args.mode == "enumerate" else acc.ACC_MODE_COUNT)
     counter.prepare(k)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -383,6 +384,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1000.0 * max_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": args.workload, "k": k, "n": g.n, "m": g.m, "subgraphs_per_step": n_k,
+                   "mode": args.mode,
                    "l2": "flushed between timed steps (256 MiB device write)",
                    "parallelism": f"replicas{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
@@ -641,6 +643,8 @@ def main():
     ap.add_argument("--reference-roots", type=int, default=1000,
                     help="reference arm: ESU roots per step (bounded CPU sample)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["count", "enumerate"], default="count",
+                    help="last two levels counted by state-vector groups, or every leaf enumerated")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -255,6 +255,20 @@ ACC_API int acc_motif_copy_table(acc_ctx *ctx, int k, int16_t *h_table);
 ACC_API int acc_motif_last_stats(acc_ctx *ctx, int64_t *h_stats);
 
 /*
+ * How the last two levels of the enumeration are counted.
+ *  ACC_MODE_COUNT (default): per extension list, the pairs of members that
+ *   are not adjacent are counted per pair of state-vector groups (their class
+ *   depends only on the two members' states to the prefix), the adjacent
+ *   pairs are corrected one by one from the members' neighbour lists, as the
+ *   paper's Table starb counts patterns from set sizes minus edges.
+ *  ACC_MODE_ENUMERATE: every k-subset is visited and classified on its own.
+ * Both give identical counts.  Errors: ACC_ERR_ARG.
+ */
+#define ACC_MODE_COUNT 0
+#define ACC_MODE_ENUMERATE 1
+ACC_API int acc_ctx_set_mode(acc_ctx *ctx, int mode);
+
+/*
  * Stage timing.  With timing on (on != 0), every acc_motif_count records CUDA
  * events on its stream around its stages.  acc_motif_last_timing waits for
  * the last call's end event and writes float h_ms[4], in milliseconds:

@@ -37,10 +37,11 @@ EXPORTS = (
     "acc_motif_count", "acc_motif_count_host", "acc_motif_batch_prepare", "acc_motif_batch_run",
     "acc_motif_count_batch", "acc_motif_zscores", "acc_motif_class_code", "acc_motif_classify_code",
     "acc_motif_copy_table", "acc_motif_last_stats", "acc_ctx_set_timing", "acc_motif_last_timing",
-    "acc_motif_build_table_static", "acc_server_create", "acc_server_destroy", "acc_server_add_graph",
+    "acc_motif_build_table_static", "acc_ctx_set_mode", "acc_server_create", "acc_server_destroy", "acc_server_add_graph",
     "acc_server_reserve", "acc_server_submit", "acc_server_progress", "acc_server_poll", "acc_server_drain",
 )
 ACC_REQ_QUEUED, ACC_REQ_RUNNING, ACC_REQ_DONE = 0, 1, 2
+ACC_MODE_COUNT, ACC_MODE_ENUMERATE = 0, 1
 
 
 def _load():
@@ -67,6 +68,7 @@ def _load():
     lib.acc_motif_copy_table.argtypes = [vp, ctypes.c_int, vp]
     lib.acc_motif_last_stats.argtypes = [vp, vp]
     lib.acc_ctx_set_timing.argtypes = [vp, ctypes.c_int]
+    lib.acc_ctx_set_mode.argtypes = [vp, ctypes.c_int]
     lib.acc_motif_last_timing.argtypes = [vp, vp]
     lib.acc_motif_build_table_static.argtypes = [ctypes.c_int, vp, vp, vp]
     lib.acc_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, i32, i64]
@@ -181,6 +183,10 @@ def acc_motif_copy_table(ctx: int, k: int, h_table: int) -> int:
 
 def acc_motif_last_stats(ctx: int, h_stats: int) -> int:
     return _L().acc_motif_last_stats(ctx, h_stats)
+
+
+def acc_ctx_set_mode(ctx: int, mode: int) -> int:
+    return _L().acc_ctx_set_mode(ctx, mode)
 
 
 def acc_ctx_set_timing(ctx: int, on: int) -> int:
@@ -390,6 +396,10 @@ class Counter:
 
     def classify_code(self, k: int, code: int) -> int:
         return acc_motif_classify_code(self.ctx, k, code)
+
+    def set_mode(self, mode: int):
+        """ACC_MODE_COUNT (default) or ACC_MODE_ENUMERATE; same counts."""
+        _check(acc_ctx_set_mode(self.ctx, mode), "acc_ctx_set_mode")
 
     def set_timing(self, on: bool = True):
         _check(acc_ctx_set_timing(self.ctx, 1 if on else 0), "acc_ctx_set_timing")

@@ -83,7 +83,9 @@ struct Layout {
     static constexpr size_t pending = 16;
     static constexpr size_t hist = (K == 5 ? size_t(NCLS) * 4 : size_t(kWarpsPerBlock) * NCLS * 4 + 15) & ~size_t(15);
     static constexpr size_t ebuf = size_t(kWarpsPerBlock) * LISTS * CAP * 4;
-    static constexpr size_t total = lut + pending + hist + ebuf;
+    static constexpr int G = 1 << (2 * (K - 2));  // state vectors to the prefix: 4, 16, 64
+    static constexpr size_t groups = size_t(kWarpsPerBlock) * 3 * 64 * 4;  // count mode: sizes + list
+    static constexpr size_t total = lut + pending + hist + ebuf + groups;
 };
 
 __device__ __forceinline__ uint32_t probe(const uint32_t *__restrict__ st, long long pitch, uint32_t a, uint32_t b) {
@@ -179,6 +181,27 @@ struct Sink {
     unsigned long long *counts_base;  // int64[B * NCLS]
     int gcur;           // graph whose counts this warp accumulates
     bool direct;        // k = 5 with several graphs: runs go straight to the int64 counts
+    unsigned long long moved;  // count mode: this lane's |increments| since the last accounting
+
+    // Count mode: add delta (may be negative) to class cls.  Shared counters
+    // are read as signed 32-bit when drained; a delta too large for them goes
+    // straight to the int64 counts.
+    __device__ __forceinline__ void add(int cls, long long delta) {
+        if (cls < 0) {
+            set_status(status, ACC_ERR_INTERNAL);
+            return;
+        }
+        if (direct || delta >= (1ll << 28) || delta <= -(1ll << 28)) {
+            atomicAdd(&counts[cls], (unsigned long long)delta);
+            return;
+        }
+        atomicAdd(&hist[cls], (uint32_t)(int32_t)delta);
+        moved += (unsigned long long)(delta < 0 ? -delta : delta);
+    }
+
+    __device__ __forceinline__ int cls_of(uint32_t code) const {
+        return Layout<K>::SMEM_LUT ? (int)lut[code] : (int)__ldg(lut + code);
+    }
 
     __device__ __forceinline__ void flush() {
         if (run_len) {
@@ -196,10 +219,10 @@ struct Sink {
         if (K <= 4 && gcur >= 0) {
             __syncwarp();
             for (int c = lane; c < Layout<K>::NCLS; c += kWarp) {
-                const uint32_t v = hist[c];
+                const int32_t v = (int32_t)hist[c];
                 if (v) {
                     hist[c] = 0;
-                    atomicAdd(&counts[c], (unsigned long long)v);
+                    atomicAdd(&counts[c], (unsigned long long)(long long)v);
                 }
             }
             __syncwarp();
@@ -241,10 +264,10 @@ struct Sink {
                 flush();
                 __syncwarp();
                 for (int c = lane; c < Layout<K>::NCLS; c += kWarp) {
-                    const uint32_t v = hist[c];
+                    const int32_t v = (int32_t)hist[c];
                     if (v) {
                         hist[c] = 0;
-                        atomicAdd(&counts[c], (unsigned long long)v);
+                        atomicAdd(&counts[c], (unsigned long long)(long long)v);
                     }
                 }
                 __syncwarp();
@@ -261,8 +284,8 @@ struct Sink {
             old = __shfl_sync(kFull, old, 0);
             if (old < kDrainAt && old + since >= kDrainAt) {
                 for (int c = lane; c < Layout<K>::NCLS; c += kWarp) {
-                    const uint32_t v = atomicExch(&hist[c], 0u);
-                    if (v) atomicAdd(&counts[c], (unsigned long long)v);
+                    const int32_t v = (int32_t)atomicExch(&hist[c], 0u);
+                    if (v) atomicAdd(&counts[c], (unsigned long long)(long long)v);
                 }
                 __syncwarp();
                 if (lane == 0) atomicSub(pending, old + since);
@@ -272,10 +295,27 @@ struct Sink {
     }
 };
 
+// Count mode: fold the lanes' |increments| into the warp's accounting (whole
+// warp, between batches).
+template <int K>
+__device__ __forceinline__ void account_moved(Sink<K> &sink, int lane) {
+    unsigned long long t = sink.moved;
+#pragma unroll
+    for (int d = 16; d; d >>= 1) t += __shfl_xor_sync(kFull, t, d);
+    sink.moved = 0;
+    while (t > 0) {  // at most 2^28 per step keeps the 32-bit accounting exact
+        const uint32_t step = t > (1ull << 28) ? (1u << 28) : (uint32_t)t;
+        sink.after_batch(step, lane);
+        t -= step;
+    }
+}
+
 struct Scratch {
     uint32_t *buf[2];  // shared-memory lists (buf[1] only for k = 5)
     uint32_t *ovf[2];  // global overflow lists of this warp
     int cap;
+    uint8_t *vmap;     // count mode: this warp's member marks, one byte per vertex
+    uint32_t *gcnt;    // count mode: group sizes and the non-empty group list
 };
 
 // The last two ESU levels over extension list E[0..B), virtual rows
@@ -378,6 +418,109 @@ __device__ __forceinline__ void leaves(const GView &g, Sink<K> &sink, const uint
     }
 }
 
+// Count mode for the last two ESU levels over E[0..B), rows [jlo, jend).
+// The class of a pair leaf P + {x, y} with x, y not adjacent depends only on
+// the two state vectors (states to the prefix), so all such pairs are counted
+// per pair of state-vector groups, |g_a| |g_b| or C(|g|, 2) of them, as the
+// paper's per-vertex tables count patterns from set sizes (Table starb).
+// Adjacent pairs are then moved to their own classes one by one, found in
+// the neighbour lists of the list members (the paper's m / m' corrections),
+// and the same scan yields the exclusive leaves P + {x, u}.  `bulk` (set for
+// exactly one chunk of a list) adds the group-pair counts.  vmap marks the
+// list members (state vector + 1) and is all zero again on return.
+template <int K>
+__device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, const uint32_t *E, int B, int jlo,
+                                             int jend, bool bulk, const uint32_t *pm, uint32_t pcode,
+                                             uint32_t root, uint8_t *vmap, uint32_t *gcnt, int lane) {
+    using L = Layout<K>;
+    uint32_t *glist = gcnt + 64;  // (group << 16 | 0) packed as value, count pairs
+    if (bulk)
+        for (int i = lane; i < L::G; i += kWarp) gcnt[i] = 0;
+    __syncwarp();
+    for (int q = lane; q < B; q += kWarp) {
+        const uint32_t e = E[q];
+        vmap[e_id(e)] = (uint8_t)(e_sv(e) + 1u);
+        if (bulk) atomicAdd(&gcnt[e_sv(e)], 1u);
+    }
+    __syncwarp();
+    if (bulk) {
+        // the non-empty groups, compacted
+        int ng = 0;
+        for (int b0 = 0; b0 < L::G; b0 += kWarp) {
+            const int gi = b0 + lane;
+            const uint32_t c = gi < L::G ? gcnt[gi] : 0u;
+            const unsigned m = __ballot_sync(kFull, c > 0);
+            if (c > 0) {
+                const int pos = ng + __popc(m & ((1u << lane) - 1u));
+                glist[2 * pos] = (uint32_t)gi;
+                glist[2 * pos + 1] = c;
+            }
+            ng += __popc(m);
+        }
+        __syncwarp();
+        // every unordered pair of members, as if not adjacent
+        for (int ia = 0; ia < ng; ia++) {
+            const uint32_t ga = glist[2 * ia], ca = glist[2 * ia + 1];
+            const uint32_t ra = pcode | (ga << L::SH_ROW);
+            for (int ib = ia + lane; ib < ng; ib += kWarp) {
+                const uint32_t gb = glist[2 * ib], cb = glist[2 * ib + 1];
+                const long long pairs = ib == ia ? (long long)ca * (ca - 1) / 2 : (long long)ca * cb;
+                if (pairs) sink.add(sink.cls_of(ra | gb), pairs);
+            }
+        }
+        account_moved(sink, lane);
+    }
+    // neighbour scan of rows [jlo, jend): adjacent member pairs (each once,
+    // from its smaller vertex) and exclusive neighbours
+    for (int jb = jlo; jb < jend; jb += kWarp) {
+        const int j = jb + lane;
+        uint32_t ej = 0, first = 0;
+        int cnt = 0;
+        if (j < jend) {
+            ej = E[j];
+            const uint32_t x = e_id(ej);
+            const long long nb = g.nptr[x];
+            const int d = g.deg[x];
+            const int st = first_above(g.nbr, nb, d, root);
+            first = (uint32_t)(nb + st);
+            cnt = d - st;
+        }
+        int tot;
+        const int pre = excl_scan(cnt, lane, &tot);
+        const uint32_t cj = pcode | (e_sv(ej) << L::SH_ROW);
+        const uint32_t xj = e_id(ej);
+        const uint32_t off = first - (uint32_t)pre;
+        for (int t0 = 0; t0 < tot; t0 += kWarp) {
+            const int t = t0 + lane;
+            const int r = lb_search(pre, t);
+            const uint32_t cr = __shfl_sync(kFull, cj, r);
+            const uint32_t orow = __shfl_sync(kFull, off, r);
+            const uint32_t xr = __shfl_sync(kFull, xj, r);
+            if (t < tot) {
+                const uint32_t ue = __ldg(g.nbr + (orow + (uint32_t)t));
+                const uint32_t u = ue >> 2, su = ue & 3u;
+                const uint32_t mu = vmap[u];
+                if (mu) {
+                    if (u > xr) {
+                        const uint32_t base = cr | (mu - 1u);
+                        sink.add(sink.cls_of(base | (su << L::SH_PAIR)), 1);
+                        sink.add(sink.cls_of(base), -1);
+                    }
+                } else {
+                    bool excl = true;
+#pragma unroll
+                    for (int k2 = 0; k2 < K - 2; k2++) excl = excl && probe(g.state, g.pitch, pm[k2], u) == 0u;
+                    if (excl) sink.add(sink.cls_of(cr | (su << L::SH_PAIR)), 1);
+                }
+            }
+        }
+        account_moved(sink, lane);
+    }
+    __syncwarp();
+    for (int q = lane; q < B; q += kWarp) vmap[e_id(E[q])] = 0;
+    __syncwarp();
+}
+
 // Extension list of the prefix {v, w1} for k >= 4 (unit = arc position p in
 // row v, w1 = N*(v)[p - nptr[v]] > v): N*(v) after w1, then the exclusive
 // neighbours of w1 (above v, not adjacent to v).  Entry states:
@@ -445,6 +588,30 @@ __device__ int queue_closed_form(const EnumArgs &a, uint32_t unit, int v, long l
         const unsigned ball = __ballot_sync(kFull, lost);
         if (ball) {
             rest = (int)((c0 + __ffs(ball) - 1) * Pu / C);
+            break;
+        }
+    }
+    return rest;
+}
+
+// Count mode: queue rows [0, rows) of a heavy unit as C chunks of equal row
+// counts.  Returns the first row the queue could not take (rows when all fit).
+__device__ int queue_uniform(const EnumArgs &a, uint32_t unit, int v, long long rows, long long C, int lane) {
+    if (C > rows) C = rows;
+    if (C < 1) C = 1;
+    const unsigned long long base = reserve(a, (unsigned long long)C, lane);
+    int rest = (int)rows;
+    for (long long c0 = 0; c0 < C; c0 += kWarp) {
+        const long long c = c0 + lane;
+        bool lost = false;
+        if (c < C) {
+            const uint32_t lo = (uint32_t)(c * rows / C), hi = (uint32_t)((c + 1) * rows / C);
+            if (base + c < a.queue_cap) a.queue[base + c] = make_uint4(unit, lo, hi, (uint32_t)v);
+            else lost = true;
+        }
+        const unsigned ball = __ballot_sync(kFull, lost);
+        if (ball) {
+            rest = (int)((c0 + __ffs(ball) - 1) * rows / C);
             break;
         }
     }
@@ -525,10 +692,34 @@ __device__ __forceinline__ int row_of(const long long *__restrict__ nptr, int n,
 // jhi = all) a unit with more than kLight estimated work is queued in chunks
 // instead.  D is the per-row allowance for exclusive neighbours (mean degree
 // + 1).
-template <int K>
+template <int K, bool COUNT>
 __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, const Scratch &sc, uint32_t unit,
                              int v, int vglob, int jlo, int jhi, bool phase1, long long D, int lane) {
     using L = Layout<K>;
+    if (K == 3 && COUNT) {
+        // prefix {v}; E = neighbours of v above v; rows chunked uniformly
+        const int dv = g.deg[v], l = g.lo[v];
+        const int B = dv - l;
+        if (B <= 0) return;
+        int hi = min(jhi, B), rest = B;
+        if (phase1 && (long long)B * D + 64 > kLight) {
+            rest = queue_uniform(a, unit, vglob, B, ((long long)B * D + 64 + kTarget - 1) / kTarget, lane);
+            if (rest >= B) return;
+            hi = 0;
+        }
+        uint32_t *E = B <= sc.cap ? sc.buf[0] : sc.ovf[0];
+        const long long rb = g.nptr[v] + l;
+        for (int q = lane; q < B; q += kWarp) {
+            const uint32_t xe = __ldg(g.nbr + rb + q);
+            E[q] = ((xe >> 2) << 6) | (xe & 3u);
+        }
+        __syncwarp();
+        const uint32_t pm[1] = {(uint32_t)v};
+        if (hi > jlo) count_leaves<K>(g, sink, E, B, jlo, hi, jlo == 0, pm, 0u, (uint32_t)v, sc.vmap, sc.gcnt, lane);
+        if (rest < B) count_leaves<K>(g, sink, E, B, rest, B, rest == 0, pm, 0u, (uint32_t)v, sc.vmap, sc.gcnt, lane);
+        __syncwarp();
+        return;
+    }
     if (K == 3) {
         // prefix {v}; E = neighbours of v above v
         const int dv = g.deg[v], l = g.lo[v];
@@ -561,6 +752,31 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
     const uint32_t e = __ldg(g.nbr + unit);
     const uint32_t w1 = e >> 2, s01 = e & 3u;
     int hi = jhi, rest = 0x7FFFFFFF;
+    if (K == 4 && COUNT) {
+        if (phase1) {
+            long long Bu = (long long)(g.deg[v] - t - 1) + g.deg[w1];
+            if (Bu > g.n - 2) Bu = g.n - 2;
+            if (Bu <= 0) return;
+            if (Bu * D + 64 > kLight) {
+                rest = queue_uniform(a, unit, vglob, Bu, (Bu * D + 64 + kTarget - 1) / kTarget, lane);
+                if (rest >= Bu) return;
+                hi = 0;
+            }
+        }
+        uint32_t *E2;
+        const int B2 = build_level2(g, unit, v, w1, sc, &E2, lane);
+        if (B2 <= 0) return;
+        hi = min(hi, B2);
+        rest = min(rest, B2);
+        const uint32_t pm[2] = {(uint32_t)v, w1};
+        const uint32_t pcode = s01 << (L::SH_ROW + 4);
+        if (hi > jlo)
+            count_leaves<K>(g, sink, E2, B2, jlo, hi, jlo == 0, pm, pcode, (uint32_t)v, sc.vmap, sc.gcnt, lane);
+        if (rest < B2)
+            count_leaves<K>(g, sink, E2, B2, rest, B2, rest == 0, pm, pcode, (uint32_t)v, sc.vmap, sc.gcnt, lane);
+        __syncwarp();
+        return;
+    }
     if (K == 4 && phase1) {
         long long Bu = (long long)(g.deg[v] - t - 1) + g.deg[w1];
         if (Bu > g.n - 2) Bu = g.n - 2;
@@ -594,7 +810,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
     if (phase1) {
         auto work = [&](int j) {
             const long long b = (long long)(B2 - 1 - j) + g.deg[e_id(E2[j])];
-            return b * (b - 1) / 2 + b * D + 1;
+            return COUNT ? b * (D + 1) + 64 : b * (b - 1) / 2 + b * D + 1;
         };
         if (total_work(B2, work, lane) > kLight) {
             rest = queue_rows(a, unit, vglob, B2, work, lane);
@@ -637,7 +853,8 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
             }
             __syncwarp();
             const uint32_t pm[3] = {(uint32_t)v, w1, w2};
-            leaves<K>(g, sink, E3, pos, 0, (pos + 1) / 2, pm, pcode, (uint32_t)v, lane);
+            if (COUNT) count_leaves<K>(g, sink, E3, pos, 0, pos, true, pm, pcode, (uint32_t)v, sc.vmap, sc.gcnt, lane);
+            else leaves<K>(g, sink, E3, pos, 0, (pos + 1) / 2, pm, pcode, (uint32_t)v, lane);
             __syncwarp();
         }
         if (rest >= B2) break;
@@ -646,7 +863,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
     __syncwarp();
 }
 
-template <int K>
+template <int K, bool COUNT>
 __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : ACC_MINB34) k_enum(EnumArgs a, int phase) {
     using L = Layout<K>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -654,6 +871,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : ACC_MINB34) k_enum(Enum
     uint32_t *pending = reinterpret_cast<uint32_t *>(smem + L::lut);
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem + L::lut + L::pending);
     uint32_t *ebuf = reinterpret_cast<uint32_t *>(smem + L::lut + L::pending + L::hist);
+    uint32_t *groups = reinterpret_cast<uint32_t *>(smem + L::lut + L::pending + L::hist + L::ebuf);
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     const bool several = a.gs.B > 1;
 
@@ -684,6 +902,9 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : ACC_MINB34) k_enum(Enum
     sc.ovf[0] = a.scratch + gw * a.scratch_per_warp;
     sc.ovf[1] = sc.ovf[0] + a.scratch_per_warp / 2;
     sc.cap = L::CAP;
+    sc.vmap = a.vmap + gw * a.vmap_per_warp;
+    sc.gcnt = groups + (size_t)wib * 3 * 64;
+    sink.moved = 0;
     const long long nnz = a.info->nnz;
     const long long NV = a.gs.NV;
     const long long D = (NV > 0 ? nnz / NV : 0) + 1;
@@ -706,8 +927,8 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : ACC_MINB34) k_enum(Enum
                 const int gi = a.gs.graph_of(vg);
                 const GMeta mt = a.gs.meta(gi);
                 sink.switch_graph(gi, lane);
-                process_unit<K>(a, view_of(a, mt), sink, sc, (uint32_t)u, vg - mt.voff, vg, 0, 0x7FFFFFFF, true, D,
-                                lane);
+                process_unit<K, COUNT>(a, view_of(a, mt), sink, sc, (uint32_t)u, vg - mt.voff, vg, 0, 0x7FFFFFFF,
+                                       true, D, lane);
             }
         }
     } else {
@@ -722,8 +943,8 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : ACC_MINB34) k_enum(Enum
             const int gi = a.gs.graph_of(vg);
             const GMeta mt = a.gs.meta(gi);
             sink.switch_graph(gi, lane);
-            process_unit<K>(a, view_of(a, mt), sink, sc, it.x, vg - mt.voff, vg, (int)it.y, (int)it.z, false, D,
-                            lane);
+            process_unit<K, COUNT>(a, view_of(a, mt), sink, sc, it.x, vg - mt.voff, vg, (int)it.y, (int)it.z,
+                                   false, D, lane);
         }
     }
 
@@ -733,63 +954,75 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : ACC_MINB34) k_enum(Enum
         // (k = 5 with several graphs counted straight into int64)
         if (K <= 4 && sink.gcur >= 0) {
             for (int c = lane; c < L::NCLS; c += kWarp) {
-                const uint32_t v = sink.hist[c];
-                if (v) atomicAdd(&sink.counts[c], (unsigned long long)v);
+                const int32_t v = (int32_t)sink.hist[c];
+                if (v) atomicAdd(&sink.counts[c], (unsigned long long)(long long)v);
             }
         }
     } else if (K == 5) {
         for (int c = tid; c < L::NCLS; c += blockDim.x) {
-            const uint32_t v = hist[c];
-            if (v) atomicAdd(&a.counts[c], (unsigned long long)v);
+            const int32_t v = (int32_t)hist[c];
+            if (v) atomicAdd(&a.counts[c], (unsigned long long)(long long)v);
         }
     } else {
         for (int c = tid; c < L::NCLS; c += blockDim.x) {
-            unsigned long long s = 0;
-            for (int w = 0; w < kWarpsPerBlock; w++) s += hist[w * L::NCLS + c];
-            if (s) atomicAdd(&a.counts[c], s);
+            long long s = 0;
+            for (int w = 0; w < kWarpsPerBlock; w++) s += (int32_t)hist[w * L::NCLS + c];
+            if (s) atomicAdd(&a.counts[c], (unsigned long long)s);
         }
     }
 }
 
-template <int K>
+template <int K, bool COUNT>
 int blocks_per_sm() {
     static int cached = 0;
     if (cached) return cached;
-    if (cudaFuncSetAttribute(k_enum<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<K>::total) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(k_enum<K, COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Layout<K>::total) != cudaSuccess)
         return -1;
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_enum<K>, kThreads, Layout<K>::total) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_enum<K, COUNT>, kThreads, Layout<K>::total) !=
+            cudaSuccess ||
         b < 1)
         return -1;
     cached = b;
     return b;
 }
 
-template <int K>
+template <int K, bool COUNT>
 int launch_k(const EnumArgs &a, int num_sms, int phase, cudaStream_t s, int grid_num, int grid_den) {
-    const int bps = blocks_per_sm<K>();
+    const int bps = blocks_per_sm<K, COUNT>();
     if (bps < 1) return ACC_ERR_CUDA;
     int grid = (int)((long long)num_sms * bps * grid_num / grid_den);
     if (grid < num_sms) grid = num_sms;
     if (grid > num_sms * bps) grid = num_sms * bps;
-    k_enum<K><<<grid, kThreads, Layout<K>::total, s>>>(a, phase);
+    k_enum<K, COUNT><<<grid, kThreads, Layout<K>::total, s>>>(a, phase);
     return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
+}
+
+template <int K>
+int bps_max() {
+    const int a = blocks_per_sm<K, false>(), b = blocks_per_sm<K, true>();
+    if (a < 1 || b < 1) return -1;
+    return a > b ? a : b;
 }
 
 }  // namespace
 
 int enum_grid_warps(int k, int num_sms) {
-    int bps = k == 3 ? blocks_per_sm<3>() : (k == 4 ? blocks_per_sm<4>() : blocks_per_sm<5>());
+    const int bps = k == 3 ? bps_max<3>() : (k == 4 ? bps_max<4>() : bps_max<5>());
     if (bps < 1) return ACC_ERR_CUDA;
     return num_sms * bps * kWarpsPerBlock;
 }
 
 int launch_enumerate(int k, const EnumArgs &a, int num_sms, int phase, cudaStream_t s, int grid_num, int grid_den) {
+    const bool c = a.mode == 0;
     switch (k) {
-    case 3: return launch_k<3>(a, num_sms, phase, s, grid_num, grid_den);
-    case 4: return launch_k<4>(a, num_sms, phase, s, grid_num, grid_den);
-    case 5: return launch_k<5>(a, num_sms, phase, s, grid_num, grid_den);
+    case 3: return c ? launch_k<3, true>(a, num_sms, phase, s, grid_num, grid_den)
+                     : launch_k<3, false>(a, num_sms, phase, s, grid_num, grid_den);
+    case 4: return c ? launch_k<4, true>(a, num_sms, phase, s, grid_num, grid_den)
+                     : launch_k<4, false>(a, num_sms, phase, s, grid_num, grid_den);
+    case 5: return c ? launch_k<5, true>(a, num_sms, phase, s, grid_num, grid_den)
+                     : launch_k<5, false>(a, num_sms, phase, s, grid_num, grid_den);
     default: return ACC_ERR_K;
     }
 }

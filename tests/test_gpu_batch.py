@@ -16,13 +16,14 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
-@pytest.fixture(scope="module")
-def counter():
+@pytest.fixture(scope="module", params=[0, 1], ids=["count_mode", "enumerate_mode"])
+def counter(request):
     import torch  # noqa: F401
     from paper_1203_3415_gb300 import build
     build.build()
     import paper_1203_3415_gb300 as p
     c = p.Counter(0)
+    c.set_mode(request.param)
     yield c
     c.close()
 
