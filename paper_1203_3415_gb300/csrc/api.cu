@@ -129,19 +129,6 @@ int ensure_workspace(acc_ctx *c, long long NV, long long state_words, long long 
     const int warps = enum_grid_warps(k, c->num_sms);
     if (warps < 0) return warps;
     if ((rc = grow(&c->scratch, &c->scratch_cap, (size_t)scratch_per_warp(max_n) * (size_t)warps))) return rc;
-    // member marks: one byte per vertex per warp, zero between lists (the
-    // kernels clear what they mark), so zeroed once when (re)allocated
-    const long long per_warp = ((long long)max_n + 64 + 15) & ~15LL;
-    const size_t need = (size_t)per_warp * (size_t)warps;
-    if (need > c->vmap_cap || !c->vmap) {
-        if ((rc = grow(&c->vmap, &c->vmap_cap, need))) return rc;
-        if (!ok(cudaMemset(c->vmap, 0, c->vmap_cap))) return ACC_ERR_CUDA;
-        c->vmap_per_warp = per_warp;
-    } else if (per_warp > c->vmap_per_warp) {
-        // same allocation, wider rows: zero again under the new layout
-        if (!ok(cudaMemset(c->vmap, 0, c->vmap_cap))) return ACC_ERR_CUDA;
-        c->vmap_per_warp = per_warp;
-    }
     return ACC_OK;
 }
 
@@ -171,8 +158,6 @@ int run_set(acc_ctx *c, const GSet &gs, long long state_words, int max_n, int k,
     a.queue_cap = c->queue_cap;
     a.scratch = c->scratch;
     a.scratch_per_warp = scratch_per_warp(max_n);
-    a.vmap = c->vmap;
-    a.vmap_per_warp = c->vmap_per_warp;
     a.mode = c->mode;
     a.counts = reinterpret_cast<unsigned long long *>(counts);
     a.status = status;
@@ -240,8 +225,7 @@ long long ctx_footprint(const acc_ctx *c, long long n, long long m, int k) {
     const long long pitch = state_pitch((int)n);
     const long long warps = enum_grid_warps(k, c->num_sms);
     const long long bytes = n * pitch * 4 + 4 * 4 * (n + 1) + 8 * (n + 1) + 4 * (2 * m + 1) +
-                            (long long)kQueueCap * 16 + scratch_per_warp((int)n) * (warps > 0 ? warps : 0) * 4 +
-                            (n + 80) * (warps > 0 ? warps : 0);
+                            (long long)kQueueCap * 16 + scratch_per_warp((int)n) * (warps > 0 ? warps : 0) * 4;
     return bytes + bytes / 4;
 }
 
@@ -315,7 +299,6 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaFree(c->info);
     cudaFree(c->queue);
     cudaFree(c->scratch);
-    cudaFree(c->vmap);
     cudaFree(c->status_dev);
     cudaFree(c->meta_dev);
     cudaFree(c->gid);

@@ -135,8 +135,6 @@ struct EnumArgs {
     unsigned long long queue_cap;
     uint32_t *scratch;          // per-warp overflow buffers for the extension sets
     long long scratch_per_warp; // entries per warp
-    uint8_t *vmap;              // count mode: per-warp member marks (all zero between lists)
-    long long vmap_per_warp;    // bytes per warp (>= largest graph)
     int mode;                   // 0: count the last two levels by groups, 1: enumerate every leaf
     unsigned long long *counts; // int64[B * num_classes]
     int *status;

@@ -37,9 +37,6 @@ struct acc_ctx {
     unsigned long long queue_cap = 0;
     uint32_t *scratch = nullptr;
     size_t scratch_cap = 0;
-    uint8_t *vmap = nullptr;  // count mode member marks, zero between lists
-    size_t vmap_cap = 0;
-    long long vmap_per_warp = 0;
     int mode = 0;             // ACC_MODE_COUNT or ACC_MODE_ENUMERATE
     int *status_dev = nullptr;
     int *status_host = nullptr;  // pinned

@@ -60,6 +60,9 @@ namespace {
 #ifndef ACC_HIST_MATCH
 #define ACC_HIST_MATCH 0  // 1: warp-aggregate increments with __match_any_sync
 #endif
+#ifndef ACC_CUNROLL
+#define ACC_CUNROLL 2  // count mode: neighbour entries in flight per lane
+#endif
 #ifndef ACC_MINB34
 #define ACC_MINB34 4  // resident blocks per SM the k = 3, 4 kernels are compiled for
 #endif
@@ -68,6 +71,7 @@ constexpr int kCap5 = 512;                // per-warp shared entries per list, k
 constexpr int kGrab = ACC_GRAB;           // base units per atomic grab
 constexpr long long kLight = ACC_LIGHT;   // phase 1 runs units up to this much work
 constexpr long long kTarget = ACC_TARGET; // work per queued chunk
+constexpr long long kRowCost = 4;         // count mode: fixed work of one list row
 constexpr uint32_t kDrainAt = 1u << 30;
 
 template <int K>
@@ -314,7 +318,6 @@ struct Scratch {
     uint32_t *buf[2];  // shared-memory lists (buf[1] only for k = 5)
     uint32_t *ovf[2];  // global overflow lists of this warp
     int cap;
-    uint8_t *vmap;     // count mode: this warp's member marks, one byte per vertex
     uint32_t *gcnt;    // count mode: group sizes and the non-empty group list
 };
 
@@ -418,6 +421,31 @@ __device__ __forceinline__ void leaves(const GView &g, Sink<K> &sink, const uint
     }
 }
 
+// Whether u (above the root; s[i] = state(p_i, u) to the prefix vertices
+// p_0 = v, p_1 = w1, p_2 = w2) is in the prefix's extension list.  ESU builds
+// every list from adjacency and vertex order alone: level 1 is N(v) above v;
+// level 2 is N(v) above w1 (part A, ascending) then the neighbours of w1 above
+// v not adjacent to v (part B, ascending); level 3 is level 2's list after w2
+// then the neighbours of w2 above v adjacent to neither v nor w1.  So the
+// states the exclusivity test reads decide membership too, and u's state
+// vector (its group in the list) is those same states.  Prefix vertices
+// never pass: each is adjacent to an earlier one and not above it.
+template <int K>
+__device__ __forceinline__ bool in_list(const uint32_t *s, uint32_t u, const uint32_t *pm, bool w2_in_a) {
+    if constexpr (K == 3) {
+        return s[0] != 0u;
+    } else {
+        const bool a = s[0] != 0u && u > pm[1];
+        const bool b = s[0] == 0u && s[1] != 0u;
+        if constexpr (K == 4) {
+            return a || b;
+        } else {
+            const bool after = w2_in_a ? ((a && u > pm[2]) || b) : (b && u > pm[2]);
+            return after || (s[0] == 0u && s[1] == 0u && s[2] != 0u);
+        }
+    }
+}
+
 // Count mode for the last two ESU levels over E[0..B), rows [jlo, jend).
 // The class of a pair leaf P + {x, y} with x, y not adjacent depends only on
 // the two state vectors (states to the prefix), so all such pairs are counted
@@ -426,25 +454,20 @@ __device__ __forceinline__ void leaves(const GView &g, Sink<K> &sink, const uint
 // Adjacent pairs are then moved to their own classes one by one, found in
 // the neighbour lists of the list members (the paper's m / m' corrections),
 // and the same scan yields the exclusive leaves P + {x, u}.  `bulk` (set for
-// exactly one chunk of a list) adds the group-pair counts.  vmap marks the
-// list members (state vector + 1) and is all zero again on return.
+// exactly one chunk of a list) adds the group-pair counts.  w2_in_a (k = 5)
+// says whether w2 lies in part A of the level-2 list.
 template <int K>
 __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, const uint32_t *E, int B, int jlo,
                                              int jend, bool bulk, const uint32_t *pm, uint32_t pcode,
-                                             uint32_t root, uint8_t *vmap, uint32_t *gcnt, int lane) {
+                                             uint32_t root, bool w2_in_a, uint32_t *gcnt, int lane) {
     using L = Layout<K>;
-    uint32_t *glist = gcnt + 64;  // (group << 16 | 0) packed as value, count pairs
-    if (bulk)
-        for (int i = lane; i < L::G; i += kWarp) gcnt[i] = 0;
-    __syncwarp();
-    for (int q = lane; q < B; q += kWarp) {
-        const uint32_t e = E[q];
-        vmap[e_id(e)] = (uint8_t)(e_sv(e) + 1u);
-        if (bulk) atomicAdd(&gcnt[e_sv(e)], 1u);
-    }
-    __syncwarp();
+    constexpr int U = ACC_CUNROLL;
     if (bulk) {
-        // the non-empty groups, compacted
+        uint32_t *glist = gcnt + 64;  // (group, count) pairs of the non-empty groups
+        for (int i = lane; i < L::G; i += kWarp) gcnt[i] = 0;
+        __syncwarp();
+        for (int q = lane; q < B; q += kWarp) atomicAdd(&gcnt[e_sv(E[q])], 1u);
+        __syncwarp();
         int ng = 0;
         for (int b0 = 0; b0 < L::G; b0 += kWarp) {
             const int gi = b0 + lane;
@@ -490,41 +513,44 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
         const uint32_t cj = pcode | (e_sv(ej) << L::SH_ROW);
         const uint32_t xj = e_id(ej);
         const uint32_t off = first - (uint32_t)pre;
-        for (int t0 = 0; t0 < tot; t0 += kWarp) {
-            const int t = t0 + lane;
-            const int r = lb_search(pre, t);
-            const uint32_t cr = __shfl_sync(kFull, cj, r);
-            const uint32_t orow = __shfl_sync(kFull, off, r);
-            const uint32_t xr = __shfl_sync(kFull, xj, r);
-            if (t < tot) {
-                const uint32_t ue = __ldg(g.nbr + (orow + (uint32_t)t));
-                const uint32_t u = ue >> 2, su = ue & 3u;
-                const uint32_t mu = vmap[u];
-                if (mu) {
-                    if (u > xr) {
-                        const uint32_t base = cr | (mu - 1u);
-                        sink.add(sink.cls_of(base | (su << L::SH_PAIR)), 1);
-                        sink.add(sink.cls_of(base), -1);
-                    }
-                } else {
-                    bool excl = true;
+        for (int t0 = 0; t0 < tot; t0 += kWarp * U) {
+            uint32_t ue[U], cr[U], xr[U];
 #pragma unroll
-                    for (int k2 = 0; k2 < K - 2; k2++) excl = excl && probe(g.state, g.pitch, pm[k2], u) == 0u;
-                    if (excl) sink.add(sink.cls_of(cr | (su << L::SH_PAIR)), 1);
+            for (int i = 0; i < U; i++) {
+                const int t = t0 + i * kWarp + lane;
+                const int r = lb_search(pre, t);
+                cr[i] = __shfl_sync(kFull, cj, r);
+                const uint32_t orow = __shfl_sync(kFull, off, r);
+                xr[i] = __shfl_sync(kFull, xj, r);
+                ue[i] = t < tot ? __ldg(g.nbr + (orow + (uint32_t)t)) : 0xFFFFFFFFu;
+            }
+            uint32_t sv[U][K - 2];
+#pragma unroll
+            for (int i = 0; i < U; i++)
+#pragma unroll
+                for (int k2 = 0; k2 < K - 2; k2++)
+                    sv[i][k2] = ue[i] != 0xFFFFFFFFu ? probe(g.state, g.pitch, pm[k2], ue[i] >> 2) : 0u;
+#pragma unroll
+            for (int i = 0; i < U; i++) {
+                if (ue[i] == 0xFFFFFFFFu) continue;
+                const uint32_t u = ue[i] >> 2, su = ue[i] & 3u;
+                uint32_t mu = 0;
+#pragma unroll
+                for (int k2 = 0; k2 < K - 2; k2++) mu |= sv[i][k2] << (2 * k2);
+                if (mu == 0u) {
+                    sink.add(sink.cls_of(cr[i] | (su << L::SH_PAIR)), 1);  // exclusive leaf
+                } else if (u > xr[i] && in_list<K>(sv[i], u, pm, w2_in_a)) {
+                    const uint32_t base = cr[i] | mu;
+                    sink.add(sink.cls_of(base | (su << L::SH_PAIR)), 1);
+                    sink.add(sink.cls_of(base), -1);
                 }
             }
         }
         account_moved(sink, lane);
     }
     __syncwarp();
-    for (int q = lane; q < B; q += kWarp) vmap[e_id(E[q])] = 0;
-    __syncwarp();
 }
 
-// Extension list of the prefix {v, w1} for k >= 4 (unit = arc position p in
-// row v, w1 = N*(v)[p - nptr[v]] > v): N*(v) after w1, then the exclusive
-// neighbours of w1 (above v, not adjacent to v).  Entry states:
-// state(v, x) | state(w1, x) << 2.  Returns B.
 __device__ __forceinline__ int build_level2(const GView &a, long long p, int v, uint32_t w1, const Scratch &sc,
                                             uint32_t **E_out, int lane) {
     const long long rb = a.nptr[v];
@@ -697,16 +723,11 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
                              int v, int vglob, int jlo, int jhi, bool phase1, long long D, int lane) {
     using L = Layout<K>;
     if (K == 3 && COUNT) {
-        // prefix {v}; E = neighbours of v above v; rows chunked uniformly
+        // prefix {v}; E = neighbours of v above v; a heavy list is queued as
+        // row ranges of equal scan work (the rows' neighbour counts)
         const int dv = g.deg[v], l = g.lo[v];
         const int B = dv - l;
         if (B <= 0) return;
-        int hi = min(jhi, B), rest = B;
-        if (phase1 && (long long)B * D + 64 > kLight) {
-            rest = queue_uniform(a, unit, vglob, B, ((long long)B * D + 64 + kTarget - 1) / kTarget, lane);
-            if (rest >= B) return;
-            hi = 0;
-        }
         uint32_t *E = B <= sc.cap ? sc.buf[0] : sc.ovf[0];
         const long long rb = g.nptr[v] + l;
         for (int q = lane; q < B; q += kWarp) {
@@ -714,9 +735,18 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
             E[q] = ((xe >> 2) << 6) | (xe & 3u);
         }
         __syncwarp();
+        int hi = min(jhi, B), rest = B;
+        if (phase1) {
+            auto work = [&](int j) { return (long long)g.deg[e_id(E[j])] + kRowCost; };
+            if (total_work(B, work, lane) > kLight) {
+                rest = queue_rows(a, unit, vglob, B, work, lane);
+                if (rest >= B) return;
+                hi = 0;
+            }
+        }
         const uint32_t pm[1] = {(uint32_t)v};
-        if (hi > jlo) count_leaves<K>(g, sink, E, B, jlo, hi, jlo == 0, pm, 0u, (uint32_t)v, sc.vmap, sc.gcnt, lane);
-        if (rest < B) count_leaves<K>(g, sink, E, B, rest, B, rest == 0, pm, 0u, (uint32_t)v, sc.vmap, sc.gcnt, lane);
+        if (hi > jlo) count_leaves<K>(g, sink, E, B, jlo, hi, jlo == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, lane);
+        if (rest < B) count_leaves<K>(g, sink, E, B, rest, B, rest == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, lane);
         __syncwarp();
         return;
     }
@@ -753,27 +783,25 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
     const uint32_t w1 = e >> 2, s01 = e & 3u;
     int hi = jhi, rest = 0x7FFFFFFF;
     if (K == 4 && COUNT) {
-        if (phase1) {
-            long long Bu = (long long)(g.deg[v] - t - 1) + g.deg[w1];
-            if (Bu > g.n - 2) Bu = g.n - 2;
-            if (Bu <= 0) return;
-            if (Bu * D + 64 > kLight) {
-                rest = queue_uniform(a, unit, vglob, Bu, (Bu * D + 64 + kTarget - 1) / kTarget, lane);
-                if (rest >= Bu) return;
-                hi = 0;
-            }
-        }
         uint32_t *E2;
         const int B2 = build_level2(g, unit, v, w1, sc, &E2, lane);
         if (B2 <= 0) return;
         hi = min(hi, B2);
-        rest = min(rest, B2);
+        rest = B2;
+        if (phase1) {
+            auto work = [&](int j) { return (long long)g.deg[e_id(E2[j])] + kRowCost; };
+            if (total_work(B2, work, lane) > kLight) {
+                rest = queue_rows(a, unit, vglob, B2, work, lane);
+                if (rest >= B2) return;
+                hi = 0;
+            }
+        }
         const uint32_t pm[2] = {(uint32_t)v, w1};
         const uint32_t pcode = s01 << (L::SH_ROW + 4);
         if (hi > jlo)
-            count_leaves<K>(g, sink, E2, B2, jlo, hi, jlo == 0, pm, pcode, (uint32_t)v, sc.vmap, sc.gcnt, lane);
+            count_leaves<K>(g, sink, E2, B2, jlo, hi, jlo == 0, pm, pcode, (uint32_t)v, false, sc.gcnt, lane);
         if (rest < B2)
-            count_leaves<K>(g, sink, E2, B2, rest, B2, rest == 0, pm, pcode, (uint32_t)v, sc.vmap, sc.gcnt, lane);
+            count_leaves<K>(g, sink, E2, B2, rest, B2, rest == 0, pm, pcode, (uint32_t)v, false, sc.gcnt, lane);
         __syncwarp();
         return;
     }
@@ -853,7 +881,9 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
             }
             __syncwarp();
             const uint32_t pm[3] = {(uint32_t)v, w1, w2};
-            if (COUNT) count_leaves<K>(g, sink, E3, pos, 0, pos, true, pm, pcode, (uint32_t)v, sc.vmap, sc.gcnt, lane);
+            if (COUNT)
+                count_leaves<K>(g, sink, E3, pos, 0, pos, true, pm, pcode, (uint32_t)v, (e2 & 3u) != 0u, sc.gcnt,
+                                lane);
             else leaves<K>(g, sink, E3, pos, 0, (pos + 1) / 2, pm, pcode, (uint32_t)v, lane);
             __syncwarp();
         }
@@ -902,7 +932,6 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : ACC_MINB34) k_enum(Enum
     sc.ovf[0] = a.scratch + gw * a.scratch_per_warp;
     sc.ovf[1] = sc.ovf[0] + a.scratch_per_warp / 2;
     sc.cap = L::CAP;
-    sc.vmap = a.vmap + gw * a.vmap_per_warp;
     sc.gcnt = groups + (size_t)wib * 3 * 64;
     sink.moved = 0;
     const long long nnz = a.info->nnz;
