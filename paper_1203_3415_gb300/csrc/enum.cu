@@ -64,7 +64,10 @@ namespace {
 #define ACC_CUNROLL 2  // count mode: neighbour entries in flight per lane
 #endif
 #ifndef ACC_MINB34
-#define ACC_MINB34 4  // resident blocks per SM the k = 3, 4 kernels are compiled for
+#define ACC_MINB34 4  // resident blocks per SM the k = 3, 4 leaf kernels are compiled for
+#endif
+#ifndef ACC_MINB34C
+#define ACC_MINB34C 3  // the same for the k = 3, 4 count-mode kernels
 #endif
 constexpr int kCap34 = ACC_CAP34;         // per-warp shared extension entries, k = 3, 4
 constexpr int kCap5 = 512;                // per-warp shared entries per list, k = 5
@@ -894,7 +897,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
 }
 
 template <int K, bool COUNT>
-__global__ void __launch_bounds__(kThreads, K == 5 ? 3 : ACC_MINB34) k_enum(EnumArgs a, int phase) {
+__global__ void __launch_bounds__(kThreads, K == 5 ? 3 : (COUNT ? ACC_MINB34C : ACC_MINB34)) k_enum(EnumArgs a, int phase) {
     using L = Layout<K>;
     extern __shared__ __align__(16) unsigned char smem[];
     int16_t *lut_s = reinterpret_cast<int16_t *>(smem);
