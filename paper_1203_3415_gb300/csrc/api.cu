@@ -97,20 +97,30 @@ long long scratch_per_warp(int max_n) { return 2 * (((long long)max_n + 32 + 31)
 // most `arcs` arcs and graphs of at most max_n vertices.
 int ensure_workspace(acc_ctx *c, long long NV, long long state_words, long long arcs, int max_n, int k) {
     int rc;
-    if ((rc = grow(&c->state, &c->state_cap, (size_t)state_words + 4))) return rc;
+    {
+        const uint32_t *before = c->state;
+        if ((rc = grow(&c->state, &c->state_cap, (size_t)state_words + 4))) {
+            c->state_clean = false;
+            return rc;
+        }
+        if (c->state != before) c->state_clean = false;  // fresh memory: swept by the next build
+    }
     if ((size_t)NV + 1 > c->n_cap || !c->deg) {
         size_t a = 0, b = 0, d = 0, e = 0;
         cudaFree(c->deg);
         cudaFree(c->lo);
         cudaFree(c->nptr);
         cudaFree(c->label);
-        c->deg = c->lo = c->label = nullptr;
+        cudaFree(c->deg_in);
+        c->deg = c->lo = c->label = c->deg_in = nullptr;
         c->nptr = nullptr;
         c->n_cap = 0;
         if ((rc = grow(&c->deg, &a, (size_t)NV + 1))) return rc;
         if ((rc = grow(&c->lo, &b, (size_t)NV + 1))) return rc;
         if ((rc = grow(&c->nptr, &d, (size_t)NV + 1))) return rc;
         if ((rc = grow(&c->label, &e, (size_t)NV + 1))) return rc;
+        e = 0;
+        if ((rc = grow(&c->deg_in, &e, (size_t)NV + 1))) return rc;
         c->n_cap = a;
     }
     if ((rc = grow(&c->tiles, &c->tiles_cap, (size_t)scan_tiles_needed(NV) + 1))) return rc;
@@ -133,13 +143,17 @@ int ensure_workspace(acc_ctx *c, long long NV, long long state_words, long long 
 }
 
 // Build + enumerate one graph set into counts[B * num_classes(k)].
-int run_set(acc_ctx *c, const GSet &gs, long long state_words, int max_n, int k, bool relabel, cudaStream_t s,
+int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStream_t s,
             int64_t *counts, int *status) {
     int launches = 0;
     c->timed_call = c->timing;
     if (c->timing && !ok(cudaEventRecord(c->ev[0], s))) return ACC_ERR_CUDA;
-    int rc = launch_build_graph(gs, state_words, c->state, c->deg, c->lo, c->nptr, c->tiles, c->nbr, c->label,
-                                c->info, status, reinterpret_cast<unsigned long long *>(counts),
+    const bool clean = c->state_clean;
+    c->state_clean = false;  // until the closing clear below is enqueued
+    // a buffer not known to be clean is swept whole (capacity, not just this
+    // set's blocks): a later, larger set may use any part of it
+    int rc = launch_build_graph(gs, (long long)c->state_cap, c->state, clean, c->deg, c->lo, c->deg_in, c->nptr, c->tiles, c->nbr,
+                                c->label, c->info, status, reinterpret_cast<unsigned long long *>(counts),
                                 (long long)gs.B * num_classes(k), relabel, c->num_sms, s);
     if (rc < 0) return rc;
     launches += rc;
@@ -174,6 +188,10 @@ int run_set(acc_ctx *c, const GSet &gs, long long state_words, int max_n, int k,
         launches += rc;
     }
     if (c->timing && !ok(cudaEventRecord(c->ev[2], s))) return ACC_ERR_CUDA;
+    rc = launch_clear_graph(gs, c->state, c->label, relabel, c->num_sms, s);
+    if (rc < 0) return rc;
+    launches += rc;
+    c->state_clean = true;
     c->last_launches = launches;
     c->last_k = k;
     c->last_units = gs.NV;
@@ -212,7 +230,7 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
     gs.B = 1;
     gs.NV = n;
     int *status = status_user ? status_user : c->status_dev;
-    rc = run_set(c, gs, (long long)n * pitch, n, k, n >= kRelabelMinN, s, counts, status);
+    rc = run_set(c, gs, n, k, n >= kRelabelMinN, s, counts, status);
     if (rc) return rc;
     return finish(c, s, status_user);
 }
@@ -224,7 +242,7 @@ namespace acc {
 long long ctx_footprint(const acc_ctx *c, long long n, long long m, int k) {
     const long long pitch = state_pitch((int)n);
     const long long warps = enum_grid_warps(k, c->num_sms);
-    const long long bytes = n * pitch * 4 + 4 * 4 * (n + 1) + 8 * (n + 1) + 4 * (2 * m + 1) +
+    const long long bytes = n * pitch * 4 + 5 * 4 * (n + 1) + 8 * (n + 1) + 4 * (2 * m + 1) +
                             (long long)kQueueCap * 16 + scratch_per_warp((int)n) * (warps > 0 ? warps : 0) * 4;
     return bytes + bytes / 4;
 }
@@ -294,6 +312,7 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaFree(c->lo);
     cudaFree(c->nptr);
     cudaFree(c->label);
+    cudaFree(c->deg_in);
     cudaFree(c->tiles);
     cudaFree(c->nbr);
     cudaFree(c->info);
@@ -414,7 +433,7 @@ int acc_motif_batch_run(acc_ctx *c, void *stream, int64_t *d_counts, int32_t *d_
     cudaStream_t s = (cudaStream_t)stream;
     if (c->batch_set.B == 0) return ACC_OK;
     int *status = d_status ? d_status : c->status_dev;
-    const int rc = run_set(c, c->batch_set, c->batch_words, c->batch_max_n, c->batch_k, true, s, d_counts, status);
+    const int rc = run_set(c, c->batch_set, c->batch_max_n, c->batch_k, true, s, d_counts, status);
     if (rc) return rc;
     return finish(c, s, d_status);
 }

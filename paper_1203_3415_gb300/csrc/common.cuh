@@ -103,9 +103,14 @@ __device__ inline void set_status(int *status, int err) {
 // descending G* degree (label[v] = new global id of input vertex v), which
 // leaves the counts unchanged.  tile_scratch holds scan_tiles_needed(NV)
 // values.
-int launch_build_graph(const GSet &gs, long long state_words, uint32_t *state, int *deg, int *lo, long long *nptr,
-                       long long *tile_scratch, uint32_t *nbr, int *label, GraphInfo *info, int *status,
-                       unsigned long long *counts, long long ncounts, bool relabel, int num_sms, cudaStream_t s);
+// state_words: the whole pair-state buffer, swept unless state_clean says it
+// is known to be all zero; deg_in: NV ints of scratch for the renumbering.
+int launch_build_graph(const GSet &gs, long long state_words, uint32_t *state, bool state_clean, int *deg, int *lo,
+                       int *deg_in, long long *nptr, long long *tile_scratch, uint32_t *nbr, int *label,
+                       GraphInfo *info, int *status, unsigned long long *counts, long long ncounts, bool relabel,
+                       int num_sms, cudaStream_t s);
+// Zero the pair-state words a build set, leaving the buffer all zero.
+int launch_clear_graph(const GSet &gs, uint32_t *state, const int *label, bool relabel, int num_sms, cudaStream_t s);
 long long scan_tiles_needed(long long NV);
 // gid[v] for a set of several graphs (no launch for one graph).
 int launch_graph_ids(const GSet &gs, int *gid, cudaStream_t s);

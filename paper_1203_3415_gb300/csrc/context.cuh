@@ -25,7 +25,8 @@ struct acc_ctx {
     // workspace (grow-only)
     uint32_t *state = nullptr;
     size_t state_cap = 0;
-    int *deg = nullptr, *lo = nullptr, *label = nullptr;
+    bool state_clean = false;  // every pair-state word is zero (each call clears what it set)
+    int *deg = nullptr, *lo = nullptr, *label = nullptr, *deg_in = nullptr;
     long long *nptr = nullptr;
     size_t n_cap = 0;
     long long *tiles = nullptr;

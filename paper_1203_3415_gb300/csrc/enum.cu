@@ -70,7 +70,7 @@ namespace {
 #define ACC_MINB34C 3  // the same for the k = 3, 4 count-mode kernels
 #endif
 constexpr int kCap34 = ACC_CAP34;         // per-warp shared extension entries, k = 3, 4
-constexpr int kCap5 = 512;                // per-warp shared entries per list, k = 5
+constexpr int kCap5 = 384;                // per-warp shared entries per list, k = 5
 constexpr int kGrab = ACC_GRAB;           // base units per atomic grab
 constexpr long long kLight = ACC_LIGHT;   // phase 1 runs units up to this much work
 constexpr long long kTarget = ACC_TARGET; // work per queued chunk
@@ -91,7 +91,7 @@ struct Layout {
     static constexpr size_t hist = (K == 5 ? size_t(NCLS) * 4 : size_t(kWarpsPerBlock) * NCLS * 4 + 15) & ~size_t(15);
     static constexpr size_t ebuf = size_t(kWarpsPerBlock) * LISTS * CAP * 4;
     static constexpr int G = 1 << (2 * (K - 2));  // state vectors to the prefix: 4, 16, 64
-    static constexpr size_t groups = size_t(kWarpsPerBlock) * 3 * 64 * 4;  // count mode: sizes + list
+    static constexpr size_t groups = size_t(kWarpsPerBlock) * 3 * G * 4;  // count mode: sizes + list
     static constexpr size_t total = lut + pending + hist + ebuf + groups;
 };
 
@@ -466,7 +466,7 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
     using L = Layout<K>;
     constexpr int U = ACC_CUNROLL;
     if (bulk) {
-        uint32_t *glist = gcnt + 64;  // (group, count) pairs of the non-empty groups
+        uint32_t *glist = gcnt + L::G;  // (group, count) pairs of the non-empty groups
         for (int i = lane; i < L::G; i += kWarp) gcnt[i] = 0;
         __syncwarp();
         for (int q = lane; q < B; q += kWarp) atomicAdd(&gcnt[e_sv(E[q])], 1u);
@@ -617,30 +617,6 @@ __device__ int queue_closed_form(const EnumArgs &a, uint32_t unit, int v, long l
         const unsigned ball = __ballot_sync(kFull, lost);
         if (ball) {
             rest = (int)((c0 + __ffs(ball) - 1) * Pu / C);
-            break;
-        }
-    }
-    return rest;
-}
-
-// Count mode: queue rows [0, rows) of a heavy unit as C chunks of equal row
-// counts.  Returns the first row the queue could not take (rows when all fit).
-__device__ int queue_uniform(const EnumArgs &a, uint32_t unit, int v, long long rows, long long C, int lane) {
-    if (C > rows) C = rows;
-    if (C < 1) C = 1;
-    const unsigned long long base = reserve(a, (unsigned long long)C, lane);
-    int rest = (int)rows;
-    for (long long c0 = 0; c0 < C; c0 += kWarp) {
-        const long long c = c0 + lane;
-        bool lost = false;
-        if (c < C) {
-            const uint32_t lo = (uint32_t)(c * rows / C), hi = (uint32_t)((c + 1) * rows / C);
-            if (base + c < a.queue_cap) a.queue[base + c] = make_uint4(unit, lo, hi, (uint32_t)v);
-            else lost = true;
-        }
-        const unsigned ball = __ballot_sync(kFull, lost);
-        if (ball) {
-            rest = (int)((c0 + __ffs(ball) - 1) * rows / C);
             break;
         }
     }
@@ -935,7 +911,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : (COUNT ? ACC_MINB34C : 
     sc.ovf[0] = a.scratch + gw * a.scratch_per_warp;
     sc.ovf[1] = sc.ovf[0] + a.scratch_per_warp / 2;
     sc.cap = L::CAP;
-    sc.gcnt = groups + (size_t)wib * 3 * 64;
+    sc.gcnt = groups + (size_t)wib * 3 * L::G;
     sink.moved = 0;
     const long long nnz = a.info->nnz;
     const long long NV = a.gs.NV;

@@ -12,6 +12,14 @@
 // Vertices of graph g occupy the global range [voff_g, voff_g + n_g); its
 // pair-state block starts at word soff_g.  deg, lo, label, nptr are indexed
 // by global vertex; neighbour entries and block rows/columns use local ids.
+//
+// The pair-state buffer is all zero between calls: a build sets only the
+// words its arcs touch and the call ends by clearing exactly those words
+// (k_clear_arcs), so no pass ever sweeps the whole n x n block.  G* degrees
+// come out of the ingest itself: of the atomics that touch the field of pair
+// {a, u} in row a (arc a -> u sets bit 0, arc u -> a sets bit 1 as its
+// mirror), exactly one finds the field still zero, and that one counts u as
+// a neighbour of a.  Repeated arcs therefore count once.
 #include "common.cuh"
 
 namespace acc {
@@ -29,22 +37,30 @@ __device__ __forceinline__ int warp_excl_scan(int x, int lane, int *total) {
     return incl - x;
 }
 
+struct IntRanges {
+    int *p[3];
+    long long n[3];
+};
+
 __global__ void k_zero(uint4 *p, size_t n16, unsigned char *tail, size_t ntail, int *status,
-                       unsigned long long *counts, long long ncounts, int *ints, long long nints) {
+                       unsigned long long *counts, long long ncounts, IntRanges ints) {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t j = i; j < n16; j += stride) p[j] = make_uint4(0, 0, 0, 0);
     if (i < ntail) tail[i] = 0;
     for (size_t j = i; j < (size_t)ncounts; j += stride) counts[j] = 0;
-    for (size_t j = i; j < (size_t)nints; j += stride) ints[j] = 0;
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+        for (size_t j = i; j < (size_t)ints.n[r]; j += stride) ints.p[r][j] = 0;
     if (i == 0 && status) *status = 0;
 }
 
 // Warp per global row: set the pair-state bits of every arc, validating the
 // CSR on the way.  Invalid rows and arcs are skipped (never read out of
 // range) and reported through *status.  With `label` non-null, vertex x is
-// written as label[x] (the renumbered block).
-__global__ void k_ingest(GSet gs, uint32_t *state, const int *__restrict__ label, int *status) {
+// written as label[x] (the renumbered block).  deg[voff + a] counts the G*
+// neighbours of block vertex a; lo (if non-null) those below a.
+__global__ void k_ingest(GSet gs, uint32_t *state, const int *__restrict__ label, int *status, int *deg, int *lo) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -67,50 +83,54 @@ __global__ void k_ingest(GSet gs, uint32_t *state, const int *__restrict__ label
                 continue;
             }
             const int u = label ? label[mt.voff + u0] - mt.voff : u0;
-            atomicOr(&blk[a * mt.pitch + (u >> 4)], 1u << ((u & 15) * 2));
-            atomicOr(&blk[(long long)u * mt.pitch + (a >> 4)], 2u << ((a & 15) * 2));
+            const int su = (u & 15) * 2, sa = (int)(a & 15) * 2;
+            const uint32_t oa = atomicOr(&blk[a * mt.pitch + (u >> 4)], 1u << su);
+            const uint32_t ou = atomicOr(&blk[(long long)u * mt.pitch + (a >> 4)], 2u << sa);
+            if (((oa >> su) & 3u) == 0u) {
+                atomicAdd(&deg[mt.voff + a], 1);
+                if (lo && u < a) atomicAdd(&lo[mt.voff + a], 1);
+            }
+            if (((ou >> sa) & 3u) == 0u) {
+                atomicAdd(&deg[mt.voff + u], 1);
+                if (lo && a < u) atomicAdd(&lo[mt.voff + u], 1);
+            }
         }
     }
 }
 
-// Warp per global row: degree of v in G*, neighbours below v, and (for the
-// renumbering) the per-graph degree histogram dhist[voff + degree].
-__global__ void k_degrees(GSet gs, const uint32_t *__restrict__ state, int *deg, int *lo, int *dhist) {
+// Warp per global row: zero the pair-state words the arcs of the row set
+// (the same rows and arcs k_ingest accepted, under the same labels), and
+// with zero_deg the degree counters of the row's vertex.
+__global__ void k_clear_arcs(GSet gs, uint32_t *state, const int *__restrict__ label, int *deg, int *lo) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long v = warp; v < gs.NV; v += nwarps) {
+        if (lane == 0 && deg) {
+            deg[v] = 0;
+            lo[v] = 0;
+        }
         const GMeta mt = gs.meta(gs.graph_of((int)v));
         const int lv = (int)v - mt.voff;
-        const int words = (mt.n + 15) >> 4;
-        const uint4 *row4 = reinterpret_cast<const uint4 *>(state + mt.soff + (long long)lv * mt.pitch);
-        const int vw = lv >> 4;
-        const uint32_t below_mask = (1u << ((lv & 15) * 2)) - 1u;
-        int cnt = 0, below = 0;
-        for (int w4 = lane; w4 * 4 < words; w4 += kWarp) {
-            uint4 q = row4[w4];
-            uint32_t ws[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int t = 0; t < 4; t++) {
-                const int w = w4 * 4 + t;
-                const uint32_t nz = (ws[t] | (ws[t] >> 1)) & 0x55555555u;
-                const int c = __popc(nz);
-                cnt += c;
-                if (w < vw) below += c;
-                else if (w == vw) below += __popc(nz & below_mask);
-            }
-        }
-#pragma unroll
-        for (int d = 16; d; d >>= 1) {
-            cnt += __shfl_xor_sync(kFull, cnt, d);
-            below += __shfl_xor_sync(kFull, below, d);
-        }
-        if (lane == 0) {
-            deg[v] = cnt;
-            if (lo) lo[v] = below;
-            if (dhist) atomicAdd(&dhist[mt.voff + cnt], 1);
+        const long long b = mt.rowptr[lv], e = mt.rowptr[lv + 1];
+        if (b < 0 || e < b || e > mt.m) continue;
+        const long long a = label ? label[v] - mt.voff : lv;
+        uint32_t *blk = state + mt.soff;
+        for (long long p = b + lane; p < e; p += kWarp) {
+            const int u0 = mt.col[p];
+            if (u0 < 0 || u0 >= mt.n || u0 == lv) continue;
+            const int u = label ? label[mt.voff + u0] - mt.voff : u0;
+            blk[a * mt.pitch + (u >> 4)] = 0u;
+            blk[(long long)u * mt.pitch + (a >> 4)] = 0u;
         }
     }
+}
+
+// Per-graph degree histogram dhist[voff + degree] (for the renumbering).
+__global__ void k_dhist(GSet gs, const int *__restrict__ deg, int *dhist) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < gs.NV;
+         v += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&dhist[gs.meta(gs.graph_of((int)v)).voff + deg[v]], 1);
 }
 
 // Block per graph: start[voff + d] = vertices of the graph with degree above d.
@@ -350,7 +370,8 @@ __global__ void k_scan_apply(const int *__restrict__ deg, int n, const long long
 }
 
 // Warp per global row: write the sorted neighbour entries (u << 2) | state(v, u)
-// with local u.
+// with local u.  Each lane reads 16 bytes (64 columns) per step; steps where
+// the whole warp's 2048 columns are empty are skipped after one ballot.
 __global__ void k_fill(GSet gs, const uint32_t *__restrict__ state, const long long *__restrict__ nptr,
                        uint32_t *nbr) {
     const int lane = threadIdx.x & 31;
@@ -359,21 +380,33 @@ __global__ void k_fill(GSet gs, const uint32_t *__restrict__ state, const long l
     for (long long v = warp; v < gs.NV; v += nwarps) {
         const GMeta mt = gs.meta(gs.graph_of((int)v));
         const int lv = (int)v - mt.voff;
-        const int words = (mt.n + 15) >> 4;
-        const uint32_t *row = state + mt.soff + (long long)lv * mt.pitch;
+        const int quads = (((mt.n + 15) >> 4) + 3) >> 2;  // within the pitch (a multiple of 4 words)
+        const uint4 *row4 = reinterpret_cast<const uint4 *>(state + mt.soff + (long long)lv * mt.pitch);
         long long base = nptr[v];
-        for (int w0 = 0; w0 < words; w0 += kWarp) {
-            const int w = w0 + lane;
-            const uint32_t x = w < words ? row[w] : 0u;
-            uint32_t nz = (x | (x >> 1)) & 0x55555555u;
+        for (int q0 = 0; q0 < quads; q0 += kWarp) {
+            const int q = q0 + lane;
+            const uint4 x4 = q < quads ? row4[q] : make_uint4(0, 0, 0, 0);
+            const uint32_t xs[4] = {x4.x, x4.y, x4.z, x4.w};
+            uint32_t nz[4];
+            int c = 0;
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                nz[t] = (xs[t] | (xs[t] >> 1)) & 0x55555555u;
+                c += __popc(nz[t]);
+            }
+            if (!__ballot_sync(kFull, c != 0)) continue;
             int total;
-            const int off = warp_excl_scan(__popc(nz), lane, &total);
+            const int off = warp_excl_scan(c, lane, &total);
             long long pos = base + off;
-            while (nz) {
-                const int bit = __ffs(nz) - 1;
-                const uint32_t u = (uint32_t)(w * 16 + (bit >> 1));
-                nbr[pos++] = (u << 2) | ((x >> bit) & 3u);
-                nz &= nz - 1;
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                uint32_t m = nz[t];
+                while (m) {
+                    const int bit = __ffs(m) - 1;
+                    const uint32_t u = (uint32_t)((q * 4 + t) * 16 + (bit >> 1));
+                    nbr[pos++] = (u << 2) | ((xs[t] >> bit) & 3u);
+                    m &= m - 1;
+                }
             }
             base += total;
         }
@@ -400,11 +433,11 @@ int grid_for(long long work_items, int per_block, int num_sms) {
 
 int launch_zero(void *p, size_t bytes, int num_sms, cudaStream_t s, int *status, unsigned long long *counts,
                 long long ncounts, int *ints, long long nints) {
+    IntRanges r = {{ints, nullptr, nullptr}, {ints ? nints : 0, 0, 0}};
     const size_t n16 = bytes / 16, ntail = bytes % 16;
     const int grid = grid_for((long long)(n16 > 0 ? n16 : 1), 256 * 4, num_sms);
     k_zero<<<grid, 256, 0, s>>>(reinterpret_cast<uint4 *>(p), n16,
-                                reinterpret_cast<unsigned char *>(p) + n16 * 16, ntail, status, counts, ncounts,
-                                ints, nints);
+                                reinterpret_cast<unsigned char *>(p) + n16 * 16, ntail, status, counts, ncounts, r);
     return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
 
@@ -416,38 +449,41 @@ int launch_graph_ids(const GSet &gs, int *gid, cudaStream_t s) {
 
 long long scan_tiles_needed(long long NV) { return NV <= kScanSingleMax ? 0 : (NV + kScanTile - 1) / kScanTile; }
 
-int launch_build_graph(const GSet &gs, long long state_words, uint32_t *state, int *deg, int *lo, long long *nptr,
-                       long long *tile_scratch, uint32_t *nbr, int *label, GraphInfo *info, int *status,
-                       unsigned long long *counts, long long ncounts, bool relabel, int num_sms, cudaStream_t s) {
+int launch_build_graph(const GSet &gs, long long state_words, uint32_t *state, bool state_clean, int *deg, int *lo,
+                       int *deg_in, long long *nptr, long long *tile_scratch, uint32_t *nbr, int *label,
+                       GraphInfo *info, int *status, unsigned long long *counts, long long ncounts, bool relabel,
+                       int num_sms, cudaStream_t s) {
     int launches = 0;
-    const size_t state_bytes = (size_t)state_words * 4;
     const long long NV = gs.NV;
     const int rows_grid = grid_for(NV * kWarp, 256, num_sms);
-    // zero the pair-state blocks, the counts, the status word and (for the
-    // renumbering) the degree histograms kept in lo[]
-    int r = launch_zero(state, state_bytes, num_sms, s, status, counts, ncounts, relabel ? lo : nullptr,
-                        relabel ? NV + 1 : 0);
-    if (r < 0) return r;
-    launches += r;
-    k_ingest<<<rows_grid, 256, 0, s>>>(gs, state, nullptr, status);
-    launches++;
-    if (relabel) {
-        // G* degrees under the input labels, then each graph's vertices
-        // renumbered by descending degree and its block rebuilt
-        int *dhist = lo;
-        int *start = reinterpret_cast<int *>(nptr);
-        k_degrees<<<rows_grid, 256, 0, s>>>(gs, state, deg, nullptr, dhist);
-        k_desc_starts<<<gs.B, 1024, 0, s>>>(gs, dhist, start);
-        k_desc_scatter<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, deg, start, label);
-        launches += 3;
-        r = launch_zero(state, state_bytes, num_sms, s);
-        if (r < 0) return r;
-        launches += r;
-        k_ingest<<<rows_grid, 256, 0, s>>>(gs, state, label, nullptr);
+    // zero the counts, the status word, the degree counters and, unless the
+    // previous call left it clean, the pair-state buffer
+    {
+        const size_t bytes = state_clean ? 0 : (size_t)state_words * 4;
+        IntRanges r = {{deg, lo, deg_in}, {NV, NV, relabel ? NV : 0}};
+        const size_t n16 = bytes / 16, ntail = bytes % 16;
+        const long long items = (long long)max((size_t)1, max(n16, (size_t)max(NV, ncounts)));
+        k_zero<<<grid_for(items, 256 * 4, num_sms), 256, 0, s>>>(reinterpret_cast<uint4 *>(state), n16,
+                                                                 reinterpret_cast<unsigned char *>(state) + n16 * 16,
+                                                                 ntail, status, counts, ncounts, r);
         launches++;
     }
-    k_degrees<<<rows_grid, 256, 0, s>>>(gs, state, deg, lo, nullptr);
-    launches++;
+    if (relabel) {
+        // G* degrees under the input labels; each graph's vertices renumbered
+        // by descending degree; the arcs' words cleared and the block rebuilt
+        int *dhist = lo;  // zeroed above, cleared again by k_clear_arcs
+        int *start = reinterpret_cast<int *>(nptr);
+        k_ingest<<<rows_grid, 256, 0, s>>>(gs, state, nullptr, status, deg_in, nullptr);
+        k_dhist<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, deg_in, dhist);
+        k_desc_starts<<<gs.B, 1024, 0, s>>>(gs, dhist, start);
+        k_desc_scatter<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, deg_in, start, label);
+        k_clear_arcs<<<rows_grid, 256, 0, s>>>(gs, state, nullptr, deg, lo);
+        k_ingest<<<rows_grid, 256, 0, s>>>(gs, state, label, nullptr, deg, lo);
+        launches += 6;
+    } else {
+        k_ingest<<<rows_grid, 256, 0, s>>>(gs, state, nullptr, status, deg, lo);
+        launches++;
+    }
     if (NV <= kScanSingleMax) {
         k_scan_degrees<<<1, 1024, 0, s>>>(deg, (int)NV, nptr, info);
         launches++;
@@ -462,6 +498,13 @@ int launch_build_graph(const GSet &gs, long long state_words, uint32_t *state, i
     k_fill<<<rows_grid, 256, 0, s>>>(gs, state, nptr, nbr);
     launches++;
     return cudaGetLastError() == cudaSuccess ? launches : ACC_ERR_CUDA;
+}
+
+int launch_clear_graph(const GSet &gs, uint32_t *state, const int *label, bool relabel, int num_sms, cudaStream_t s) {
+    if (gs.NV == 0) return 0;
+    k_clear_arcs<<<grid_for(gs.NV * kWarp, 256, num_sms), 256, 0, s>>>(gs, state, relabel ? label : nullptr, nullptr,
+                                                                       nullptr);
+    return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
 
 }  // namespace acc

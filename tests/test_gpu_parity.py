@@ -147,6 +147,31 @@ def test_edge_cases(counter, k):
     assert gpu_count(counter, 45, s, d, k).tolist() == base.tolist()
 
 
+@pytest.mark.parametrize("k", [3, 4])
+def test_repeated_arcs_relabelled_and_buffer_reuse(counter, k):
+    """Graphs above the renumbering threshold with repeated arcs and reversed
+    rows, interleaved with other sizes and a malformed call on one context:
+    each call must see an all-zero pair-state buffer."""
+    import torch
+    import paper_1203_3415_gb300 as p
+    g = synth.chung_lu(1500, 6000, 2.2, 120, 10, 71)
+    s2 = np.concatenate([g.src, g.src[::3], g.dst[:50]])
+    d2 = np.concatenate([g.dst, g.dst[::3], g.src[:50]])  # repeats, plus 50 reverse arcs
+    rowptr, col = csr_arrays(g.n, s2, d2)
+    for v in range(g.n):
+        col[rowptr[v]:rowptr[v + 1]] = col[rowptr[v]:rowptr[v + 1]][::-1].copy()
+    want = oracle.count(g.n, s2, d2, k, threads=oracle.max_threads())
+    r_dev, c_dev = torch.from_numpy(rowptr).cuda(), torch.from_numpy(col).cuda()
+    assert counter.count(r_dev, c_dev, g.n, k).cpu().numpy().tolist() == want.tolist()
+    h = synth.chung_lu(3000, 9000, 2.2, 150, 10, 72)
+    assert gpu_count(counter, h.n, h.src, h.dst, k).tolist() == \
+        oracle.count(h.n, h.src, h.dst, k, threads=oracle.max_threads()).tolist()
+    bad_r, bad_c = csr_arrays(1200, [0, 1], [1, 1])  # self-loop
+    with pytest.raises(p.MotifError):
+        counter.count(torch.from_numpy(bad_r).cuda(), torch.from_numpy(bad_c).cuda(), 1200, k)
+    assert counter.count(r_dev, c_dev, g.n, k).cpu().numpy().tolist() == want.tolist()
+
+
 def test_malformed_input(counter):
     import torch
     import paper_1203_3415_gb300 as p
