@@ -48,12 +48,20 @@ DEFAULT_WORKLOAD = "chung_lu_n20000_m100000_k4"
 BATCH_WORKLOAD = "batch_k4"
 SERVING_WORKLOAD = "serving"
 
-# Algorithmic integer operations per classified subgraph (the method's minimum
-# at the leaf): k-1 pair states, each an address, a load and a 2-bit extract
-# (4 ops) placed into the code (2 ops), then one table load and one histogram
-# increment: 6(k-1) + 2.
+# Algorithmic integer operations per classified subgraph when every leaf is
+# visited (the leaf-enumerating form): k-1 pair states, each an address, a
+# load and a 2-bit extract (4 ops) placed into the code (2 ops), then one
+# table load and one histogram increment: 6(k-1) + 2.
 def ops_per_subgraph(k: int) -> int:
     return 6 * (k - 1) + 2
+
+
+# The counting form's unit of work is one neighbour entry scanned by the last
+# two levels: the entry's load and its test against the root (2 ops), its
+# k-2 pair states to the prefix (4 ops each: address, load, shift, mask),
+# then one table load and one histogram increment: 4(k-2) + 4.
+def ops_per_scanned_entry(k: int) -> int:
+    return 4 * (k - 2) + 4
 
 
 L2_FLUSH_BYTES = 256 << 20
@@ -181,9 +189,9 @@ def kernel_source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """Bytes per enumeration stage from profiles/<workload>_traffic.txt, when it
-    was taken on the current kernel source; else None."""
+def profiled_traffic(workload: str, mode: str):
+    """Bytes per enumeration stage from profiles/enum_<workload>_traffic.txt,
+    when it was taken on the current kernel source in this mode; else None."""
     path = os.path.join(ROOT, "profiles", f"enum_{workload}_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -192,7 +200,7 @@ def profiled_traffic(workload: str):
         if ":" in line and not line.startswith("#"):
             key, _, val = line.partition(":")
             kv[key.strip()] = val.strip()
-    if kv.get("source_digest") != kernel_source_digest():
+    if kv.get("source_digest") != kernel_source_digest() or kv.get("mode", "count") != mode:
         return None
     try:
         return float(kv["dram_bytes_per_stage"])
@@ -368,8 +376,15 @@ def run_ours(args):
     # issue peak: SMs x 4 schedulers x 32 lanes per clock
     peak_gops = props.multi_processor_count * 4 * 32 * sm_max * 1e6 / 1e9
     enum_s = statistics.mean(enum_ms) / 1000.0
-    achieved = ops_per_subgraph(k) * n_k / enum_s / 1e9
-    traffic = profiled_traffic(args.workload)
+    leaf_achieved = ops_per_subgraph(k) * n_k / enum_s / 1e9
+    if args.mode == "count":
+        units, per_unit = int(stats["scanned_entries"]), ops_per_scanned_entry(k)
+        unit_name = "neighbour entries scanned by the last two levels"
+    else:
+        units, per_unit = n_k, ops_per_subgraph(k)
+        unit_name = "classified subgraphs"
+    achieved = per_unit * units / enum_s / 1e9
+    traffic = profiled_traffic(args.workload, args.mode)
 
     # CPU baseline: the oracle on this host's cores, the whole workload
     cpu = None
@@ -390,7 +405,11 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved / peak_gops, "traffic": traffic,
                      "kernel": f"k_enum<{k}> (phase 1 + phase 2)",
-                     "ops_per_subgraph": ops_per_subgraph(k), "peak_source": peak_src},
+                     "work_unit": unit_name, "units_per_launch": units, "ops_per_unit": per_unit,
+                     "peak_source": peak_src,
+                     # what a kernel visiting every leaf would have to sustain for this rate
+                     "leaf_equivalent": {"ops_per_subgraph": ops_per_subgraph(k), "achieved": leaf_achieved,
+                                         "frac": leaf_achieved / peak_gops}},
         "cpu_baseline": cpu,
         "e2e": {"value": whole_job_rate(e2e_units, e2e_max), "unit": UNIT,
                 "h2d_bytes_per_step": int(rowptr_np.nbytes + col_np.nbytes),

@@ -249,9 +249,10 @@ ACC_API int acc_motif_copy_table(acc_ctx *ctx, int k, int16_t *h_table);
  *   [0] kernels the call launched, [1] base work units (vertices for k = 3,
  *   neighbour-list positions for k = 4, 5), [2] chunks heavy units were split
  *   into, [3] undirected edges |E*|, [4] largest degree in G*, [5] blocks of
- *   each enumeration launch.
+ *   each enumeration launch, [6] neighbour entries the last two levels
+ *   scanned (ACC_MODE_COUNT; 0 in ACC_MODE_ENUMERATE).
  */
-#define ACC_STATS_LEN 6
+#define ACC_STATS_LEN 7
 ACC_API int acc_motif_last_stats(acc_ctx *ctx, int64_t *h_stats);
 
 /*

@@ -27,7 +27,7 @@ ACC_ERR_ARG = -7
 ACC_ERR_TOO_LARGE = -8
 ACC_ERR_INTERNAL = -9
 ACC_MAX_N = 131072
-ACC_STATS_LEN = 6
+ACC_STATS_LEN = 7
 
 NUM_CLASSES = {3: 13, 4: 199, 5: 9364}
 
@@ -301,6 +301,7 @@ class Counter:
 
     def __init__(self, device: int = 0):
         self.device = device
+        self.mode = ACC_MODE_COUNT
         self.ctx = acc_ctx_create(device)
 
     def close(self):
@@ -400,6 +401,7 @@ class Counter:
     def set_mode(self, mode: int):
         """ACC_MODE_COUNT (default) or ACC_MODE_ENUMERATE; same counts."""
         _check(acc_ctx_set_mode(self.ctx, mode), "acc_ctx_set_mode")
+        self.mode = mode
 
     def set_timing(self, on: bool = True):
         _check(acc_ctx_set_timing(self.ctx, 1 if on else 0), "acc_ctx_set_timing")
@@ -417,4 +419,5 @@ class Counter:
         out = np.zeros(ACC_STATS_LEN, dtype=np.int64)
         _check(acc_motif_last_stats(self.ctx, out.ctypes.data), "acc_motif_last_stats")
         return {"launches": int(out[0]), "units": int(out[1]), "chunks": int(out[2]),
-                "undirected_edges": int(out[3]), "max_degree": int(out[4]), "blocks": int(out[5])}
+                "undirected_edges": int(out[3]), "max_degree": int(out[4]), "blocks": int(out[5]),
+                "scanned_entries": int(out[6])}

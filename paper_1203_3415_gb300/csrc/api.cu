@@ -499,6 +499,7 @@ int acc_motif_last_stats(acc_ctx *c, int64_t *h_stats) {
     h_stats[3] = (int64_t)(gi.nnz / 2);
     h_stats[4] = gi.maxdeg;
     h_stats[5] = c->last_blocks;
+    h_stats[6] = (int64_t)gi.scanned;
     return ACC_OK;
 }
 

@@ -43,6 +43,7 @@ struct GraphInfo {
     unsigned long long queue_head;  // chunks taken by phase 2
     unsigned long long unit_ctr;    // base units taken by phase 1
     unsigned long long chunks_pushed;
+    unsigned long long scanned;     // count mode: neighbour entries the last two levels scanned
 };
 
 // One graph of a set.  Its vertices are the global ids [voff, voff + n); its

@@ -189,6 +189,7 @@ struct Sink {
     int gcur;           // graph whose counts this warp accumulates
     bool direct;        // k = 5 with several graphs: runs go straight to the int64 counts
     unsigned long long moved;  // count mode: this lane's |increments| since the last accounting
+    unsigned long long scanned;  // count mode: neighbour entries this warp scanned
 
     // Count mode: add delta (may be negative) to class cls.  Shared counters
     // are read as signed 32-bit when drained; a delta too large for them goes
@@ -513,6 +514,7 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
         }
         int tot;
         const int pre = excl_scan(cnt, lane, &tot);
+        sink.scanned += (unsigned long long)tot;
         const uint32_t cj = pcode | (e_sv(ej) << L::SH_ROW);
         const uint32_t xj = e_id(ej);
         const uint32_t off = first - (uint32_t)pre;
@@ -913,6 +915,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : (COUNT ? ACC_MINB34C : 
     sc.cap = L::CAP;
     sc.gcnt = groups + (size_t)wib * 3 * L::G;
     sink.moved = 0;
+    sink.scanned = 0;
     const long long nnz = a.info->nnz;
     const long long NV = a.gs.NV;
     const long long D = (NV > 0 ? nnz / NV : 0) + 1;
@@ -956,6 +959,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : (COUNT ? ACC_MINB34C : 
         }
     }
 
+    if (COUNT && lane == 0 && sink.scanned) atomicAdd(&a.info->scanned, sink.scanned);
     __syncthreads();
     if (several) {
         // each warp drains its own histogram to the graph it ended on

@@ -240,6 +240,7 @@ __global__ void k_scan_degrees(const int *__restrict__ deg, int n, long long *np
         info->queue_head = 0;
         info->unit_ctr = 0;
         info->chunks_pushed = 0;
+        info->scanned = 0;
     }
 }
 
@@ -326,6 +327,7 @@ __global__ void k_scan_top(long long *tile_sum, int ntiles, long long *nptr, int
         info->queue_head = 0;
         info->unit_ctr = 0;
         info->chunks_pushed = 0;
+        info->scanned = 0;
     }
 }
 

@@ -57,3 +57,38 @@ def in_star(leaves):
 def relabel(perm, src, dst):
     perm = np.asarray(perm)
     return _arr(perm[src], perm[dst])
+
+
+def esu_scanned_entries(n, src, dst, k):
+    """Neighbour entries the last two ESU levels read when they are counted
+    from the extension lists: for every prefix P of k-2 vertices (root v = its
+    smallest) with extension list E(P), the sum over x in E(P) of the
+    neighbours of x above v.  Lists follow ESU's order: N(v) above v; then
+    N(v) above w1 followed by the neighbours of w1 above v not adjacent to v;
+    then level 2's list after w2 followed by the neighbours of w2 above v
+    adjacent to neither v nor w1.  Vertex ids as given (no renumbering)."""
+    nb = [set() for _ in range(n)]
+    for a, b in zip(src, dst):
+        if a != b:
+            nb[a].add(b)
+            nb[b].add(a)
+    adj = [sorted(x) for x in nb]
+
+    def above(x, v):
+        return sum(1 for u in adj[x] if u > v)
+
+    total = 0
+    for v in range(n):
+        E1 = [x for x in adj[v] if x > v]
+        if k == 3:
+            total += sum(above(x, v) for x in E1)
+            continue
+        for w1 in E1:
+            E2 = [x for x in adj[v] if x > w1] + [u for u in adj[w1] if u > v and u not in nb[v]]
+            if k == 4:
+                total += sum(above(x, v) for x in E2)
+                continue
+            for j2, w2 in enumerate(E2):
+                E3 = E2[j2 + 1:] + [u for u in adj[w2] if u > v and u not in nb[v] and u not in nb[w1]]
+                total += sum(above(x, v) for x in E3)
+    return total

@@ -17,8 +17,8 @@ import pytest
 import oracle
 import synth
 from tests.gpu_helpers import csr_arrays, gpu_count
-from tests.graph_helpers import (complete_bidirected, directed_cycle, directed_path, in_star, out_star,
-                                 random_digraph, transitive_tournament)
+from tests.graph_helpers import (complete_bidirected, directed_cycle, directed_path, esu_scanned_entries, in_star,
+                                 out_star, random_digraph, transitive_tournament)
 
 pytestmark = pytest.mark.gpu
 
@@ -59,6 +59,20 @@ def test_random_small_graphs(counter, k):
         n = int(rng.integers(k, 48))
         s, d = random_digraph(rng, n, p=float(rng.random()) ** 2, recip=float(rng.random()))
         assert gpu_count(counter, n, s, d, k).tolist() == oracle.count(n, s, d, k).tolist(), (trial, n)
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_scanned_entries_stat(counter, k):
+    """The count mode's work figure (neighbour entries scanned by the last two
+    levels) equals the same sum taken over a plain ESU walk."""
+    if counter.mode != 0:
+        pytest.skip("count mode only")
+    rng = np.random.default_rng(2000 + k)
+    for trial in range(6):
+        n = int(rng.integers(k, 160 if k < 5 else 70))
+        s, d = random_digraph(rng, n, p=float(rng.random()) ** 2 * 0.5, recip=float(rng.random()))
+        gpu_count(counter, n, s, d, k)
+        assert counter.last_stats()["scanned_entries"] == esu_scanned_entries(n, s, d, k), (trial, n)
 
 
 @pytest.mark.parametrize("k,n,m,seed", [(3, 4000, 24000, 11), (4, 3000, 12000, 12), (5, 1200, 3000, 13)])
