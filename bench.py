@@ -576,6 +576,7 @@ def run_serving_bench(args):
     graphs = [synth.serving_graph(sp) for sp in specs]
     reqs = synth.serving_requests(duration_s=args.serve_seconds)
     srv = acc.Server(local, slots=args.slots, mem_budget_bytes=int(args.mem_budget_gb * (1 << 30)))
+    srv.set_policy(acc.ACC_SERVE_FIFO if args.serve_policy == "fifo" else acc.ACC_SERVE_SHORTEST, args.serve_aging_s)
     tens = []
     for g in graphs:
         r, c = g.csr()
@@ -635,6 +636,7 @@ def run_serving_bench(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": SERVING_WORKLOAD, "graphs": len(graphs), "requests": len(rids),
                    "arrival_rate_per_s": 200, "window_s": args.serve_seconds, "slots": args.slots,
+                   "policy": args.serve_policy, "aging_s": args.serve_aging_s,
                    "mem_budget_gb": args.mem_budget_gb, "parallelism": f"replicas{world}"},
         "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": pct(lat, 100),
                        "by_k_p50": {str(k): pct(np.array(v), 50) for k, v in by_k.items()},
@@ -662,6 +664,9 @@ def main():
     ap.add_argument("--reference-roots", type=int, default=1000,
                     help="reference arm: ESU roots per step (bounded CPU sample)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-policy", choices=["shortest", "fifo"], default="shortest",
+                    help="serving admission order: smallest aged work estimate first, or submission order")
+    ap.add_argument("--serve-aging-s", type=float, default=1.0)
     ap.add_argument("--mode", choices=["count", "enumerate"], default="count",
                     help="last two levels counted by state-vector groups, or every leaf enumerated")
     args = ap.parse_args()

@@ -190,8 +190,9 @@ ACC_API int acc_motif_zscores(const int64_t *d_counts, int32_t groups, int32_t g
  *
  * Requests (resident graph, k) are submitted at any time.  A request is
  * admitted as soon as one of the server's slots is free and the slot's device
- * workspace for it fits the memory budget (FIFO; a request that cannot fit
- * even with every slot idle fails with ACC_ERR_NOMEM).  Each slot has its own
+ * workspace for it fits the memory budget, in the order of the admission
+ * policy (acc_server_set_policy; a request that cannot fit even with every
+ * slot idle fails with ACC_ERR_NOMEM).  Each slot has its own
  * context and CUDA stream, so admitted requests overlap on the device; a
  * request's enumeration grid is capped (1/8 of the GPU for graphs of at most
  * 4096 vertices, 5/8 above) so that one large request cannot hold every SM.
@@ -208,10 +209,27 @@ typedef struct acc_server acc_server;
 /* Server on `device` with `slots` (1..64) concurrent requests and a device
  * memory budget for the slots' workspaces in bytes. */
 ACC_API int acc_server_create(acc_server **out, int device, int32_t slots, int64_t mem_budget_bytes);
+/* Admission order of queued requests.
+ *  ACC_SERVE_SHORTEST (default): the request with the smallest
+ *   est * exp(-wait / aging_s) goes first, where est is the graph's work
+ *   estimate for its k (sum over vertices of d^(k-1), d = out- plus
+ *   in-degree, taken when the graph is registered) and wait the seconds it
+ *   has queued; small requests overtake large ones, and a large request's
+ *   key halves every aging_s * ln 2 seconds, so none waits forever.
+ *  ACC_SERVE_FIFO: submission order.
+ * If the chosen request does not fit the budget, admission waits for a
+ * running request to finish.  Errors: ACC_ERR_ARG (unknown policy,
+ * aging_s <= 0). */
+#define ACC_SERVE_FIFO 0
+#define ACC_SERVE_SHORTEST 1
+ACC_API int acc_server_set_policy(acc_server *srv, int policy, double aging_s);
 /* Waits for running requests, releases everything (NULL is a no-op). */
 ACC_API void acc_server_destroy(acc_server *srv);
 /* Register a resident graph (device arrays as in acc_motif_count; they must
- * stay valid while the server may count it).  *graph_id receives its id. */
+ * hold the graph when this is called and stay valid while the server may
+ * count it).  Reads the arrays once to estimate the graph's work per k (a
+ * synchronous copy to the host for graphs of at most 2^26 arcs; larger
+ * graphs are estimated from n and m).  *graph_id receives its id. */
 ACC_API int acc_server_add_graph(acc_server *srv, const int64_t *d_rowptr, const int32_t *d_col, int32_t n,
                                  int64_t m, int32_t *graph_id);
 /* Pre-size every slot (within the budget) for the largest registered graph

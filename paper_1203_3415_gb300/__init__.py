@@ -39,8 +39,10 @@ EXPORTS = (
     "acc_motif_copy_table", "acc_motif_last_stats", "acc_ctx_set_timing", "acc_motif_last_timing",
     "acc_motif_build_table_static", "acc_ctx_set_mode", "acc_server_create", "acc_server_destroy", "acc_server_add_graph",
     "acc_server_reserve", "acc_server_submit", "acc_server_progress", "acc_server_poll", "acc_server_drain",
+    "acc_server_set_policy",
 )
 ACC_REQ_QUEUED, ACC_REQ_RUNNING, ACC_REQ_DONE = 0, 1, 2
+ACC_SERVE_FIFO, ACC_SERVE_SHORTEST = 0, 1
 ACC_MODE_COUNT, ACC_MODE_ENUMERATE = 0, 1
 
 
@@ -80,6 +82,7 @@ def _load():
     lib.acc_server_progress.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.acc_server_poll.argtypes = [vp, i64, ctypes.POINTER(i32), vp, ctypes.POINTER(ctypes.c_double)]
     lib.acc_server_drain.argtypes = [vp]
+    lib.acc_server_set_policy.argtypes = [vp, ctypes.c_int, ctypes.c_double]
     return lib
 
 
@@ -246,6 +249,10 @@ def acc_server_drain(srv: int) -> int:
     return _L().acc_server_drain(srv)
 
 
+def acc_server_set_policy(srv: int, policy: int, aging_s: float) -> int:
+    return _L().acc_server_set_policy(srv, policy, aging_s)
+
+
 class Server:
     """Request server with continuous batching (see include/acc_motif.h)."""
 
@@ -261,6 +268,10 @@ class Server:
 
     def reserve(self):
         _check(acc_server_reserve(self.srv), "acc_server_reserve")
+
+    def set_policy(self, policy: int, aging_s: float = 1.0):
+        """ACC_SERVE_SHORTEST (default) or ACC_SERVE_FIFO admission order."""
+        _check(acc_server_set_policy(self.srv, policy, aging_s), "acc_server_set_policy")
 
     def submit(self, graph_id: int, k: int) -> int:
         rid = acc_server_submit(self.srv, graph_id, k)

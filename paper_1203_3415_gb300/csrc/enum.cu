@@ -61,13 +61,13 @@ namespace {
 #define ACC_HIST_MATCH 0  // 1: warp-aggregate increments with __match_any_sync
 #endif
 #ifndef ACC_CUNROLL
-#define ACC_CUNROLL 2  // count mode: neighbour entries in flight per lane
+#define ACC_CUNROLL 4  // count mode: neighbour entries in flight per lane
 #endif
 #ifndef ACC_MINB34
 #define ACC_MINB34 4  // resident blocks per SM the k = 3, 4 leaf kernels are compiled for
 #endif
 #ifndef ACC_MINB34C
-#define ACC_MINB34C 3  // the same for the k = 3, 4 count-mode kernels
+#define ACC_MINB34C 4  // the same for the k = 3, 4 count-mode kernels
 #endif
 constexpr int kCap34 = ACC_CAP34;         // per-warp shared extension entries, k = 3, 4
 constexpr int kCap5 = 384;                // per-warp shared entries per list, k = 5
@@ -874,8 +874,10 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
     __syncwarp();
 }
 
-template <int K, bool COUNT>
-__global__ void __launch_bounds__(kThreads, K == 5 ? 3 : (COUNT ? ACC_MINB34C : ACC_MINB34)) k_enum(EnumArgs a, int phase) {
+// One instantiation per phase, so each is register-allocated for its own path
+// (phase 1: the unit loop, work estimates and queueing; phase 2: the queue).
+template <int K, bool COUNT, int PHASE>
+__global__ void __launch_bounds__(kThreads, K == 5 ? 3 : (COUNT ? ACC_MINB34C : ACC_MINB34)) k_enum(EnumArgs a) {
     using L = Layout<K>;
     extern __shared__ __align__(16) unsigned char smem[];
     int16_t *lut_s = reinterpret_cast<int16_t *>(smem);
@@ -920,7 +922,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : (COUNT ? ACC_MINB34C : 
     const long long NV = a.gs.NV;
     const long long D = (NV > 0 ? nnz / NV : 0) + 1;
 
-    if (phase == 1) {
+    if constexpr (PHASE == 1) {
         const long long nunits = K == 3 ? NV : nnz;
         for (;;) {
             unsigned long long u0 = 0;
@@ -984,15 +986,15 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? 3 : (COUNT ? ACC_MINB34C : 
     }
 }
 
-template <int K, bool COUNT>
+template <int K, bool COUNT, int PHASE>
 int blocks_per_sm() {
     static int cached = 0;
     if (cached) return cached;
-    if (cudaFuncSetAttribute(k_enum<K, COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_enum<K, COUNT, PHASE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Layout<K>::total) != cudaSuccess)
         return -1;
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_enum<K, COUNT>, kThreads, Layout<K>::total) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_enum<K, COUNT, PHASE>, kThreads, Layout<K>::total) !=
             cudaSuccess ||
         b < 1)
         return -1;
@@ -1000,22 +1002,35 @@ int blocks_per_sm() {
     return b;
 }
 
-template <int K, bool COUNT>
-int launch_k(const EnumArgs &a, int num_sms, int phase, cudaStream_t s, int grid_num, int grid_den) {
-    const int bps = blocks_per_sm<K, COUNT>();
+template <int K, bool COUNT, int PHASE>
+int launch_phase(const EnumArgs &a, int num_sms, cudaStream_t s, int grid_num, int grid_den) {
+    const int bps = blocks_per_sm<K, COUNT, PHASE>();
     if (bps < 1) return ACC_ERR_CUDA;
     int grid = (int)((long long)num_sms * bps * grid_num / grid_den);
     if (grid < num_sms) grid = num_sms;
     if (grid > num_sms * bps) grid = num_sms * bps;
-    k_enum<K, COUNT><<<grid, kThreads, Layout<K>::total, s>>>(a, phase);
+    k_enum<K, COUNT, PHASE><<<grid, kThreads, Layout<K>::total, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
 
+template <int K, bool COUNT>
+int launch_k(const EnumArgs &a, int num_sms, int phase, cudaStream_t s, int grid_num, int grid_den) {
+    return phase == 1 ? launch_phase<K, COUNT, 1>(a, num_sms, s, grid_num, grid_den)
+                      : launch_phase<K, COUNT, 2>(a, num_sms, s, grid_num, grid_den);
+}
+
+// Most resident blocks per SM of any instantiation for k (sizes the per-warp
+// overflow lists).
 template <int K>
 int bps_max() {
-    const int a = blocks_per_sm<K, false>(), b = blocks_per_sm<K, true>();
-    if (a < 1 || b < 1) return -1;
-    return a > b ? a : b;
+    const int b[4] = {blocks_per_sm<K, false, 1>(), blocks_per_sm<K, false, 2>(), blocks_per_sm<K, true, 1>(),
+                      blocks_per_sm<K, true, 2>()};
+    int m = 0;
+    for (int x : b) {
+        if (x < 1) return -1;
+        if (x > m) m = x;
+    }
+    return m;
 }
 
 }  // namespace

@@ -8,13 +8,14 @@
 // detected with CUDA events, results are copied to pinned host memory in
 // stream order.  The enumeration grid of a request is capped (a small graph
 // takes 1/8 of the GPU's persistent grid, a large one 5/8) so that one large
-// request cannot lock every SM while small requests wait.  Admission is FIFO.
+// request cannot lock every SM while small requests wait.  Admission takes
+// the queued request with the smallest aged work estimate (or FIFO order).
 // Host work happens only inside the caller's calls (no threads).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <chrono>
-#include <deque>
+#include <cmath>
 #include <new>
 #include <vector>
 
@@ -45,7 +46,42 @@ struct Graph {
     const int32_t *col;
     int32_t n;
     int64_t m;
+    double est[3];  // work estimate for k = 3, 4, 5: sum over v of d(v)^(k-1)
 };
+
+constexpr int64_t kEstimateCopyMax = 1ll << 26;  // arcs; larger graphs are estimated from n and m
+
+// Work estimate of a registered graph: sum over vertices of d^(k-1), with d
+// the out- plus in-degree (ESU's work grows with the (k-1)-th power of the
+// degrees; the ordering of requests is all it is used for).
+int estimate_work(Graph &g) {
+    for (int k = 3; k <= 5; k++) {
+        const double d = g.n > 0 ? 2.0 * (double)g.m / g.n : 0.0;
+        g.est[k - 3] = (double)g.n * std::pow(d, k - 1);
+    }
+    if (g.n == 0 || g.m == 0 || g.m > kEstimateCopyMax) return ACC_OK;
+    std::vector<int64_t> rp((size_t)g.n + 1);
+    std::vector<int32_t> col((size_t)g.m);
+    if (cudaMemcpy(rp.data(), g.rowptr, rp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(col.data(), g.col, col.size() * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return ACC_ERR_CUDA;
+    }
+    std::vector<double> deg((size_t)g.n, 0.0);
+    for (int32_t v = 0; v < g.n; v++) {
+        const int64_t b = rp[(size_t)v], e = rp[(size_t)v + 1];
+        if (b < 0 || e < b || e > g.m) continue;  // malformed: the count reports it
+        deg[(size_t)v] += (double)(e - b);
+        for (int64_t p = b; p < e; p++)
+            if (col[(size_t)p] >= 0 && col[(size_t)p] < g.n) deg[(size_t)col[(size_t)p]] += 1.0;
+    }
+    for (int k = 3; k <= 5; k++) {
+        double s = 0.0;
+        for (double d : deg) s += std::pow(d, k - 1);
+        g.est[k - 3] = s;
+    }
+    return ACC_OK;
+}
 
 struct Req {
     int32_t graph;
@@ -60,10 +96,12 @@ struct Req {
 struct acc_server {
     int device = 0;
     long long budget = 0;
+    int policy = ACC_SERVE_SHORTEST;
+    double aging_s = 1.0;
     std::vector<Slot> slots;
     std::vector<Graph> graphs;
     std::vector<Req> reqs;
-    std::deque<long long> queue;
+    std::vector<long long> queue;  // request ids in submission order
 };
 
 namespace {
@@ -97,7 +135,24 @@ int progress(acc_server *sv) {
         sl.req = -1;
     }
     while (!sv->queue.empty()) {
-        const long long id = sv->queue.front();
+        bool any_free = false;
+        for (const Slot &sl : sv->slots) any_free = any_free || sl.req < 0;
+        if (!any_free) break;
+        // the request to admit next
+        size_t pick = 0;
+        if (sv->policy == ACC_SERVE_SHORTEST) {
+            const double t = now_s();
+            double best_key = 0.0;
+            for (size_t q = 0; q < sv->queue.size(); q++) {
+                const Req &c = sv->reqs[(size_t)sv->queue[q]];
+                const double key = sv->graphs[(size_t)c.graph].est[c.k - 3] * std::exp(-(t - c.t_submit) / sv->aging_s);
+                if (q == 0 || key < best_key) {
+                    best_key = key;
+                    pick = q;
+                }
+            }
+        }
+        const long long id = sv->queue[pick];
         Req &r = sv->reqs[(size_t)id];
         const Graph &g = sv->graphs[(size_t)r.graph];
         // the free slot that needs the least growth and stays within budget
@@ -121,7 +176,7 @@ int progress(acc_server *sv) {
             // nothing runs and it still does not fit: it never will
             r.state = ACC_ERR_NOMEM;
             r.t_done = now_s();
-            sv->queue.pop_front();
+            sv->queue.erase(sv->queue.begin() + (long)pick);
             continue;
         }
         Slot &sl = sv->slots[(size_t)best];
@@ -130,7 +185,7 @@ int progress(acc_server *sv) {
         sl.ctx->grid_den = 8;
         r.t_start = now_s();
         const int rc = acc_motif_count(sl.ctx, g.rowptr, g.col, g.n, g.m, r.k, sl.s, sl.d_counts, sl.d_status);
-        sv->queue.pop_front();
+        sv->queue.erase(sv->queue.begin() + (long)pick);
         if (rc != ACC_OK) {
             r.state = rc;
             r.t_done = now_s();
@@ -205,8 +260,19 @@ int acc_server_add_graph(acc_server *sv, const int64_t *d_rowptr, const int32_t 
     if (!sv || !d_rowptr || !graph_id || (m > 0 && !d_col)) return ACC_ERR_ARG;
     if (n < 0 || m < 0 || m >= (1ll << 31)) return ACC_ERR_INPUT;
     if (n > ACC_MAX_N) return ACC_ERR_TOO_LARGE;
-    sv->graphs.push_back(Graph{d_rowptr, d_col, n, m});
+    Graph g{d_rowptr, d_col, n, m, {0.0, 0.0, 0.0}};
+    if (!ok(cudaSetDevice(sv->device))) return ACC_ERR_CUDA;
+    const int rc = estimate_work(g);
+    if (rc) return rc;
+    sv->graphs.push_back(g);
     *graph_id = (int32_t)sv->graphs.size() - 1;
+    return ACC_OK;
+}
+
+int acc_server_set_policy(acc_server *sv, int policy, double aging_s) {
+    if (!sv || (policy != ACC_SERVE_FIFO && policy != ACC_SERVE_SHORTEST) || !(aging_s > 0.0)) return ACC_ERR_ARG;
+    sv->policy = policy;
+    sv->aging_s = aging_s;
     return ACC_OK;
 }
 

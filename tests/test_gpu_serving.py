@@ -109,3 +109,36 @@ def test_request_errors(acc):
     srv.drain()
     assert srv.poll(rid)[0] == acc.ACC_ERR_NOMEM
     srv.close()
+
+
+@pytest.mark.parametrize("policy", ["shortest", "fifo"])
+def test_admission_policy_order(acc, policy):
+    """One slot, three large requests then a small one: shortest-first runs
+    the small one as soon as the slot frees, FIFO runs it last; the counts
+    are the same either way."""
+    graphs = pool()
+    big, small = graphs[7], graphs[4]
+    (rb, cb), (rs, cs) = to_dev(big), to_dev(small)
+    srv = acc.Server(0, slots=1, mem_budget_bytes=16 << 30)
+    if policy == "fifo":
+        srv.set_policy(acc.ACC_SERVE_FIFO)
+    gb, gs = srv.add_graph(rb, cb, big.n), srv.add_graph(rs, cs, small.n)
+    srv.reserve()
+    bigs = [srv.submit(gb, 5) for _ in range(3)]
+    s = srv.submit(gs, 3)
+    while srv.poll(s)[0] != acc.ACC_REQ_DONE:
+        pass
+    last_big_state = srv.poll(bigs[2])[0]
+    if policy == "fifo":
+        assert last_big_state == acc.ACC_REQ_DONE
+    else:
+        assert last_big_state == acc.ACC_REQ_QUEUED
+    srv.drain()
+    want_big = srv.poll(bigs[0])[1]
+    for rid in bigs:
+        st, counts, _ = srv.poll(rid)
+        assert st == acc.ACC_REQ_DONE and counts.tolist() == want_big.tolist()
+    assert srv.poll(s)[1].tolist() == oracle.count(small.n, small.src, small.dst, 3).tolist()
+    with pytest.raises(acc.MotifError):
+        srv.set_policy(7)
+    srv.close()
