@@ -98,12 +98,14 @@ long long scratch_per_warp(int max_n) { return 2 * (((long long)max_n + 32 + 31)
 int ensure_workspace(acc_ctx *c, long long NV, long long state_words, long long arcs, int max_n, int k) {
     int rc;
     {
-        const uint32_t *before = c->state;
+        // a reallocation (the capacity changes; the address may not) brings
+        // memory that is not zero: the next build sweeps it
+        const size_t cap_before = c->state_cap;
         if ((rc = grow(&c->state, &c->state_cap, (size_t)state_words + 4))) {
             c->state_clean = false;
             return rc;
         }
-        if (c->state != before) c->state_clean = false;  // fresh memory: swept by the next build
+        if (c->state_cap != cap_before) c->state_clean = false;
     }
     if ((size_t)NV + 1 > c->n_cap || !c->deg) {
         size_t a = 0, b = 0, d = 0, e = 0;
@@ -125,6 +127,7 @@ int ensure_workspace(acc_ctx *c, long long NV, long long state_words, long long 
     }
     if ((rc = grow(&c->tiles, &c->tiles_cap, (size_t)scan_tiles_needed(NV) + 1))) return rc;
     if ((rc = grow(&c->nbr, &c->nbr_cap, (size_t)(2 * arcs) + 1))) return rc;
+    if ((rc = grow(&c->occ, &c->occ_cap, (size_t)NV * (size_t)occ_words(max_n) + 1))) return rc;
     if (!c->info) {
         if (!ok(cudaMalloc(&c->info, sizeof(GraphInfo)))) return ACC_ERR_NOMEM;
         if (!ok(cudaMemset(c->info, 0, sizeof(GraphInfo)))) return ACC_ERR_CUDA;
@@ -152,8 +155,21 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     c->state_clean = false;  // until the closing clear below is enqueued
     // a buffer not known to be clean is swept whole (capacity, not just this
     // set's blocks): a later, larger set may use any part of it
-    int rc = launch_build_graph(gs, (long long)c->state_cap, c->state, clean, c->deg, c->lo, c->deg_in, c->nptr, c->tiles, c->nbr,
-                                c->label, c->info, status, reinterpret_cast<unsigned long long *>(counts),
+    BuildBufs bb;
+    bb.state = c->state;
+    bb.state_words = (long long)c->state_cap;
+    bb.state_clean = clean;
+    bb.deg = c->deg;
+    bb.lo = c->lo;
+    bb.label = c->label;
+    bb.deg_in = c->deg_in;
+    bb.nptr = c->nptr;
+    bb.tiles = c->tiles;
+    bb.nbr = c->nbr;
+    bb.occ = c->occ;
+    bb.occ_w = occ_words(max_n);
+    bb.info = c->info;
+    int rc = launch_build_graph(gs, bb, max_n, status, reinterpret_cast<unsigned long long *>(counts),
                                 (long long)gs.B * num_classes(k), relabel, c->num_sms, s);
     if (rc < 0) return rc;
     launches += rc;
@@ -188,7 +204,7 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
         launches += rc;
     }
     if (c->timing && !ok(cudaEventRecord(c->ev[2], s))) return ACC_ERR_CUDA;
-    rc = launch_clear_graph(gs, c->state, c->label, relabel, c->num_sms, s);
+    rc = launch_clear_graph(gs, c->state, c->occ, occ_words(max_n), c->num_sms, s);
     if (rc < 0) return rc;
     launches += rc;
     c->state_clean = true;
@@ -224,11 +240,13 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
     gs.one.col = col;
     gs.one.m = m;
     gs.one.soff = 0;
+    gs.one.moff = 0;
     gs.one.pitch = pitch;
     gs.one.n = n;
     gs.one.voff = 0;
     gs.B = 1;
     gs.NV = n;
+    gs.M = m;
     int *status = status_user ? status_user : c->status_dev;
     rc = run_set(c, gs, n, k, n >= kRelabelMinN, s, counts, status);
     if (rc) return rc;
@@ -243,6 +261,7 @@ long long ctx_footprint(const acc_ctx *c, long long n, long long m, int k) {
     const long long pitch = state_pitch((int)n);
     const long long warps = enum_grid_warps(k, c->num_sms);
     const long long bytes = n * pitch * 4 + 5 * 4 * (n + 1) + 8 * (n + 1) + 4 * (2 * m + 1) +
+                            4 * n * occ_words((int)n) +
                             (long long)kQueueCap * 16 + scratch_per_warp((int)n) * (warps > 0 ? warps : 0) * 4;
     return bytes + bytes / 4;
 }
@@ -314,6 +333,7 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaFree(c->label);
     cudaFree(c->deg_in);
     cudaFree(c->tiles);
+    cudaFree(c->occ);
     cudaFree(c->nbr);
     cudaFree(c->info);
     cudaFree(c->queue);
@@ -396,6 +416,7 @@ int acc_motif_batch_prepare(acc_ctx *c, const acc_graph_desc *graphs, int32_t B,
         mt.n = d.n;
         mt.pitch = state_pitch(d.n);
         mt.soff = words;
+        mt.moff = arcs;
         mt.voff = (int)NV;
         words += (long long)d.n * mt.pitch;
         NV += d.n;
@@ -416,6 +437,7 @@ int acc_motif_batch_prepare(acc_ctx *c, const acc_graph_desc *graphs, int32_t B,
     gs.gid = c->gid;
     gs.B = B;
     gs.NV = NV;
+    gs.M = arcs;
     if ((rc = launch_graph_ids(gs, c->gid, s)) < 0) return rc;
     if (!ok(cudaStreamSynchronize(s))) return ACC_ERR_CUDA;
     c->batch_set = gs;

@@ -54,6 +54,7 @@ struct GMeta {
     long long m;
     long long soff;
     long long pitch;
+    long long moff;           // first arc of the graph in the set's arc numbering
     int n;
     int voff;
 };
@@ -65,12 +66,27 @@ struct GSet {
     const int *gid;       // graph of each global vertex when B > 1
     int B;
     long long NV;         // total vertices
+    long long M;          // total arcs
     __device__ __forceinline__ GMeta meta(int g) const { return B == 1 ? one : many[g]; }
     __device__ __forceinline__ int graph_of(int v) const { return B == 1 ? 0 : gid[v]; }
 };
 
-// Sets with at most this many vertices scan their degrees in one block.
-constexpr long long kScanSingleMax = 1 << 17;
+// Sets with at most this many vertices scan their degrees in one block,
+// through shared memory; larger sets scan in tiles.
+constexpr long long kScanSingleMax = 1 << 15;
+// Graph sets whose graphs all have at most this many vertices renumber each
+// graph in one block with a shared-memory degree histogram.
+constexpr int kRelabelSmemMax = 1 << 15;
+
+// Occupancy bitmap of the pair-state rows: one bit per 32-word (128-byte)
+// chunk of a row, set by the ingest when it first writes a word of the chunk,
+// so the neighbour-list fill reads only chunks that hold neighbours.
+// Words of bitmap per row for graphs of up to max_n vertices.
+inline int occ_words(int max_n) {
+    const long long pitch = ((long long)max_n + 15) / 16;
+    const long long chunks = (pitch + 31) / 32;
+    return (int)((chunks + 31) / 32 > 0 ? (chunks + 31) / 32 : 1);
+}
 
 // Bit of the adjacency code for the arc from tuple slot i to slot j.
 __host__ __device__ constexpr int code_bit(int k, int i, int j) {
@@ -104,14 +120,26 @@ __device__ inline void set_status(int *status, int err) {
 // descending G* degree (label[v] = new global id of input vertex v), which
 // leaves the counts unchanged.  tile_scratch holds scan_tiles_needed(NV)
 // values.
-// state_words: the whole pair-state buffer, swept unless state_clean says it
-// is known to be all zero; deg_in: NV ints of scratch for the renumbering.
-int launch_build_graph(const GSet &gs, long long state_words, uint32_t *state, bool state_clean, int *deg, int *lo,
-                       int *deg_in, long long *nptr, long long *tile_scratch, uint32_t *nbr, int *label,
-                       GraphInfo *info, int *status, unsigned long long *counts, long long ncounts, bool relabel,
-                       int num_sms, cudaStream_t s);
-// Zero the pair-state words a build set, leaving the buffer all zero.
-int launch_clear_graph(const GSet &gs, uint32_t *state, const int *label, bool relabel, int num_sms, cudaStream_t s);
+// Device buffers of the graph builder (sizes for NV vertices, at most max_n
+// per graph).
+struct BuildBufs {
+    uint32_t *state;         // pair-state buffer of state_words words
+    long long state_words;   // swept whole unless state_clean
+    bool state_clean;        // known to be all zero
+    int *deg, *lo, *label;   // NV each
+    int *deg_in;             // NV: renumbering keys
+    long long *nptr;         // NV + 1
+    long long *tiles;        // scan_tiles_needed(NV) + 1
+    uint32_t *nbr;           // 2 |E*|
+    uint32_t *occ;           // NV * occ_words(max_n)
+    int occ_w;               // occ_words(max_n)
+    GraphInfo *info;
+};
+int launch_build_graph(const GSet &gs, const BuildBufs &b, int max_n, int *status, unsigned long long *counts,
+                       long long ncounts, bool relabel, int num_sms, cudaStream_t s);
+// Zero the pair-state chunks a build set (by its occupancy bitmap), leaving
+// the buffer all zero.
+int launch_clear_graph(const GSet &gs, uint32_t *state, const uint32_t *occ, int occ_w, int num_sms, cudaStream_t s);
 long long scan_tiles_needed(long long NV);
 // gid[v] for a set of several graphs (no launch for one graph).
 int launch_graph_ids(const GSet &gs, int *gid, cudaStream_t s);

@@ -32,6 +32,8 @@ struct acc_ctx {
     long long *tiles = nullptr;
     size_t tiles_cap = 0;
     uint32_t *nbr = nullptr;
+    uint32_t *occ = nullptr;  // pair-state row occupancy bitmaps
+    size_t occ_cap = 0;
     size_t nbr_cap = 0;
     GraphInfo *info = nullptr;
     uint4 *queue = nullptr;

@@ -14,12 +14,24 @@
 // by global vertex; neighbour entries and block rows/columns use local ids.
 //
 // The pair-state buffer is all zero between calls: a build sets only the
-// words its arcs touch and the call ends by clearing exactly those words
-// (k_clear_arcs), so no pass ever sweeps the whole n x n block.  G* degrees
+// words its arcs touch, marking their 128-byte chunks in a per-row
+// occupancy bitmap, and the call ends by zeroing the marked chunks
+// (k_clear_chunks; it reads neither the input nor the labels), so no pass
+// ever sweeps the whole n x n block.  G* degrees
 // come out of the ingest itself: of the atomics that touch the field of pair
 // {a, u} in row a (arc a -> u sets bit 0, arc u -> a sets bit 1 as its
 // mirror), exactly one finds the field still zero, and that one counts u as
 // a neighbour of a.  Repeated arcs therefore count once.
+//
+// The degree-descending renumbering only needs high-degree vertices first
+// (the counts do not depend on the numbering), so it orders by out- plus
+// in-degree taken straight from the CSR, before any pair state exists.
+//
+// Arc kernels run a thread per arc of the whole set: the arc's graph and row
+// are found by binary search (arc offsets of the graphs, then the graph's
+// rowptr), so a hub row costs no more than any other and ingest and clear
+// attribute every arc identically, malformed rows included (those are
+// reported by the ingest's row check).
 #include "common.cuh"
 
 namespace acc {
@@ -38,8 +50,8 @@ __device__ __forceinline__ int warp_excl_scan(int x, int lane, int *total) {
 }
 
 struct IntRanges {
-    int *p[3];
-    long long n[3];
+    int *p[4];
+    long long n[4];
 };
 
 __global__ void k_zero(uint4 *p, size_t n16, unsigned char *tail, size_t ntail, int *status,
@@ -50,91 +62,142 @@ __global__ void k_zero(uint4 *p, size_t n16, unsigned char *tail, size_t ntail, 
     if (i < ntail) tail[i] = 0;
     for (size_t j = i; j < (size_t)ncounts; j += stride) counts[j] = 0;
 #pragma unroll
-    for (int r = 0; r < 3; r++)
+    for (int r = 0; r < 4; r++)
         for (size_t j = i; j < (size_t)ints.n[r]; j += stride) ints.p[r][j] = 0;
     if (i == 0 && status) *status = 0;
 }
 
-// Warp per global row: set the pair-state bits of every arc, validating the
-// CSR on the way.  Invalid rows and arcs are skipped (never read out of
-// range) and reported through *status.  With `label` non-null, vertex x is
+// Graph of arc p of the set: the last graph whose first arc is at most p.
+__device__ __forceinline__ int graph_of_arc(const GSet &gs, long long p) {
+    if (gs.B == 1) return 0;
+    int lo = 0, hi = gs.B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (gs.many[mid].moff <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Row of local arc position p: the last row whose rowptr is at most p, or
+// -1 when there is none (rowptr[0] > p, or no rows: a malformed graph).
+__device__ __forceinline__ int row_of_arc(const GMeta &mt, long long p) {
+    if (mt.n <= 0 || mt.rowptr[0] > p) return -1;
+    int lo = 0, hi = mt.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (mt.rowptr[mid] <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// f(v, mt, lv, p) for every arc p of the set, thread per arc (grid-stride).
+template <typename F>
+__device__ __forceinline__ void for_each_arc(const GSet &gs, F f) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < gs.M; q += stride) {
+        const GMeta mt = gs.meta(graph_of_arc(gs, q));
+        const long long p = q - mt.moff;
+        const int lv = row_of_arc(mt, p);
+        if (lv >= 0) f(mt.voff + lv, mt, lv, p);
+    }
+}
+
+// Out- plus in-degree of every vertex from the CSR alone (repeated arcs and
+// both arcs of a mutual pair counted), the key of the renumbering.  Arcs
+// with a bad target are skipped here (k_ingest reports them).
+__global__ void k_arc_degrees(GSet gs, int *deg_io) {
+    for_each_arc(gs, [&](int v, const GMeta &mt, int lv, long long p) {
+        const int u0 = mt.col[p];
+        if (u0 < 0 || u0 >= mt.n || u0 == lv) return;
+        atomicAdd(&deg_io[v], 1);
+        atomicAdd(&deg_io[mt.voff + u0], 1);
+    });
+}
+
+// Set the pair-state bits of every arc, validating the CSR on the way:
+// malformed rows (rowptr decreasing or outside [0, m], rowptr[0] != 0,
+// rowptr[n] != m), targets out of range and self-loops are reported through
+// *status; nothing is read out of range.  With `label` non-null, vertex x is
 // written as label[x] (the renumbered block).  deg[voff + a] counts the G*
-// neighbours of block vertex a; lo (if non-null) those below a.
-__global__ void k_ingest(GSet gs, uint32_t *state, const int *__restrict__ label, int *status, int *deg, int *lo) {
-    const int lane = threadIdx.x & 31;
-    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long v = warp; v < gs.NV; v += nwarps) {
+// neighbours of block vertex a; lo (if non-null) those below a.  The atomic
+// that finds a state word empty marks the word's 32-word chunk in its row's
+// occupancy bitmap.
+__global__ void k_ingest(GSet gs, uint32_t *state, const int *__restrict__ label, int *status, int *deg, int *lo,
+                         uint32_t *occ, int occ_w) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < gs.NV; v += stride) {
         const GMeta mt = gs.meta(gs.graph_of((int)v));
         const int lv = (int)v - mt.voff;
-        if (lv == 0 && lane == 0 && (mt.rowptr[0] != 0 || mt.rowptr[mt.n] != mt.m))
+        const long long b = mt.rowptr[lv], e = mt.rowptr[lv + 1];
+        if (b < 0 || e < b || e > mt.m || (lv == 0 && b != 0) || (lv == mt.n - 1 && e != mt.m))
             set_status(status, ACC_ERR_INPUT);
-        const long long b = mt.rowptr[lv], e = mt.rowptr[lv + 1];
-        if (b < 0 || e < b || e > mt.m) {
-            if (lane == 0) set_status(status, ACC_ERR_INPUT);
-            continue;
+    }
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < gs.B; g += stride) {
+        const GMeta mt = gs.meta((int)g);  // arcs of a graph without vertices
+        if (mt.n == 0 && mt.m != 0) set_status(status, ACC_ERR_INPUT);
+    }
+    for_each_arc(gs, [&](int v, const GMeta &mt, int lv, long long p) {
+        const int u0 = mt.col[p];
+        if (u0 < 0 || u0 >= mt.n || u0 == lv) {
+            set_status(status, ACC_ERR_INPUT);
+            return;
         }
         const long long a = label ? label[v] - mt.voff : lv;
+        const int u = label ? label[mt.voff + u0] - mt.voff : u0;
         uint32_t *blk = state + mt.soff;
-        for (long long p = b + lane; p < e; p += kWarp) {
-            const int u0 = mt.col[p];
-            if (u0 < 0 || u0 >= mt.n || u0 == lv) {
-                set_status(status, ACC_ERR_INPUT);
-                continue;
-            }
-            const int u = label ? label[mt.voff + u0] - mt.voff : u0;
-            const int su = (u & 15) * 2, sa = (int)(a & 15) * 2;
-            const uint32_t oa = atomicOr(&blk[a * mt.pitch + (u >> 4)], 1u << su);
-            const uint32_t ou = atomicOr(&blk[(long long)u * mt.pitch + (a >> 4)], 2u << sa);
-            if (((oa >> su) & 3u) == 0u) {
-                atomicAdd(&deg[mt.voff + a], 1);
-                if (lo && u < a) atomicAdd(&lo[mt.voff + a], 1);
-            }
-            if (((ou >> sa) & 3u) == 0u) {
-                atomicAdd(&deg[mt.voff + u], 1);
-                if (lo && a < u) atomicAdd(&lo[mt.voff + u], 1);
-            }
+        const int su = (u & 15) * 2, sa = (int)(a & 15) * 2;
+        const uint32_t oa = atomicOr(&blk[a * mt.pitch + (u >> 4)], 1u << su);
+        const uint32_t ou = atomicOr(&blk[(long long)u * mt.pitch + (a >> 4)], 2u << sa);
+        if (oa == 0u) atomicOr(&occ[(mt.voff + a) * occ_w + (u >> 14)], 1u << ((u >> 9) & 31));
+        if (ou == 0u) atomicOr(&occ[((long long)mt.voff + u) * occ_w + (a >> 14)], 1u << ((a >> 9) & 31));
+        if (((oa >> su) & 3u) == 0u) {
+            atomicAdd(&deg[mt.voff + a], 1);
+            if (lo && u < a) atomicAdd(&lo[mt.voff + a], 1);
         }
-    }
+        if (((ou >> sa) & 3u) == 0u) {
+            atomicAdd(&deg[mt.voff + u], 1);
+            if (lo && a < u) atomicAdd(&lo[mt.voff + u], 1);
+        }
+    });
 }
 
-// Warp per global row: zero the pair-state words the arcs of the row set
-// (the same rows and arcs k_ingest accepted, under the same labels), and
-// with zero_deg the degree counters of the row's vertex.
-__global__ void k_clear_arcs(GSet gs, uint32_t *state, const int *__restrict__ label, int *deg, int *lo) {
+// Warp per global row: zero the 32-word chunks of the row that the occupancy
+// bitmap marks (every word the ingest set lies in one), lane j taking the
+// j-th marked chunk of a bitmap word.  The buffer is all zero afterwards.
+__global__ void k_clear_chunks(GSet gs, uint32_t *state, const uint32_t *__restrict__ occ, int occ_w) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long v = warp; v < gs.NV; v += nwarps) {
-        if (lane == 0 && deg) {
-            deg[v] = 0;
-            lo[v] = 0;
-        }
         const GMeta mt = gs.meta(gs.graph_of((int)v));
-        const int lv = (int)v - mt.voff;
-        const long long b = mt.rowptr[lv], e = mt.rowptr[lv + 1];
-        if (b < 0 || e < b || e > mt.m) continue;
-        const long long a = label ? label[v] - mt.voff : lv;
-        uint32_t *blk = state + mt.soff;
-        for (long long p = b + lane; p < e; p += kWarp) {
-            const int u0 = mt.col[p];
-            if (u0 < 0 || u0 >= mt.n || u0 == lv) continue;
-            const int u = label ? label[mt.voff + u0] - mt.voff : u0;
-            blk[a * mt.pitch + (u >> 4)] = 0u;
-            blk[(long long)u * mt.pitch + (a >> 4)] = 0u;
+        const int quads = (((mt.n + 15) >> 4) + 3) >> 2;
+        uint4 *row4 = reinterpret_cast<uint4 *>(state + mt.soff + (long long)(v - mt.voff) * mt.pitch);
+        for (int mw = 0; mw < occ_w; mw++) {
+            const uint32_t mask = occ[v * occ_w + mw];
+            if (lane < __popc(mask)) {
+                const int q0 = (mw * 32 + (int)__fns(mask, 0, lane + 1)) * 8;
+#pragma unroll
+                for (int g = 0; g < 8; g++)
+                    if (q0 + g < quads) row4[q0 + g] = make_uint4(0, 0, 0, 0);
+            }
         }
     }
 }
 
-// Per-graph degree histogram dhist[voff + degree] (for the renumbering).
-__global__ void k_dhist(GSet gs, const int *__restrict__ deg, int *dhist) {
+// Per-graph histogram dhist[voff + key] of the renumbering keys (clamped to
+// n - 1: the out- plus in-degree can exceed it).
+__global__ void k_dhist(GSet gs, const int *__restrict__ key, int *dhist) {
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < gs.NV;
-         v += (long long)gridDim.x * blockDim.x)
-        atomicAdd(&dhist[gs.meta(gs.graph_of((int)v)).voff + deg[v]], 1);
+         v += (long long)gridDim.x * blockDim.x) {
+        const GMeta mt = gs.meta(gs.graph_of((int)v));
+        atomicAdd(&dhist[mt.voff + min(key[v], mt.n - 1)], 1);
+    }
 }
 
 // Block per graph: start[voff + d] = vertices of the graph with degree above d.
-__global__ void k_desc_starts(GSet gs, const int *__restrict__ dhist, int *start) {
+__global__ void __launch_bounds__(1024) k_desc_starts(GSet gs, const int *__restrict__ dhist, int *start) {
     __shared__ int warp_sum[32];
     const GMeta mt = gs.meta(blockIdx.x);
     const int n = mt.n;
@@ -173,22 +236,40 @@ __global__ void k_desc_starts(GSet gs, const int *__restrict__ dhist, int *start
     }
 }
 
-// label[v] = voff + the next free position of v's degree class in its graph
-// (ties in any order).
-__global__ void k_desc_scatter(GSet gs, const int *__restrict__ deg, int *start, int *label) {
+// label[v] = voff + the next free position of v's key class in its graph
+// (ties in any order); also zeroes dhist (dead once the starts exist).
+__global__ void k_desc_scatter(GSet gs, const int *__restrict__ key, int *start, int *label, int *dhist) {
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < gs.NV;
          v += (long long)gridDim.x * blockDim.x) {
-        const int voff = gs.meta(gs.graph_of((int)v)).voff;
-        label[v] = voff + atomicAdd(&start[voff + deg[v]], 1);
+        const GMeta mt = gs.meta(gs.graph_of((int)v));
+        label[v] = mt.voff + atomicAdd(&start[mt.voff + min(key[v], mt.n - 1)], 1);
+        dhist[v] = 0;
     }
 }
 
 // Exclusive scan of the degrees into nptr, with the largest degree and the
-// reset of the work counters.  Small sets: one block.
-__global__ void k_scan_degrees(const int *__restrict__ deg, int n, long long *nptr, GraphInfo *info) {
+// reset of the work counters.  Small sets: one block, the degrees staged in
+// shared memory by coalesced loads (n ints of dynamic shared memory).
+__global__ void __launch_bounds__(1024) k_scan_degrees(const int *__restrict__ deg_g, int n, long long *nptr, GraphInfo *info) {
+    extern __shared__ int deg[];
     __shared__ long long warp_sum[32];
     __shared__ int warp_max[32];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    {
+        constexpr int kPer = (int)(kScanSingleMax / 1024);  // n <= kPer * blockDim.x
+        int dv[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; j++) {
+            const int i = t + j * (int)blockDim.x;
+            dv[j] = i < n ? deg_g[i] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; j++) {
+            const int i = t + j * (int)blockDim.x;
+            if (i < n) deg[i] = dv[j];
+        }
+    }
+    __syncthreads();
     const int nthreads = blockDim.x;
     const int chunk = (n + nthreads - 1) / nthreads;
     const int b = min(n, t * chunk), e = min(n, b + chunk);
@@ -229,11 +310,16 @@ __global__ void k_scan_degrees(const int *__restrict__ deg, int n, long long *np
         }
     }
     __syncthreads();
-    long long run = warp_sum[wid] + (incl - s);
+    // offsets back into shared memory (below 2^32: they count 2 |E*| < 2^32
+    // entries), then written out coalesced
+    unsigned run = (unsigned)(warp_sum[wid] + (incl - s));
     for (int i = b; i < e; i++) {
-        nptr[i] = run;
-        run += deg[i];
+        const int d = deg[i];
+        deg[i] = (int)run;
+        run += (unsigned)d;
     }
+    __syncthreads();
+    for (int i = t; i < n; i += blockDim.x) nptr[i] = (long long)(unsigned)deg[i];
     if (t == 0) {
         info->maxdeg = warp_max[0];
         info->queue_tail = 0;
@@ -249,7 +335,7 @@ __global__ void k_scan_degrees(const int *__restrict__ deg, int n, long long *np
 // own scan plus its offset.  The caller zeroes info->maxdeg first.
 constexpr int kScanTile = 4096;
 
-__global__ void k_scan_tiles(const int *__restrict__ deg, int n, long long *tile_sum, GraphInfo *info) {
+__global__ void __launch_bounds__(1024) k_scan_tiles(const int *__restrict__ deg, int n, long long *tile_sum, GraphInfo *info) {
     __shared__ long long ws[32];
     __shared__ int wm[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -285,7 +371,7 @@ __global__ void k_scan_tiles(const int *__restrict__ deg, int n, long long *tile
     }
 }
 
-__global__ void k_scan_top(long long *tile_sum, int ntiles, long long *nptr, int n, GraphInfo *info) {
+__global__ void __launch_bounds__(1024) k_scan_top(long long *tile_sum, int ntiles, long long *nptr, int n, GraphInfo *info) {
     __shared__ long long warp_sum[32];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int chunk = (ntiles + blockDim.x - 1) / blockDim.x;
@@ -331,7 +417,7 @@ __global__ void k_scan_top(long long *tile_sum, int ntiles, long long *nptr, int
     }
 }
 
-__global__ void k_scan_apply(const int *__restrict__ deg, int n, const long long *__restrict__ tile_off,
+__global__ void __launch_bounds__(1024) k_scan_apply(const int *__restrict__ deg, int n, const long long *__restrict__ tile_off,
                              long long *nptr) {
     __shared__ long long warp_sum[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -372,46 +458,116 @@ __global__ void k_scan_apply(const int *__restrict__ deg, int n, const long long
 }
 
 // Warp per global row: write the sorted neighbour entries (u << 2) | state(v, u)
-// with local u.  Each lane reads 16 bytes (64 columns) per step; steps where
-// the whole warp's 2048 columns are empty are skipped after one ballot.
-__global__ void k_fill(GSet gs, const uint32_t *__restrict__ state, const long long *__restrict__ nptr,
-                       uint32_t *nbr) {
+// with local u, reading only the 32-word chunks the occupancy bitmap marks:
+// lane j takes the j-th marked chunk of a bitmap word (all in one round).
+__global__ void k_fill(GSet gs, const uint32_t *__restrict__ state, const uint32_t *__restrict__ occ, int occ_w,
+                       const long long *__restrict__ nptr, uint32_t *nbr) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long v = warp; v < gs.NV; v += nwarps) {
         const GMeta mt = gs.meta(gs.graph_of((int)v));
         const int lv = (int)v - mt.voff;
-        const int quads = (((mt.n + 15) >> 4) + 3) >> 2;  // within the pitch (a multiple of 4 words)
+        const int quads = (((mt.n + 15) >> 4) + 3) >> 2;  // 16-byte groups within the pitch
         const uint4 *row4 = reinterpret_cast<const uint4 *>(state + mt.soff + (long long)lv * mt.pitch);
         long long base = nptr[v];
-        for (int q0 = 0; q0 < quads; q0 += kWarp) {
-            const int q = q0 + lane;
-            const uint4 x4 = q < quads ? row4[q] : make_uint4(0, 0, 0, 0);
-            const uint32_t xs[4] = {x4.x, x4.y, x4.z, x4.w};
-            uint32_t nz[4];
-            int c = 0;
+        for (int mw = 0; mw < occ_w; mw++) {
+            const uint32_t mask = occ[v * occ_w + mw];
+            const int nch = __popc(mask);
+            uint32_t xs[32];
+            int cnt = 0;
+            int q0 = 0;
+            if (lane < nch) {
+                q0 = (mw * 32 + (int)__fns(mask, 0, lane + 1)) * 8;  // first 16-byte group of the chunk
 #pragma unroll
-            for (int t = 0; t < 4; t++) {
-                nz[t] = (xs[t] | (xs[t] >> 1)) & 0x55555555u;
-                c += __popc(nz[t]);
+                for (int g = 0; g < 8; g++) {
+                    const uint4 x4 = q0 + g < quads ? row4[q0 + g] : make_uint4(0, 0, 0, 0);
+                    xs[4 * g] = x4.x;
+                    xs[4 * g + 1] = x4.y;
+                    xs[4 * g + 2] = x4.z;
+                    xs[4 * g + 3] = x4.w;
+                }
+#pragma unroll
+                for (int t = 0; t < 32; t++) cnt += __popc((xs[t] | (xs[t] >> 1)) & 0x55555555u);
             }
-            if (!__ballot_sync(kFull, c != 0)) continue;
             int total;
-            const int off = warp_excl_scan(c, lane, &total);
-            long long pos = base + off;
+            const int off = warp_excl_scan(cnt, lane, &total);
+            if (cnt) {
+                long long pos = base + off;
 #pragma unroll
-            for (int t = 0; t < 4; t++) {
-                uint32_t m = nz[t];
-                while (m) {
-                    const int bit = __ffs(m) - 1;
-                    const uint32_t u = (uint32_t)((q * 4 + t) * 16 + (bit >> 1));
-                    nbr[pos++] = (u << 2) | ((xs[t] >> bit) & 3u);
-                    m &= m - 1;
+                for (int t = 0; t < 32; t++) {
+                    uint32_t nz = (xs[t] | (xs[t] >> 1)) & 0x55555555u;
+                    while (nz) {
+                        const int bit = __ffs(nz) - 1;
+                        nbr[pos++] = ((uint32_t)((q0 * 4 + t) * 16 + (bit >> 1)) << 2) | ((xs[t] >> bit) & 3u);
+                        nz &= nz - 1;
+                    }
                 }
             }
             base += total;
         }
+    }
+}
+
+// Block per graph (every graph of the set has at most kRelabelSmemMax
+// vertices): renumber the graph's vertices by descending key, ties in any
+// order, with the key histogram and its starts in shared memory.
+__global__ void __launch_bounds__(1024) k_relabel_graph(GSet gs, const int *__restrict__ key, int *label) {
+    extern __shared__ int h[];
+    __shared__ int warp_sum[32];
+    const GMeta mt = gs.meta(blockIdx.x);
+    const int n = mt.n;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    // this thread's keys, loaded in one batch (n <= 32 * blockDim.x)
+    constexpr int kPer = kRelabelSmemMax / 1024;
+    int kv[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; j++) {
+        const int v = t + j * (int)blockDim.x;
+        kv[j] = v < n ? min(key[mt.voff + v], n - 1) : 0;
+    }
+    for (int i = t; i < n; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPer; j++)
+        if (t + j * (int)blockDim.x < n) atomicAdd(&h[kv[j]], 1);
+    __syncthreads();
+    // h[d] <- vertices with key above d (position i of the scan is key n-1-i)
+    const int chunk = (n + blockDim.x - 1) / blockDim.x;
+    const int b = min(n, t * chunk), e = min(n, b + chunk);
+    int sum = 0;
+    for (int i = b; i < e; i++) sum += h[n - 1 - i];
+    int incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) warp_sum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        const int ws = lane < nw ? warp_sum[lane] : 0;
+        int wi = ws;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(kFull, wi, d);
+            if (lane >= d) wi += y;
+        }
+        if (lane < nw) warp_sum[lane] = wi - ws;
+    }
+    __syncthreads();
+    int run = warp_sum[wid] + (incl - sum);
+    for (int i = b; i < e; i++) {
+        const int c = h[n - 1 - i];
+        h[n - 1 - i] = run;
+        run += c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPer; j++) {
+        const int v = t + j * (int)blockDim.x;
+        if (v < n) label[mt.voff + v] = mt.voff + atomicAdd(&h[kv[j]], 1);
     }
 }
 
@@ -422,6 +578,7 @@ __global__ void k_graph_ids(GSet gs, int *gid) {
 }
 
 __global__ void k_reset_maxdeg(GraphInfo *info) { info->maxdeg = 0; }
+
 
 int grid_for(long long work_items, int per_block, int num_sms) {
     long long b = (work_items + per_block - 1) / per_block;
@@ -435,7 +592,7 @@ int grid_for(long long work_items, int per_block, int num_sms) {
 
 int launch_zero(void *p, size_t bytes, int num_sms, cudaStream_t s, int *status, unsigned long long *counts,
                 long long ncounts, int *ints, long long nints) {
-    IntRanges r = {{ints, nullptr, nullptr}, {ints ? nints : 0, 0, 0}};
+    IntRanges r = {{ints, nullptr, nullptr, nullptr}, {ints ? nints : 0, 0, 0, 0}};
     const size_t n16 = bytes / 16, ntail = bytes % 16;
     const int grid = grid_for((long long)(n16 > 0 ? n16 : 1), 256 * 4, num_sms);
     k_zero<<<grid, 256, 0, s>>>(reinterpret_cast<uint4 *>(p), n16,
@@ -451,61 +608,74 @@ int launch_graph_ids(const GSet &gs, int *gid, cudaStream_t s) {
 
 long long scan_tiles_needed(long long NV) { return NV <= kScanSingleMax ? 0 : (NV + kScanTile - 1) / kScanTile; }
 
-int launch_build_graph(const GSet &gs, long long state_words, uint32_t *state, bool state_clean, int *deg, int *lo,
-                       int *deg_in, long long *nptr, long long *tile_scratch, uint32_t *nbr, int *label,
-                       GraphInfo *info, int *status, unsigned long long *counts, long long ncounts, bool relabel,
-                       int num_sms, cudaStream_t s) {
+int launch_build_graph(const GSet &gs, const BuildBufs &bb, int max_n, int *status, unsigned long long *counts,
+                       long long ncounts, bool relabel, int num_sms, cudaStream_t s) {
+    static bool smem_opt_in = false;
+    if (!smem_opt_in) {
+        if (cudaFuncSetAttribute(k_scan_degrees, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kScanSingleMax * 4)) != cudaSuccess ||
+            cudaFuncSetAttribute(k_relabel_graph, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kRelabelSmemMax * 4) != cudaSuccess)
+            return ACC_ERR_CUDA;
+        smem_opt_in = true;
+    }
     int launches = 0;
     const long long NV = gs.NV;
     const int rows_grid = grid_for(NV * kWarp, 256, num_sms);
-    // zero the counts, the status word, the degree counters and, unless the
-    // previous call left it clean, the pair-state buffer
+    const int arcs_grid = grid_for(max(gs.M, NV), 256, num_sms);
+    // zero the counts, the status word, the degree counters, the occupancy
+    // bitmap and, unless the previous call left it clean, the pair-state buffer
     {
-        const size_t bytes = state_clean ? 0 : (size_t)state_words * 4;
-        IntRanges r = {{deg, lo, deg_in}, {NV, NV, relabel ? NV : 0}};
+        const size_t bytes = bb.state_clean ? 0 : (size_t)bb.state_words * 4;
+        const long long nocc = NV * bb.occ_w;
+        IntRanges r = {{bb.deg, bb.lo, bb.deg_in, reinterpret_cast<int *>(bb.occ)},
+                       {NV, NV, relabel ? NV : 0, nocc}};
         const size_t n16 = bytes / 16, ntail = bytes % 16;
-        const long long items = (long long)max((size_t)1, max(n16, (size_t)max(NV, ncounts)));
-        k_zero<<<grid_for(items, 256 * 4, num_sms), 256, 0, s>>>(reinterpret_cast<uint4 *>(state), n16,
-                                                                 reinterpret_cast<unsigned char *>(state) + n16 * 16,
+        const long long items = (long long)max((size_t)1, max(n16, (size_t)max(max(NV, ncounts), nocc)));
+        k_zero<<<grid_for(items, 256 * 4, num_sms), 256, 0, s>>>(reinterpret_cast<uint4 *>(bb.state), n16,
+                                                                 reinterpret_cast<unsigned char *>(bb.state) + n16 * 16,
                                                                  ntail, status, counts, ncounts, r);
         launches++;
     }
     if (relabel) {
-        // G* degrees under the input labels; each graph's vertices renumbered
-        // by descending degree; the arcs' words cleared and the block rebuilt
-        int *dhist = lo;  // zeroed above, cleared again by k_clear_arcs
-        int *start = reinterpret_cast<int *>(nptr);
-        k_ingest<<<rows_grid, 256, 0, s>>>(gs, state, nullptr, status, deg_in, nullptr);
-        k_dhist<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, deg_in, dhist);
-        k_desc_starts<<<gs.B, 1024, 0, s>>>(gs, dhist, start);
-        k_desc_scatter<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, deg_in, start, label);
-        k_clear_arcs<<<rows_grid, 256, 0, s>>>(gs, state, nullptr, deg, lo);
-        k_ingest<<<rows_grid, 256, 0, s>>>(gs, state, label, nullptr, deg, lo);
-        launches += 6;
-    } else {
-        k_ingest<<<rows_grid, 256, 0, s>>>(gs, state, nullptr, status, deg, lo);
+        // each graph's vertices renumbered by descending out- plus in-degree,
+        // then the block built under the new ids
+        k_arc_degrees<<<arcs_grid, 256, 0, s>>>(gs, bb.deg_in);
         launches++;
+        if (max_n <= kRelabelSmemMax) {
+            k_relabel_graph<<<gs.B, 1024, (size_t)max_n * 4, s>>>(gs, bb.deg_in, bb.label);
+            launches++;
+        } else {
+            int *dhist = bb.deg;  // zeroed above, zeroed again by k_desc_scatter
+            int *start = reinterpret_cast<int *>(bb.nptr);
+            k_dhist<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, bb.deg_in, dhist);
+            k_desc_starts<<<gs.B, 1024, 0, s>>>(gs, dhist, start);
+            k_desc_scatter<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, bb.deg_in, start, bb.label, dhist);
+            launches += 3;
+        }
     }
+    k_ingest<<<arcs_grid, 256, 0, s>>>(gs, bb.state, relabel ? bb.label : nullptr, status, bb.deg, bb.lo, bb.occ,
+                                       bb.occ_w);
+    launches++;
     if (NV <= kScanSingleMax) {
-        k_scan_degrees<<<1, 1024, 0, s>>>(deg, (int)NV, nptr, info);
+        k_scan_degrees<<<1, 1024, (size_t)(NV > 0 ? NV : 1) * 4, s>>>(bb.deg, (int)NV, bb.nptr, bb.info);
         launches++;
     } else {
         const int ntiles = (int)scan_tiles_needed(NV);
-        k_reset_maxdeg<<<1, 1, 0, s>>>(info);
-        k_scan_tiles<<<ntiles, 1024, 0, s>>>(deg, (int)NV, tile_scratch, info);
-        k_scan_top<<<1, 1024, 0, s>>>(tile_scratch, ntiles, nptr, (int)NV, info);
-        k_scan_apply<<<ntiles, 1024, 0, s>>>(deg, (int)NV, tile_scratch, nptr);
+        k_reset_maxdeg<<<1, 1, 0, s>>>(bb.info);
+        k_scan_tiles<<<ntiles, 1024, 0, s>>>(bb.deg, (int)NV, bb.tiles, bb.info);
+        k_scan_top<<<1, 1024, 0, s>>>(bb.tiles, ntiles, bb.nptr, (int)NV, bb.info);
+        k_scan_apply<<<ntiles, 1024, 0, s>>>(bb.deg, (int)NV, bb.tiles, bb.nptr);
         launches += 4;
     }
-    k_fill<<<rows_grid, 256, 0, s>>>(gs, state, nptr, nbr);
+    k_fill<<<rows_grid, 256, 0, s>>>(gs, bb.state, bb.occ, bb.occ_w, bb.nptr, bb.nbr);
     launches++;
     return cudaGetLastError() == cudaSuccess ? launches : ACC_ERR_CUDA;
 }
 
-int launch_clear_graph(const GSet &gs, uint32_t *state, const int *label, bool relabel, int num_sms, cudaStream_t s) {
+int launch_clear_graph(const GSet &gs, uint32_t *state, const uint32_t *occ, int occ_w, int num_sms, cudaStream_t s) {
     if (gs.NV == 0) return 0;
-    k_clear_arcs<<<grid_for(gs.NV * kWarp, 256, num_sms), 256, 0, s>>>(gs, state, relabel ? label : nullptr, nullptr,
-                                                                       nullptr);
+    k_clear_chunks<<<grid_for(gs.NV * kWarp, 256, num_sms), 256, 0, s>>>(gs, state, occ, occ_w);
     return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
 

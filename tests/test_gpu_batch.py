@@ -77,7 +77,8 @@ def test_batch_single_graph_and_singles_agree(counter):
     good = (5, np.array([0, 1], np.int32), np.array([1, 2], np.int32))
     bad = (5, np.array([0, 1], np.int32), np.array([1, 1], np.int32))
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
-    counter.prepare_batch(to_device([good, bad]), 3)
+    gb = to_device([good, bad])  # alive until the run is done
+    counter.prepare_batch(gb, 3)
     counter.run_batch(status=st)
     torch.cuda.synchronize()
     assert int(st.item()) == -2

@@ -186,6 +186,14 @@ def test_repeated_arcs_relabelled_and_buffer_reuse(counter, k):
     assert counter.count(r_dev, c_dev, g.n, k).cpu().numpy().tolist() == want.tolist()
 
 
+def test_large_graph_paths(counter):
+    """n = 40000: the renumbering without the shared-memory histogram, the
+    tiled degree scan and three occupancy words per row."""
+    g = synth.chung_lu(40000, 160000, 2.2, 300, 10, 73)
+    want = oracle.count(g.n, g.src, g.dst, 3, threads=oracle.max_threads())
+    assert gpu_count(counter, g.n, g.src, g.dst, 3).tolist() == want.tolist()
+
+
 def test_malformed_input(counter):
     import torch
     import paper_1203_3415_gb300 as p
