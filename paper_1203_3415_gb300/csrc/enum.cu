@@ -130,7 +130,10 @@ __device__ __forceinline__ GView view_of(const EnumArgs &a, const GMeta &mt) {
 // First position of N*(x) (entries (u << 2) | s, sorted) with u > root.
 __device__ __forceinline__ int first_above(const uint32_t *__restrict__ nbr, long long base, int d, uint32_t root) {
     const uint32_t key = (root + 1u) << 2;
-    int lo = 0, hi = d;
+    // under the degree-descending numbering most lists lie wholly above
+    // the root: one load settles them
+    if (d == 0 || __ldg(nbr + base) >= key) return 0;
+    int lo = 1, hi = d;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (__ldg(nbr + base + mid) < key) lo = mid + 1;
@@ -486,14 +489,20 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
         }
         __syncwarp();
         // every unordered pair of members, as if not adjacent
-        for (int ia = 0; ia < ng; ia++) {
+        // pair q of the triangle ia <= ib < ng, rows of ng - ia entries
+        // starting at off(ia) = ia ng - ia (ia - 1) / 2, spread over the lanes
+        const int npairs = ng * (ng + 1) / 2;
+        const int w = 2 * ng + 1;
+        for (int q = lane; q < npairs; q += kWarp) {
+            int ia = (int)(0.5f * ((float)w - sqrtf((float)(w * w - 8 * q))));
+            ia = max(0, min(ia, ng - 1));
+            if (ia * ng - ia * (ia - 1) / 2 > q) ia--;
+            else if (ia + 1 < ng && (ia + 1) * ng - (ia + 1) * ia / 2 <= q) ia++;
+            const int ib = ia + (q - (ia * ng - ia * (ia - 1) / 2));
             const uint32_t ga = glist[2 * ia], ca = glist[2 * ia + 1];
-            const uint32_t ra = pcode | (ga << L::SH_ROW);
-            for (int ib = ia + lane; ib < ng; ib += kWarp) {
-                const uint32_t gb = glist[2 * ib], cb = glist[2 * ib + 1];
-                const long long pairs = ib == ia ? (long long)ca * (ca - 1) / 2 : (long long)ca * cb;
-                if (pairs) sink.add(sink.cls_of(ra | gb), pairs);
-            }
+            const uint32_t gb = glist[2 * ib], cb = glist[2 * ib + 1];
+            const long long pairs = ib == ia ? (long long)ca * (ca - 1) / 2 : (long long)ca * cb;
+            if (pairs) sink.add(sink.cls_of(pcode | (ga << L::SH_ROW) | gb), pairs);
         }
         account_moved(sink, lane);
     }
