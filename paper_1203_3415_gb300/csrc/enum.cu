@@ -49,10 +49,10 @@ namespace {
 #define ACC_GRAB 1
 #endif
 #ifndef ACC_LIGHT
-#define ACC_LIGHT (1 << 12)
+#define ACC_LIGHT (1 << 11)
 #endif
 #ifndef ACC_TARGET
-#define ACC_TARGET (1 << 14)
+#define ACC_TARGET (1 << 12)
 #endif
 #ifndef ACC_UNROLL
 #define ACC_UNROLL 4
