@@ -43,7 +43,7 @@ namespace {
 
 // Tuning knobs (compile-time; -D overrides for sweeps).
 #ifndef ACC_CAP34
-#define ACC_CAP34 1024
+#define ACC_CAP34 512
 #endif
 #ifndef ACC_GRAB
 #define ACC_GRAB 1
@@ -63,6 +63,12 @@ namespace {
 #ifndef ACC_CUNROLL
 #define ACC_CUNROLL 4  // count mode: neighbour entries in flight per lane
 #endif
+#ifndef ACC_CAP5
+#define ACC_CAP5 64  // per-warp shared-memory list entries (each of two lists), k = 5
+#endif
+#ifndef ACC_MINB5
+#define ACC_MINB5 4  // resident blocks per SM the k = 5 kernels are compiled for
+#endif
 #ifndef ACC_MINB34
 #define ACC_MINB34 4  // resident blocks per SM the k = 3, 4 leaf kernels are compiled for
 #endif
@@ -70,7 +76,7 @@ namespace {
 #define ACC_MINB34C 4  // the same for the k = 3, 4 count-mode kernels
 #endif
 constexpr int kCap34 = ACC_CAP34;         // per-warp shared extension entries, k = 3, 4
-constexpr int kCap5 = 384;                // per-warp shared entries per list, k = 5
+constexpr int kCap5 = ACC_CAP5;           // per-warp shared entries per list, k = 5
 constexpr int kGrab = ACC_GRAB;           // base units per atomic grab
 constexpr long long kLight = ACC_LIGHT;   // phase 1 runs units up to this much work
 constexpr long long kTarget = ACC_TARGET; // work per queued chunk
@@ -886,7 +892,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
 // One instantiation per phase, so each is register-allocated for its own path
 // (phase 1: the unit loop, work estimates and queueing; phase 2: the queue).
 template <int K, bool COUNT, int PHASE>
-__global__ void __launch_bounds__(kThreads, K == 5 ? 3 : (COUNT ? ACC_MINB34C : ACC_MINB34)) k_enum(EnumArgs a) {
+__global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? ACC_MINB34C : ACC_MINB34)) k_enum(EnumArgs a) {
     using L = Layout<K>;
     extern __shared__ __align__(16) unsigned char smem[];
     int16_t *lut_s = reinterpret_cast<int16_t *>(smem);
