@@ -189,23 +189,33 @@ def kernel_source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, mode: str):
-    """Bytes per enumeration stage from profiles/enum_<workload>_traffic.txt,
-    when it was taken on the current kernel source in this mode; else None."""
+def profiled_counters(workload: str, mode: str):
+    """(dram bytes per enumeration stage, ncu counters) from
+    profiles/enum_<workload>_traffic.txt, when it was taken on the current
+    kernel source in this mode; else (None, None)."""
     path = os.path.join(ROOT, "profiles", f"enum_{workload}_traffic.txt")
     if not os.path.exists(path):
-        return None
+        return None, None
     kv = {}
     for line in open(path):
         if ":" in line and not line.startswith("#"):
             key, _, val = line.partition(":")
             kv[key.strip()] = val.strip()
     if kv.get("source_digest") != kernel_source_digest() or kv.get("mode", "count") != mode:
-        return None
+        return None, None
     try:
-        return float(kv["dram_bytes_per_stage"])
+        traffic = float(kv["dram_bytes_per_stage"])
     except (KeyError, ValueError):
-        return None
+        traffic = None
+    counters = {}
+    for key in ("issue_active_pct", "lts_throughput_pct", "l1tex_throughput_pct", "warps_active_pct"):
+        if key in kv:
+            counters[key] = [float(x) for x in kv[key].split(",")]
+    if counters:
+        counters["phases"] = ["phase 1", "phase 2"]
+        counters["source"] = "ncu --set full capture in profiles/, % of peak sustained"
+    return traffic, (counters or None)
+
 
 
 def golden_counts(workload: str):
@@ -384,7 +394,7 @@ def run_ours(args):
         units, per_unit = n_k, ops_per_subgraph(k)
         unit_name = "classified subgraphs"
     achieved = per_unit * units / enum_s / 1e9
-    traffic = profiled_traffic(args.workload, args.mode)
+    traffic, counters = profiled_counters(args.workload, args.mode)
 
     # CPU baseline: the oracle on this host's cores, the whole workload
     cpu = None
@@ -409,7 +419,9 @@ def run_ours(args):
                      "peak_source": peak_src,
                      # what a kernel visiting every leaf would have to sustain for this rate
                      "leaf_equivalent": {"ops_per_subgraph": ops_per_subgraph(k), "achieved": leaf_achieved,
-                                         "frac": leaf_achieved / peak_gops}},
+                                         "frac": leaf_achieved / peak_gops},
+                     # measured issue-slot and cache throughput of the same kernel (ncu)
+                     "ncu_counters": counters},
         "cpu_baseline": cpu,
         "e2e": {"value": whole_job_rate(e2e_units, e2e_max), "unit": UNIT,
                 "h2d_bytes_per_step": int(rowptr_np.nbytes + col_np.nbytes),
