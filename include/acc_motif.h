@@ -171,6 +171,17 @@ ACC_API int acc_motif_count_batch(acc_ctx *ctx, const acc_graph_desc *h_graphs, 
                                   int64_t *d_counts, int32_t *d_status);
 
 /*
+ * Tune the schedule for the prepared batch: runs the batch once for each of
+ * a fixed set of candidate (light, target) pairs, timed with CUDA events on
+ * `stream`, and keeps the fastest in the context (acc_ctx_set_schedule).
+ * Waits for the device.  h_light, h_target, h_ms (nullable) receive the
+ * chosen pair and its time.  Errors: ACC_ERR_ARG (no prepared batch), any
+ * error a batch run returns (the previous schedule is then kept).
+ */
+ACC_API int acc_motif_batch_autotune(acc_ctx *ctx, void *stream, int64_t *h_light, int64_t *h_target,
+                                     float *h_ms);
+
+/*
  * Z-scores of class counts against randomised copies (significance step of
  * the motif pipeline; the paper gives no formula).  d_counts is device
  * int64[groups][group_size][num_classes(k)]: entry 0 of each group is the
@@ -286,6 +297,19 @@ ACC_API int acc_motif_last_stats(acc_ctx *ctx, int64_t *h_stats);
 #define ACC_MODE_COUNT 0
 #define ACC_MODE_ENUMERATE 1
 ACC_API int acc_ctx_set_mode(acc_ctx *ctx, int mode);
+
+/*
+ * Work schedule of the enumeration (not in the paper: how the ESU units are
+ * spread over the GPU).  A unit (a root, or a root and one neighbour) whose
+ * estimated work is at most `light` runs whole on one warp; a heavier one is
+ * cut into row tiles of about `target` work that any warp may take.  Work is
+ * counted in scanned neighbour entries (count mode) or leaves (enumerate
+ * mode).  0 selects the built-in default; values above 2^40 or negative are
+ * ACC_ERR_ARG.  The schedule changes speed only, never the counts.
+ * acc_ctx_get_schedule reports the values in effect.
+ */
+ACC_API int acc_ctx_set_schedule(acc_ctx *ctx, int64_t light, int64_t target);
+ACC_API int acc_ctx_get_schedule(acc_ctx *ctx, int64_t *light, int64_t *target);
 
 /*
  * Stage timing.  With timing on (on != 0), every acc_motif_count records CUDA

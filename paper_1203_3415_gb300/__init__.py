@@ -39,7 +39,7 @@ EXPORTS = (
     "acc_motif_copy_table", "acc_motif_last_stats", "acc_ctx_set_timing", "acc_motif_last_timing",
     "acc_motif_build_table_static", "acc_ctx_set_mode", "acc_server_create", "acc_server_destroy", "acc_server_add_graph",
     "acc_server_reserve", "acc_server_submit", "acc_server_progress", "acc_server_poll", "acc_server_drain",
-    "acc_server_set_policy",
+    "acc_server_set_policy", "acc_ctx_set_schedule", "acc_ctx_get_schedule", "acc_motif_batch_autotune",
 )
 ACC_REQ_QUEUED, ACC_REQ_RUNNING, ACC_REQ_DONE = 0, 1, 2
 ACC_SERVE_FIFO, ACC_SERVE_SHORTEST = 0, 1
@@ -83,6 +83,10 @@ def _load():
     lib.acc_server_poll.argtypes = [vp, i64, ctypes.POINTER(i32), vp, ctypes.POINTER(ctypes.c_double)]
     lib.acc_server_drain.argtypes = [vp]
     lib.acc_server_set_policy.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+    lib.acc_ctx_set_schedule.argtypes = [vp, i64, i64]
+    lib.acc_ctx_get_schedule.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.acc_motif_batch_autotune.argtypes = [vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                             ctypes.POINTER(ctypes.c_float)]
     return lib
 
 
@@ -253,6 +257,25 @@ def acc_server_set_policy(srv: int, policy: int, aging_s: float) -> int:
     return _L().acc_server_set_policy(srv, policy, aging_s)
 
 
+def acc_ctx_set_schedule(ctx: int, light: int, target: int) -> int:
+    return _L().acc_ctx_set_schedule(ctx, light, target)
+
+
+def acc_ctx_get_schedule(ctx: int):
+    """(light, target) in effect."""
+    light, target = ctypes.c_int64(), ctypes.c_int64()
+    _check(_L().acc_ctx_get_schedule(ctx, ctypes.byref(light), ctypes.byref(target)), "acc_ctx_get_schedule")
+    return light.value, target.value
+
+
+def acc_motif_batch_autotune(ctx: int, stream: int):
+    """(light, target, ms) chosen for the prepared batch."""
+    light, target, ms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_float()
+    _check(_L().acc_motif_batch_autotune(ctx, stream, ctypes.byref(light), ctypes.byref(target), ctypes.byref(ms)),
+           "acc_motif_batch_autotune")
+    return light.value, target.value, ms.value
+
+
 class Server:
     """Request server with continuous batching (see include/acc_motif.h)."""
 
@@ -413,6 +436,20 @@ class Counter:
         """ACC_MODE_COUNT (default) or ACC_MODE_ENUMERATE; same counts."""
         _check(acc_ctx_set_mode(self.ctx, mode), "acc_ctx_set_mode")
         self.mode = mode
+
+    def set_schedule(self, light: int = 0, target: int = 0):
+        """Enumeration work schedule (0: default); see acc_ctx_set_schedule."""
+        _check(acc_ctx_set_schedule(self.ctx, light, target), "acc_ctx_set_schedule")
+
+    def schedule(self):
+        """(light, target) in effect."""
+        return acc_ctx_get_schedule(self.ctx)
+
+    def autotune_batch(self, stream=None):
+        """Pick the fastest schedule for the prepared batch: (light, target, ms)."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return acc_motif_batch_autotune(self.ctx, s.cuda_stream)
 
     def set_timing(self, on: bool = True):
         _check(acc_ctx_set_timing(self.ctx, 1 if on else 0), "acc_ctx_set_timing")

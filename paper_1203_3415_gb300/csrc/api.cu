@@ -189,6 +189,8 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     a.scratch = c->scratch;
     a.scratch_per_warp = scratch_per_warp(max_n);
     a.mode = c->mode;
+    a.light = c->sched_light > 0 ? c->sched_light : enum_default_light();
+    a.target = c->sched_target > 0 ? c->sched_target : enum_default_target();
     a.counts = reinterpret_cast<unsigned long long *>(counts);
     a.status = status;
     const bool any = gs.NV > 0;
@@ -528,6 +530,88 @@ int acc_motif_last_stats(acc_ctx *c, int64_t *h_stats) {
 int acc_ctx_set_mode(acc_ctx *c, int mode) {
     if (!c || (mode != ACC_MODE_COUNT && mode != ACC_MODE_ENUMERATE)) return ACC_ERR_ARG;
     c->mode = mode;
+    return ACC_OK;
+}
+
+int acc_ctx_set_schedule(acc_ctx *c, int64_t light, int64_t target) {
+    constexpr int64_t kMax = 1ll << 40;
+    if (!c || light < 0 || target < 0 || light > kMax || target > kMax) return ACC_ERR_ARG;
+    c->sched_light = light;
+    c->sched_target = target;
+    return ACC_OK;
+}
+
+int acc_ctx_get_schedule(acc_ctx *c, int64_t *light, int64_t *target) {
+    if (!c || !light || !target) return ACC_ERR_ARG;
+    *light = c->sched_light > 0 ? c->sched_light : enum_default_light();
+    *target = c->sched_target > 0 ? c->sched_target : enum_default_target();
+    return ACC_OK;
+}
+
+int acc_motif_batch_autotune(acc_ctx *c, void *stream, int64_t *h_light, int64_t *h_target, float *h_ms) {
+    if (!c || !c->batch_ready) return ACC_ERR_ARG;
+    if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long B = c->batch_set.B;
+    const long long light0 = c->sched_light, target0 = c->sched_target;
+    // candidate schedules: light units from a warp each up to large units,
+    // heavy units cut into small or large row tiles
+    const long long lights[] = {512, 2048, 8192, 32768};
+    const long long targets[] = {1024, 4096, 16384};
+    int64_t *counts = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = ACC_OK;
+    long long best_l = 0, best_t = 0;
+    float best = -1.0f;
+    if (B == 0) {
+        best_l = enum_default_light();
+        best_t = enum_default_target();
+        best = 0.0f;
+        goto done;
+    }
+    if (!ok(cudaMalloc(&counts, (size_t)B * num_classes(c->batch_k) * sizeof(int64_t)))) return ACC_ERR_NOMEM;
+    if (!ok(cudaEventCreate(&e0)) || !ok(cudaEventCreate(&e1))) {
+        rc = ACC_ERR_CUDA;
+        goto done;
+    }
+    for (long long l : lights) {
+        for (long long t : targets) {
+            c->sched_light = l;
+            c->sched_target = t;
+            if (!ok(cudaEventRecord(e0, s))) {
+                rc = ACC_ERR_CUDA;
+                goto done;
+            }
+            rc = run_set(c, c->batch_set, c->batch_max_n, c->batch_k, true, s, counts, c->status_dev);
+            if (rc) goto done;
+            float ms = 0.0f;
+            if (!ok(cudaEventRecord(e1, s)) || !ok(cudaEventSynchronize(e1)) ||
+                !ok(cudaEventElapsedTime(&ms, e0, e1))) {
+                rc = ACC_ERR_CUDA;
+                goto done;
+            }
+            if ((rc = finish(c, s, nullptr))) goto done;  // a failing batch fails the tuning
+            if (best < 0.0f || ms < best) {
+                best = ms;
+                best_l = l;
+                best_t = t;
+            }
+        }
+    }
+done:
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(counts);
+    if (rc) {
+        c->sched_light = light0;
+        c->sched_target = target0;
+        return rc;
+    }
+    c->sched_light = best_l;
+    c->sched_target = best_t;
+    if (h_light) *h_light = best_l;
+    if (h_target) *h_target = best_t;
+    if (h_ms) *h_ms = best;
     return ACC_OK;
 }
 

@@ -170,6 +170,8 @@ struct EnumArgs {
     uint32_t *scratch;          // per-warp overflow buffers for the extension sets
     long long scratch_per_warp; // entries per warp
     int mode;                   // 0: count the last two levels by groups, 1: enumerate every leaf
+    long long light;            // schedule: phase 1 runs units of at most this much work whole
+    long long target;           // schedule: work of one queued chunk of a heavy unit
     unsigned long long *counts; // int64[B * num_classes]
     int *status;
 };
@@ -181,6 +183,9 @@ int launch_zscores(const long long *counts, int groups, int group_size, int K, d
 // one block per SM).
 int launch_enumerate(int k, const EnumArgs &a, int num_sms, int phase, cudaStream_t s, int grid_num = 1,
                      int grid_den = 1);
+// Default schedule of the enumeration kernels (see EnumArgs::light, target).
+long long enum_default_light();
+long long enum_default_target();
 int enum_grid_warps(int k, int num_sms);
 
 }  // namespace acc

@@ -41,6 +41,8 @@ struct acc_ctx {
     uint32_t *scratch = nullptr;
     size_t scratch_cap = 0;
     int mode = 0;             // ACC_MODE_COUNT or ACC_MODE_ENUMERATE
+    long long sched_light = 0;   // enumeration schedule (0: the kernels' default)
+    long long sched_target = 0;
     int *status_dev = nullptr;
     int *status_host = nullptr;  // pinned
 

@@ -78,8 +78,6 @@ namespace {
 constexpr int kCap34 = ACC_CAP34;         // per-warp shared extension entries, k = 3, 4
 constexpr int kCap5 = ACC_CAP5;           // per-warp shared entries per list, k = 5
 constexpr int kGrab = ACC_GRAB;           // base units per atomic grab
-constexpr long long kLight = ACC_LIGHT;   // phase 1 runs units up to this much work
-constexpr long long kTarget = ACC_TARGET; // work per queued chunk
 constexpr long long kRowCost = 4;         // count mode: fixed work of one list row
 constexpr uint32_t kDrainAt = 1u << 30;
 
@@ -611,14 +609,14 @@ __device__ __forceinline__ unsigned long long reserve(const EnumArgs &a, unsigne
 }
 
 // Queue a heavy unit whose extension list has at most Bu entries as chunks
-// of about kTarget work: its Pu = ceil(Bu/2) virtual rows all carry Bu-1
+// of about a.target work: its Pu = ceil(Bu/2) virtual rows all carry Bu-1
 // pairs (plus an allowance D per list row for exclusive leaves), so equal
 // ranges of virtual rows are equal work.  Returns the first virtual row whose
 // chunk did not fit the queue (Pu when all fit); the caller runs the rest.
 __device__ int queue_closed_form(const EnumArgs &a, uint32_t unit, int v, long long Bu, long long D, int lane) {
     const long long Pu = (Bu + 1) / 2;
     const long long W = Pu * (Bu - 1) + Bu * D;
-    long long C = (W + kTarget - 1) / kTarget;
+    long long C = (W + a.target - 1) / a.target;
     if (C > Pu) C = Pu;
     if (C < 1) C = 1;
     const unsigned long long base = reserve(a, (unsigned long long)C, lane);
@@ -640,7 +638,7 @@ __device__ int queue_closed_form(const EnumArgs &a, uint32_t unit, int v, long l
     return rest;
 }
 
-// Queue rows [0, B) with per-row work work(j) as chunks of about kTarget
+// Queue rows [0, B) with per-row work work(j) as chunks of about a.target
 // (two passes over the rows: count, then write).  Returns the first row the
 // queue could not take (B when all fit).
 template <typename WorkFn>
@@ -657,7 +655,7 @@ __device__ int queue_rows(const EnumArgs &a, uint32_t unit, int v, int B, WorkFn
             const long long btot = __shfl_sync(kFull, incl, kWarp - 1);
             long long used = 0;
             for (;;) {
-                const unsigned ball = __ballot_sync(kFull, j < B && acc + incl - used >= kTarget);
+                const unsigned ball = __ballot_sync(kFull, j < B && acc + incl - used >= a.target);
                 if (!ball) {
                     acc += btot - used;
                     break;
@@ -711,7 +709,7 @@ __device__ __forceinline__ int row_of(const long long *__restrict__ nptr, int n,
 
 // Run part [jlo, jhi) of one unit: virtual rows of its extension list for
 // k = 3, 4, rows of the level-2 list E2 for k = 5.  In phase 1 (jlo = 0,
-// jhi = all) a unit with more than kLight estimated work is queued in chunks
+// jhi = all) a unit with more than a.light estimated work is queued in chunks
 // instead.  D is the per-row allowance for exclusive neighbours (mean degree
 // + 1).
 template <int K, bool COUNT>
@@ -734,7 +732,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
         int hi = min(jhi, B), rest = B;
         if (phase1) {
             auto work = [&](int j) { return (long long)g.deg[e_id(E[j])] + kRowCost; };
-            if (total_work(B, work, lane) > kLight) {
+            if (total_work(B, work, lane) > a.light) {
                 rest = queue_rows(a, unit, vglob, B, work, lane);
                 if (rest >= B) return;
                 hi = 0;
@@ -753,7 +751,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
         if (B <= 0) return;
         const int P = (B + 1) / 2;
         int hi = min(jhi, P), rest = P;
-        if (phase1 && (long long)P * (B - 1) + (long long)B * D > kLight) {
+        if (phase1 && (long long)P * (B - 1) + (long long)B * D > a.light) {
             rest = queue_closed_form(a, unit, vglob, B, D, lane);
             if (rest >= P) return;
             hi = 0;
@@ -786,7 +784,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
         rest = B2;
         if (phase1) {
             auto work = [&](int j) { return (long long)g.deg[e_id(E2[j])] + kRowCost; };
-            if (total_work(B2, work, lane) > kLight) {
+            if (total_work(B2, work, lane) > a.light) {
                 rest = queue_rows(a, unit, vglob, B2, work, lane);
                 if (rest >= B2) return;
                 hi = 0;
@@ -806,7 +804,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
         if (Bu > g.n - 2) Bu = g.n - 2;
         if (Bu <= 0) return;
         const long long Pu = (Bu + 1) / 2;
-        if (Pu * (Bu - 1) + Bu * D > kLight) {
+        if (Pu * (Bu - 1) + Bu * D > a.light) {
             rest = queue_closed_form(a, unit, vglob, Bu, D, lane);
             if (rest >= Pu) return;
             hi = 0;
@@ -836,7 +834,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
             const long long b = (long long)(B2 - 1 - j) + g.deg[e_id(E2[j])];
             return COUNT ? b * (D + 1) + 64 : b * (b - 1) / 2 + b * D + 1;
         };
-        if (total_work(B2, work, lane) > kLight) {
+        if (total_work(B2, work, lane) > a.light) {
             rest = queue_rows(a, unit, vglob, B2, work, lane);
             hi = 0;
         }
@@ -1049,6 +1047,9 @@ int bps_max() {
 }
 
 }  // namespace
+
+long long enum_default_light() { return ACC_LIGHT; }
+long long enum_default_target() { return ACC_TARGET; }
 
 int enum_grid_warps(int k, int num_sms) {
     const int bps = k == 3 ? bps_max<3>() : (k == 4 ? bps_max<4>() : bps_max<5>());

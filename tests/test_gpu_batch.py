@@ -84,6 +84,20 @@ def test_batch_single_graph_and_singles_agree(counter):
     assert int(st.item()) == -2
 
 
+def test_batch_autotune_keeps_counts(counter):
+    graphs = mixed_graphs(70)
+    dev = to_device(graphs)
+    counter.prepare_batch(dev, 4)
+    try:
+        light, target, ms = counter.autotune_batch()
+        assert (light, target) == counter.schedule() and ms > 0.0
+        got = counter.run_batch().cpu().numpy()
+        for i, (n, s, d) in enumerate(graphs):
+            assert got[i].tolist() == oracle.count(n, s, d, 4).tolist(), i
+    finally:
+        counter.set_schedule(0, 0)
+
+
 def small_ensemble(b, n_rand):
     base = synth.batch_base(b)
     return [base] + [synth.batch_randomisation(base, b, i) for i in range(n_rand)]

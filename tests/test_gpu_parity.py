@@ -194,6 +194,25 @@ def test_large_graph_paths(counter):
     assert gpu_count(counter, g.n, g.src, g.dst, 3).tolist() == want.tolist()
 
 
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_schedules_give_identical_counts(counter, k):
+    """Every unit heavy and cut into one-unit tiles (the queue overflows and
+    units finish their own rows), every unit light, and mixtures: the
+    schedule moves work between warps, never the counts."""
+    import paper_1203_3415_gb300 as p
+    n, m = {3: (3000, 15000), 4: (2000, 8000), 5: (800, 2400)}[k]
+    g = synth.chung_lu(n, m, 2.2, 150, 10, 90 + k)
+    want = oracle.count(g.n, g.src, g.dst, k, threads=threads()).tolist()
+    try:
+        for light, target in [(1, 1), (1, 64), (1 << 40, 1 << 40), (64, 1 << 40), (0, 0)]:
+            counter.set_schedule(light, target)
+            assert gpu_count(counter, g.n, g.src, g.dst, k).tolist() == want, (light, target)
+        with pytest.raises(p.MotifError):
+            counter.set_schedule(-1, 0)
+    finally:
+        counter.set_schedule(0, 0)
+
+
 def test_malformed_input(counter):
     import torch
     import paper_1203_3415_gb300 as p
