@@ -60,8 +60,9 @@ extern "C" {
 #define ACC_ERR_INTERNAL (-9)  /* an internal consistency check failed (a library bug) */
 
 /* Largest vertex count the dense n x n pair-state matrix is built for
- * (n^2/4 bytes: 4 GiB at this limit). */
-#define ACC_MAX_N 131072
+ * (n^2/4 bytes: 64 GiB at this limit, within one GB300's memory; the
+ * per-warp overflow lists add 8(n + 64) bytes per resident warp). */
+#define ACC_MAX_N 524288
 
 typedef struct acc_ctx acc_ctx;
 

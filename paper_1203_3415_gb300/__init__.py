@@ -26,7 +26,7 @@ ACC_ERR_CUDA = -6
 ACC_ERR_ARG = -7
 ACC_ERR_TOO_LARGE = -8
 ACC_ERR_INTERNAL = -9
-ACC_MAX_N = 131072
+ACC_MAX_N = 524288
 ACC_STATS_LEN = 7
 
 NUM_CLASSES = {3: 13, 4: 199, 5: 9364}

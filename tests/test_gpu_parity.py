@@ -213,6 +213,14 @@ def test_schedules_give_identical_counts(counter, k):
         counter.set_schedule(0, 0)
 
 
+def test_graph_above_131072_vertices(counter):
+    """n = 140000 (a 4.9 GB pair-state block): 64-bit offsets and the
+    renumbering and scan paths for large sets."""
+    g = synth.chung_lu(140000, 420000, 2.2, 300, 10, 74)
+    want = oracle.count(g.n, g.src, g.dst, 3, threads=oracle.max_threads())
+    assert gpu_count(counter, g.n, g.src, g.dst, 3).tolist() == want.tolist()
+
+
 def test_malformed_input(counter):
     import torch
     import paper_1203_3415_gb300 as p
