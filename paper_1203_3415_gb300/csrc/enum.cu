@@ -61,7 +61,10 @@ namespace {
 #define ACC_HIST_MATCH 0  // 1: warp-aggregate increments with __match_any_sync
 #endif
 #ifndef ACC_CUNROLL
-#define ACC_CUNROLL 4  // count mode: neighbour entries in flight per lane
+#define ACC_CUNROLL 4  // count mode: neighbour entries in flight per lane, k = 3, 4
+#endif
+#ifndef ACC_CUNROLL5
+#define ACC_CUNROLL5 3  // the same for k = 5
 #endif
 #ifndef ACC_CAP5
 #define ACC_CAP5 64  // per-warp shared-memory list entries (each of two lists), k = 5
@@ -472,7 +475,7 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
                                              int jend, bool bulk, const uint32_t *pm, uint32_t pcode,
                                              uint32_t root, bool w2_in_a, uint32_t *gcnt, int lane) {
     using L = Layout<K>;
-    constexpr int U = ACC_CUNROLL;
+    constexpr int U = K == 5 ? ACC_CUNROLL5 : ACC_CUNROLL;
     if (bulk) {
         uint32_t *glist = gcnt + L::G;  // (group, count) pairs of the non-empty groups
         for (int i = lane; i < L::G; i += kWarp) gcnt[i] = 0;
