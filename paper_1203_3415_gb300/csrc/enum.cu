@@ -45,6 +45,9 @@ namespace {
 #ifndef ACC_CAP34
 #define ACC_CAP34 512
 #endif
+#ifndef ACC_GRAB4
+#define ACC_GRAB4 2  // base units per atomic grab for k = 4 (lighter units, one hot counter)
+#endif
 #ifndef ACC_GRAB
 #define ACC_GRAB 1
 #endif
@@ -942,10 +945,11 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? ACC_MI
         const long long nunits = K == 3 ? NV : nnz;
         for (;;) {
             unsigned long long u0 = 0;
-            if (lane == 0) u0 = atomicAdd(&a.info->unit_ctr, (unsigned long long)kGrab);
+            constexpr int grab = K == 4 ? ACC_GRAB4 : kGrab;
+            if (lane == 0) u0 = atomicAdd(&a.info->unit_ctr, (unsigned long long)grab);
             u0 = __shfl_sync(kFull, u0, 0);
             if ((long long)u0 >= nunits) break;
-            const long long u1 = min((long long)u0 + kGrab, nunits);
+            const long long u1 = min((long long)u0 + grab, nunits);
             int vg = K == 3 ? 0 : row_of(a.nptr, (int)NV, (long long)u0);
             for (long long u = (long long)u0; u < u1; u++) {
                 if (K == 3) {
