@@ -60,9 +60,6 @@ namespace {
 #ifndef ACC_UNROLL
 #define ACC_UNROLL 4
 #endif
-#ifndef ACC_HIST_MATCH
-#define ACC_HIST_MATCH 0  // 1: warp-aggregate increments with __match_any_sync
-#endif
 #ifndef ACC_CUNROLL
 #define ACC_CUNROLL 4  // count mode: neighbour entries in flight per lane, k = 3, 4
 #endif
@@ -253,17 +250,9 @@ struct Sink {
         counts = counts_base + (size_t)g * Layout<K>::NCLS;
     }
 
-    // Called by all lanes of the warp together; `valid` lanes count one leaf
-    // with adjacency code `code`.
+    // Enumerate mode: a `valid` lane counts one leaf with adjacency code
+    // `code` (into its run, added to the histogram when the class changes).
     __device__ __forceinline__ void bump(uint32_t code, bool valid) {
-#if ACC_HIST_MATCH
-        const int cls = valid ? (Layout<K>::SMEM_LUT ? (int)lut[code] : (int)__ldg(lut + code)) : -2;
-        const unsigned peers = __match_any_sync(kFull, cls);
-        if (valid && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) {
-            if (cls >= 0) atomicAdd(&hist[cls], (uint32_t)__popc(peers));
-            else set_status(status, ACC_ERR_INTERNAL);
-        }
-#else
         if (!valid) return;
         const int cls = Layout<K>::SMEM_LUT ? (int)lut[code] : (int)__ldg(lut + code);
         if (cls == run_cls) {
@@ -273,7 +262,6 @@ struct Sink {
             run_cls = cls;
             run_len = 1;
         }
-#endif
     }
 
     // Called by the whole warp after each batch of at most `tot` bumps: keeps
