@@ -4,9 +4,14 @@
 //
 // Which subsets: the problem of the paper (Problems Motifs-3/4/5), i.e. the
 // k-sets S whose undirected version G*[S] is connected (Notation section).
-// The paper counts them through per-vertex / per-edge / per-triple
-// combinatorial formulas; here they are enumerated, which makes the cost
-// proportional to the count but lets one kernel serve every class.
+// The paper counts them through per-vertex / per-edge / per-triple formulas
+// over set sizes with corrections for edges among the sets.  Here ESU visits
+// every connected (k-2)-prefix once; the last two levels are counted the
+// paper's way (count mode, the default: pairs of extension-list members per
+// pair of state-vector groups, corrected by the adjacent pairs and completed
+// by the exclusive leaves found in the members' neighbour lists) or visited
+// leaf by leaf (enumerate mode).  One table over all adjacency codes serves
+// every class, so no multiplicity correction is needed.
 //
 // Exactly-once rule (ESU, Wernicke 2006, the FANMOD algorithm the paper
 // cites): a set is grown from its smallest vertex v (the root).  The current
@@ -14,7 +19,7 @@
 // the member at position j into Vsub leaves Vext[j+1..] plus the exclusive
 // neighbours of that member (neighbours above v that are neither in Vsub nor
 // adjacent to it) as the next extension list.  The last two levels are the
-// hot loop, run warp-parallel over all leaves at once:
+// hot loop, run warp-parallel:
 //
 //   prefix P = the first k-2 vertices, E = its extension list, then the
 //   leaves are  (a) P + {E[j], E[l]}  for j < l          ("pair leaves")
