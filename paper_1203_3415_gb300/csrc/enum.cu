@@ -527,8 +527,6 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
         int tot;
         const int pre = excl_scan(cnt, lane, &tot);
         sink.scanned += (unsigned long long)tot;
-        const uint32_t cj = pcode | (e_sv(ej) << L::SH_ROW);
-        const uint32_t xj = e_id(ej);
         const uint32_t off = first - (uint32_t)pre;
         for (int t0 = 0; t0 < tot; t0 += kWarp * U) {
             uint32_t ue[U], cr[U], xr[U];
@@ -536,9 +534,10 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
             for (int i = 0; i < U; i++) {
                 const int t = t0 + i * kWarp + lane;
                 const int r = lb_search(pre, t);
-                cr[i] = __shfl_sync(kFull, cj, r);
+                const uint32_t er = __shfl_sync(kFull, ej, r);  // the row's list entry: vertex and state vector
                 const uint32_t orow = __shfl_sync(kFull, off, r);
-                xr[i] = __shfl_sync(kFull, xj, r);
+                cr[i] = pcode | (e_sv(er) << L::SH_ROW);
+                xr[i] = e_id(er);
                 ue[i] = t < tot ? __ldg(g.nbr + (orow + (uint32_t)t)) : 0xFFFFFFFFu;
             }
             uint32_t sv[U][K - 2];
