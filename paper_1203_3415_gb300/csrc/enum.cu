@@ -898,6 +898,9 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? ACC_MI
     uint32_t *groups = reinterpret_cast<uint32_t *>(smem + L::lut + L::pending + L::hist + L::ebuf);
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     const bool several = a.gs.B > 1;
+    // phase 2 with nothing queued: no table to stage, nothing to flush
+    if constexpr (PHASE == 2)
+        if (a.info->queue_tail == 0) return;
 
     if (L::SMEM_LUT)
         for (int i = tid; i < (1 << L::NB); i += blockDim.x) lut_s[i] = a.lut[i];
