@@ -297,7 +297,8 @@ def run_ours(args):
     counts = torch.zeros(acc.NUM_CLASSES[k], dtype=torch.int64, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     counter = acc.Counter(local)
-    counter.set_mode(acc.ACC_MODE_ENUMERATE if args.mode == "enumerate" else acc.ACC_MODE_COUNT)
+    counter.set_mode({"count": acc.ACC_MODE_COUNT, "enumerate": acc.ACC_MODE_ENUMERATE,
+                      "formula": acc.ACC_MODE_FORMULA}[args.mode])
     counter.prepare(k)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -390,6 +391,9 @@ def run_ours(args):
     if args.mode == "count":
         units, per_unit = int(stats["scanned_entries"]), ops_per_scanned_entry(k)
         unit_name = "neighbour entries scanned by the last two levels"
+    elif args.mode == "formula" and k == 3:
+        units, per_unit = n_k, ops_per_subgraph(k)
+        unit_name = "classified subgraphs (leaf-equivalent: the formula path visits none)"
     else:
         units, per_unit = n_k, ops_per_subgraph(k)
         unit_name = "classified subgraphs"
@@ -682,8 +686,9 @@ def main():
     ap.add_argument("--serve-policy", choices=["shortest", "fifo"], default="shortest",
                     help="serving admission order: smallest aged work estimate first, or submission order")
     ap.add_argument("--serve-aging-s", type=float, default=1.0)
-    ap.add_argument("--mode", choices=["count", "enumerate"], default="count",
-                    help="last two levels counted by state-vector groups, or every leaf enumerated")
+    ap.add_argument("--mode", choices=["count", "enumerate", "formula"], default="count",
+                    help="last two levels counted by state-vector groups, every leaf enumerated, or (k=3) the "
+                         "per-vertex formulas")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

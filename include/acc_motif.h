@@ -293,10 +293,16 @@ ACC_API int acc_motif_last_stats(acc_ctx *ctx, int64_t *h_stats);
  *   pairs are corrected one by one from the members' neighbour lists, as the
  *   paper's Table starb counts patterns from set sizes minus edges.
  *  ACC_MODE_ENUMERATE: every k-subset is visited and classified on its own.
- * Both give identical counts.  Errors: ACC_ERR_ARG.
+ *  ACC_MODE_FORMULA: for k = 3, the paper's per-vertex formulas (Thm teo3,
+ *   Algorithm s3, Table starb): open triples from the sizes of each vertex's
+ *   out-only / in-only / bidirected neighbour sets, triangles listed once and
+ *   the open triples they were counted as moved out; no subset is visited.
+ *   For k = 4, 5 it counts as ACC_MODE_COUNT.
+ * All modes give identical counts.  Errors: ACC_ERR_ARG.
  */
 #define ACC_MODE_COUNT 0
 #define ACC_MODE_ENUMERATE 1
+#define ACC_MODE_FORMULA 2
 ACC_API int acc_ctx_set_mode(acc_ctx *ctx, int mode);
 
 /*

@@ -43,7 +43,7 @@ EXPORTS = (
 )
 ACC_REQ_QUEUED, ACC_REQ_RUNNING, ACC_REQ_DONE = 0, 1, 2
 ACC_SERVE_FIFO, ACC_SERVE_SHORTEST = 0, 1
-ACC_MODE_COUNT, ACC_MODE_ENUMERATE = 0, 1
+ACC_MODE_COUNT, ACC_MODE_ENUMERATE, ACC_MODE_FORMULA = 0, 1, 2
 
 
 def _load():

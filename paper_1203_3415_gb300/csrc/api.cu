@@ -194,13 +194,19 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     a.counts = reinterpret_cast<unsigned long long *>(counts);
     a.status = status;
     const bool any = gs.NV > 0;
-    if (any) {
+    const bool formula = k == 3 && c->mode == ACC_MODE_FORMULA;
+    if (any && formula) {
+        rc = launch_formula3(gs, c->state, c->nptr, c->deg, c->lo, c->nbr, c->lut[3],
+                             reinterpret_cast<unsigned long long *>(counts), status, c->num_sms, s);
+        if (rc < 0) return rc;
+        launches += rc;
+    } else if (any) {
         rc = launch_enumerate(k, a, c->num_sms, 1, s, c->grid_num, c->grid_den);
         if (rc < 0) return rc;
         launches += rc;
     }
     if (c->timing && !ok(cudaEventRecord(c->ev[3], s))) return ACC_ERR_CUDA;
-    if (any) {
+    if (any && !formula) {
         rc = launch_enumerate(k, a, c->num_sms, 2, s, c->grid_num, c->grid_den);
         if (rc < 0) return rc;
         launches += rc;
@@ -528,7 +534,7 @@ int acc_motif_last_stats(acc_ctx *c, int64_t *h_stats) {
 }
 
 int acc_ctx_set_mode(acc_ctx *c, int mode) {
-    if (!c || (mode != ACC_MODE_COUNT && mode != ACC_MODE_ENUMERATE)) return ACC_ERR_ARG;
+    if (!c || (mode != ACC_MODE_COUNT && mode != ACC_MODE_ENUMERATE && mode != ACC_MODE_FORMULA)) return ACC_ERR_ARG;
     c->mode = mode;
     return ACC_OK;
 }

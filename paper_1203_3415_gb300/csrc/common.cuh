@@ -175,6 +175,10 @@ struct EnumArgs {
     unsigned long long *counts; // int64[B * num_classes]
     int *status;
 };
+// formula3.cu: k = 3 counts by the per-vertex formulas (one launch).
+int launch_formula3(const GSet &gs, const uint32_t *state, const long long *nptr, const int *deg, const int *lo,
+                    const uint32_t *nbr, const int16_t *lut, unsigned long long *counts, int *status, int num_sms,
+                    cudaStream_t s);
 // batch.cu: Z-scores of each group's real graph against its randomisations.
 int launch_zscores(const long long *counts, int groups, int group_size, int K, double *z, cudaStream_t s);
 
