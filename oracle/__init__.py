@@ -71,6 +71,10 @@ def _load():
                                      ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, i64p]
     lib.oracle_max_threads.argtypes = []
     lib.oracle_zscores.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, f64p]
+    lib.oracle_swap_randomise.argtypes = [ctypes.c_int32, ctypes.c_int64, i64p, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.c_int64, ctypes.c_uint64, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int32)]
+    lib.oracle_swap_randomise.restype = ctypes.c_int64
     lib.oracle_zscores.restype = None
     _lib = lib
     return lib
@@ -177,3 +181,17 @@ def zscores(real: np.ndarray, rand: np.ndarray) -> np.ndarray:
     z = np.empty(K, dtype=np.float64)
     _load().oracle_zscores(K, R, _p(real, ctypes.c_int64), _p(rand, ctypes.c_int64), _p(z, ctypes.c_double))
     return z
+
+
+def swap_randomise(n: int, rowptr, col, attempts: int, seed: int, mode: int = 0) -> tuple[np.ndarray, int]:
+    """Randomised copy of the out-CSR graph (rowptr, col): the copy's targets
+    in the positions of ``col`` and the number of accepted swaps.  mode 0:
+    double-edge swaps; mode 1: swaps that keep mutual arcs mutual."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    out = np.empty(len(col), dtype=np.int32)
+    acc = _load().oracle_swap_randomise(n, len(col), _p(rowptr, ctypes.c_int64), _p(col, ctypes.c_int32),
+                                        attempts, seed & 0xFFFFFFFFFFFFFFFF, mode, _p(out, ctypes.c_int32))
+    if acc < 0:
+        raise ValueError("oracle_swap_randomise: invalid argument")
+    return out, int(acc)

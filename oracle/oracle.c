@@ -441,3 +441,106 @@ void oracle_zscores(int K, int R, const int64_t *real, const int64_t *rand, doub
         z[c] = sd == 0.0 ? __builtin_nan("") : num / sd;
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Significance: degree-preserving randomised copies                    */
+/* ------------------------------------------------------------------ */
+
+/*
+ * SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014): add the golden-ratio increment to the state,
+ * then two xor-shift-multiply rounds and a final xor-shift of the sum.
+ */
+static uint64_t orand_next(uint64_t *state)
+{
+    uint64_t z;
+    *state = *state + 0x9E3779B97F4A7C15ULL;
+    z = *state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* A uniform integer below `bound` by the multiply-shift map (Lemire, "Fast
+ * random integer generation in an interval", 2019): the high 64 bits of
+ * the 128-bit product of a draw and the bound. */
+static uint64_t orand_below(uint64_t *state, uint64_t bound)
+{
+    unsigned __int128 prod = (unsigned __int128)orand_next(state) * (unsigned __int128)bound;
+    return (uint64_t)(prod >> 64);
+}
+
+/* Position of target t in row v of the copy, or -1. */
+static int64_t orand_find(const int64_t *rowptr, const int32_t *cur, int32_t v, int32_t t)
+{
+    for (int64_t p = rowptr[v]; p < rowptr[v + 1]; p++)
+        if (cur[p] == t) return p;
+    return -1;
+}
+
+/*
+ * Randomised copy of a simple digraph for the random ensemble of the
+ * significance step (Implementation section, steps i and iii: the paper
+ * counts the real graph and a set of random graphs but fixes no generator).
+ *
+ * The graph is an out-CSR: arc e runs from the row that holds position e to
+ * col[e].  The copy starts as col and keeps rowptr: an accepted swap changes
+ * targets only, so every out-degree stays, and it moves targets between
+ * arcs, so every in-degree stays.  `attempts` attempts, each drawing e1 then
+ * e2 uniformly below m from the stream seeded with `seed`; with
+ * a -> b = arc e1 and c -> d = arc e2 of the copy:
+ *
+ *   mode 0 (double-edge swap): rejected if e1 == e2, a == d, c == b, or
+ *     a -> d or c -> b is already an arc; otherwise the arcs become a -> d
+ *     and c -> b.
+ *   mode 1 (mutual arcs kept): an arc is mutual when its reverse is an arc
+ *     too.  Rejected if e1 == e2, a == d, c == b, one arc is mutual and the
+ *     other is not, or a, d or c, b are adjacent (an arc either way).  Two
+ *     single arcs become a -> d and c -> b; two mutual pairs a <-> b and
+ *     c <-> d become a <-> d and c <-> b (the reverse arcs b -> a and d -> c
+ *     are retargeted to c and a).  Every vertex keeps its numbers of single
+ *     out-arcs, single in-arcs and mutual neighbours.
+ *
+ * out (int32[m]) receives the copy's targets in the positions of col.
+ * Returns the number of accepted swaps, or -1 for an invalid argument.
+ */
+int64_t oracle_swap_randomise(int32_t n, int64_t m, const int64_t *rowptr, const int32_t *col, int64_t attempts,
+                              uint64_t seed, int mode, int32_t *out)
+{
+    if (n < 0 || m < 0 || attempts < 0 || (mode != 0 && mode != 1)) return -1;
+    int32_t *row = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    if (!row) return -1;
+    for (int32_t v = 0; v < n; v++)
+        for (int64_t p = rowptr[v]; p < rowptr[v + 1]; p++) row[p] = v;
+    for (int64_t e = 0; e < m; e++) out[e] = col[e];
+    uint64_t state = seed;
+    int64_t accepted = 0;
+    for (int64_t t = 0; m >= 2 && t < attempts; t++) {
+        int64_t e1 = (int64_t)orand_below(&state, (uint64_t)m);
+        int64_t e2 = (int64_t)orand_below(&state, (uint64_t)m);
+        if (e1 == e2) continue;
+        int32_t a = row[e1], b = out[e1], c = row[e2], d = out[e2];
+        if (a == d || c == b) continue;
+        if (mode == 0) {
+            if (orand_find(rowptr, out, a, d) >= 0 || orand_find(rowptr, out, c, b) >= 0) continue;
+            out[e1] = d;
+            out[e2] = b;
+            accepted++;
+            continue;
+        }
+        int64_t r1 = orand_find(rowptr, out, b, a); /* b -> a, if a -> b is mutual */
+        int64_t r2 = orand_find(rowptr, out, d, c);
+        if ((r1 >= 0) != (r2 >= 0)) continue;
+        if (orand_find(rowptr, out, a, d) >= 0 || orand_find(rowptr, out, d, a) >= 0) continue;
+        if (orand_find(rowptr, out, c, b) >= 0 || orand_find(rowptr, out, b, c) >= 0) continue;
+        out[e1] = d;
+        out[e2] = b;
+        if (r1 >= 0) {
+            out[r1] = c;
+            out[r2] = a;
+        }
+        accepted++;
+    }
+    free(row);
+    return accepted;
+}

@@ -20,7 +20,9 @@ Workload recipes (the shapes the counter is measured on):
                    capped at 200, uniform targets, 3% reciprocal, seed 3 (k=5).
 * ``batch_k4``     8 directed Chung-Lu base graphs (exponent 2.3, m=4n,
                    n in [500, 5000] log-uniform with both ends), each with 500
-                   degree-preserving randomisations of 3m swap attempts.
+                   degree-preserving randomisations of 3m swap attempts
+                   (arcs drawn by their position in the base's out-CSR,
+                   copy i of base b seeded 10^6 (b+1) + i).
 * ``serving_pool`` 64 directed Chung-Lu graphs (exponent 2.2, cap 200),
                    n log-uniform in [100, 50000], mean out-degree in [4, 10],
                    plus a Poisson request stream at 200 req/s.
@@ -235,9 +237,18 @@ def batch_base_sizes() -> list[int]:
     return sizes
 
 
+def csr_order(g: Graph) -> Graph:
+    """The same graph with its arcs listed in out-CSR order (by source, then
+    target), so that arc e of the list is position e of ``g.csr()``."""
+    order = np.lexsort((g.dst, g.src))
+    return Graph(g.n, np.ascontiguousarray(g.src[order]), np.ascontiguousarray(g.dst[order]), g.name)
+
+
 def batch_base(b: int) -> Graph:
+    """Base graph b of the batch, arcs in out-CSR order: the swaps of its
+    randomisations pick arcs by CSR position."""
     n = batch_base_sizes()[b]
-    g = chung_lu(n, 4 * n, 2.3, min(500, n // 2), 10, 100 + b)
+    g = csr_order(chung_lu(n, 4 * n, 2.3, min(500, n // 2), 10, 100 + b))
     g.name = f"batch_base{b}_n{n}"
     return g
 

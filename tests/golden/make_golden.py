@@ -55,18 +55,28 @@ def graphs_digest(graphs):
     return h.hexdigest()
 
 
+def oracle_randomisation(base, b, i):
+    """Copy i of batch base b by the oracle's double-edge swaps: 3m attempts
+    on the base's out-CSR positions, seed 10^6 (b+1) + i."""
+    rowptr, col = base.csr()
+    src = np.repeat(np.arange(base.n, dtype=np.int32), np.diff(rowptr))
+    dst, _ = oracle.swap_randomise(base.n, rowptr, col, 3 * base.m, 1_000_000 * (b + 1) + i)
+    return synth.Graph(base.n, src, dst, f"batch_base{b}_rand{i}")
+
+
 def make_batch_golden(path, threads, n_rand=synth.BATCH_RANDOMISATIONS):
     """Batched k=4 workload: per base graph, the digest of its 1 + n_rand
     graphs, the digest and total of their int64 counts [1 + n_rand, 199] and
     the Z-scores of the base against its randomisations (hex doubles)."""
     with open(path, "w") as f:
         f.write("# workload batch_k4: 8 directed Chung-Lu bases (exponent 2.3, m = 4n) x "
-                f"(1 + {n_rand} degree-preserving randomisations, 3m swap attempts)\n")
+                f"(1 + {n_rand} degree-preserving randomisations, 3m swap attempts "
+                "on out-CSR positions, copy i of base b seeded 10^6 (b+1) + i)\n")
         f.write(f"# oracle ESU, {threads} threads; one line per base:\n")
         f.write("# base n m graphs_sha256 counts_sha256 total z_hex[199]\n")
         for b in range(synth.BATCH_BASES):
             base = synth.batch_base(b)
-            graphs = [base] + [synth.batch_randomisation(base, b, i) for i in range(n_rand)]
+            graphs = [base] + [oracle_randomisation(base, b, i) for i in range(n_rand)]
             t = time.time()
             counts = np.stack([oracle.count(g.n, g.src, g.dst, 4, threads=threads) for g in graphs])
             z = oracle.zscores(counts[0], counts[1:])
