@@ -46,6 +46,7 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "chung_lu_n20000_m100000_k4"
 BATCH_WORKLOAD = "batch_k4"
+SIGNIFICANCE_WORKLOAD = "significance_k4"
 SERVING_WORKLOAD = "serving"
 
 # Algorithmic integer operations per classified subgraph when every leaf is
@@ -573,6 +574,170 @@ def run_batch_bench(args):
     return 0
 
 
+def run_significance_bench(args):
+    """The significance step on the device for the batched k=4 workload: each
+    step randomises 8 Chung-Lu bases x 500 copies (3m double-edge swap
+    attempts each), counts the 4008 graphs as one batch and scores every base
+    against its copies; the three calls are replayed from one CUDA graph."""
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    from paper_1203_3415_gb300 import build as lib_build
+    if rank == 0 or world == 1:
+        lib_build.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_1203_3415_gb300 as acc
+
+    bases = [synth.batch_base(b) for b in range(synth.BATCH_BASES)]
+    graphs = []
+    for g in bases:
+        r, c = g.csr()
+        graphs.append((torch.from_numpy(r).to(dev), torch.from_numpy(c).to(dev), g.n))
+    R = synth.BATCH_RANDOMISATIONS
+    G, B = len(graphs), len(graphs) * (R + 1)
+    seeds = [1_000_000 * (b + 1) for b in range(G)]
+    counter = acc.Counter(local)
+    stream = torch.cuda.Stream(dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    counts = torch.zeros((B, 199), dtype=torch.int64, device=dev)
+    z = torch.zeros((G, 199), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    m_total = sum(int(c.numel()) for _, c, _ in graphs)
+    out = torch.empty(R * m_total, dtype=torch.int32, device=dev)
+    accepted = torch.empty((G, R), dtype=torch.int64, device=dev)
+
+    def step():
+        counter.randomise(graphs, R, seeds, 3, out=out, accepted=accepted, status=status, stream=stream)
+        counter.run_batch(counts=counts, status=status, stream=stream)
+        acc._check(acc.acc_motif_zscores(counts.data_ptr(), G, R + 1, 4, stream.cuda_stream, z.data_ptr()),
+                   "acc_motif_zscores")
+
+    with torch.cuda.stream(stream):
+        counter.randomise(graphs, R, seeds, 3, out=out, accepted=accepted, status=status, stream=stream)
+        batch = []
+        for g, cps in zip(graphs, acc.Counter.copies(graphs, R, out)):
+            batch.append(g)
+            batch.extend(cps)
+        counter.prepare_batch(batch, 4, stream=stream)
+        sched = counter.autotune_batch(stream=stream)
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize(dev)
+    if int(status.item()) != 0:
+        raise RuntimeError(f"significance step failed: {acc.acc_strerror(int(status.item()))}")
+    eager = counts.clone()
+    # the randomisation alone, eager, for its share of the step
+    rt = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+    with torch.cuda.stream(stream):
+        for a, b in rt:
+            flush.fill_(3)
+            a.record(stream)
+            counter.randomise(graphs, R, seeds, 3, out=out, accepted=accepted, status=status, stream=stream)
+            b.record(stream)
+    torch.cuda.synchronize(dev)
+    rand_ms = min(a.elapsed_time(b) for a, b in rt)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        step()
+    steps = max(1, args.steps)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    sampler = ClockSampler(local) if rank == 0 else None
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.start()
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            graph.replay()
+            ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    local_s = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
+    if not torch.equal(counts, eager) or int(status.item()) != 0:
+        raise RuntimeError("graph replay differs from the eager significance step")
+    total = int(counts.sum().item())
+    attempts = 3 * R * m_total
+    acc_swaps = int(accepted.sum().item())
+    max_s = reduce_max(dist, local_s, dev)
+    value = whole_job_rate(reduce_sum(dist, float(B) * steps, dev), max_s)
+    if rank != 0:
+        counter.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    gold = os.path.join(ROOT, "tests", "golden", "batch_k4.txt")
+    parity = None
+    if os.path.exists(gold):
+        import hashlib
+        rows = [ln.split() for ln in open(gold) if ln.strip() and not ln.startswith("#")]
+        host = counts.cpu().numpy()
+        zh = z.cpu().numpy()
+        parity = all(
+            hashlib.sha256(np.ascontiguousarray(host[b * (R + 1):(b + 1) * (R + 1)], dtype="<i8").tobytes())
+            .hexdigest() == rows[b][4]
+            and all(float(x).hex() == w or (np.isnan(x) and w == "nan") for x, w in zip(zh[b], rows[b][6:]))
+            for b in range(len(rows)))
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = significance_cpu_baseline(bases)
+    line = {
+        "metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * max_s / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": SIGNIFICANCE_WORKLOAD, "k": 4, "graphs": B, "bases": G,
+                   "randomisations_per_base": R, "swap_attempts_per_copy": "3m",
+                   "subgraphs_per_step": total,
+                   "l2": "flushed between timed steps (256 MiB device write)",
+                   "launch": "randomise + batched count + Z-scores replayed from one captured CUDA graph",
+                   "schedule": {"light": sched[0], "target": sched[1], "autotuned": True},
+                   "parallelism": f"replicas{world}"},
+        "randomise_ms": rand_ms,
+        "swap_attempts_per_s": attempts / (rand_ms / 1000.0),
+        "accepted_swaps": acc_swaps,
+        "swap_attempts": attempts,
+        "subgraphs_per_s": total * steps / max_s,
+        "gpu_launches": (2 + counter.last_stats()["launches"] + 1) * steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "parity_vs_stored_oracle_counts_and_z": parity,
+    }
+    print(json.dumps(line), flush=True)
+    counter.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def significance_cpu_baseline(bases, budget_s=10.0):
+    """The oracle's copy and count of randomised copies of the smallest base,
+    one after another until about budget_s seconds."""
+    import oracle
+    oracle.build()
+    b = min(range(len(bases)), key=lambda i: bases[i].n)
+    g = bases[b]
+    rowptr, col = g.csr()
+    src = np.repeat(np.arange(g.n, dtype=np.int32), np.diff(rowptr))
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    done = 0
+    while time.perf_counter() - t0 < budget_s:
+        dst, _ = oracle.swap_randomise(g.n, rowptr, col, 3 * g.m, 1_000_000 * (b + 1) + done)
+        oracle.count(g.n, src, dst, 4, threads=threads)
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "graphs/s", "cores": threads, "kind": "oracle",
+            "sample": f"{done} randomised copies of base {b} (n={g.n}, m={g.m}): swaps and ESU count each"}
+
+
 def run_serving_bench(args):
     """Serving workload: 64 resident directed Chung-Lu graphs (n log-uniform
     in [100, 50000], mean out-degree 4-10), a Poisson stream of requests at
@@ -675,7 +840,8 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD, SERVING_WORKLOAD],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD, SERVING_WORKLOAD,
+                                                               SIGNIFICANCE_WORKLOAD],
                     default=DEFAULT_WORKLOAD)
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="serving: arrival window")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent requests")
@@ -692,13 +858,15 @@ def main():
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":
-        if args.workload in (BATCH_WORKLOAD, SERVING_WORKLOAD):
+        if args.workload in (BATCH_WORKLOAD, SERVING_WORKLOAD, SIGNIFICANCE_WORKLOAD):
             args.workload = DEFAULT_WORKLOAD
         return run_reference(args)
     if args.workload == BATCH_WORKLOAD:
         return run_batch_bench(args)
     if args.workload == SERVING_WORKLOAD:
         return run_serving_bench(args)
+    if args.workload == SIGNIFICANCE_WORKLOAD:
+        return run_significance_bench(args)
     return run_ours(args)
 
 

@@ -198,6 +198,55 @@ ACC_API int acc_motif_zscores(const int64_t *d_counts, int32_t groups, int32_t g
                               double *d_z);
 
 /*
+ * Randomised copies for the random ensemble of the significance step
+ * (Implementation section, steps i and iii: the real graph and a set of
+ * random graphs are counted; the paper fixes no generator).
+ *
+ * Each of the G graphs (h_graphs, host array; same layout and rules as
+ * acc_motif_count's arguments, and simple: no repeated arc) gets R copies.
+ * Arc e of a graph is (row holding position e) -> col[e].  A copy keeps
+ * rowptr and starts as col; it then makes attempts_per_arc * m attempts,
+ * each drawing positions e1 then e2 uniformly below m from SplitMix64
+ * (Steele, Lea and Flood, 2014; a draw x maps to the high 64 bits of x * m),
+ * the stream of copy r of graph g seeded h_seeds[g] + r (mod 2^64).  With
+ * a -> b = arc e1 and c -> d = arc e2 of the copy:
+ *   ACC_RAND_SWAP    rejected if e1 == e2, a == d, c == b, or a -> d or
+ *                    c -> b is already an arc; otherwise a -> d and c -> b.
+ *                    Every in- and out-degree is kept.
+ *   ACC_RAND_MUTUAL  an arc is mutual when its reverse is an arc.  Rejected
+ *                    if e1 == e2, a == d, c == b, exactly one of the two
+ *                    arcs is mutual, or a and d or c and b are adjacent;
+ *                    otherwise two single arcs become a -> d and c -> b, and
+ *                    two mutual pairs a <-> b and c <-> d become a <-> d and
+ *                    c <-> b.  Every vertex keeps its single in- and
+ *                    out-degree and its number of mutual neighbours.
+ * A repeated arc in the input is not an error, but the copies are then only
+ * defined by the procedure above (a row entry counts as an arc).
+ *
+ *  d_out       device int32[R * sum of m]: graph g's copies start at element
+ *              R * (m_0 + ... + m_{g-1}), copy r at that start + r * m_g,
+ *              each m_g targets in the positions of the graph's col (so copy
+ *              r is the out-CSR (rowptr_g, that slice)).
+ *  d_accepted  device int64[G * R] or NULL: accepted swaps of copy r of
+ *              graph g at g * R + r.
+ *  d_status    as in acc_motif_count (ACC_ERR_INPUT for a malformed graph;
+ *              d_out is then unspecified).
+ * The call waits for `stream` and uploads the descriptors (graphs, R,
+ * attempts and seeds) unless they equal the previous call's on this context;
+ * then, with d_status non-NULL, it only enqueues its kernels, so a repeated
+ * call can be captured into a CUDA graph and replayed.  Host-checked
+ * errors: ACC_ERR_ARG (null pointers, G or R negative, unknown mode,
+ * attempts_per_arc negative), ACC_ERR_INPUT (negative sizes, m >= 2^31, m > 0
+ * with n = 0), ACC_ERR_OVERFLOW (attempts_per_arc * m above 2^62),
+ * ACC_ERR_NOMEM, ACC_ERR_CUDA.
+ */
+#define ACC_RAND_SWAP 0
+#define ACC_RAND_MUTUAL 1
+ACC_API int acc_swap_randomise(acc_ctx *ctx, const acc_graph_desc *h_graphs, int32_t G, int32_t R,
+                               int64_t attempts_per_arc, const uint64_t *h_seeds, int mode, void *stream,
+                               int32_t *d_out, int64_t *d_accepted, int32_t *d_status);
+
+/*
  * Serving form: a request server with continuous batching on one GPU.
  *
  * Requests (resident graph, k) are submitted at any time.  A request is

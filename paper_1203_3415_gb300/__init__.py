@@ -35,7 +35,7 @@ NUM_CLASSES = {3: 13, 4: 199, 5: 9364}
 EXPORTS = (
     "acc_strerror", "acc_motif_num_classes", "acc_ctx_create", "acc_ctx_destroy", "acc_motif_prepare",
     "acc_motif_count", "acc_motif_count_host", "acc_motif_batch_prepare", "acc_motif_batch_run",
-    "acc_motif_count_batch", "acc_motif_zscores", "acc_motif_class_code", "acc_motif_classify_code",
+    "acc_motif_count_batch", "acc_motif_zscores", "acc_swap_randomise", "acc_motif_class_code", "acc_motif_classify_code",
     "acc_motif_copy_table", "acc_motif_last_stats", "acc_ctx_set_timing", "acc_motif_last_timing",
     "acc_motif_build_table_static", "acc_ctx_set_mode", "acc_server_create", "acc_server_destroy", "acc_server_add_graph",
     "acc_server_reserve", "acc_server_submit", "acc_server_progress", "acc_server_poll", "acc_server_drain",
@@ -44,6 +44,7 @@ EXPORTS = (
 ACC_REQ_QUEUED, ACC_REQ_RUNNING, ACC_REQ_DONE = 0, 1, 2
 ACC_SERVE_FIFO, ACC_SERVE_SHORTEST = 0, 1
 ACC_MODE_COUNT, ACC_MODE_ENUMERATE, ACC_MODE_FORMULA = 0, 1, 2
+ACC_RAND_SWAP, ACC_RAND_MUTUAL = 0, 1
 
 
 def _load():
@@ -65,6 +66,7 @@ def _load():
     lib.acc_motif_batch_run.argtypes = [vp, vp, vp, vp]
     lib.acc_motif_count_batch.argtypes = [vp, vp, i32, ctypes.c_int, vp, vp, vp]
     lib.acc_motif_zscores.argtypes = [vp, i32, i32, ctypes.c_int, vp, vp]
+    lib.acc_swap_randomise.argtypes = [vp, vp, i32, i32, i64, vp, ctypes.c_int, vp, vp, vp, vp]
     lib.acc_motif_class_code.argtypes = [vp, ctypes.c_int, i32, ctypes.POINTER(ctypes.c_uint32)]
     lib.acc_motif_classify_code.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(i32)]
     lib.acc_motif_copy_table.argtypes = [vp, ctypes.c_int, vp]
@@ -170,6 +172,13 @@ def acc_motif_count_batch(ctx: int, h_graphs, B: int, k: int, stream: int, d_cou
 
 def acc_motif_zscores(d_counts: int, groups: int, group_size: int, k: int, stream: int, d_z: int) -> int:
     return _L().acc_motif_zscores(d_counts, groups, group_size, k, stream, d_z)
+
+
+def acc_swap_randomise(ctx: int, h_graphs, G: int, R: int, attempts_per_arc: int, h_seeds, mode: int,
+                       stream: int, d_out: int, d_accepted: int | None, d_status: int | None) -> int:
+    return _L().acc_swap_randomise(ctx, ctypes.cast(h_graphs, ctypes.c_void_p), G, R, attempts_per_arc,
+                                   ctypes.cast(h_seeds, ctypes.c_void_p), mode, stream, d_out, d_accepted,
+                                   d_status)
 
 
 def acc_motif_class_code(ctx: int, k: int, cls: int) -> int:
@@ -419,6 +428,66 @@ class Counter:
         _check(acc_motif_zscores(counts.data_ptr(), groups, group_size, k, s.cuda_stream, z.data_ptr()),
                "acc_motif_zscores")
         return z
+
+    def randomise(self, graphs, R: int, seeds, attempts_per_arc: int = 3, mode: int = ACC_RAND_SWAP,
+                  out=None, accepted=None, status=None, stream=None):
+        """R randomised copies of each graph of ``graphs`` ((rowptr, col, n)
+        CUDA tensors) by acc_swap_randomise; copy r of graph g uses the stream
+        seeded seeds[g] + r.  Returns (out, accepted): out is the int32 tensor
+        of every copy's targets (graph g's copies from R * (m_0 + ... +
+        m_{g-1}), copy r at that start + r * m_g), accepted int64 [G, R]."""
+        import torch
+        G = len(graphs)
+        dev = graphs[0][0].device if G else torch.device("cuda", self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        descs = (acc_graph_desc * max(1, G))()
+        total = 0
+        for i, (rowptr, col, n) in enumerate(graphs):
+            assert rowptr.dtype == torch.int64 and col.dtype == torch.int32 and rowptr.is_cuda and col.is_cuda
+            descs[i].rowptr = rowptr.data_ptr()
+            descs[i].col = col.data_ptr() if col.numel() else 0
+            descs[i].n = n
+            descs[i].m = col.numel()
+            total += col.numel()
+        seeds_arr = (ctypes.c_uint64 * max(1, G))(*[int(x) & 0xFFFFFFFFFFFFFFFF for x in seeds][:G])
+        if out is None:
+            out = torch.empty(max(1, R * total), dtype=torch.int32, device=dev)
+        if accepted is None:
+            accepted = torch.empty((G, R), dtype=torch.int64, device=dev)
+        rc = acc_swap_randomise(self.ctx, descs, G, R, attempts_per_arc, seeds_arr, mode, s.cuda_stream,
+                                out.data_ptr(), accepted.data_ptr() if accepted.numel() else None,
+                                status.data_ptr() if status is not None else None)
+        _check(rc, "acc_swap_randomise")
+        return out, accepted
+
+    @staticmethod
+    def copies(graphs, R: int, out):
+        """The copies in ``out`` (from randomise) as [(rowptr, col, n), ...]
+        per graph: R views sharing the graph's rowptr."""
+        res, off = [], 0
+        for rowptr, col, n in graphs:
+            m = col.numel()
+            res.append([(rowptr, out[off + r * m: off + (r + 1) * m], n) for r in range(R)])
+            off += R * m
+        return res
+
+    def significance(self, graphs, k: int, R: int, seeds, attempts_per_arc: int = 3,
+                     mode: int = ACC_RAND_SWAP, stream=None):
+        """The significance step on the device: R randomised copies of each
+        graph, the real graphs and their copies counted as one batch, and the
+        Z-scores of each real graph against its copies.  Returns (counts
+        int64 [G, 1 + R, num_classes], z float64 [G, num_classes], out)."""
+        import torch
+        G = len(graphs)
+        out, _ = self.randomise(graphs, R, seeds, attempts_per_arc, mode, stream=stream)
+        batch = []
+        for g, cps in zip(graphs, self.copies(graphs, R, out)):
+            batch.append(g)
+            batch.extend(cps)
+        self.prepare_batch(batch, k, stream=stream)
+        counts = self.run_batch(stream=stream)
+        z = self.zscores(counts, G, R + 1, k, stream=stream)
+        return counts.view(G, R + 1, NUM_CLASSES[k]), z, out
 
     def table(self, k: int):
         import numpy as np

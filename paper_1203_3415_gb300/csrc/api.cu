@@ -349,6 +349,8 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaFree(c->status_dev);
     cudaFree(c->meta_dev);
     cudaFree(c->gid);
+    cudaFree(c->rand_meta);
+    cudaFree(c->rand_rows);
     cudaFree(c->h2d_rowptr);
     cudaFree(c->h2d_col);
     cudaFree(c->h2d_counts);
@@ -483,6 +485,60 @@ int acc_motif_zscores(const int64_t *d_counts, int32_t groups, int32_t group_siz
     const int rc = launch_zscores(reinterpret_cast<const long long *>(d_counts), groups, group_size, num_classes(k),
                                   d_z, (cudaStream_t)stream);
     return rc < 0 ? rc : ACC_OK;
+}
+
+int acc_swap_randomise(acc_ctx *c, const acc_graph_desc *graphs, int32_t G, int32_t R, int64_t attempts_per_arc,
+                       const uint64_t *seeds, int mode, void *stream, int32_t *d_out, int64_t *d_accepted,
+                       int32_t *d_status) {
+    if (!c || G < 0 || R < 0 || attempts_per_arc < 0) return ACC_ERR_ARG;
+    if (mode != ACC_RAND_SWAP && mode != ACC_RAND_MUTUAL) return ACC_ERR_ARG;
+    if (G > 0 && (!graphs || !seeds)) return ACC_ERR_ARG;
+    if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<RGraph> metas((size_t)G);
+    long long M = 0, NV = 0;
+    for (int g = 0; g < G; g++) {
+        const acc_graph_desc &d = graphs[g];
+        if (!d.rowptr || (d.m > 0 && !d.col)) return ACC_ERR_ARG;
+        if (d.n < 0 || d.m < 0 || d.m >= (1ll << 31) || (d.n == 0 && d.m > 0)) return ACC_ERR_INPUT;
+        if (d.m > 0 && attempts_per_arc > (1ll << 62) / d.m) return ACC_ERR_OVERFLOW;
+        RGraph &rg = metas[(size_t)g];
+        rg.rowptr = reinterpret_cast<const long long *>(d.rowptr);
+        rg.col = d.col;
+        rg.m = d.m;
+        rg.n = d.n;
+        rg.moff = M;
+        rg.ooff = M * (long long)R;
+        rg.attempts = attempts_per_arc * d.m;
+        rg.seed = seeds[g];
+        rg.voff = (int)NV;
+        M += d.m;
+        NV += d.n;
+        if (M >= (1ll << 40) || NV >= (1ll << 31)) return ACC_ERR_OVERFLOW;
+    }
+    if (R > 0 && M > (1ll << 62) / R) return ACC_ERR_OVERFLOW;
+    if (M * (long long)R > 0 && !d_out) return ACC_ERR_ARG;
+    int rc;
+    const bool same = c->rand_meta && c->rand_rows && c->rand_host.size() == metas.size() &&
+                      (G == 0 || memcmp(c->rand_host.data(), metas.data(), sizeof(RGraph) * (size_t)G) == 0);
+    if (!same) {
+        // the previous call on this stream may still read the descriptors
+        if (!ok(cudaStreamSynchronize(s))) return ACC_ERR_CUDA;
+        c->rand_host.clear();
+        if ((rc = grow(&c->rand_meta, &c->rand_meta_cap, (size_t)G + 1))) return rc;
+        if ((rc = grow(&c->rand_rows, &c->rand_rows_cap, (size_t)M + 1))) return rc;
+        if (G > 0 &&
+            !ok(cudaMemcpy(c->rand_meta, metas.data(), sizeof(RGraph) * (size_t)G, cudaMemcpyHostToDevice)))
+            return ACC_ERR_CUDA;
+        c->rand_host = metas;
+    }
+    if (!c->status_dev && !ok(cudaMalloc(&c->status_dev, sizeof(int)))) return ACC_ERR_NOMEM;
+    int *status = d_status ? d_status : c->status_dev;
+    if (!ok(cudaMemsetAsync(status, 0, sizeof(int), s))) return ACC_ERR_CUDA;
+    rc = launch_randomise(c->rand_meta, G, R, M, NV, mode, c->rand_rows, d_out,
+                          reinterpret_cast<long long *>(d_accepted), status, c->num_sms, s);
+    if (rc < 0) return rc;
+    return finish(c, s, d_status);
 }
 
 int acc_motif_class_code(acc_ctx *c, int k, int32_t cls, uint32_t *code) {

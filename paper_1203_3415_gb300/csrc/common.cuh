@@ -182,6 +182,26 @@ int launch_formula3(const GSet &gs, const uint32_t *state, const long long *nptr
 // batch.cu: Z-scores of each group's real graph against its randomisations.
 int launch_zscores(const long long *counts, int groups, int group_size, int K, double *z, cudaStream_t s);
 
+// randomise.cu: randomised copies of a set of graphs.  Graph g's copies
+// start at element ooff of the output, copy r at ooff + r * m, and use the
+// SplitMix64 stream seeded seed + r.
+struct RGraph {
+    const long long *rowptr;  // input out-CSR (device)
+    const int *col;
+    long long m;
+    long long moff;           // first arc of the graph in the set's numbering (row table)
+    long long ooff;           // first element of the graph's copies in the output
+    long long attempts;       // swap attempts per copy
+    unsigned long long seed;  // stream of copy 0
+    int n;
+    int voff;                 // first vertex of the graph in the set's numbering
+};
+// Validates the graphs and fills rows (int4[M]: begin, end, source of each
+// position), then runs the copies (mode ACC_RAND_SWAP or ACC_RAND_MUTUAL);
+// the copies are skipped when *status is set.
+int launch_randomise(const RGraph *meta, int G, int R, long long M, long long NV, int mode, int4 *rows, int *out,
+                     long long *accepted, int *status, int num_sms, cudaStream_t s);
+
 // phase 1: light units run, heavy units queued; phase 2: the queue drained.
 // The grid is the full persistent grid times grid_num / grid_den (at least
 // one block per SM).

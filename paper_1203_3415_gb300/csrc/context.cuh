@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 using acc::GMeta;
@@ -56,6 +58,13 @@ struct acc_ctx {
     GSet batch_set = {};
     long long batch_words = 0, batch_arcs = 0;
     int batch_max_n = 0;
+
+    // randomised copies: graph descriptors and the per-position row table
+    acc::RGraph *rand_meta = nullptr;
+    size_t rand_meta_cap = 0;
+    int4 *rand_rows = nullptr;
+    size_t rand_rows_cap = 0;
+    std::vector<acc::RGraph> rand_host;  // the descriptors on the device
 
     // host-buffer entry point
     long long *h2d_rowptr = nullptr;

@@ -1,0 +1,238 @@
+// Randomised copies on the device: the random ensemble of the significance
+// step (Implementation section, steps i and iii: the real graph and a set of
+// random graphs are counted; the paper fixes no generator).
+//
+// Double-edge swaps on the out-CSR: arc e runs from the row holding position
+// e to col[e].  A copy starts as col and keeps rowptr; an attempt draws two
+// positions e1, e2 uniformly and, for arcs a -> b and c -> d, retargets them
+// to a -> d and c -> b unless that makes a self-loop or a repeated arc, so
+// every out- and in-degree is kept.  The mutual mode also keeps mutual arcs
+// mutual (two single arcs swap as above; two mutual pairs a <-> b and c <-> d
+// become a <-> d and c <-> b; mixed draws are rejected), so every vertex keeps
+// its single in-, single out- and mutual degree.
+//
+// Random numbers: SplitMix64 (Steele, Lea and Flood, 2014), one stream per
+// copy started at its seed, two draws per attempt, a draw mapped below m by
+// the high half of its 64 x 64-bit product with m (Lemire, 2019).
+//
+// Layout: a warp per copy.  "Is a -> d an arc?" is a scan of row a of the
+// copy itself (m ints, which is also the output), so no other per-copy
+// structure exists.  Positions are grouped by row, so the rows of e1 and e2
+// (the rows of a and c) come from a per-position table shared by every copy
+// ({begin, end, source}), read one attempt ahead.  Each half-warp holds one
+// of the two rows; in the plain mode an attempt costs one round trip to
+// memory (both rows and both targets at once), the mutual mode two more
+// (the rows of b and d).
+#include "common.cuh"
+
+namespace acc {
+
+namespace {
+
+constexpr int kRandThreads = 128;
+constexpr int kRandU = 4;  // row entries per lane read with the attempt's first loads
+constexpr int kHalf = 16;
+
+__device__ __forceinline__ uint64_t splitmix_next(uint64_t &s) {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ int splitmix_below(uint64_t &s, int bound) {
+    return (int)__umul64hi(splitmix_next(s), (uint64_t)bound);
+}
+
+__device__ __forceinline__ int find_graph(const RGraph *gr, int G, long long q, bool by_vertex) {
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((by_vertex ? (long long)gr[mid].voff : gr[mid].moff) <= q) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per-position row table and input validation (thread per arc, then thread
+// per vertex).  Malformed rows (rowptr[0] != 0, decreasing, outside [0, m],
+// rowptr[n] != m), targets outside [0, n) and self-loops set *status; every
+// table entry stays inside the graph's positions.
+__global__ void k_rand_rows(const RGraph *__restrict__ gr, int G, long long M, long long NV, int4 *rows,
+                            int *status) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (long long q = t0; q < M; q += stride) {
+        const RGraph rg = gr[find_graph(gr, G, q, false)];
+        const int p = (int)(q - rg.moff);
+        int lo = 0, hi = rg.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (rg.rowptr[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        const long long beg = rg.n > 0 ? rg.rowptr[lo] : 1, end = rg.n > 0 ? rg.rowptr[lo + 1] : 0;
+        const int u = rg.col[p];
+        int4 e = make_int4(p, p + 1, lo, 0);
+        if (beg < 0 || beg > p || end <= p || end > rg.m || u < 0 || u >= rg.n || u == lo)
+            set_status(status, ACC_ERR_INPUT);
+        else
+            e = make_int4((int)beg, (int)end, lo, 0);
+        rows[q] = e;
+    }
+    for (long long x = t0; x < NV; x += stride) {
+        const RGraph rg = gr[find_graph(gr, G, x, true)];
+        const int v = (int)(x - rg.voff);
+        const long long b = rg.rowptr[v], e = rg.rowptr[v + 1];
+        if (b < 0 || e < b || e > rg.m || (v == 0 && b != 0) || (v == rg.n - 1 && e != rg.m))
+            set_status(status, ACC_ERR_INPUT);
+    }
+}
+
+// In this half-warp's row cp[beg, end): the position of w1 (or -1) and
+// whether w2 occurs.  The first kRandU * 16 entries were read into v.
+__device__ __forceinline__ void half_search(const int *cp, int beg, int end, int hl, const int (&v)[kRandU], int w1,
+                                            int w2, int &pos1, bool &has2) {
+    pos1 = -1;
+    has2 = false;
+#pragma unroll
+    for (int j = 0; j < kRandU; j++) {
+        const int q = beg + hl + kHalf * j;
+        if (q < end) {
+            if (v[j] == w1) pos1 = q;
+            has2 |= v[j] == w2;
+        }
+    }
+    for (int q = beg + kHalf * kRandU + hl; q < end; q += kHalf) {
+        const int x = cp[q];
+        if (x == w1) pos1 = q;
+        has2 |= x == w2;
+    }
+}
+
+__device__ __forceinline__ void half_load(const int *cp, int beg, int end, int hl, int (&v)[kRandU]) {
+#pragma unroll
+    for (int j = 0; j < kRandU; j++) {
+        const int q = beg + hl + kHalf * j;
+        v[j] = q < end ? cp[q] : -1;
+    }
+}
+
+// One attempt on copy cp (e1 != e2; r1, r2 the rows of e1 and e2).  Returns
+// whether it was accepted; the copy is updated and the update is visible to
+// the whole warp on return.
+template <bool MUTUAL>
+__device__ __forceinline__ bool attempt(int *cp, const long long *__restrict__ rowptr, int m, int e1, int e2,
+                                        int4 r1, int4 r2, int lane) {
+    const int half = lane >> 4, hl = lane & 15;
+    const int4 rr = half ? r2 : r1;  // half 0: row a (arc e1), half 1: row c (arc e2)
+    const int x = cp[half ? e2 : e1];
+    int v[kRandU];
+    half_load(cp, rr.x, rr.y, hl, v);
+    const int b = __shfl_sync(kFull, x, 0), d = __shfl_sync(kFull, x, kHalf);
+    const int a = r1.z, c = r2.z;
+    if (a == d || c == b) return false;
+    int p;
+    bool unused;
+    half_search(cp, rr.x, rr.y, hl, v, half ? b : d, -2, p, unused);  // a -> d (half 0), c -> b (half 1)
+    if (__any_sync(kFull, p >= 0)) return false;
+    int p1 = -1, p2 = -1;
+    if (MUTUAL) {
+        // rows of b (half 0) and d (half 1): the reverse arcs b -> a and d -> c
+        // (mutual arcs) and the arcs b -> c and d -> a (adjacency)
+        const int y = half ? d : b;
+        const int beg = (int)min(max(rowptr[y], 0ll), (long long)m);
+        const int end = (int)min(max(rowptr[y + 1], (long long)beg), (long long)m);
+        int u[kRandU];
+        half_load(cp, beg, end, hl, u);
+        int pm;
+        bool rev;
+        half_search(cp, beg, end, hl, u, half ? c : a, half ? a : c, pm, rev);
+        if (__any_sync(kFull, rev)) return false;
+        p1 = __reduce_max_sync(kFull, half ? -1 : pm);
+        p2 = __reduce_max_sync(kFull, half ? pm : -1);
+        if ((p1 >= 0) != (p2 >= 0)) return false;
+    }
+    if (lane == 0) {
+        cp[e1] = d;
+        cp[e2] = b;
+        if (MUTUAL && p1 >= 0) {
+            cp[p1] = c;
+            cp[p2] = a;
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+template <bool MUTUAL>
+__global__ void __launch_bounds__(kRandThreads) k_rand_swap(const RGraph *__restrict__ gr, int G, int R,
+                                                            const int4 *__restrict__ rows, int *out,
+                                                            long long *accepted, const int *status) {
+    if (*(volatile const int *)status) return;
+    const int lane = threadIdx.x & 31;
+    const long long items = (long long)G * R;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < items; w += nw) {
+        const int g = (int)(w / R), r = (int)(w - (long long)g * R);
+        const RGraph rg = gr[g];
+        const int m = (int)rg.m;
+        int *cp = out + rg.ooff + (long long)r * rg.m;
+        for (int e = lane; e < m; e += kWarp) cp[e] = __ldg(rg.col + e);
+        __syncwarp();
+        long long acc = 0;
+        if (m >= 2 && rg.attempts > 0) {
+            const int4 *rw = rows + rg.moff;
+            uint64_t s = rg.seed + (uint64_t)r;
+            int e1 = splitmix_below(s, m);
+            int e2 = splitmix_below(s, m);
+            int4 r1 = __ldg(rw + e1), r2 = __ldg(rw + e2);
+            for (long long t = 0; t < rg.attempts; t++) {
+                // the next attempt's draws and rows do not depend on this one
+                int f1 = 0, f2 = 0;
+                int4 q1 = r1, q2 = r2;
+                if (t + 1 < rg.attempts) {
+                    f1 = splitmix_below(s, m);
+                    f2 = splitmix_below(s, m);
+                    q1 = __ldg(rw + f1);
+                    q2 = __ldg(rw + f2);
+                }
+                if (e1 != e2 && attempt<MUTUAL>(cp, rg.rowptr, m, e1, e2, r1, r2, lane)) acc++;
+                e1 = f1;
+                e2 = f2;
+                r1 = q1;
+                r2 = q2;
+            }
+        }
+        if (lane == 0 && accepted) accepted[w] = acc;
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+int launch_randomise(const RGraph *meta, int G, int R, long long M, long long NV, int mode, int4 *rows, int *out,
+                     long long *accepted, int *status, int num_sms, cudaStream_t s) {
+    int launches = 0;
+    const long long work = M > NV ? M : NV;
+    if (work > 0) {
+        long long blocks = (work + 255) / 256;
+        if (blocks > (long long)num_sms * 8) blocks = (long long)num_sms * 8;
+        k_rand_rows<<<(int)blocks, 256, 0, s>>>(meta, G, M, NV, rows, status);
+        launches++;
+    }
+    const long long items = (long long)G * R;
+    if (items > 0) {
+        long long blocks = (items * kWarp + kRandThreads - 1) / kRandThreads;
+        if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
+        if (mode == ACC_RAND_MUTUAL)
+            k_rand_swap<true><<<(int)blocks, kRandThreads, 0, s>>>(meta, G, R, rows, out, accepted, status);
+        else
+            k_rand_swap<false><<<(int)blocks, kRandThreads, 0, s>>>(meta, G, R, rows, out, accepted, status);
+        launches++;
+    }
+    return cudaGetLastError() == cudaSuccess ? launches : ACC_ERR_CUDA;
+}
+
+}  // namespace acc
