@@ -247,6 +247,16 @@ ACC_API int acc_swap_randomise(acc_ctx *ctx, const acc_graph_desc *h_graphs, int
                                int32_t *d_out, int64_t *d_accepted, int32_t *d_status);
 
 /*
+ * Device memory acc_swap_randomise may keep for the copies' adjacency
+ * bitmaps (R * sum over graphs of n * ceil(n / 128) * 16 bytes; default
+ * 16 GiB).  Within the limit, and when growing to it leaves half of the free
+ * memory, ACC_RAND_SWAP decides 16 attempts per step speculatively; else it
+ * decides them one by one by scanning rows.  The copies are the same either
+ * way.  0 always scans rows.  Errors: ACC_ERR_ARG.
+ */
+ACC_API int acc_ctx_set_randomise_memory(acc_ctx *ctx, int64_t bytes);
+
+/*
  * Serving form: a request server with continuous batching on one GPU.
  *
  * Requests (resident graph, k) are submitted at any time.  A request is

@@ -351,6 +351,7 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaFree(c->gid);
     cudaFree(c->rand_meta);
     cudaFree(c->rand_rows);
+    cudaFree(c->rand_bits);
     cudaFree(c->h2d_rowptr);
     cudaFree(c->h2d_col);
     cudaFree(c->h2d_counts);
@@ -496,7 +497,7 @@ int acc_swap_randomise(acc_ctx *c, const acc_graph_desc *graphs, int32_t G, int3
     if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<RGraph> metas((size_t)G);
-    long long M = 0, NV = 0;
+    long long M = 0, NV = 0, bwords = 0;
     for (int g = 0; g < G; g++) {
         const acc_graph_desc &d = graphs[g];
         if (!d.rowptr || (d.m > 0 && !d.col)) return ACC_ERR_ARG;
@@ -512,9 +513,13 @@ int acc_swap_randomise(acc_ctx *c, const acc_graph_desc *graphs, int32_t G, int3
         rg.attempts = attempts_per_arc * d.m;
         rg.seed = seeds[g];
         rg.voff = (int)NV;
+        rg.bw = (int)((((long long)d.n + 31) / 32 + 3) & ~3ll);
+        rg.boff = bwords;
         M += d.m;
         NV += d.n;
         if (M >= (1ll << 40) || NV >= (1ll << 31)) return ACC_ERR_OVERFLOW;
+        const long long per_copy = (long long)d.n * rg.bw;
+        bwords = (R > 0 && per_copy > ((1ll << 60) - bwords) / R) ? (1ll << 60) : bwords + per_copy * R;
     }
     if (R > 0 && M > (1ll << 62) / R) return ACC_ERR_OVERFLOW;
     if (M * (long long)R > 0 && !d_out) return ACC_ERR_ARG;
@@ -532,13 +537,32 @@ int acc_swap_randomise(acc_ctx *c, const acc_graph_desc *graphs, int32_t G, int3
             return ACC_ERR_CUDA;
         c->rand_host = metas;
     }
+    // the plain mode runs speculatively when the copies' adjacency bitmaps fit
+    // the limit (and half of the free device memory when they must grow)
+    uint32_t *bits = nullptr;
+    if (mode == ACC_RAND_SWAP && bwords > 0 && bwords < (1ll << 60) && bwords * 4 <= c->rand_bits_limit) {
+        bool fits = (size_t)bwords <= c->rand_bits_cap;
+        if (!fits) {
+            size_t free_b = 0, total_b = 0;
+            fits = ok(cudaMemGetInfo(&free_b, &total_b)) && (size_t)bwords * 4 * 2 <= free_b;
+            cudaGetLastError();
+            if (fits && grow(&c->rand_bits, &c->rand_bits_cap, (size_t)bwords) != ACC_OK) fits = false;
+        }
+        if (fits) bits = c->rand_bits;
+    }
     if (!c->status_dev && !ok(cudaMalloc(&c->status_dev, sizeof(int)))) return ACC_ERR_NOMEM;
     int *status = d_status ? d_status : c->status_dev;
     if (!ok(cudaMemsetAsync(status, 0, sizeof(int), s))) return ACC_ERR_CUDA;
-    rc = launch_randomise(c->rand_meta, G, R, M, NV, mode, c->rand_rows, d_out,
+    rc = launch_randomise(c->rand_meta, G, R, M, NV, mode, c->rand_rows, d_out, bits,
                           reinterpret_cast<long long *>(d_accepted), status, c->num_sms, s);
     if (rc < 0) return rc;
     return finish(c, s, d_status);
+}
+
+int acc_ctx_set_randomise_memory(acc_ctx *c, int64_t bytes) {
+    if (!c || bytes < 0) return ACC_ERR_ARG;
+    c->rand_bits_limit = bytes;
+    return ACC_OK;
 }
 
 int acc_motif_class_code(acc_ctx *c, int k, int32_t cls, uint32_t *code) {

@@ -193,14 +193,18 @@ struct RGraph {
     long long ooff;           // first element of the graph's copies in the output
     long long attempts;       // swap attempts per copy
     unsigned long long seed;  // stream of copy 0
+    long long boff;           // first word of the graph's copies' adjacency bitmaps
     int n;
     int voff;                 // first vertex of the graph in the set's numbering
+    int bw;                   // bitmap words per row (a multiple of 4)
+    int pad;
 };
 // Validates the graphs and fills rows (int4[M]: begin, end, source of each
 // position), then runs the copies (mode ACC_RAND_SWAP or ACC_RAND_MUTUAL);
-// the copies are skipped when *status is set.
+// the copies are skipped when *status is set.  With bits non-null (R times
+// the graphs' n * bw words) the plain mode runs the speculative kernel.
 int launch_randomise(const RGraph *meta, int G, int R, long long M, long long NV, int mode, int4 *rows, int *out,
-                     long long *accepted, int *status, int num_sms, cudaStream_t s);
+                     uint32_t *bits, long long *accepted, int *status, int num_sms, cudaStream_t s);
 
 // phase 1: light units run, heavy units queued; phase 2: the queue drained.
 // The grid is the full persistent grid times grid_num / grid_den (at least

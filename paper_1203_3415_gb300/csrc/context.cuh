@@ -65,6 +65,9 @@ struct acc_ctx {
     int4 *rand_rows = nullptr;
     size_t rand_rows_cap = 0;
     std::vector<acc::RGraph> rand_host;  // the descriptors on the device
+    uint32_t *rand_bits = nullptr;       // the copies' adjacency bitmaps
+    size_t rand_bits_cap = 0;
+    long long rand_bits_limit = 16ll << 30;  // bytes the bitmaps may take
 
     // host-buffer entry point
     long long *h2d_rowptr = nullptr;

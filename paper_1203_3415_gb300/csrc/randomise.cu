@@ -15,14 +15,23 @@
 // copy started at its seed, two draws per attempt, a draw mapped below m by
 // the high half of its 64 x 64-bit product with m (Lemire, 2019).
 //
-// Layout: a warp per copy.  "Is a -> d an arc?" is a scan of row a of the
-// copy itself (m ints, which is also the output), so no other per-copy
-// structure exists.  Positions are grouped by row, so the rows of e1 and e2
-// (the rows of a and c) come from a per-position table shared by every copy
-// ({begin, end, source}), read one attempt ahead.  Each half-warp holds one
-// of the two rows; in the plain mode an attempt costs one round trip to
-// memory (both rows and both targets at once), the mutual mode two more
-// (the rows of b and d).
+// Layout: a warp per copy; positions are grouped by row, so the rows of e1
+// and e2 (the rows of a and c) come from a per-position table shared by every
+// copy ({begin, end, source}).  Two kernels:
+//  - speculative (plain mode, when the copies' adjacency bitmaps fit the
+//    context's limit): the stream is counter-based (draw k is the mix of
+//    seed + (k + 1) * increment), so the warp draws 16 attempts at once, two
+//    lanes each, and decides all of them against the copy as it stands: one
+//    round trip for both targets and rows, one for the two bitmap bits.  An
+//    attempt reads and writes only its own two rows (targets, bits), so the
+//    decisions are exact up to the first attempt that shares a row with an
+//    earlier accepted one; that prefix is applied and the next batch starts
+//    at the first such attempt.  The copies equal the one-by-one procedure's.
+//  - one by one (mutual mode, or bitmaps over the limit): "is a -> d an
+//    arc?" is a scan of row a of the copy itself, each half-warp holding one
+//    of the two rows; the next attempt's draws and rows are read ahead.  An
+//    attempt costs one round trip in the plain mode, two more in the mutual
+//    mode (the rows of b and d).
 #include "common.cuh"
 
 namespace acc {
@@ -166,6 +175,90 @@ __device__ __forceinline__ bool attempt(int *cp, const long long *__restrict__ r
     return true;
 }
 
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+// Draw k (0-based) of the stream seeded `seed`, mapped below `bound`.
+__device__ __forceinline__ int splitmix_draw_below(uint64_t seed, unsigned long long k, int bound) {
+    uint64_t s = seed + (uint64_t)k * kGamma;  // the state before draw k
+    return splitmix_below(s, bound);
+}
+
+// Plain mode, speculative batches of 16 attempts (lanes 2p and 2p + 1 hold
+// the arcs e1 and e2 of attempt t + p).  bits: the copies' adjacency bitmaps,
+// row a of a copy at a * bw words.
+__global__ void __launch_bounds__(kRandThreads) k_rand_swap_spec(const RGraph *__restrict__ gr, int G, int R,
+                                                                 const int4 *__restrict__ rows, int *out,
+                                                                 uint32_t *bits, long long *accepted,
+                                                                 int *status) {
+    if (*(volatile const int *)status) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned earlier = (1u << (lane & ~1)) - 1u;  // lanes of the batch's earlier attempts
+    const long long items = (long long)G * R;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < items; w += nw) {
+        const int g = (int)(w / R), r = (int)(w - (long long)g * R);
+        const RGraph rg = gr[g];
+        const int m = (int)rg.m, bw = rg.bw;
+        const int4 *rw = rows + rg.moff;
+        int *cp = out + rg.ooff + (long long)r * rg.m;
+        uint32_t *bm = bits + rg.boff + (long long)r * rg.n * bw;
+        uint4 *bm4 = reinterpret_cast<uint4 *>(bm);
+        const long long words4 = (long long)rg.n * bw / 4;
+        for (long long i = lane; i < words4; i += kWarp) bm4[i] = make_uint4(0u, 0u, 0u, 0u);
+        __syncwarp();
+        for (int e = lane; e < m; e += kWarp) {
+            const int u = __ldg(rg.col + e);
+            cp[e] = u;
+            atomicOr(&bm[(long long)__ldg(&rw[e].z) * bw + (u >> 5)], 1u << (u & 31));
+        }
+        __syncwarp();
+        long long acc = 0;
+        const uint64_t seed = rg.seed + (uint64_t)r;
+        long long t = 0, batches = 0;
+        while (m >= 2 && t < rg.attempts) {
+            if (++batches > rg.attempts) {  // every batch applies at least one attempt
+                set_status(status, ACC_ERR_INTERNAL);
+                break;
+            }
+            const long long left = rg.attempts - t;
+            const int P = left < 16 ? (int)left : 16;
+            const bool live = (lane >> 1) < P;
+            const int e = splitmix_draw_below(seed, (unsigned long long)(2 * t + lane), m);
+            const int src = __ldg(&rw[e].z);
+            const int x = cp[e];                              // this arc's target
+            const int y = __shfl_xor_sync(kFull, x, 1);       // the other arc's target
+            const int ep = __shfl_xor_sync(kFull, e, 1);
+            // even lane: a -> b with b = x, looks up a -> d (d = y); odd lane:
+            // c -> d with d = x, looks up c -> b (b = y)
+            // (every lane takes part in each shuffle: none sits behind && or ?:)
+            const bool ok = live && e != ep && src != y;
+            const bool ok_other = __shfl_xor_sync(kFull, ok, 1);
+            const bool pair_ok = ok && ok_other;
+            bool hit = false;
+            if (pair_ok) hit = (bm[(long long)src * bw + (y >> 5)] >> (y & 31)) & 1u;
+            const bool hit_other = __shfl_xor_sync(kFull, hit, 1);
+            const bool take = pair_ok && !hit && !hit_other;
+            const unsigned A = __ballot_sync(kFull, take);
+            const unsigned same_row = __match_any_sync(kFull, src);
+            const unsigned C = __ballot_sync(kFull, live && (same_row & A & earlier) != 0u);
+            const unsigned Cp = (C | (C >> 1)) & 0x55555555u;  // bit 2p: attempt p shares a row
+            const int adv = Cp ? min(P, (__ffs(Cp) - 1) >> 1) : P;
+            const bool commit = take && (lane >> 1) < adv;
+            if (commit) {
+                uint32_t *row = bm + (long long)src * bw;
+                cp[e] = y;
+                atomicAnd(&row[x >> 5], ~(1u << (x & 31)));
+                atomicOr(&row[y >> 5], 1u << (y & 31));
+            }
+            acc += __popc(__ballot_sync(kFull, commit)) >> 1;
+            __syncwarp();
+            t += adv;
+        }
+        if (lane == 0 && accepted) accepted[w] = acc;
+        __syncwarp();
+    }
+}
+
 template <bool MUTUAL>
 __global__ void __launch_bounds__(kRandThreads) k_rand_swap(const RGraph *__restrict__ gr, int G, int R,
                                                             const int4 *__restrict__ rows, int *out,
@@ -213,7 +306,7 @@ __global__ void __launch_bounds__(kRandThreads) k_rand_swap(const RGraph *__rest
 }  // namespace
 
 int launch_randomise(const RGraph *meta, int G, int R, long long M, long long NV, int mode, int4 *rows, int *out,
-                     long long *accepted, int *status, int num_sms, cudaStream_t s) {
+                     uint32_t *bits, long long *accepted, int *status, int num_sms, cudaStream_t s) {
     int launches = 0;
     const long long work = M > NV ? M : NV;
     if (work > 0) {
@@ -228,6 +321,8 @@ int launch_randomise(const RGraph *meta, int G, int R, long long M, long long NV
         if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
         if (mode == ACC_RAND_MUTUAL)
             k_rand_swap<true><<<(int)blocks, kRandThreads, 0, s>>>(meta, G, R, rows, out, accepted, status);
+        else if (bits)
+            k_rand_swap_spec<<<(int)blocks, kRandThreads, 0, s>>>(meta, G, R, rows, out, bits, accepted, status);
         else
             k_rand_swap<false><<<(int)blocks, kRandThreads, 0, s>>>(meta, G, R, rows, out, accepted, status);
         launches++;

@@ -69,13 +69,18 @@ def mixed(seed):
     return graphs
 
 
-@pytest.mark.parametrize("mode", [0, 1], ids=["swap", "mutual"])
-def test_copies_equal_oracle(counter, mode):
-    graphs = mixed(70 + mode)
+@pytest.mark.parametrize("mode,bitmaps", [(0, True), (0, False), (1, True)],
+                         ids=["swap_speculative", "swap_row_scan", "mutual"])
+def test_copies_equal_oracle(counter, mode, bitmaps):
+    graphs = mixed(70 + mode + 2 * bitmaps)
     dev = to_device(graphs)
     R = 5
     seeds = [1_000 * (g + 1) + 17 for g in range(len(graphs))]
-    out, acc = counter.randomise(dev, R, seeds, attempts_per_arc=3, mode=mode)
+    counter.set_randomise_memory(16 << 30 if bitmaps else 0)
+    try:
+        out, acc = counter.randomise(dev, R, seeds, attempts_per_arc=3, mode=mode)
+    finally:
+        counter.set_randomise_memory(16 << 30)
     check_against_oracle(graphs, dev, R, seeds, 3, mode, out, acc)
 
 
@@ -94,9 +99,11 @@ def test_large_graph_with_hubs(counter):
     g = synth.chung_lu_k4()  # n=20000, m=100000, rows up to 500 arcs
     graphs = [(g.n, g.src, g.dst)]
     dev = to_device(graphs)
-    for mode in (0, 1):
+    for mode, limit in ((0, 16 << 30), (0, 0), (1, 16 << 30)):
+        counter.set_randomise_memory(limit)
         out, acc = counter.randomise(dev, 2, [42], attempts_per_arc=3, mode=mode)
         check_against_oracle(graphs, dev, 2, [42], 3, mode, out, acc)
+    counter.set_randomise_memory(16 << 30)
 
 
 def test_async_status_and_empty_calls(counter):
