@@ -356,7 +356,12 @@ ACC_API int acc_motif_last_stats(acc_ctx *ctx, int64_t *h_stats);
  *   Algorithm s3, Table starb): open triples from the sizes of each vertex's
  *   out-only / in-only / bidirected neighbour sets, triangles listed once and
  *   the open triples they were counted as moved out; no subset is visited.
- *   For k = 4, 5 it counts as ACC_MODE_COUNT.
+ *   For k = 4, the paper's per-edge formulas (Thm lema4d, Cor coro:a,
+ *   Algorithm mine, Fact correction): for each edge {u, v} of G*, pairs of
+ *   vertices adjacent to u or v counted per pair of its 15 neighbour sets
+ *   (Fig. edgesets), linked pairs moved to their own class, each class then
+ *   divided by the number of edges that reach its pattern.  For k = 5 it
+ *   counts as ACC_MODE_COUNT.
  * All modes give identical counts.  Errors: ACC_ERR_ARG.
  */
 #define ACC_MODE_COUNT 0

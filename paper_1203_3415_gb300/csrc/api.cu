@@ -188,16 +188,20 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     a.queue_cap = c->queue_cap;
     a.scratch = c->scratch;
     a.scratch_per_warp = scratch_per_warp(max_n);
-    a.mode = c->mode;
+    a.mode = c->mode == ACC_MODE_ENUMERATE ? 1 : 0;  // the formula mode counts k = 5 as the count mode
     a.light = c->sched_light > 0 ? c->sched_light : enum_default_light();
     a.target = c->sched_target > 0 ? c->sched_target : enum_default_target();
     a.counts = reinterpret_cast<unsigned long long *>(counts);
     a.status = status;
     const bool any = gs.NV > 0;
-    const bool formula = k == 3 && c->mode == ACC_MODE_FORMULA;
+    const bool formula = (k == 3 || k == 4) && c->mode == ACC_MODE_FORMULA;
     if (any && formula) {
-        rc = launch_formula3(gs, c->state, c->nptr, c->deg, c->lo, c->nbr, c->lut[3],
-                             reinterpret_cast<unsigned long long *>(counts), status, c->num_sms, s);
+        if (k == 3)
+            rc = launch_formula3(gs, c->state, c->nptr, c->deg, c->lo, c->nbr, c->lut[3],
+                                 reinterpret_cast<unsigned long long *>(counts), status, c->num_sms, s);
+        else
+            rc = launch_formula4(gs, c->state, c->nptr, c->deg, c->lo, c->nbr, c->lut[4], c->class_code_dev[4],
+                                 c->info, reinterpret_cast<unsigned long long *>(counts), status, c->num_sms, s);
         if (rc < 0) return rc;
         launches += rc;
     } else if (any) {

@@ -179,6 +179,11 @@ struct EnumArgs {
 int launch_formula3(const GSet &gs, const uint32_t *state, const long long *nptr, const int *deg, const int *lo,
                     const uint32_t *nbr, const int16_t *lut, unsigned long long *counts, int *status, int num_sms,
                     cudaStream_t s);
+// formula4.cu: k = 4 counts by the per-edge formulas, then the division by
+// each class's multiplicity (two launches).
+int launch_formula4(const GSet &gs, const uint32_t *state, const long long *nptr, const int *deg, const int *lo,
+                    const uint32_t *nbr, const int16_t *lut, const uint32_t *class_code, const GraphInfo *info,
+                    unsigned long long *counts, int *status, int num_sms, cudaStream_t s);
 // batch.cu: Z-scores of each group's real graph against its randomisations.
 int launch_zscores(const long long *counts, int groups, int group_size, int K, double *z, cudaStream_t s);
 
