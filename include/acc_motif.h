@@ -360,8 +360,12 @@ ACC_API int acc_motif_last_stats(acc_ctx *ctx, int64_t *h_stats);
  *   Algorithm mine, Fact correction): for each edge {u, v} of G*, pairs of
  *   vertices adjacent to u or v counted per pair of its 15 neighbour sets
  *   (Fig. edgesets), linked pairs moved to their own class, each class then
- *   divided by the number of edges that reach its pattern.  For k = 5 it
- *   counts as ACC_MODE_COUNT.
+ *   divided by the number of edges that reach its pattern.  For k = 5, the
+ *   paper's per-triple formulas (Lemma lema5d, Algorithm fived, Algorithm
+ *   partfive): for each connected 3-set of G*, pairs of vertices adjacent to
+ *   it counted per pair of its 63 neighbour sets, linked pairs moved to their
+ *   own class, each class divided by the number of connected 3-sets that
+ *   reach its pattern.
  * All modes give identical counts.  Errors: ACC_ERR_ARG.
  */
 #define ACC_MODE_COUNT 0

@@ -126,6 +126,7 @@ int ensure_workspace(acc_ctx *c, long long NV, long long state_words, long long 
         c->n_cap = a;
     }
     if ((rc = grow(&c->tiles, &c->tiles_cap, (size_t)scan_tiles_needed(NV) + 1))) return rc;
+    if ((rc = grow(&c->f5_pre, &c->f5_pre_cap, (size_t)NV + 1))) return rc;
     if ((rc = grow(&c->nbr, &c->nbr_cap, (size_t)(2 * arcs) + 1))) return rc;
     if ((rc = grow(&c->occ, &c->occ_cap, (size_t)NV * (size_t)occ_words(max_n) + 1))) return rc;
     if (!c->info) {
@@ -188,20 +189,23 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     a.queue_cap = c->queue_cap;
     a.scratch = c->scratch;
     a.scratch_per_warp = scratch_per_warp(max_n);
-    a.mode = c->mode == ACC_MODE_ENUMERATE ? 1 : 0;  // the formula mode counts k = 5 as the count mode
+    a.mode = c->mode == ACC_MODE_ENUMERATE ? 1 : 0;
     a.light = c->sched_light > 0 ? c->sched_light : enum_default_light();
     a.target = c->sched_target > 0 ? c->sched_target : enum_default_target();
     a.counts = reinterpret_cast<unsigned long long *>(counts);
     a.status = status;
     const bool any = gs.NV > 0;
-    const bool formula = (k == 3 || k == 4) && c->mode == ACC_MODE_FORMULA;
+    const bool formula = c->mode == ACC_MODE_FORMULA;
     if (any && formula) {
         if (k == 3)
             rc = launch_formula3(gs, c->state, c->nptr, c->deg, c->lo, c->nbr, c->lut[3],
                                  reinterpret_cast<unsigned long long *>(counts), status, c->num_sms, s);
-        else
+        else if (k == 4)
             rc = launch_formula4(gs, c->state, c->nptr, c->deg, c->lo, c->nbr, c->lut[4], c->class_code_dev[4],
                                  c->info, reinterpret_cast<unsigned long long *>(counts), status, c->num_sms, s);
+        else
+            rc = launch_formula5(gs, c->state, c->nptr, c->deg, c->nbr, c->lut[5], c->class_code_dev[5], c->f5_pre,
+                                 reinterpret_cast<unsigned long long *>(counts), status, c->num_sms, s);
         if (rc < 0) return rc;
         launches += rc;
     } else if (any) {
@@ -345,6 +349,7 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaFree(c->label);
     cudaFree(c->deg_in);
     cudaFree(c->tiles);
+    cudaFree(c->f5_pre);
     cudaFree(c->occ);
     cudaFree(c->nbr);
     cudaFree(c->info);

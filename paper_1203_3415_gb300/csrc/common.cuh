@@ -184,6 +184,11 @@ int launch_formula3(const GSet &gs, const uint32_t *state, const long long *nptr
 int launch_formula4(const GSet &gs, const uint32_t *state, const long long *nptr, const int *deg, const int *lo,
                     const uint32_t *nbr, const int16_t *lut, const uint32_t *class_code, const GraphInfo *info,
                     unsigned long long *counts, int *status, int num_sms, cudaStream_t s);
+// formula5.cu: k = 5 counts by the per-triple formulas (pre: NV + 1 values of
+// scratch), then the division by each class's multiplicity (three launches).
+int launch_formula5(const GSet &gs, const uint32_t *state, const long long *nptr, const int *deg, const uint32_t *nbr,
+                    const int16_t *lut, const uint32_t *class_code, long long *pre, unsigned long long *counts,
+                    int *status, int num_sms, cudaStream_t s);
 // batch.cu: Z-scores of each group's real graph against its randomisations.
 int launch_zscores(const long long *counts, int groups, int group_size, int K, double *z, cudaStream_t s);
 

@@ -33,6 +33,8 @@ struct acc_ctx {
     size_t n_cap = 0;
     long long *tiles = nullptr;
     size_t tiles_cap = 0;
+    long long *f5_pre = nullptr;  // k = 5 formula path: prefix of C(deg, 2)
+    size_t f5_pre_cap = 0;
     uint32_t *nbr = nullptr;
     uint32_t *occ = nullptr;  // pair-state row occupancy bitmaps
     size_t occ_cap = 0;

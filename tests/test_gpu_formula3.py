@@ -83,7 +83,7 @@ def test_batch_and_mode_agreement(counter):
     got = counter.run_batch().cpu().numpy()
     for i, (n, s, d) in enumerate(graphs):
         assert got[i].tolist() == oracle.count(n, s, d, 3).tolist(), i
-    # k = 5 in this mode counts as the count mode does
+    # k = 5 in this mode runs the per-triple formulas
     h = synth.chung_lu(600, 2400, 2.2, 60, 10, 15)
     assert gpu_count(counter, h.n, h.src, h.dst, 5).tolist() == \
         oracle.count(h.n, h.src, h.dst, 5, threads=oracle.max_threads()).tolist()
