@@ -651,7 +651,7 @@ int acc_motif_batch_autotune(acc_ctx *c, void *stream, int64_t *h_light, int64_t
     const long long light0 = c->sched_light, target0 = c->sched_target;
     // candidate schedules: light units from a warp each up to large units,
     // heavy units cut into small or large row tiles
-    const long long lights[] = {512, 2048, 8192, 32768};
+    const long long lights[] = {512, 2048, 8192, 32768, 131072, 1ll << 20};
     const long long targets[] = {1024, 4096, 16384};
     int64_t *counts = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
