@@ -8,6 +8,8 @@
 
 #include "common.cuh"
 #include "context.cuh"
+#include "formula.cuh"
+#include "randomise.cuh"
 
 using namespace acc;
 

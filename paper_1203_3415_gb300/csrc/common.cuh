@@ -175,46 +175,8 @@ struct EnumArgs {
     unsigned long long *counts; // int64[B * num_classes]
     int *status;
 };
-// formula3.cu: k = 3 counts by the per-vertex formulas (one launch).
-int launch_formula3(const GSet &gs, const uint32_t *state, const long long *nptr, const int *deg, const int *lo,
-                    const uint32_t *nbr, const int16_t *lut, unsigned long long *counts, int *status, int num_sms,
-                    cudaStream_t s);
-// formula4.cu: k = 4 counts by the per-edge formulas, then the division by
-// each class's multiplicity (two launches).
-int launch_formula4(const GSet &gs, const uint32_t *state, const long long *nptr, const int *deg, const int *lo,
-                    const uint32_t *nbr, const int16_t *lut, const uint32_t *class_code, const GraphInfo *info,
-                    unsigned long long *counts, int *status, int num_sms, cudaStream_t s);
-// formula5.cu: k = 5 counts by the per-triple formulas (pre: NV + 1 values of
-// scratch), then the division by each class's multiplicity (three launches).
-int launch_formula5(const GSet &gs, const uint32_t *state, const long long *nptr, const int *deg, const uint32_t *nbr,
-                    const int16_t *lut, const uint32_t *class_code, long long *pre, unsigned long long *counts,
-                    int *status, int num_sms, cudaStream_t s);
 // batch.cu: Z-scores of each group's real graph against its randomisations.
 int launch_zscores(const long long *counts, int groups, int group_size, int K, double *z, cudaStream_t s);
-
-// randomise.cu: randomised copies of a set of graphs.  Graph g's copies
-// start at element ooff of the output, copy r at ooff + r * m, and use the
-// SplitMix64 stream seeded seed + r.
-struct RGraph {
-    const long long *rowptr;  // input out-CSR (device)
-    const int *col;
-    long long m;
-    long long moff;           // first arc of the graph in the set's numbering (row table)
-    long long ooff;           // first element of the graph's copies in the output
-    long long attempts;       // swap attempts per copy
-    unsigned long long seed;  // stream of copy 0
-    long long boff;           // first word of the graph's copies' adjacency bitmaps
-    int n;
-    int voff;                 // first vertex of the graph in the set's numbering
-    int bw;                   // bitmap words per row (a multiple of 4)
-    int pad;
-};
-// Validates the graphs and fills rows (int4[M]: begin, end, source of each
-// position), then runs the copies (mode ACC_RAND_SWAP or ACC_RAND_MUTUAL);
-// the copies are skipped when *status is set.  With bits non-null (R times
-// the graphs' n * bw words) the plain mode runs the speculative kernel.
-int launch_randomise(const RGraph *meta, int G, int R, long long M, long long NV, int mode, int4 *rows, int *out,
-                     uint32_t *bits, long long *accepted, int *status, int num_sms, cudaStream_t s);
 
 // phase 1: light units run, heavy units queued; phase 2: the queue drained.
 // The grid is the full persistent grid times grid_num / grid_den (at least

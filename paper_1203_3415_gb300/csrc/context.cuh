@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "randomise.cuh"
 
 using acc::GMeta;
 using acc::GSet;

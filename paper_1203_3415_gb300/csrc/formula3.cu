@@ -13,7 +13,7 @@
 // of x, one pair-state probe), adds 1 to its own class and moves the three
 // pairs it was counted as (one per centre) out of their open-triple classes.
 // Warp per vertex; classes come from the canonical-layout code table.
-#include "common.cuh"
+#include "formula.cuh"
 
 namespace acc {
 

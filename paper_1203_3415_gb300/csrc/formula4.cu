@@ -20,7 +20,7 @@
 // Warp per edge, taken from its smaller end; the linked pairs come from
 // scanning the lists of the union's members (each pair once, from its smaller
 // vertex), the entries spread over the lanes.
-#include "common.cuh"
+#include "formula.cuh"
 
 namespace acc {
 

@@ -17,7 +17,7 @@
 // its middle vertex p1, a triangle at its smallest vertex.  A work item is a
 // pair of entries of one list, the items of all lists numbered through a
 // prefix sum of C(deg, 2), a warp per item.
-#include "common.cuh"
+#include "formula.cuh"
 
 namespace acc {
 

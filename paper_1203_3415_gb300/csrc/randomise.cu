@@ -32,7 +32,7 @@
 //    of the two rows; the next attempt's draws and rows are read ahead.  An
 //    attempt costs one round trip in the plain mode, two more in the mutual
 //    mode (the rows of b and d).
-#include "common.cuh"
+#include "randomise.cuh"
 
 namespace acc {
 
