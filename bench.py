@@ -610,14 +610,16 @@ def run_significance_bench(args):
     out = torch.empty(R * m_total, dtype=torch.int32, device=dev)
     accepted = torch.empty((G, R), dtype=torch.int64, device=dev)
 
+    rmode = acc.ACC_RAND_MUTUAL if args.rand_mode == "mutual" else acc.ACC_RAND_SWAP
+
     def step():
-        counter.randomise(graphs, R, seeds, 3, out=out, accepted=accepted, status=status, stream=stream)
+        counter.randomise(graphs, R, seeds, 3, mode=rmode, out=out, accepted=accepted, status=status, stream=stream)
         counter.run_batch(counts=counts, status=status, stream=stream)
         acc._check(acc.acc_motif_zscores(counts.data_ptr(), G, R + 1, 4, stream.cuda_stream, z.data_ptr()),
                    "acc_motif_zscores")
 
     with torch.cuda.stream(stream):
-        counter.randomise(graphs, R, seeds, 3, out=out, accepted=accepted, status=status, stream=stream)
+        counter.randomise(graphs, R, seeds, 3, mode=rmode, out=out, accepted=accepted, status=status, stream=stream)
         batch = []
         for g, cps in zip(graphs, acc.Counter.copies(graphs, R, out)):
             batch.append(g)
@@ -636,7 +638,8 @@ def run_significance_bench(args):
         for a, b in rt:
             flush.fill_(3)
             a.record(stream)
-            counter.randomise(graphs, R, seeds, 3, out=out, accepted=accepted, status=status, stream=stream)
+            counter.randomise(graphs, R, seeds, 3, mode=rmode, out=out, accepted=accepted, status=status,
+                              stream=stream)
             b.record(stream)
     torch.cuda.synchronize(dev)
     rand_ms = min(a.elapsed_time(b) for a, b in rt)
@@ -676,7 +679,7 @@ def run_significance_bench(args):
         return 0
     gold = os.path.join(ROOT, "tests", "golden", "batch_k4.txt")
     parity = None
-    if os.path.exists(gold):
+    if os.path.exists(gold) and rmode == acc.ACC_RAND_SWAP:  # stored for the double-edge swaps
         import hashlib
         rows = [ln.split() for ln in open(gold) if ln.strip() and not ln.startswith("#")]
         host = counts.cpu().numpy()
@@ -695,6 +698,7 @@ def run_significance_bench(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": SIGNIFICANCE_WORKLOAD, "k": 4, "graphs": B, "bases": G,
                    "randomisations_per_base": R, "swap_attempts_per_copy": "3m",
+                   "randomisation": "mutual arcs kept" if rmode == acc.ACC_RAND_MUTUAL else "double-edge swaps",
                    "subgraphs_per_step": total,
                    "l2": "flushed between timed steps (256 MiB device write)",
                    "launch": "randomise + batched count + Z-scores replayed from one captured CUDA graph",
@@ -852,6 +856,8 @@ def main():
     ap.add_argument("--serve-policy", choices=["shortest", "fifo"], default="shortest",
                     help="serving admission order: smallest aged work estimate first, or submission order")
     ap.add_argument("--serve-aging-s", type=float, default=1.0)
+    ap.add_argument("--rand-mode", choices=["swap", "mutual"], default="swap",
+                    help="significance workload: double-edge swaps, or swaps that keep mutual arcs mutual")
     ap.add_argument("--mode", choices=["count", "enumerate", "formula"], default="count",
                     help="last two levels counted by state-vector groups, every leaf enumerated, or (k=3) the "
                          "per-vertex formulas")

@@ -249,10 +249,11 @@ ACC_API int acc_swap_randomise(acc_ctx *ctx, const acc_graph_desc *h_graphs, int
 /*
  * Device memory acc_swap_randomise may keep for the copies' adjacency
  * bitmaps (R * sum over graphs of n * ceil(n / 128) * 16 bytes; default
- * 16 GiB).  Within the limit, and when growing to it leaves half of the free
- * memory, ACC_RAND_SWAP decides 16 attempts per step speculatively; else it
- * decides them one by one by scanning rows.  The copies are the same either
- * way.  0 always scans rows.  Errors: ACC_ERR_ARG.
+ * 16 GiB), plus, for ACC_RAND_MUTUAL, 4 (R + 1) bytes per arc of reverse
+ * positions.  Within the limit, and when growing to it leaves half of the
+ * free memory, both modes decide 16 attempts per step speculatively; else
+ * they decide them one by one by scanning rows.  The copies are the same
+ * either way.  0 always scans rows.  Errors: ACC_ERR_ARG.
  */
 ACC_API int acc_ctx_set_randomise_memory(acc_ctx *ctx, int64_t bytes);
 

@@ -363,6 +363,8 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaFree(c->rand_meta);
     cudaFree(c->rand_rows);
     cudaFree(c->rand_bits);
+    cudaFree(c->rand_rpart);
+    cudaFree(c->rand_pts);
     cudaFree(c->h2d_rowptr);
     cudaFree(c->h2d_col);
     cudaFree(c->h2d_counts);
@@ -548,23 +550,39 @@ int acc_swap_randomise(acc_ctx *c, const acc_graph_desc *graphs, int32_t G, int3
             return ACC_ERR_CUDA;
         c->rand_host = metas;
     }
-    // the plain mode runs speculatively when the copies' adjacency bitmaps fit
-    // the limit (and half of the free device memory when they must grow)
+    // both modes run speculatively when the copies' adjacency bitmaps (and,
+    // for the mutual mode, the reverse positions of the graphs' and the
+    // copies' arcs) fit the limit, and half of the free device memory when
+    // they must grow
     uint32_t *bits = nullptr;
-    if (mode == ACC_RAND_SWAP && bwords > 0 && bwords < (1ll << 60) && bwords * 4 <= c->rand_bits_limit) {
-        bool fits = (size_t)bwords <= c->rand_bits_cap;
+    int *rpart = nullptr, *pts = nullptr;
+    const bool mutual = mode == ACC_RAND_MUTUAL;
+    const long long extra = mutual ? M + M * (long long)R : 0;  // ints
+    if (bwords > 0 && bwords < (1ll << 60) && (bwords + extra) * 4 <= c->rand_bits_limit) {
+        bool fits = (size_t)bwords <= c->rand_bits_cap &&
+                    (!mutual || ((size_t)M <= c->rand_rpart_cap && (size_t)(M * (long long)R) <= c->rand_pts_cap));
         if (!fits) {
             size_t free_b = 0, total_b = 0;
-            fits = ok(cudaMemGetInfo(&free_b, &total_b)) && (size_t)bwords * 4 * 2 <= free_b;
+            fits = ok(cudaMemGetInfo(&free_b, &total_b)) && (size_t)(bwords + extra) * 4 * 2 <= free_b;
             cudaGetLastError();
             if (fits && grow(&c->rand_bits, &c->rand_bits_cap, (size_t)bwords) != ACC_OK) fits = false;
+            if (fits && mutual &&
+                (grow(&c->rand_rpart, &c->rand_rpart_cap, (size_t)M) != ACC_OK ||
+                 grow(&c->rand_pts, &c->rand_pts_cap, (size_t)(M * (long long)R)) != ACC_OK))
+                fits = false;
         }
-        if (fits) bits = c->rand_bits;
+        if (fits) {
+            bits = c->rand_bits;
+            if (mutual) {
+                rpart = c->rand_rpart;
+                pts = c->rand_pts;
+            }
+        }
     }
     if (!c->status_dev && !ok(cudaMalloc(&c->status_dev, sizeof(int)))) return ACC_ERR_NOMEM;
     int *status = d_status ? d_status : c->status_dev;
     if (!ok(cudaMemsetAsync(status, 0, sizeof(int), s))) return ACC_ERR_CUDA;
-    rc = launch_randomise(c->rand_meta, G, R, M, NV, mode, c->rand_rows, d_out, bits,
+    rc = launch_randomise(c->rand_meta, G, R, M, NV, mode, c->rand_rows, d_out, bits, rpart, pts,
                           reinterpret_cast<long long *>(d_accepted), status, c->num_sms, s);
     if (rc < 0) return rc;
     return finish(c, s, d_status);

@@ -70,7 +70,11 @@ struct acc_ctx {
     std::vector<acc::RGraph> rand_host;  // the descriptors on the device
     uint32_t *rand_bits = nullptr;       // the copies' adjacency bitmaps
     size_t rand_bits_cap = 0;
-    long long rand_bits_limit = 16ll << 30;  // bytes the bitmaps may take
+    long long rand_bits_limit = 16ll << 30;  // bytes the bitmaps (and reverse positions) may take
+    int *rand_rpart = nullptr;           // mutual mode: reverse position of each arc of the graphs
+    size_t rand_rpart_cap = 0;
+    int *rand_pts = nullptr;             // mutual mode: the copies' reverse positions
+    size_t rand_pts_cap = 0;
 
     // host-buffer entry point
     long long *h2d_rowptr = nullptr;

@@ -69,7 +69,7 @@ __device__ __forceinline__ int find_graph(const RGraph *gr, int G, long long q, 
 // rowptr[n] != m), targets outside [0, n) and self-loops set *status; every
 // table entry stays inside the graph's positions.
 __global__ void k_rand_rows(const RGraph *__restrict__ gr, int G, long long M, long long NV, int4 *rows,
-                            int *status) {
+                            int *rpart, int *status) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     for (long long q = t0; q < M; q += stride) {
@@ -84,11 +84,25 @@ __global__ void k_rand_rows(const RGraph *__restrict__ gr, int G, long long M, l
         const long long beg = rg.n > 0 ? rg.rowptr[lo] : 1, end = rg.n > 0 ? rg.rowptr[lo + 1] : 0;
         const int u = rg.col[p];
         int4 e = make_int4(p, p + 1, lo, 0);
-        if (beg < 0 || beg > p || end <= p || end > rg.m || u < 0 || u >= rg.n || u == lo)
+        const bool bad = beg < 0 || beg > p || end <= p || end > rg.m || u < 0 || u >= rg.n || u == lo;
+        if (bad)
             set_status(status, ACC_ERR_INPUT);
         else
             e = make_int4((int)beg, (int)end, lo, 0);
         rows[q] = e;
+        if (rpart) {
+            // position of the reverse arc u -> lo in row u, or -1
+            int rp = -1;
+            if (!bad) {
+                const long long rb = min(max(rg.rowptr[u], 0ll), rg.m), re = min(max(rg.rowptr[u + 1], rb), rg.m);
+                for (long long k = rb; k < re; k++)
+                    if (rg.col[k] == lo) {
+                        rp = (int)k;
+                        break;
+                    }
+            }
+            rpart[q] = rp;
+        }
     }
     for (long long x = t0; x < NV; x += stride) {
         const RGraph rg = gr[find_graph(gr, G, x, true)];
@@ -259,6 +273,117 @@ __global__ void __launch_bounds__(kRandThreads) k_rand_swap_spec(const RGraph *_
     }
 }
 
+// Mutual mode, speculative batches of 16 attempts.  pt: each copy's reverse
+// position of every arc (-1 for a single arc), started from the graph's
+// (rpart).  An attempt reads rows a, b, c, d; an accepted swap of two single
+// arcs writes rows a and c, of two mutual pairs all four; the batch applies
+// the attempts before the first one that reads a row an earlier accepted
+// one writes.
+__global__ void __launch_bounds__(kRandThreads) k_rand_swap_spec_mutual(const RGraph *__restrict__ gr, int G, int R,
+                                                                        const int4 *__restrict__ rows,
+                                                                        const int *__restrict__ rpart, int *out,
+                                                                        int *pts, uint32_t *bits,
+                                                                        long long *accepted, int *status) {
+    if (*(volatile const int *)status) return;
+    const int lane = threadIdx.x & 31;
+    const long long items = (long long)G * R;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < items; w += nw) {
+        const int g = (int)(w / R), r = (int)(w - (long long)g * R);
+        const RGraph rg = gr[g];
+        const int m = (int)rg.m, bw = rg.bw;
+        const int4 *rw = rows + rg.moff;
+        int *cp = out + rg.ooff + (long long)r * rg.m;
+        int *pt = pts + rg.ooff + (long long)r * rg.m;
+        uint32_t *bm = bits + rg.boff + (long long)r * rg.n * bw;
+        uint4 *bm4 = reinterpret_cast<uint4 *>(bm);
+        const long long words4 = (long long)rg.n * bw / 4;
+        for (long long i = lane; i < words4; i += kWarp) bm4[i] = make_uint4(0u, 0u, 0u, 0u);
+        __syncwarp();
+        for (int e = lane; e < m; e += kWarp) {
+            const int u = __ldg(rg.col + e);
+            cp[e] = u;
+            pt[e] = __ldg(rpart + rg.moff + e);
+            atomicOr(&bm[(long long)__ldg(&rw[e].z) * bw + (u >> 5)], 1u << (u & 31));
+        }
+        __syncwarp();
+        long long acc = 0;
+        const uint64_t seed = rg.seed + (uint64_t)r;
+        long long t = 0, batches = 0;
+        while (m >= 2 && t < rg.attempts) {
+            if (++batches > rg.attempts) {  // every batch applies at least one attempt
+                set_status(status, ACC_ERR_INTERNAL);
+                break;
+            }
+            const long long left = rg.attempts - t;
+            const int P = left < 16 ? (int)left : 16;
+            const bool live = (lane >> 1) < P;
+            // even lane: arc e1 = a -> b; odd lane: arc e2 = c -> d.  src is
+            // a (c), x is b (d), y the other arc's target, so the arcs to be
+            // made are src -> y on both lanes
+            const int e = splitmix_draw_below(seed, (unsigned long long)(2 * t + lane), m);
+            const int src = __ldg(&rw[e].z);
+            const int x = cp[e];
+            const int pe = pt[e];
+            const int y = __shfl_xor_sync(kFull, x, 1);
+            const int ep = __shfl_xor_sync(kFull, e, 1);
+            const int pe_o = __shfl_xor_sync(kFull, pe, 1);
+            const int src_o = __shfl_xor_sync(kFull, src, 1);
+            const bool ok = live && e != ep && src != y && (pe >= 0) == (pe_o >= 0);
+            const bool ok_other = __shfl_xor_sync(kFull, ok, 1);
+            const bool pair_ok = ok && ok_other;
+            bool hit = false;
+            if (pair_ok) {
+                const uint32_t f = (bm[(long long)src * bw + (y >> 5)] >> (y & 31)) & 1u;   // a -> d / c -> b
+                const uint32_t b2 = (bm[(long long)y * bw + (src >> 5)] >> (src & 31)) & 1u; // d -> a / b -> c
+                hit = (f | b2) != 0u;
+            }
+            const bool hit_other = __shfl_xor_sync(kFull, hit, 1);
+            const bool take = pair_ok && !hit && !hit_other;
+            const bool mut = pe >= 0;
+            // rows this lane's attempt reads: src and x (with the other lane's, a b c d)
+            bool clash = false;
+#pragma unroll 1
+            for (int jp = 0; jp < 16; jp++) {
+                const bool tj = __shfl_sync(kFull, take, 2 * jp);
+                const bool mj = __shfl_sync(kFull, mut, 2 * jp);
+                const int a_j = __shfl_sync(kFull, src, 2 * jp), c_j = __shfl_sync(kFull, src, 2 * jp + 1);
+                const int b_j = __shfl_sync(kFull, x, 2 * jp), d_j = __shfl_sync(kFull, x, 2 * jp + 1);
+                if (tj && jp < (lane >> 1)) {
+                    clash |= src == a_j || src == c_j || x == a_j || x == c_j;
+                    if (mj) clash |= src == b_j || src == d_j || x == b_j || x == d_j;
+                }
+            }
+            const unsigned C = __ballot_sync(kFull, live && clash);
+            const unsigned Cp = (C | (C >> 1)) & 0x55555555u;
+            const int adv = Cp ? min(P, (__ffs(Cp) - 1) >> 1) : P;
+            const bool commit = take && (lane >> 1) < adv;
+            if (commit) {
+                uint32_t *row = bm + (long long)src * bw;
+                cp[e] = y;
+                atomicAnd(&row[x >> 5], ~(1u << (x & 31)));
+                atomicOr(&row[y >> 5], 1u << (y & 31));
+                if (mut) {
+                    // the reverse arc x -> src becomes x -> (the other arc's source);
+                    // new pairs: src <-> y (this arc, the other's reverse) and
+                    // x <-> other source (this reverse, the other arc)
+                    uint32_t *rrow = bm + (long long)x * bw;
+                    cp[pe] = src_o;
+                    atomicAnd(&rrow[src >> 5], ~(1u << (src & 31)));
+                    atomicOr(&rrow[src_o >> 5], 1u << (src_o & 31));
+                    pt[e] = pe_o;
+                    pt[pe] = ep;
+                }
+            }
+            acc += __popc(__ballot_sync(kFull, commit)) >> 1;
+            __syncwarp();
+            t += adv;
+        }
+        if (lane == 0 && accepted) accepted[w] = acc;
+        __syncwarp();
+    }
+}
+
 template <bool MUTUAL>
 __global__ void __launch_bounds__(kRandThreads) k_rand_swap(const RGraph *__restrict__ gr, int G, int R,
                                                             const int4 *__restrict__ rows, int *out,
@@ -306,20 +431,25 @@ __global__ void __launch_bounds__(kRandThreads) k_rand_swap(const RGraph *__rest
 }  // namespace
 
 int launch_randomise(const RGraph *meta, int G, int R, long long M, long long NV, int mode, int4 *rows, int *out,
-                     uint32_t *bits, long long *accepted, int *status, int num_sms, cudaStream_t s) {
+                     uint32_t *bits, int *rpart, int *pts, long long *accepted, int *status, int num_sms,
+                     cudaStream_t s) {
+    const bool mutual_spec = mode == ACC_RAND_MUTUAL && bits && rpart && pts;
     int launches = 0;
     const long long work = M > NV ? M : NV;
     if (work > 0) {
         long long blocks = (work + 255) / 256;
         if (blocks > (long long)num_sms * 8) blocks = (long long)num_sms * 8;
-        k_rand_rows<<<(int)blocks, 256, 0, s>>>(meta, G, M, NV, rows, status);
+        k_rand_rows<<<(int)blocks, 256, 0, s>>>(meta, G, M, NV, rows, mutual_spec ? rpart : nullptr, status);
         launches++;
     }
     const long long items = (long long)G * R;
     if (items > 0) {
         long long blocks = (items * kWarp + kRandThreads - 1) / kRandThreads;
         if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
-        if (mode == ACC_RAND_MUTUAL)
+        if (mutual_spec)
+            k_rand_swap_spec_mutual<<<(int)blocks, kRandThreads, 0, s>>>(meta, G, R, rows, rpart, out, pts, bits,
+                                                                          accepted, status);
+        else if (mode == ACC_RAND_MUTUAL)
             k_rand_swap<true><<<(int)blocks, kRandThreads, 0, s>>>(meta, G, R, rows, out, accepted, status);
         else if (bits)
             k_rand_swap_spec<<<(int)blocks, kRandThreads, 0, s>>>(meta, G, R, rows, out, bits, accepted, status);

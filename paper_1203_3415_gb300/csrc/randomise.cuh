@@ -25,8 +25,11 @@ struct RGraph {
 // Validates the graphs and fills rows (int4[M]: begin, end, source of each
 // position), then runs the copies (mode ACC_RAND_SWAP or ACC_RAND_MUTUAL);
 // the copies are skipped when *status is set.  With bits non-null (R times
-// the graphs' n * bw words) the plain mode runs the speculative kernel.
+// the graphs' n * bw words) the plain mode runs the speculative kernel, and
+// so does the mutual mode when rpart (M ints: reverse position of each arc)
+// and pts (R * M ints: the copies' reverse positions) are non-null too.
 int launch_randomise(const RGraph *meta, int G, int R, long long M, long long NV, int mode, int4 *rows, int *out,
-                     uint32_t *bits, long long *accepted, int *status, int num_sms, cudaStream_t s);
+                     uint32_t *bits, int *rpart, int *pts, long long *accepted, int *status, int num_sms,
+                     cudaStream_t s);
 
 }  // namespace acc

@@ -69,8 +69,8 @@ def mixed(seed):
     return graphs
 
 
-@pytest.mark.parametrize("mode,bitmaps", [(0, True), (0, False), (1, True)],
-                         ids=["swap_speculative", "swap_row_scan", "mutual"])
+@pytest.mark.parametrize("mode,bitmaps", [(0, True), (0, False), (1, True), (1, False)],
+                         ids=["swap_speculative", "swap_row_scan", "mutual_speculative", "mutual_row_scan"])
 def test_copies_equal_oracle(counter, mode, bitmaps):
     graphs = mixed(70 + mode + 2 * bitmaps)
     dev = to_device(graphs)
@@ -99,7 +99,7 @@ def test_large_graph_with_hubs(counter):
     g = synth.chung_lu_k4()  # n=20000, m=100000, rows up to 500 arcs
     graphs = [(g.n, g.src, g.dst)]
     dev = to_device(graphs)
-    for mode, limit in ((0, 16 << 30), (0, 0), (1, 16 << 30)):
+    for mode, limit in ((0, 16 << 30), (0, 0), (1, 16 << 30), (1, 0)):
         counter.set_randomise_memory(limit)
         out, acc = counter.randomise(dev, 2, [42], attempts_per_arc=3, mode=mode)
         check_against_oracle(graphs, dev, 2, [42], 3, mode, out, acc)
