@@ -457,31 +457,67 @@ __global__ void __launch_bounds__(1024) k_scan_apply(const int *__restrict__ deg
     }
 }
 
-// Warp per global row: write the sorted neighbour entries (u << 2) | state(v, u)
-// with local u, reading only the 32-word chunks the occupancy bitmap marks:
-// lane j takes the j-th marked chunk of a bitmap word (all in one round).
+// Warp per rw consecutive global rows (a power of two up to 32): write the
+// sorted neighbour entries (u << 2) | state(v, u) with local u, reading only
+// the 32-word chunks the occupancy bitmap marks.  The rows' marked chunks are
+// numbered row by row
+// and spread over the lanes (a lane per chunk, 128 bytes each); a chunk's
+// entries go to its row's offset plus the entries of the row's earlier
+// chunks (a scan over the lanes, segmented by row and carried from one round
+// to the next), so rows with few neighbours share a warp.
 __global__ void k_fill(GSet gs, const uint32_t *__restrict__ state, const uint32_t *__restrict__ occ, int occ_w,
-                       const long long *__restrict__ nptr, uint32_t *nbr) {
+                       const long long *__restrict__ nptr, uint32_t *nbr, int rw) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long v = warp; v < gs.NV; v += nwarps) {
-        const GMeta mt = gs.meta(gs.graph_of((int)v));
-        const int lv = (int)v - mt.voff;
-        const int quads = (((mt.n + 15) >> 4) + 3) >> 2;  // 16-byte groups within the pitch
-        const uint4 *row4 = reinterpret_cast<const uint4 *>(state + mt.soff + (long long)lv * mt.pitch);
-        long long base = nptr[v];
-        for (int mw = 0; mw < occ_w; mw++) {
-            const uint32_t mask = occ[v * occ_w + mw];
-            const int nch = __popc(mask);
+    for (long long r0 = warp * rw; r0 < gs.NV; r0 += nwarps * rw) {
+        const long long v = r0 + lane;
+        int nch = 0, quads = 0;
+        long long row_word = 0, rbase = 0;
+        if (lane < rw && v < gs.NV) {
+            for (int w = 0; w < occ_w; w++) nch += __popc(occ[v * occ_w + w]);
+            const GMeta mt = gs.meta(gs.graph_of((int)v));
+            row_word = mt.soff + (long long)((int)v - mt.voff) * mt.pitch;
+            quads = (((mt.n + 15) >> 4) + 3) >> 2;  // 16-byte groups within the pitch
+            rbase = nptr[v];
+        }
+        int total;
+        const int pre = warp_excl_scan(nch, lane, &total);
+        int carry_row = -1, carry = 0;  // the row the last round ended in, and its entries so far
+        for (int i0 = 0; i0 < total; i0 += kWarp) {
+            const int idx = i0 + lane;
+            const bool act = idx < total;
+            // owner: the last lane whose chunks start at or before idx
+            int owner = 0;
+#pragma unroll
+            for (int step = 16; step; step >>= 1) {
+                const int cand = owner + step;
+                const int pc = __shfl_sync(kFull, pre, cand & 31);
+                if (cand < kWarp && pc <= idx) owner = cand;
+            }
+            const int o_pre = __shfl_sync(kFull, pre, owner);
+            const long long o_word = __shfl_sync(kFull, row_word, owner);
+            const long long o_base = __shfl_sync(kFull, rbase, owner);
+            const int o_quads = __shfl_sync(kFull, quads, owner);
             uint32_t xs[32];
-            int cnt = 0;
-            int q0 = 0;
-            if (lane < nch) {
-                q0 = (mw * 32 + (int)__fns(mask, 0, lane + 1)) * 8;  // first 16-byte group of the chunk
+            int cnt = 0, q0 = 0;
+            if (act) {
+                // the (idx - o_pre)-th marked chunk of the owner's row
+                const long long vo = r0 + owner;
+                int j = idx - o_pre;
+                for (int w = 0; w < occ_w; w++) {
+                    const uint32_t mk = occ[vo * occ_w + w];
+                    const int pc = __popc(mk);
+                    if (j < pc) {
+                        q0 = (w * 32 + (int)__fns(mk, 0, j + 1)) * 8;  // first 16-byte group of the chunk
+                        break;
+                    }
+                    j -= pc;
+                }
+                const uint4 *row4 = reinterpret_cast<const uint4 *>(state + o_word);
 #pragma unroll
                 for (int g = 0; g < 8; g++) {
-                    const uint4 x4 = q0 + g < quads ? row4[q0 + g] : make_uint4(0, 0, 0, 0);
+                    const uint4 x4 = q0 + g < o_quads ? row4[q0 + g] : make_uint4(0, 0, 0, 0);
                     xs[4 * g] = x4.x;
                     xs[4 * g + 1] = x4.y;
                     xs[4 * g + 2] = x4.z;
@@ -490,10 +526,14 @@ __global__ void k_fill(GSet gs, const uint32_t *__restrict__ state, const uint32
 #pragma unroll
                 for (int t = 0; t < 32; t++) cnt += __popc((xs[t] | (xs[t] >> 1)) & 0x55555555u);
             }
-            int total;
-            const int off = warp_excl_scan(cnt, lane, &total);
-            if (cnt) {
-                long long pos = base + off;
+            int round_total;
+            const int ex = warp_excl_scan(cnt, lane, &round_total);
+            // chunks of a row sit on consecutive lanes: the row's first lane here
+            const unsigned same = __match_any_sync(kFull, act ? owner : -1 - lane);
+            const int first = __ffs(same) - 1;
+            const int ex_first = __shfl_sync(kFull, ex, first);
+            if (act) {
+                long long pos = o_base + (ex - ex_first) + (owner == carry_row ? carry : 0);
 #pragma unroll
                 for (int t = 0; t < 32; t++) {
                     uint32_t nz = (xs[t] | (xs[t] >> 1)) & 0x55555555u;
@@ -504,7 +544,13 @@ __global__ void k_fill(GSet gs, const uint32_t *__restrict__ state, const uint32
                     }
                 }
             }
-            base += total;
+            // the round's last row may go on in the next round
+            const int last = min(total - i0, kWarp) - 1;
+            const int last_owner = __shfl_sync(kFull, owner, last);
+            const int last_first = __shfl_sync(kFull, first, last);
+            const int in_round = __shfl_sync(kFull, ex + cnt, last) - __shfl_sync(kFull, ex, last_first);
+            carry = (last_owner == carry_row ? carry : 0) + in_round;
+            carry_row = last_owner;
         }
     }
 }
@@ -621,7 +667,6 @@ int launch_build_graph(const GSet &gs, const BuildBufs &bb, int max_n, int *stat
     }
     int launches = 0;
     const long long NV = gs.NV;
-    const int rows_grid = grid_for(NV * kWarp, 256, num_sms);
     const int arcs_grid = grid_for(max(gs.M, NV), 256, num_sms);
     // zero the counts, the status word, the degree counters, the occupancy
     // bitmap and, unless the previous call left it clean, the pair-state buffer
@@ -668,7 +713,11 @@ int launch_build_graph(const GSet &gs, const BuildBufs &bb, int max_n, int *stat
         k_scan_apply<<<ntiles, 1024, 0, s>>>(bb.deg, (int)NV, bb.tiles, bb.nptr);
         launches += 4;
     }
-    k_fill<<<rows_grid, 256, 0, s>>>(gs, bb.state, bb.occ, bb.occ_w, bb.nptr, bb.nbr);
+    // rows per warp: enough warps to fill the GPU (64 per SM) first
+    int rw = 1;
+    while (rw < kWarp && (long long)rw * 2 * num_sms * 64 <= NV) rw *= 2;
+    k_fill<<<grid_for((NV + rw - 1) / rw * kWarp, 256, num_sms), 256, 0, s>>>(gs, bb.state, bb.occ, bb.occ_w,
+                                                                              bb.nptr, bb.nbr, rw);
     launches++;
     return cudaGetLastError() == cudaSuccess ? launches : ACC_ERR_CUDA;
 }
