@@ -53,6 +53,9 @@ namespace {
 #ifndef ACC_GRAB4
 #define ACC_GRAB4 2  // base units per atomic grab for k = 4 (lighter units, one hot counter)
 #endif
+#ifndef ACC_GRAB_SET
+#define ACC_GRAB_SET 16  // base units per grab when several graphs are counted (fewer graph switches)
+#endif
 #ifndef ACC_GRAB
 #define ACC_GRAB 1
 #endif
@@ -940,7 +943,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? ACC_MI
         const long long nunits = K == 3 ? NV : nnz;
         for (;;) {
             unsigned long long u0 = 0;
-            constexpr int grab = K == 4 ? ACC_GRAB4 : kGrab;
+            const int grab = a.gs.B > 1 ? ACC_GRAB_SET : (K == 4 ? ACC_GRAB4 : kGrab);
             if (lane == 0) u0 = atomicAdd(&a.info->unit_ctr, (unsigned long long)grab);
             u0 = __shfl_sync(kFull, u0, 0);
             if ((long long)u0 >= nunits) break;
