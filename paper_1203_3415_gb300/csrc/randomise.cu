@@ -17,21 +17,24 @@
 //
 // Layout: a warp per copy; positions are grouped by row, so the rows of e1
 // and e2 (the rows of a and c) come from a per-position table shared by every
-// copy ({begin, end, source}).  Two kernels:
-//  - speculative (plain mode, when the copies' adjacency bitmaps fit the
-//    context's limit): the stream is counter-based (draw k is the mix of
-//    seed + (k + 1) * increment), so the warp draws 16 attempts at once, two
-//    lanes each, and decides all of them against the copy as it stands: one
-//    round trip for both targets and rows, one for the two bitmap bits.  An
-//    attempt reads and writes only its own two rows (targets, bits), so the
-//    decisions are exact up to the first attempt that shares a row with an
-//    earlier accepted one; that prefix is applied and the next batch starts
-//    at the first such attempt.  The copies equal the one-by-one procedure's.
-//  - one by one (mutual mode, or bitmaps over the limit): "is a -> d an
-//    arc?" is a scan of row a of the copy itself, each half-warp holding one
-//    of the two rows; the next attempt's draws and rows are read ahead.  An
-//    attempt costs one round trip in the plain mode, two more in the mutual
-//    mode (the rows of b and d).
+// copy ({begin, end, source}).  Two forms:
+//  - speculative (when the copies' adjacency bitmaps fit the context's
+//    limit): the stream is counter-based (draw k is the mix of seed + (k + 1)
+//    * increment), so the warp draws 16 attempts at once, two lanes each, and
+//    decides all of them against the copy as it stands: one round trip for
+//    both targets and rows, one for the bitmap bits.  In the plain mode an
+//    attempt reads and writes only its own two rows (targets, bits); in the
+//    mutual mode it also reads the rows of b and d (and each copy keeps the
+//    position of every arc's reverse), and an accepted swap of mutual pairs
+//    writes them.  The decisions are exact up to the first attempt that
+//    reads a row an earlier accepted one writes; that prefix is applied and
+//    the next batch starts there.  The copies equal the one-by-one
+//    procedure's.
+//  - one by one (bitmaps over the limit): "is a -> d an arc?" is a scan of
+//    row a of the copy itself, each half-warp holding one of the two rows;
+//    the next attempt's draws and rows are read ahead.  An attempt costs one
+//    round trip in the plain mode, two more in the mutual mode (the rows of b
+//    and d).
 #include "randomise.cuh"
 
 namespace acc {
