@@ -396,6 +396,18 @@ ACC_API int acc_ctx_get_schedule(acc_ctx *ctx, int64_t *light, int64_t *target);
  * Errors: ACC_ERR_ARG (timing off or no count yet), ACC_ERR_CUDA.
  */
 ACC_API int acc_ctx_set_timing(acc_ctx *ctx, int on);
+
+/*
+ * Launch graphs for repeated counts (on = 1, the default): a count that
+ * repeats the previous one on this context (same device buffers, n, m, k,
+ * mode, schedule and workspace) replays one CUDA graph of its whole launch
+ * sequence instead of launching the kernels one by one; any other count
+ * captures the graph for the next repeat.  The kernels, and so the results,
+ * are the same either way; the contents of the buffers may change between
+ * repeats.  Stage timing (acc_ctx_set_timing) always launches one by one.
+ * Errors: ACC_ERR_ARG.
+ */
+ACC_API int acc_ctx_set_launch_graphs(acc_ctx *ctx, int on);
 ACC_API int acc_motif_last_timing(acc_ctx *ctx, float *h_ms);
 
 /*

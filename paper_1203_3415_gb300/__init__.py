@@ -35,7 +35,7 @@ NUM_CLASSES = {3: 13, 4: 199, 5: 9364}
 EXPORTS = (
     "acc_strerror", "acc_motif_num_classes", "acc_ctx_create", "acc_ctx_destroy", "acc_motif_prepare",
     "acc_motif_count", "acc_motif_count_host", "acc_motif_batch_prepare", "acc_motif_batch_run",
-    "acc_motif_count_batch", "acc_motif_zscores", "acc_swap_randomise", "acc_ctx_set_randomise_memory", "acc_motif_class_code", "acc_motif_classify_code",
+    "acc_motif_count_batch", "acc_motif_zscores", "acc_swap_randomise", "acc_ctx_set_randomise_memory", "acc_ctx_set_launch_graphs", "acc_motif_class_code", "acc_motif_classify_code",
     "acc_motif_copy_table", "acc_motif_last_stats", "acc_ctx_set_timing", "acc_motif_last_timing",
     "acc_motif_build_table_static", "acc_ctx_set_mode", "acc_server_create", "acc_server_destroy", "acc_server_add_graph",
     "acc_server_reserve", "acc_server_submit", "acc_server_progress", "acc_server_poll", "acc_server_drain",
@@ -68,6 +68,7 @@ def _load():
     lib.acc_motif_zscores.argtypes = [vp, i32, i32, ctypes.c_int, vp, vp]
     lib.acc_swap_randomise.argtypes = [vp, vp, i32, i32, i64, vp, ctypes.c_int, vp, vp, vp, vp]
     lib.acc_ctx_set_randomise_memory.argtypes = [vp, i64]
+    lib.acc_ctx_set_launch_graphs.argtypes = [vp, ctypes.c_int]
     lib.acc_motif_class_code.argtypes = [vp, ctypes.c_int, i32, ctypes.POINTER(ctypes.c_uint32)]
     lib.acc_motif_classify_code.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(i32)]
     lib.acc_motif_copy_table.argtypes = [vp, ctypes.c_int, vp]
@@ -180,6 +181,10 @@ def acc_swap_randomise(ctx: int, h_graphs, G: int, R: int, attempts_per_arc: int
     return _L().acc_swap_randomise(ctx, ctypes.cast(h_graphs, ctypes.c_void_p), G, R, attempts_per_arc,
                                    ctypes.cast(h_seeds, ctypes.c_void_p), mode, stream, d_out, d_accepted,
                                    d_status)
+
+
+def acc_ctx_set_launch_graphs(ctx: int, on: int) -> int:
+    return _L().acc_ctx_set_launch_graphs(ctx, on)
 
 
 def acc_ctx_set_randomise_memory(ctx: int, nbytes: int) -> int:
@@ -464,6 +469,10 @@ class Counter:
                                 status.data_ptr() if status is not None else None)
         _check(rc, "acc_swap_randomise")
         return out, accepted
+
+    def set_launch_graphs(self, on: bool):
+        """Replay one CUDA graph for repeated counts (default on)."""
+        _check(acc_ctx_set_launch_graphs(self.ctx, 1 if on else 0), "acc_ctx_set_launch_graphs")
 
     def set_randomise_memory(self, nbytes: int):
         """Bytes the copies' adjacency bitmaps may take (0: scan rows)."""

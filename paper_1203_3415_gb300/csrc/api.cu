@@ -266,7 +266,66 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
     gs.NV = n;
     gs.M = m;
     int *status = status_user ? status_user : c->status_dev;
-    rc = run_set(c, gs, n, k, n >= kRelabelMinN, s, counts, status);
+    const bool relabel = n >= kRelabelMinN;
+    if (c->graphs && !c->timing && c->state_clean && n > 0) {
+        // repeat counts replay one CUDA graph of the whole launch sequence;
+        // it is captured (on the context's stream, not run) only while the
+        // pair-state buffer is known clean, so it holds no full sweep
+        acc_ctx::CountKey key;
+        memset(&key, 0, sizeof(key));
+        key.rowptr = rowptr;
+        key.col = col;
+        key.counts = counts;
+        key.status = status;
+        key.m = m;
+        key.light = c->sched_light;
+        key.target = c->sched_target;
+        key.n = n;
+        key.k = k;
+        key.mode = c->mode;
+        key.grid_num = c->grid_num;
+        key.grid_den = c->grid_den;
+        const void *ws[18] = {c->state, c->deg, c->lo, c->label, c->deg_in, c->nptr, c->tiles, c->nbr, c->occ,
+                              c->info, c->queue, c->scratch, c->lut[k], c->lut_sv[k], c->class_code_dev[k],
+                              c->f5_pre, c->status_dev, nullptr};
+        memcpy(key.ws, ws, sizeof(ws));
+        bool have = c->cg_exec && memcmp(&key, &c->cg_key, sizeof(key)) == 0;
+        if (!have) {
+            if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);
+            c->cg_exec = nullptr;
+            cudaGraph_t g = nullptr;
+            if (ok(cudaStreamBeginCapture(c->own, cudaStreamCaptureModeRelaxed))) {
+                rc = run_set(c, gs, n, k, relabel, c->own, counts, status);
+                const cudaError_t ce = cudaStreamEndCapture(c->own, &g);
+                c->state_clean = true;  // nothing ran
+                if (rc) {
+                    if (g) cudaGraphDestroy(g);
+                    return rc;
+                }
+                if (ce == cudaSuccess && g && ok(cudaGraphInstantiate(&c->cg_exec, g, 0))) {
+                    c->cg_key = key;
+                    c->cg_launches = c->last_launches;
+                    c->cg_units = c->last_units;
+                    c->cg_blocks = c->last_blocks;
+                    have = true;
+                } else {
+                    c->cg_exec = nullptr;
+                }
+                if (g) cudaGraphDestroy(g);
+            }
+            cudaGetLastError();  // a refused capture leaves the eager path below
+        }
+        if (have) {
+            if (!ok(cudaGraphLaunch(c->cg_exec, s))) return ACC_ERR_CUDA;
+            c->state_clean = true;  // the sequence ends with the clear
+            c->last_launches = c->cg_launches;
+            c->last_k = k;
+            c->last_units = c->cg_units;
+            c->last_blocks = c->cg_blocks;
+            return finish(c, s, status_user);
+        }
+    }
+    rc = run_set(c, gs, n, k, relabel, s, counts, status);
     if (rc) return rc;
     return finish(c, s, status_user);
 }
@@ -360,6 +419,7 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaFree(c->status_dev);
     cudaFree(c->meta_dev);
     cudaFree(c->gid);
+    if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);
     cudaFree(c->rand_meta);
     cudaFree(c->rand_rows);
     cudaFree(c->rand_bits);
@@ -586,6 +646,12 @@ int acc_swap_randomise(acc_ctx *c, const acc_graph_desc *graphs, int32_t G, int3
                           reinterpret_cast<long long *>(d_accepted), status, c->num_sms, s);
     if (rc < 0) return rc;
     return finish(c, s, d_status);
+}
+
+int acc_ctx_set_launch_graphs(acc_ctx *c, int on) {
+    if (!c || (on != 0 && on != 1)) return ACC_ERR_ARG;
+    c->graphs = on != 0;
+    return ACC_OK;
 }
 
 int acc_ctx_set_randomise_memory(acc_ctx *c, int64_t bytes) {

@@ -83,6 +83,20 @@ struct acc_ctx {
     size_t h2d_col_cap = 0;
     unsigned long long *h2d_counts = nullptr;
 
+    // launch graph of the last single count, replayed while a count repeats
+    // it (same buffers, sizes, k, mode, schedule and workspace)
+    bool graphs = true;
+    cudaGraphExec_t cg_exec = nullptr;
+    struct CountKey {
+        const void *rowptr, *col, *counts, *status;
+        long long m, light, target;
+        int n, k, mode, grid_num, grid_den, pad;
+        const void *ws[18];
+    } cg_key = {};
+    int cg_launches = 0;
+    long long cg_units = 0;
+    int cg_blocks = 0;
+
     // stage timing
     bool timing = false;
     bool timed_call = false;
