@@ -224,6 +224,9 @@ int acc_server_create(acc_server **out, int device, int32_t slots, int64_t mem_b
             acc_server_destroy(sv);
             return rc;
         }
+        // a slot's consecutive requests are rarely the same graph and k:
+        // launch one by one rather than capture a graph per request
+        acc_ctx_set_launch_graphs(sl.ctx, 0);
         if (!ok(cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking)) ||
             !ok(cudaMalloc(&sl.d_counts, sizeof(int64_t) * 9364)) || !ok(cudaMalloc(&sl.d_status, sizeof(int32_t))) ||
             !ok(cudaMallocHost(&sl.h_counts, sizeof(int64_t) * 9364)) ||
