@@ -301,6 +301,9 @@ def run_ours(args):
     counter.set_mode({"count": acc.ACC_MODE_COUNT, "enumerate": acc.ACC_MODE_ENUMERATE,
                       "formula": acc.ACC_MODE_FORMULA}[args.mode])
     counter.prepare(k)
+    if args.schedule:
+        light, target = (int(x) for x in args.schedule.split(","))
+        counter.set_schedule(light, target)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -866,6 +869,8 @@ def main():
     ap.add_argument("--serve-policy", choices=["shortest", "fifo"], default="shortest",
                     help="serving admission order: smallest aged work estimate first, or submission order")
     ap.add_argument("--serve-aging-s", type=float, default=1.0)
+    ap.add_argument("--schedule", default="",
+                    help="enumeration schedule LIGHT,TARGET for the single-graph workloads (default: the kernels')")
     ap.add_argument("--rand-mode", choices=["swap", "mutual"], default="swap",
                     help="significance workload: double-edge swaps, or swaps that keep mutual arcs mutual")
     ap.add_argument("--mode", choices=["count", "enumerate", "formula"], default="count",
