@@ -954,6 +954,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? ACC_MI
                     vg = (int)u;
                 } else {
                     while (a.nptr[vg + 1] <= u) vg++;
+                    if (u - a.nptr[vg] < a.lo[vg]) continue;  // a neighbour below the row's vertex: not a unit
                 }
                 const int gi = a.gs.graph_of(vg);
                 const GMeta mt = a.gs.meta(gi);
