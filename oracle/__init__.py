@@ -7,8 +7,9 @@ shares no code with the CUDA path.
 
 ``oracle.c`` holds the arithmetic: the adjacency-code convention, brute-force
 canonical forms (minimum over all k! relabellings), the code -> class table,
-the all-subsets counter for tiny graphs, the ESU enumeration counter and the
-Z-score formula.  This module compiles it with gcc and wraps it with ctypes.
+the all-subsets counter for tiny graphs, the ESU enumeration counter, the
+Z-score formula and the randomised copies (double-edge swaps, with or without
+keeping mutual arcs mutual).  This module compiles it with gcc and wraps it with ctypes.
 
 Every function follows the problem statement of the paper (Problems
 Motifs-3/4/5, Background section): count the connected induced subgraphs of
