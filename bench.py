@@ -370,7 +370,9 @@ def run_ours(args):
     h_col = torch.from_numpy(col_np).pin_memory()
     h_counts = torch.zeros(acc.NUM_CLASSES[k], dtype=torch.int64).pin_memory()
     e2e_steps = max(3, min(args.steps, 20))
-    counter.count_host(h_rowptr, h_col, g.n, k, counts=h_counts)
+    # two untimed calls: the second captures the launch graph the timed calls replay
+    for _ in range(2):
+        counter.count_host(h_rowptr, h_col, g.n, k, counts=h_counts)
     e2e_t = 0.0
     for _ in range(e2e_steps):
         flush.fill_(3)

@@ -401,8 +401,9 @@ ACC_API int acc_ctx_set_timing(acc_ctx *ctx, int on);
  * Launch graphs for repeated counts (on = 1, the default): a count that
  * repeats the previous one on this context (same device buffers, n, m, k,
  * mode, schedule and workspace) replays one CUDA graph of its whole launch
- * sequence instead of launching the kernels one by one; any other count
- * captures the graph for the next repeat.  The kernels, and so the results,
+ * sequence instead of launching the kernels one by one; the graph is
+ * captured at the first repeat (a one-off count launches one by one and
+ * captures nothing).  The kernels, and so the results,
  * are the same either way; the contents of the buffers may change between
  * repeats.  Stage timing (acc_ctx_set_timing) always launches one by one.
  * Errors: ACC_ERR_ARG.

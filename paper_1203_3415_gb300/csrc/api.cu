@@ -269,8 +269,9 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
     const bool relabel = n >= kRelabelMinN;
     if (c->graphs && !c->timing && c->state_clean && n > 0) {
         // repeat counts replay one CUDA graph of the whole launch sequence;
-        // it is captured (on the context's stream, not run) only while the
-        // pair-state buffer is known clean, so it holds no full sweep
+        // it is captured (on the context's stream, not run) at the second
+        // count with the same key, and only while the pair-state buffer is
+        // known clean, so it holds no full sweep
         acc_ctx::CountKey key;
         memset(&key, 0, sizeof(key));
         key.rowptr = rowptr;
@@ -290,7 +291,10 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
                               c->f5_pre, c->status_dev, nullptr};
         memcpy(key.ws, ws, sizeof(ws));
         bool have = c->cg_exec && memcmp(&key, &c->cg_key, sizeof(key)) == 0;
-        if (!have) {
+        // capture only when a count repeats: a one-off count runs one by one
+        const bool repeat = memcmp(&key, &c->cg_seen, sizeof(key)) == 0;
+        if (!have && !repeat) c->cg_seen = key;
+        if (!have && repeat) {
             if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);
             c->cg_exec = nullptr;
             cudaGraph_t g = nullptr;

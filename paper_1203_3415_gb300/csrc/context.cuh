@@ -92,7 +92,7 @@ struct acc_ctx {
         long long m, light, target;
         int n, k, mode, grid_num, grid_den, pad;
         const void *ws[18];
-    } cg_key = {};
+    } cg_key = {}, cg_seen = {};  // the captured graph's key; the last key counted one by one
     int cg_launches = 0;
     long long cg_units = 0;
     int cg_blocks = 0;
