@@ -47,3 +47,40 @@ def test_single_rank_identity():
     assert bench.reduce_max(None, 3.0) == 3.0
     assert bench.reduce_sum(None, 4.0) == 4.0
     assert bench.whole_job_rate(10.0, 2.0) == 5.0
+
+
+def _run_bench(args, env_extra=None):
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **(env_extra or {}))
+    p = subprocess.run([sys.executable, os.path.join(root, "bench.py")] + args, capture_output=True, text=True,
+                       env=env, cwd=root, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.strip()]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_line():
+    # the reference arm (the oracle on this host's cores) prints one line with
+    # the contract's keys, on the same metric as our arm
+    out = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "3", "--workload", "er_n1000_m5000_k3",
+                      "--reference-roots", "50"])
+    assert len(out) == 1
+    d = out[0]
+    import bench
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3 and d["higher_is_better"] is True
+    assert d["config"]["workload"] == "er_n1000_m5000_k3"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    out = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "3", "--workload", "er_n1000_m5000_k3",
+                      "--reference-roots", "10"], {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert out == []
