@@ -23,8 +23,10 @@
  *    exception crosses this interface.
  *  - "device" pointers are CUDA device (or managed) memory of the context's
  *    device; "host" pointers are ordinary (preferably pinned) host memory.
- *    The caller owns every pointer it passes; the library never frees or
- *    keeps one after the call returns.
+ *    The caller owns every pointer it passes; the library never frees one,
+ *    and reads or writes one only inside a call that passes it (a prepared
+ *    batch's graphs: until its last run).  Pointers remembered to recognise
+ *    a repeated call are compared, never dereferenced.
  *  - stream is a cudaStream_t passed as void* (NULL = the legacy default
  *    stream).  Work is stream-ordered: results are valid once the caller
  *    synchronises the stream, unless the entry point says it synchronises.
