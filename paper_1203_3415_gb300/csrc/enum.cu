@@ -712,10 +712,11 @@ __device__ __forceinline__ int row_of(const long long *__restrict__ nptr, int n,
 // k = 3, 4, rows of the level-2 list E2 for k = 5.  In phase 1 (jlo = 0,
 // jhi = all) a unit with more than a.light estimated work is queued in chunks
 // instead.  D is the per-row allowance for exclusive neighbours (mean degree
-// + 1).
+// + 1); wmax bounds the count mode's work of one row (largest degree + row
+// cost), so a short list skips summing its rows' work.
 template <int K, bool COUNT>
 __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, const Scratch &sc, uint32_t unit,
-                             int v, int vglob, int jlo, int jhi, bool phase1, long long D, int lane) {
+                             int v, int vglob, int jlo, int jhi, bool phase1, long long D, long long wmax, int lane) {
     using L = Layout<K>;
     if (K == 3 && COUNT) {
         // prefix {v}; E = neighbours of v above v; a heavy list is queued as
@@ -733,7 +734,11 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
         int hi = min(jhi, B), rest = B;
         if (phase1) {
             auto work = [&](int j) { return (long long)g.deg[e_id(E[j])] + kRowCost; };
-            if (total_work(B, work, lane) > a.light) {
+            // a list that cannot exceed the threshold even at the largest
+            // degree of the set skips the sum (warp-uniform condition)
+            bool heavy = false;
+            if ((long long)B * wmax > a.light) heavy = total_work(B, work, lane) > a.light;
+            if (heavy) {
                 rest = queue_rows(a, unit, vglob, B, work, lane);
                 if (rest >= B) return;
                 hi = 0;
@@ -785,7 +790,9 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
         rest = B2;
         if (phase1) {
             auto work = [&](int j) { return (long long)g.deg[e_id(E2[j])] + kRowCost; };
-            if (total_work(B2, work, lane) > a.light) {
+            bool heavy = false;  // as for k = 3: the sum only when it can pass the threshold
+            if ((long long)B2 * wmax > a.light) heavy = total_work(B2, work, lane) > a.light;
+            if (heavy) {
                 rest = queue_rows(a, unit, vglob, B2, work, lane);
                 if (rest >= B2) return;
                 hi = 0;
@@ -938,6 +945,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? ACC_MI
     const long long nnz = a.info->nnz;
     const long long NV = a.gs.NV;
     const long long D = (NV > 0 ? nnz / NV : 0) + 1;
+    const long long wmax = (long long)a.info->maxdeg + kRowCost;  // largest work of one list row
 
     if constexpr (PHASE == 1) {
         const long long nunits = K == 3 ? NV : nnz;
@@ -960,7 +968,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? ACC_MI
                 const GMeta mt = a.gs.meta(gi);
                 sink.switch_graph(gi, lane);
                 process_unit<K, COUNT>(a, view_of(a, mt), sink, sc, (uint32_t)u, vg - mt.voff, vg, 0, 0x7FFFFFFF,
-                                       true, D, lane);
+                                       true, D, wmax, lane);
             }
         }
     } else {
@@ -976,7 +984,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? ACC_MI
             const GMeta mt = a.gs.meta(gi);
             sink.switch_graph(gi, lane);
             process_unit<K, COUNT>(a, view_of(a, mt), sink, sc, it.x, vg - mt.voff, vg, (int)it.y, (int)it.z,
-                                   false, D, lane);
+                                   false, D, wmax, lane);
         }
     }
 
