@@ -1,0 +1,138 @@
+// CPU stand-ins for the CUDA constructs the library's kernels use, so that a
+// kernel's own source can run on the host: one std::thread per lane, every
+// warp collective (shuffles, ballot, match, reduce, __syncwarp) a barrier of
+// the 32 lane threads, and atomics on std::atomic_ref.  A lane that skips a
+// collective its warp reaches leaves the others waiting at the barrier,
+// which the driver reports as a hang.  Shared arrays are static (one block
+// runs at a time, one warp per block).
+#pragma once
+#include <algorithm>
+#include <atomic>
+#include <barrier>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#define __global__
+#define __device__
+#define __host__
+#define __forceinline__ inline
+#define __restrict__
+#define __launch_bounds__(...)
+#define __shared__ static
+using std::max;
+using std::min;
+
+struct int4 { int x, y, z, w; };
+struct uint4 { unsigned x, y, z, w; };
+inline int4 make_int4(int a, int b, int c, int d) { return {a, b, c, d}; }
+inline uint4 make_uint4(unsigned a, unsigned b, unsigned c, unsigned d) { return {a, b, c, d}; }
+struct dim { unsigned x; };
+extern thread_local dim threadIdx, blockIdx;
+extern dim blockDim, gridDim;
+struct WarpCtx { std::barrier<> *bar; uint64_t slot[32]; };
+extern thread_local WarpCtx *tw;
+
+template <class T> inline T __ldg(const T *p) { return *p; }
+inline uint64_t __umul64hi(uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128)a * b) >> 64); }
+inline int lane_() { return threadIdx.x & 31; }
+inline void wsync() { tw->bar->arrive_and_wait(); }
+inline void __syncwarp(unsigned = 0xffffffffu) { wsync(); }
+inline void __syncthreads() { wsync(); }
+template <class T> inline T exch(T v, int src) {
+    wsync();
+    tw->slot[lane_()] = (uint64_t)(int64_t)v;
+    wsync();
+    T r = (T)(int64_t)tw->slot[src & 31];
+    wsync();
+    return r;
+}
+template <class T> inline T __shfl_xor_sync(unsigned, T v, int d) { return exch(v, lane_() ^ d); }
+template <class T> inline T __shfl_sync(unsigned, T v, int src) { return exch(v, src); }
+template <class T> inline T __shfl_up_sync(unsigned, T v, int d) {
+    T r = exch(v, lane_() >= d ? lane_() - d : lane_());
+    return r;
+}
+inline unsigned __ballot_sync(unsigned, int p) {
+    wsync();
+    tw->slot[lane_()] = p ? 1 : 0;
+    wsync();
+    unsigned r = 0;
+    for (int i = 0; i < 32; i++) r |= (tw->slot[i] ? 1u : 0u) << i;
+    wsync();
+    return r;
+}
+inline int __any_sync(unsigned m, int p) { return __ballot_sync(m, p) != 0; }
+inline unsigned __match_any_sync(unsigned, int v) {
+    wsync();
+    tw->slot[lane_()] = (uint64_t)(uint32_t)v;
+    wsync();
+    unsigned r = 0;
+    for (int i = 0; i < 32; i++) r |= (tw->slot[i] == (uint64_t)(uint32_t)v ? 1u : 0u) << i;
+    wsync();
+    return r;
+}
+inline int __reduce_max_sync(unsigned, int v) {
+    wsync();
+    tw->slot[lane_()] = (uint64_t)(int64_t)v;
+    wsync();
+    int r = (int)(int64_t)tw->slot[0];
+    for (int i = 1; i < 32; i++) r = std::max(r, (int)(int64_t)tw->slot[i]);
+    wsync();
+    return r;
+}
+inline int __ffs(int x) { return x ? __builtin_ctz((unsigned)x) + 1 : 0; }
+inline int __popc(unsigned x) { return __builtin_popcount(x); }
+// position of the offset-th (1-based) set bit of mask at or above base
+inline unsigned __fns(unsigned mask, unsigned base, int offset) {
+    int c = 0;
+    for (unsigned i = base; i < 32; i++)
+        if ((mask >> i) & 1u && ++c == offset) return i;
+    return 0xffffffffu;
+}
+inline unsigned atomicOr(unsigned *p, unsigned v) { return std::atomic_ref<unsigned>(*p).fetch_or(v); }
+inline unsigned atomicAnd(unsigned *p, unsigned v) { return std::atomic_ref<unsigned>(*p).fetch_and(v); }
+inline int atomicAdd(int *p, int v) { return std::atomic_ref<int>(*p).fetch_add(v); }
+inline unsigned long long atomicAdd(unsigned long long *p, unsigned long long v) {
+    return std::atomic_ref<unsigned long long>(*p).fetch_add(v);
+}
+inline int atomicCAS(int *p, int c, int v) {
+    std::atomic_ref<int>(*p).compare_exchange_strong(c, v);
+    return c;
+}
+
+// Run f() as blocks x (threads / 32) warps, one warp at a time; returns false
+// when a warp does not finish within the limit (a lane left a collective).
+template <class F> bool run_warps(int blocks, int threads, F f, int limit_s = 120) {
+    blockDim.x = threads;
+    gridDim.x = blocks;
+    for (int b = 0; b < blocks; b++)
+        for (int w = 0; w < threads / 32; w++) {
+            std::barrier<> bar(32);
+            WarpCtx ctx;
+            ctx.bar = &bar;
+            std::atomic<int> done{0};
+            std::vector<std::thread> th;
+            for (int l = 0; l < 32; l++)
+                th.emplace_back([&, l] {
+                    threadIdx.x = w * 32 + l;
+                    blockIdx.x = b;
+                    tw = &ctx;
+                    f();
+                    done++;
+                });
+            for (int t = 0; t < limit_s * 100 && done.load() < 32; t++)
+                std::this_thread::sleep_for(std::chrono::milliseconds(10));
+            if (done.load() < 32) {
+                fprintf(stderr, "warp %d of block %d did not finish\n", w, b);
+                std::_Exit(3);
+            }
+            for (auto &t : th) t.join();
+        }
+    return true;
+}
