@@ -5,7 +5,7 @@ per lane and a 32-thread barrier for every warp collective, so a lane that
 skips a collective its warp reaches hangs the warp and the driver reports
 it.  The kernels' code is cut from the CUDA sources between fixed anchors
 and compiled with g++ together with the library's own internal headers; the
-results are compared with the oracle (copies, k = 4 formula counts) or with
+results are compared with the oracle (copies, k = 3, 4, 5 formula counts) or with
 the lists a plain host loop writes (neighbour-list fill).  This checks the
 kernels' logic and warp discipline without a GPU; the GPU tests check the
 compiled kernels."""
@@ -47,12 +47,16 @@ def emu_bins(tmp_path_factory):
     open(out / "rand_kernels.inc", "w").write(_region(rand, "constexpr int kRandThreads", "}  // namespace\n"))
     f4 = open(os.path.join(CSRC, "formula4.cu")).read()
     open(out / "f4_kernels.inc", "w").write(_region(f4, "constexpr int kF4Classes", "}  // namespace\n"))
+    f3 = open(os.path.join(CSRC, "formula3.cu")).read()
+    open(out / "f3_kernels.inc", "w").write(_region(f3, "constexpr int kF3Classes", "}  // namespace\n"))
+    f5 = open(os.path.join(CSRC, "formula5.cu")).read()
+    open(out / "f5_kernels.inc", "w").write(_region(f5, "constexpr int kF5Classes", "}  // namespace\n"))
     graph = open(os.path.join(CSRC, "graph.cu")).read()
     open(out / "fill_kernels.inc", "w").write(
         _function(graph, "__device__ __forceinline__ int warp_excl_scan") + "\n" +
         _function(graph, "__global__ void k_fill("))
     bins = {}
-    for name in ("emu_rand", "emu_f4", "emu_fill"):
+    for name in ("emu_rand", "emu_f4", "emu_f35", "emu_fill"):
         exe = out / name
         cmd = ["g++", "-std=c++20", "-O1", "-pthread", "-w", "-I", str(out), "-I", EMU, "-I",
                os.path.join(EMU, "fake"), "-I", CSRC, "-o", str(exe), os.path.join(EMU, name + ".cpp")]
@@ -150,6 +154,27 @@ def test_k4_formula_kernels_equal_oracle(emu_bins):
         vals = [int(x) for x in _run(emu_bins["emu_f4"], buf, False, emu_bins["dir"]).split()]
         assert vals[0] == 0
         assert vals[1:] == oracle.count(n, s, d, 4).tolist(), n
+
+
+@pytest.mark.parametrize("k", [3, 5])
+def test_k3_k5_formula_kernels_equal_oracle(emu_bins, k):
+    rng = np.random.default_rng(30 + k)
+    cases = []
+    for _ in range(3):
+        n = int(rng.integers(4, 40 if k == 3 else 14))
+        cases.append((n, *random_digraph(rng, n, p=float(rng.uniform(0.1, 0.5)), recip=float(rng.random()))))
+    if k == 3:
+        g = synth.chung_lu(200, 800, 2.1, 40, 20, 6)
+        cases.append((g.n, g.src, g.dst))
+    cls, cc = oracle.table(k)
+    for n, s, d in cases:
+        pitch, st, nptr, deg, lo, nbr = _gstar(n, s, d)
+        buf = struct.pack("<4q", k, n, pitch, len(nbr)) + st.tobytes() + nptr.astype("<i8").tobytes() + \
+            deg.astype("<i4").tobytes() + lo.astype("<i4").tobytes() + nbr.astype("<u4").tobytes() + \
+            np.asarray(cls, "<i2").tobytes() + np.asarray(cc, "<u4").tobytes()
+        vals = [int(x) for x in _run(emu_bins["emu_f35"], buf, False, emu_bins["dir"]).split()]
+        assert vals[0] == 0
+        assert vals[1:] == oracle.count(n, s, d, k).tolist(), (k, n)
 
 
 @pytest.mark.parametrize("rw", [1, 4, 32])
