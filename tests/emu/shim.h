@@ -98,6 +98,10 @@ inline unsigned __fns(unsigned mask, unsigned base, int offset) {
 inline unsigned atomicOr(unsigned *p, unsigned v) { return std::atomic_ref<unsigned>(*p).fetch_or(v); }
 inline unsigned atomicAnd(unsigned *p, unsigned v) { return std::atomic_ref<unsigned>(*p).fetch_and(v); }
 inline int atomicAdd(int *p, int v) { return std::atomic_ref<int>(*p).fetch_add(v); }
+inline unsigned atomicAdd(unsigned *p, unsigned v) { return std::atomic_ref<unsigned>(*p).fetch_add(v); }
+inline unsigned atomicSub(unsigned *p, unsigned v) { return std::atomic_ref<unsigned>(*p).fetch_sub(v); }
+inline unsigned atomicExch(unsigned *p, unsigned v) { return std::atomic_ref<unsigned>(*p).exchange(v); }
+inline void __threadfence_block() { std::atomic_thread_fence(std::memory_order_seq_cst); }
 inline unsigned long long atomicAdd(unsigned long long *p, unsigned long long v) {
     return std::atomic_ref<unsigned long long>(*p).fetch_add(v);
 }

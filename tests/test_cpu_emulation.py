@@ -5,10 +5,13 @@ per lane and a 32-thread barrier for every warp collective, so a lane that
 skips a collective its warp reaches hangs the warp and the driver reports
 it.  The kernels' code is cut from the CUDA sources between fixed anchors
 and compiled with g++ together with the library's own internal headers; the
-results are compared with the oracle (copies, k = 3, 4, 5 formula counts) or with
-the lists a plain host loop writes (neighbour-list fill).  This checks the
-kernels' logic and warp discipline without a GPU; the GPU tests check the
-compiled kernels."""
+results are compared with the oracle (copies, k = 3, 4, 5 formula counts,
+k = 3, 4, 5 enumeration counts in both modes and under light, heavy and
+queue-full schedules) or with the lists a plain host loop writes
+(neighbour-list fill).  The enumeration kernels also run with tiny
+shared-memory lists and histogram drain threshold, so their overflow lists
+and drain run on small graphs.  This checks the kernels' logic and warp
+discipline without a GPU; the GPU tests check the compiled kernels."""
 import os
 import shutil
 import struct
@@ -55,15 +58,35 @@ def emu_bins(tmp_path_factory):
     open(out / "fill_kernels.inc", "w").write(
         _function(graph, "__device__ __forceinline__ int warp_excl_scan") + "\n" +
         _function(graph, "__global__ void k_fill("))
-    bins = {}
-    for name in ("emu_rand", "emu_f4", "emu_f35", "emu_fill"):
+    en = open(os.path.join(CSRC, "enum.cu")).read()
+    region = _region(en, "// Tuning knobs", "template <int K, bool COUNT, int PHASE>\nint blocks_per_sm")
+    # the kernels' dynamic shared memory becomes a static host buffer; the
+    # histogram drain threshold becomes a compile-time parameter
+    for old, new in (("extern __shared__ __align__(16) unsigned char smem[];", "unsigned char *smem = emu_smem;"),
+                     ("constexpr uint32_t kDrainAt = 1u << 30;", "constexpr uint32_t kDrainAt = EMU_DRAIN_AT;")):
+        assert region.count(old) == 1, old
+        region = region.replace(old, new)
+    open(out / "enum_kernels.inc", "w").write(region)
+    lut = open(os.path.join(CSRC, "lut.cu")).read()
+    open(out / "relayout.inc", "w").write(_function(lut, "template <int K>\n__global__ void k_relayout("))
+    # (binary, source, extra flags): the enumeration kernels as built, and
+    # with tiny shared-memory lists and drain threshold so that the overflow
+    # lists and the histogram drain run on small graphs
+    targets = [(n, n, []) for n in ("emu_rand", "emu_f4", "emu_f35", "emu_fill")]
+    targets += [("emu_enum", "emu_enum", ["-DEMU_DRAIN_AT=(1u<<30)"]),
+                ("emu_enum_small", "emu_enum", ["-DEMU_DRAIN_AT=256u", "-DACC_CAP34=16", "-DACC_CAP5=8"])]
+    procs = []
+    for name, src, extra in targets:
         exe = out / name
-        cmd = ["g++", "-std=c++20", "-O1", "-pthread", "-w", "-I", str(out), "-I", EMU, "-I",
-               os.path.join(EMU, "fake"), "-I", CSRC, "-o", str(exe), os.path.join(EMU, name + ".cpp")]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode and "barrier" in r.stderr:
+        cmd = ["g++", "-std=c++20", "-O1", "-pthread", "-w", *extra, "-I", str(out), "-I", EMU, "-I",
+               os.path.join(EMU, "fake"), "-I", CSRC, "-o", str(exe), os.path.join(EMU, src + ".cpp")]
+        procs.append((name, exe, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)))
+    bins = {}
+    for name, exe, pr in procs:
+        _, err = pr.communicate()
+        if pr.returncode and "barrier" in err:
             pytest.skip("the host compiler has no C++20 <barrier>")
-        assert r.returncode == 0, r.stderr[-3000:]
+        assert pr.returncode == 0, err[-3000:]
         bins[name] = str(exe)
     bins["dir"] = out
     return bins
@@ -194,3 +217,87 @@ def test_fill_kernel_writes_sorted_lists(emu_bins, rw):
         buf = struct.pack("<4q", n, pitch, occ_w, rw) + st.tobytes() + occ.tobytes() + nptr.astype("<i8").tobytes()
         got = np.frombuffer(_run(emu_bins["emu_fill"], buf, True, emu_bins["dir"]), "<u4")
         assert np.array_equal(got, nbr), (n, rw)
+
+
+def _enum(exe, tmp, k, n, s, d, mode, light=2048, target=4096, blocks=2, qcap=1 << 16):
+    pitch, st, nptr, deg, lo, nbr = _gstar(n, s, d)
+    cls, _ = oracle.table(k)
+    hdr = struct.pack("<10q", k, n, pitch, len(nbr), int(deg.max(initial=0)), mode, light, target, blocks, qcap)
+    buf = hdr + st.tobytes() + nptr.astype("<i8").tobytes() + deg.astype("<i4").tobytes() + \
+        lo.astype("<i4").tobytes() + nbr.astype("<u4").tobytes() + np.asarray(cls, "<i2").tobytes()
+    vals = [int(x) for x in _run(exe, buf, False, tmp).split()]
+    return vals[0], vals[1], vals[2], vals[3:]
+
+
+def _enum_cases(rng, k, count, nmax):
+    cases = []
+    for _ in range(count):
+        n = int(rng.integers(3, nmax))
+        cases.append((n, *random_digraph(rng, n, p=float(rng.uniform(0.1, 0.5)), recip=float(rng.random()))))
+    return cases
+
+
+# (light, target, queue capacity): every unit light; every unit heavy and cut
+# into one-row chunks; every unit heavy with a queue of 3 chunks, so most
+# heavy units run their unqueued rows in phase 1
+SCHEDULES = {"light": (1 << 30, 1 << 30, 1 << 16), "heavy": (0, 1, 1 << 16), "queue_full": (0, 1, 3)}
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+@pytest.mark.parametrize("mode", [0, 1], ids=["count", "enumerate"])
+@pytest.mark.parametrize("sched", list(SCHEDULES))
+def test_enumeration_kernels_equal_oracle(emu_bins, k, mode, sched):
+    light, target, qcap = SCHEDULES[sched]
+    rng = np.random.default_rng(700 + 10 * k + mode)
+    cases = _enum_cases(rng, k, 3, {3: 40, 4: 24, 5: 13}[k])
+    cases.append((5, np.array([0, 1, 2, 3], np.int64), np.array([1, 2, 3, 4], np.int64)))  # a directed path
+    cases.append((6, np.zeros(0, np.int64), np.zeros(0, np.int64)))  # no arcs
+    most = 0
+    for n, s, d in cases:
+        status, queued, scanned, got = _enum(emu_bins["emu_enum"], emu_bins["dir"], k, n, s, d, mode, light,
+                                             target, qcap=qcap)
+        assert status == 0
+        assert got == oracle.count(n, s, d, k).tolist(), (k, mode, sched, n)
+        if mode == 1:
+            assert scanned == 0
+        most = max(most, queued)
+    # chunks reserved (past the capacity too when the queue is full)
+    if sched == "light":
+        assert most == 0
+    elif k > 3:
+        assert most > (3 if sched == "queue_full" else 0)
+
+
+def _by_degree(n, s, d):
+    """The same graph renumbered by descending G* degree, as the library's
+    builder does (hubs become roots); counts do not change."""
+    s, d = np.asarray(s, np.int64), np.asarray(d, np.int64)
+    und = set(zip(np.minimum(s, d).tolist(), np.maximum(s, d).tolist()))
+    deg = np.zeros(n, np.int64)
+    for a, b in und:
+        deg[a] += 1
+        deg[b] += 1
+    new = np.empty(n, np.int64)
+    new[np.argsort(-deg, kind="stable")] = np.arange(n)
+    return new[s], new[d]
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+@pytest.mark.parametrize("mode", [0, 1], ids=["count", "enumerate"])
+def test_enumeration_overflow_lists_and_drain(emu_bins, k, mode):
+    """Shared-memory lists of 16 entries (8 for k = 5) and a histogram drained
+    every 256 increments: hub graphs send the extension lists to the per-warp
+    overflow buffers and the counts through the drain."""
+    if k == 5:
+        gs = [synth.chung_lu(20, 45, 2.1, 12, 20, 40 + mode)]
+    elif k == 4:
+        gs = [synth.chung_lu(40, 110, 2.1, 26, 20, 34 + mode)]
+    else:
+        gs = [synth.chung_lu(70, 260, 2.1, 45, 20, 33 + mode), synth.regulatory(60, 200, 6, 2.1, 40, 10, 9)]
+    for g in gs:
+        s, d = _by_degree(g.n, g.src, g.dst)
+        for light, target in ((1 << 30, 1 << 30), (64, 64)):
+            status, _, _, got = _enum(emu_bins["emu_enum_small"], emu_bins["dir"], k, g.n, s, d, mode, light,
+                                      target)
+            assert status == 0
+            assert got == oracle.count(g.n, g.src, g.dst, k).tolist(), (k, mode, g.name, light)
