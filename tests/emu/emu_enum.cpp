@@ -1,13 +1,15 @@
 // Runs the enumeration kernels (source extracted from csrc/enum.cu into
 // enum_kernels.inc, the class-table relayout from csrc/lut.cu into
-// relayout.inc) on the host over a G* build given as input, the way the
-// library launches them: phase 1 (light units whole, heavy units queued),
-// then phase 2 (the queue drained).  Input: k n pitch nnz maxdeg mode light
-// target blocks queue_cap (int64 each), state[n * pitch], nptr[n + 1],
-// deg[n], lo[n], nbr[nnz] and the canonical code -> class table
+// relayout.inc) on the host over the G* build of a set of B graphs given as
+// input, the way the library launches them: phase 1 (light units whole,
+// heavy units queued), then phase 2 (the queue drained).  Input (int64
+// unless noted): k B mode light target blocks queue_cap, then n pitch nnz of
+// each graph, then the set's arrays: state (the graphs' blocks one after
+// another), nptr[NV + 1] (positions over the whole set), deg[NV], lo[NV]
+// (int32), nbr (uint32, local ids) and the canonical code -> class table
 // (2^(k(k-1)) int16).  Output: status, chunks queued, entries scanned, the
-// counts.  Blocks run one warp each, one after another, so the kernels'
-// shared memory is one static buffer.
+// B x classes counts.  Blocks run one warp each, one after another, so the
+// kernels' shared memory is one static buffer.
 #include "shim.h"
 #include "common.cuh"
 thread_local dim threadIdx, blockIdx;
@@ -46,33 +48,51 @@ static void relayout(const int16_t *lut, int16_t *lut_sv) {
 
 int main(int argc, char **argv) {
     FILE *f = fopen(argv[1], "rb");
-    long long h[10];
-    if (!rd(f, h, 10)) return 2;
-    const long long k = h[0], n = h[1], pitch = h[2], nnz = h[3], maxdeg = h[4], mode = h[5];
-    const int blocks = (int)h[8];
+    long long h[7];
+    if (!rd(f, h, 7)) return 2;
+    const long long k = h[0], B = h[1], mode = h[2];
+    const int blocks = (int)h[5];
     const int ncls = k == 3 ? 13 : (k == 4 ? 199 : 9364);
     const size_t ncode = (size_t)1 << (k * (k - 1));
-    std::vector<uint32_t> st(n * pitch + 1);
-    std::vector<long long> nptr(n + 1);
-    std::vector<int> deg(n + 1), lo(n + 1);
+    std::vector<acc::GMeta> meta(B);
+    long long NV = 0, words = 0, nnz = 0, max_n = 0;
+    for (long long g = 0; g < B; g++) {
+        long long d[3];
+        if (!rd(f, d, 3)) return 2;
+        meta[g] = acc::GMeta{};
+        meta[g].n = (int)d[0];
+        meta[g].pitch = d[1];
+        meta[g].voff = (int)NV;
+        meta[g].soff = words;
+        NV += d[0];
+        words += d[0] * d[1];
+        nnz += d[2];
+        max_n = std::max(max_n, d[0]);
+    }
+    std::vector<uint32_t> st(words + 1);
+    std::vector<long long> nptr(NV + 1);
+    std::vector<int> deg(NV + 1), lo(NV + 1), gid(NV + 1);
     std::vector<uint32_t> nbr(nnz + 1);
     std::vector<int16_t> lut(ncode), lut_sv(ncode);
-    if (!rd(f, st.data(), n * pitch) || !rd(f, nptr.data(), n + 1) || !rd(f, deg.data(), n) || !rd(f, lo.data(), n) ||
+    if (!rd(f, st.data(), words) || !rd(f, nptr.data(), NV + 1) || !rd(f, deg.data(), NV) || !rd(f, lo.data(), NV) ||
         !rd(f, nbr.data(), nnz) || !rd(f, lut.data(), ncode))
         return 2;
     fclose(f);
+    for (long long g = 0; g < B; g++)
+        for (int v = 0; v < meta[g].n; v++) gid[meta[g].voff + v] = (int)g;
     if (k == 3) relayout<3>(lut.data(), lut_sv.data());
     else if (k == 4) relayout<4>(lut.data(), lut_sv.data());
     else relayout<5>(lut.data(), lut_sv.data());
 
     acc::GraphInfo info{};
     info.nnz = nnz;
-    info.maxdeg = (int)maxdeg;
-    // per-warp overflow lists as the host sizes them: 2 (n + 32) rounded up
-    const long long spw = 2 * ((n + 32 + 31) & ~31LL);
+    info.maxdeg = 0;
+    for (long long v = 0; v < NV; v++) info.maxdeg = std::max(info.maxdeg, deg[v]);
+    // per-warp overflow lists as the host sizes them: 2 (max_n + 32) rounded up
+    const long long spw = 2 * ((max_n + 32 + 31) & ~31LL);
     std::vector<uint32_t> scratch((size_t)spw * blocks * acc::kWarpsPerBlock + 1);
-    std::vector<uint4> queue((size_t)h[9] + 1);
-    std::vector<unsigned long long> counts(ncls, 0);
+    std::vector<uint4> queue((size_t)h[6] + 1);
+    std::vector<unsigned long long> counts((size_t)B * ncls, 0);
     int status = 0;
 
     EnumArgs a{};
@@ -82,30 +102,31 @@ int main(int argc, char **argv) {
     a.nptr = nptr.data();
     a.nbr = nbr.data();
     a.lut = lut_sv.data();
-    a.gs.B = 1;
-    a.gs.NV = n;
+    a.gs.B = (int)B;
+    a.gs.NV = NV;
     a.gs.M = nnz / 2;
-    a.gs.one.n = (int)n;
-    a.gs.one.pitch = pitch;
-    a.max_n = (int)n;
+    if (B == 1) a.gs.one = meta[0];
+    a.gs.many = meta.data();
+    a.gs.gid = gid.data();
+    a.max_n = (int)max_n;
     a.info = &info;
     a.queue = queue.data();
-    a.queue_cap = (unsigned long long)h[9];
+    a.queue_cap = (unsigned long long)h[6];
     a.scratch = scratch.data();
     a.scratch_per_warp = spw;
     a.mode = (int)mode;
-    a.light = h[6];
-    a.target = h[7];
+    a.light = h[3];
+    a.target = h[4];
     a.counts = counts.data();
     a.status = &status;
     const bool count = mode == 0;
-    if (n > 0) {
+    if (NV > 0) {
         if (k == 3) count ? run<3, true>(a, blocks) : run<3, false>(a, blocks);
         else if (k == 4) count ? run<4, true>(a, blocks) : run<4, false>(a, blocks);
         else count ? run<5, true>(a, blocks) : run<5, false>(a, blocks);
     }
     printf("%d %llu %llu", status, info.queue_tail, info.scanned);
-    for (int i = 0; i < ncls; i++) printf(" %llu", counts[i]);
+    for (size_t i = 0; i < counts.size(); i++) printf(" %llu", counts[i]);
     printf("\n");
     return 0;
 }

@@ -6,8 +6,8 @@ skips a collective its warp reaches hangs the warp and the driver reports
 it.  The kernels' code is cut from the CUDA sources between fixed anchors
 and compiled with g++ together with the library's own internal headers; the
 results are compared with the oracle (copies, k = 3, 4, 5 formula counts,
-k = 3, 4, 5 enumeration counts in both modes and under light, heavy and
-queue-full schedules) or with the lists a plain host loop writes
+k = 3, 4, 5 enumeration counts in both modes, under light, heavy and
+queue-full schedules, for single graphs and for sets of graphs) or with the lists a plain host loop writes
 (neighbour-list fill).  The enumeration kernels also run with tiny
 shared-memory lists and histogram drain threshold, so their overflow lists
 and drain run on small graphs.  This checks the kernels' logic and warp
@@ -219,14 +219,34 @@ def test_fill_kernel_writes_sorted_lists(emu_bins, rw):
         assert np.array_equal(got, nbr), (n, rw)
 
 
-def _enum(exe, tmp, k, n, s, d, mode, light=2048, target=4096, blocks=2, qcap=1 << 16):
-    pitch, st, nptr, deg, lo, nbr = _gstar(n, s, d)
+def _enum_set(exe, tmp, k, graphs, mode, light=2048, target=4096, blocks=2, qcap=1 << 16):
+    """Counts of a set of graphs [(n, src, dst)] by the enumeration kernels:
+    (status, chunks queued, entries scanned, counts per graph)."""
     cls, _ = oracle.table(k)
-    hdr = struct.pack("<10q", k, n, pitch, len(nbr), int(deg.max(initial=0)), mode, light, target, blocks, qcap)
-    buf = hdr + st.tobytes() + nptr.astype("<i8").tobytes() + deg.astype("<i4").tobytes() + \
-        lo.astype("<i4").tobytes() + nbr.astype("<u4").tobytes() + np.asarray(cls, "<i2").tobytes()
+    dims, st, nptr, deg, lo, nbr = [], [], [np.zeros(1, np.int64)], [], [], []
+    base = 0
+    for n, s, d in graphs:
+        pitch, st_g, nptr_g, deg_g, lo_g, nbr_g = _gstar(n, s, d)
+        dims.append((n, pitch, len(nbr_g)))
+        st.append(st_g)
+        nptr.append(nptr_g[1:] + base)
+        base += len(nbr_g)
+        deg.append(deg_g)
+        lo.append(lo_g)
+        nbr.append(nbr_g)
+    buf = struct.pack("<7q", k, len(graphs), mode, light, target, blocks, qcap)
+    buf += b"".join(struct.pack("<3q", *x) for x in dims)
+    buf += np.concatenate(st).astype("<u4").tobytes() + np.concatenate(nptr).astype("<i8").tobytes() + \
+        np.concatenate(deg).astype("<i4").tobytes() + np.concatenate(lo).astype("<i4").tobytes() + \
+        np.concatenate(nbr).astype("<u4").tobytes() + np.asarray(cls, "<i2").tobytes()
     vals = [int(x) for x in _run(exe, buf, False, tmp).split()]
-    return vals[0], vals[1], vals[2], vals[3:]
+    ncls = len(oracle.count(3, [], [], k))
+    return vals[0], vals[1], vals[2], [vals[3 + g * ncls: 3 + (g + 1) * ncls] for g in range(len(graphs))]
+
+
+def _enum(exe, tmp, k, n, s, d, mode, light=2048, target=4096, blocks=2, qcap=1 << 16):
+    status, queued, scanned, counts = _enum_set(exe, tmp, k, [(n, s, d)], mode, light, target, blocks, qcap)
+    return status, queued, scanned, counts[0]
 
 
 def _enum_cases(rng, k, count, nmax):
@@ -289,7 +309,7 @@ def test_enumeration_overflow_lists_and_drain(emu_bins, k, mode):
     every 256 increments: hub graphs send the extension lists to the per-warp
     overflow buffers and the counts through the drain."""
     if k == 5:
-        gs = [synth.chung_lu(20, 45, 2.1, 12, 20, 40 + mode)]
+        gs = [synth.chung_lu(18, 38, 2.1, 11, 20, 40 + mode)]
     elif k == 4:
         gs = [synth.chung_lu(40, 110, 2.1, 26, 20, 34 + mode)]
     else:
@@ -301,3 +321,19 @@ def test_enumeration_overflow_lists_and_drain(emu_bins, k, mode):
                                       target)
             assert status == 0
             assert got == oracle.count(g.n, g.src, g.dst, k).tolist(), (k, mode, g.name, light)
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+@pytest.mark.parametrize("mode", [0, 1], ids=["count", "enumerate"])
+def test_enumeration_kernels_on_graph_sets(emu_bins, k, mode):
+    """Several graphs in one launch pair (the batched form): units of every
+    graph interleave in the warps' grabs, each graph's counts stay apart."""
+    rng = np.random.default_rng(800 + 10 * k + mode)
+    graphs = _enum_cases(rng, k, 4, {3: 24, 4: 14, 5: 10}[k])
+    graphs.insert(2, (7, np.zeros(0, np.int64), np.zeros(0, np.int64)))
+    want = [oracle.count(n, s, d, k).tolist() for n, s, d in graphs]
+    for light, target, qcap in SCHEDULES.values():
+        status, _, _, got = _enum_set(emu_bins["emu_enum"], emu_bins["dir"], k, graphs, mode, light, target,
+                                      blocks=3, qcap=qcap)
+        assert status == 0
+        assert got == want, (k, mode, light, qcap)
