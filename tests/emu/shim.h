@@ -1,20 +1,29 @@
 // CPU stand-ins for the CUDA constructs the library's kernels use, so that a
-// kernel's own source can run on the host: one std::thread per lane, every
+// kernel's own source can run on the host: one host thread per lane (from a
+// pool of persistent threads), every
 // warp collective (shuffles, ballot, match, reduce, __syncwarp) a barrier of
 // the 32 lane threads, and atomics on std::atomic_ref.  A lane that skips a
 // collective its warp reaches leaves the others waiting at the barrier,
-// which the driver reports as a hang.  Shared arrays are static (one block
-// runs at a time, one warp per block).
+// which the driver reports as a hang.  Shared arrays are static: one block
+// runs at a time, either one warp after another (run_warps, for kernels
+// whose blocks never synchronise across warps) or all its threads at once
+// (run_blocks / emu_launch, where __syncthreads is a barrier of the block's
+// threads and a thread that returns leaves it, as an exited GPU thread no
+// longer holds a block barrier back).
 #pragma once
 #include <algorithm>
 #include <atomic>
 #include <barrier>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
+#include <memory>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -37,13 +46,18 @@ extern thread_local dim threadIdx, blockIdx;
 extern dim blockDim, gridDim;
 struct WarpCtx { std::barrier<> *bar; uint64_t slot[32]; };
 extern thread_local WarpCtx *tw;
+// the block barrier of the running thread (null under run_warps)
+inline thread_local std::barrier<> *tblk = nullptr;
 
 template <class T> inline T __ldg(const T *p) { return *p; }
 inline uint64_t __umul64hi(uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128)a * b) >> 64); }
 inline int lane_() { return threadIdx.x & 31; }
 inline void wsync() { tw->bar->arrive_and_wait(); }
 inline void __syncwarp(unsigned = 0xffffffffu) { wsync(); }
-inline void __syncthreads() { wsync(); }
+inline void __syncthreads() {
+    if (tblk) tblk->arrive_and_wait();
+    else wsync();
+}
 template <class T> inline T exch(T v, int src) {
     wsync();
     tw->slot[lane_()] = (uint64_t)(int64_t)v;
@@ -105,13 +119,70 @@ inline void __threadfence_block() { std::atomic_thread_fence(std::memory_order_s
 inline unsigned long long atomicAdd(unsigned long long *p, unsigned long long v) {
     return std::atomic_ref<unsigned long long>(*p).fetch_add(v);
 }
+inline int atomicMax(int *p, int v) {
+    std::atomic_ref<int> r(*p);
+    int old = r.load();
+    while (old < v && !r.compare_exchange_weak(old, v)) {
+    }
+    return old;
+}
 inline int atomicCAS(int *p, int c, int v) {
     std::atomic_ref<int>(*p).compare_exchange_strong(c, v);
     return c;
 }
 
-// Run f() as blocks x (threads / 32) warps, one warp at a time; returns false
-// when a warp does not finish within the limit (a lane left a collective).
+// Persistent host threads that play the lanes: run(n, job) has threads
+// 0..n-1 call job(i) once each and waits for them; false when they have not
+// all returned within the limit (a lane left a collective).  Threads are
+// created once and reused, so a launch costs no thread creation.
+struct LanePool {
+    std::mutex m;
+    std::condition_variable go, fin;
+    std::vector<std::thread> th;
+    std::function<void(int)> job;
+    long long gen = 0;
+    int active = 0, remaining = 0;
+    void loop(int id) {
+        long long seen = 0;
+        for (;;) {
+            std::function<void(int)> j;
+            {
+                std::unique_lock<std::mutex> lk(m);
+                go.wait(lk, [&] { return gen != seen; });
+                seen = gen;
+                if (id >= active) continue;
+                j = job;
+            }
+            j(id);
+            std::lock_guard<std::mutex> lk(m);
+            if (--remaining == 0) fin.notify_all();
+        }
+    }
+    bool run(int n, std::function<void(int)> j, int limit_s) {
+        while ((int)th.size() < n) {
+            const int id = (int)th.size();
+            th.emplace_back([this, id] { loop(id); });
+            th.back().detach();
+        }
+        {
+            std::lock_guard<std::mutex> lk(m);
+            job = std::move(j);
+            active = n;
+            remaining = n;
+            gen++;
+        }
+        go.notify_all();
+        std::unique_lock<std::mutex> lk(m);
+        return fin.wait_for(lk, std::chrono::seconds(limit_s), [&] { return remaining == 0; });
+    }
+};
+inline LanePool *lane_pool() {
+    static LanePool *p = new LanePool;  // never destroyed: its threads outlive main
+    return p;
+}
+
+// Run f() as blocks x (threads / 32) warps, one warp at a time; exits the
+// process when a warp does not finish within the limit.
 template <class F> bool run_warps(int blocks, int threads, F f, int limit_s = 120) {
     blockDim.x = threads;
     gridDim.x = blocks;
@@ -120,23 +191,59 @@ template <class F> bool run_warps(int blocks, int threads, F f, int limit_s = 12
             std::barrier<> bar(32);
             WarpCtx ctx;
             ctx.bar = &bar;
-            std::atomic<int> done{0};
-            std::vector<std::thread> th;
-            for (int l = 0; l < 32; l++)
-                th.emplace_back([&, l] {
-                    threadIdx.x = w * 32 + l;
-                    blockIdx.x = b;
-                    tw = &ctx;
-                    f();
-                    done++;
-                });
-            for (int t = 0; t < limit_s * 100 && done.load() < 32; t++)
-                std::this_thread::sleep_for(std::chrono::milliseconds(10));
-            if (done.load() < 32) {
+            const bool ok = lane_pool()->run(32, [&](int l) {
+                threadIdx.x = w * 32 + l;
+                blockIdx.x = b;
+                tw = &ctx;
+                tblk = nullptr;
+                f();
+            }, limit_s);
+            if (!ok) {
                 fprintf(stderr, "warp %d of block %d did not finish\n", w, b);
                 std::_Exit(3);
             }
-            for (auto &t : th) t.join();
         }
     return true;
+}
+
+// Run f() as `blocks` blocks of `threads` threads, one block at a time, all
+// threads of a block at once; exits the process when a block does not
+// finish within the limit.
+template <class F> bool run_blocks(int blocks, int threads, F f, int limit_s = 120) {
+    blockDim.x = threads;
+    gridDim.x = blocks;
+    const int nw = (threads + 31) / 32;
+    for (int b = 0; b < blocks; b++) {
+        std::barrier<> block_bar(threads);
+        std::vector<std::unique_ptr<std::barrier<>>> wbar;
+        std::vector<WarpCtx> ctx(nw);
+        for (int w = 0; w < nw; w++) {
+            wbar.emplace_back(new std::barrier<>(std::min(32, threads - 32 * w)));
+            ctx[w].bar = wbar.back().get();
+        }
+        const bool ok = lane_pool()->run(threads, [&](int t) {
+            threadIdx.x = t;
+            blockIdx.x = b;
+            tw = &ctx[t / 32];
+            tblk = &block_bar;
+            f();
+            block_bar.arrive_and_drop();
+            tblk = nullptr;
+        }, limit_s);
+        if (!ok) {
+            fprintf(stderr, "block %d did not finish\n", b);
+            std::_Exit(3);
+        }
+    }
+    return true;
+}
+
+// Stand-in for a kernel launch <<<grid, block, dynamic smem, stream>>>: the
+// dynamic shared memory is emu_dyn_smem (zeroed, at least `smem` bytes).
+inline std::vector<uint64_t> emu_dyn_buf;
+inline unsigned char *emu_dyn_smem = nullptr;
+template <class F> void emu_launch(long long grid, long long block, size_t smem, void *, F f) {
+    emu_dyn_buf.assign(smem / 8 + 2, 0);
+    emu_dyn_smem = reinterpret_cast<unsigned char *>(emu_dyn_buf.data());
+    run_blocks((int)grid, (int)block, f);
 }

@@ -8,7 +8,10 @@ and compiled with g++ together with the library's own internal headers; the
 results are compared with the oracle (copies, k = 3, 4, 5 formula counts,
 k = 3, 4, 5 enumeration counts in both modes, under light, heavy and
 queue-full schedules, for single graphs and for sets of graphs) or with the lists a plain host loop writes
-(neighbour-list fill).  The enumeration kernels also run with tiny
+(neighbour-list fill; the whole graph builder, kernels and host launcher,
+against a plain construction of the same pair states, lists and
+renumbering, and on malformed inputs under the address sanitizer).  The
+enumeration kernels also run with tiny
 shared-memory lists and histogram drain threshold, so their overflow lists
 and drain run on small graphs.  This checks the kernels' logic and warp
 discipline without a GPU; the GPU tests check the compiled kernels."""
@@ -41,6 +44,38 @@ def _function(src, head):
     return src[a:src.index("\n}\n", a) + 3]
 
 
+def _launches_to_calls(src):
+    """Every `kernel<<<grid, block, smem, stream>>>(args);` of a CUDA source as
+    `emu_launch(grid, block, smem, stream, [&] { kernel(args); });`, and its
+    dynamic shared arrays as the launch's buffer."""
+    out, i = [], 0
+    while True:
+        a = src.find("<<<", i)
+        if a < 0:
+            break
+        name_start = a
+        while name_start > 0 and (src[name_start - 1].isalnum() or src[name_start - 1] == "_"):
+            name_start -= 1
+        b = src.index(">>>(", a)
+        depth, c = 1, b + 4
+        while depth:
+            depth += {"(": 1, ")": -1}.get(src[c], 0)
+            c += 1
+        assert src[c] == ";", src[a:c + 1]
+        out.append(src[i:name_start])
+        out.append("emu_launch(%s, [&] { %s(%s); })" % (src[a + 3:b], src[name_start:a], src[b + 4:c - 1]))
+        i = c
+    out.append(src[i:])
+    src = "".join(out)
+    n = 0
+    for name in ("deg", "h"):
+        old = "extern __shared__ int %s[];" % name
+        n += src.count(old)
+        src = src.replace(old, "int *%s = reinterpret_cast<int *>(emu_dyn_smem);" % name)
+    assert n == 2 and "extern __shared__" not in src
+    return src
+
+
 @pytest.fixture(scope="session")
 def emu_bins(tmp_path_factory):
     if shutil.which("g++") is None:
@@ -69,12 +104,29 @@ def emu_bins(tmp_path_factory):
     open(out / "enum_kernels.inc", "w").write(region)
     lut = open(os.path.join(CSRC, "lut.cu")).read()
     open(out / "relayout.inc", "w").write(_function(lut, "template <int K>\n__global__ void k_relayout("))
+    # the graph builder whole, kernels and launcher: each <<<...>>> launch
+    # becomes emu_launch, the dynamic shared arrays its buffer; a copy of the
+    # internal header with small single-block limits, so that the tiled
+    # degree scan and the histogram renumbering run on small sets
+    bdir = out / "build"
+    bdir.mkdir()
+    open(bdir / "graph_kernels.inc", "w").write(_launches_to_calls(
+        open(os.path.join(CSRC, "graph.cu")).read().split('#include "common.cuh"\n', 1)[1]))
+    common = open(os.path.join(CSRC, "common.cuh")).read()
+    for old, new in (('#include "../../include/acc_motif.h"',
+                      '#include "' + os.path.join(ROOT, "include", "acc_motif.h") + '"'),
+                     ("constexpr long long kScanSingleMax = 1 << 15;", "constexpr long long kScanSingleMax = 2048;"),
+                     ("constexpr int kRelabelSmemMax = 1 << 15;", "constexpr int kRelabelSmemMax = 2048;")):
+        assert common.count(old) == 1, old
+        common = common.replace(old, new)
+    open(bdir / "common.cuh", "w").write(common)
     # (binary, source, extra flags): the enumeration kernels as built, and
     # with tiny shared-memory lists and drain threshold so that the overflow
     # lists and the histogram drain run on small graphs
     targets = [(n, n, []) for n in ("emu_rand", "emu_f4", "emu_f35", "emu_fill")]
     targets += [("emu_enum", "emu_enum", ["-DEMU_DRAIN_AT=(1u<<30)"]),
-                ("emu_enum_small", "emu_enum", ["-DEMU_DRAIN_AT=256u", "-DACC_CAP34=16", "-DACC_CAP5=8"])]
+                ("emu_enum_small", "emu_enum", ["-DEMU_DRAIN_AT=256u", "-DACC_CAP34=16", "-DACC_CAP5=8"]),
+                ("emu_build", "emu_build", ["-I", str(bdir), "-fsanitize=address"])]
     procs = []
     for name, src, extra in targets:
         exe = out / name
@@ -101,11 +153,26 @@ def csr(n, s, d):
 
 
 def _run(exe, inp, out, tmp):
-    ip, op = os.path.join(tmp, "in.bin"), os.path.join(tmp, "out.bin")
-    open(ip, "wb").write(inp)
-    r = subprocess.run([exe, ip, op], capture_output=True, text=True, timeout=600)
-    assert r.returncode == 0, r.stderr[-2000:]
-    return open(op, "rb").read() if out else r.stdout
+    return _run_many(exe, [inp], out, tmp)[0]
+
+
+def _run_many(exe, inps, out, tmp):
+    """Run the emulator once per input, a few processes at a time (each is
+    mostly waiting on its lanes' barriers); outputs in input order."""
+    width = max(1, min(4, (os.cpu_count() or 2) // 2))
+    res, running, nxt = [None] * len(inps), [], 0
+    while nxt < len(inps) or running:
+        while nxt < len(inps) and len(running) < width:
+            ip, op = os.path.join(tmp, "in%d.bin" % nxt), os.path.join(tmp, "out%d.bin" % nxt)
+            open(ip, "wb").write(inps[nxt])
+            pr = subprocess.Popen([exe, ip, op], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+            running.append((nxt, op, pr))
+            nxt += 1
+        i, op, pr = running.pop(0)
+        so, se = pr.communicate(timeout=600)
+        assert pr.returncode == 0, se[-2000:]
+        res[i] = open(op, "rb").read() if out else so
+    return res
 
 
 @pytest.mark.parametrize("mode,use_bits", [(0, 1), (0, 0), (1, 1), (1, 0)],
@@ -219,9 +286,8 @@ def test_fill_kernel_writes_sorted_lists(emu_bins, rw):
         assert np.array_equal(got, nbr), (n, rw)
 
 
-def _enum_set(exe, tmp, k, graphs, mode, light=2048, target=4096, blocks=2, qcap=1 << 16):
-    """Counts of a set of graphs [(n, src, dst)] by the enumeration kernels:
-    (status, chunks queued, entries scanned, counts per graph)."""
+def _enum_input(k, graphs, mode, light=2048, target=4096, blocks=2, qcap=1 << 16):
+    """Emulator input for counting a set of graphs [(n, src, dst)]."""
     cls, _ = oracle.table(k)
     dims, st, nptr, deg, lo, nbr = [], [], [np.zeros(1, np.int64)], [], [], []
     base = 0
@@ -239,14 +305,20 @@ def _enum_set(exe, tmp, k, graphs, mode, light=2048, target=4096, blocks=2, qcap
     buf += np.concatenate(st).astype("<u4").tobytes() + np.concatenate(nptr).astype("<i8").tobytes() + \
         np.concatenate(deg).astype("<i4").tobytes() + np.concatenate(lo).astype("<i4").tobytes() + \
         np.concatenate(nbr).astype("<u4").tobytes() + np.asarray(cls, "<i2").tobytes()
-    vals = [int(x) for x in _run(exe, buf, False, tmp).split()]
-    ncls = len(oracle.count(3, [], [], k))
-    return vals[0], vals[1], vals[2], [vals[3 + g * ncls: 3 + (g + 1) * ncls] for g in range(len(graphs))]
+    return buf
 
 
-def _enum(exe, tmp, k, n, s, d, mode, light=2048, target=4096, blocks=2, qcap=1 << 16):
-    status, queued, scanned, counts = _enum_set(exe, tmp, k, [(n, s, d)], mode, light, target, blocks, qcap)
-    return status, queued, scanned, counts[0]
+def _enum_many(exe, tmp, k, jobs):
+    """Run [(graphs, kwargs)] through the enumeration kernels: per job
+    (status, chunks queued, entries scanned, counts per graph)."""
+    outs = _run_many(exe, [_enum_input(k, g, **kw) for g, kw in jobs], False, tmp)
+    ncls = {3: 13, 4: 199, 5: 9364}[k]
+    res = []
+    for (graphs, _), o in zip(jobs, outs):
+        vals = [int(x) for x in o.split()]
+        res.append((vals[0], vals[1], vals[2],
+                    [vals[3 + g * ncls: 3 + (g + 1) * ncls] for g in range(len(graphs))]))
+    return res
 
 
 def _enum_cases(rng, k, count, nmax):
@@ -273,9 +345,10 @@ def test_enumeration_kernels_equal_oracle(emu_bins, k, mode, sched):
     cases.append((5, np.array([0, 1, 2, 3], np.int64), np.array([1, 2, 3, 4], np.int64)))  # a directed path
     cases.append((6, np.zeros(0, np.int64), np.zeros(0, np.int64)))  # no arcs
     most = 0
-    for n, s, d in cases:
-        status, queued, scanned, got = _enum(emu_bins["emu_enum"], emu_bins["dir"], k, n, s, d, mode, light,
-                                             target, qcap=qcap)
+    jobs = [([c], dict(mode=mode, light=light, target=target, qcap=qcap)) for c in cases]
+    for (n, s, d), (status, queued, scanned, counts) in zip(cases, _enum_many(emu_bins["emu_enum"],
+                                                                                emu_bins["dir"], k, jobs)):
+        got = counts[0]
         assert status == 0
         assert got == oracle.count(n, s, d, k).tolist(), (k, mode, sched, n)
         if mode == 1:
@@ -314,13 +387,16 @@ def test_enumeration_overflow_lists_and_drain(emu_bins, k, mode):
         gs = [synth.chung_lu(40, 110, 2.1, 26, 20, 34 + mode)]
     else:
         gs = [synth.chung_lu(70, 260, 2.1, 45, 20, 33 + mode), synth.regulatory(60, 200, 6, 2.1, 40, 10, 9)]
+    jobs, want = [], []
     for g in gs:
         s, d = _by_degree(g.n, g.src, g.dst)
         for light, target in ((1 << 30, 1 << 30), (64, 64)):
-            status, _, _, got = _enum(emu_bins["emu_enum_small"], emu_bins["dir"], k, g.n, s, d, mode, light,
-                                      target)
-            assert status == 0
-            assert got == oracle.count(g.n, g.src, g.dst, k).tolist(), (k, mode, g.name, light)
+            jobs.append(([(g.n, s, d)], dict(mode=mode, light=light, target=target)))
+            want.append(oracle.count(g.n, g.src, g.dst, k).tolist())
+    for (status, _, _, got), w, (_, kw) in zip(_enum_many(emu_bins["emu_enum_small"], emu_bins["dir"], k, jobs),
+                                               want, jobs):
+        assert status == 0
+        assert got[0] == w, (k, kw)
 
 
 @pytest.mark.parametrize("k", [3, 4, 5])
@@ -332,8 +408,146 @@ def test_enumeration_kernels_on_graph_sets(emu_bins, k, mode):
     graphs = _enum_cases(rng, k, 4, {3: 24, 4: 14, 5: 10}[k])
     graphs.insert(2, (7, np.zeros(0, np.int64), np.zeros(0, np.int64)))
     want = [oracle.count(n, s, d, k).tolist() for n, s, d in graphs]
-    for light, target, qcap in SCHEDULES.values():
-        status, _, _, got = _enum_set(emu_bins["emu_enum"], emu_bins["dir"], k, graphs, mode, light, target,
-                                      blocks=3, qcap=qcap)
+    jobs = [(graphs, dict(mode=mode, light=light, target=target, blocks=3, qcap=qcap))
+            for light, target, qcap in SCHEDULES.values()]
+    for (status, _, _, got), (_, kw) in zip(_enum_many(emu_bins["emu_enum"], emu_bins["dir"], k, jobs), jobs):
         assert status == 0
-        assert got == want, (k, mode, light, qcap)
+        assert got == want, (k, kw)
+
+
+def _err_input():
+    import re
+    hdr = open(os.path.join(ROOT, "include", "acc_motif.h")).read()
+    return int(re.search(r"#define\s+ACC_ERR_INPUT\s+\(?(-?\d+)\)?", hdr).group(1))
+
+
+def _build_many(bins, jobs):
+    """Run the graph builder over [(graphs, relabel, num_sms)], graphs a list
+    of (n, rowptr, col): per job, the two builds' records."""
+    inps = []
+    for graphs, relabel, num_sms in jobs:
+        buf = struct.pack("<3q", int(relabel), num_sms, len(graphs))
+        buf += b"".join(struct.pack("<2q", n, len(cl)) for n, _, cl in graphs)
+        for n, rp, cl in graphs:
+            buf += np.asarray(rp, "<i8").tobytes() + np.asarray(cl, "<i4").tobytes()
+        inps.append(buf)
+    names = ("head", "label", "deg", "lo", "nptr", "nbr", "state", "occ", "clean")
+    res = []
+    for o in _run_many(bins["emu_build"], inps, True, bins["dir"]):
+        raw = np.frombuffer(o, "<i8")
+        recs, i = [], 0
+        while i < len(raw):
+            recs.append(raw[i + 1:i + 1 + raw[i]])
+            i += 1 + raw[i]
+        assert len(recs) == 2 * len(names)
+        res.append([dict(zip(names, recs[j * len(names):(j + 1) * len(names)])) for j in range(2)])
+    return res
+
+
+def _check_build(r, graphs, relabel):
+    """The builder's records against a plain construction: per graph, the
+    renumbering orders vertices by descending (clamped) out- plus in-degree
+    and is a permutation; the pair states, degrees, below-counts, neighbour
+    lists (positions over the whole set) and occupancy bits are those of the
+    renumbered graph."""
+    status, _, nnz, maxdeg, zeroed = r["head"].tolist()
+    assert status == 0 and zeroed == 1 and r["clean"][0] == 1
+    voff, base = 0, 0
+    st_all, nptr_all, deg_all, lo_all, nbr_all, occ_all = [], [np.zeros(1, np.int64)], [], [], [], []
+    occ_w = max(1, ((((max([n for n, _, _ in graphs] + [0]) + 15) // 16) + 31) // 32 + 31) // 32)
+    for n, rp, cl in graphs:
+        src = np.repeat(np.arange(n), np.diff(np.asarray(rp, np.int64)))
+        dst = np.asarray(cl, np.int64)
+        new = np.arange(n)
+        if relabel:
+            lab = r["label"][voff:voff + n] - voff
+            assert sorted(lab.tolist()) == list(range(n))
+            key = np.minimum(np.bincount(src, minlength=n) + np.bincount(dst, minlength=n), max(n - 1, 0))
+            inv = np.empty(n, np.int64)
+            inv[lab] = np.arange(n)
+            assert np.all(np.diff(key[inv]) <= 0)
+            new = lab
+        pitch, st, nptr, deg, lo, nbr = _gstar(n, new[src], new[dst])
+        st_all.append(st)
+        nptr_all.append(nptr[1:] + base)
+        base += len(nbr)
+        deg_all.append(deg)
+        lo_all.append(lo)
+        nbr_all.append(nbr)
+        occ = np.zeros(n * occ_w, np.int64)
+        for v in range(n):
+            for wd in np.nonzero(st[v * pitch:(v + 1) * pitch])[0]:
+                ch = int(wd) // 32
+                occ[v * occ_w + ch // 32] |= 1 << (ch % 32)
+        occ_all.append(occ)
+        voff += n
+    cat = lambda xs: np.concatenate(xs).astype(np.int64) if xs else np.zeros(0, np.int64)  # noqa: E731
+    assert np.array_equal(r["state"], cat(st_all))
+    assert np.array_equal(r["deg"], cat(deg_all)) and np.array_equal(r["lo"], cat(lo_all))
+    assert np.array_equal(r["nptr"], cat(nptr_all)) and np.array_equal(r["nbr"], cat(nbr_all))
+    assert np.array_equal(r["occ"], cat(occ_all))
+    assert nnz == base and maxdeg == (int(max(d.max(initial=0) for d in deg_all)) if deg_all else 0)
+
+
+def _raw_csr(n, s, d, rng):
+    """An out-CSR with the rows' arcs in random order (repeats kept)."""
+    s, d = np.asarray(s, np.int64), np.asarray(d, np.int64)
+    order = np.lexsort((rng.random(len(s)), s))
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(s, minlength=n), out=rp[1:])
+    return n, rp, d[order].astype(np.int32)
+
+
+@pytest.mark.parametrize("relabel", [False, True], ids=["as_given", "renumbered"])
+def test_graph_builder_equals_plain_construction(emu_bins, relabel):
+    """The whole builder (zeroing, renumbering, ingest, degree scan, fill,
+    then the clear) on the host, built with 2048-vertex single-block limits:
+    one small graph (one-block scan, shared-memory renumbering), and a set
+    of 5270 vertices with two graphs over 2048 (tiled scan over two tiles,
+    histogram renumbering), an empty graph and repeated and mutual arcs."""
+    rng = np.random.default_rng(900 + relabel)
+    n = 300
+    s, d = random_digraph(rng, n, p=0.02, recip=0.3)
+    small = [_raw_csr(n, s, d, rng)]
+    big = []
+    for n in (50, 2500, 0, 120, 2600):
+        s, d = random_digraph(rng, n, p=min(0.1, 3.0 / max(n, 1)), recip=0.3) if n else ([], [])
+        s, d = np.asarray(s, np.int64), np.asarray(d, np.int64)
+        if len(s):  # repeat some arcs
+            k = rng.integers(0, len(s), size=len(s) // 10)
+            s, d = np.concatenate([s, s[k]]), np.concatenate([d, d[k]])
+        big.append(_raw_csr(n, s, d, rng))
+    jobs = [(small, relabel, 1), (big, relabel, 2)]
+    for (graphs, _, _), builds in zip(jobs, _build_many(emu_bins, jobs)):
+        for r in builds:
+            _check_build(r, graphs, relabel)
+
+
+def test_graph_builder_reports_malformed_input(emu_bins):
+    """Self-loops, targets out of range, rows out of order or outside the
+    arcs, and arcs of a graph without vertices set ACC_ERR_INPUT; the clear
+    still leaves the pair-state buffer all zero (the build runs under the
+    address sanitizer, so nothing is read or written out of bounds either)."""
+    err = _err_input()
+    ok_rp, ok_col = np.array([0, 2, 3, 4], np.int64), np.array([1, 2, 2, 0], np.int32)
+    bad = [
+        (3, ok_rp, np.array([1, 2, 2, 2], np.int32)),   # self-loop 2 -> 2
+        (3, ok_rp, np.array([1, 3, 2, 0], np.int32)),   # target n
+        (3, ok_rp, np.array([1, -1, 2, 0], np.int32)),  # negative target
+        (3, np.array([0, 3, 2, 4], np.int64), ok_col),  # rowptr decreasing
+        (3, np.array([1, 2, 3, 4], np.int64), ok_col),  # rowptr[0] != 0
+        (3, np.array([0, 2, 3, 3], np.int64), ok_col),  # rowptr[n] != m
+        (3, np.array([0, 2, 3, 9], np.int64), ok_col),  # rowptr past m
+    ]
+    empty_with_arcs = (0, np.array([0], np.int64), np.array([0], np.int32))
+    jobs = [([case], True, 1) for case in bad] + [([(3, ok_rp, ok_col), case], True, 1) for case in bad]
+    jobs.append(([(3, ok_rp, ok_col), empty_with_arcs], False, 1))
+    good = [(3, ok_rp, ok_col)]
+    jobs.append((good, True, 1))
+    res = _build_many(emu_bins, jobs)
+    for (graphs, _, _), builds in zip(jobs[:-1], res[:-1]):
+        for r in builds:
+            assert r["head"][0] == err, graphs
+            assert r["clean"][0] == 1
+    for r in res[-1]:
+        _check_build(r, good, True)
