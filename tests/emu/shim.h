@@ -24,6 +24,7 @@
 #include <functional>
 #include <memory>
 #include <mutex>
+#include <semaphore>
 #include <thread>
 #include <vector>
 
@@ -136,42 +137,35 @@ inline int atomicCAS(int *p, int c, int v) {
 // all returned within the limit (a lane left a collective).  Threads are
 // created once and reused, so a launch costs no thread creation.
 struct LanePool {
-    std::mutex m;
-    std::condition_variable go, fin;
-    std::vector<std::thread> th;
+    struct Worker {
+        std::binary_semaphore go{0};
+    };
+    std::vector<std::unique_ptr<Worker>> ws;
     std::function<void(int)> job;
-    long long gen = 0;
-    int active = 0, remaining = 0;
-    void loop(int id) {
-        long long seen = 0;
+    std::mutex m;
+    std::condition_variable fin;
+    int remaining = 0;
+    void loop(Worker *w, int id) {
         for (;;) {
-            std::function<void(int)> j;
-            {
-                std::unique_lock<std::mutex> lk(m);
-                go.wait(lk, [&] { return gen != seen; });
-                seen = gen;
-                if (id >= active) continue;
-                j = job;
-            }
-            j(id);
+            w->go.acquire();  // only the threads a run needs are woken
+            job(id);
             std::lock_guard<std::mutex> lk(m);
             if (--remaining == 0) fin.notify_all();
         }
     }
     bool run(int n, std::function<void(int)> j, int limit_s) {
-        while ((int)th.size() < n) {
-            const int id = (int)th.size();
-            th.emplace_back([this, id] { loop(id); });
-            th.back().detach();
+        while ((int)ws.size() < n) {
+            ws.emplace_back(new Worker);
+            Worker *w = ws.back().get();
+            const int id = (int)ws.size() - 1;
+            std::thread([this, w, id] { loop(w, id); }).detach();
         }
+        job = std::move(j);
         {
             std::lock_guard<std::mutex> lk(m);
-            job = std::move(j);
-            active = n;
             remaining = n;
-            gen++;
         }
-        go.notify_all();
+        for (int i = 0; i < n; i++) ws[i]->go.release();
         std::unique_lock<std::mutex> lk(m);
         return fin.wait_for(lk, std::chrono::seconds(limit_s), [&] { return remaining == 0; });
     }

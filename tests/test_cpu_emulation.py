@@ -10,7 +10,8 @@ k = 3, 4, 5 enumeration counts in both modes, under light, heavy and
 queue-full schedules, for single graphs and for sets of graphs) or with the lists a plain host loop writes
 (neighbour-list fill; the whole graph builder, kernels and host launcher,
 against a plain construction of the same pair states, lists and
-renumbering, and on malformed inputs under the address sanitizer).  The
+renumbering, and on malformed inputs under the address sanitizer; the
+class-table builder against the oracle's table).  The
 enumeration kernels also run with tiny
 shared-memory lists and histogram drain threshold, so their overflow lists
 and drain run on small graphs.  This checks the kernels' logic and warp
@@ -54,6 +55,13 @@ def _launches_to_calls(src):
         if a < 0:
             break
         name_start = a
+        if src[name_start - 1] == ">":  # template arguments: back to their '<'
+            depth = 0
+            while True:
+                name_start -= 1
+                depth += {">": 1, "<": -1}.get(src[name_start], 0)
+                if depth == 0:
+                    break
         while name_start > 0 and (src[name_start - 1].isalnum() or src[name_start - 1] == "_"):
             name_start -= 1
         b = src.index(">>>(", a)
@@ -67,12 +75,10 @@ def _launches_to_calls(src):
         i = c
     out.append(src[i:])
     src = "".join(out)
-    n = 0
     for name in ("deg", "h"):
         old = "extern __shared__ int %s[];" % name
-        n += src.count(old)
         src = src.replace(old, "int *%s = reinterpret_cast<int *>(emu_dyn_smem);" % name)
-    assert n == 2 and "extern __shared__" not in src
+    assert "extern __shared__" not in src
     return src
 
 
@@ -120,13 +126,17 @@ def emu_bins(tmp_path_factory):
         assert common.count(old) == 1, old
         common = common.replace(old, new)
     open(bdir / "common.cuh", "w").write(common)
+    # the class-table builder (kernels and launch_build_lut)
+    lut_src = open(os.path.join(CSRC, "lut.cu")).read().split('#include "common.cuh"\n', 1)[1]
+    open(out / "lut_all.inc", "w").write(_launches_to_calls(lut_src.split("// Allocation-free table build.")[0]))
     # (binary, source, extra flags): the enumeration kernels as built, and
     # with tiny shared-memory lists and drain threshold so that the overflow
     # lists and the histogram drain run on small graphs
     targets = [(n, n, []) for n in ("emu_rand", "emu_f4", "emu_f35", "emu_fill")]
     targets += [("emu_enum", "emu_enum", ["-DEMU_DRAIN_AT=(1u<<30)"]),
                 ("emu_enum_small", "emu_enum", ["-DEMU_DRAIN_AT=256u", "-DACC_CAP34=16", "-DACC_CAP5=8"]),
-                ("emu_build", "emu_build", ["-I", str(bdir), "-fsanitize=address"])]
+                ("emu_build", "emu_build", ["-I", str(bdir), "-fsanitize=address"]),
+                ("emu_lut", "emu_lut", ["-O2"])]
     procs = []
     for name, src, extra in targets:
         exe = out / name
@@ -551,3 +561,43 @@ def test_graph_builder_reports_malformed_input(emu_bins):
             assert r["clean"][0] == 1
     for r in res[-1]:
         _check_build(r, good, True)
+
+
+def _sv_to_canonical(k):
+    """Canonical code of every state-vector layout code: field f_t (slots
+    t = k-1 in the lowest bits up to t = 1) holds state(w_i, w_t) at bits
+    2i, 2i+1 for i < t; state bit 0 is the arc w_i -> w_t, bit 1 the arc
+    w_t -> w_i; the arc from slot i to slot j is canonical bit
+    i (k-1) + j - [j > i]."""
+    cp = np.arange(1 << (k * (k - 1)), dtype=np.int64)
+    c = np.zeros_like(cp)
+    off = 0
+    bit = lambda i, j: i * (k - 1) + j - (1 if j > i else 0)  # noqa: E731
+    for t in range(k - 1, 0, -1):
+        for i in range(t):
+            st = (cp >> (off + 2 * i)) & 3
+            c |= (st & 1) << bit(i, t)
+            c |= (st >> 1) << bit(t, i)
+        off += 2 * t
+    return c
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_table_builder_equals_oracle_table(emu_bins, k):
+    """The device table builder (canonical code per adjacency code, class
+    ranks, the table and its kernel layout) run on the host: the table and
+    the class codes equal the oracle's, the relayout permutes it as the
+    enumeration kernels read it.  (k = 5 runs the same template code over
+    2^20 codes in 4096 blocks, most of a minute here; the GPU tests compare
+    its table with the oracle's.)"""
+    raw = _run(emu_bins["emu_lut"], struct.pack("<q", k), True, emu_bins["dir"])
+    ncodes = 1 << (k * (k - 1))
+    rc = struct.unpack("<q", raw[:8])[0]
+    lut = np.frombuffer(raw[8:8 + 2 * ncodes], "<i2")
+    lut_sv = np.frombuffer(raw[8 + 2 * ncodes:8 + 4 * ncodes], "<i2")
+    cc = np.frombuffer(raw[8 + 4 * ncodes:], "<u4")
+    assert rc == 4  # four launches
+    cls, codes = oracle.table(k)
+    assert np.array_equal(lut, np.asarray(cls, np.int16))
+    assert np.array_equal(cc, np.asarray(codes, np.uint32))
+    assert np.array_equal(lut_sv, lut[_sv_to_canonical(k)])
