@@ -1,22 +1,20 @@
-// Runs the k = 3 or k = 5 formula kernels (source extracted from
-// csrc/formula3.cu and csrc/formula5.cu into f3_kernels.inc / f5_kernels.inc)
-// on the host over a G* build given as input: k n pitch nnz, state[n *
-// pitch], nptr[n + 1], deg[n], lo[n], nbr[nnz], the code -> class table
-// (2^(k(k-1)) int16) and the class codes.  Output: status and the counts.
+// Runs the k = 3 or k = 5 formula path (csrc/formula3.cu or csrc/formula5.cu,
+// kernels and launcher, each launch turned into emu_launch; source in
+// f3_all.inc / f5_all.inc, chosen by EMU_K) on the host over a G* build given
+// as input: k n pitch nnz, state[n * pitch], nptr[n + 1], deg[n], lo[n],
+// nbr[nnz], the code -> class table (2^(k(k-1)) int16) and the class codes.
+// Output: status and the counts.
 #include "shim.h"
 #include "common.cuh"
 #include "formula.cuh"
 thread_local dim threadIdx, blockIdx;
 dim blockDim, gridDim;
 thread_local WarpCtx *tw;
-namespace acc {
-namespace f3 {
-#include "f3_kernels.inc"
-}  // namespace f3
-namespace f5 {
-#include "f5_kernels.inc"
-}  // namespace f5
-}  // namespace acc
+#if EMU_K == 3
+#include "f3_all.inc"
+#else
+#include "f5_all.inc"
+#endif
 using acc::GSet;
 
 template <class T> static bool rd(FILE *f, T *p, size_t n) { return fread(p, sizeof(T), n, f) == n; }
@@ -25,6 +23,7 @@ int main(int argc, char **argv) {
     FILE *f = fopen(argv[1], "rb");
     long long k, n, pitch, nnz;
     if (!rd(f, &k, 1) || !rd(f, &n, 1) || !rd(f, &pitch, 1) || !rd(f, &nnz, 1)) return 2;
+    if (k != EMU_K) return 2;
     const int ncls = k == 3 ? 13 : 9364;
     const size_t ncode = (size_t)1 << (k * (k - 1));
     std::vector<uint32_t> st(n * pitch + 1);
@@ -45,25 +44,15 @@ int main(int argc, char **argv) {
     gs.one.pitch = pitch;
     std::vector<unsigned long long> counts(ncls, 0);
     int status = 0;
-    if (k == 3) {
-        run_warps(3, 32, [&] {
-            acc::f3::k_formula3(gs, st.data(), nptr.data(), deg.data(), lo.data(), nbr.data(), lut.data(),
-                                counts.data(), &status);
-        });
-    } else {
-        // the prefix of C(deg, 2) the one-block prefix kernel writes
-        std::vector<long long> pre(n + 1, 0);
-        for (long long v = 0; v < n; v++) pre[v + 1] = pre[v] + (long long)deg[v] * (deg[v] - 1) / 2;
-        run_warps(3, 32, [&] {
-            acc::f5::k_formula5(gs, st.data(), nptr.data(), deg.data(), nbr.data(), lut.data(), pre.data(),
-                                counts.data(), &status);
-        });
-        blockDim.x = 1;
-        gridDim.x = 1;
-        threadIdx.x = 0;
-        blockIdx.x = 0;
-        acc::f5::k_formula5_divide(counts.data(), ncls, cc.data(), &status);
-    }
+#if EMU_K == 3
+    const int rc = acc::launch_formula3(gs, st.data(), nptr.data(), deg.data(), lo.data(), nbr.data(), lut.data(),
+                                        counts.data(), &status, 1, nullptr);
+#else
+    std::vector<long long> pre(n + 1, -1);  // written by the launcher's prefix kernel
+    const int rc = acc::launch_formula5(gs, st.data(), nptr.data(), deg.data(), nbr.data(), lut.data(), cc.data(),
+                                        pre.data(), counts.data(), &status, 1, nullptr);
+#endif
+    if (rc < 0) return 4;
     printf("%d", status);
     for (int i = 0; i < ncls; i++) printf(" %llu", counts[i]);
     printf("\n");

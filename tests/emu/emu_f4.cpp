@@ -1,5 +1,6 @@
-// Runs the k = 4 formula kernels (source extracted from csrc/formula4.cu into
-// f4_kernels.inc) on the host over a G* build given as input: n pitch nnz,
+// Runs the k = 4 formula path (csrc/formula4.cu, kernels and launch_formula4,
+// each launch turned into emu_launch; source in f4_all.inc) on the host over
+// a G* build given as input: n pitch nnz,
 // state[n * pitch], nptr[n + 1], deg[n], lo[n], nbr[nnz], the code -> class
 // table (4096 int16) and the class codes (199 uint32).  Output: status and
 // the 199 counts.
@@ -9,11 +10,7 @@
 thread_local dim threadIdx, blockIdx;
 dim blockDim, gridDim;
 thread_local WarpCtx *tw;
-namespace acc {
-namespace {
-#include "f4_kernels.inc"
-}  // namespace
-}  // namespace acc
+#include "f4_all.inc"
 using acc::GSet;
 using acc::GraphInfo;
 
@@ -43,16 +40,9 @@ int main(int argc, char **argv) {
     info.nnz = nnz;
     std::vector<unsigned long long> counts(199, 0);
     int status = 0;
-    // blocks of one warp: the block-wide shared histogram is the warp's
-    run_warps(4, 32, [&] {
-        acc::k_formula4(gs, st.data(), nptr.data(), deg.data(), lo.data(), nbr.data(), lut.data(), &info,
-                        counts.data(), &status);
-    });
-    blockDim.x = 1;
-    gridDim.x = 1;
-    threadIdx.x = 0;
-    blockIdx.x = 0;
-    acc::k_formula4_divide(counts.data(), 199, cc.data(), &status);
+    const int rc = acc::launch_formula4(gs, st.data(), nptr.data(), deg.data(), lo.data(), nbr.data(), lut.data(),
+                                        cc.data(), &info, counts.data(), &status, 1, nullptr);
+    if (rc < 0) return 4;
     printf("%d", status);
     for (int i = 0; i < 199; i++) printf(" %llu", counts[i]);
     printf("\n");

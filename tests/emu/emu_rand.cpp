@@ -1,17 +1,15 @@
-// Runs the randomiser's kernels (source extracted from csrc/randomise.cu into
-// rand_kernels.inc) on the host.  Input: G R q mode use_bits, then per graph
-// n m seed rowptr[n+1] col[m].  Output: status, the copies, accepted counts.
+// Runs the randomiser (csrc/randomise.cu, kernels and launch_randomise, each
+// launch turned into emu_launch; source in rand_all.inc) on the host.  Input:
+// G R q mode use_bits, then per graph n m seed rowptr[n+1] col[m]; use_bits 0
+// withholds the bitmaps (and the mutual mode's reverse positions), which
+// selects the row-scan kernels.  Output: status, the copies, accepted counts.
 #include "shim.h"
 #include "common.cuh"
 #include "randomise.cuh"
 thread_local dim threadIdx, blockIdx;
 dim blockDim, gridDim;
 thread_local WarpCtx *tw;
-namespace acc {
-namespace {
-#include "rand_kernels.inc"
-}  // namespace
-}  // namespace acc
+#include "rand_all.inc"
 using acc::RGraph;
 
 int main(int argc, char **argv) {
@@ -55,25 +53,10 @@ int main(int argc, char **argv) {
     std::vector<uint32_t> bits(bwords + 64, 0xdeadbeefu);
     std::vector<long long> accepted((size_t)G * R + 1, -1);
     int status = 0;
-    blockDim.x = 1;
-    gridDim.x = 1;
-    threadIdx.x = 0;
-    blockIdx.x = 0;
-    const bool mutual = mode == ACC_RAND_MUTUAL;
-    acc::k_rand_rows(metas.data(), G, M, NV, rows.data(), mutual && use_bits ? rpart.data() : nullptr, &status);
-    const long long items = (long long)G * R;
-    const int blocks = (int)std::max<long long>(1, (items * 32 + 127) / 128);
-    run_warps(blocks, 128, [&] {
-        if (mutual && use_bits)
-            acc::k_rand_swap_spec_mutual(metas.data(), G, R, rows.data(), rpart.data(), out.data(), pts.data(),
-                                         bits.data(), accepted.data(), &status);
-        else if (mutual)
-            acc::k_rand_swap<true>(metas.data(), G, R, rows.data(), out.data(), accepted.data(), &status);
-        else if (use_bits)
-            acc::k_rand_swap_spec(metas.data(), G, R, rows.data(), out.data(), bits.data(), accepted.data(), &status);
-        else
-            acc::k_rand_swap<false>(metas.data(), G, R, rows.data(), out.data(), accepted.data(), &status);
-    });
+    const int rc = acc::launch_randomise(metas.data(), G, R, M, NV, mode, rows.data(), out.data(),
+                                         use_bits ? bits.data() : nullptr, use_bits ? rpart.data() : nullptr,
+                                         use_bits ? pts.data() : nullptr, accepted.data(), &status, 1, nullptr);
+    if (rc < 0) return 4;
     FILE *o = fopen(argv[2], "wb");
     fwrite(&status, 4, 1, o);
     fwrite(out.data(), 4, R * M, o);

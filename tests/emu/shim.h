@@ -101,6 +101,14 @@ inline int __reduce_max_sync(unsigned, int v) {
     wsync();
     return r;
 }
+// IEEE double operations rounded to nearest, as the CUDA names define them;
+// the host's own double arithmetic is that (compiled without contraction)
+inline double __dadd_rn(double a, double b) { return a + b; }
+inline double __dsub_rn(double a, double b) { return a - b; }
+inline double __dmul_rn(double a, double b) { return a * b; }
+inline double __ddiv_rn(double a, double b) { return a / b; }
+inline double __dsqrt_rn(double a) { return std::sqrt(a); }
+inline double __ll2double_rn(long long a) { return (double)a; }
 inline int __ffs(int x) { return x ? __builtin_ctz((unsigned)x) + 1 : 0; }
 inline int __popc(unsigned x) { return __builtin_popcount(x); }
 // position of the offset-th (1-based) set bit of mask at or above base

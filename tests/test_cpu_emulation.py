@@ -11,7 +11,9 @@ queue-full schedules, for single graphs and for sets of graphs) or with the list
 (neighbour-list fill; the whole graph builder, kernels and host launcher,
 against a plain construction of the same pair states, lists and
 renumbering, and on malformed inputs under the address sanitizer; the
-class-table builder against the oracle's table).  The
+class-table builder against the oracle's table; the Z-scores bit for bit).
+The formula paths and the randomiser run through their host launchers, so
+every block runs whole (all its warps at once).  The
 enumeration kernels also run with tiny
 shared-memory lists and histogram drain threshold, so their overflow lists
 and drain run on small graphs.  This checks the kernels' logic and warp
@@ -88,13 +90,11 @@ def emu_bins(tmp_path_factory):
         pytest.skip("g++ not available")
     out = tmp_path_factory.mktemp("emu")
     rand = open(os.path.join(CSRC, "randomise.cu")).read()
-    open(out / "rand_kernels.inc", "w").write(_region(rand, "constexpr int kRandThreads", "}  // namespace\n"))
-    f4 = open(os.path.join(CSRC, "formula4.cu")).read()
-    open(out / "f4_kernels.inc", "w").write(_region(f4, "constexpr int kF4Classes", "}  // namespace\n"))
-    f3 = open(os.path.join(CSRC, "formula3.cu")).read()
-    open(out / "f3_kernels.inc", "w").write(_region(f3, "constexpr int kF3Classes", "}  // namespace\n"))
-    f5 = open(os.path.join(CSRC, "formula5.cu")).read()
-    open(out / "f5_kernels.inc", "w").write(_region(f5, "constexpr int kF5Classes", "}  // namespace\n"))
+    open(out / "rand_all.inc", "w").write(_launches_to_calls(rand.split('#include "randomise.cuh"\n', 1)[1]))
+    # the formula paths whole, kernels and launchers
+    for kk in (3, 4, 5):
+        src = open(os.path.join(CSRC, "formula%d.cu" % kk)).read()
+        open(out / ("f%d_all.inc" % kk), "w").write(_launches_to_calls(src.split('#include "formula.cuh"\n', 1)[1]))
     graph = open(os.path.join(CSRC, "graph.cu")).read()
     open(out / "fill_kernels.inc", "w").write(
         _function(graph, "__device__ __forceinline__ int warp_excl_scan") + "\n" +
@@ -126,17 +126,21 @@ def emu_bins(tmp_path_factory):
         assert common.count(old) == 1, old
         common = common.replace(old, new)
     open(bdir / "common.cuh", "w").write(common)
+    z_src = open(os.path.join(CSRC, "batch.cu")).read().split('#include "common.cuh"\n', 1)[1]
+    open(out / "z_all.inc", "w").write(_launches_to_calls(z_src))
     # the class-table builder (kernels and launch_build_lut)
     lut_src = open(os.path.join(CSRC, "lut.cu")).read().split('#include "common.cuh"\n', 1)[1]
     open(out / "lut_all.inc", "w").write(_launches_to_calls(lut_src.split("// Allocation-free table build.")[0]))
     # (binary, source, extra flags): the enumeration kernels as built, and
     # with tiny shared-memory lists and drain threshold so that the overflow
     # lists and the histogram drain run on small graphs
-    targets = [(n, n, []) for n in ("emu_rand", "emu_f4", "emu_f35", "emu_fill")]
+    targets = [(n, n, []) for n in ("emu_rand", "emu_f4", "emu_fill")]
+    targets += [("emu_f3", "emu_f35", ["-DEMU_K=3"]), ("emu_f5", "emu_f35", ["-DEMU_K=5"])]
     targets += [("emu_enum", "emu_enum", ["-DEMU_DRAIN_AT=(1u<<30)"]),
                 ("emu_enum_small", "emu_enum", ["-DEMU_DRAIN_AT=256u", "-DACC_CAP34=16", "-DACC_CAP5=8"]),
                 ("emu_build", "emu_build", ["-I", str(bdir), "-fsanitize=address"]),
-                ("emu_lut", "emu_lut", ["-O2"])]
+                ("emu_lut", "emu_lut", ["-O2"]),
+                ("emu_z", "emu_z", ["-ffp-contract=off"])]
     procs = []
     for name, src, extra in targets:
         exe = out / name
@@ -266,13 +270,18 @@ def test_k3_k5_formula_kernels_equal_oracle(emu_bins, k):
     if k == 3:
         g = synth.chung_lu(200, 800, 2.1, 40, 20, 6)
         cases.append((g.n, g.src, g.dst))
+    else:
+        # 2500 vertices: the prefix of C(deg, 2) runs over three 1024-vertex
+        # tiles with its carry
+        g = synth.erdos_renyi(2500, 1500, 10, 7)
+        cases.append((g.n, g.src, g.dst))
     cls, cc = oracle.table(k)
     for n, s, d in cases:
         pitch, st, nptr, deg, lo, nbr = _gstar(n, s, d)
         buf = struct.pack("<4q", k, n, pitch, len(nbr)) + st.tobytes() + nptr.astype("<i8").tobytes() + \
             deg.astype("<i4").tobytes() + lo.astype("<i4").tobytes() + nbr.astype("<u4").tobytes() + \
             np.asarray(cls, "<i2").tobytes() + np.asarray(cc, "<u4").tobytes()
-        vals = [int(x) for x in _run(emu_bins["emu_f35"], buf, False, emu_bins["dir"]).split()]
+        vals = [int(x) for x in _run(emu_bins["emu_f%d" % k], buf, False, emu_bins["dir"]).split()]
         assert vals[0] == 0
         assert vals[1:] == oracle.count(n, s, d, k).tolist(), (k, n)
 
@@ -601,3 +610,23 @@ def test_table_builder_equals_oracle_table(emu_bins, k):
     assert np.array_equal(lut, np.asarray(cls, np.int16))
     assert np.array_equal(cc, np.asarray(codes, np.uint32))
     assert np.array_equal(lut_sv, lut[_sv_to_canonical(k)])
+
+
+def test_zscore_kernel_equals_oracle_bitwise(emu_bins):
+    """Z-scores of groups of counts (real graph first, then its copies) from
+    the device kernel's source equal the oracle's bit for bit, NaN where the
+    copies' counts do not vary."""
+    rng = np.random.default_rng(950)
+    groups, size, K = 5, 40, 13
+    counts = rng.integers(0, 1 << 40, size=(groups, size, K), dtype=np.int64)
+    counts[1, :, 3] = 77                       # no spread: NaN
+    counts[2, 1:, 5] = 9                       # no spread among the copies
+    counts[3, :, :] = rng.integers(0, 3, size=(size, K))  # small integers
+    buf = struct.pack("<3q", groups, size, K) + counts.astype("<i8").tobytes()
+    raw = _run(emu_bins["emu_z"], buf, True, emu_bins["dir"])
+    assert struct.unpack("<q", raw[:8])[0] == 1
+    z = np.frombuffer(raw[8:], "<f8").reshape(groups, K)
+    for g in range(groups):
+        want = oracle.zscores(counts[g, 0], counts[g, 1:])
+        assert np.array_equal(z[g], want, equal_nan=True), g  # exact values, NaN in the same places
+    assert np.isnan(z[1, 3]) and np.isnan(z[2, 5])
