@@ -1,10 +1,172 @@
-// Host stand-in for the CUDA runtime header, enough for the library's
-// internal headers and the graph builder's launcher to compile on the host
-// in the kernel emulation tests.
+// Host stand-in for the CUDA runtime, enough for the library's sources to
+// compile and run on the host in the kernel emulation tests.  "Device"
+// memory is host memory; every stream runs its work at once, in order,
+// except while it is being captured, when kernel launches, copies, memsets
+// and event records are kept (by value, as a launch keeps its arguments)
+// and a launch of the graph made from them runs them in the same order.
+// Events read the host clock.
 #pragma once
-typedef void *cudaStream_t;
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <vector>
+
 typedef int cudaError_t;
 #define cudaSuccess 0
-inline cudaError_t cudaGetLastError() { return cudaSuccess; }
+#define cudaErrorNotReady 600
+#define cudaErrorInvalidValue 1
+
+struct EmuStream {
+    bool capturing = false;
+    std::vector<std::function<void()>> rec;
+};
+typedef EmuStream *cudaStream_t;
+struct EmuEvent {
+    double t = 0.0;
+};
+typedef EmuEvent *cudaEvent_t;
+struct EmuGraph {
+    std::vector<std::function<void()>> ops;
+};
+typedef EmuGraph *cudaGraph_t;
+typedef EmuGraph *cudaGraphExec_t;
+
+enum cudaMemcpyKind { cudaMemcpyHostToHost, cudaMemcpyHostToDevice, cudaMemcpyDeviceToHost, cudaMemcpyDeviceToDevice,
+                      cudaMemcpyDefault };
+enum cudaStreamCaptureMode { cudaStreamCaptureModeGlobal, cudaStreamCaptureModeThreadLocal,
+                             cudaStreamCaptureModeRelaxed };
+enum cudaDeviceAttr { cudaDevAttrMultiProcessorCount = 16 };
 enum cudaFuncAttribute { cudaFuncAttributeMaxDynamicSharedMemorySize = 8 };
+#define cudaStreamNonBlocking 1
+#define cudaEventDisableTiming 2
+
+// streaming multiprocessors the emulated device reports
+#ifndef EMU_NUM_SMS
+#define EMU_NUM_SMS 2
+#endif
+
+// run op now, or keep it when s is being captured
+inline void emu_submit(cudaStream_t s, std::function<void()> op) {
+    if (s && s->capturing) s->rec.push_back(std::move(op));
+    else op();
+}
+
+inline cudaError_t cudaGetLastError() { return cudaSuccess; }
+inline const char *cudaGetErrorString(cudaError_t) { return "emulated"; }
 template <class T> inline cudaError_t cudaFuncSetAttribute(T, cudaFuncAttribute, int) { return cudaSuccess; }
+template <class T> inline cudaError_t cudaOccupancyMaxActiveBlocksPerMultiprocessor(int *b, T, int, size_t) {
+    *b = 1;
+    return cudaSuccess;
+}
+inline cudaError_t cudaSetDevice(int d) { return d == 0 ? cudaSuccess : cudaErrorInvalidValue; }
+inline cudaError_t cudaGetDevice(int *d) {
+    *d = 0;
+    return cudaSuccess;
+}
+inline cudaError_t cudaDeviceGetAttribute(int *v, cudaDeviceAttr, int) {
+    *v = EMU_NUM_SMS;
+    return cudaSuccess;
+}
+inline cudaError_t cudaDeviceSynchronize() { return cudaSuccess; }
+inline cudaError_t cudaMemGetInfo(size_t *free_b, size_t *total_b) {
+    *free_b = size_t(8) << 30;
+    *total_b = size_t(16) << 30;
+    return cudaSuccess;
+}
+
+template <class T> inline cudaError_t cudaMalloc(T **p, size_t bytes) {
+    *p = static_cast<T *>(std::aligned_alloc(256, (bytes + 255) / 256 * 256 + 256));
+    return *p ? cudaSuccess : 2;
+}
+inline cudaError_t cudaFree(void *p) {
+    std::free(p);
+    return cudaSuccess;
+}
+template <class T> inline cudaError_t cudaMallocHost(T **p, size_t bytes) { return cudaMalloc(p, bytes); }
+inline cudaError_t cudaFreeHost(void *p) { return cudaFree(p); }
+template <class T> inline cudaError_t cudaGetSymbolAddress(void **p, T &sym) {
+    *p = static_cast<void *>(&sym);
+    return cudaSuccess;
+}
+
+inline cudaError_t cudaMemcpy(void *d, const void *s, size_t n, cudaMemcpyKind) {
+    if (n) std::memmove(d, s, n);
+    return cudaSuccess;
+}
+inline cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, cudaMemcpyKind, cudaStream_t st) {
+    emu_submit(st, [=] {
+        if (n) std::memmove(d, s, n);
+    });
+    return cudaSuccess;
+}
+inline cudaError_t cudaMemset(void *p, int v, size_t n) {
+    std::memset(p, v, n);
+    return cudaSuccess;
+}
+inline cudaError_t cudaMemsetAsync(void *p, int v, size_t n, cudaStream_t st) {
+    emu_submit(st, [=] { std::memset(p, v, n); });
+    return cudaSuccess;
+}
+
+inline cudaError_t cudaStreamCreateWithFlags(cudaStream_t *s, unsigned) {
+    *s = new EmuStream;
+    return cudaSuccess;
+}
+inline cudaError_t cudaStreamDestroy(cudaStream_t s) {
+    delete s;
+    return cudaSuccess;
+}
+inline cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
+inline cudaError_t cudaStreamBeginCapture(cudaStream_t s, cudaStreamCaptureMode) {
+    if (!s || s->capturing) return cudaErrorInvalidValue;
+    s->capturing = true;
+    s->rec.clear();
+    return cudaSuccess;
+}
+inline cudaError_t cudaStreamEndCapture(cudaStream_t s, cudaGraph_t *g) {
+    if (!s || !s->capturing) return cudaErrorInvalidValue;
+    s->capturing = false;
+    *g = new EmuGraph{std::move(s->rec)};
+    s->rec.clear();
+    return cudaSuccess;
+}
+inline cudaError_t cudaGraphInstantiate(cudaGraphExec_t *e, cudaGraph_t g, unsigned long long) {
+    *e = new EmuGraph(*g);
+    return cudaSuccess;
+}
+inline cudaError_t cudaGraphLaunch(cudaGraphExec_t e, cudaStream_t s) {
+    for (auto &op : e->ops) emu_submit(s, op);
+    return cudaSuccess;
+}
+inline cudaError_t cudaGraphDestroy(cudaGraph_t g) {
+    delete g;
+    return cudaSuccess;
+}
+inline cudaError_t cudaGraphExecDestroy(cudaGraphExec_t e) {
+    delete e;
+    return cudaSuccess;
+}
+
+inline double emu_now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+inline cudaError_t cudaEventCreate(cudaEvent_t *e) {
+    *e = new EmuEvent;
+    return cudaSuccess;
+}
+inline cudaError_t cudaEventCreateWithFlags(cudaEvent_t *e, unsigned) { return cudaEventCreate(e); }
+inline cudaError_t cudaEventDestroy(cudaEvent_t e) {
+    delete e;
+    return cudaSuccess;
+}
+inline cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t s) {
+    emu_submit(s, [=] { e->t = emu_now_ms(); });
+    return cudaSuccess;
+}
+inline cudaError_t cudaEventQuery(cudaEvent_t) { return cudaSuccess; }
+inline cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
+inline cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t a, cudaEvent_t b) {
+    *ms = (float)(b->t - a->t);
+    return cudaSuccess;
+}

@@ -1,32 +1,31 @@
 // CPU stand-ins for the CUDA constructs the library's kernels use, so that a
-// kernel's own source can run on the host: one host thread per lane (from a
-// pool of persistent threads), every
-// warp collective (shuffles, ballot, match, reduce, __syncwarp) a barrier of
-// the 32 lane threads, and atomics on std::atomic_ref.  A lane that skips a
-// collective its warp reaches leaves the others waiting at the barrier,
-// which the driver reports as a hang.  Shared arrays are static: one block
-// runs at a time, either one warp after another (run_warps, for kernels
-// whose blocks never synchronise across warps) or all its threads at once
-// (run_blocks / emu_launch, where __syncthreads is a barrier of the block's
-// threads and a thread that returns leaves it, as an exited GPU thread no
-// longer holds a block barrier back).
+// kernel's own source can run on the host.  Every GPU thread is a fiber
+// (ucontext) on the calling host thread; every warp collective (shuffles,
+// ballot, match, reduce, __syncwarp) is a barrier of the warp's 32 lanes and
+// __syncthreads one of the block's threads, and a fiber runs until it
+// reaches a barrier or returns, so lanes interleave only at collectives (a
+// valid GPU schedule, the same on every run).  A lane that skips a
+// collective its warp reaches leaves the others waiting with nothing left
+// to run, which is reported as a hang at once.  A thread that returns
+// leaves its block's barrier, as an exited GPU thread no longer holds
+// __syncthreads back.  Blocks run one at a time, either as one warp after
+// another (run_warps, for kernels whose blocks never synchronise across
+// warps) or whole (run_blocks / emu_launch); shared arrays are static.
 #pragma once
 #include <algorithm>
 #include <atomic>
-#include <barrier>
 #include <chrono>
 #include <cmath>
-#include <condition_variable>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <memory>
-#include <mutex>
-#include <semaphore>
-#include <thread>
+#include <ucontext.h>
 #include <vector>
+
+#include <cuda_runtime.h>  // the host stand-in (streams, capture)
 
 #define __global__
 #define __device__
@@ -35,6 +34,7 @@
 #define __restrict__
 #define __launch_bounds__(...)
 #define __shared__ static
+#define __align__(n) __attribute__((aligned(n)))
 using std::max;
 using std::min;
 
@@ -45,18 +45,122 @@ inline uint4 make_uint4(unsigned a, unsigned b, unsigned c, unsigned d) { return
 struct dim { unsigned x; };
 extern thread_local dim threadIdx, blockIdx;
 extern dim blockDim, gridDim;
-struct WarpCtx { std::barrier<> *bar; uint64_t slot[32]; };
+// A barrier of a fixed group of lanes: a warp, or a block's threads.
+struct Bar {
+    int expected = 0, arrived = 0;
+};
+struct WarpCtx {
+    Bar *bar;
+    uint64_t slot[32];
+};
 extern thread_local WarpCtx *tw;
-// the block barrier of the running thread (null under run_warps)
-inline thread_local std::barrier<> *tblk = nullptr;
+// the block barrier of the running lane (null under run_warps)
+inline thread_local Bar *tblk = nullptr;
+
+// One GPU thread: its fiber, ids and barriers, and what it waits on.
+struct Lane {
+    ucontext_t ctx;
+    int tid = 0, bid = 0;
+    WarpCtx *warp = nullptr;
+    Bar *block = nullptr;
+    int state = 0;  // 0 runnable, 1 waiting at wbar, 2 returned
+    Bar *wbar = nullptr;
+};
+struct FiberSched {
+    ucontext_t main;
+    std::vector<Lane> lanes;
+    std::vector<std::unique_ptr<char[]>> stacks;
+    int cur = -1;
+    std::function<void()> *job = nullptr;
+};
+inline FiberSched &fsched() {
+    static FiberSched s;
+    return s;
+}
+constexpr size_t kLaneStack = 256 * 1024;
+
+inline void bar_release(Bar *b) {
+    b->arrived = 0;
+    for (auto &l : fsched().lanes)
+        if (l.state == 1 && l.wbar == b) {
+            l.state = 0;
+            l.wbar = nullptr;
+        }
+}
+inline void bar_wait(Bar *b) {
+    FiberSched &s = fsched();
+    if (++b->arrived >= b->expected) {
+        bar_release(b);
+        return;
+    }
+    Lane &l = s.lanes[s.cur];
+    l.state = 1;
+    l.wbar = b;
+    swapcontext(&l.ctx, &s.main);
+}
+// a lane that returns leaves the group
+inline void bar_drop(Bar *b) {
+    b->expected--;
+    if (b->arrived > 0 && b->arrived >= b->expected) bar_release(b);
+}
+inline void lane_entry() {
+    FiberSched &s = fsched();
+    (*s.job)();
+    Lane &l = s.lanes[s.cur];
+    if (l.block) bar_drop(l.block);
+    l.state = 2;  // returning resumes the scheduler (uc_link)
+}
+// Run job() once on each of n lanes set up by init(lane, i), switching to a
+// lane only when the one running waits or returns; false when lanes are
+// left waiting with none runnable (a collective some lane never reaches).
+template <class Init> bool run_lanes(int n, std::function<void()> job, Init init) {
+    FiberSched &s = fsched();
+    while ((int)s.stacks.size() < n) s.stacks.emplace_back(new char[kLaneStack]);
+    s.lanes.assign(n, Lane{});
+    s.job = &job;
+    for (int i = 0; i < n; i++) {
+        Lane &l = s.lanes[i];
+        init(l, i);
+        getcontext(&l.ctx);
+        l.ctx.uc_stack.ss_sp = s.stacks[i].get();
+        l.ctx.uc_stack.ss_size = kLaneStack;
+        l.ctx.uc_link = &s.main;
+        makecontext(&l.ctx, lane_entry, 0);
+    }
+    bool ok = true;
+    for (;;) {
+        bool ran = false, left = false;
+        for (int i = 0; i < n; i++) {
+            Lane &l = s.lanes[i];
+            if (l.state == 2) continue;
+            left = true;
+            if (l.state != 0) continue;
+            s.cur = i;
+            threadIdx.x = l.tid;
+            blockIdx.x = l.bid;
+            tw = l.warp;
+            tblk = l.block;
+            swapcontext(&s.main, &l.ctx);
+            ran = true;
+        }
+        if (!left) break;
+        if (!ran) {
+            ok = false;
+            break;
+        }
+    }
+    s.cur = -1;
+    tblk = nullptr;
+    return ok;
+}
 
 template <class T> inline T __ldg(const T *p) { return *p; }
 inline uint64_t __umul64hi(uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128)a * b) >> 64); }
 inline int lane_() { return threadIdx.x & 31; }
-inline void wsync() { tw->bar->arrive_and_wait(); }
+inline void wsync() { bar_wait(tw->bar); }
 inline void __syncwarp(unsigned = 0xffffffffu) { wsync(); }
 inline void __syncthreads() {
-    if (tblk) tblk->arrive_and_wait();
+    if (tblk) bar_wait(tblk);
     else wsync();
 }
 template <class T> inline T exch(T v, int src) {
@@ -140,66 +244,22 @@ inline int atomicCAS(int *p, int c, int v) {
     return c;
 }
 
-// Persistent host threads that play the lanes: run(n, job) has threads
-// 0..n-1 call job(i) once each and waits for them; false when they have not
-// all returned within the limit (a lane left a collective).  Threads are
-// created once and reused, so a launch costs no thread creation.
-struct LanePool {
-    struct Worker {
-        std::binary_semaphore go{0};
-    };
-    std::vector<std::unique_ptr<Worker>> ws;
-    std::function<void(int)> job;
-    std::mutex m;
-    std::condition_variable fin;
-    int remaining = 0;
-    void loop(Worker *w, int id) {
-        for (;;) {
-            w->go.acquire();  // only the threads a run needs are woken
-            job(id);
-            std::lock_guard<std::mutex> lk(m);
-            if (--remaining == 0) fin.notify_all();
-        }
-    }
-    bool run(int n, std::function<void(int)> j, int limit_s) {
-        while ((int)ws.size() < n) {
-            ws.emplace_back(new Worker);
-            Worker *w = ws.back().get();
-            const int id = (int)ws.size() - 1;
-            std::thread([this, w, id] { loop(w, id); }).detach();
-        }
-        job = std::move(j);
-        {
-            std::lock_guard<std::mutex> lk(m);
-            remaining = n;
-        }
-        for (int i = 0; i < n; i++) ws[i]->go.release();
-        std::unique_lock<std::mutex> lk(m);
-        return fin.wait_for(lk, std::chrono::seconds(limit_s), [&] { return remaining == 0; });
-    }
-};
-inline LanePool *lane_pool() {
-    static LanePool *p = new LanePool;  // never destroyed: its threads outlive main
-    return p;
-}
-
 // Run f() as blocks x (threads / 32) warps, one warp at a time; exits the
-// process when a warp does not finish within the limit.
-template <class F> bool run_warps(int blocks, int threads, F f, int limit_s = 120) {
+// process when a warp's lanes wait at a collective some lane never reaches.
+template <class F> bool run_warps(int blocks, int threads, F f) {
     blockDim.x = threads;
     gridDim.x = blocks;
     for (int b = 0; b < blocks; b++)
         for (int w = 0; w < threads / 32; w++) {
-            std::barrier<> bar(32);
-            WarpCtx ctx;
+            Bar bar;
+            bar.expected = 32;
+            WarpCtx ctx{};
             ctx.bar = &bar;
-            const bool ok = lane_pool()->run(32, [&](int l) {
-                threadIdx.x = w * 32 + l;
-                blockIdx.x = b;
-                tw = &ctx;
-                tblk = nullptr;
-                f();
-            }, limit_s);
+            const bool ok = run_lanes(32, [&] { f(); }, [&](Lane &l, int i) {
+                l.tid = w * 32 + i;
+                l.bid = b;
+                l.warp = &ctx;
+            });
             if (!ok) {
                 fprintf(stderr, "warp %d of block %d did not finish\n", w, b);
                 std::_Exit(3);
@@ -209,29 +269,27 @@ template <class F> bool run_warps(int blocks, int threads, F f, int limit_s = 12
 }
 
 // Run f() as `blocks` blocks of `threads` threads, one block at a time, all
-// threads of a block at once; exits the process when a block does not
-// finish within the limit.
-template <class F> bool run_blocks(int blocks, int threads, F f, int limit_s = 120) {
+// threads of a block together; exits the process on a hang as above.
+template <class F> bool run_blocks(int blocks, int threads, F f) {
     blockDim.x = threads;
     gridDim.x = blocks;
     const int nw = (threads + 31) / 32;
+    std::vector<Bar> wbar(nw);
+    std::vector<WarpCtx> ctx(nw);
     for (int b = 0; b < blocks; b++) {
-        std::barrier<> block_bar(threads);
-        std::vector<std::unique_ptr<std::barrier<>>> wbar;
-        std::vector<WarpCtx> ctx(nw);
+        Bar block_bar;
+        block_bar.expected = threads;
         for (int w = 0; w < nw; w++) {
-            wbar.emplace_back(new std::barrier<>(std::min(32, threads - 32 * w)));
-            ctx[w].bar = wbar.back().get();
+            wbar[w] = Bar{};
+            wbar[w].expected = std::min(32, threads - 32 * w);
+            ctx[w].bar = &wbar[w];
         }
-        const bool ok = lane_pool()->run(threads, [&](int t) {
-            threadIdx.x = t;
-            blockIdx.x = b;
-            tw = &ctx[t / 32];
-            tblk = &block_bar;
-            f();
-            block_bar.arrive_and_drop();
-            tblk = nullptr;
-        }, limit_s);
+        const bool ok = run_lanes(threads, [&] { f(); }, [&](Lane &l, int t) {
+            l.tid = t;
+            l.bid = b;
+            l.warp = &ctx[t / 32];
+            l.block = &block_bar;
+        });
         if (!ok) {
             fprintf(stderr, "block %d did not finish\n", b);
             std::_Exit(3);
@@ -240,12 +298,15 @@ template <class F> bool run_blocks(int blocks, int threads, F f, int limit_s = 1
     return true;
 }
 
-// Stand-in for a kernel launch <<<grid, block, dynamic smem, stream>>>: the
-// dynamic shared memory is emu_dyn_smem (zeroed, at least `smem` bytes).
+// Stand-in for a kernel launch <<<grid, block, dynamic smem, stream>>> (kept
+// by value while the stream is being captured): the dynamic shared memory is
+// emu_dyn_smem (zeroed, at least `smem` bytes).
 inline std::vector<uint64_t> emu_dyn_buf;
 inline unsigned char *emu_dyn_smem = nullptr;
-template <class F> void emu_launch(long long grid, long long block, size_t smem, void *, F f) {
-    emu_dyn_buf.assign(smem / 8 + 2, 0);
-    emu_dyn_smem = reinterpret_cast<unsigned char *>(emu_dyn_buf.data());
-    run_blocks((int)grid, (int)block, f);
+template <class F> void emu_launch(long long grid, long long block, size_t smem, cudaStream_t s, F f) {
+    emu_submit(s, [=] {
+        emu_dyn_buf.assign(smem / 8 + 2, 0);
+        emu_dyn_smem = reinterpret_cast<unsigned char *>(emu_dyn_buf.data());
+        run_blocks((int)grid, (int)block, f);
+    });
 }

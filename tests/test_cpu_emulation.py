@@ -1,9 +1,10 @@
 """The library's own kernel source, run on the CPU.
 
-tests/emu/shim.h stands in for the CUDA constructs the kernels use: a thread
-per lane and a 32-thread barrier for every warp collective, so a lane that
-skips a collective its warp reaches hangs the warp and the driver reports
-it.  The kernels' code is cut from the CUDA sources between fixed anchors
+tests/emu/shim.h stands in for the CUDA constructs the kernels use: a fiber
+per GPU thread and a barrier of the warp's 32 lanes for every warp
+collective (of the block's threads for __syncthreads), so a lane that skips
+a collective its warp reaches leaves the warp waiting, which the shim
+reports as a hang.  The kernels' code is cut from the CUDA sources between fixed anchors
 and compiled with g++ together with the library's own internal headers; the
 results are compared with the oracle (copies, k = 3, 4, 5 formula counts,
 k = 3, 4, 5 enumeration counts in both modes, under light, heavy and
@@ -19,6 +20,7 @@ shared-memory lists and histogram drain threshold, so their overflow lists
 and drain run on small graphs.  This checks the kernels' logic and warp
 discipline without a GPU; the GPU tests check the compiled kernels."""
 import os
+import re
 import shutil
 import struct
 import subprocess
@@ -73,13 +75,12 @@ def _launches_to_calls(src):
             c += 1
         assert src[c] == ";", src[a:c + 1]
         out.append(src[i:name_start])
-        out.append("emu_launch(%s, [&] { %s(%s); })" % (src[a + 3:b], src[name_start:a], src[b + 4:c - 1]))
+        out.append("emu_launch(%s, [=] { %s(%s); })" % (src[a + 3:b], src[name_start:a], src[b + 4:c - 1]))
         i = c
     out.append(src[i:])
     src = "".join(out)
-    for name in ("deg", "h"):
-        old = "extern __shared__ int %s[];" % name
-        src = src.replace(old, "int *%s = reinterpret_cast<int *>(emu_dyn_smem);" % name)
+    src = re.sub(r"extern __shared__ (?:__align__\(\d+\) )?([\w ]+?) (\w+)\[\];",
+                 r"\1 *\2 = reinterpret_cast<\1 *>(emu_dyn_smem);", src)
     assert "extern __shared__" not in src
     return src
 
