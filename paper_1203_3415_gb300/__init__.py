@@ -51,7 +51,12 @@ def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is not built: run paper_1203_3415_gb300.build.build() "
                           f"(the counter has no CPU fallback)")
-    lib = ctypes.CDLL(LIB_PATH)
+    return declare(ctypes.CDLL(LIB_PATH))
+
+
+def declare(lib):
+    """Set the argument and result types of every entry point of the C ABI
+    on a loaded library handle; returns it."""
     vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     lib.acc_strerror.argtypes = [ctypes.c_int]
     lib.acc_strerror.restype = ctypes.c_char_p

@@ -135,7 +135,9 @@ inline cudaError_t cudaGraphInstantiate(cudaGraphExec_t *e, cudaGraph_t g, unsig
     *e = new EmuGraph(*g);
     return cudaSuccess;
 }
+inline long long emu_graph_launches = 0;  // graphs launched so far (read by the tests)
 inline cudaError_t cudaGraphLaunch(cudaGraphExec_t e, cudaStream_t s) {
+    emu_graph_launches++;
     for (auto &op : e->ops) emu_submit(s, op);
     return cudaSuccess;
 }

@@ -1,0 +1,350 @@
+"""Scenarios run against the whole library built for the host (every CUDA
+source compiled with the shim and the stand-in runtime, where device memory
+is host memory), through the C ABI with the Python binding's own signature
+table.  Run as a child process, one scenario per call:
+
+    python tests/emu/lib_scenarios.py <library.so> <scenario>
+
+Each scenario compares what the library returns with the oracle and raises
+on the first difference; exit status 0 means it passed.  Buffers the ABI
+calls device buffers are numpy arrays here."""
+import ctypes
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+import paper_1203_3415_gb300 as acc  # noqa: E402  (constants and the signature table only)
+import synth  # noqa: E402
+from tests.graph_helpers import random_digraph  # noqa: E402
+
+NCLS = {3: 13, 4: 199, 5: 9364}
+
+
+def P(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def csr(n, s, d):
+    s, d = np.asarray(s, np.int64), np.asarray(d, np.int64)
+    order = np.lexsort((d, s))
+    col = np.ascontiguousarray(d[order], dtype=np.int32)
+    rowptr = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(s, minlength=n), out=rowptr[1:])
+    return rowptr, col
+
+
+def ok(rc, what):
+    if rc != 0:
+        raise AssertionError(f"{what}: returned {rc}")
+
+
+class Ctx:
+    def __init__(self, lib):
+        self.lib = lib
+        self.h = ctypes.c_void_p()
+        self.bufs = {}
+        ok(lib.acc_ctx_create(ctypes.byref(self.h), 0), "acc_ctx_create")
+
+    def count(self, rowptr, col, n, k):
+        # the same output buffers every call, as a caller repeating a count
+        # does (the launch-graph replay recognises a repeat by its pointers)
+        out, st = self.bufs.setdefault(k, (np.zeros(NCLS[k], np.int64), np.zeros(1, np.int32)))
+        out[:] = -1
+        st[:] = -1
+        rc = self.lib.acc_motif_count(self.h, P(rowptr), P(col), n, len(col), k, None, P(out), P(st))
+        return rc, int(st[0]), out.copy()
+
+    def stats(self):
+        s = np.zeros(acc.ACC_STATS_LEN, np.int64)
+        ok(self.lib.acc_motif_last_stats(self.h, P(s)), "acc_motif_last_stats")
+        return s
+
+    def close(self):
+        self.lib.acc_ctx_destroy(self.h)
+
+
+def graphs(seed, count, nmax):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(rng.integers(3, nmax))
+        s, d = random_digraph(rng, n, p=float(rng.uniform(0.1, 0.4)), recip=float(rng.random()))
+        out.append((n, np.asarray(s, np.int64), np.asarray(d, np.int64)))
+    return out
+
+
+def scenario_modes(lib):
+    """Every k in every counting mode, on several graphs, on one context."""
+    c = Ctx(lib)
+    cases = {3: graphs(1, 3, 40), 4: graphs(2, 3, 22), 5: graphs(3, 2, 12)}
+    g = synth.chung_lu(60, 200, 2.1, 30, 20, 4)
+    cases[4].append((g.n, g.src, g.dst))
+    for mode in (acc.ACC_MODE_COUNT, acc.ACC_MODE_ENUMERATE, acc.ACC_MODE_FORMULA):
+        ok(lib.acc_ctx_set_mode(c.h, mode), "acc_ctx_set_mode")
+        for k, gs in cases.items():
+            for n, s, d in gs:
+                rp, cl = csr(n, s, d)
+                rc, st, got = c.count(rp, cl, n, k)
+                want = oracle.count(n, s, d, k)
+                if rc or st or got.tolist() != want.tolist():
+                    raise AssertionError(f"mode {mode} k {k} n {n}: rc {rc} status {st}")
+    c.close()
+
+
+def scenario_repeats(lib):
+    """Repeated counts replay one captured launch sequence: the same counts
+    as launching one by one, also when the buffers' contents change, after a
+    malformed repeat, and with launch graphs switched off."""
+    replays = lib.emu_graph_launch_count
+    replays.restype = ctypes.c_longlong
+    c = Ctx(lib)
+    # 1200 vertices: renumbered, so the sequence is 9 kernels
+    g = synth.chung_lu(1200, 2400, 2.2, 60, 20, 5)
+    rp, cl = csr(g.n, g.src, g.dst)
+    want = oracle.count(g.n, g.src, g.dst, 3).tolist()
+    for i in range(4):
+        rc, st, got = c.count(rp, cl, g.n, 3)
+        if rc or st or got.tolist() != want or c.stats()[0] != 9:
+            raise AssertionError(f"repeat {i}: rc {rc} status {st} launches {c.stats()[0]}")
+    # a fresh context's first count leaves the pair-state buffer clean, the
+    # second is remembered, the third is captured and launched, the fourth
+    # replayed
+    if replays() != 2:
+        raise AssertionError(f"{replays()} graph launches for 4 counts")
+    # 120 vertices (7 kernels: no renumbering), k = 4
+    g = synth.chung_lu(120, 400, 2.1, 40, 20, 5)
+    rp, cl = csr(g.n, g.src, g.dst)
+    want = oracle.count(g.n, g.src, g.dst, 4).tolist()
+    for i in range(3):
+        rc, st, got = c.count(rp, cl, g.n, 4)
+        if rc or st or got.tolist() != want or c.stats()[0] != 7:
+            raise AssertionError(f"k = 4 repeat {i}")
+    # new arcs in the same buffers (same n and m)
+    for seed in (11, 12):
+        h = synth.erdos_renyi(g.n, len(cl), 10, seed)
+        r2, c2 = csr(g.n, h.src, h.dst)
+        rp[:] = r2
+        cl[:] = c2
+        rc, st, got = c.count(rp, cl, g.n, 4)
+        if rc or st or got.tolist() != oracle.count(g.n, h.src, h.dst, 4).tolist():
+            raise AssertionError(f"contents changed, seed {seed}")
+    keep = int(cl[0])
+    cl[0] = 0  # row 0's first arc becomes a self-loop
+    rc, st, _ = c.count(rp, cl, g.n, 4)
+    if rc != 0 or st != acc.ACC_ERR_INPUT:
+        raise AssertionError(f"malformed repeat: rc {rc} status {st}")
+    cl[0] = keep
+    want = oracle.count(g.n, np.repeat(np.arange(g.n), np.diff(rp)), cl.astype(np.int64), 4).tolist()
+    for i in range(2):
+        rc, st, got = c.count(rp, cl, g.n, 4)
+        if rc or st or got.tolist() != want:
+            raise AssertionError(f"recovery {i}")
+    before = replays()
+    if before != 2 + 7:
+        raise AssertionError(f"k = 4 repeats replayed {before - 2} times")
+    ok(lib.acc_ctx_set_launch_graphs(c.h, 0), "acc_ctx_set_launch_graphs")
+    for i in range(2):
+        rc, st, got = c.count(rp, cl, g.n, 4)
+        if rc or st or got.tolist() != want:
+            raise AssertionError("launch graphs off")
+    if replays() != before:
+        raise AssertionError("a graph replayed with launch graphs off")
+    c.close()
+
+
+def scenario_host_and_errors(lib):
+    """The host-buffer entry point, the synchronous status (NULL status
+    pointer), and the host-checked argument errors."""
+    c = Ctx(lib)
+    n, s, d = graphs(6, 1, 30)[0]
+    rp, cl = csr(n, s, d)
+    for k in (3, 4):
+        out = np.zeros(NCLS[k], np.int64)
+        ok(lib.acc_motif_count_host(c.h, P(rp), P(cl), n, len(cl), k, P(out)), "count_host")
+        if out.tolist() != oracle.count(n, s, d, k).tolist():
+            raise AssertionError(f"count_host k {k}")
+    bad = cl.copy()
+    bad[0] = n  # target out of range
+    out = np.zeros(13, np.int64)
+    rc = lib.acc_motif_count(c.h, P(rp), P(bad), n, len(bad), 3, None, P(out), None)
+    if rc != acc.ACC_ERR_INPUT:
+        raise AssertionError(f"synchronous status: {rc}")
+    if lib.acc_motif_count(c.h, P(rp), P(cl), n, len(cl), 6, None, P(out), None) != acc.ACC_ERR_K:
+        raise AssertionError("k = 6 accepted")
+    if lib.acc_motif_count(c.h, None, P(cl), n, len(cl), 3, None, P(out), None) != acc.ACC_ERR_ARG:
+        raise AssertionError("null rowptr accepted")
+    if lib.acc_motif_count(c.h, P(rp), P(cl), acc.ACC_MAX_N + 1, len(cl), 3, None, P(out), None) != \
+            acc.ACC_ERR_TOO_LARGE:
+        raise AssertionError("n above the limit accepted")
+    # an empty graph counts nothing
+    e_rp = np.zeros(5, np.int64)
+    rc = lib.acc_motif_count(c.h, P(e_rp), P(np.zeros(1, np.int32)), 4, 0, 3, None, P(out), None)
+    if rc or out.any():
+        raise AssertionError("empty graph")
+    c.close()
+
+
+def _descs(gs):
+    arrays = [csr(n, s, d) for n, s, d in gs]
+    descs = (acc.acc_graph_desc * len(gs))() if hasattr(acc, "acc_graph_desc") else None
+    if descs is None:
+        class Desc(ctypes.Structure):
+            _fields_ = [("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("n", ctypes.c_int32),
+                        ("m", ctypes.c_int64)]
+        descs = (Desc * len(gs))()
+    for i, ((n, _, _), (rp, cl)) in enumerate(zip(gs, arrays)):
+        descs[i].rowptr = rp.ctypes.data
+        descs[i].col = cl.ctypes.data
+        descs[i].n = n
+        descs[i].m = len(cl)
+    return descs, arrays
+
+
+def scenario_batch(lib):
+    """A batch of graphs prepared once and run several times, then the
+    autotuner, for k = 3, 4 and 5."""
+    c = Ctx(lib)
+    for k, nmax in ((3, 30), (4, 18), (5, 10)):
+        gs = graphs(20 + k, 6, nmax)
+        gs.insert(2, (5, np.zeros(0, np.int64), np.zeros(0, np.int64)))
+        descs, keep = _descs(gs)
+        ok(lib.acc_motif_batch_prepare(c.h, descs, len(gs), k, None), "batch_prepare")
+        want = [oracle.count(n, s, d, k).tolist() for n, s, d in gs]
+        for rep in range(2):
+            out = np.full(len(gs) * NCLS[k], -1, np.int64)
+            st = np.full(1, -1, np.int32)
+            ok(lib.acc_motif_batch_run(c.h, None, P(out), P(st)), "batch_run")
+            if st[0] != 0 or out.reshape(len(gs), -1).tolist() != want:
+                raise AssertionError(f"batch k {k} rep {rep}")
+        if k == 4:
+            light, target = ctypes.c_int64(), ctypes.c_int64()
+            ms = ctypes.c_float()
+            ok(lib.acc_motif_batch_autotune(c.h, None, ctypes.byref(light), ctypes.byref(target), ctypes.byref(ms)),
+               "autotune")
+            out = np.full(len(gs) * NCLS[k], -1, np.int64)
+            ok(lib.acc_motif_batch_run(c.h, None, P(out), None), "batch_run after autotune")
+            if out.reshape(len(gs), -1).tolist() != want:
+                raise AssertionError("batch after autotune")
+        out = np.full(len(gs) * NCLS[k], -1, np.int64)
+        ok(lib.acc_motif_count_batch(c.h, descs, len(gs), k, None, P(out), None), "count_batch")
+        if out.reshape(len(gs), -1).tolist() != want:
+            raise AssertionError(f"count_batch k {k}")
+    c.close()
+
+
+def scenario_significance(lib):
+    """Device randomisation (both modes, speculative and row-scanning) then
+    counting the copies and Z-scores, against the oracle's copies, counts
+    and Z-scores."""
+    c = Ctx(lib)
+    gs = graphs(30, 3, 16)
+    descs, arrays = _descs(gs)
+    R, q = 3, 2
+    seeds = np.array([5, 6, 7], np.uint64)
+    M = sum(len(cl) for _, cl in arrays)
+    for mode in (acc.ACC_RAND_SWAP, acc.ACC_RAND_MUTUAL):
+        for mem in (1 << 30, 0):
+            ok(lib.acc_ctx_set_randomise_memory(c.h, mem), "set_randomise_memory")
+            out = np.full(R * M, -1, np.int32)
+            accepted = np.full(len(gs) * R, -1, np.int64)
+            st = np.full(1, -1, np.int32)
+            ok(lib.acc_swap_randomise(c.h, descs, len(gs), R, q, P(seeds), mode, None, P(out), P(accepted), P(st)),
+               "swap_randomise")
+            if st[0] != 0:
+                raise AssertionError(f"randomise status {st[0]}")
+            off = 0
+            for g, ((n, _, _), (rp, cl)) in enumerate(zip(gs, arrays)):
+                m = len(cl)
+                for r in range(R):
+                    want, wa = oracle.swap_randomise(n, rp, cl, q * m, int(seeds[g]) + r, mode)
+                    if not np.array_equal(out[off + r * m: off + (r + 1) * m], want) or accepted[g * R + r] != wa:
+                        raise AssertionError(f"copy mode {mode} mem {mem} graph {g} copy {r}")
+                off += R * m
+    # count the real graph and its copies as one batch, then Z-scores
+    k = 3
+    g0, (rp0, cl0) = gs[0], arrays[0]
+    n0, m0 = g0[0], len(cl0)
+    copies = [cl0] + [out[r * m0:(r + 1) * m0].copy() for r in range(R)]
+    group = [(n0, np.repeat(np.arange(n0), np.diff(rp0)), cc.astype(np.int64)) for cc in copies]
+    descs2, keep2 = _descs(group)
+    counts = np.zeros((R + 1) * NCLS[k], np.int64)
+    ok(lib.acc_motif_count_batch(c.h, descs2, R + 1, k, None, P(counts), None), "count_batch copies")
+    z = np.zeros(NCLS[k], np.float64)
+    ok(lib.acc_motif_zscores(P(counts), 1, R + 1, k, None, P(z)), "zscores")
+    cnt = counts.reshape(R + 1, -1)
+    want = oracle.zscores(cnt[0], cnt[1:])
+    if not np.array_equal(z, want, equal_nan=True):
+        raise AssertionError("zscores")
+    c.close()
+
+
+def scenario_server(lib):
+    """The request server: resident graphs, requests of every k, both
+    policies, polled and drained; every finished request's counts equal the
+    oracle's."""
+    srv = ctypes.c_void_p()
+    ok(lib.acc_server_create(ctypes.byref(srv), 0, 3, 1 << 30), "server_create")
+    gs = graphs(40, 4, 20)
+    arrays = [csr(n, s, d) for n, s, d in gs]
+    ids = []
+    for (n, _, _), (rp, cl) in zip(gs, arrays):
+        gid = ctypes.c_int32()
+        ok(lib.acc_server_add_graph(srv, P(rp), P(cl), n, len(cl), ctypes.byref(gid)), "add_graph")
+        ids.append(gid.value)
+    ok(lib.acc_server_reserve(srv), "reserve")
+    for policy in (acc.ACC_SERVE_FIFO, acc.ACC_SERVE_SHORTEST):
+        ok(lib.acc_server_set_policy(srv, policy, 0.5), "set_policy")
+        reqs = []
+        for i, gid in enumerate(ids):
+            for k in (3, 4, 5) if i < 2 else (3, 4):
+                rid = ctypes.c_int64()
+                ok(lib.acc_server_submit(srv, gid, k, ctypes.byref(rid)), "submit")
+                reqs.append((rid.value, i, k))
+        running, queued = ctypes.c_int32(), ctypes.c_int32()
+        ok(lib.acc_server_progress(srv, ctypes.byref(running), ctypes.byref(queued)), "progress")
+        ok(lib.acc_server_drain(srv), "drain")
+        for rid, i, k in reqs:
+            state = ctypes.c_int32()
+            out = np.zeros(NCLS[k], np.int64)
+            lat = ctypes.c_double()
+            ok(lib.acc_server_poll(srv, rid, ctypes.byref(state), P(out), ctypes.byref(lat)), "poll")
+            n, s, d = gs[i]
+            if state.value != acc.ACC_REQ_DONE or out.tolist() != oracle.count(n, s, d, k).tolist():
+                raise AssertionError(f"request {rid} graph {i} k {k}: state {state.value}")
+    lib.acc_server_destroy(srv)
+
+
+def scenario_tables(lib):
+    """The class table through the context (copy, classify, class codes) and
+    the allocation-free build, against the oracle's table."""
+    c = Ctx(lib)
+    for k in (3, 4, 5):
+        cls, codes = oracle.table(k)
+        t = np.zeros(1 << (k * (k - 1)), np.int16)
+        ok(lib.acc_motif_copy_table(c.h, k, P(t)), "copy_table")
+        if not np.array_equal(t, np.asarray(cls, np.int16)):
+            raise AssertionError(f"copy_table k {k}")
+        for ci in (0, NCLS[k] // 2, NCLS[k] - 1):
+            code = ctypes.c_uint32()
+            ok(lib.acc_motif_class_code(c.h, k, ci, ctypes.byref(code)), "class_code")
+            back = ctypes.c_int32()
+            ok(lib.acc_motif_classify_code(c.h, k, code.value, ctypes.byref(back)), "classify_code")
+            if code.value != codes[ci] or back.value != ci:
+                raise AssertionError(f"class {ci} k {k}")
+        st = np.zeros(1 << (k * (k - 1)), np.int16)
+        sc = np.zeros(NCLS[k], np.uint32)
+        ok(lib.acc_motif_build_table_static(k, None, P(st), P(sc)), "build_table_static")
+        if not np.array_equal(st, t) or not np.array_equal(sc, np.asarray(codes, np.uint32)):
+            raise AssertionError(f"static table k {k}")
+    c.close()
+
+
+if __name__ == "__main__":
+    lib = acc.declare(ctypes.CDLL(sys.argv[1]))
+    globals()["scenario_" + sys.argv[2]](lib)
+    print("ok")

@@ -14,7 +14,9 @@ against a plain construction of the same pair states, lists and
 renumbering, and on malformed inputs under the address sanitizer; the
 class-table builder against the oracle's table; the Z-scores bit for bit).
 The formula paths and the randomiser run through their host launchers, so
-every block runs whole (all its warps at once).  The
+every block runs whole (all its warps at once); the whole library, built
+for the host against a stand-in CUDA runtime, runs end to end through its C
+ABI (tests/emu/lib_scenarios.py).  The
 enumeration kernels also run with tiny
 shared-memory lists and histogram drain threshold, so their overflow lists
 and drain run on small graphs.  This checks the kernels' logic and warp
@@ -24,6 +26,7 @@ import re
 import shutil
 import struct
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -592,14 +595,12 @@ def _sv_to_canonical(k):
     return c
 
 
-@pytest.mark.parametrize("k", [3, 4])
+@pytest.mark.parametrize("k", [3, 4, 5])
 def test_table_builder_equals_oracle_table(emu_bins, k):
     """The device table builder (canonical code per adjacency code, class
     ranks, the table and its kernel layout) run on the host: the table and
     the class codes equal the oracle's, the relayout permutes it as the
-    enumeration kernels read it.  (k = 5 runs the same template code over
-    2^20 codes in 4096 blocks, most of a minute here; the GPU tests compare
-    its table with the oracle's.)"""
+    enumeration kernels read it."""
     raw = _run(emu_bins["emu_lut"], struct.pack("<q", k), True, emu_bins["dir"])
     ncodes = 1 << (k * (k - 1))
     rc = struct.unpack("<q", raw[:8])[0]
@@ -631,3 +632,62 @@ def test_zscore_kernel_equals_oracle_bitwise(emu_bins):
         want = oracle.zscores(counts[g, 0], counts[g, 1:])
         assert np.array_equal(z[g], want, equal_nan=True), g  # exact values, NaN in the same places
     assert np.isnan(z[1, 3]) and np.isnan(z[2, 5])
+
+
+LIB_SCENARIOS = ("modes", "repeats", "host_and_errors", "batch", "significance", "server", "tables")
+
+
+@pytest.fixture(scope="session")
+def emu_lib_results(tmp_path_factory):
+    """Build the whole library for the host (every CUDA source with its
+    launches rewritten, the shim and the stand-in runtime) as one shared
+    library, then run every scenario of tests/emu/lib_scenarios.py against it
+    in child processes, a few at a time: {scenario: (exit status, output)}."""
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    out = tmp_path_factory.mktemp("emulib")
+    units = []
+    for name in sorted(os.listdir(CSRC)):
+        if name.endswith(".cu"):
+            src = '#include "shim.h"\n' + _launches_to_calls(open(os.path.join(CSRC, name)).read())
+            open(out / (name[:-3] + ".cpp"), "w").write(src)
+            units.append(str(out / (name[:-3] + ".cpp")))
+    units.append(os.path.join(EMU, "emu_rt.cpp"))
+    procs = []
+    for i, u in enumerate(units):
+        cmd = ["g++", "-std=c++20", "-O1", "-fPIC", "-pthread", "-w", "-I", EMU, "-I", os.path.join(EMU, "fake"),
+               "-I", CSRC, "-c", u, "-o", str(out / ("u%d.o" % i))]
+        procs.append(subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    for pr in procs:
+        _, err = pr.communicate()
+        assert pr.returncode == 0, err[-3000:]
+    so = str(out / "libacc_emu.so")
+    r = subprocess.run(["g++", "-shared", "-pthread", "-o", so] + [str(out / ("u%d.o" % i)) for i in range(len(units))],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    width = max(1, min(4, (os.cpu_count() or 2) // 2))
+    results, running, todo = {}, [], list(LIB_SCENARIOS)
+    while todo or running:
+        while todo and len(running) < width:
+            name = todo.pop(0)
+            pr = subprocess.Popen([sys.executable, os.path.join(EMU, "lib_scenarios.py"), so, name], cwd=ROOT,
+                                  stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+            running.append((name, pr))
+        name, pr = running.pop(0)
+        try:
+            so_out, _ = pr.communicate(timeout=900)
+        except subprocess.TimeoutExpired:
+            pr.kill()
+            so_out, _ = pr.communicate()
+        results[name] = (pr.returncode, so_out)
+    return results
+
+
+@pytest.mark.parametrize("scenario", LIB_SCENARIOS)
+def test_library_on_the_host(emu_lib_results, scenario):
+    """The library's C ABI end to end on the host: counts in every mode, the
+    launch-graph replay of repeated counts, the host-buffer entry point and
+    argument errors, batches and the autotuner, randomisation and Z-scores,
+    the request server, and the class tables, each against the oracle."""
+    rc, output = emu_lib_results[scenario]
+    assert rc == 0, output[-3000:]
