@@ -75,8 +75,17 @@ inline cudaError_t cudaMemGetInfo(size_t *free_b, size_t *total_b) {
     return cudaSuccess;
 }
 
+// Allocations are 256-byte aligned, as the device's; with EMU_EXACT_ALLOC
+// (address-sanitizer builds) they have exactly the requested size, so a
+// read or write past the end of a buffer is caught.
 template <class T> inline cudaError_t cudaMalloc(T **p, size_t bytes) {
+#ifdef EMU_EXACT_ALLOC
+    void *q = nullptr;
+    if (posix_memalign(&q, 256, bytes ? bytes : 1)) q = nullptr;
+    *p = static_cast<T *>(q);
+#else
     *p = static_cast<T *>(std::aligned_alloc(256, (bytes + 255) / 256 * 256 + 256));
+#endif
     return *p ? cudaSuccess : 2;
 }
 inline cudaError_t cudaFree(void *p) {

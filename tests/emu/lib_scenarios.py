@@ -116,8 +116,8 @@ def scenario_repeats(lib):
     # replayed
     if replays() != 2:
         raise AssertionError(f"{replays()} graph launches for 4 counts")
-    # 120 vertices (7 kernels: no renumbering), k = 4
-    g = synth.chung_lu(120, 400, 2.1, 40, 20, 5)
+    # 80 vertices (7 kernels: no renumbering), k = 4
+    g = synth.chung_lu(80, 250, 2.1, 30, 20, 5)
     rp, cl = csr(g.n, g.src, g.dst)
     want = oracle.count(g.n, g.src, g.dst, 4).tolist()
     for i in range(3):

@@ -77,7 +77,10 @@ inline FiberSched &fsched() {
     static FiberSched s;
     return s;
 }
-constexpr size_t kLaneStack = 256 * 1024;
+#ifndef EMU_LANE_STACK
+#define EMU_LANE_STACK (256 * 1024)
+#endif
+constexpr size_t kLaneStack = EMU_LANE_STACK;  // bytes of stack per lane
 
 inline void bar_release(Bar *b) {
     b->arrived = 0;

@@ -142,7 +142,7 @@ def emu_bins(tmp_path_factory):
     targets += [("emu_f3", "emu_f35", ["-DEMU_K=3"]), ("emu_f5", "emu_f35", ["-DEMU_K=5"])]
     targets += [("emu_enum", "emu_enum", ["-DEMU_DRAIN_AT=(1u<<30)"]),
                 ("emu_enum_small", "emu_enum", ["-DEMU_DRAIN_AT=256u", "-DACC_CAP34=16", "-DACC_CAP5=8"]),
-                ("emu_build", "emu_build", ["-I", str(bdir), "-fsanitize=address"]),
+                ("emu_build", "emu_build", ["-I", str(bdir), "-fsanitize=address", "-DEMU_LANE_STACK=65536"]),
                 ("emu_lut", "emu_lut", ["-O2"]),
                 ("emu_z", "emu_z", ["-ffp-contract=off"])]
     procs = []
@@ -170,14 +170,18 @@ def csr(n, s, d):
     return rowptr, col
 
 
+def _width():
+    return max(1, min(8, (os.cpu_count() or 2) - 1))
+
+
 def _run(exe, inp, out, tmp):
     return _run_many(exe, [inp], out, tmp)[0]
 
 
 def _run_many(exe, inps, out, tmp):
-    """Run the emulator once per input, a few processes at a time (each is
-    mostly waiting on its lanes' barriers); outputs in input order."""
-    width = max(1, min(4, (os.cpu_count() or 2) // 2))
+    """Run the emulator once per input, one process per core at most (each
+    runs its lanes as fibers on one host thread); outputs in input order."""
+    width = _width()
     res, running, nxt = [None] * len(inps), [], 0
     while nxt < len(inps) or running:
         while nxt < len(inps) and len(running) < width:
@@ -640,9 +644,11 @@ LIB_SCENARIOS = ("modes", "repeats", "host_and_errors", "batch", "significance",
 @pytest.fixture(scope="session")
 def emu_lib_results(tmp_path_factory):
     """Build the whole library for the host (every CUDA source with its
-    launches rewritten, the shim and the stand-in runtime) as one shared
+    launches rewritten, the shim and the stand-in runtime; address-sanitized
+    with exact-size device allocations where the compiler can) as one shared
     library, then run every scenario of tests/emu/lib_scenarios.py against it
-    in child processes, a few at a time: {scenario: (exit status, output)}."""
+    in child processes, one per core at most: {scenario: (exit status,
+    output)}."""
     if shutil.which("g++") is None:
         pytest.skip("g++ not available")
     out = tmp_path_factory.mktemp("emulib")
@@ -653,25 +659,36 @@ def emu_lib_results(tmp_path_factory):
             open(out / (name[:-3] + ".cpp"), "w").write(src)
             units.append(str(out / (name[:-3] + ".cpp")))
     units.append(os.path.join(EMU, "emu_rt.cpp"))
+    # under the address sanitizer when the compiler has it, with every device
+    # allocation exactly its requested size: any access past a buffer fails
+    asan = subprocess.run(["g++", "-print-file-name=libasan.so"], capture_output=True, text=True).stdout.strip()
+    # (64 KiB lane stacks: the sanitizer clears a lane's whole stack shadow
+    # at every switch)
+    san = ["-fsanitize=address", "-DEMU_EXACT_ALLOC", "-DEMU_LANE_STACK=65536"] \
+        if os.path.isabs(asan) and os.path.exists(asan) else []
     procs = []
     for i, u in enumerate(units):
-        cmd = ["g++", "-std=c++20", "-O1", "-fPIC", "-pthread", "-w", "-I", EMU, "-I", os.path.join(EMU, "fake"),
-               "-I", CSRC, "-c", u, "-o", str(out / ("u%d.o" % i))]
+        cmd = ["g++", "-std=c++20", "-O1", "-fPIC", "-pthread", "-w", *san, "-I", EMU, "-I",
+               os.path.join(EMU, "fake"), "-I", CSRC, "-c", u, "-o", str(out / ("u%d.o" % i))]
         procs.append(subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
     for pr in procs:
         _, err = pr.communicate()
         assert pr.returncode == 0, err[-3000:]
     so = str(out / "libacc_emu.so")
-    r = subprocess.run(["g++", "-shared", "-pthread", "-o", so] + [str(out / ("u%d.o" % i)) for i in range(len(units))],
-                       capture_output=True, text=True)
+    r = subprocess.run(["g++", "-shared", "-pthread", *san[:1], "-o", so] +
+                       [str(out / ("u%d.o" % i)) for i in range(len(units))], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]
-    width = max(1, min(4, (os.cpu_count() or 2) // 2))
+    env = dict(os.environ)
+    if san:  # the interpreter is not instrumented: load the runtime first
+        env["LD_PRELOAD"] = asan
+        env["ASAN_OPTIONS"] = "detect_leaks=0"
+    width = _width()
     results, running, todo = {}, [], list(LIB_SCENARIOS)
     while todo or running:
         while todo and len(running) < width:
             name = todo.pop(0)
             pr = subprocess.Popen([sys.executable, os.path.join(EMU, "lib_scenarios.py"), so, name], cwd=ROOT,
-                                  stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+                                  env=env, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
             running.append((name, pr))
         name, pr = running.pop(0)
         try:
