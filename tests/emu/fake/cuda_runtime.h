@@ -4,6 +4,9 @@
 // except while it is being captured, when kernel launches, copies, memsets
 // and event records are kept (by value, as a launch keeps its arguments)
 // and a launch of the graph made from them runs them in the same order.
+// As on the device, a capture refuses the calls it cannot hold: waiting on
+// the captured stream, and, while any capture in the global mode is open,
+// allocating, freeing, synchronous copies and sets, and waits on anything.
 // Events read the host clock.
 #pragma once
 #include <chrono>
@@ -16,11 +19,16 @@ typedef int cudaError_t;
 #define cudaSuccess 0
 #define cudaErrorNotReady 600
 #define cudaErrorInvalidValue 1
+#define cudaErrorStreamCaptureUnsupported 900
 
 struct EmuStream {
     bool capturing = false;
+    bool global = false;  // captured in the global mode
     std::vector<std::function<void()>> rec;
 };
+inline int emu_global_captures = 0;  // captures open in the global mode
+#define EMU_REFUSE_IN_CAPTURE \
+    if (emu_global_captures > 0) return cudaErrorStreamCaptureUnsupported
 typedef EmuStream *cudaStream_t;
 struct EmuEvent {
     double t = 0.0;
@@ -68,7 +76,10 @@ inline cudaError_t cudaDeviceGetAttribute(int *v, cudaDeviceAttr, int) {
     *v = EMU_NUM_SMS;
     return cudaSuccess;
 }
-inline cudaError_t cudaDeviceSynchronize() { return cudaSuccess; }
+inline cudaError_t cudaDeviceSynchronize() {
+    EMU_REFUSE_IN_CAPTURE;
+    return cudaSuccess;
+}
 inline cudaError_t cudaMemGetInfo(size_t *free_b, size_t *total_b) {
     *free_b = size_t(8) << 30;
     *total_b = size_t(16) << 30;
@@ -79,6 +90,7 @@ inline cudaError_t cudaMemGetInfo(size_t *free_b, size_t *total_b) {
 // (address-sanitizer builds) they have exactly the requested size, so a
 // read or write past the end of a buffer is caught.
 template <class T> inline cudaError_t cudaMalloc(T **p, size_t bytes) {
+    EMU_REFUSE_IN_CAPTURE;
 #ifdef EMU_EXACT_ALLOC
     void *q = nullptr;
     if (posix_memalign(&q, 256, bytes ? bytes : 1)) q = nullptr;
@@ -89,6 +101,7 @@ template <class T> inline cudaError_t cudaMalloc(T **p, size_t bytes) {
     return *p ? cudaSuccess : 2;
 }
 inline cudaError_t cudaFree(void *p) {
+    EMU_REFUSE_IN_CAPTURE;
     std::free(p);
     return cudaSuccess;
 }
@@ -100,6 +113,7 @@ template <class T> inline cudaError_t cudaGetSymbolAddress(void **p, T &sym) {
 }
 
 inline cudaError_t cudaMemcpy(void *d, const void *s, size_t n, cudaMemcpyKind) {
+    EMU_REFUSE_IN_CAPTURE;
     if (n) std::memmove(d, s, n);
     return cudaSuccess;
 }
@@ -110,6 +124,7 @@ inline cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, cudaMemcpyK
     return cudaSuccess;
 }
 inline cudaError_t cudaMemset(void *p, int v, size_t n) {
+    EMU_REFUSE_IN_CAPTURE;
     std::memset(p, v, n);
     return cudaSuccess;
 }
@@ -126,16 +141,23 @@ inline cudaError_t cudaStreamDestroy(cudaStream_t s) {
     delete s;
     return cudaSuccess;
 }
-inline cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
-inline cudaError_t cudaStreamBeginCapture(cudaStream_t s, cudaStreamCaptureMode) {
+inline cudaError_t cudaStreamSynchronize(cudaStream_t s) {
+    EMU_REFUSE_IN_CAPTURE;
+    return s && s->capturing ? cudaErrorStreamCaptureUnsupported : cudaSuccess;
+}
+inline cudaError_t cudaStreamBeginCapture(cudaStream_t s, cudaStreamCaptureMode mode) {
     if (!s || s->capturing) return cudaErrorInvalidValue;
     s->capturing = true;
+    s->global = mode != cudaStreamCaptureModeRelaxed;
+    emu_global_captures += s->global;
     s->rec.clear();
     return cudaSuccess;
 }
 inline cudaError_t cudaStreamEndCapture(cudaStream_t s, cudaGraph_t *g) {
     if (!s || !s->capturing) return cudaErrorInvalidValue;
     s->capturing = false;
+    emu_global_captures -= s->global;
+    s->global = false;
     *g = new EmuGraph{std::move(s->rec)};
     s->rec.clear();
     return cudaSuccess;
@@ -176,7 +198,10 @@ inline cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t s) {
     return cudaSuccess;
 }
 inline cudaError_t cudaEventQuery(cudaEvent_t) { return cudaSuccess; }
-inline cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
+inline cudaError_t cudaEventSynchronize(cudaEvent_t) {
+    EMU_REFUSE_IN_CAPTURE;
+    return cudaSuccess;
+}
 inline cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t a, cudaEvent_t b) {
     *ms = (float)(b->t - a->t);
     return cudaSuccess;

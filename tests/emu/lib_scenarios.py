@@ -344,6 +344,96 @@ def scenario_tables(lib):
     c.close()
 
 
+def scenario_captured_pipeline(lib):
+    """The significance step captured by the caller into one graph on its
+    own stream (global capture mode: an allocation, a free, a synchronous
+    copy or a wait inside would fail the capture) and replayed: R copies of
+    each base graph randomised, the bases and copies counted as one
+    prepared batch, Z-scores; every replay equals the oracle's copies,
+    counts and Z-scores."""
+    for f in (lib.emu_stream_create, lib.emu_capture_end):
+        f.restype = ctypes.c_void_p
+    lib.emu_capture_begin.argtypes = [ctypes.c_void_p]
+    lib.emu_capture_end.argtypes = [ctypes.c_void_p]
+    lib.emu_graph_replay.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    c = Ctx(lib)
+    s = lib.emu_stream_create()
+    k, R, q = 3, 3, 2
+    bases = graphs(50, 3, 24)
+    descs, arrays = _descs(bases)
+    G = len(bases)
+    seeds = np.array([100 + g for g in range(G)], np.uint64)
+    M = sum(len(cl) for _, cl in arrays)
+    out = np.zeros(R * M, np.int32)
+    accepted = np.zeros(G * R, np.int64)
+    status = np.zeros(1, np.int32)
+    counts = np.zeros(G * (R + 1) * NCLS[k], np.int64)
+    z = np.zeros(G * NCLS[k], np.float64)
+
+    def randomise():
+        ok(lib.acc_swap_randomise(c.h, descs, G, R, q, P(seeds), acc.ACC_RAND_SWAP, s, P(out), P(accepted),
+                                  P(status)), "swap_randomise")
+
+    # eager: randomise once, then lay out the batch (each base, then its copies)
+    randomise()
+    batch, off = [], 0
+    for (n, _, _), (rp, cl) in zip(bases, arrays):
+        m = len(cl)
+        batch.append((rp, cl, n))
+        batch.extend((rp, out[off + r * m: off + (r + 1) * m], n) for r in range(R))
+        off += R * m
+
+    class Desc(ctypes.Structure):
+        _fields_ = [("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("n", ctypes.c_int32),
+                    ("m", ctypes.c_int64)]
+    bdesc = (Desc * len(batch))()
+    for i, (rp, cl, n) in enumerate(batch):
+        bdesc[i].rowptr, bdesc[i].col, bdesc[i].n, bdesc[i].m = rp.ctypes.data, cl.ctypes.data, n, len(cl)
+    ok(lib.acc_motif_batch_prepare(c.h, bdesc, len(batch), k, s), "batch_prepare")
+
+    def step():
+        randomise()
+        ok(lib.acc_motif_batch_run(c.h, s, P(counts), P(status)), "batch_run")
+        ok(lib.acc_motif_zscores(P(counts), G, R + 1, k, s, P(z)), "zscores")
+
+    step()  # eager once more, as a warm-up
+    ok(lib.emu_capture_begin(s), "capture begin")
+    step()
+    ex = lib.emu_capture_end(s)
+    if not ex:
+        raise AssertionError("the step could not be captured")
+    # expected values, from the oracle alone
+    want_out, want_acc, want_counts = [], [], []
+    for g, ((n, _, _), (rp, cl)) in enumerate(zip(bases, arrays)):
+        m = len(cl)
+        src = np.repeat(np.arange(n), np.diff(rp))
+        want_counts.append(oracle.count(n, src, cl.astype(np.int64), k))
+        for r in range(R):
+            cp, a = oracle.swap_randomise(n, rp, cl, q * m, int(seeds[g]) + r, acc.ACC_RAND_SWAP)
+            want_out.append(cp)
+            want_acc.append(a)
+            want_counts.append(oracle.count(n, src, cp.astype(np.int64), k))
+    want_counts = np.array(want_counts)
+    want_z = np.concatenate([oracle.zscores(want_counts[g * (R + 1)], want_counts[g * (R + 1) + 1:(g + 1) * (R + 1)])
+                             for g in range(G)])
+    for rep in range(2):
+        out[:] = -1
+        accepted[:] = -1
+        counts[:] = -1
+        z[:] = 0
+        status[:] = -1
+        ok(lib.emu_graph_replay(ex, s), "graph replay")
+        if status[0] != 0:
+            raise AssertionError(f"replay {rep}: status {status[0]}")
+        if not np.array_equal(out, np.concatenate(want_out)) or accepted.tolist() != want_acc:
+            raise AssertionError(f"replay {rep}: copies")
+        if not np.array_equal(counts.reshape(len(batch), -1), want_counts):
+            raise AssertionError(f"replay {rep}: counts")
+        if not np.array_equal(z, want_z, equal_nan=True):
+            raise AssertionError(f"replay {rep}: Z-scores")
+    c.close()
+
+
 if __name__ == "__main__":
     lib = acc.declare(ctypes.CDLL(sys.argv[1]))
     globals()["scenario_" + sys.argv[2]](lib)

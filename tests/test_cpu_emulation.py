@@ -638,7 +638,8 @@ def test_zscore_kernel_equals_oracle_bitwise(emu_bins):
     assert np.isnan(z[1, 3]) and np.isnan(z[2, 5])
 
 
-LIB_SCENARIOS = ("modes", "repeats", "host_and_errors", "batch", "significance", "server", "tables")
+LIB_SCENARIOS = ("modes", "repeats", "host_and_errors", "batch", "significance", "captured_pipeline", "server",
+                 "tables")
 
 
 @pytest.fixture(scope="session")
@@ -705,6 +706,7 @@ def test_library_on_the_host(emu_lib_results, scenario):
     """The library's C ABI end to end on the host: counts in every mode, the
     launch-graph replay of repeated counts, the host-buffer entry point and
     argument errors, batches and the autotuner, randomisation and Z-scores,
-    the request server, and the class tables, each against the oracle."""
+    the significance step captured by the caller and replayed, the request
+    server, and the class tables, each against the oracle."""
     rc, output = emu_lib_results[scenario]
     assert rc == 0, output[-3000:]
