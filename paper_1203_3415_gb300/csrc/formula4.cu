@@ -29,6 +29,14 @@ namespace {
 constexpr int kF4Classes = 199;
 constexpr int kF4Warps = 8;
 
+// True when the launch just enqueued was accepted; a refused launch's error
+// is cleared, and the caller launches nothing that would read its output.
+bool launch_ok() {
+    if (cudaPeekAtLastError() == cudaSuccess) return true;
+    cudaGetLastError();
+    return false;
+}
+
 __device__ __forceinline__ uint32_t probe4(const uint32_t *__restrict__ st, long long pitch, uint32_t a, uint32_t b) {
     return (__ldg(st + (long long)a * pitch + (b >> 4)) >> ((b & 15u) << 1)) & 3u;
 }
@@ -227,6 +235,7 @@ int launch_formula4(const GSet &gs, const uint32_t *state, const long long *nptr
     int launches = 0;
     if (blocks > 0) {
         k_formula4<<<(int)blocks, kF4Warps * 32, 0, s>>>(gs, state, nptr, deg, lo, nbr, lut, info, counts, status);
+        if (!launch_ok()) return ACC_ERR_CUDA;
         launches++;
     }
     const long long n = (long long)gs.B * kF4Classes;

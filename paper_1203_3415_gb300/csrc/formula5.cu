@@ -27,6 +27,14 @@ constexpr int kF5Classes = 9364;
 constexpr int kF5Warps = 8;
 constexpr int kF5Bins = 64;
 
+// True when the launch just enqueued was accepted; a refused launch's error
+// is cleared, and the caller launches nothing that would read its output.
+bool launch_ok() {
+    if (cudaPeekAtLastError() == cudaSuccess) return true;
+    cudaGetLastError();
+    return false;
+}
+
 __device__ __forceinline__ uint32_t probe5(const uint32_t *__restrict__ st, long long pitch, uint32_t a, uint32_t b) {
     return (__ldg(st + (long long)a * pitch + (b >> 4)) >> ((b & 15u) << 1)) & 3u;
 }
@@ -293,7 +301,9 @@ int launch_formula5(const GSet &gs, const uint32_t *state, const long long *nptr
                     int *status, int num_sms, cudaStream_t s) {
     if (gs.NV == 0) return 0;
     k_f5_prefix<<<1, 1024, 0, s>>>(deg, gs.NV, pre);
+    if (!launch_ok()) return ACC_ERR_CUDA;
     k_formula5<<<num_sms * 8, kF5Warps * 32, 0, s>>>(gs, state, nptr, deg, nbr, lut, pre, counts, status);
+    if (!launch_ok()) return ACC_ERR_CUDA;
     const long long n = (long long)gs.B * kF5Classes;
     long long db = (n + 255) / 256;
     if (db > (long long)num_sms * 4) db = (long long)num_sms * 4;

@@ -625,6 +625,14 @@ __global__ void k_graph_ids(GSet gs, int *gid) {
 
 __global__ void k_reset_maxdeg(GraphInfo *info) { info->maxdeg = 0; }
 
+// True when the launch just enqueued was accepted; a refused launch's error
+// is cleared, and the caller launches nothing that would read its output.
+bool launch_ok() {
+    if (cudaPeekAtLastError() == cudaSuccess) return true;
+    cudaGetLastError();
+    return false;
+}
+
 
 int grid_for(long long work_items, int per_block, int num_sms) {
     long long b = (work_items + per_block - 1) / per_block;
@@ -680,37 +688,49 @@ int launch_build_graph(const GSet &gs, const BuildBufs &bb, int max_n, int *stat
         k_zero<<<grid_for(items, 256 * 4, num_sms), 256, 0, s>>>(reinterpret_cast<uint4 *>(bb.state), n16,
                                                                  reinterpret_cast<unsigned char *>(bb.state) + n16 * 16,
                                                                  ntail, status, counts, ncounts, r);
+        if (!launch_ok()) return ACC_ERR_CUDA;
         launches++;
     }
     if (relabel) {
         // each graph's vertices renumbered by descending out- plus in-degree,
         // then the block built under the new ids
         k_arc_degrees<<<arcs_grid, 256, 0, s>>>(gs, bb.deg_in);
+        if (!launch_ok()) return ACC_ERR_CUDA;
         launches++;
         if (max_n <= kRelabelSmemMax) {
             k_relabel_graph<<<gs.B, 1024, (size_t)max_n * 4, s>>>(gs, bb.deg_in, bb.label);
+            if (!launch_ok()) return ACC_ERR_CUDA;
             launches++;
         } else {
             int *dhist = bb.deg;  // zeroed above, zeroed again by k_desc_scatter
             int *start = reinterpret_cast<int *>(bb.nptr);
             k_dhist<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, bb.deg_in, dhist);
+            if (!launch_ok()) return ACC_ERR_CUDA;
             k_desc_starts<<<gs.B, 1024, 0, s>>>(gs, dhist, start);
+            if (!launch_ok()) return ACC_ERR_CUDA;
             k_desc_scatter<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, bb.deg_in, start, bb.label, dhist);
+            if (!launch_ok()) return ACC_ERR_CUDA;
             launches += 3;
         }
     }
     k_ingest<<<arcs_grid, 256, 0, s>>>(gs, bb.state, relabel ? bb.label : nullptr, status, bb.deg, bb.lo, bb.occ,
                                        bb.occ_w);
+    if (!launch_ok()) return ACC_ERR_CUDA;
     launches++;
     if (NV <= kScanSingleMax) {
         k_scan_degrees<<<1, 1024, (size_t)(NV > 0 ? NV : 1) * 4, s>>>(bb.deg, (int)NV, bb.nptr, bb.info);
+        if (!launch_ok()) return ACC_ERR_CUDA;
         launches++;
     } else {
         const int ntiles = (int)scan_tiles_needed(NV);
         k_reset_maxdeg<<<1, 1, 0, s>>>(bb.info);
+        if (!launch_ok()) return ACC_ERR_CUDA;
         k_scan_tiles<<<ntiles, 1024, 0, s>>>(bb.deg, (int)NV, bb.tiles, bb.info);
+        if (!launch_ok()) return ACC_ERR_CUDA;
         k_scan_top<<<1, 1024, 0, s>>>(bb.tiles, ntiles, bb.nptr, (int)NV, bb.info);
+        if (!launch_ok()) return ACC_ERR_CUDA;
         k_scan_apply<<<ntiles, 1024, 0, s>>>(bb.deg, (int)NV, bb.tiles, bb.nptr);
+        if (!launch_ok()) return ACC_ERR_CUDA;
         launches += 4;
     }
     // rows per warp: enough warps to fill the GPU (64 per SM) first

@@ -16,6 +16,14 @@ namespace {
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
+// True when the launch just enqueued was accepted; a refused launch's error
+// is cleared, and the caller launches nothing that would read its output.
+bool launch_ok() {
+    if (cudaPeekAtLastError() == cudaSuccess) return true;
+    cudaGetLastError();
+    return false;
+}
+
 template <int K>
 struct Fact { static constexpr int v = K * Fact<K - 1>::v; };
 template <>
@@ -163,8 +171,11 @@ int launch_build_lut(int k, uint32_t *canon, int *rank, int16_t *lut, uint32_t *
     case 5: k_canon<5><<<grid, threads, 0, s>>>(canon); break;
     default: return ACC_ERR_K;
     }
+    if (!launch_ok()) return ACC_ERR_CUDA;
     k_rank<<<1, 1024, 0, s>>>(canon, ncodes, rank);
+    if (!launch_ok()) return ACC_ERR_CUDA;
     k_finish<<<grid, threads, 0, s>>>(canon, rank, ncodes, num_classes(k), lut, class_code);
+    if (!launch_ok()) return ACC_ERR_CUDA;
     switch (k) {
     case 3: k_relayout<3><<<grid, threads, 0, s>>>(lut, lut_sv); break;
     case 4: k_relayout<4><<<grid, threads, 0, s>>>(lut, lut_sv); break;
@@ -246,7 +257,9 @@ extern "C" ACC_API int acc_motif_build_table_static(int k, void *stream, int16_t
     case 4: k_canon<4><<<grid, threads, 0, s>>>(canon); break;
     default: k_canon<5><<<grid, threads, 0, s>>>(canon); break;
     }
+    if (!launch_ok()) return ACC_ERR_CUDA;
     k_rank<<<1, 1024, 0, s>>>(canon, ncodes, rank);
+    if (!launch_ok()) return ACC_ERR_CUDA;
     k_finish<<<grid, threads, 0, s>>>(canon, rank, ncodes, num_classes(k), d_table, d_class_code);
     return cudaGetLastError() == cudaSuccess ? ACC_OK : ACC_ERR_CUDA;
 }

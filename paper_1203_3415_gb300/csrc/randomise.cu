@@ -45,6 +45,14 @@ constexpr int kRandThreads = 128;
 constexpr int kRandU = 4;  // row entries per lane read with the attempt's first loads
 constexpr int kHalf = 16;
 
+// True when the launch just enqueued was accepted; a refused launch's error
+// is cleared, and the caller launches nothing that would read its output.
+bool launch_ok() {
+    if (cudaPeekAtLastError() == cudaSuccess) return true;
+    cudaGetLastError();
+    return false;
+}
+
 __device__ __forceinline__ uint64_t splitmix_next(uint64_t &s) {
     s += 0x9E3779B97F4A7C15ull;
     uint64_t z = s;
@@ -443,6 +451,7 @@ int launch_randomise(const RGraph *meta, int G, int R, long long M, long long NV
         long long blocks = (work + 255) / 256;
         if (blocks > (long long)num_sms * 8) blocks = (long long)num_sms * 8;
         k_rand_rows<<<(int)blocks, 256, 0, s>>>(meta, G, M, NV, rows, mutual_spec ? rpart : nullptr, status);
+        if (!launch_ok()) return ACC_ERR_CUDA;
         launches++;
     }
     const long long items = (long long)G * R;

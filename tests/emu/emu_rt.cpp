@@ -30,3 +30,9 @@ extern "C" void *emu_capture_end(void *s) {
 extern "C" int emu_graph_replay(void *e, void *s) {
     return cudaGraphLaunch(static_cast<cudaGraphExec_t>(e), static_cast<cudaStream_t>(s));
 }
+
+// Failure injection: the n-th allocation (kind 0), kernel launch (1), copy
+// or set (2) or graph launch (3) from now fails; n = 0 clears it.
+extern "C" void emu_inject(int kind, long long n) {
+    (kind == 0 ? emu_fail_malloc : kind == 1 ? emu_fail_launch : kind == 2 ? emu_fail_copy : emu_fail_graph) = n;
+}

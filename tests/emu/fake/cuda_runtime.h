@@ -7,7 +7,10 @@
 // As on the device, a capture refuses the calls it cannot hold: waiting on
 // the captured stream, and, while any capture in the global mode is open,
 // allocating, freeing, synchronous copies and sets, and waits on anything.
-// Events read the host clock.
+// Events read the host clock.  For failure tests, emu_fail_* make the n-th
+// allocation, kernel launch, copy or graph launch from now fail as the
+// device would report it (a launch error is returned by the next cudaGetLastError; a
+// failure inside a capture invalidates the capture).
 #pragma once
 #include <chrono>
 #include <cstdlib>
@@ -23,13 +26,22 @@ typedef int cudaError_t;
 
 struct EmuStream {
     bool capturing = false;
-    bool global = false;  // captured in the global mode
+    bool global = false;   // captured in the global mode
+    bool invalid = false;  // an operation failed while captured
     std::vector<std::function<void()>> rec;
 };
 inline int emu_global_captures = 0;  // captures open in the global mode
+inline long long emu_fail_malloc = 0, emu_fail_launch = 0, emu_fail_copy = 0, emu_fail_graph = 0;
+inline cudaError_t emu_last_error = 0;  // returned (and cleared) by cudaGetLastError
+// true when this call is the one a countdown selects
+inline bool emu_trip(long long &countdown) { return countdown > 0 && --countdown == 0; }
+
 #define EMU_REFUSE_IN_CAPTURE \
     if (emu_global_captures > 0) return cudaErrorStreamCaptureUnsupported
 typedef EmuStream *cudaStream_t;
+inline void emu_spoil(cudaStream_t s) {
+    if (s && s->capturing) s->invalid = true;
+}
 struct EmuEvent {
     double t = 0.0;
 };
@@ -60,7 +72,12 @@ inline void emu_submit(cudaStream_t s, std::function<void()> op) {
     else op();
 }
 
-inline cudaError_t cudaGetLastError() { return cudaSuccess; }
+inline cudaError_t cudaGetLastError() {
+    const cudaError_t e = emu_last_error;
+    emu_last_error = cudaSuccess;
+    return e;
+}
+inline cudaError_t cudaPeekAtLastError() { return emu_last_error; }
 inline const char *cudaGetErrorString(cudaError_t) { return "emulated"; }
 template <class T> inline cudaError_t cudaFuncSetAttribute(T, cudaFuncAttribute, int) { return cudaSuccess; }
 template <class T> inline cudaError_t cudaOccupancyMaxActiveBlocksPerMultiprocessor(int *b, T, int, size_t) {
@@ -91,6 +108,10 @@ inline cudaError_t cudaMemGetInfo(size_t *free_b, size_t *total_b) {
 // read or write past the end of a buffer is caught.
 template <class T> inline cudaError_t cudaMalloc(T **p, size_t bytes) {
     EMU_REFUSE_IN_CAPTURE;
+    if (emu_trip(emu_fail_malloc)) {
+        *p = nullptr;
+        return 2;  // out of memory
+    }
 #ifdef EMU_EXACT_ALLOC
     void *q = nullptr;
     if (posix_memalign(&q, 256, bytes ? bytes : 1)) q = nullptr;
@@ -114,10 +135,15 @@ template <class T> inline cudaError_t cudaGetSymbolAddress(void **p, T &sym) {
 
 inline cudaError_t cudaMemcpy(void *d, const void *s, size_t n, cudaMemcpyKind) {
     EMU_REFUSE_IN_CAPTURE;
+    if (emu_trip(emu_fail_copy)) return cudaErrorInvalidValue;
     if (n) std::memmove(d, s, n);
     return cudaSuccess;
 }
 inline cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, cudaMemcpyKind, cudaStream_t st) {
+    if (emu_trip(emu_fail_copy)) {
+        emu_spoil(st);
+        return cudaErrorInvalidValue;
+    }
     emu_submit(st, [=] {
         if (n) std::memmove(d, s, n);
     });
@@ -129,6 +155,10 @@ inline cudaError_t cudaMemset(void *p, int v, size_t n) {
     return cudaSuccess;
 }
 inline cudaError_t cudaMemsetAsync(void *p, int v, size_t n, cudaStream_t st) {
+    if (emu_trip(emu_fail_copy)) {
+        emu_spoil(st);
+        return cudaErrorInvalidValue;
+    }
     emu_submit(st, [=] { std::memset(p, v, n); });
     return cudaSuccess;
 }
@@ -158,6 +188,12 @@ inline cudaError_t cudaStreamEndCapture(cudaStream_t s, cudaGraph_t *g) {
     s->capturing = false;
     emu_global_captures -= s->global;
     s->global = false;
+    if (s->invalid) {  // as the device: a capture that saw a failure gives no graph
+        s->invalid = false;
+        s->rec.clear();
+        *g = nullptr;
+        return 901;
+    }
     *g = new EmuGraph{std::move(s->rec)};
     s->rec.clear();
     return cudaSuccess;
@@ -168,6 +204,7 @@ inline cudaError_t cudaGraphInstantiate(cudaGraphExec_t *e, cudaGraph_t g, unsig
 }
 inline long long emu_graph_launches = 0;  // graphs launched so far (read by the tests)
 inline cudaError_t cudaGraphLaunch(cudaGraphExec_t e, cudaStream_t s) {
+    if (emu_trip(emu_fail_graph)) return cudaErrorInvalidValue;
     emu_graph_launches++;
     for (auto &op : e->ops) emu_submit(s, op);
     return cudaSuccess;

@@ -434,6 +434,91 @@ def scenario_captured_pipeline(lib):
     c.close()
 
 
+def scenario_injected_failures(lib):
+    """Failure detection without a device fault: the n-th allocation, kernel
+    launch, copy or graph launch of a call fails.  The call returns
+    ACC_ERR_NOMEM (allocation) or ACC_ERR_CUDA (the others), and the same
+    context then counts correctly.  Counts are failed at every point they
+    reach on a fresh context (tables and workspace made), on the call that
+    captures the launch graph (third count of a context) and on one that
+    replays it; a batch and the randomiser are failed at a spread of
+    points."""
+    lib.emu_inject.argtypes = [ctypes.c_int, ctypes.c_longlong]
+    expect = {0: acc.ACC_ERR_NOMEM, 1: acc.ACC_ERR_CUDA, 2: acc.ACC_ERR_CUDA, 3: acc.ACC_ERR_CUDA}
+    g = synth.chung_lu(40, 120, 2.1, 20, 20, 9)
+    rp, cl = csr(g.n, g.src, g.dst)
+    want = oracle.count(g.n, g.src, g.dst, 3).tolist()
+    tripped = {}
+    for before in (0, 2, 3):  # counts made before the failing one
+        for kind in (0, 1, 2, 3):
+            for n in range(1, 80):
+                c = Ctx(lib)
+                for _ in range(before):
+                    c.count(rp, cl, g.n, 3)
+                lib.emu_inject(kind, n)
+                rc, st, got = c.count(rp, cl, g.n, 3)
+                lib.emu_inject(kind, 0)
+                if rc == 0:
+                    if st != 0 or got.tolist() != want:
+                        raise AssertionError(f"kind {kind} n {n}: wrong counts without an error")
+                    c.close()
+                    break  # the call makes fewer than n such calls
+                if rc != expect[kind]:
+                    raise AssertionError(f"after {before} kind {kind} n {n}: returned {rc}")
+                tripped[(before, kind)] = n
+                for _ in range(2):
+                    rc, st, got = c.count(rp, cl, g.n, 3)
+                    if rc or st or got.tolist() != want:
+                        raise AssertionError(f"after {before} kind {kind} n {n}: not usable after the failure")
+                c.close()
+    # every kind fails a fresh count; launches fail the capturing count; the
+    # graph launch fails the capturing and the replaying count
+    for key in [(0, 0), (0, 1), (0, 2), (2, 1), (2, 3), (3, 3)]:
+        if key not in tripped:
+            raise AssertionError(f"no failure injected for {key}: {sorted(tripped)}")
+    spread = (1, 2, 3, 5, 8, 13, 21, 34)
+    gs = graphs(60, 3, 14)
+    descs, arrays = _descs(gs)
+    bwant = [oracle.count(n, s, d, 3).tolist() for n, s, d in gs]
+    for kind in (0, 1, 2):
+        for n in spread:
+            c = Ctx(lib)
+            out = np.zeros(len(gs) * 13, np.int64)
+            lib.emu_inject(kind, n)
+            rc = lib.acc_motif_count_batch(c.h, descs, len(gs), 3, None, P(out), None)
+            lib.emu_inject(kind, 0)
+            ok(lib.acc_motif_count_batch(c.h, descs, len(gs), 3, None, P(out), None), "batch after a failure")
+            if out.reshape(len(gs), -1).tolist() != bwant:
+                raise AssertionError(f"batch kind {kind} n {n}")
+            c.close()
+            if rc == 0:
+                break
+            if rc != expect[kind]:
+                raise AssertionError(f"batch kind {kind} n {n}: returned {rc}")
+    R, seeds = 2, np.array([3, 4, 5], np.uint64)
+    rwant = np.concatenate([oracle.swap_randomise(n, rp_, cl_, 2 * len(cl_), int(seeds[g]) + r)[0]
+                            for g, ((n, _, _), (rp_, cl_)) in enumerate(zip(gs, arrays)) for r in range(R)])
+    M = len(rwant) // R
+    for kind in (0, 1, 2):
+        for n in spread:
+            c = Ctx(lib)
+            out = np.zeros(R * M, np.int32)
+            accd = np.zeros(len(gs) * R, np.int64)
+            lib.emu_inject(kind, n)
+            rc = lib.acc_swap_randomise(c.h, descs, len(gs), R, 2, P(seeds), acc.ACC_RAND_SWAP, None, P(out),
+                                        P(accd), None)
+            lib.emu_inject(kind, 0)
+            ok(lib.acc_swap_randomise(c.h, descs, len(gs), R, 2, P(seeds), acc.ACC_RAND_SWAP, None, P(out), P(accd),
+                                      None), "randomise after a failure")
+            if not np.array_equal(out, rwant):
+                raise AssertionError(f"randomise kind {kind} n {n}")
+            c.close()
+            if rc == 0:
+                break
+            if rc != expect[kind]:
+                raise AssertionError(f"randomise kind {kind} n {n}: returned {rc}")
+
+
 if __name__ == "__main__":
     lib = acc.declare(ctypes.CDLL(sys.argv[1]))
     globals()["scenario_" + sys.argv[2]](lib)

@@ -307,6 +307,11 @@ template <class F> bool run_blocks(int blocks, int threads, F f) {
 inline std::vector<uint64_t> emu_dyn_buf;
 inline unsigned char *emu_dyn_smem = nullptr;
 template <class F> void emu_launch(long long grid, long long block, size_t smem, cudaStream_t s, F f) {
+    if (emu_trip(emu_fail_launch)) {  // the launch is refused: nothing runs
+        emu_last_error = 98;
+        emu_spoil(s);
+        return;
+    }
     emu_submit(s, [=] {
         emu_dyn_buf.assign(smem / 8 + 2, 0);
         emu_dyn_smem = reinterpret_cast<unsigned char *>(emu_dyn_buf.data());
