@@ -317,6 +317,78 @@ def scenario_server(lib):
             if state.value != acc.ACC_REQ_DONE or out.tolist() != oracle.count(n, s, d, k).tolist():
                 raise AssertionError(f"request {rid} graph {i} k {k}: state {state.value}")
     lib.acc_server_destroy(srv)
+    # request errors: a malformed graph, and a graph whose workspace can
+    # never fit the budget
+    srv = ctypes.c_void_p()
+    ok(lib.acc_server_create(ctypes.byref(srv), 0, 2, 1 << 30), "server_create")
+    rp, cl = np.array([0, 1, 2, 2, 2], np.int64), np.array([1, 1], np.int32)  # self-loop 1 -> 1
+    gid, rid, state = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+    ok(lib.acc_server_add_graph(srv, P(rp), P(cl), 4, 2, ctypes.byref(gid)), "add_graph")
+    ok(lib.acc_server_submit(srv, gid.value, 3, ctypes.byref(rid)), "submit")
+    ok(lib.acc_server_drain(srv), "drain")
+    ok(lib.acc_server_poll(srv, rid.value, ctypes.byref(state), None, None), "poll")
+    if state.value != acc.ACC_ERR_INPUT:
+        raise AssertionError(f"malformed request: state {state.value}")
+    if lib.acc_server_submit(srv, 99, 3, ctypes.byref(rid)) != acc.ACC_ERR_ARG:
+        raise AssertionError("unknown graph id accepted")
+    if lib.acc_server_set_policy(srv, 7, 0.0) != acc.ACC_ERR_ARG:
+        raise AssertionError("unknown policy accepted")
+    lib.acc_server_destroy(srv)
+    g = synth.chung_lu(3000, 9000, 2.2, 100, 10, 3)
+    rp, cl = csr(g.n, g.src, g.dst)
+    ok(lib.acc_server_create(ctypes.byref(srv), 0, 1, 1 << 16), "server_create")
+    ok(lib.acc_server_add_graph(srv, P(rp), P(cl), g.n, len(cl), ctypes.byref(gid)), "add_graph")
+    ok(lib.acc_server_submit(srv, gid.value, 4, ctypes.byref(rid)), "submit")
+    ok(lib.acc_server_drain(srv), "drain")
+    ok(lib.acc_server_poll(srv, rid.value, ctypes.byref(state), None, None), "poll")
+    if state.value != acc.ACC_ERR_NOMEM:
+        raise AssertionError(f"request over the budget: state {state.value}")
+    lib.acc_server_destroy(srv)
+
+
+def scenario_misc_api(lib):
+    """The small entry points: error strings, class counts, prepare, the
+    schedule, timing, statistics, options and their argument checks."""
+    lib.acc_strerror.restype = ctypes.c_char_p
+    for code in range(0, -10, -1):
+        if not lib.acc_strerror(code):
+            raise AssertionError(f"no message for {code}")
+    if [lib.acc_motif_num_classes(k) for k in (3, 4, 5)] != [13, 199, 9364]:
+        raise AssertionError("num_classes")
+    c = Ctx(lib)
+    for k in (3, 4, 5):
+        ok(lib.acc_motif_prepare(c.h, k, None), f"prepare k {k}")
+    if lib.acc_motif_prepare(c.h, 7, None) != acc.ACC_ERR_K:
+        raise AssertionError("prepare k = 7 accepted")
+    light, target = ctypes.c_int64(), ctypes.c_int64()
+    ok(lib.acc_ctx_set_schedule(c.h, 777, 3333), "set_schedule")
+    ok(lib.acc_ctx_get_schedule(c.h, ctypes.byref(light), ctypes.byref(target)), "get_schedule")
+    if (light.value, target.value) != (777, 3333):
+        raise AssertionError("schedule round trip")
+    n, s, d = graphs(70, 1, 30)[0]
+    rp, cl = csr(n, s, d)
+    want = oracle.count(n, s, d, 4).tolist()
+    ok(lib.acc_ctx_set_timing(c.h, 1), "set_timing")
+    rc, st, got = c.count(rp, cl, n, 4)
+    if rc or st or got.tolist() != want:
+        raise AssertionError("count with schedule and timing")
+    ms = np.zeros(4, np.float32)
+    ok(lib.acc_motif_last_timing(c.h, P(ms)), "last_timing")
+    if (ms < 0).any():
+        raise AssertionError(f"negative stage times {ms}")
+    st7 = c.stats()
+    if st7[0] < 7 or st7[3] != len({(min(a, b), max(a, b)) for a, b in zip(s.tolist(), d.tolist())}):
+        raise AssertionError(f"stats {st7}")
+    ok(lib.acc_ctx_set_timing(c.h, 0), "set_timing off")
+    ok(lib.acc_ctx_set_schedule(c.h, 0, 0), "schedule back to the default")
+    for bad in (lambda: lib.acc_ctx_set_mode(c.h, 9), lambda: lib.acc_ctx_set_randomise_memory(c.h, -1),
+                lambda: lib.acc_ctx_set_schedule(c.h, -5, 10)):
+        if bad() != acc.ACC_ERR_ARG:
+            raise AssertionError("a bad option was accepted")
+    rc, st, got = c.count(rp, cl, n, 4)
+    if rc or st or got.tolist() != want:
+        raise AssertionError("count after the options")
+    c.close()
 
 
 def scenario_tables(lib):

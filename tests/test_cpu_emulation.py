@@ -639,7 +639,7 @@ def test_zscore_kernel_equals_oracle_bitwise(emu_bins):
 
 
 LIB_SCENARIOS = ("modes", "repeats", "host_and_errors", "batch", "significance", "captured_pipeline", "server",
-                 "tables", "injected_failures")
+                 "tables", "injected_failures", "misc_api")
 
 
 @pytest.fixture(scope="session")
