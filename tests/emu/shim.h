@@ -82,6 +82,39 @@ inline FiberSched &fsched() {
 #endif
 constexpr size_t kLaneStack = EMU_LANE_STACK;  // bytes of stack per lane
 
+// The order in which runnable lanes are resumed and blocks are run, from the
+// environment variable EMU_SCHED: 0 (or unset) ascending, 1 descending,
+// n >= 2 pseudo-random orders drawn from seed n.  Every order is a schedule
+// the GPU may take, so no result may depend on it: running the same work
+// under several orders is a race check.
+inline unsigned long long emu_sched() {
+    static const unsigned long long v = [] {
+        const char *e = std::getenv("EMU_SCHED");
+        return e ? std::strtoull(e, nullptr, 10) : 0ull;
+    }();
+    return v;
+}
+inline std::vector<int> emu_order(int n) {
+    static unsigned long long draws = 0;
+    std::vector<int> o(n);
+    for (int i = 0; i < n; i++) o[i] = i;
+    const unsigned long long mode = emu_sched();
+    if (mode == 1) {
+        std::reverse(o.begin(), o.end());
+    } else if (mode >= 2) {
+        unsigned long long x = mode * 0x9E3779B97F4A7C15ull + ++draws;
+        for (int i = n - 1; i > 0; i--) {  // Fisher-Yates with SplitMix64 draws
+            x += 0x9E3779B97F4A7C15ull;
+            unsigned long long z = x;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            std::swap(o[i], o[(int)(z % (unsigned long long)(i + 1))]);
+        }
+    }
+    return o;
+}
+
 inline void bar_release(Bar *b) {
     b->arrived = 0;
     for (auto &l : fsched().lanes)
@@ -133,7 +166,7 @@ template <class Init> bool run_lanes(int n, std::function<void()> job, Init init
     bool ok = true;
     for (;;) {
         bool ran = false, left = false;
-        for (int i = 0; i < n; i++) {
+        for (int i : emu_order(n)) {
             Lane &l = s.lanes[i];
             if (l.state == 2) continue;
             left = true;
@@ -252,7 +285,7 @@ inline int atomicCAS(int *p, int c, int v) {
 template <class F> bool run_warps(int blocks, int threads, F f) {
     blockDim.x = threads;
     gridDim.x = blocks;
-    for (int b = 0; b < blocks; b++)
+    for (int b : emu_order(blocks))
         for (int w = 0; w < threads / 32; w++) {
             Bar bar;
             bar.expected = 32;
@@ -279,7 +312,7 @@ template <class F> bool run_blocks(int blocks, int threads, F f) {
     const int nw = (threads + 31) / 32;
     std::vector<Bar> wbar(nw);
     std::vector<WarpCtx> ctx(nw);
-    for (int b = 0; b < blocks; b++) {
+    for (int b : emu_order(blocks)) {
         Bar block_bar;
         block_bar.expected = threads;
         for (int w = 0; w < nw; w++) {

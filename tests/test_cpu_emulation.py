@@ -640,6 +640,11 @@ def test_zscore_kernel_equals_oracle_bitwise(emu_bins):
 
 LIB_SCENARIOS = ("modes", "repeats", "host_and_errors", "batch", "significance", "captured_pipeline", "server",
                  "tables", "injected_failures", "misc_api")
+# (scenario, EMU_SCHED): the scenarios that run every kernel, again with the
+# lanes resumed and the blocks run in reverse and in pseudo-random orders
+LIB_RUNS = [(s, 0) for s in LIB_SCENARIOS] + [("modes", 1), ("modes", 7777), ("batch", 1), ("batch", 4242),
+                                               ("captured_pipeline", 1), ("captured_pipeline", 31337),
+                                               ("server", 99)]
 
 
 @pytest.fixture(scope="session")
@@ -648,8 +653,8 @@ def emu_lib_results(tmp_path_factory):
     launches rewritten, the shim and the stand-in runtime; address-sanitized
     with exact-size device allocations where the compiler can) as one shared
     library, then run every scenario of tests/emu/lib_scenarios.py against it
-    in child processes, one per core at most: {scenario: (exit status,
-    output)}."""
+    in child processes, one per core at most: {(scenario, schedule): (exit
+    status, output)}."""
     if shutil.which("g++") is None:
         pytest.skip("g++ not available")
     out = tmp_path_factory.mktemp("emulib")
@@ -684,12 +689,13 @@ def emu_lib_results(tmp_path_factory):
         env["LD_PRELOAD"] = asan
         env["ASAN_OPTIONS"] = "detect_leaks=0"
     width = _width()
-    results, running, todo = {}, [], list(LIB_SCENARIOS)
+    results, running, todo = {}, [], list(LIB_RUNS)
     while todo or running:
         while todo and len(running) < width:
             name = todo.pop(0)
-            pr = subprocess.Popen([sys.executable, os.path.join(EMU, "lib_scenarios.py"), so, name], cwd=ROOT,
-                                  env=env, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+            env["EMU_SCHED"] = str(name[1])
+            pr = subprocess.Popen([sys.executable, os.path.join(EMU, "lib_scenarios.py"), so, name[0]], cwd=ROOT,
+                                  env=dict(env), stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
             running.append((name, pr))
         name, pr = running.pop(0)
         try:
@@ -701,12 +707,14 @@ def emu_lib_results(tmp_path_factory):
     return results
 
 
-@pytest.mark.parametrize("scenario", LIB_SCENARIOS)
+@pytest.mark.parametrize("scenario", LIB_RUNS, ids=lambda r: r[0] + ("" if not r[1] else "-sched%d" % r[1]))
 def test_library_on_the_host(emu_lib_results, scenario):
     """The library's C ABI end to end on the host: counts in every mode, the
     launch-graph replay of repeated counts, the host-buffer entry point and
     argument errors, batches and the autotuner, randomisation and Z-scores,
     the significance step captured by the caller and replayed, the request
-    server, and the class tables, each against the oracle."""
+    server, and the class tables, each against the oracle; the scenarios
+    that run every kernel also under other lane and block orders (a race
+    check: every order is a valid GPU schedule)."""
     rc, output = emu_lib_results[scenario]
     assert rc == 0, output[-3000:]
