@@ -206,8 +206,8 @@ def _descs(gs):
 
 
 def scenario_batch(lib):
-    """A batch of graphs prepared once and run several times, then the
-    autotuner, for k = 3, 4 and 5."""
+    """A batch of graphs prepared once and run several times in every mode,
+    then the autotuner, for k = 3, 4 and 5."""
     c = Ctx(lib)
     for k, nmax in ((3, 30), (4, 18), (5, 10)):
         gs = graphs(20 + k, 6, nmax)
@@ -215,12 +215,16 @@ def scenario_batch(lib):
         descs, keep = _descs(gs)
         ok(lib.acc_motif_batch_prepare(c.h, descs, len(gs), k, None), "batch_prepare")
         want = [oracle.count(n, s, d, k).tolist() for n, s, d in gs]
-        for rep in range(2):
-            out = np.full(len(gs) * NCLS[k], -1, np.int64)
-            st = np.full(1, -1, np.int32)
-            ok(lib.acc_motif_batch_run(c.h, None, P(out), P(st)), "batch_run")
-            if st[0] != 0 or out.reshape(len(gs), -1).tolist() != want:
-                raise AssertionError(f"batch k {k} rep {rep}")
+        # every mode on the same prepared batch (graph sets take each mode's
+        # per-graph counting branch)
+        for mode in (acc.ACC_MODE_ENUMERATE, acc.ACC_MODE_FORMULA, acc.ACC_MODE_COUNT):
+            ok(lib.acc_ctx_set_mode(c.h, mode), "set_mode")
+            for rep in range(2):
+                out = np.full(len(gs) * NCLS[k], -1, np.int64)
+                st = np.full(1, -1, np.int32)
+                ok(lib.acc_motif_batch_run(c.h, None, P(out), P(st)), "batch_run")
+                if st[0] != 0 or out.reshape(len(gs), -1).tolist() != want:
+                    raise AssertionError(f"batch k {k} mode {mode} rep {rep}")
         if k == 4:
             light, target = ctypes.c_int64(), ctypes.c_int64()
             ms = ctypes.c_float()
