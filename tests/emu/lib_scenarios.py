@@ -18,7 +18,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 sys.path.insert(0, ROOT)
 
 import oracle  # noqa: E402
-import paper_1203_3415_gb300 as acc  # noqa: E402  (constants and the signature table only)
+import paper_1203_3415_gb300 as acc  # noqa: E402  (constants, types and the signature table only)
 import synth  # noqa: E402
 from tests.graph_helpers import random_digraph  # noqa: E402
 
@@ -191,12 +191,7 @@ def scenario_host_and_errors(lib):
 
 def _descs(gs):
     arrays = [csr(n, s, d) for n, s, d in gs]
-    descs = (acc.acc_graph_desc * len(gs))() if hasattr(acc, "acc_graph_desc") else None
-    if descs is None:
-        class Desc(ctypes.Structure):
-            _fields_ = [("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("n", ctypes.c_int32),
-                        ("m", ctypes.c_int64)]
-        descs = (Desc * len(gs))()
+    descs = (acc.acc_graph_desc * len(gs))()
     for i, ((n, _, _), (rp, cl)) in enumerate(zip(gs, arrays)):
         descs[i].rowptr = rp.ctypes.data
         descs[i].col = cl.ctypes.data
@@ -458,11 +453,7 @@ def scenario_captured_pipeline(lib):
         batch.append((rp, cl, n))
         batch.extend((rp, out[off + r * m: off + (r + 1) * m], n) for r in range(R))
         off += R * m
-
-    class Desc(ctypes.Structure):
-        _fields_ = [("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("n", ctypes.c_int32),
-                    ("m", ctypes.c_int64)]
-    bdesc = (Desc * len(batch))()
+    bdesc = (acc.acc_graph_desc * len(batch))()
     for i, (rp, cl, n) in enumerate(batch):
         bdesc[i].rowptr, bdesc[i].col, bdesc[i].n, bdesc[i].m = rp.ctypes.data, cl.ctypes.data, n, len(cl)
     ok(lib.acc_motif_batch_prepare(c.h, bdesc, len(batch), k, s), "batch_prepare")
