@@ -390,6 +390,72 @@ def scenario_misc_api(lib):
     c.close()
 
 
+def scenario_fuzz(lib, seed=2024, ops=60):
+    """A seeded random sequence of calls on one context: counts (fresh and
+    repeated on the same buffers, so launch graphs are captured, replayed and
+    dropped), batches, randomisation, mode, schedule and launch-graph
+    switches, over graphs of 0 to 40 vertices; every result against the
+    oracle."""
+    rng = np.random.default_rng(seed)
+    c = Ctx(lib)
+    held = None  # (n, s, d, rowptr, col) kept for repeats
+    mode_names = (acc.ACC_MODE_COUNT, acc.ACC_MODE_ENUMERATE, acc.ACC_MODE_FORMULA)
+
+    def draw(nmax):
+        n = int(rng.integers(0, nmax + 1))
+        if n == 0:
+            return 0, np.zeros(0, np.int64), np.zeros(0, np.int64)
+        s, d = random_digraph(rng, n, p=float(rng.uniform(0.0, 0.5)), recip=float(rng.random()))
+        return n, np.asarray(s, np.int64), np.asarray(d, np.int64)
+
+    for i in range(ops):
+        op = rng.choice(["count", "repeat", "repeat", "batch", "randomise", "mode", "schedule", "graphs"])
+        if op in ("count", "repeat"):
+            if op == "count" or held is None:
+                n, s, d = draw(40)
+                held = (n, s, d, *csr(n, s, d))
+            n, s, d, rp, cl = held
+            k = int(rng.choice([3, 4] if n > 12 else [3, 4, 5]))
+            rc, st, got = c.count(rp, cl, n, k)
+            if rc or st or got.tolist() != oracle.count(n, s, d, k).tolist():
+                raise AssertionError(f"op {i} {op}: n {n} k {k} rc {rc} status {st}")
+        elif op == "batch":
+            gs = [draw(16) for _ in range(int(rng.integers(1, 5)))]
+            k = int(rng.choice([3, 4]))
+            descs, keep = _descs(gs)
+            out = np.full(len(gs) * NCLS[k], -1, np.int64)
+            ok(lib.acc_motif_count_batch(c.h, descs, len(gs), k, None, P(out), None), f"op {i} batch")
+            if out.reshape(len(gs), -1).tolist() != [oracle.count(n, s, d, k).tolist() for n, s, d in gs]:
+                raise AssertionError(f"op {i} batch")
+        elif op == "randomise":
+            gs = [draw(20) for _ in range(int(rng.integers(1, 3)))]
+            descs, arrays = _descs(gs)
+            R, q = int(rng.integers(1, 3)), int(rng.integers(0, 3))
+            mode = int(rng.integers(0, 2))
+            seeds = rng.integers(0, 1 << 62, size=len(gs)).astype(np.uint64)
+            M = sum(len(cl) for _, cl in arrays)
+            out = np.full(max(1, R * M), -1, np.int32)
+            accd = np.full(len(gs) * R, -1, np.int64)
+            ok(lib.acc_swap_randomise(c.h, descs, len(gs), R, q, P(seeds), mode, None, P(out), P(accd), None),
+               f"op {i} randomise")
+            off = 0
+            for g, ((n, _, _), (rp, cl)) in enumerate(zip(gs, arrays)):
+                m = len(cl)
+                for r in range(R):
+                    want, wa = oracle.swap_randomise(n, rp, cl, q * m, int(seeds[g]) + r, mode)
+                    if not np.array_equal(out[off + r * m: off + (r + 1) * m], want) or accd[g * R + r] != wa:
+                        raise AssertionError(f"op {i} randomise graph {g} copy {r}")
+                off += R * m
+        elif op == "mode":
+            ok(lib.acc_ctx_set_mode(c.h, int(rng.choice(mode_names))), f"op {i} mode")
+        elif op == "schedule":
+            light, target = (0, 0) if rng.random() < 0.3 else (int(rng.integers(1, 5000)), int(rng.integers(1, 5000)))
+            ok(lib.acc_ctx_set_schedule(c.h, light, target), f"op {i} schedule")
+        else:
+            ok(lib.acc_ctx_set_launch_graphs(c.h, int(rng.integers(0, 2))), f"op {i} graphs")
+    c.close()
+
+
 def scenario_tables(lib):
     """The class table through the context (copy, classify, class codes) and
     the allocation-free build, against the oracle's table."""

@@ -639,12 +639,12 @@ def test_zscore_kernel_equals_oracle_bitwise(emu_bins):
 
 
 LIB_SCENARIOS = ("modes", "repeats", "host_and_errors", "batch", "significance", "captured_pipeline", "server",
-                 "tables", "injected_failures", "misc_api")
+                 "tables", "injected_failures", "misc_api", "fuzz")
 # (scenario, EMU_SCHED): the scenarios that run every kernel, again with the
 # lanes resumed and the blocks run in reverse and in pseudo-random orders
 LIB_RUNS = [(s, 0) for s in LIB_SCENARIOS] + [("modes", 1), ("modes", 7777), ("batch", 1), ("batch", 4242),
                                                ("captured_pipeline", 1), ("captured_pipeline", 31337),
-                                               ("server", 99)]
+                                               ("server", 99), ("fuzz", 5150)]
 
 
 @pytest.fixture(scope="session")
