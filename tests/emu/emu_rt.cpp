@@ -36,3 +36,6 @@ extern "C" int emu_graph_replay(void *e, void *s) {
 extern "C" void emu_inject(int kind, long long n) {
     (kind == 0 ? emu_fail_malloc : kind == 1 ? emu_fail_launch : kind == 2 ? emu_fail_copy : emu_fail_graph) = n;
 }
+
+// Wait for all queued work (deferred mode), as cudaDeviceSynchronize.
+extern "C" void emu_device_synchronize() { emu_flush_all(); }

@@ -15,7 +15,9 @@
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
+#include <cstdint>
 #include <functional>
+#include <map>
 #include <vector>
 
 typedef int cudaError_t;
@@ -29,6 +31,7 @@ struct EmuStream {
     bool global = false;   // captured in the global mode
     bool invalid = false;  // an operation failed while captured
     std::vector<std::function<void()>> rec;
+    std::vector<std::function<void()>> pending;  // deferred mode: work not yet run
 };
 inline int emu_global_captures = 0;  // captures open in the global mode
 inline long long emu_fail_malloc = 0, emu_fail_launch = 0, emu_fail_copy = 0, emu_fail_graph = 0;
@@ -44,6 +47,8 @@ inline void emu_spoil(cudaStream_t s) {
 }
 struct EmuEvent {
     double t = 0.0;
+    bool done = true;           // the work before its record has run
+    EmuStream *s = nullptr;     // the stream it was recorded on
 };
 typedef EmuEvent *cudaEvent_t;
 struct EmuGraph {
@@ -66,9 +71,43 @@ enum cudaFuncAttribute { cudaFuncAttributeMaxDynamicSharedMemorySize = 8 };
 #define EMU_NUM_SMS 2
 #endif
 
-// run op now, or keep it when s is being captured
+// Deferred mode (environment variable EMU_DEFER=1): work waits in its
+// stream's queue until something waits for that stream (a stream, event or
+// device synchronisation, a blocking copy or set on the null stream, a
+// free), as on the device, where it runs behind the host.  A host read of a
+// result before such a wait then sees the buffer as it was.  Streams are
+// run in the order they are waited on: the library orders work on several
+// streams only through such waits.
+inline bool emu_defer() {
+    static const bool v = [] {
+        const char *e = std::getenv("EMU_DEFER");
+        return e && e[0] == '1';
+    }();
+    return v;
+}
+inline EmuStream emu_null_stream;  // the legacy stream's queue
+inline std::vector<EmuStream *> &emu_streams() {
+    static std::vector<EmuStream *> v;
+    return v;
+}
+inline EmuStream *emu_queue(cudaStream_t s) { return s ? s : &emu_null_stream; }
+inline void emu_flush(cudaStream_t s) {
+    EmuStream *q = emu_queue(s);
+    while (!q->pending.empty()) {
+        std::vector<std::function<void()>> ops;
+        ops.swap(q->pending);
+        for (auto &op : ops) op();
+    }
+}
+inline void emu_flush_all() {
+    emu_flush(nullptr);
+    for (size_t i = 0; i < emu_streams().size(); i++) emu_flush(emu_streams()[i]);
+}
+
+// run op now (deferred mode: queue it), or keep it when s is being captured
 inline void emu_submit(cudaStream_t s, std::function<void()> op) {
     if (s && s->capturing) s->rec.push_back(std::move(op));
+    else if (emu_defer()) emu_queue(s)->pending.push_back(std::move(op));
     else op();
 }
 
@@ -95,6 +134,7 @@ inline cudaError_t cudaDeviceGetAttribute(int *v, cudaDeviceAttr, int) {
 }
 inline cudaError_t cudaDeviceSynchronize() {
     EMU_REFUSE_IN_CAPTURE;
+    emu_flush_all();
     return cudaSuccess;
 }
 inline cudaError_t cudaMemGetInfo(size_t *free_b, size_t *total_b) {
@@ -123,11 +163,33 @@ template <class T> inline cudaError_t cudaMalloc(T **p, size_t bytes) {
 }
 inline cudaError_t cudaFree(void *p) {
     EMU_REFUSE_IN_CAPTURE;
+    emu_flush_all();  // a free waits for the device
     std::free(p);
     return cudaSuccess;
 }
-template <class T> inline cudaError_t cudaMallocHost(T **p, size_t bytes) { return cudaMalloc(p, bytes); }
-inline cudaError_t cudaFreeHost(void *p) { return cudaFree(p); }
+// pinned host allocations (start -> bytes): copies to and from them are
+// asynchronous; copies to and from other (pageable) host memory wait, as on
+// the device
+inline std::map<uintptr_t, size_t> &emu_pinned() {
+    static std::map<uintptr_t, size_t> m;
+    return m;
+}
+inline bool emu_is_pinned(const void *p) {
+    auto &m = emu_pinned();
+    auto it = m.upper_bound((uintptr_t)p);
+    if (it == m.begin()) return false;
+    --it;
+    return (uintptr_t)p < it->first + it->second;
+}
+template <class T> inline cudaError_t cudaMallocHost(T **p, size_t bytes) {
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) emu_pinned()[(uintptr_t)*p] = bytes ? bytes : 1;
+    return e;
+}
+inline cudaError_t cudaFreeHost(void *p) {
+    emu_pinned().erase((uintptr_t)p);
+    return cudaFree(p);
+}
 template <class T> inline cudaError_t cudaGetSymbolAddress(void **p, T &sym) {
     *p = static_cast<void *>(&sym);
     return cudaSuccess;
@@ -136,13 +198,21 @@ template <class T> inline cudaError_t cudaGetSymbolAddress(void **p, T &sym) {
 inline cudaError_t cudaMemcpy(void *d, const void *s, size_t n, cudaMemcpyKind) {
     EMU_REFUSE_IN_CAPTURE;
     if (emu_trip(emu_fail_copy)) return cudaErrorInvalidValue;
+    emu_flush(nullptr);  // blocking: after the null stream's work
     if (n) std::memmove(d, s, n);
     return cudaSuccess;
 }
-inline cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, cudaMemcpyKind, cudaStream_t st) {
+inline cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, cudaMemcpyKind kind, cudaStream_t st) {
     if (emu_trip(emu_fail_copy)) {
         emu_spoil(st);
         return cudaErrorInvalidValue;
+    }
+    const bool pageable = (kind == cudaMemcpyHostToDevice && !emu_is_pinned(s)) ||
+                          (kind == cudaMemcpyDeviceToHost && !emu_is_pinned(d));
+    if (emu_defer() && pageable && !(st && st->capturing)) {
+        emu_flush(st);  // a pageable copy waits for the stream and completes before returning
+        if (n) std::memmove(d, s, n);
+        return cudaSuccess;
     }
     emu_submit(st, [=] {
         if (n) std::memmove(d, s, n);
@@ -151,6 +221,7 @@ inline cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, cudaMemcpyK
 }
 inline cudaError_t cudaMemset(void *p, int v, size_t n) {
     EMU_REFUSE_IN_CAPTURE;
+    emu_flush(nullptr);
     std::memset(p, v, n);
     return cudaSuccess;
 }
@@ -165,15 +236,25 @@ inline cudaError_t cudaMemsetAsync(void *p, int v, size_t n, cudaStream_t st) {
 
 inline cudaError_t cudaStreamCreateWithFlags(cudaStream_t *s, unsigned) {
     *s = new EmuStream;
+    emu_streams().push_back(*s);
     return cudaSuccess;
 }
 inline cudaError_t cudaStreamDestroy(cudaStream_t s) {
+    emu_flush(s);  // its work still completes
+    auto &v = emu_streams();
+    for (size_t i = 0; i < v.size(); i++)
+        if (v[i] == s) {
+            v.erase(v.begin() + (long)i);
+            break;
+        }
     delete s;
     return cudaSuccess;
 }
 inline cudaError_t cudaStreamSynchronize(cudaStream_t s) {
     EMU_REFUSE_IN_CAPTURE;
-    return s && s->capturing ? cudaErrorStreamCaptureUnsupported : cudaSuccess;
+    if (s && s->capturing) return cudaErrorStreamCaptureUnsupported;
+    emu_flush(s);
+    return cudaSuccess;
 }
 inline cudaError_t cudaStreamBeginCapture(cudaStream_t s, cudaStreamCaptureMode mode) {
     if (!s || s->capturing) return cudaErrorInvalidValue;
@@ -227,16 +308,31 @@ inline cudaError_t cudaEventCreate(cudaEvent_t *e) {
 }
 inline cudaError_t cudaEventCreateWithFlags(cudaEvent_t *e, unsigned) { return cudaEventCreate(e); }
 inline cudaError_t cudaEventDestroy(cudaEvent_t e) {
+    if (!e->done) emu_flush(e->s);  // its record still runs
     delete e;
     return cudaSuccess;
 }
 inline cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t s) {
-    emu_submit(s, [=] { e->t = emu_now_ms(); });
+    if (!(s && s->capturing)) {
+        e->done = false;
+        e->s = s;
+    }
+    emu_submit(s, [=] {
+        e->t = emu_now_ms();
+        e->done = true;
+    });
     return cudaSuccess;
 }
-inline cudaError_t cudaEventQuery(cudaEvent_t) { return cudaSuccess; }
-inline cudaError_t cudaEventSynchronize(cudaEvent_t) {
+// not ready the first time the work before it is still queued; the device
+// runs that work meanwhile
+inline cudaError_t cudaEventQuery(cudaEvent_t e) {
+    if (e->done) return cudaSuccess;
+    emu_flush(e->s);
+    return cudaErrorNotReady;
+}
+inline cudaError_t cudaEventSynchronize(cudaEvent_t e) {
     EMU_REFUSE_IN_CAPTURE;
+    if (!e->done) emu_flush(e->s);
     return cudaSuccess;
 }
 inline cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t a, cudaEvent_t b) {

@@ -38,6 +38,13 @@ def csr(n, s, d):
     return rowptr, col
 
 
+def sync(lib):
+    """Wait for the device, as a caller does before reading what an
+    asynchronous call wrote (the stand-in runtime's deferred mode holds the
+    work until then)."""
+    lib.emu_device_synchronize()
+
+
 def ok(rc, what):
     if rc != 0:
         raise AssertionError(f"{what}: returned {rc}")
@@ -57,6 +64,7 @@ class Ctx:
         out[:] = -1
         st[:] = -1
         rc = self.lib.acc_motif_count(self.h, P(rowptr), P(col), n, len(col), k, None, P(out), P(st))
+        sync(self.lib)  # with a status pointer the count only enqueues
         return rc, int(st[0]), out.copy()
 
     def stats(self):
@@ -218,6 +226,7 @@ def scenario_batch(lib):
                 out = np.full(len(gs) * NCLS[k], -1, np.int64)
                 st = np.full(1, -1, np.int32)
                 ok(lib.acc_motif_batch_run(c.h, None, P(out), P(st)), "batch_run")
+                sync(lib)
                 if st[0] != 0 or out.reshape(len(gs), -1).tolist() != want:
                     raise AssertionError(f"batch k {k} mode {mode} rep {rep}")
         if k == 4:
@@ -227,6 +236,7 @@ def scenario_batch(lib):
                "autotune")
             out = np.full(len(gs) * NCLS[k], -1, np.int64)
             ok(lib.acc_motif_batch_run(c.h, None, P(out), None), "batch_run after autotune")
+            sync(lib)
             if out.reshape(len(gs), -1).tolist() != want:
                 raise AssertionError("batch after autotune")
         out = np.full(len(gs) * NCLS[k], -1, np.int64)
@@ -254,6 +264,7 @@ def scenario_significance(lib):
             st = np.full(1, -1, np.int32)
             ok(lib.acc_swap_randomise(c.h, descs, len(gs), R, q, P(seeds), mode, None, P(out), P(accepted), P(st)),
                "swap_randomise")
+            sync(lib)
             if st[0] != 0:
                 raise AssertionError(f"randomise status {st[0]}")
             off = 0
@@ -275,6 +286,7 @@ def scenario_significance(lib):
     ok(lib.acc_motif_count_batch(c.h, descs2, R + 1, k, None, P(counts), None), "count_batch copies")
     z = np.zeros(NCLS[k], np.float64)
     ok(lib.acc_motif_zscores(P(counts), 1, R + 1, k, None, P(z)), "zscores")
+    sync(lib)
     cnt = counts.reshape(R + 1, -1)
     want = oracle.zscores(cnt[0], cnt[1:])
     if not np.array_equal(z, want, equal_nan=True):
@@ -513,6 +525,7 @@ def scenario_captured_pipeline(lib):
 
     # eager: randomise once, then lay out the batch (each base, then its copies)
     randomise()
+    sync(lib)
     batch, off = [], 0
     for (n, _, _), (rp, cl) in zip(bases, arrays):
         m = len(cl)
@@ -530,6 +543,7 @@ def scenario_captured_pipeline(lib):
         ok(lib.acc_motif_zscores(P(counts), G, R + 1, k, s, P(z)), "zscores")
 
     step()  # eager once more, as a warm-up
+    sync(lib)
     ok(lib.emu_capture_begin(s), "capture begin")
     step()
     ex = lib.emu_capture_end(s)
@@ -556,6 +570,7 @@ def scenario_captured_pipeline(lib):
         z[:] = 0
         status[:] = -1
         ok(lib.emu_graph_replay(ex, s), "graph replay")
+        sync(lib)
         if status[0] != 0:
             raise AssertionError(f"replay {rep}: status {status[0]}")
         if not np.array_equal(out, np.concatenate(want_out)) or accepted.tolist() != want_acc:

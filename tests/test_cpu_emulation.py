@@ -640,11 +640,15 @@ def test_zscore_kernel_equals_oracle_bitwise(emu_bins):
 
 LIB_SCENARIOS = ("modes", "repeats", "host_and_errors", "batch", "significance", "captured_pipeline", "server",
                  "tables", "injected_failures", "misc_api", "fuzz")
-# (scenario, EMU_SCHED): the scenarios that run every kernel, again with the
-# lanes resumed and the blocks run in reverse and in pseudo-random orders
-LIB_RUNS = [(s, 0) for s in LIB_SCENARIOS] + [("modes", 1), ("modes", 7777), ("batch", 1), ("batch", 4242),
-                                               ("captured_pipeline", 1), ("captured_pipeline", 31337),
-                                               ("server", 99), ("fuzz", 5150)]
+# (scenario, EMU_SCHED, EMU_DEFER): the scenarios that run every kernel,
+# again with the lanes resumed and the blocks run in reverse and in
+# pseudo-random orders, and with the device's work deferred until the host
+# waits for it
+LIB_RUNS = [(s, 0, 0) for s in LIB_SCENARIOS] + \
+    [("modes", 1, 0), ("modes", 7777, 0), ("batch", 1, 0), ("batch", 4242, 0), ("captured_pipeline", 1, 0),
+     ("captured_pipeline", 31337, 0), ("server", 99, 0), ("fuzz", 5150, 0)] + \
+    [(s, 0, 1) for s in ("modes", "repeats", "host_and_errors", "batch", "significance", "captured_pipeline",
+                         "server", "misc_api", "fuzz")]
 
 
 @pytest.fixture(scope="session")
@@ -694,6 +698,7 @@ def emu_lib_results(tmp_path_factory):
         while todo and len(running) < width:
             name = todo.pop(0)
             env["EMU_SCHED"] = str(name[1])
+            env["EMU_DEFER"] = str(name[2])
             pr = subprocess.Popen([sys.executable, os.path.join(EMU, "lib_scenarios.py"), so, name[0]], cwd=ROOT,
                                   env=dict(env), stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
             running.append((name, pr))
@@ -707,7 +712,8 @@ def emu_lib_results(tmp_path_factory):
     return results
 
 
-@pytest.mark.parametrize("scenario", LIB_RUNS, ids=lambda r: r[0] + ("" if not r[1] else "-sched%d" % r[1]))
+@pytest.mark.parametrize("scenario", LIB_RUNS,
+                         ids=lambda r: r[0] + ("-sched%d" % r[1] if r[1] else "") + ("-deferred" if r[2] else ""))
 def test_library_on_the_host(emu_lib_results, scenario):
     """The library's C ABI end to end on the host: counts in every mode, the
     launch-graph replay of repeated counts, the host-buffer entry point and
