@@ -20,7 +20,7 @@ sys.path.insert(0, ROOT)
 import oracle  # noqa: E402
 import paper_1203_3415_gb300 as acc  # noqa: E402  (constants, types and the signature table only)
 import synth  # noqa: E402
-from tests.graph_helpers import random_digraph  # noqa: E402
+from tests.graph_helpers import esu_scanned_entries, random_digraph  # noqa: E402
 
 NCLS = {3: 13, 4: 199, 5: 9364}
 
@@ -101,6 +101,10 @@ def scenario_modes(lib):
                 want = oracle.count(n, s, d, k)
                 if rc or st or got.tolist() != want.tolist():
                     raise AssertionError(f"mode {mode} k {k} n {n}: rc {rc} status {st}")
+                # the count mode's work figure equals the same sum over a
+                # plain ESU walk (below 1024 vertices nothing is renumbered)
+                if mode == acc.ACC_MODE_COUNT and c.stats()[6] != esu_scanned_entries(n, s, d, k):
+                    raise AssertionError(f"k {k} n {n}: {c.stats()[6]} entries scanned")
     c.close()
 
 
