@@ -1,26 +1,30 @@
-"""The library's own kernel source, run on the CPU.
+"""The library's own CUDA source, run on the CPU.
 
 tests/emu/shim.h stands in for the CUDA constructs the kernels use: a fiber
-per GPU thread and a barrier of the warp's 32 lanes for every warp
-collective (of the block's threads for __syncthreads), so a lane that skips
-a collective its warp reaches leaves the warp waiting, which the shim
-reports as a hang.  The kernels' code is cut from the CUDA sources between fixed anchors
-and compiled with g++ together with the library's own internal headers; the
-results are compared with the oracle (copies, k = 3, 4, 5 formula counts,
-k = 3, 4, 5 enumeration counts in both modes, under light, heavy and
-queue-full schedules, for single graphs and for sets of graphs) or with the lists a plain host loop writes
-(neighbour-list fill; the whole graph builder, kernels and host launcher,
-against a plain construction of the same pair states, lists and
-renumbering, and on malformed inputs under the address sanitizer; the
-class-table builder against the oracle's table; the Z-scores bit for bit).
-The formula paths and the randomiser run through their host launchers, so
-every block runs whole (all its warps at once); the whole library, built
-for the host against a stand-in CUDA runtime, runs end to end through its C
-ABI (tests/emu/lib_scenarios.py).  The
-enumeration kernels also run with tiny
-shared-memory lists and histogram drain threshold, so their overflow lists
-and drain run on small graphs.  This checks the kernels' logic and warp
-discipline without a GPU; the GPU tests check the compiled kernels."""
+per GPU thread, a barrier of the warp's 32 lanes for every warp collective
+and of the block's threads for __syncthreads, so a lane that skips a
+collective its warp reaches leaves the warp waiting, which the shim reports
+as a hang.  Kernel launches are rewritten into host calls and the sources
+compiled with g++ against the library's own internal headers and a
+stand-in CUDA runtime (tests/emu/fake/cuda_runtime.h).
+
+Kernel by kernel: the randomiser, the k = 3, 4, 5 formula paths and the
+Z-scores through their launchers; the enumeration kernels (both modes,
+light, heavy and queue-full schedules, single graphs and graph sets, and
+with tiny shared-memory lists and drain threshold so their overflow lists
+and drain run on small graphs); the neighbour-list fill; the whole graph
+builder (against a plain construction, and on malformed inputs under the
+address sanitizer); the class-table builder (against the oracle's table).
+Results are compared with the oracle or with what a plain host loop writes.
+
+End to end: the whole library built for the host runs through its C ABI
+(tests/emu/lib_scenarios.py), under the address sanitizer, also under other
+lane and block orders, with device work deferred until the host waits for
+it, and with injected allocation, launch, copy and graph-launch failures.
+
+This checks the kernels' logic, their warp and block discipline and the
+host orchestration without a GPU; the GPU tests check the compiled
+kernels."""
 import os
 import re
 import shutil
