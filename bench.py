@@ -5,16 +5,21 @@ One step = one pass of the whole counting path over one graph already in HBM:
 graph ingest (pair-state matrix, G* neighbour lists), the two enumeration
 launches and the histogram flush, through the C ABI acc_motif_count.  The
 default workload is the directed Chung-Lu graph n=20000, m=100000 (Pareto
-exponent 2.2, degrees capped at 500, 10% reciprocal arcs) at k=4.
+exponent 2.2, degrees capped at 500, 10% reciprocal arcs) at k=4; its line
+is the headline, and the default run adds "sub_records" for every other
+workload of the benchmark set, each timed under its own clock samples: k=3
+on the Erdos-Renyi graph, k=5 on the regulatory-shaped graph, the 4008-graph
+batch (graphs/s, beside one graph per launch) and the request server at 200
+and 100 requests/s (latency percentiles, subgraphs/s).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload NAME]
+                    [--workload NAME] [--headline-only]
 
 N>1 runs one independent replica per GPU (rank), each counting its own copy
 of the workload ("replicas only": the count has no exchange step), and
 reports the units all ranks processed over the slowest rank's time.
-``--impl reference`` times the CPU oracle on a bounded sample of the same
-workload on this host's cores.
+``--impl reference`` times the CPU oracle on this host's cores over the same
+workload (every ESU root in every step).
 """
 from __future__ import annotations
 
@@ -248,7 +253,7 @@ def run_reference(args):
         return 0
     make, k = WORKLOADS[args.workload]
     g = make()
-    roots = (0, min(g.n, args.reference_roots))
+    roots = (0, g.n if args.reference_roots <= 0 else min(g.n, args.reference_roots))
     times, units = [], 0
     threads = 1
     for i in range(args.warmup + args.steps):
@@ -257,7 +262,8 @@ def run_reference(args):
             times.append(dt)
     total = sum(times)
     value = units * len(times) / total
-    sample = f"ESU roots {roots[0]}..{roots[1] - 1} of {g.n} ({units} subgraphs per step)"
+    sample = (f"the whole workload, all {g.n} ESU roots ({units} subgraphs per step)" if roots[1] == g.n else
+              f"ESU roots {roots[0]}..{roots[1] - 1} of {g.n} ({units} subgraphs per step)")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * total / len(times), "higher_is_better": True,
@@ -275,39 +281,66 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------
 
-def run_ours(args):
-    import torch
+class GpuEnv:
+    """Torch, the process group, the device and the library of one rank."""
 
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = dist_init(world, "nccl")
-    dev = torch.device("cuda", local)
+    def __init__(self):
+        import torch
+        self.torch = torch
+        self.world, self.rank, self.local = dist_env()
+        torch.cuda.set_device(self.local)
+        self.dist = dist_init(self.world, "nccl")
+        self.dev = torch.device("cuda", self.local)
+        from paper_1203_3415_gb300 import build as lib_build
+        if self.rank == 0 or self.world == 1:
+            lib_build.build()
+        if self.dist is not None:
+            self.dist.barrier()
+        import paper_1203_3415_gb300 as acc
+        self.acc = acc
 
-    from paper_1203_3415_gb300 import build as lib_build
-    if rank == 0 or world == 1:
-        lib_build.build()
-    if dist is not None:
-        dist.barrier()
-    import paper_1203_3415_gb300 as acc
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
 
-    make, k = WORKLOADS[args.workload]
+
+def issue_peak_gops(env):
+    """Integer issue peak: SMs x 4 schedulers x 32 lanes per clock, at the
+    measured maximum SM clock; (Gop/s, source)."""
+    props = env.torch.cuda.get_device_properties(env.dev)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    sm_max = 2070.0
+    src = "recipe nominal max SM clock 2070 MHz"
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as f:
+            sm_max = float(json.load(f).get("sm_max_mhz", sm_max))
+        src = "SM clock from MEASURED_PEAKS.json"
+    return props.multi_processor_count * 4 * 32 * sm_max * 1e6 / 1e9, src
+
+
+def measure_single(env, workload, steps, warmup, mode="count", schedule="", cpu_baseline=True):
+    """One graph counted per step through acc_motif_count, inputs resident in
+    HBM, L2 flushed between steps; then the same through the host-buffer
+    entry point.  Returns the bench line (without the run-wide keys)."""
+    torch, acc, dev, dist = env.torch, env.acc, env.dev, env.dist
+    make, k = WORKLOADS[workload]
     g = make()
     rowptr_np, col_np = g.csr()
     rowptr = torch.from_numpy(rowptr_np).to(dev)
     col = torch.from_numpy(col_np).to(dev)
     counts = torch.zeros(acc.NUM_CLASSES[k], dtype=torch.int64, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
-    counter = acc.Counter(local)
+    counter = acc.Counter(env.local)
     counter.set_mode({"count": acc.ACC_MODE_COUNT, "enumerate": acc.ACC_MODE_ENUMERATE,
-                      "formula": acc.ACC_MODE_FORMULA}[args.mode])
+                      "formula": acc.ACC_MODE_FORMULA}[mode])
     counter.prepare(k)
-    if args.schedule:
-        light, target = (int(x) for x in args.schedule.split(","))
+    if schedule:
+        light, target = (int(x) for x in schedule.split(","))
         counter.set_schedule(light, target)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         flush.fill_(1)
         counter.count(rowptr, col, g.n, k, counts=counts, status=status, stream=stream)
     torch.cuda.synchronize(dev)
@@ -315,7 +348,7 @@ def run_ours(args):
         raise RuntimeError(f"count failed: {acc.acc_strerror(int(status.item()))}")
     stats = counter.last_stats()
     n_k = int(counts.sum().item())
-    gold = golden_counts(args.workload)
+    gold = golden_counts(workload)
     parity = None
     if gold is not None:
         parity = bool(np.array_equal(counts.cpu().numpy(), gold[1]))
@@ -323,14 +356,14 @@ def run_ours(args):
     # timed region: K steps, each bracketed by events on the launching stream;
     # L2 flushed (256 MiB write) between steps, outside the events.  Repeated
     # counts replay the library's launch graph of the whole sequence.
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    sampler = ClockSampler(local) if rank == 0 else None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    sampler = ClockSampler(env.local) if env.rank == 0 else None
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize(dev)
     if sampler:
         sampler.start()
-    for i in range(args.steps):
+    for i in range(steps):
         flush.fill_(i & 0xFF)
         ev[i][0].record(stream)
         counter.count(rowptr, col, g.n, k, counts=counts, status=status, stream=stream)
@@ -346,7 +379,7 @@ def run_ours(args):
     # launched one by one)
     counter.set_timing(True)
     build_ms, enum_ms, p1_ms, p2_ms = [], [], [], []
-    for i in range(max(3, min(args.steps, 20))):
+    for i in range(max(3, min(steps, 20))):
         flush.fill_(i & 0xFF)
         counter.count(rowptr, col, g.n, k, counts=counts, status=status, stream=stream)
         b, e, e1, e2 = counter.last_timing()
@@ -361,7 +394,7 @@ def run_ours(args):
         raise RuntimeError("timed steps disagree with the warm-up result")
 
     max_s = reduce_max(dist, local_s, dev)
-    units = reduce_sum(dist, float(n_k) * args.steps, dev)
+    units = reduce_sum(dist, float(n_k) * steps, dev)
     value = whole_job_rate(units, max_s)
 
     # end to end through the public host-buffer entry point: pinned host
@@ -369,7 +402,7 @@ def run_ours(args):
     h_rowptr = torch.from_numpy(rowptr_np).pin_memory()
     h_col = torch.from_numpy(col_np).pin_memory()
     h_counts = torch.zeros(acc.NUM_CLASSES[k], dtype=torch.int64).pin_memory()
-    e2e_steps = max(3, min(args.steps, 20))
+    e2e_steps = max(3, min(steps, 20))
     # two untimed calls: the second captures the launch graph the timed calls replay
     for _ in range(2):
         counter.count_host(h_rowptr, h_col, g.n, k, counts=h_counts)
@@ -384,53 +417,39 @@ def run_ours(args):
         raise RuntimeError("host-buffer count differs from the device count")
     e2e_max = reduce_max(dist, e2e_t, dev)
     e2e_units = reduce_sum(dist, float(n_k) * e2e_steps, dev)
+    counter.close()
+    if env.rank != 0:
+        return None
 
-    if rank != 0:
-        counter.close()
-        if dist is not None:
-            dist.destroy_process_group()
-        return 0
-
-    props = torch.cuda.get_device_properties(dev)
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    sm_max = 2070.0
-    peak_src = "recipe nominal max SM clock 2070 MHz"
-    if os.path.exists(peaks_path):
-        with open(peaks_path) as f:
-            sm_max = float(json.load(f).get("sm_max_mhz", sm_max))
-        peak_src = "SM clock from MEASURED_PEAKS.json"
-    # issue peak: SMs x 4 schedulers x 32 lanes per clock
-    peak_gops = props.multi_processor_count * 4 * 32 * sm_max * 1e6 / 1e9
+    peak_gops, peak_src = issue_peak_gops(env)
     enum_s = statistics.mean(enum_ms) / 1000.0
     leaf_achieved = ops_per_subgraph(k) * n_k / enum_s / 1e9
-    if args.mode == "count":
+    if mode == "count":
         units, per_unit = int(stats["scanned_entries"]), ops_per_scanned_entry(k)
         unit_name = "neighbour entries scanned by the last two levels"
-    elif args.mode == "formula" and k == 3:
+    elif mode == "formula" and k == 3:
         units, per_unit = n_k, ops_per_subgraph(k)
         unit_name = "classified subgraphs (leaf-equivalent: the formula path visits none)"
     else:
         units, per_unit = n_k, ops_per_subgraph(k)
         unit_name = "classified subgraphs"
     achieved = per_unit * units / enum_s / 1e9
-    traffic, counters = profiled_counters(args.workload, args.mode)
+    traffic, counters = profiled_counters(workload, mode)
 
     # CPU baseline: the oracle on this host's cores, the whole workload
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if env.world == 1 and cpu_baseline:
         units_cpu, dt, threads = time_oracle(g, k, (0, g.n))
         cpu = {"value": units_cpu / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"the whole workload, all {g.n} ESU roots ({units_cpu} subgraphs), one pass, "
                          f"{dt:.2f} s"}
-
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1000.0 * max_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": args.workload, "k": k, "n": g.n, "m": g.m, "subgraphs_per_step": n_k,
-                   "mode": args.mode,
+    return {
+        "value": value, "unit": UNIT, "steps": steps, "warmup": warmup,
+        "ms_per_step": 1000.0 * max_s / steps,
+        "config": {"workload": workload, "k": k, "n": g.n, "m": g.m, "subgraphs_per_step": n_k,
+                   "mode": mode,
                    "l2": "flushed between timed steps (256 MiB device write)",
-                   "parallelism": f"replicas{world}"},
+                   "parallelism": f"replicas{env.world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved / peak_gops, "traffic": traffic,
                      "kernel": f"k_enum<{k}> (phase 1 + phase 2)",
@@ -445,7 +464,7 @@ def run_ours(args):
         "e2e": {"value": whole_job_rate(e2e_units, e2e_max), "unit": UNIT,
                 "h2d_bytes_per_step": int(rowptr_np.nbytes + col_np.nbytes),
                 "d2h_bytes_per_step": int(acc.NUM_CLASSES[k] * 8)},
-        "gpu_launches": int(stats["launches"]) * args.steps,
+        "gpu_launches": int(stats["launches"]) * steps,
         "clocks": clocks,
         "stages_ms": {"how": "separate pass, per-stage events, kernels launched one by one",
                       "build": statistics.mean(build_ms), "enumerate": statistics.mean(enum_ms),
@@ -455,41 +474,90 @@ def run_ours(args):
         "work": {"chunks": stats["chunks"], "undirected_edges": stats["undirected_edges"],
                  "max_degree": stats["max_degree"], "blocks": stats["blocks"]},
     }
-    print(json.dumps(line), flush=True)
-    counter.close()
-    if dist is not None:
-        dist.destroy_process_group()
+
+
+def bench_line(env, rec, steps, warmup):
+    """The contract's JSON line around one measurement record."""
+    line = {"metric": METRIC, "value": rec["value"], "unit": rec["unit"], "n_gpus": env.world, "steps": steps,
+            "warmup": warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic"}
+    line.update({k: v for k, v in rec.items() if k not in line})
+    return line
+
+
+def run_ours(args):
+    env = GpuEnv()
+    rec = measure_single(env, args.workload, args.steps, args.warmup, args.mode, args.schedule,
+                         not args.no_cpu_baseline)
+    subs = None
+    if args.workload == DEFAULT_WORKLOAD and not args.headline_only:
+        # every other workload of the benchmark set, each under its own
+        # clock samples, in the same run
+        subs = {}
+        for w in ("er_n1000_m5000_k3", "regulatory_n5000_m15000_k5"):
+            r = measure_single(env, w, args.steps, args.warmup, "count", "", not args.no_cpu_baseline)
+            if r is not None:
+                subs[w] = r
+        r = measure_batch(env, max(3, min(args.steps, 10)), args.warmup, not args.no_cpu_baseline, cpu_budget_s=5.0)
+        if r is not None:
+            subs[BATCH_WORKLOAD] = r
+        for rate in (200.0, 100.0):
+            r = measure_serving(env, args.sub_serve_seconds, rate, args.slots, args.mem_budget_gb, args.serve_policy,
+                                args.serve_aging_s)
+            if r is not None:
+                subs[f"{SERVING_WORKLOAD}_{int(rate)}_per_s"] = r
+    if env.rank == 0:
+        line = bench_line(env, rec, args.steps, args.warmup)
+        if subs is not None:
+            line["sub_records"] = subs
+        print(json.dumps(line), flush=True)
+    env.close()
     return 0
 
 
-def run_batch_bench(args):
-    """Batched k=4 workload: 8 Chung-Lu bases x (1 + 500 randomisations) =
-    4008 graphs counted by one prepared batch, replayed from a captured CUDA
-    graph; compared with one acc_motif_count launch sequence per graph."""
-    import torch
-
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = dist_init(world, "nccl")
-    dev = torch.device("cuda", local)
-    from paper_1203_3415_gb300 import build as lib_build
-    if rank == 0 or world == 1:
-        lib_build.build()
-    if dist is not None:
-        dist.barrier()
-    import paper_1203_3415_gb300 as acc
-
+def batch_graphs():
     graphs = []
     for b in range(synth.BATCH_BASES):
         base = synth.batch_base(b)
         graphs.append(base)
         graphs.extend(synth.batch_randomisation(base, b, i) for i in range(synth.BATCH_RANDOMISATIONS))
+    return graphs
+
+
+def batch_cpu_baseline(graphs, budget_s):
+    """The oracle counting graphs of the batch (taken round-robin over the
+    bases, so the sample has the batch's size mix) until about budget_s
+    seconds; graphs/s."""
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    oracle.table(4)
+    R1 = synth.BATCH_RANDOMISATIONS + 1
+    order = [b * R1 + i for i in range(R1) for b in range(synth.BATCH_BASES)]
+    t0 = time.perf_counter()
+    done = 0
+    while done < len(order) and time.perf_counter() - t0 < budget_s:
+        g = graphs[order[done]]
+        oracle.count(g.n, g.src, g.dst, 4, threads=threads)
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "graphs/s", "cores": threads, "kind": "oracle",
+            "sample": f"{done} of the {len(graphs)} graphs (round-robin over the {synth.BATCH_BASES} bases), "
+                      f"ESU count each, {dt:.1f} s"}
+
+
+def measure_batch(env, steps, warmup, cpu_baseline=True, cpu_budget_s=10.0):
+    """Batched k=4 workload: 8 Chung-Lu bases x (1 + 500 randomisations) =
+    4008 graphs counted by one prepared batch, replayed from a captured CUDA
+    graph; compared with one acc_motif_count launch sequence per graph."""
+    torch, acc, dev, dist = env.torch, env.acc, env.dev, env.dist
+    graphs = batch_graphs()
     B, R1 = len(graphs), synth.BATCH_RANDOMISATIONS + 1
     tens = []
     for g in graphs:
         r, c = g.csr()
         tens.append((torch.from_numpy(r).to(dev), torch.from_numpy(c).to(dev), g.n))
-    counter = acc.Counter(local)
+    counter = acc.Counter(env.local)
     stream = torch.cuda.Stream(dev)
     counts = torch.zeros((B, 199), dtype=torch.int64, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -498,18 +566,18 @@ def run_batch_bench(args):
         counter.prepare_batch(tens, 4, stream=stream)
         # the schedule is tuned once per prepared batch, outside the timed region
         sched = counter.autotune_batch(stream=stream)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             counter.run_batch(counts=counts, status=status, stream=stream)
     torch.cuda.synchronize(dev)
     if int(status.item()) != 0:
         raise RuntimeError(f"batch failed: {acc.acc_strerror(int(status.item()))}")
     eager = counts.clone()
+    stats = counter.last_stats()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
         counter.run_batch(counts=counts, status=status, stream=stream)
-    steps = max(1, args.steps)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    sampler = ClockSampler(local) if rank == 0 else None
+    sampler = ClockSampler(env.local) if env.rank == 0 else None
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -532,6 +600,15 @@ def run_batch_bench(args):
     max_s = reduce_max(dist, local_s, dev)
     value = whole_job_rate(reduce_sum(dist, float(B) * steps, dev), max_s)
     sub_rate = whole_job_rate(reduce_sum(dist, float(total) * steps, dev), max_s)
+    # the enumeration stage alone (per-stage events, launched one by one)
+    counter.set_timing(True)
+    enum_ms = []
+    with torch.cuda.stream(stream):
+        for i in range(3):
+            flush.fill_(i & 0xFF)
+            counter.run_batch(counts=counts, status=status, stream=stream)
+            enum_ms.append(counter.last_timing()[1])
+    counter.set_timing(False)
     # Z-scores of each base against its randomisations
     z = counter.zscores(counts, synth.BATCH_BASES, R1, 4)
     torch.cuda.synchronize(dev)
@@ -549,43 +626,57 @@ def run_batch_bench(args):
         t1.record(stream)
     torch.cuda.synchronize(dev)
     single_rate = B / (t0.elapsed_time(t1) / 1000.0)
-    if rank != 0:
-        counter.close()
-        if dist is not None:
-            dist.destroy_process_group()
-        return 0
+    counter.close()
+    if env.rank != 0:
+        return None
     gold = os.path.join(ROOT, "tests", "golden", "batch_k4.txt")
     parity = None
     if os.path.exists(gold):
-        import hashlib
         rows = [ln.split() for ln in open(gold) if ln.strip() and not ln.startswith("#")]
         host = counts.cpu().numpy()
+        zh = z.cpu().numpy()
         parity = all(
             hashlib.sha256(np.ascontiguousarray(host[b * R1:(b + 1) * R1], dtype="<i8").tobytes()).hexdigest()
-            == rows[b][4] for b in range(len(rows)))
-    line = {
-        "metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": steps,
-        "warmup": args.warmup, "ms_per_step": 1000.0 * max_s / steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            == rows[b][4]
+            and all(float(x).hex() == w or (np.isnan(x) and w == "nan") for x, w in zip(zh[b], rows[b][6:]))
+            for b in range(len(rows)))
+    peak_gops, peak_src = issue_peak_gops(env)
+    enum_s = statistics.mean(enum_ms) / 1000.0
+    scanned = int(stats["scanned_entries"])
+    achieved = ops_per_scanned_entry(4) * scanned / enum_s / 1e9
+    cpu = batch_cpu_baseline(graphs, cpu_budget_s) if (env.world == 1 and cpu_baseline) else None
+    return {
+        "value": value, "unit": "graphs/s", "steps": steps, "warmup": warmup, "ms_per_step": 1000.0 * max_s / steps,
         "config": {"workload": BATCH_WORKLOAD, "k": 4, "graphs": B, "bases": synth.BATCH_BASES,
                    "randomisations_per_base": synth.BATCH_RANDOMISATIONS, "subgraphs_per_step": total,
                    "l2": "flushed between timed steps (256 MiB device write)",
                    "launch": "prepared batch replayed from a captured CUDA graph",
                    "schedule": {"light": sched[0], "target": sched[1], "autotuned": True},
-                   "parallelism": f"replicas{world}"},
+                   "parallelism": f"replicas{env.world}"},
         "subgraphs_per_s": sub_rate,
         "one_graph_per_launch": {"value": single_rate, "unit": "graphs/s",
                                  "how": "acc_motif_count per graph, same stream, same GPU"},
         "batched_over_single": value / single_rate,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
+                     "frac": achieved / peak_gops, "traffic": None, "kernel": "k_enum<4> (phase 1 + phase 2)",
+                     "work_unit": "neighbour entries scanned by the last two levels", "units_per_launch": scanned,
+                     "ops_per_unit": ops_per_scanned_entry(4), "peak_source": peak_src,
+                     "enumerate_ms": statistics.mean(enum_ms)},
+        "cpu_baseline": cpu,
         "zscores_finite": int(np.isfinite(z.cpu().numpy()).sum()),
-        "gpu_launches": 16 * steps,
+        "gpu_launches": int(stats["launches"]) * steps,
         "clocks": clocks,
         "parity_vs_stored_oracle_counts": parity,
     }
-    print(json.dumps(line), flush=True)
-    counter.close()
-    if dist is not None:
-        dist.destroy_process_group()
+
+
+def run_batch_bench(args):
+    env = GpuEnv()
+    steps = max(1, args.steps)
+    rec = measure_batch(env, steps, args.warmup, not args.no_cpu_baseline)
+    if env.rank == 0:
+        print(json.dumps(bench_line(env, rec, steps, args.warmup)), flush=True)
+    env.close()
     return 0
 
 
@@ -757,29 +848,18 @@ def significance_cpu_baseline(bases, budget_s=10.0):
             "sample": f"{done} randomised copies of base {b} (n={g.n}, m={g.m}): swaps and ESU count each"}
 
 
-def run_serving_bench(args):
+def measure_serving(env, window_s, rate, slots, mem_budget_gb, policy, aging_s):
     """Serving workload: 64 resident directed Chung-Lu graphs (n log-uniform
     in [100, 50000], mean out-degree 4-10), a Poisson stream of requests at
-    200/s with k in {3: 50%, 4: 35%, 5: 15%}, replayed in real time against
-    the request server; latency = completion - scheduled arrival."""
-    import torch
-
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = dist_init(world, "nccl")
-    dev = torch.device("cuda", local)
-    from paper_1203_3415_gb300 import build as lib_build
-    if rank == 0 or world == 1:
-        lib_build.build()
-    if dist is not None:
-        dist.barrier()
-    import paper_1203_3415_gb300 as acc
-
+    `rate` per second with k in {3: 50%, 4: 35%, 5: 15%}, replayed in real
+    time against the request server; latency = completion - scheduled
+    arrival."""
+    torch, acc, dev, dist = env.torch, env.acc, env.dev, env.dist
     specs = synth.serving_pool_specs()
     graphs = [synth.serving_graph(sp) for sp in specs]
-    reqs = synth.serving_requests(duration_s=args.serve_seconds)
-    srv = acc.Server(local, slots=args.slots, mem_budget_bytes=int(args.mem_budget_gb * (1 << 30)))
-    srv.set_policy(acc.ACC_SERVE_FIFO if args.serve_policy == "fifo" else acc.ACC_SERVE_SHORTEST, args.serve_aging_s)
+    reqs = synth.serving_requests(duration_s=window_s, rate=rate)
+    srv = acc.Server(env.local, slots=slots, mem_budget_bytes=int(mem_budget_gb * (1 << 30)))
+    srv.set_policy(acc.ACC_SERVE_FIFO if policy == "fifo" else acc.ACC_SERVE_SHORTEST, aging_s)
     tens = []
     for g in graphs:
         r, c = g.csr()
@@ -792,24 +872,38 @@ def run_serving_bench(args):
     srv.drain()
     if dist is not None:
         dist.barrier()
-    sampler = ClockSampler(local) if rank == 0 else None
+    sampler = ClockSampler(env.local) if env.rank == 0 else None
     if sampler:
         sampler.start()
     t0 = time.perf_counter()
     rids, arrivals = [], []
+    busy, t_last, was_busy = 0.0, 0.0, False
     i = 0
     while i < len(reqs):
         now = time.perf_counter() - t0
+        if was_busy:
+            busy += now - t_last
+        t_last = now
         while i < len(reqs) and reqs[i][0] <= now:
             t_arr, gid, k = reqs[i]
             rids.append(srv.submit(ids[gid], k))
             arrivals.append((t_arr, now, gid, k))
             i += 1
-        srv.progress()
+        running, _ = srv.progress()
+        was_busy = running > 0
         if i < len(reqs):
             wait = reqs[i][0] - (time.perf_counter() - t0)
             if wait > 0.0005:
                 time.sleep(min(wait, 0.001))
+    while True:
+        now = time.perf_counter() - t0
+        if was_busy:
+            busy += now - t_last
+        t_last = now
+        running, queued = srv.progress()
+        was_busy = running > 0
+        if running == 0 and queued == 0:
+            break
     srv.drain()
     t_end = time.perf_counter() - t0
     clocks = sampler.stop() if sampler else None
@@ -828,28 +922,35 @@ def run_serving_bench(args):
     lat = np.array(lat)
     local_rate = units / t_end
     value = reduce_sum(dist, local_rate, dev) if dist is not None else local_rate
-    if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
-        return 0
-    pct = lambda a, q: float(np.percentile(a, q) * 1000.0) if len(a) else None
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(rids),
-        "warmup": 3, "ms_per_step": 1000.0 * t_end / max(1, len(rids)), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+    if env.rank != 0:
+        return None
+    pct = lambda a, q: float(np.percentile(a, q) * 1000.0) if len(a) else None  # noqa: E731
+    return {
+        "value": value, "unit": UNIT, "steps": len(rids), "warmup": 3,
+        "ms_per_step": 1000.0 * t_end / max(1, len(rids)),
         "config": {"workload": SERVING_WORKLOAD, "graphs": len(graphs), "requests": len(rids),
-                   "arrival_rate_per_s": 200, "window_s": args.serve_seconds, "slots": args.slots,
-                   "policy": args.serve_policy, "aging_s": args.serve_aging_s,
-                   "mem_budget_gb": args.mem_budget_gb, "parallelism": f"replicas{world}"},
+                   "arrival_rate_per_s": rate, "window_s": window_s, "slots": slots,
+                   "policy": policy, "aging_s": aging_s,
+                   "mem_budget_gb": mem_budget_gb, "parallelism": f"replicas{env.world}"},
         "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": pct(lat, 100),
                        "by_k_p50": {str(k): pct(np.array(v), 50) for k, v in by_k.items()},
                        "by_k_p99": {str(k): pct(np.array(v), 99) for k, v in by_k.items()}},
-        "completed_per_s": len(lat) / t_end, "failed": failed, "wall_s": t_end,
+        "completed_per_s": len(lat) / t_end, "offered_per_s": len(rids) / window_s,
+        "failed": failed, "wall_s": t_end,
+        "gpu_busy_frac": busy / t_end if t_end > 0 else None,
+        "subgraphs_served": units,
         "clocks": clocks,
+        "parity": "every served result equals the oracle's: tests/test_gpu_serving.py",
     }
-    print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+
+
+def run_serving_bench(args):
+    env = GpuEnv()
+    rec = measure_serving(env, args.serve_seconds, args.serve_rate, args.slots, args.mem_budget_gb,
+                          args.serve_policy, args.serve_aging_s)
+    if env.rank == 0:
+        print(json.dumps(bench_line(env, rec, rec["steps"], 3)), flush=True)
+    env.close()
     return 0
 
 
@@ -863,10 +964,15 @@ def main():
                                                                SIGNIFICANCE_WORKLOAD],
                     default=DEFAULT_WORKLOAD)
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="serving: arrival window")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="serving: Poisson arrival rate per second")
+    ap.add_argument("--sub-serve-seconds", type=float, default=5.0,
+                    help="serving window of the default run's serving sub-records (200 and 100 requests/s)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="default workload: print the headline line without the other workloads' sub-records")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent requests")
     ap.add_argument("--mem-budget-gb", type=float, default=96.0, help="serving: workspace budget")
-    ap.add_argument("--reference-roots", type=int, default=1000,
-                    help="reference arm: ESU roots per step (bounded CPU sample)")
+    ap.add_argument("--reference-roots", type=int, default=0,
+                    help="reference arm: ESU roots per step (0: all roots, the whole workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-policy", choices=["shortest", "fifo"], default="shortest",
                     help="serving admission order: smallest aged work estimate first, or submission order")

@@ -76,19 +76,22 @@ ACC_API int acc_motif_num_classes(int k);
 
 /*
  * Create a context on CUDA device `device` (the device is made current for
- * the calling thread).  The context owns the code -> class tables (built on
- * the device on first use of each k) and a grow-only workspace.
- * *out receives the handle.  Errors: ACC_ERR_ARG (out NULL), ACC_ERR_CUDA.
+ * the calling thread).  The context owns a grow-only workspace.  The code ->
+ * class tables are shared by every context on the device: built on the
+ * device at the first use of each k by any of them, freed with the last
+ * context that used them.  *out receives the handle.  Errors: ACC_ERR_ARG
+ * (out NULL), ACC_ERR_CUDA.
  */
 ACC_API int acc_ctx_create(acc_ctx **out, int device);
 
-/* Release a context and all its device memory (NULL is a no-op).  Waits
+/* Release a context and all its device memory (NULL is a no-op; the shared
+ * class tables are released with the last context on the device).  Waits
  * for the context's outstanding work. */
 ACC_API void acc_ctx_destroy(acc_ctx *ctx);
 
 /*
- * Build (once) and cache the code -> class table for k on the context's
- * device, stream-ordered on `stream`, then wait for it.  Counting calls do
+ * Build (once per device) and cache the code -> class table for k on the
+ * context's device, stream-ordered on `stream`, then wait for it.  Counting calls do
  * this themselves on first use; call it ahead to keep the one-time cost
  * (largest for k = 5: 2^20 codes x 120 relabellings) out of a timed region.
  * Errors: ACC_ERR_ARG, ACC_ERR_K, ACC_ERR_NOMEM, ACC_ERR_CUDA.
@@ -115,9 +118,22 @@ ACC_API int acc_motif_prepare(acc_ctx *ctx, int k, void *stream);
  *            a malformed graph, in which case d_counts is unspecified).  When
  *            NULL the call waits for its own work and returns that status.
  *
- * Host-checked errors (returned before anything is enqueued): ACC_ERR_ARG,
- * ACC_ERR_K, ACC_ERR_INPUT (negative sizes), ACC_ERR_TOO_LARGE,
- * ACC_ERR_NOMEM, ACC_ERR_CUDA.
+ * Overflow guard (the paper keeps its counts in "integer" variables; here
+ * they are int64): before enumerating, the device bounds N_k from the G*
+ * degrees (every connected k-set has a spanning tree; each tree shape is
+ * counted from its centre, every further neighbour taken at the largest
+ * degree D: k = 3 sum C(d,2); k = 4 sum C(d,3) + (D-1) sum d(d-1)/2;
+ * k = 5 sum C(d,4) + (D-1) sum d(d-1)(d-2)/2 + (D-1)^2 sum d^2/2; and never
+ * above C(n,k)).  If the bound exceeds 2^62 the status becomes
+ * ACC_ERR_OVERFLOW, nothing is enumerated and d_counts is unspecified.  The
+ * bound is loose for hubs with many low-degree neighbours, so such a graph
+ * can be refused although its exact counts would fit: for example an out-star
+ * with 50000 leaves at k = 5 (bound 6.5e18, exact N_5 = C(50000, 4) = 2.6e17).
+ *
+ * Device-found errors: ACC_ERR_INPUT, ACC_ERR_OVERFLOW (above),
+ * ACC_ERR_INTERNAL.  Host-checked errors (returned before anything is
+ * enqueued): ACC_ERR_ARG, ACC_ERR_K, ACC_ERR_INPUT (negative sizes),
+ * ACC_ERR_TOO_LARGE, ACC_ERR_NOMEM, ACC_ERR_CUDA.
  */
 ACC_API int acc_motif_count(acc_ctx *ctx, const int64_t *d_rowptr, const int32_t *d_col, int32_t n,
                     int64_t m, int k, void *stream, int64_t *d_counts, int32_t *d_status);
@@ -149,10 +165,13 @@ typedef struct {
 
 /*
  * Prepare a batch of B graphs (h_graphs: host array of B descriptors) for
- * k: validates sizes, lays out every graph's buffers in the context's
- * workspace, uploads the descriptors and builds the table for k; waits.  The
- * graphs' device arrays must stay valid and unchanged until the batch's last
- * acc_motif_batch_run.  Preparing replaces the previous batch.  Errors:
+ * k: first waits for `stream` (an earlier run on it may still read the
+ * previous batch's descriptors), then validates sizes, lays out every graph's
+ * buffers in the context's workspace, uploads the descriptors and builds the
+ * table for k; waits.  The graphs' device arrays must stay valid and
+ * unchanged until the batch's last acc_motif_batch_run.  Preparing replaces
+ * the previous batch; a run of the previous batch still in flight on another
+ * stream must be waited for by the caller first.  Errors:
  * ACC_ERR_ARG, ACC_ERR_K, ACC_ERR_INPUT, ACC_ERR_TOO_LARGE (some n above
  * ACC_MAX_N), ACC_ERR_OVERFLOW (more than 2^31-1 vertices or arcs in total),
  * ACC_ERR_NOMEM, ACC_ERR_CUDA.
@@ -162,10 +181,14 @@ ACC_API int acc_motif_batch_prepare(acc_ctx *ctx, const acc_graph_desc *h_graphs
 /*
  * Count every graph of the prepared batch: d_counts is device
  * int64[B * num_classes(k)], row g = graph g, overwritten.  d_status as in
- * acc_motif_count.  With d_status non-NULL the call only enqueues kernels
+ * acc_motif_count (the overflow guard bounds every graph of the batch by
+ * the degree sums of all of them, and by C(largest n, k)).  With d_status non-NULL the call only enqueues kernels
  * (no allocation, no copy, no wait), so it can be captured into a CUDA graph
- * and replayed; a captured run stays valid while no later call on the
- * context grows its workspace (prepare the largest batch first).
+ * and replayed.  A captured run stays valid until the next
+ * acc_motif_batch_prepare on the context (which rewrites the descriptors the
+ * capture reads; the batch's sizes are baked into the captured launches) or
+ * until a later call on the context grows its workspace; capture again after
+ * either.
  */
 ACC_API int acc_motif_batch_run(acc_ctx *ctx, void *stream, int64_t *d_counts, int32_t *d_status);
 
@@ -425,16 +448,23 @@ ACC_API int acc_motif_last_timing(acc_ctx *ctx, float *h_ms);
  *  k             3, 4 or 5 (ACC_ERR_K otherwise).
  *  stream        cudaStream_t (void*); the call only enqueues work.
  *  d_table       device int16[2^(k(k-1))]: receives the same table as
- *                acc_motif_copy_table (-1 = not weakly connected).
+ *                acc_motif_copy_table (-1 = not weakly connected).  An entry
+ *                of -2 would mark a canonical code ranked past the last class
+ *                (a library bug; the context entry points check for it and
+ *                fail with ACC_ERR_INTERNAL, this one leaves the check to the
+ *                caller: every entry is >= -1 in a correct table).
  *  d_class_code  device uint32[num_classes(k)]: canonical code of each class,
  *                as acc_motif_class_code.
  *
- * Working memory: a fixed 8 MiB array inside the library (room for the
- * 2^20 codes of k = 5; anything larger is rejected with ACC_ERR_TOO_LARGE).
- * Every GPU that loads the library holds those 8 MiB until the process
- * exits.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array: each call writes
+ * Working memory: a fixed array of 8 MiB and 8 KiB inside the library (room
+ * for the 2^20 codes of k = 5; anything larger is rejected with
+ * ACC_ERR_TOO_LARGE).  Every GPU that loads the library holds it until the
+ * process exits.  A call looks up the array's device address (cudaGetSymbolAddress)
+ * on the current device, except while `stream` is being captured: then it
+ * reuses the address an earlier call on that device found, and fails with
+ * ACC_ERR_CUDA if there was none.  So make one call on each device before any
+ * stream capture, and one more after a cudaDeviceReset (which reloads the
+ * library's device image, possibly elsewhere).  All calls share the array: each call writes
  * every word of it that it reads, so no state carries over, but calls that
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.

@@ -3,6 +3,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -39,34 +40,49 @@ int grow(T **p, size_t *cap, size_t need) {
 
 bool valid_k(int k) { return k >= 3 && k <= 5; }
 
-int ensure_lut(acc_ctx *c, int k, cudaStream_t s) {
-    if (c->lut[k]) return ACC_OK;
+// Class tables are built once per device and k and shared by every context
+// on that device (the request server runs one context per slot); each
+// context holds a reference, and the last one released frees the table.
+struct SharedTable {
+    int refs = 0;
+    int16_t *lut = nullptr, *lut_sv = nullptr;
+    uint32_t *class_code = nullptr;
+    int16_t *lut_host = nullptr;
+    uint32_t *class_code_host = nullptr;
+};
+constexpr int kTableDevices = 64;
+SharedTable g_tables[kTableDevices][6];
+std::mutex g_tables_mu;
+
+// Build the table for k on stream s (waits for it) into t; on failure t is
+// left empty.
+int build_table(int k, cudaStream_t s, SharedTable &t) {
     const size_t ncodes = size_t(1) << code_bits(k);
     const int ncls = num_classes(k);
     uint32_t *canon = nullptr;
     int *rank = nullptr;
     int16_t *lut = nullptr, *lut_sv = nullptr;
     uint32_t *cc = nullptr;
+    int16_t *lut_host = new (std::nothrow) int16_t[ncodes];
+    uint32_t *cc_host = new (std::nothrow) uint32_t[ncls];
     int rc = ACC_ERR_NOMEM;
-    c->lut_host[k] = new (std::nothrow) int16_t[ncodes];
-    c->class_code_host[k] = new (std::nothrow) uint32_t[ncls];
-    if (!c->lut_host[k] || !c->class_code_host[k]) goto fail;
-    if (!ok(cudaMalloc(&canon, ncodes * 4)) || !ok(cudaMalloc(&rank, ncodes * 4)) ||
+    if (!lut_host || !cc_host) goto fail;
+    if (!ok(cudaMalloc(&canon, ncodes * 4)) || !ok(cudaMalloc(&rank, (size_t)rank_ints(k) * 4)) ||
         !ok(cudaMalloc(&lut, ncodes * 2)) || !ok(cudaMalloc(&lut_sv, ncodes * 2)) ||
         !ok(cudaMalloc(&cc, ncls * 4)))
         goto fail;
     rc = launch_build_lut(k, canon, rank, lut, cc, lut_sv, s);
     if (rc < 0) goto fail;
     rc = ACC_ERR_CUDA;
-    if (!ok(cudaMemcpyAsync(c->lut_host[k], lut, ncodes * 2, cudaMemcpyDeviceToHost, s))) goto fail;
-    if (!ok(cudaMemcpyAsync(c->class_code_host[k], cc, ncls * 4, cudaMemcpyDeviceToHost, s))) goto fail;
+    if (!ok(cudaMemcpyAsync(lut_host, lut, ncodes * 2, cudaMemcpyDeviceToHost, s))) goto fail;
+    if (!ok(cudaMemcpyAsync(cc_host, cc, ncls * 4, cudaMemcpyDeviceToHost, s))) goto fail;
     if (!ok(cudaStreamSynchronize(s))) goto fail;
     {
         // the table must use every class index exactly up to ncls - 1
         int mx = -1;
         for (size_t i = 0; i < ncodes; i++) {
-            if (c->lut_host[k][i] < -1) mx = 1 << 20;
-            if (c->lut_host[k][i] > mx) mx = c->lut_host[k][i];
+            if (lut_host[i] < -1) mx = 1 << 20;
+            if (lut_host[i] > mx) mx = lut_host[i];
         }
         if (mx != ncls - 1) {
             rc = ACC_ERR_INTERNAL;
@@ -75,9 +91,11 @@ int ensure_lut(acc_ctx *c, int k, cudaStream_t s) {
     }
     cudaFree(canon);
     cudaFree(rank);
-    c->lut[k] = lut;
-    c->lut_sv[k] = lut_sv;
-    c->class_code_dev[k] = cc;
+    t.lut = lut;
+    t.lut_sv = lut_sv;
+    t.class_code = cc;
+    t.lut_host = lut_host;
+    t.class_code_host = cc_host;
     return ACC_OK;
 fail:
     cudaGetLastError();
@@ -86,11 +104,48 @@ fail:
     cudaFree(lut);
     cudaFree(lut_sv);
     cudaFree(cc);
-    delete[] c->lut_host[k];
-    delete[] c->class_code_host[k];
-    c->lut_host[k] = nullptr;
-    c->class_code_host[k] = nullptr;
+    delete[] lut_host;
+    delete[] cc_host;
     return rc;
+}
+
+int ensure_lut(acc_ctx *c, int k, cudaStream_t s) {
+    if (c->lut[k]) return ACC_OK;
+    if (c->device < 0 || c->device >= kTableDevices) return ACC_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_tables_mu);
+    SharedTable &t = g_tables[c->device][k];
+    if (t.refs == 0) {
+        const int rc = build_table(k, s, t);
+        if (rc) return rc;
+    }
+    t.refs++;
+    c->lut[k] = t.lut;
+    c->lut_sv[k] = t.lut_sv;
+    c->class_code_dev[k] = t.class_code;
+    c->lut_host[k] = t.lut_host;
+    c->class_code_host[k] = t.class_code_host;
+    return ACC_OK;
+}
+
+// Drop the context's references to the shared tables (the device is current).
+void release_luts(acc_ctx *c) {
+    std::lock_guard<std::mutex> lock(g_tables_mu);
+    for (int k = 3; k <= 5; k++) {
+        if (!c->lut[k]) continue;
+        SharedTable &t = g_tables[c->device][k];
+        if (--t.refs == 0) {
+            cudaFree(t.lut);
+            cudaFree(t.lut_sv);
+            cudaFree(t.class_code);
+            delete[] t.lut_host;
+            delete[] t.class_code_host;
+            t = SharedTable();
+        }
+        c->lut[k] = c->lut_sv[k] = nullptr;
+        c->class_code_dev[k] = nullptr;
+        c->lut_host[k] = nullptr;
+        c->class_code_host[k] = nullptr;
+    }
 }
 
 long long scratch_per_warp(int max_n) { return 2 * (((long long)max_n + 32 + 31) & ~31LL); }
@@ -172,6 +227,7 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     bb.occ = c->occ;
     bb.occ_w = occ_words(max_n);
     bb.info = c->info;
+    bb.k = k;
     int rc = launch_build_graph(gs, bb, max_n, status, reinterpret_cast<unsigned long long *>(counts),
                                 (long long)gs.B * num_classes(k), relabel, c->num_sms, s);
     if (rc < 0) return rc;
@@ -400,13 +456,7 @@ void acc_ctx_destroy(acc_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    for (int k = 0; k < 6; k++) {
-        cudaFree(c->lut[k]);
-        cudaFree(c->lut_sv[k]);
-        cudaFree(c->class_code_dev[k]);
-        delete[] c->lut_host[k];
-        delete[] c->class_code_host[k];
-    }
+    release_luts(c);
     cudaFree(c->state);
     cudaFree(c->deg);
     cudaFree(c->lo);
@@ -512,6 +562,10 @@ int acc_motif_batch_prepare(acc_ctx *c, const acc_graph_desc *graphs, int32_t B,
         if (d.n > max_n) max_n = d.n;
         if (NV >= (1ll << 31) || arcs >= (1ll << 31)) return ACC_ERR_OVERFLOW;
     }
+    // an earlier run on this stream (enqueued only, when it had a status
+    // word) may still read the descriptors and graph ids rewritten below;
+    // the pageable copy would not wait for it
+    if (!ok(cudaStreamSynchronize(s))) return ACC_ERR_CUDA;
     int rc = ensure_lut(c, k, s);
     if (rc) return rc;
     if ((rc = ensure_workspace(c, NV, words, arcs, max_n, k))) return rc;

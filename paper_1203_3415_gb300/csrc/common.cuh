@@ -44,7 +44,46 @@ struct GraphInfo {
     unsigned long long unit_ctr;    // base units taken by phase 1
     unsigned long long chunks_pushed;
     unsigned long long scanned;     // count mode: neighbour entries the last two levels scanned
+    float bound[3];                 // degree sums of the count bound (count_bound_terms)
 };
+
+// Largest count the library reports: a set whose upper bound on N_k (below)
+// exceeds it is refused with ACC_ERR_OVERFLOW (int64 holds 2^63 - 1).
+constexpr double kCountLimit = 4611686018427387904.0;  // 2^62
+
+// Upper bound on the connected induced k-subsets of a graph from its G*
+// degrees.  Every connected k-set has a spanning tree, so it is reached by
+// choosing one embedded tree shape: k = 3 the path a-c-b from its centre c,
+// C(d_c, 2); k = 4 the star at its centre, C(d_c, 3), or the path a-b-c-d
+// from its middle edge, (d_b - 1)(d_c - 1); k = 5 the star, C(d_c, 4), the
+// fork (centre c of degree 3, one leg b extended), C(d_c - 1, 2) sum_b (d_b
+// - 1), or the path from its centre, at most (sum_b (d_b - 1))^2 / 2.  With
+// every neighbour's degree taken as the largest degree D, the bound is
+//   s0 + (D - 1) s1 + (D - 1)^2 s2,  per-vertex sums of count_bound_terms,
+// and never above C(n, k).  The terms are single precision (FP64 is slow on
+// this GPU and the scan runs on one SM for small sets); count_bound raises
+// the sums by 1% to cover their rounding (at most a few 1e-4 relative for
+// any set size the library takes).
+__host__ __device__ inline void count_bound_terms(int k, int d, float *s) {
+    const float x = (float)d;
+    if (k == 3) {
+        s[0] += x * (x - 1.0f) * 0.5f;
+    } else if (k == 4) {
+        s[0] += x * (x - 1.0f) * (x - 2.0f) * (1.0f / 6.0f);
+        s[1] += x * (x - 1.0f) * 0.5f;
+    } else if (k == 5) {
+        s[0] += x * (x - 1.0f) * (x - 2.0f) * (x - 3.0f) * (1.0f / 24.0f);
+        s[1] += x * (x - 1.0f) * (x - 2.0f) * 0.5f;
+        s[2] += x * x * 0.5f;
+    }
+}
+__host__ __device__ inline double count_bound(int k, int max_n, int maxdeg, const float *s) {
+    const double dm = maxdeg > 0 ? maxdeg - 1.0 : 0.0;
+    double b = 1.01 * ((double)s[0] + dm * (double)s[1] + dm * dm * (double)s[2]);
+    double c = max_n >= k ? 1.0 : 0.0;
+    for (int i = 0; i < k; i++) c = c * (double)(max_n - i) / (double)(i + 1);
+    return c < b ? c : b;
+}
 
 // One graph of a set.  Its vertices are the global ids [voff, voff + n); its
 // pair-state block is n rows of `pitch` words starting at word soff.
@@ -134,6 +173,8 @@ struct BuildBufs {
     uint32_t *occ;           // NV * occ_words(max_n)
     int occ_w;               // occ_words(max_n)
     GraphInfo *info;
+    int k = 0;               // 3..5: refuse (ACC_ERR_OVERFLOW) a set whose count bound
+                             // exceeds kCountLimit; 0: no check
 };
 int launch_build_graph(const GSet &gs, const BuildBufs &b, int max_n, int *status, unsigned long long *counts,
                        long long ncounts, bool relabel, int num_sms, cudaStream_t s);
@@ -151,6 +192,8 @@ int launch_zero(void *p, size_t bytes, int num_sms, cudaStream_t s, int *status 
 
 // lut.cu: lut = code -> class in the canonical code layout (public API),
 // lut_sv = the same classes indexed in the state-vector layout (kernels).
+// scratch_canon holds 2^(k(k-1)) words, scratch_rank rank_ints(k) ints.
+int rank_ints(int k);
 int launch_build_lut(int k, uint32_t *scratch_canon, int *scratch_rank, int16_t *lut,
                      uint32_t *class_code, int16_t *lut_sv, cudaStream_t s);
 

@@ -911,6 +911,10 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? ACC_MI
     // phase 2 with nothing queued: no table to stage, nothing to flush
     if constexpr (PHASE == 2)
         if (a.info->queue_tail == 0) return;
+    // a set refused by the count bound of the degree scan is not enumerated
+    // (phase 1 then queues nothing, so phase 2 returns above)
+    if constexpr (PHASE == 1)
+        if (a.status && *(volatile int *)a.status == ACC_ERR_OVERFLOW) return;
 
     if (L::SMEM_LUT)
         for (int i = tid; i < (1 << L::NB); i += blockDim.x) lut_s[i] = a.lut[i];

@@ -250,10 +250,12 @@ __global__ void k_desc_scatter(GSet gs, const int *__restrict__ key, int *start,
 // Exclusive scan of the degrees into nptr, with the largest degree and the
 // reset of the work counters.  Small sets: one block, the degrees staged in
 // shared memory by coalesced loads (n ints of dynamic shared memory).
-__global__ void __launch_bounds__(1024) k_scan_degrees(const int *__restrict__ deg_g, int n, long long *nptr, GraphInfo *info) {
+__global__ void __launch_bounds__(1024) k_scan_degrees(const int *__restrict__ deg_g, int n, long long *nptr, GraphInfo *info,
+                                                       int k, int max_n, int *status) {
     extern __shared__ int deg[];
     __shared__ long long warp_sum[32];
     __shared__ int warp_max[32];
+    __shared__ float warp_bound[32][3];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     {
         constexpr int kPer = (int)(kScanSingleMax / 1024);  // n <= kPer * blockDim.x
@@ -275,9 +277,11 @@ __global__ void __launch_bounds__(1024) k_scan_degrees(const int *__restrict__ d
     const int b = min(n, t * chunk), e = min(n, b + chunk);
     long long s = 0;
     int mx = 0;
+    float bs[3] = {0.0f, 0.0f, 0.0f};
     for (int i = b; i < e; i++) {
         s += deg[i];
         mx = max(mx, deg[i]);
+        if (k) count_bound_terms(k, deg[i], bs);
     }
     long long incl = s;
 #pragma unroll
@@ -287,6 +291,14 @@ __global__ void __launch_bounds__(1024) k_scan_degrees(const int *__restrict__ d
     }
 #pragma unroll
     for (int d = 16; d; d >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, d));
+    if (k) {
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+#pragma unroll
+            for (int d = 16; d; d >>= 1) bs[j] += __shfl_xor_sync(kFull, bs[j], d);
+        if (lane == 0)
+            for (int j = 0; j < 3; j++) warp_bound[wid][j] = bs[j];
+    }
     if (lane == 31) warp_sum[wid] = incl;
     if (lane == 0) warp_max[wid] = mx;
     __syncthreads();
@@ -321,6 +333,12 @@ __global__ void __launch_bounds__(1024) k_scan_degrees(const int *__restrict__ d
     __syncthreads();
     for (int i = t; i < n; i += blockDim.x) nptr[i] = (long long)(unsigned)deg[i];
     if (t == 0) {
+        if (k) {
+            float tb[3] = {0.0f, 0.0f, 0.0f};
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++)
+                for (int j = 0; j < 3; j++) tb[j] += warp_bound[w][j];
+            if (count_bound(k, max_n, warp_max[0], tb) > kCountLimit) set_status(status, ACC_ERR_OVERFLOW);
+        }
         info->maxdeg = warp_max[0];
         info->queue_tail = 0;
         info->queue_head = 0;
@@ -335,43 +353,55 @@ __global__ void __launch_bounds__(1024) k_scan_degrees(const int *__restrict__ d
 // own scan plus its offset.  The caller zeroes info->maxdeg first.
 constexpr int kScanTile = 4096;
 
-__global__ void __launch_bounds__(1024) k_scan_tiles(const int *__restrict__ deg, int n, long long *tile_sum, GraphInfo *info) {
+__global__ void __launch_bounds__(1024) k_scan_tiles(const int *__restrict__ deg, int n, long long *tile_sum, GraphInfo *info,
+                                                     int k) {
     __shared__ long long ws[32];
     __shared__ int wm[32];
+    __shared__ float wb[32][3];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long base = (long long)blockIdx.x * kScanTile;
     long long s = 0;
     int mx = 0;
+    float bs[3] = {0.0f, 0.0f, 0.0f};
     for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
         const long long j = base + i;
         if (j < n) {
             s += deg[j];
             mx = max(mx, deg[j]);
+            if (k) count_bound_terms(k, deg[j], bs);
         }
     }
 #pragma unroll
     for (int d = 16; d; d >>= 1) {
         s += __shfl_xor_sync(kFull, s, d);
         mx = max(mx, __shfl_xor_sync(kFull, mx, d));
+#pragma unroll
+        for (int j = 0; j < 3; j++) bs[j] += __shfl_xor_sync(kFull, bs[j], d);
     }
     if (lane == 0) {
         ws[wid] = s;
         wm[wid] = mx;
+        for (int j = 0; j < 3; j++) wb[wid][j] = bs[j];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         long long t = 0;
         int m = 0;
+        float tb[3] = {0.0f, 0.0f, 0.0f};
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
             t += ws[w];
             m = max(m, wm[w]);
+            for (int j = 0; j < 3; j++) tb[j] += wb[w][j];
         }
         tile_sum[blockIdx.x] = t;
         atomicMax(&info->maxdeg, m);
+        if (k)
+            for (int j = 0; j < 3; j++) atomicAdd(&info->bound[j], tb[j]);
     }
 }
 
-__global__ void __launch_bounds__(1024) k_scan_top(long long *tile_sum, int ntiles, long long *nptr, int n, GraphInfo *info) {
+__global__ void __launch_bounds__(1024) k_scan_top(long long *tile_sum, int ntiles, long long *nptr, int n, GraphInfo *info,
+                                                   int k, int max_n, int *status) {
     __shared__ long long warp_sum[32];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int chunk = (ntiles + blockDim.x - 1) / blockDim.x;
@@ -409,6 +439,7 @@ __global__ void __launch_bounds__(1024) k_scan_top(long long *tile_sum, int ntil
         run += v;
     }
     if (t == 0) {
+        if (k && count_bound(k, max_n, info->maxdeg, info->bound) > kCountLimit) set_status(status, ACC_ERR_OVERFLOW);
         info->queue_tail = 0;
         info->queue_head = 0;
         info->unit_ctr = 0;
@@ -623,7 +654,10 @@ __global__ void k_graph_ids(GSet gs, int *gid) {
     for (int i = threadIdx.x; i < mt.n; i += blockDim.x) gid[mt.voff + i] = blockIdx.x;
 }
 
-__global__ void k_reset_maxdeg(GraphInfo *info) { info->maxdeg = 0; }
+__global__ void k_reset_maxdeg(GraphInfo *info) {
+    info->maxdeg = 0;
+    info->bound[0] = info->bound[1] = info->bound[2] = 0.0f;
+}
 
 // True when the launch just enqueued was accepted; a refused launch's error
 // is cleared, and the caller launches nothing that would read its output.
@@ -718,16 +752,17 @@ int launch_build_graph(const GSet &gs, const BuildBufs &bb, int max_n, int *stat
     if (!launch_ok()) return ACC_ERR_CUDA;
     launches++;
     if (NV <= kScanSingleMax) {
-        k_scan_degrees<<<1, 1024, (size_t)(NV > 0 ? NV : 1) * 4, s>>>(bb.deg, (int)NV, bb.nptr, bb.info);
+        k_scan_degrees<<<1, 1024, (size_t)(NV > 0 ? NV : 1) * 4, s>>>(bb.deg, (int)NV, bb.nptr, bb.info, bb.k, max_n,
+                                                                      status);
         if (!launch_ok()) return ACC_ERR_CUDA;
         launches++;
     } else {
         const int ntiles = (int)scan_tiles_needed(NV);
         k_reset_maxdeg<<<1, 1, 0, s>>>(bb.info);
         if (!launch_ok()) return ACC_ERR_CUDA;
-        k_scan_tiles<<<ntiles, 1024, 0, s>>>(bb.deg, (int)NV, bb.tiles, bb.info);
+        k_scan_tiles<<<ntiles, 1024, 0, s>>>(bb.deg, (int)NV, bb.tiles, bb.info, bb.k);
         if (!launch_ok()) return ACC_ERR_CUDA;
-        k_scan_top<<<1, 1024, 0, s>>>(bb.tiles, ntiles, bb.nptr, (int)NV, bb.info);
+        k_scan_top<<<1, 1024, 0, s>>>(bb.tiles, ntiles, bb.nptr, (int)NV, bb.info, bb.k, max_n, status);
         if (!launch_ok()) return ACC_ERR_CUDA;
         k_scan_apply<<<ntiles, 1024, 0, s>>>(bb.deg, (int)NV, bb.tiles, bb.nptr);
         if (!launch_ok()) return ACC_ERR_CUDA;

@@ -1,6 +1,7 @@
 // Runs the graph builder (csrc/graph.cu, kernels and host launcher, with each
 // launch turned into emu_launch; source in graph_kernels.inc) on the host
-// over a set of B graphs given as input CSRs: relabel num_sms B (int64), then
+// over a set of B graphs given as input CSRs: relabel + 256 k num_sms B
+// (int64; k > 0 turns on the count-bound check for that k), then
 // n m of each graph (int64), then each graph's rowptr[n + 1] (int64) and
 // col[m] (int32).  The set is built twice: first over a pair-state buffer
 // full of garbage (swept by the build's zeroing), then, after the builder's
@@ -34,7 +35,8 @@ int main(int argc, char **argv) {
     FILE *f = fopen(argv[1], "rb");
     long long h[3];
     if (!rd(f, h, 3)) return 2;
-    const bool relabel = h[0] != 0;
+    const bool relabel = (h[0] & 1) != 0;
+    const int guard_k = (int)(h[0] >> 8);
     const int num_sms = (int)h[1];
     const long long B = h[2];
     std::vector<long long> ns(B), ms(B);
@@ -99,6 +101,7 @@ int main(int argc, char **argv) {
     bb.occ = occ.data();
     bb.occ_w = occ_w;
     bb.info = &info;
+    bb.k = guard_k;
     for (int pass = 0; pass < 2; pass++) {
         std::fill(counts.begin(), counts.end(), 123ull);
         const int launches = acc::launch_build_graph(gs, bb, max_n, &status, counts.data(), (long long)counts.size(),

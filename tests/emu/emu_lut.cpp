@@ -1,4 +1,4 @@
-// Runs the class-table builder (csrc/lut.cu: k_canon, k_rank, k_finish,
+// Runs the class-table builder (csrc/lut.cu: k_canon, k_rank_scan, k_finish,
 // k_relayout through launch_build_lut, each launch turned into emu_launch;
 // source in lut_all.inc) on the host for one k given on the command line's
 // input file (int64 k).  Output: the launcher's return value, then the
@@ -19,7 +19,7 @@ int main(int argc, char **argv) {
     const size_t ncodes = (size_t)1 << acc::code_bits((int)k);
     const int ncls = acc::num_classes((int)k);
     std::vector<uint32_t> canon(ncodes), class_code(ncls, 0xFFFFFFFFu);
-    std::vector<int> rank(ncodes);
+    std::vector<int> rank((size_t)acc::rank_ints((int)k));
     std::vector<int16_t> lut(ncodes, 0x5555), lut_sv(ncodes, 0x5555);
     const long long rc = acc::launch_build_lut((int)k, canon.data(), rank.data(), lut.data(), class_code.data(),
                                                lut_sv.data(), nullptr);

@@ -264,6 +264,13 @@ inline cudaError_t cudaStreamBeginCapture(cudaStream_t s, cudaStreamCaptureMode 
     s->rec.clear();
     return cudaSuccess;
 }
+enum cudaStreamCaptureStatus { cudaStreamCaptureStatusNone, cudaStreamCaptureStatusActive,
+                               cudaStreamCaptureStatusInvalidated };
+inline cudaError_t cudaStreamIsCapturing(cudaStream_t s, cudaStreamCaptureStatus *st) {
+    *st = s && s->capturing ? (s->invalid ? cudaStreamCaptureStatusInvalidated : cudaStreamCaptureStatusActive)
+                            : cudaStreamCaptureStatusNone;
+    return cudaSuccess;
+}
 inline cudaError_t cudaStreamEndCapture(cudaStream_t s, cudaGraph_t *g) {
     if (!s || !s->capturing) return cudaErrorInvalidValue;
     s->capturing = false;

@@ -265,6 +265,7 @@ inline unsigned atomicAdd(unsigned *p, unsigned v) { return std::atomic_ref<unsi
 inline unsigned atomicSub(unsigned *p, unsigned v) { return std::atomic_ref<unsigned>(*p).fetch_sub(v); }
 inline unsigned atomicExch(unsigned *p, unsigned v) { return std::atomic_ref<unsigned>(*p).exchange(v); }
 inline void __threadfence_block() { std::atomic_thread_fence(std::memory_order_seq_cst); }
+inline float atomicAdd(float *p, float v) { return std::atomic_ref<float>(*p).fetch_add(v); }
 inline unsigned long long atomicAdd(unsigned long long *p, unsigned long long v) {
     return std::atomic_ref<unsigned long long>(*p).fetch_add(v);
 }

@@ -5,7 +5,7 @@ Calls only the CPU oracle (``oracle/``) and the seeded generators
 the workload, the SHA-256 of the generated arc list (so a test can tell that
 it regenerated the same graph), N_k and every nonzero class count.
 
-    python tests/golden/make_golden.py [--threads T] [--only NAME ...]
+    python tests/golden/make_golden.py [--threads T] [--only NAME ...] [--batch] [--serving]
 """
 import argparse
 import hashlib
@@ -86,14 +86,37 @@ def make_batch_golden(path, threads, n_rand=synth.BATCH_RANDOMISATIONS):
             print(f"batch base {b}: n={base.n} total={int(counts.sum())} in {time.time() - t:.1f} s", flush=True)
 
 
+def make_serving_pool_golden(path, threads):
+    """Serving tests' graph pool: per graph and k = 3, 4, 5, the graph's
+    digest, N_k and the digest of its int64 counts."""
+    from tests.graph_helpers import serving_test_pool
+    with open(path, "w") as f:
+        f.write("# serving test pool: directed Chung-Lu graphs (exponent 2.2, cap 120, 10% reciprocal)\n")
+        f.write(f"# oracle ESU, {threads} threads; one line per graph and k:\n")
+        f.write("# graph k n m graph_sha256 total counts_sha256\n")
+        for gi, g in enumerate(serving_test_pool()):
+            for k in (3, 4, 5):
+                t = time.time()
+                counts = oracle.count(g.n, g.src, g.dst, k, threads=threads)
+                f.write(f"{gi} {k} {g.n} {g.m} {synth.graph_digest(g)} {int(counts.sum())} "
+                        f"{counts_digest(counts)}\n")
+                f.flush()
+                print(f"serving graph {gi} k={k}: N_k = {int(counts.sum())} in {time.time() - t:.1f} s", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--threads", type=int, default=oracle.max_threads())
     ap.add_argument("--only", nargs="*")
     ap.add_argument("--batch", action="store_true", help="also write the batched k=4 expectations")
+    ap.add_argument("--serving", action="store_true", help="also write the serving test pool's expectations")
     args = ap.parse_args()
     if args.batch:
         make_batch_golden(os.path.join(HERE, "batch_k4.txt"), args.threads)
+    if args.serving:
+        make_serving_pool_golden(os.path.join(HERE, "serving_pool.txt"), args.threads)
+        if args.only is not None and not args.only:
+            return
     for name, (make, k) in WORKLOADS.items():
         if args.only and name not in args.only:
             continue

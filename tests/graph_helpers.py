@@ -92,3 +92,14 @@ def esu_scanned_entries(n, src, dst, k):
                 E3 = E2[j2 + 1:] + [u for u in adj[w2] if u > v and u not in nb[v] and u not in nb[w1]]
                 total += sum(above(x, v) for x in E3)
     return total
+
+
+# Graph pool of the serving tests: (n, m, seed) of directed Chung-Lu graphs
+# (exponent 2.2, degree cap 120, 10% reciprocal, seed 7000 + s).
+SERVING_TEST_POOL = [(300, 1200, 1), (800, 3200, 2), (2500, 12000, 3), (6000, 30000, 4), (150, 600, 5),
+                     (4000, 16000, 6), (1200, 9000, 7), (9000, 40000, 8)]
+
+
+def serving_test_pool():
+    import synth
+    return [synth.chung_lu(n, m, 2.2, 120, 10, 7000 + s) for n, m, s in SERVING_TEST_POOL]

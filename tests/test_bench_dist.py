@@ -84,3 +84,12 @@ def test_reference_arm_other_ranks_exit_quietly():
     out = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "3", "--workload", "er_n1000_m5000_k3",
                       "--reference-roots", "10"], {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert out == []
+
+
+def test_reference_arm_times_the_whole_workload_by_default():
+    # without --reference-roots every ESU root is counted in each step: the
+    # same config as our arm, not a sample of it
+    out = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "3", "--workload", "er_n1000_m5000_k3"])
+    assert len(out) == 1
+    d = out[0]
+    assert d["cpu_baseline"]["sample"].startswith("the whole workload, all 1000 ESU roots (44842 subgraphs")

@@ -37,7 +37,7 @@ import pytest
 
 import oracle
 import synth
-from tests.graph_helpers import random_digraph
+from tests.graph_helpers import random_digraph, out_star, complete_bidirected, directed_path
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -134,6 +134,13 @@ def emu_bins(tmp_path_factory):
         assert common.count(old) == 1, old
         common = common.replace(old, new)
     open(bdir / "common.cuh", "w").write(common)
+    # the same with a count limit of 10^4, for the overflow guard on small graphs
+    gdir = out / "guard"
+    gdir.mkdir()
+    old = "constexpr double kCountLimit = 4611686018427387904.0;  // 2^62"
+    assert common.count(old) == 1, old
+    open(gdir / "common.cuh", "w").write(common.replace(old, "constexpr double kCountLimit = 10000.0;"))
+    open(gdir / "graph_kernels.inc", "w").write(open(bdir / "graph_kernels.inc").read())
     z_src = open(os.path.join(CSRC, "batch.cu")).read().split('#include "common.cuh"\n', 1)[1]
     open(out / "z_all.inc", "w").write(_launches_to_calls(z_src))
     # the class-table builder (kernels and launch_build_lut)
@@ -147,6 +154,7 @@ def emu_bins(tmp_path_factory):
     targets += [("emu_enum", "emu_enum", ["-DEMU_DRAIN_AT=(1u<<30)"]),
                 ("emu_enum_small", "emu_enum", ["-DEMU_DRAIN_AT=256u", "-DACC_CAP34=16", "-DACC_CAP5=8"]),
                 ("emu_build", "emu_build", ["-I", str(bdir), "-fsanitize=address", "-DEMU_LANE_STACK=65536"]),
+                ("emu_build_guard", "emu_build", ["-I", str(gdir), "-DEMU_LANE_STACK=65536"]),
                 ("emu_lut", "emu_lut", ["-O2"]),
                 ("emu_z", "emu_z", ["-ffp-contract=off"])]
     procs = []
@@ -452,19 +460,19 @@ def _err_input():
     return int(re.search(r"#define\s+ACC_ERR_INPUT\s+\(?(-?\d+)\)?", hdr).group(1))
 
 
-def _build_many(bins, jobs):
+def _build_many(bins, jobs, binary="emu_build", guard_k=0):
     """Run the graph builder over [(graphs, relabel, num_sms)], graphs a list
     of (n, rowptr, col): per job, the two builds' records."""
     inps = []
     for graphs, relabel, num_sms in jobs:
-        buf = struct.pack("<3q", int(relabel), num_sms, len(graphs))
+        buf = struct.pack("<3q", int(relabel) + 256 * guard_k, num_sms, len(graphs))
         buf += b"".join(struct.pack("<2q", n, len(cl)) for n, _, cl in graphs)
         for n, rp, cl in graphs:
             buf += np.asarray(rp, "<i8").tobytes() + np.asarray(cl, "<i4").tobytes()
         inps.append(buf)
     names = ("head", "label", "deg", "lo", "nptr", "nbr", "state", "occ", "clean")
     res = []
-    for o in _run_many(bins["emu_build"], inps, True, bins["dir"]):
+    for o in _run_many(bins[binary], inps, True, bins["dir"]):
         raw = np.frombuffer(o, "<i8")
         recs, i = [], 0
         while i < len(raw):
@@ -582,6 +590,32 @@ def test_graph_builder_reports_malformed_input(emu_bins):
             assert r["clean"][0] == 1
     for r in res[-1]:
         _check_build(r, good, True)
+
+
+def test_count_bound_guard(emu_bins):
+    """The degree scan's overflow guard, built with a count limit of 10^4, on
+    one-block scans and on tiled scans (sets above this build's 2048-vertex
+    single-block limit).  A set holding a graph whose exact count (oracle)
+    exceeds the limit must be refused with ACC_ERR_OVERFLOW, since the guard
+    is an upper bound; a set whose graphs have at most C(n, k) <= 10^4
+    k-subsets must pass, by the bound's C(n, k) cap; a directed path passes
+    too (its bound is sum d^2 / 2 ~ 2n at k = 5: every factor D - 1 is 1)."""
+    overflow = -5
+    star = (31, *out_star(30))           # N_5 = C(30, 4) = 27405
+    k12 = (12, *complete_bidirected(12))  # C(12, 4) = 495, C(12, 5) = 792
+    rng = np.random.default_rng(77)
+    cases = [([star], 5, True), ([k12], 4, False), ([k12], 5, False),
+             ([(2000, *directed_path(2000))], 5, False),
+             ([(2500, *directed_path(2500)), star], 5, True),
+             ([k12] * 200, 4, False), ([k12] * 200 + [star], 5, True)]
+    for graphs, k, refused in cases:
+        exact = [int(oracle.count(n, s, d, k).sum()) for n, s, d in graphs]
+        if refused:
+            assert max(exact) > 10000
+        jobs = [([_raw_csr(n, s, d, rng) for n, s, d in graphs], True, 2)]
+        (builds,) = _build_many(emu_bins, jobs, binary="emu_build_guard", guard_k=k)
+        for r in builds:
+            assert r["head"][0] == (overflow if refused else 0), (k, [g[0] for g in graphs])
 
 
 def _sv_to_canonical(k):

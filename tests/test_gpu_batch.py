@@ -181,3 +181,29 @@ def test_full_batch_against_stored_oracle_counts(counter):
         assert np.array_equal(want[ok].view(np.int64), z[b][ok].view(np.int64))
     del dev
     torch.cuda.synchronize()
+
+
+def test_prepare_waits_for_an_enqueued_run(counter):
+    """prepare(A), an asynchronous run of A on a non-blocking stream, then
+    prepare(B) on the same stream: the run of A still reads A's descriptors,
+    so the second prepare must not overwrite them under it."""
+    import torch
+    ga = [synth.chung_lu(n, 4 * n, 2.2, 150, 10, 900 + n) for n in (4000, 2500, 3000)]
+    gb = [synth.chung_lu(n, 5 * n, 2.2, 100, 10, 950 + n) for n in (300, 200, 600, 100)]
+    da = to_device([(g.n, g.src, g.dst) for g in ga])
+    db = to_device([(g.n, g.src, g.dst) for g in gb])
+    s = torch.cuda.Stream()  # non-blocking with respect to the legacy stream
+    ca = torch.zeros((len(ga), 199), dtype=torch.int64, device="cuda")
+    cb = torch.zeros((len(gb), 199), dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(s):
+        counter.prepare_batch(da, 4, stream=s)
+        counter.run_batch(counts=ca, status=st, stream=s)  # enqueued only
+        counter.prepare_batch(db, 4, stream=s)
+        counter.run_batch(counts=cb, status=st, stream=s)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    for i, g in enumerate(ga):
+        assert ca[i].cpu().numpy().tolist() == oracle.count(g.n, g.src, g.dst, 4, threads=oracle.max_threads()).tolist(), i
+    for i, g in enumerate(gb):
+        assert cb[i].cpu().numpy().tolist() == oracle.count(g.n, g.src, g.dst, 4).tolist(), i

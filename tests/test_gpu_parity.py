@@ -302,3 +302,31 @@ def test_workspace_reuse_across_sizes(counter):
         assert gpu_count(counter, a.n, a.src, a.dst, 4).tolist() == ea.tolist()
         gpu_count(counter, b.n, b.src, b.dst, 5)
         gpu_count(counter, b.n, b.src, b.dst, 3)
+
+
+def test_count_bound_guard(counter):
+    """The overflow guard: an out-star with 50000 leaves at k = 5 has a
+    degree bound of about 6.5e18 > 2^62, so it is refused with
+    ACC_ERR_OVERFLOW (synchronously and through the status word) without
+    being enumerated; at k = 4 its bound (about 8.3e13) passes and the count
+    is the closed form C(50000, 3) in the out-star class (count mode; the
+    enumerate mode would visit all 2e13 leaves).  The context then counts a
+    small graph correctly."""
+    import torch
+    import paper_1203_3415_gb300 as p
+    L = 50000
+    r, c = csr_arrays(L + 1, np.zeros(L, np.int32), np.arange(1, L + 1, dtype=np.int32))
+    rr, cc = torch.from_numpy(r).cuda(), torch.from_numpy(c).cuda()
+    with pytest.raises(p.MotifError) as e:
+        counter.count(rr, cc, L + 1, 5)
+    assert e.value.code == p.ACC_ERR_OVERFLOW
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    counter.count(rr, cc, L + 1, 5, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == p.ACC_ERR_OVERFLOW
+    if counter.mode == p.ACC_MODE_COUNT:
+        got = counter.count(rr, cc, L + 1, 4).cpu().numpy()
+        n, s, d = 4, *out_star(3)
+        want_cls = int(np.flatnonzero(oracle.count(n, s, d, 4))[0])
+        assert int(got.sum()) == math.comb(L, 3) and int(got[want_cls]) == math.comb(L, 3)
+    assert gpu_count(counter, 5, [0, 1, 2], [1, 2, 3], 3).tolist() == oracle.count(5, [0, 1, 2], [1, 2, 3], 3).tolist()

@@ -1,14 +1,22 @@
 """Serving form: requests admitted by free slots and device memory, running
 concurrently on the GPU, give exactly the counts they give alone (tolerance
-0: int64 histograms)."""
+0: int64 histograms), and every served result equals the CPU oracle's counts
+(stored by tests/golden/make_golden.py --serving for the test pool, or
+computed here)."""
+import hashlib
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 import synth
 from tests.gpu_helpers import csr_arrays
+from tests.graph_helpers import serving_test_pool
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "serving_pool.txt")
 
 
 @pytest.fixture(scope="module")
@@ -21,9 +29,23 @@ def acc():
 
 
 def pool():
-    specs = [(300, 1200, 1), (800, 3200, 2), (2500, 12000, 3), (6000, 30000, 4), (150, 600, 5),
-             (4000, 16000, 6), (1200, 9000, 7), (9000, 40000, 8)]
-    return [synth.chung_lu(n, m, 2.2, 120, 10, 7000 + s) for n, m, s in specs]
+    return serving_test_pool()
+
+
+def stored_pool_counts(graphs):
+    """{(graph index, k): (N_k, counts sha256)} of the oracle's counts of the
+    test pool, after checking that the generator still makes the same graphs."""
+    rows = [ln.split() for ln in open(GOLDEN) if ln.strip() and not ln.startswith("#")]
+    want = {}
+    for gi, k, n, m, gsha, total, csha in rows:
+        g = graphs[int(gi)]
+        assert (g.n, g.m, synth.graph_digest(g)) == (int(n), int(m), gsha), "generator drifted from the stored graphs"
+        want[(int(gi), int(k))] = (int(total), csha)
+    return want
+
+
+def digest(counts):
+    return hashlib.sha256(np.ascontiguousarray(counts, dtype="<i8").tobytes()).hexdigest()
 
 
 def to_dev(g):
@@ -39,6 +61,7 @@ def requests(n_graphs, count, seed):
 
 def test_mix_equals_alone(acc):
     graphs = pool()
+    stored = stored_pool_counts(graphs)
     dev = [to_dev(g) for g in graphs]
     reqs = requests(len(graphs), 48, 11)
     counter = acc.Counter(0)
@@ -46,11 +69,10 @@ def test_mix_equals_alone(acc):
     for gi, k in set(reqs):
         alone[(gi, k)] = counter.count(dev[gi][0], dev[gi][1], graphs[gi].n, k).cpu().numpy()
     counter.close()
-    # the oracle agrees on the small ones
-    for gi, k in alone:
-        if graphs[gi].n <= 1200 and k < 5:
-            g = graphs[gi]
-            assert alone[(gi, k)].tolist() == oracle.count(g.n, g.src, g.dst, k).tolist()
+    # every request's count alone equals the oracle's (stored), k = 5 and the
+    # largest graphs included
+    for key, counts in alone.items():
+        assert (int(counts.sum()), digest(counts)) == stored[key], key
     srv = acc.Server(0, slots=4, mem_budget_bytes=48 << 30)
     ids = [srv.add_graph(r, c, g.n) for (r, c), g in zip(dev, graphs)]
     srv.reserve()
@@ -67,15 +89,14 @@ def test_mix_equals_alone(acc):
         st, counts, lat = srv.poll(rid)
         assert st == acc.ACC_REQ_DONE and lat >= 0.0
         assert counts.tolist() == alone[(gi, k)].tolist(), (gi, k)
+        assert (int(counts.sum()), digest(counts)) == stored[(gi, k)], (gi, k)
     srv.close()
 
 
 def test_memory_admission_serialises(acc):
     graphs = [synth.chung_lu(n, 4 * n, 2.2, 120, 10, 7100 + n) for n in (6000, 5600, 5800, 6000)]
     dev = [to_dev(g) for g in graphs]
-    counter = acc.Counter(0)
-    want = [counter.count(r, c, g.n, 4).cpu().numpy() for (r, c), g in zip(dev, graphs)]
-    counter.close()
+    want = [oracle.count(g.n, g.src, g.dst, 4, threads=oracle.max_threads()) for g in graphs]
     # a budget that holds one such workspace (~0.4 GB) but not two
     srv = acc.Server(0, slots=4, mem_budget_bytes=int(0.6e9))
     ids = [srv.add_graph(r, c, g.n) for (r, c), g in zip(dev, graphs)]
@@ -134,10 +155,11 @@ def test_admission_policy_order(acc, policy):
     else:
         assert last_big_state == acc.ACC_REQ_QUEUED
     srv.drain()
-    want_big = srv.poll(bigs[0])[1]
+    stored = stored_pool_counts(graphs)
     for rid in bigs:
         st, counts, _ = srv.poll(rid)
-        assert st == acc.ACC_REQ_DONE and counts.tolist() == want_big.tolist()
+        assert st == acc.ACC_REQ_DONE
+        assert (int(counts.sum()), digest(counts)) == stored[(7, 5)]
     assert srv.poll(s)[1].tolist() == oracle.count(small.n, small.src, small.dst, 3).tolist()
     with pytest.raises(acc.MotifError):
         srv.set_policy(7)
