@@ -185,6 +185,7 @@ int ensure_workspace(acc_ctx *c, long long NV, long long state_words, long long 
     if ((rc = grow(&c->tiles, &c->tiles_cap, (size_t)scan_tiles_needed(NV) + 1))) return rc;
     if ((rc = grow(&c->f5_pre, &c->f5_pre_cap, (size_t)NV + 1))) return rc;
     if ((rc = grow(&c->nbr, &c->nbr_cap, (size_t)(2 * arcs) + 1))) return rc;
+    if ((rc = grow(&c->src, &c->src_cap, (size_t)(2 * arcs) + 1))) return rc;
     if ((rc = grow(&c->occ, &c->occ_cap, (size_t)NV * (size_t)occ_words(max_n) + 1))) return rc;
     if (!c->info) {
         if (!ok(cudaMalloc(&c->info, sizeof(GraphInfo)))) return ACC_ERR_NOMEM;
@@ -224,6 +225,7 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     bb.nptr = c->nptr;
     bb.tiles = c->tiles;
     bb.nbr = c->nbr;
+    bb.src = c->src;
     bb.occ = c->occ;
     bb.occ_w = occ_words(max_n);
     bb.info = c->info;
@@ -239,6 +241,7 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     a.lo = c->lo;
     a.nptr = c->nptr;
     a.nbr = c->nbr;
+    a.src = c->src;
     a.lut = c->lut_sv[k];
     a.gs = gs;
     a.max_n = max_n;
@@ -344,7 +347,7 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
         key.grid_den = c->grid_den;
         const void *ws[18] = {c->state, c->deg, c->lo, c->label, c->deg_in, c->nptr, c->tiles, c->nbr, c->occ,
                               c->info, c->queue, c->scratch, c->lut[k], c->lut_sv[k], c->class_code_dev[k],
-                              c->f5_pre, c->status_dev, nullptr};
+                              c->f5_pre, c->status_dev, c->src};
         memcpy(key.ws, ws, sizeof(ws));
         bool have = c->cg_exec && memcmp(&key, &c->cg_key, sizeof(key)) == 0;
         // capture only when a count repeats: a one-off count runs one by one
@@ -397,7 +400,7 @@ namespace acc {
 long long ctx_footprint(const acc_ctx *c, long long n, long long m, int k) {
     const long long pitch = state_pitch((int)n);
     const long long warps = enum_grid_warps(k, c->num_sms);
-    const long long bytes = n * pitch * 4 + 5 * 4 * (n + 1) + 8 * (n + 1) + 4 * (2 * m + 1) +
+    const long long bytes = n * pitch * 4 + 5 * 4 * (n + 1) + 8 * (n + 1) + 8 * (2 * m + 1) +
                             4 * n * occ_words((int)n) +
                             (long long)kQueueCap * 16 + scratch_per_warp((int)n) * (warps > 0 ? warps : 0) * 4;
     return bytes + bytes / 4;
@@ -467,6 +470,7 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaFree(c->f5_pre);
     cudaFree(c->occ);
     cudaFree(c->nbr);
+    cudaFree(c->src);
     cudaFree(c->info);
     cudaFree(c->queue);
     cudaFree(c->scratch);

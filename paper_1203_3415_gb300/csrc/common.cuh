@@ -14,6 +14,8 @@
 //   nptr    int64[n+1]          CSR offsets of the G* neighbour lists
 //   nbr     uint32[2|E*|]       neighbour entries (u << 2) | state(v, u),
 //                               sorted by u
+//   src     uint32[2|E*|]       global row vertex of each entry, bit 31 set
+//                               when the neighbour is below the row's vertex
 //   label   int32[n]            new number of each input vertex (vertices
 //                               are renumbered by descending G* degree, so
 //                               hubs become the roots of their subsets)
@@ -170,6 +172,7 @@ struct BuildBufs {
     long long *nptr;         // NV + 1
     long long *tiles;        // scan_tiles_needed(NV) + 1
     uint32_t *nbr;           // 2 |E*|
+    uint32_t *src = nullptr; // 2 |E*| or NULL: row of each entry (k_fill)
     uint32_t *occ;           // NV * occ_words(max_n)
     int occ_w;               // occ_words(max_n)
     GraphInfo *info;
@@ -204,6 +207,7 @@ struct EnumArgs {
     const int *lo;
     const long long *nptr;
     const uint32_t *nbr;        // entries hold local ids
+    const uint32_t *src;        // global row vertex of each entry, bit 31: neighbour below it
     const int16_t *lut;         // class table in the state-vector layout
     GSet gs;
     int max_n;                  // largest graph of the set

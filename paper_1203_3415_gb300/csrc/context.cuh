@@ -37,6 +37,8 @@ struct acc_ctx {
     long long *f5_pre = nullptr;  // k = 5 formula path: prefix of C(deg, 2)
     size_t f5_pre_cap = 0;
     uint32_t *nbr = nullptr;
+    uint32_t *src = nullptr;  // row of each neighbour entry
+    size_t src_cap = 0;
     uint32_t *occ = nullptr;  // pair-state row occupancy bitmaps
     size_t occ_cap = 0;
     size_t nbr_cap = 0;

@@ -54,7 +54,7 @@ namespace {
 #define ACC_GRAB4 2  // base units per atomic grab for k = 4 (lighter units, one hot counter)
 #endif
 #ifndef ACC_GRAB_SET
-#define ACC_GRAB_SET 16  // base units per grab when several graphs are counted (fewer graph switches)
+#define ACC_GRAB_SET 16  // base units per grab when several graphs are counted (fewer graph switches), <= 32
 #endif
 #ifndef ACC_GRAB
 #define ACC_GRAB 1
@@ -68,11 +68,17 @@ namespace {
 #ifndef ACC_UNROLL
 #define ACC_UNROLL 4
 #endif
-#ifndef ACC_CUNROLL
-#define ACC_CUNROLL 4  // count mode: neighbour entries in flight per lane, k = 3, 4
+#ifndef ACC_CWIN
+#define ACC_CWIN 3  // count mode: 32-entry windows of the flat row scan per step (entries in flight per lane), k = 3, 4
 #endif
-#ifndef ACC_CUNROLL5
-#define ACC_CUNROLL5 3  // the same for k = 5
+#ifndef ACC_CWIN5
+#define ACC_CWIN5 2  // the same for k = 5
+#endif
+#ifndef ACC_RING
+#define ACC_RING 64  // count mode: rows a warp may stage for the flat scan (a power of two, at least 64), k = 3, 4
+#endif
+#ifndef ACC_RING5
+#define ACC_RING5 64  // the same for k = 5 (its block histogram leaves less shared memory)
 #endif
 #ifndef ACC_CAP5
 #define ACC_CAP5 64  // per-warp shared-memory list entries (each of two lists), k = 5
@@ -84,7 +90,13 @@ namespace {
 #define ACC_MINB34 4  // resident blocks per SM the k = 3, 4 leaf kernels are compiled for
 #endif
 #ifndef ACC_MINB34C
-#define ACC_MINB34C 4  // the same for the k = 3, 4 count-mode kernels
+#define ACC_MINB34C 4  // the same for the k = 3, 4 count-mode kernels of one graph
+#endif
+#ifndef ACC_LUT_SMEM34
+#define ACC_LUT_SMEM34 1  // k = 3, 4: class table staged in shared memory (else read through L1)
+#endif
+#ifndef ACC_MINB34S
+#define ACC_MINB34S 4  // the same for the k = 3, 4 count-mode kernels of a set of graphs
 #endif
 constexpr int kCap34 = ACC_CAP34;         // per-warp shared extension entries, k = 3, 4
 constexpr int kCap5 = ACC_CAP5;           // per-warp shared entries per list, k = 5
@@ -96,7 +108,7 @@ template <int K>
 struct Layout {
     static constexpr int NB = K * (K - 1);
     static constexpr int NCLS = num_classes(K);
-    static constexpr bool SMEM_LUT = K <= 4;
+    static constexpr bool SMEM_LUT = K <= 4 && ACC_LUT_SMEM34;
     static constexpr int CAP = K == 5 ? kCap5 : kCap34;
     static constexpr int LISTS = K == 5 ? 2 : 1;
     static constexpr int SH_PAIR = 2 * (K - 2);  // state(E[j], leaf) within the last field
@@ -107,7 +119,12 @@ struct Layout {
     static constexpr size_t ebuf = size_t(kWarpsPerBlock) * LISTS * CAP * 4;
     static constexpr int G = 1 << (2 * (K - 2));  // state vectors to the prefix: 4, 16, 64
     static constexpr size_t groups = size_t(kWarpsPerBlock) * 3 * G * 4;  // count mode: sizes + list
-    static constexpr size_t total = lut + pending + hist + ebuf + groups;
+    // count mode: rows staged for the flat scan (a batch of 32 is staged
+    // only while the ring has room for it)
+    static constexpr int WIN = K == 5 ? ACC_CWIN5 : ACC_CWIN;
+    static constexpr int RING = K == 5 ? ACC_RING5 : ACC_RING;
+    static constexpr size_t ring = size_t(kWarpsPerBlock) * RING * 3 * 4;
+    static constexpr size_t total = lut + pending + hist + ebuf + groups + ring;
 };
 
 __device__ __forceinline__ uint32_t probe(const uint32_t *__restrict__ st, long long pitch, uint32_t a, uint32_t b) {
@@ -129,6 +146,20 @@ struct GView {
     const uint32_t *nbr;
     int n;
 };
+
+// The only graph of a single-graph count: its arrays are the kernel's own
+// (global and local ids coincide).
+__device__ __forceinline__ GView view_single(const EnumArgs &a) {
+    GView g;
+    g.state = a.state;
+    g.pitch = a.gs.one.pitch;
+    g.nptr = a.nptr;
+    g.deg = a.deg;
+    g.lo = a.lo;
+    g.nbr = a.nbr;
+    g.n = a.gs.one.n;
+    return g;
+}
 
 __device__ __forceinline__ GView view_of(const EnumArgs &a, const GMeta &mt) {
     GView g;
@@ -223,6 +254,16 @@ struct Sink {
         }
         atomicAdd(&hist[cls], (uint32_t)(int32_t)delta);
         moved += (unsigned long long)(delta < 0 ? -delta : delta);
+    }
+
+    // Count mode: add +1 or -1 to class cls (the scan's leaves and moves).
+    __device__ __forceinline__ void add1(int cls, int delta) {
+        if (cls < 0) {
+            set_status(status, ACC_ERR_INTERNAL);
+            return;
+        }
+        if (direct) atomicAdd(&counts[cls], (unsigned long long)(long long)delta);
+        else atomicAdd(&hist[cls], (uint32_t)delta);
     }
 
     __device__ __forceinline__ int cls_of(uint32_t code) const {
@@ -332,6 +373,7 @@ struct Scratch {
     uint32_t *ovf[2];  // global overflow lists of this warp
     int cap;
     uint32_t *gcnt;    // count mode: group sizes and the non-empty group list
+    uint32_t *ring;    // count mode: staged rows (flat start, entry offset, list entry), RING each
 };
 
 // The last two ESU levels over extension list E[0..B), virtual rows
@@ -472,9 +514,8 @@ __device__ __forceinline__ bool in_list(const uint32_t *s, uint32_t u, const uin
 template <int K>
 __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, const uint32_t *E, int B, int jlo,
                                              int jend, bool bulk, const uint32_t *pm, uint32_t pcode,
-                                             uint32_t root, bool w2_in_a, uint32_t *gcnt, int lane) {
+                                             uint32_t root, bool w2_in_a, uint32_t *gcnt, uint32_t *ring, int lane) {
     using L = Layout<K>;
-    constexpr int U = K == 5 ? ACC_CUNROLL5 : ACC_CUNROLL;
     if (bulk) {
         uint32_t *glist = gcnt + L::G;  // (group, count) pairs of the non-empty groups
         for (int i = lane; i < L::G; i += kWarp) gcnt[i] = 0;
@@ -513,91 +554,171 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
         account_moved(sink, lane);
     }
     // neighbour scan of rows [jlo, jend): adjacent member pairs (each once,
-    // from its smaller vertex) and exclusive neighbours
-    for (int jb = jlo; jb < jend; jb += kWarp) {
-        const int j = jb + lane;
-        uint32_t ej = 0, first = 0;
-        int cnt = 0;
-        if (j < jend) {
-            ej = E[j];
-            const uint32_t x = e_id(ej);
-            const long long nb = g.nptr[x];
-            const int d = g.deg[x];
-            const int st = first_above(g.nbr, nb, d, root);
-            first = (uint32_t)(nb + st);
-            cnt = d - st;
-        }
-        int tot;
-        const int pre = excl_scan(cnt, lane, &tot);
-        sink.scanned += (unsigned long long)tot;
-        const uint32_t off = first - (uint32_t)pre;
-        for (int t0 = 0; t0 < tot; t0 += kWarp * U) {
-            uint32_t ue[U], cr[U], xr[U];
+    // from its smaller vertex) and exclusive neighbours.  The rows' entries
+    // above the root form one flat sequence, cut into 32-entry windows with
+    // one entry per lane, across row boundaries: rows are staged 32 at a
+    // time (a lane per row) into the warp's ring as (flat start, entry
+    // offset, list entry), and a window finds each lane's row from the ring
+    // rows that start inside it (one OR-reduction of their start bits and a
+    // population count).  Flat positions wrap modulo 2^32; only differences
+    // below 2^31 are compared.
+    constexpr int W = L::WIN;
+    constexpr int RM = L::RING - 1;
+    uint32_t *rS = ring, *rO = ring + L::RING, *rE = ring + 2 * L::RING;
+    const uint32_t *rowp[K - 2];  // pair-state rows of the prefix vertices
 #pragma unroll
-            for (int i = 0; i < U; i++) {
-                const int t = t0 + i * kWarp + lane;
-                const int r = lb_search(pre, t);
-                const uint32_t er = __shfl_sync(kFull, ej, r);  // the row's list entry: vertex and state vector
-                const uint32_t orow = __shfl_sync(kFull, off, r);
-                cr[i] = pcode | (e_sv(er) << L::SH_ROW);
-                xr[i] = e_id(er);
-                ue[i] = t < tot ? __ldg(g.nbr + (orow + (uint32_t)t)) : 0xFFFFFFFFu;
+    for (int k2 = 0; k2 < K - 2; k2++) rowp[k2] = g.state + (long long)pm[k2] * g.pitch;
+    uint32_t T = 0, C = 0;  // flat entries staged, consumed
+    int tail = 0, cur = -1;  // ring rows staged; last ring row starting before C
+    int jb = jlo;
+    for (;;) {
+        // stage rows while fewer than W windows are pending and the ring has
+        // room for 32 more rows (the live rows are cur .. tail - 1)
+        while (jb < jend && T - C < 32u * W && tail - cur + kWarp <= L::RING) {
+            const int j = jb + lane;
+            uint32_t ej = 0, first = 0;
+            int cnt = 0;
+            if (j < jend) {
+                ej = E[j];
+                const uint32_t x = e_id(ej);
+                const long long nb = g.nptr[x];
+                const int d = g.deg[x];
+                const int st = first_above(g.nbr, nb, d, root);
+                first = (uint32_t)(nb + st);
+                cnt = d - st;
             }
-            uint32_t sv[U][K - 2];
-#pragma unroll
-            for (int i = 0; i < U; i++)
-#pragma unroll
-                for (int k2 = 0; k2 < K - 2; k2++)
-                    sv[i][k2] = ue[i] != 0xFFFFFFFFu ? probe(g.state, g.pitch, pm[k2], ue[i] >> 2) : 0u;
-#pragma unroll
-            for (int i = 0; i < U; i++) {
-                if (ue[i] == 0xFFFFFFFFu) continue;
-                const uint32_t u = ue[i] >> 2, su = ue[i] & 3u;
-                uint32_t mu = 0;
-#pragma unroll
-                for (int k2 = 0; k2 < K - 2; k2++) mu |= sv[i][k2] << (2 * k2);
-                if (mu == 0u) {
-                    sink.add(sink.cls_of(cr[i] | (su << L::SH_PAIR)), 1);  // exclusive leaf
-                } else if (u > xr[i] && in_list<K>(sv[i], u, pm, w2_in_a)) {
-                    const uint32_t base = cr[i] | mu;
-                    sink.add(sink.cls_of(base | (su << L::SH_PAIR)), 1);
-                    sink.add(sink.cls_of(base), -1);
-                }
+            const unsigned nz = __ballot_sync(kFull, cnt > 0);
+            int tot;
+            const int pre = excl_scan(cnt, lane, &tot);
+            if (cnt > 0) {
+                const int slot = (tail + __popc(nz & ((1u << lane) - 1u))) & RM;
+                const uint32_t sflat = T + (uint32_t)pre;
+                rS[slot] = sflat;
+                rO[slot] = first - sflat;
+                rE[slot] = ej;
             }
+            tail += __popc(nz);
+            T += (uint32_t)tot;
+            sink.scanned += (unsigned long long)tot;
+            jb += kWarp;
         }
-        account_moved(sink, lane);
+        if (T == C) break;
+        __syncwarp();
+        const uint32_t pend = T - C;
+        uint32_t ue[W], er[W];
+        bool ok[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            const uint32_t t0 = C + 32u * w;
+            // ring rows cur+1 .. cur+32 may start inside [t0, t0 + 32)
+            uint32_t bit = 0;
+            const int r = cur + 1 + lane;
+            if (r < tail) {
+                const uint32_t sd = rS[r & RM] - t0;
+                if (sd < 32u) bit = 1u << sd;
+            }
+            const uint32_t starts = __reduce_or_sync(kFull, bit);
+            const int row = cur + __popc(starts & (0xFFFFFFFFu >> (31 - lane)));
+            cur += __popc(starts);
+            ok[w] = 32u * w + lane < pend;
+            er[w] = rE[row & RM];
+            const uint32_t off = rO[row & RM];
+            ue[w] = ok[w] ? __ldg(g.nbr + (off + t0 + lane)) : 0u;
+        }
+        uint32_t sv[W][K - 2];
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            const uint32_t u = ue[w] >> 2;
+            const uint32_t wo = u >> 4, sh = (u & 15u) << 1;
+#pragma unroll
+            for (int k2 = 0; k2 < K - 2; k2++) sv[w][k2] = ok[w] ? (__ldg(rowp[k2] + wo) >> sh) & 3u : 0u;
+        }
+        // classes of the step's leaves: an exclusive leaf P + {x, u} (u
+        // adjacent to no prefix vertex) adds one to its class; an adjacent
+        // pair of list members {x, u} (each once, from its smaller vertex)
+        // moves one leaf from the non-adjacent class to its own.  Table reads
+        // of every window are issued before any histogram add, with no branch
+        // in between.
+        int add_cls[W];
+        bool add[W], adj[W];
+        uint32_t base[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            const uint32_t u = ue[w] >> 2, su = ue[w] & 3u;
+            const uint32_t cr = pcode | (e_sv(er[w]) << L::SH_ROW);
+            uint32_t mu = 0;
+#pragma unroll
+            for (int k2 = 0; k2 < K - 2; k2++) mu |= sv[w][k2] << (2 * k2);
+            adj[w] = ok[w] && mu != 0u && u > e_id(er[w]) && in_list<K>(sv[w], u, pm, w2_in_a);
+            add[w] = (ok[w] && mu == 0u) || adj[w];
+            base[w] = cr | mu;
+            add_cls[w] = sink.cls_of(base[w] | (su << L::SH_PAIR));
+        }
+#pragma unroll
+        for (int w = 0; w < W; w++)
+            if (add[w]) sink.add1(add_cls[w], 1);
+#pragma unroll
+        for (int w = 0; w < W; w++)
+            if (adj[w]) sink.add1(sink.cls_of(base[w]), -1);
+        const uint32_t used = pend < 32u * W ? pend : 32u * W;
+        C += used;
+        sink.after_batch(2u * used, lane);  // each entry moves at most two counters by one
     }
     __syncwarp();
 }
 
+// Level-2 extension list of unit (v, w1), w1 at position p of N*(v): part A
+// = the neighbours of v after w1 (ascending), part B = the neighbours of w1
+// above v not adjacent to v (ascending), each entry (x << 6) | state(v, x) |
+// state(w1, x) << 2.  Both parts are read in one pass (a lane holds one
+// position of each), and the neighbours of w1 at or below v are skipped by
+// their ids.  With work non-NULL it receives this lane's share of the list's
+// scan work, sum over members of (degree + kRowCost), gathered with the
+// probes.
 __device__ __forceinline__ int build_level2(const GView &a, long long p, int v, uint32_t w1, const Scratch &sc,
-                                            uint32_t **E_out, int lane) {
+                                            uint32_t **E_out, int lane, long long *work) {
     const long long rb = a.nptr[v];
     const int t = (int)(p - rb);
     const int dv = a.deg[v], dw = a.deg[w1];
+    const long long wb = a.nptr[w1];
     const int A = dv - t - 1;
     const long long ub = (long long)A + dw;
     uint32_t *E = ub <= sc.cap ? sc.buf[0] : sc.ovf[0];
-    for (int q = lane; q < A; q += kWarp) {
-        const uint32_t xe = __ldg(a.nbr + rb + t + 1 + q);
-        const uint32_t x = xe >> 2;
-        E[q] = (x << 6) | (xe & 3u) | (probe(a.state, a.pitch, w1, x) << 2);
-    }
-    const long long wb = a.nptr[w1];
+    const int nq = max(A, dw);
     int pos = A;
-    for (int q0 = first_above(a.nbr, wb, dw, (uint32_t)v); q0 < dw; q0 += kWarp) {
+    long long wk = 0;
+    for (int q0 = 0; q0 < nq; q0 += kWarp) {
         const int q = q0 + lane;
-        uint32_t ue = 0;
-        bool keep = false;
-        if (q < dw) {
-            ue = __ldg(a.nbr + wb + q);
-            keep = probe(a.state, a.pitch, (uint32_t)v, ue >> 2) == 0u;
+        const bool in_a = q < A;
+        uint32_t xa = 0, xb = 0;
+        if (in_a) xa = __ldg(a.nbr + rb + t + 1 + q);
+        if (q < dw) xb = __ldg(a.nbr + wb + q);
+        const uint32_t x = xa >> 2, u = xb >> 2;
+        const bool in_b = q < dw && u > (uint32_t)v;
+        uint32_t sa = 0, sb = 0;
+        int da = 0, db = 0;
+        if (in_a) {
+            sa = probe(a.state, a.pitch, w1, x);
+            if (work) da = a.deg[x];
         }
+        if (in_b) {
+            sb = probe(a.state, a.pitch, (uint32_t)v, u);
+            if (work) db = a.deg[u];
+        }
+        if (in_a) {
+            E[q] = (x << 6) | (xa & 3u) | (sa << 2);
+            wk += da + kRowCost;
+        }
+        const bool keep = in_b && sb == 0u;
         const unsigned ball = __ballot_sync(kFull, keep);
-        if (keep) E[pos + __popc(ball & ((1u << lane) - 1u))] = ((ue >> 2) << 6) | ((ue & 3u) << 2);
+        if (keep) {
+            E[pos + __popc(ball & ((1u << lane) - 1u))] = (u << 6) | ((xb & 3u) << 2);
+            wk += db + kRowCost;
+        }
         pos += __popc(ball);
     }
     __syncwarp();
+    if (work) *work = wk;
     *E_out = E;
     return pos;
 }
@@ -698,16 +819,6 @@ __device__ __forceinline__ long long total_work(int B, WorkFn work, int lane) {
     return s;
 }
 
-__device__ __forceinline__ int row_of(const long long *__restrict__ nptr, int n, long long p) {
-    int lo = 0, hi = n - 1;  // largest v with nptr[v] <= p
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (nptr[mid] <= p) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 // Run part [jlo, jhi) of one unit: virtual rows of its extension list for
 // k = 3, 4, rows of the level-2 list E2 for k = 5.  In phase 1 (jlo = 0,
 // jhi = all) a unit with more than a.light estimated work is queued in chunks
@@ -745,8 +856,10 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
             }
         }
         const uint32_t pm[1] = {(uint32_t)v};
-        if (hi > jlo) count_leaves<K>(g, sink, E, B, jlo, hi, jlo == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, lane);
-        if (rest < B) count_leaves<K>(g, sink, E, B, rest, B, rest == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, lane);
+        if (hi > jlo)
+            count_leaves<K>(g, sink, E, B, jlo, hi, jlo == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, sc.ring, lane);
+        if (rest < B)
+            count_leaves<K>(g, sink, E, B, rest, B, rest == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, sc.ring, lane);
         __syncwarp();
         return;
     }
@@ -784,14 +897,19 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
     int hi = jhi, rest = 0x7FFFFFFF;
     if (K == 4 && COUNT) {
         uint32_t *E2;
-        const int B2 = build_level2(g, unit, v, w1, sc, &E2, lane);
+        long long wk = 0;  // this lane's share of the list's scan work (phase 1)
+        const int B2 = build_level2(g, unit, v, w1, sc, &E2, lane, phase1 ? &wk : nullptr);
         if (B2 <= 0) return;
         hi = min(hi, B2);
         rest = B2;
         if (phase1) {
             auto work = [&](int j) { return (long long)g.deg[e_id(E2[j])] + kRowCost; };
             bool heavy = false;  // as for k = 3: the sum only when it can pass the threshold
-            if ((long long)B2 * wmax > a.light) heavy = total_work(B2, work, lane) > a.light;
+            if ((long long)B2 * wmax > a.light) {
+#pragma unroll
+                for (int d = 16; d; d >>= 1) wk += __shfl_xor_sync(kFull, wk, d);
+                heavy = wk > a.light;
+            }
             if (heavy) {
                 rest = queue_rows(a, unit, vglob, B2, work, lane);
                 if (rest >= B2) return;
@@ -801,9 +919,11 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
         const uint32_t pm[2] = {(uint32_t)v, w1};
         const uint32_t pcode = s01 << (L::SH_ROW + 4);
         if (hi > jlo)
-            count_leaves<K>(g, sink, E2, B2, jlo, hi, jlo == 0, pm, pcode, (uint32_t)v, false, sc.gcnt, lane);
+            count_leaves<K>(g, sink, E2, B2, jlo, hi, jlo == 0, pm, pcode, (uint32_t)v, false, sc.gcnt, sc.ring,
+                            lane);
         if (rest < B2)
-            count_leaves<K>(g, sink, E2, B2, rest, B2, rest == 0, pm, pcode, (uint32_t)v, false, sc.gcnt, lane);
+            count_leaves<K>(g, sink, E2, B2, rest, B2, rest == 0, pm, pcode, (uint32_t)v, false, sc.gcnt, sc.ring,
+                            lane);
         __syncwarp();
         return;
     }
@@ -819,7 +939,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
         }
     }
     uint32_t *E2;
-    const int B2 = build_level2(g, unit, v, w1, sc, &E2, lane);
+    const int B2 = build_level2(g, unit, v, w1, sc, &E2, lane, nullptr);
     if (B2 <= 0) return;
     if (K == 4) {
         // rows of E2 are paired into virtual rows
@@ -885,7 +1005,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
             const uint32_t pm[3] = {(uint32_t)v, w1, w2};
             if (COUNT)
                 count_leaves<K>(g, sink, E3, pos, 0, pos, true, pm, pcode, (uint32_t)v, (e2 & 3u) != 0u, sc.gcnt,
-                                lane);
+                                sc.ring, lane);
             else leaves<K>(g, sink, E3, pos, 0, (pos + 1) / 2, pm, pcode, (uint32_t)v, lane);
             __syncwarp();
         }
@@ -896,9 +1016,12 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
 }
 
 // One instantiation per phase, so each is register-allocated for its own path
-// (phase 1: the unit loop, work estimates and queueing; phase 2: the queue).
-template <int K, bool COUNT, int PHASE>
-__global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? ACC_MINB34C : ACC_MINB34)) k_enum(EnumArgs a) {
+// (phase 1: the unit loop, work estimates and queueing; phase 2: the queue),
+// and per kind of set (SET: several graphs, each seen through its offsets;
+// otherwise one graph read through the kernel's own arrays).
+template <int K, bool COUNT, int PHASE, bool SET>
+__global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? (SET ? ACC_MINB34S : ACC_MINB34C) : ACC_MINB34))
+    k_enum(EnumArgs a) {
     using L = Layout<K>;
     extern __shared__ __align__(16) unsigned char smem[];
     int16_t *lut_s = reinterpret_cast<int16_t *>(smem);
@@ -906,8 +1029,9 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? ACC_MI
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem + L::lut + L::pending);
     uint32_t *ebuf = reinterpret_cast<uint32_t *>(smem + L::lut + L::pending + L::hist);
     uint32_t *groups = reinterpret_cast<uint32_t *>(smem + L::lut + L::pending + L::hist + L::ebuf);
+    uint32_t *rings = reinterpret_cast<uint32_t *>(smem + L::lut + L::pending + L::hist + L::ebuf + L::groups);
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
-    const bool several = a.gs.B > 1;
+    constexpr bool several = SET;
     // phase 2 with nothing queued: no table to stage, nothing to flush
     if constexpr (PHASE == 2)
         if (a.info->queue_tail == 0) return;
@@ -944,6 +1068,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? ACC_MI
     sc.ovf[1] = sc.ovf[0] + a.scratch_per_warp / 2;
     sc.cap = L::CAP;
     sc.gcnt = groups + (size_t)wib * 3 * L::G;
+    sc.ring = rings + (size_t)wib * 3 * L::RING;
     sink.moved = 0;
     sink.scanned = 0;
     const long long nnz = a.info->nnz;
@@ -953,26 +1078,36 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? ACC_MI
 
     if constexpr (PHASE == 1) {
         const long long nunits = K == 3 ? NV : nnz;
+        const int grab = a.gs.B > 1 ? ACC_GRAB_SET : (K == 4 ? ACC_GRAB4 : kGrab);
         for (;;) {
             unsigned long long u0 = 0;
-            const int grab = a.gs.B > 1 ? ACC_GRAB_SET : (K == 4 ? ACC_GRAB4 : kGrab);
             if (lane == 0) u0 = atomicAdd(&a.info->unit_ctr, (unsigned long long)grab);
             u0 = __shfl_sync(kFull, u0, 0);
             if ((long long)u0 >= nunits) break;
             const long long u1 = min((long long)u0 + grab, nunits);
-            int vg = K == 3 ? 0 : row_of(a.nptr, (int)NV, (long long)u0);
+            // k = 4, 5: each grabbed position's row vertex (bit 31: a
+            // neighbour below the row's vertex, not a unit), one per lane
+            uint32_t rows = 0;
+            if (K != 3 && u0 + lane < (unsigned long long)u1) rows = __ldg(a.src + u0 + lane);
             for (long long u = (long long)u0; u < u1; u++) {
+                int vg;
                 if (K == 3) {
                     vg = (int)u;
                 } else {
-                    while (a.nptr[vg + 1] <= u) vg++;
-                    if (u - a.nptr[vg] < a.lo[vg]) continue;  // a neighbour below the row's vertex: not a unit
+                    const uint32_t r = __shfl_sync(kFull, rows, (int)(u - (long long)u0));
+                    if (r >> 31) continue;
+                    vg = (int)r;
                 }
-                const int gi = a.gs.graph_of(vg);
-                const GMeta mt = a.gs.meta(gi);
-                sink.switch_graph(gi, lane);
-                process_unit<K, COUNT>(a, view_of(a, mt), sink, sc, (uint32_t)u, vg - mt.voff, vg, 0, 0x7FFFFFFF,
-                                       true, D, wmax, lane);
+                if constexpr (SET) {
+                    const int gi = a.gs.graph_of(vg);
+                    const GMeta mt = a.gs.meta(gi);
+                    sink.switch_graph(gi, lane);
+                    process_unit<K, COUNT>(a, view_of(a, mt), sink, sc, (uint32_t)u, vg - mt.voff, vg, 0,
+                                           0x7FFFFFFF, true, D, wmax, lane);
+                } else {
+                    process_unit<K, COUNT>(a, view_single(a), sink, sc, (uint32_t)u, vg, vg, 0, 0x7FFFFFFF, true, D,
+                                           wmax, lane);
+                }
             }
         }
     } else {
@@ -984,11 +1119,16 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? ACC_MI
             if (idx >= tail) break;
             const uint4 it = a.queue[idx];
             const int vg = (int)it.w;
-            const int gi = a.gs.graph_of(vg);
-            const GMeta mt = a.gs.meta(gi);
-            sink.switch_graph(gi, lane);
-            process_unit<K, COUNT>(a, view_of(a, mt), sink, sc, it.x, vg - mt.voff, vg, (int)it.y, (int)it.z,
-                                   false, D, wmax, lane);
+            if constexpr (SET) {
+                const int gi = a.gs.graph_of(vg);
+                const GMeta mt = a.gs.meta(gi);
+                sink.switch_graph(gi, lane);
+                process_unit<K, COUNT>(a, view_of(a, mt), sink, sc, it.x, vg - mt.voff, vg, (int)it.y, (int)it.z,
+                                       false, D, wmax, lane);
+            } else {
+                process_unit<K, COUNT>(a, view_single(a), sink, sc, it.x, vg, vg, (int)it.y, (int)it.z, false, D,
+                                       wmax, lane);
+            }
         }
     }
 
@@ -1017,45 +1157,50 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? ACC_MI
     }
 }
 
-template <int K, bool COUNT, int PHASE>
+template <int K, bool COUNT, int PHASE, bool SET>
 int blocks_per_sm() {
     static int cached = 0;
     if (cached) return cached;
-    if (cudaFuncSetAttribute(k_enum<K, COUNT, PHASE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_enum<K, COUNT, PHASE, SET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Layout<K>::total) != cudaSuccess)
         return -1;
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_enum<K, COUNT, PHASE>, kThreads, Layout<K>::total) !=
-            cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_enum<K, COUNT, PHASE, SET>, kThreads,
+                                                      Layout<K>::total) != cudaSuccess ||
         b < 1)
         return -1;
     cached = b;
     return b;
 }
 
-template <int K, bool COUNT, int PHASE>
+template <int K, bool COUNT, int PHASE, bool SET>
 int launch_phase(const EnumArgs &a, int num_sms, cudaStream_t s, int grid_num, int grid_den) {
-    const int bps = blocks_per_sm<K, COUNT, PHASE>();
+    const int bps = blocks_per_sm<K, COUNT, PHASE, SET>();
     if (bps < 1) return ACC_ERR_CUDA;
     int grid = (int)((long long)num_sms * bps * grid_num / grid_den);
     if (grid < num_sms) grid = num_sms;
     if (grid > num_sms * bps) grid = num_sms * bps;
-    k_enum<K, COUNT, PHASE><<<grid, kThreads, Layout<K>::total, s>>>(a);
+    k_enum<K, COUNT, PHASE, SET><<<grid, kThreads, Layout<K>::total, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
 
 template <int K, bool COUNT>
 int launch_k(const EnumArgs &a, int num_sms, int phase, cudaStream_t s, int grid_num, int grid_den) {
-    return phase == 1 ? launch_phase<K, COUNT, 1>(a, num_sms, s, grid_num, grid_den)
-                      : launch_phase<K, COUNT, 2>(a, num_sms, s, grid_num, grid_den);
+    if (a.gs.B > 1)
+        return phase == 1 ? launch_phase<K, COUNT, 1, true>(a, num_sms, s, grid_num, grid_den)
+                          : launch_phase<K, COUNT, 2, true>(a, num_sms, s, grid_num, grid_den);
+    return phase == 1 ? launch_phase<K, COUNT, 1, false>(a, num_sms, s, grid_num, grid_den)
+                      : launch_phase<K, COUNT, 2, false>(a, num_sms, s, grid_num, grid_den);
 }
 
 // Most resident blocks per SM of any instantiation for k (sizes the per-warp
 // overflow lists).
 template <int K>
 int bps_max() {
-    const int b[4] = {blocks_per_sm<K, false, 1>(), blocks_per_sm<K, false, 2>(), blocks_per_sm<K, true, 1>(),
-                      blocks_per_sm<K, true, 2>()};
+    const int b[8] = {blocks_per_sm<K, false, 1, false>(), blocks_per_sm<K, false, 2, false>(),
+                      blocks_per_sm<K, true, 1, false>(),  blocks_per_sm<K, true, 2, false>(),
+                      blocks_per_sm<K, false, 1, true>(),  blocks_per_sm<K, false, 2, true>(),
+                      blocks_per_sm<K, true, 1, true>(),   blocks_per_sm<K, true, 2, true>()};
     int m = 0;
     for (int x : b) {
         if (x < 1) return -1;

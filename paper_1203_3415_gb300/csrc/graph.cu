@@ -496,19 +496,24 @@ __global__ void __launch_bounds__(1024) k_scan_apply(const int *__restrict__ deg
 // entries go to its row's offset plus the entries of the row's earlier
 // chunks (a scan over the lanes, segmented by row and carried from one round
 // to the next), so rows with few neighbours share a warp.
+//
+// With src non-NULL, each entry's position also records its row: src[pos] =
+// global row vertex, bit 31 set when the neighbour is below the row's vertex
+// (the enumeration's phase 1 reads a work unit's vertex from it).
 __global__ void k_fill(GSet gs, const uint32_t *__restrict__ state, const uint32_t *__restrict__ occ, int occ_w,
-                       const long long *__restrict__ nptr, uint32_t *nbr, int rw) {
+                       const long long *__restrict__ nptr, uint32_t *nbr, uint32_t *src, int rw) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long r0 = warp * rw; r0 < gs.NV; r0 += nwarps * rw) {
         const long long v = r0 + lane;
-        int nch = 0, quads = 0;
+        int nch = 0, quads = 0, vloc = 0;
         long long row_word = 0, rbase = 0;
         if (lane < rw && v < gs.NV) {
             for (int w = 0; w < occ_w; w++) nch += __popc(occ[v * occ_w + w]);
             const GMeta mt = gs.meta(gs.graph_of((int)v));
-            row_word = mt.soff + (long long)((int)v - mt.voff) * mt.pitch;
+            vloc = (int)v - mt.voff;
+            row_word = mt.soff + (long long)vloc * mt.pitch;
             quads = (((mt.n + 15) >> 4) + 3) >> 2;  // 16-byte groups within the pitch
             rbase = nptr[v];
         }
@@ -530,6 +535,7 @@ __global__ void k_fill(GSet gs, const uint32_t *__restrict__ state, const uint32
             const long long o_word = __shfl_sync(kFull, row_word, owner);
             const long long o_base = __shfl_sync(kFull, rbase, owner);
             const int o_quads = __shfl_sync(kFull, quads, owner);
+            const int o_vloc = __shfl_sync(kFull, vloc, owner);
             uint32_t xs[32];
             int cnt = 0, q0 = 0;
             if (act) {
@@ -570,7 +576,10 @@ __global__ void k_fill(GSet gs, const uint32_t *__restrict__ state, const uint32
                     uint32_t nz = (xs[t] | (xs[t] >> 1)) & 0x55555555u;
                     while (nz) {
                         const int bit = __ffs(nz) - 1;
-                        nbr[pos++] = ((uint32_t)((q0 * 4 + t) * 16 + (bit >> 1)) << 2) | ((xs[t] >> bit) & 3u);
+                        const int col = (q0 * 4 + t) * 16 + (bit >> 1);
+                        nbr[pos] = ((uint32_t)col << 2) | ((xs[t] >> bit) & 3u);
+                        if (src) src[pos] = (uint32_t)(r0 + owner) | (col < o_vloc ? 0x80000000u : 0u);
+                        pos++;
                         nz &= nz - 1;
                     }
                 }
@@ -772,7 +781,7 @@ int launch_build_graph(const GSet &gs, const BuildBufs &bb, int max_n, int *stat
     int rw = 1;
     while (rw < kWarp && (long long)rw * 2 * num_sms * 64 <= NV) rw *= 2;
     k_fill<<<grid_for((NV + rw - 1) / rw * kWarp, 256, num_sms), 256, 0, s>>>(gs, bb.state, bb.occ, bb.occ_w,
-                                                                              bb.nptr, bb.nbr, rw);
+                                                                              bb.nptr, bb.nbr, bb.src, rw);
     launches++;
     return cudaGetLastError() == cudaSuccess ? launches : ACC_ERR_CUDA;
 }

@@ -31,8 +31,14 @@ template <class T> static bool rd(FILE *f, T *p, size_t n) { return fread(p, siz
 template <int K, bool COUNT>
 static void run(EnumArgs a, int blocks) {
     static_assert(acc::en::Layout<K>::total <= sizeof(emu_smem));
-    run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 1>(a); });
-    run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 2>(a); });
+    // the instantiation the library launches: one graph, or a set of several
+    if (a.gs.B > 1) {
+        run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 1, true>(a); });
+        run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 2, true>(a); });
+    } else {
+        run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 1, false>(a); });
+        run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 2, false>(a); });
+    }
 }
 
 template <int K>
@@ -95,7 +101,15 @@ int main(int argc, char **argv) {
     std::vector<unsigned long long> counts((size_t)B * ncls, 0);
     int status = 0;
 
+    // row of each entry, bit 31 for a neighbour below the row's vertex (the
+    // first lo[v] entries of a sorted row), as the neighbour-list fill writes it
+    std::vector<uint32_t> src(nnz + 1);
+    for (long long v = 0; v < NV; v++)
+        for (long long p = nptr[v]; p < nptr[v + 1]; p++)
+            src[p] = (uint32_t)v | (p - nptr[v] < lo[v] ? 0x80000000u : 0u);
+
     EnumArgs a{};
+    a.src = src.data();
     a.state = st.data();
     a.deg = deg.data();
     a.lo = lo.data();

@@ -31,7 +31,7 @@ int main(int argc, char **argv) {
     gs.one.pitch = pitch;
     std::vector<uint32_t> out(nptr[n] + 1, 0xEEEEEEEEu);
     run_warps(2, 64, [&] {
-        acc::k_fill(gs, st.data(), occ.data(), (int)occ_w, nptr.data(), out.data(), (int)rw);
+        acc::k_fill(gs, st.data(), occ.data(), (int)occ_w, nptr.data(), out.data(), nullptr, (int)rw);
     });
     FILE *o = fopen(argv[2], "wb");
     fwrite(out.data(), 4, nptr[n], o);

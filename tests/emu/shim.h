@@ -241,6 +241,15 @@ inline int __reduce_max_sync(unsigned, int v) {
     wsync();
     return r;
 }
+inline unsigned __reduce_or_sync(unsigned, unsigned v) {
+    wsync();
+    tw->slot[lane_()] = (uint64_t)v;
+    wsync();
+    unsigned r = 0;
+    for (int i = 0; i < 32; i++) r |= (unsigned)tw->slot[i];
+    wsync();
+    return r;
+}
 // IEEE double operations rounded to nearest, as the CUDA names define them;
 // the host's own double arithmetic is that (compiled without contraction)
 inline double __dadd_rn(double a, double b) { return a + b; }

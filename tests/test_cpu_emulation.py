@@ -108,7 +108,7 @@ def emu_bins(tmp_path_factory):
         _function(graph, "__device__ __forceinline__ int warp_excl_scan") + "\n" +
         _function(graph, "__global__ void k_fill("))
     en = open(os.path.join(CSRC, "enum.cu")).read()
-    region = _region(en, "// Tuning knobs", "template <int K, bool COUNT, int PHASE>\nint blocks_per_sm")
+    region = _region(en, "// Tuning knobs", "template <int K, bool COUNT, int PHASE, bool SET>\nint blocks_per_sm")
     # the kernels' dynamic shared memory becomes a static host buffer; the
     # histogram drain threshold becomes a compile-time parameter
     for old, new in (("extern __shared__ __align__(16) unsigned char smem[];", "unsigned char *smem = emu_smem;"),
