@@ -10,7 +10,8 @@ is the headline, and the default run adds "sub_records" for every other
 workload of the benchmark set, each timed under its own clock samples: k=3
 on the Erdos-Renyi graph, k=5 on the regulatory-shaped graph, the 4008-graph
 batch (graphs/s, beside one graph per launch) and the request server at 200
-and 100 requests/s (latency percentiles, subgraphs/s).
+(saturated) and 50 (unsaturated) requests/s (latency percentiles,
+subgraphs/s, beside the same requests counted one at a time).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload NAME] [--headline-only]
@@ -501,9 +502,10 @@ def run_ours(args):
         r = measure_batch(env, max(3, min(args.steps, 10)), args.warmup, not args.no_cpu_baseline, cpu_budget_s=5.0)
         if r is not None:
             subs[BATCH_WORKLOAD] = r
-        for rate in (200.0, 100.0):
+        alone = {}
+        for rate in (200.0, 50.0):
             r = measure_serving(env, args.sub_serve_seconds, rate, args.slots, args.mem_budget_gb, args.serve_policy,
-                                args.serve_aging_s)
+                                args.serve_aging_s, alone)
             if r is not None:
                 subs[f"{SERVING_WORKLOAD}_{int(rate)}_per_s"] = r
     if env.rank == 0:
@@ -848,7 +850,33 @@ def significance_cpu_baseline(bases, budget_s=10.0):
             "sample": f"{done} randomised copies of base {b} (n={g.n}, m={g.m}): swaps and ESU count each"}
 
 
-def measure_serving(env, window_s, rate, slots, mem_budget_gb, policy, aging_s):
+def serving_alone_times(env, graphs, tens, combos):
+    """GPU seconds and subgraphs of each (graph, k) in combos counted alone
+    through acc_motif_count on the whole GPU, one after another (CUDA events
+    on the launching stream; the workspace is first grown for the largest
+    graph, outside the timed counts)."""
+    torch, acc = env.torch, env.acc
+    counter = acc.Counter(env.local)
+    stream = torch.cuda.current_stream(env.dev)
+    big = max(range(len(graphs)), key=lambda i: graphs[i].n)
+    for k in (3, 4, 5):
+        counter.prepare(k)
+    counter.count(tens[big][0], tens[big][1], graphs[big].n, 3)
+    out = {}
+    counts = torch.zeros(9364, dtype=torch.int64, device=env.dev)
+    for gi, k in sorted(combos):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c = counter.count(tens[gi][0], tens[gi][1], graphs[gi].n, k, counts=counts[:acc.NUM_CLASSES[k]],
+                          stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(env.dev)
+        out[(gi, k)] = (e0.elapsed_time(e1) / 1000.0, int(c.sum().item()))
+    counter.close()
+    return out
+
+
+def measure_serving(env, window_s, rate, slots, mem_budget_gb, policy, aging_s, alone=None):
     """Serving workload: 64 resident directed Chung-Lu graphs (n log-uniform
     in [100, 50000], mean out-degree 4-10), a Poisson stream of requests at
     `rate` per second with k in {3: 50%, 4: 35%, 5: 15%}, replayed in real
@@ -921,6 +949,18 @@ def measure_serving(env, window_s, rate, slots, mem_budget_gb, policy, aging_s):
     srv.close()
     lat = np.array(lat)
     local_rate = units / t_end
+    # the same requests counted one at a time on the whole GPU
+    one_at_a_time = None
+    if alone is not None:
+        missing = {(g, k) for _, g, k in reqs} - set(alone)
+        if missing:
+            alone.update(serving_alone_times(env, graphs, tens, missing))
+        gpu_s = sum(alone[(g, k)][0] for _, g, k in reqs)
+        sub = sum(alone[(g, k)][1] for _, g, k in reqs)
+        one_at_a_time = {"value": sub / gpu_s, "unit": UNIT, "requests_per_s": len(reqs) / gpu_s,
+                         "gpu_seconds": gpu_s,
+                         "how": "each distinct (graph, k) of the request list counted alone by acc_motif_count "
+                                "(CUDA events), summed over the requests"}
     value = reduce_sum(dist, local_rate, dev) if dist is not None else local_rate
     if env.rank != 0:
         return None
@@ -939,6 +979,8 @@ def measure_serving(env, window_s, rate, slots, mem_budget_gb, policy, aging_s):
         "failed": failed, "wall_s": t_end,
         "gpu_busy_frac": busy / t_end if t_end > 0 else None,
         "subgraphs_served": units,
+        "one_request_at_a_time": one_at_a_time,
+        "served_over_one_at_a_time": (value / one_at_a_time["value"]) if one_at_a_time else None,
         "clocks": clocks,
         "parity": "every served result equals the oracle's: tests/test_gpu_serving.py",
     }
@@ -947,7 +989,7 @@ def measure_serving(env, window_s, rate, slots, mem_budget_gb, policy, aging_s):
 def run_serving_bench(args):
     env = GpuEnv()
     rec = measure_serving(env, args.serve_seconds, args.serve_rate, args.slots, args.mem_budget_gb,
-                          args.serve_policy, args.serve_aging_s)
+                          args.serve_policy, args.serve_aging_s, {})
     if env.rank == 0:
         print(json.dumps(bench_line(env, rec, rec["steps"], 3)), flush=True)
     env.close()
@@ -966,7 +1008,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="serving: arrival window")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serving: Poisson arrival rate per second")
     ap.add_argument("--sub-serve-seconds", type=float, default=5.0,
-                    help="serving window of the default run's serving sub-records (200 and 100 requests/s)")
+                    help="serving window of the default run's serving sub-records (200 and 50 requests/s)")
     ap.add_argument("--headline-only", action="store_true",
                     help="default workload: print the headline line without the other workloads' sub-records")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent requests")

@@ -400,6 +400,27 @@ ACC_API int acc_motif_last_stats(acc_ctx *ctx, int64_t *h_stats);
 ACC_API int acc_ctx_set_mode(acc_ctx *ctx, int mode);
 
 /*
+ * Adjacency structure the count mode probes (ACC_MODE_COUNT; the other modes
+ * always read the dense pair-state block).  The paper tests adjacency "in
+ * O(1)" by hashing (its k=4 and k=5 complexity discussion).
+ *  ACC_ADJ_DENSE: the dense n x n pair-state block (2 bits per ordered pair),
+ *   one load per probe; n^2/4 bytes, so its probes leave L2 for large n.
+ *  ACC_ADJ_HASH: per-vertex open-addressing tables of the neighbour entries
+ *   (32 bytes per entry of the G* neighbour lists, built on the device after
+ *   the lists), one 16-byte load per probe in the common case.
+ *  ACC_ADJ_AUTO (default): hashed when the largest graph of the count or
+ *   batch has at least 32768 vertices for k = 5, 131072 for k = 3, 4 (where
+ *   the dense probes, out of L2, get slower than the hashed ones); dense
+ *   otherwise.
+ * The dense block is built in every case (it also deduplicates the arcs).
+ * All choices give identical counts.  Errors: ACC_ERR_ARG.
+ */
+#define ACC_ADJ_AUTO 0
+#define ACC_ADJ_DENSE 1
+#define ACC_ADJ_HASH 2
+ACC_API int acc_ctx_set_adjacency(acc_ctx *ctx, int adjacency);
+
+/*
  * Work schedule of the enumeration (not in the paper: how the ESU units are
  * spread over the GPU).  A unit (a root, or a root and one neighbour) whose
  * estimated work is at most `light` runs whole on one warp; a heavier one is

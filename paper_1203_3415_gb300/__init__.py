@@ -40,10 +40,12 @@ EXPORTS = (
     "acc_motif_build_table_static", "acc_ctx_set_mode", "acc_server_create", "acc_server_destroy", "acc_server_add_graph",
     "acc_server_reserve", "acc_server_submit", "acc_server_progress", "acc_server_poll", "acc_server_drain",
     "acc_server_set_policy", "acc_ctx_set_schedule", "acc_ctx_get_schedule", "acc_motif_batch_autotune",
+    "acc_ctx_set_adjacency",
 )
 ACC_REQ_QUEUED, ACC_REQ_RUNNING, ACC_REQ_DONE = 0, 1, 2
 ACC_SERVE_FIFO, ACC_SERVE_SHORTEST = 0, 1
 ACC_MODE_COUNT, ACC_MODE_ENUMERATE, ACC_MODE_FORMULA = 0, 1, 2
+ACC_ADJ_AUTO, ACC_ADJ_DENSE, ACC_ADJ_HASH = 0, 1, 2
 ACC_RAND_SWAP, ACC_RAND_MUTUAL = 0, 1
 
 
@@ -80,6 +82,7 @@ def declare(lib):
     lib.acc_motif_last_stats.argtypes = [vp, vp]
     lib.acc_ctx_set_timing.argtypes = [vp, ctypes.c_int]
     lib.acc_ctx_set_mode.argtypes = [vp, ctypes.c_int]
+    lib.acc_ctx_set_adjacency.argtypes = [vp, ctypes.c_int]
     lib.acc_motif_last_timing.argtypes = [vp, vp]
     lib.acc_motif_build_table_static.argtypes = [ctypes.c_int, vp, vp, vp]
     lib.acc_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, i32, i64]
@@ -218,6 +221,10 @@ def acc_motif_last_stats(ctx: int, h_stats: int) -> int:
 
 def acc_ctx_set_mode(ctx: int, mode: int) -> int:
     return _L().acc_ctx_set_mode(ctx, mode)
+
+
+def acc_ctx_set_adjacency(ctx: int, adjacency: int) -> int:
+    return _L().acc_ctx_set_adjacency(ctx, adjacency)
 
 
 def acc_ctx_set_timing(ctx: int, on: int) -> int:
@@ -528,6 +535,10 @@ class Counter:
         """ACC_MODE_COUNT (default) or ACC_MODE_ENUMERATE; same counts."""
         _check(acc_ctx_set_mode(self.ctx, mode), "acc_ctx_set_mode")
         self.mode = mode
+
+    def set_adjacency(self, adjacency: int):
+        """ACC_ADJ_AUTO (default), ACC_ADJ_DENSE or ACC_ADJ_HASH; same counts."""
+        _check(acc_ctx_set_adjacency(self.ctx, adjacency), "acc_ctx_set_adjacency")
 
     def set_schedule(self, light: int = 0, target: int = 0):
         """Enumeration work schedule (0: default); see acc_ctx_set_schedule."""

@@ -17,6 +17,14 @@ using namespace acc;
 namespace {
 
 constexpr unsigned long long kQueueCap = 1ull << 22;
+// ACC_ADJ_AUTO: count-mode probes read hashed tables for sets whose largest
+// graph has at least this many vertices (k = 5; k = 3, 4), where the dense
+// block's probes (n^2/4 bytes, out of L2) get slower than the hashed ones
+// (measured on GB300: k = 5 dense/hashed 82/87 scanned entries per ns at
+// n = 40000, 53/87 at 80000; k = 4 149/107 at 40000, 122/108 at 80000).
+constexpr int kHashMinN5 = 32768;
+constexpr int kHashMinN34 = 131072;
+bool hash_auto(int k, int max_n) { return max_n >= (k == 5 ? kHashMinN5 : kHashMinN34); }
 // Below this many vertices the renumbering pass costs more than it saves.
 constexpr int kRelabelMinN = 1024;
 
@@ -150,10 +158,17 @@ void release_luts(acc_ctx *c) {
 
 long long scratch_per_warp(int max_n) { return 2 * (((long long)max_n + 32 + 31) & ~31LL); }
 
+bool uses_hash(const acc_ctx *c, int k, int max_n) {
+    return c->mode == ACC_MODE_COUNT &&
+           (c->adjacency == ACC_ADJ_HASH || (c->adjacency == ACC_ADJ_AUTO && hash_auto(k, max_n)));
+}
+
 // Workspace for a set of NV vertices in blocks of state_words words, with at
 // most `arcs` arcs and graphs of at most max_n vertices.
 int ensure_workspace(acc_ctx *c, long long NV, long long state_words, long long arcs, int max_n, int k) {
     int rc;
+    if (uses_hash(c, k, max_n) && (rc = grow(&c->nh, &c->nh_cap, (size_t)kNhWords * (size_t)(2 * arcs) + 4)))
+        return rc;
     {
         // a reallocation (the capacity changes; the address may not) brings
         // memory that is not zero: the next build sweeps it
@@ -234,6 +249,14 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
                                 (long long)gs.B * num_classes(k), relabel, c->num_sms, s);
     if (rc < 0) return rc;
     launches += rc;
+    // count mode on a large set: probes read hashed tables, built from the
+    // sorted neighbour lists
+    const bool hash = gs.NV > 0 && uses_hash(c, k, max_n);
+    if (hash) {
+        rc = launch_nh_build(c->nptr, c->deg, c->nbr, c->src, c->info, 2 * gs.M, c->nh, c->num_sms, s);
+        if (rc < 0) return rc;
+        launches += rc;
+    }
     if (c->timing && !ok(cudaEventRecord(c->ev[1], s))) return ACC_ERR_CUDA;
     EnumArgs a;
     a.state = c->state;
@@ -242,6 +265,7 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     a.nptr = c->nptr;
     a.nbr = c->nbr;
     a.src = c->src;
+    a.nh = hash ? reinterpret_cast<const uint4 *>(c->nh) : nullptr;
     a.lut = c->lut_sv[k];
     a.gs = gs;
     a.max_n = max_n;
@@ -345,9 +369,10 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
         key.mode = c->mode;
         key.grid_num = c->grid_num;
         key.grid_den = c->grid_den;
-        const void *ws[18] = {c->state, c->deg, c->lo, c->label, c->deg_in, c->nptr, c->tiles, c->nbr, c->occ,
+        key.adjacency = c->adjacency;
+        const void *ws[20] = {c->state, c->deg, c->lo, c->label, c->deg_in, c->nptr, c->tiles, c->nbr, c->occ,
                               c->info, c->queue, c->scratch, c->lut[k], c->lut_sv[k], c->class_code_dev[k],
-                              c->f5_pre, c->status_dev, c->src};
+                              c->f5_pre, c->status_dev, c->src, c->nh, nullptr};
         memcpy(key.ws, ws, sizeof(ws));
         bool have = c->cg_exec && memcmp(&key, &c->cg_key, sizeof(key)) == 0;
         // capture only when a count repeats: a one-off count runs one by one
@@ -400,7 +425,8 @@ namespace acc {
 long long ctx_footprint(const acc_ctx *c, long long n, long long m, int k) {
     const long long pitch = state_pitch((int)n);
     const long long warps = enum_grid_warps(k, c->num_sms);
-    const long long bytes = n * pitch * 4 + 5 * 4 * (n + 1) + 8 * (n + 1) + 8 * (2 * m + 1) +
+    const long long hash_bytes = uses_hash(c, k, (int)n) ? 4LL * kNhWords * (2 * m + 1) : 0;
+    const long long bytes = n * pitch * 4 + 5 * 4 * (n + 1) + 8 * (n + 1) + 8 * (2 * m + 1) + hash_bytes +
                             4 * n * occ_words((int)n) +
                             (long long)kQueueCap * 16 + scratch_per_warp((int)n) * (warps > 0 ? warps : 0) * 4;
     return bytes + bytes / 4;
@@ -471,6 +497,7 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaFree(c->occ);
     cudaFree(c->nbr);
     cudaFree(c->src);
+    cudaFree(c->nh);
     cudaFree(c->info);
     cudaFree(c->queue);
     cudaFree(c->scratch);
@@ -767,6 +794,13 @@ int acc_motif_last_stats(acc_ctx *c, int64_t *h_stats) {
     h_stats[4] = gi.maxdeg;
     h_stats[5] = c->last_blocks;
     h_stats[6] = (int64_t)gi.scanned;
+    return ACC_OK;
+}
+
+int acc_ctx_set_adjacency(acc_ctx *c, int adjacency) {
+    if (!c || (adjacency != ACC_ADJ_AUTO && adjacency != ACC_ADJ_DENSE && adjacency != ACC_ADJ_HASH))
+        return ACC_ERR_ARG;
+    c->adjacency = adjacency;
     return ACC_OK;
 }
 

@@ -146,6 +146,24 @@ inline long long state_pitch(int n) {
     return (w + 3) & ~3LL;
 }
 
+// Hashed adjacency (for graphs whose dense pair-state block would not stay
+// in L2): vertex p's neighbour entries (u << 2) | state(p, u) sit in an
+// open-addressing table of 2^lg buckets of four 32-bit slots, lg = ceil(log2
+// deg(p)) (at most one entry per bucket on average), at word kNhWords *
+// nptr[p] of the table array (the region of kNhWords * deg(p) words holds
+// it).  0 marks an empty slot (no entry is 0: its state is nonzero).  An
+// entry goes to the bucket of its neighbour's hash, or the next bucket with a
+// free slot, cyclically.
+constexpr int kNhWords = 8;
+__host__ __device__ inline uint32_t nh_lg(int d) {
+    uint32_t lg = 0;
+    while ((1 << lg) < d) lg++;
+    return lg;
+}
+__host__ __device__ inline uint32_t nh_bucket(uint32_t u, uint32_t lg) {
+    return lg ? (u * 0x9E3779B1u) >> (32u - lg) : 0u;  // multiplicative hash, top lg bits
+}
+
 // First-error-wins status update.
 __device__ inline void set_status(int *status, int err) {
     if (status) atomicCAS(status, 0, err);
@@ -181,6 +199,11 @@ struct BuildBufs {
 };
 int launch_build_graph(const GSet &gs, const BuildBufs &b, int max_n, int *status, unsigned long long *counts,
                        long long ncounts, bool relabel, int num_sms, cudaStream_t s);
+// Hashed adjacency of a built set: nh (kNhWords * max_entries words) is
+// cleared and every neighbour entry inserted; max_entries bounds the set's
+// 2 |E*| (the exact count is read on the device).
+int launch_nh_build(const long long *nptr, const int *deg, const uint32_t *nbr, const uint32_t *src,
+                    const GraphInfo *info, long long max_entries, uint32_t *nh, int num_sms, cudaStream_t s);
 // Zero the pair-state chunks a build set (by its occupancy bitmap), leaving
 // the buffer all zero.
 int launch_clear_graph(const GSet &gs, uint32_t *state, const uint32_t *occ, int occ_w, int num_sms, cudaStream_t s);
@@ -208,6 +231,7 @@ struct EnumArgs {
     const long long *nptr;
     const uint32_t *nbr;        // entries hold local ids
     const uint32_t *src;        // global row vertex of each entry, bit 31: neighbour below it
+    const uint4 *nh;            // hashed adjacency (count mode), or NULL: probes read the dense block
     const int16_t *lut;         // class table in the state-vector layout
     GSet gs;
     int max_n;                  // largest graph of the set

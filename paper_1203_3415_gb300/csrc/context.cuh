@@ -39,6 +39,9 @@ struct acc_ctx {
     uint32_t *nbr = nullptr;
     uint32_t *src = nullptr;  // row of each neighbour entry
     size_t src_cap = 0;
+    uint32_t *nh = nullptr;   // hashed adjacency tables
+    size_t nh_cap = 0;
+    int adjacency = ACC_ADJ_AUTO;
     uint32_t *occ = nullptr;  // pair-state row occupancy bitmaps
     size_t occ_cap = 0;
     size_t nbr_cap = 0;
@@ -92,8 +95,8 @@ struct acc_ctx {
     struct CountKey {
         const void *rowptr, *col, *counts, *status;
         long long m, light, target;
-        int n, k, mode, grid_num, grid_den, pad;
-        const void *ws[18];
+        int n, k, mode, grid_num, grid_den, adjacency;
+        const void *ws[20];
     } cg_key = {}, cg_seen = {};  // the captured graph's key; the last key counted one by one
     int cg_launches = 0;
     long long cg_units = 0;

@@ -144,8 +144,44 @@ struct GView {
     const int *deg;
     const int *lo;
     const uint32_t *nbr;
+    const uint32_t *nh;     // hashed adjacency (tables at kNhWords * nptr), or NULL
     int n;
 };
+
+// One prefix vertex's adjacency as the probes read it: its dense pair-state
+// row (HASH false), or its hashed table and the table's log2 bucket count.
+struct PRow {
+    const uint32_t *p;
+    uint32_t lg;
+};
+
+template <bool HASH>
+__device__ __forceinline__ PRow prow(const GView &g, uint32_t a) {
+    if constexpr (HASH) return PRow{g.nh + (long long)kNhWords * g.nptr[a], nh_lg(g.deg[a])};
+    else return PRow{g.state + (long long)a * g.pitch, 0u};
+}
+
+// state(a, b) for the prefix vertex a of row r.  Hashed: the bucket of b,
+// then the following ones while they are full (an empty slot ends the
+// search; an empty slot also reads as state 0 when b is vertex 0).
+template <bool HASH>
+__device__ __forceinline__ uint32_t pget(const PRow &r, uint32_t b) {
+    if constexpr (HASH) {
+        const uint32_t m = (1u << r.lg) - 1u;
+        uint32_t k = nh_bucket(b, r.lg);
+        for (uint32_t tries = 0; tries <= m; tries++, k = (k + 1u) & m) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4 *>(r.p) + k);
+            if ((q.x >> 2) == b) return q.x & 3u;
+            if ((q.y >> 2) == b) return q.y & 3u;
+            if ((q.z >> 2) == b) return q.z & 3u;
+            if ((q.w >> 2) == b) return q.w & 3u;
+            if (!q.w) return 0u;  // slots fill in order: a bucket with room ends the search
+        }
+        return 0u;
+    } else {
+        return (__ldg(r.p + (b >> 4)) >> ((b & 15u) << 1)) & 3u;
+    }
+}
 
 // The only graph of a single-graph count: its arrays are the kernel's own
 // (global and local ids coincide).
@@ -157,6 +193,7 @@ __device__ __forceinline__ GView view_single(const EnumArgs &a) {
     g.deg = a.deg;
     g.lo = a.lo;
     g.nbr = a.nbr;
+    g.nh = reinterpret_cast<const uint32_t *>(a.nh);
     g.n = a.gs.one.n;
     return g;
 }
@@ -169,6 +206,7 @@ __device__ __forceinline__ GView view_of(const EnumArgs &a, const GMeta &mt) {
     g.deg = a.deg + mt.voff;
     g.lo = a.lo + mt.voff;
     g.nbr = a.nbr;
+    g.nh = reinterpret_cast<const uint32_t *>(a.nh);
     g.n = mt.n;
     return g;
 }
@@ -511,7 +549,7 @@ __device__ __forceinline__ bool in_list(const uint32_t *s, uint32_t u, const uin
 // and the same scan yields the exclusive leaves P + {x, u}.  `bulk` (set for
 // exactly one chunk of a list) adds the group-pair counts.  w2_in_a (k = 5)
 // says whether w2 lies in part A of the level-2 list.
-template <int K>
+template <int K, bool HASH>
 __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, const uint32_t *E, int B, int jlo,
                                              int jend, bool bulk, const uint32_t *pm, uint32_t pcode,
                                              uint32_t root, bool w2_in_a, uint32_t *gcnt, uint32_t *ring, int lane) {
@@ -565,9 +603,9 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
     constexpr int W = L::WIN;
     constexpr int RM = L::RING - 1;
     uint32_t *rS = ring, *rO = ring + L::RING, *rE = ring + 2 * L::RING;
-    const uint32_t *rowp[K - 2];  // pair-state rows of the prefix vertices
+    PRow rowp[K - 2];  // adjacency of the prefix vertices
 #pragma unroll
-    for (int k2 = 0; k2 < K - 2; k2++) rowp[k2] = g.state + (long long)pm[k2] * g.pitch;
+    for (int k2 = 0; k2 < K - 2; k2++) rowp[k2] = prow<HASH>(g, pm[k2]);
     uint32_t T = 0, C = 0;  // flat entries staged, consumed
     int tail = 0, cur = -1;  // ring rows staged; last ring row starting before C
     int jb = jlo;
@@ -629,9 +667,8 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
 #pragma unroll
         for (int w = 0; w < W; w++) {
             const uint32_t u = ue[w] >> 2;
-            const uint32_t wo = u >> 4, sh = (u & 15u) << 1;
 #pragma unroll
-            for (int k2 = 0; k2 < K - 2; k2++) sv[w][k2] = ok[w] ? (__ldg(rowp[k2] + wo) >> sh) & 3u : 0u;
+            for (int k2 = 0; k2 < K - 2; k2++) sv[w][k2] = ok[w] ? pget<HASH>(rowp[k2], u) : 0u;
         }
         // classes of the step's leaves: an exclusive leaf P + {x, u} (u
         // adjacent to no prefix vertex) adds one to its class; an adjacent
@@ -675,8 +712,10 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
 // their ids.  With work non-NULL it receives this lane's share of the list's
 // scan work, sum over members of (degree + kRowCost), gathered with the
 // probes.
+template <bool HASH>
 __device__ __forceinline__ int build_level2(const GView &a, long long p, int v, uint32_t w1, const Scratch &sc,
                                             uint32_t **E_out, int lane, long long *work) {
+    const PRow row_v = prow<HASH>(a, (uint32_t)v), row_w1 = prow<HASH>(a, w1);
     const long long rb = a.nptr[v];
     const int t = (int)(p - rb);
     const int dv = a.deg[v], dw = a.deg[w1];
@@ -698,11 +737,11 @@ __device__ __forceinline__ int build_level2(const GView &a, long long p, int v, 
         uint32_t sa = 0, sb = 0;
         int da = 0, db = 0;
         if (in_a) {
-            sa = probe(a.state, a.pitch, w1, x);
+            sa = pget<HASH>(row_w1, x);
             if (work) da = a.deg[x];
         }
         if (in_b) {
-            sb = probe(a.state, a.pitch, (uint32_t)v, u);
+            sb = pget<HASH>(row_v, u);
             if (work) db = a.deg[u];
         }
         if (in_a) {
@@ -825,7 +864,7 @@ __device__ __forceinline__ long long total_work(int B, WorkFn work, int lane) {
 // instead.  D is the per-row allowance for exclusive neighbours (mean degree
 // + 1); wmax bounds the count mode's work of one row (largest degree + row
 // cost), so a short list skips summing its rows' work.
-template <int K, bool COUNT>
+template <int K, bool COUNT, bool HASH>
 __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, const Scratch &sc, uint32_t unit,
                              int v, int vglob, int jlo, int jhi, bool phase1, long long D, long long wmax, int lane) {
     using L = Layout<K>;
@@ -857,9 +896,9 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
         }
         const uint32_t pm[1] = {(uint32_t)v};
         if (hi > jlo)
-            count_leaves<K>(g, sink, E, B, jlo, hi, jlo == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, sc.ring, lane);
+            count_leaves<K, HASH>(g, sink, E, B, jlo, hi, jlo == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, sc.ring, lane);
         if (rest < B)
-            count_leaves<K>(g, sink, E, B, rest, B, rest == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, sc.ring, lane);
+            count_leaves<K, HASH>(g, sink, E, B, rest, B, rest == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, sc.ring, lane);
         __syncwarp();
         return;
     }
@@ -898,7 +937,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
     if (K == 4 && COUNT) {
         uint32_t *E2;
         long long wk = 0;  // this lane's share of the list's scan work (phase 1)
-        const int B2 = build_level2(g, unit, v, w1, sc, &E2, lane, phase1 ? &wk : nullptr);
+        const int B2 = build_level2<HASH>(g, unit, v, w1, sc, &E2, lane, phase1 ? &wk : nullptr);
         if (B2 <= 0) return;
         hi = min(hi, B2);
         rest = B2;
@@ -919,10 +958,10 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
         const uint32_t pm[2] = {(uint32_t)v, w1};
         const uint32_t pcode = s01 << (L::SH_ROW + 4);
         if (hi > jlo)
-            count_leaves<K>(g, sink, E2, B2, jlo, hi, jlo == 0, pm, pcode, (uint32_t)v, false, sc.gcnt, sc.ring,
+            count_leaves<K, HASH>(g, sink, E2, B2, jlo, hi, jlo == 0, pm, pcode, (uint32_t)v, false, sc.gcnt, sc.ring,
                             lane);
         if (rest < B2)
-            count_leaves<K>(g, sink, E2, B2, rest, B2, rest == 0, pm, pcode, (uint32_t)v, false, sc.gcnt, sc.ring,
+            count_leaves<K, HASH>(g, sink, E2, B2, rest, B2, rest == 0, pm, pcode, (uint32_t)v, false, sc.gcnt, sc.ring,
                             lane);
         __syncwarp();
         return;
@@ -939,7 +978,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
         }
     }
     uint32_t *E2;
-    const int B2 = build_level2(g, unit, v, w1, sc, &E2, lane, nullptr);
+    const int B2 = build_level2<HASH>(g, unit, v, w1, sc, &E2, lane, nullptr);
     if (B2 <= 0) return;
     if (K == 4) {
         // rows of E2 are paired into virtual rows
@@ -970,6 +1009,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
     // fields: slot 1 at bit 18 (state(v, w1)), slot 2 at bit 14 (w2's states
     // to v and w1)
     const uint32_t pc01 = s01 << 18;
+    const PRow row_v = prow<HASH>(g, (uint32_t)v), row_w1 = prow<HASH>(g, w1);
     for (int pass = 0; pass < 2; pass++) {
         const int r0 = pass == 0 ? jlo : rest;
         const int r1 = pass == 0 ? hi : B2;
@@ -981,30 +1021,34 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
             const int dw = g.deg[w2];
             const long long ub = (long long)A3 + dw;
             uint32_t *E3 = ub <= sc.cap ? sc.buf[1] : sc.ovf[1];
-            for (int q = lane; q < A3; q += kWarp) {
-                const uint32_t xe = E2[j2 + 1 + q];
-                const uint32_t x = e_id(xe);
-                E3[q] = (x << 6) | (xe & 15u) | (probe(g.state, g.pitch, w2, x) << 4);
-            }
+            // level-3 list: the level-2 list after w2 (with w2's states),
+            // then the neighbours of w2 above v adjacent to neither v nor w1,
+            // both read in one pass (the neighbours at or below v skipped by
+            // their ids)
+            const PRow row_w2 = prow<HASH>(g, w2);
             const long long wb = g.nptr[w2];
+            const int nq = max(A3, dw);
             int pos = A3;
-            for (int q0 = first_above(g.nbr, wb, dw, (uint32_t)v); q0 < dw; q0 += kWarp) {
+            for (int q0 = 0; q0 < nq; q0 += kWarp) {
                 const int q = q0 + lane;
-                uint32_t ue = 0;
+                const bool in_a = q < A3;
+                uint32_t xe = 0, ue = 0;
+                if (in_a) xe = E2[j2 + 1 + q];
+                if (q < dw) ue = __ldg(g.nbr + wb + q);
+                const uint32_t x = e_id(xe), u = ue >> 2;
+                uint32_t sa = 0;
                 bool keep = false;
-                if (q < dw) {
-                    ue = __ldg(g.nbr + wb + q);
-                    const uint32_t u = ue >> 2;
-                    keep = probe(g.state, g.pitch, (uint32_t)v, u) == 0u && probe(g.state, g.pitch, w1, u) == 0u;
-                }
+                if (in_a) sa = pget<HASH>(row_w2, x);
+                if (q < dw && u > (uint32_t)v) keep = pget<HASH>(row_v, u) == 0u && pget<HASH>(row_w1, u) == 0u;
+                if (in_a) E3[q] = (x << 6) | (xe & 15u) | (sa << 4);
                 const unsigned ball = __ballot_sync(kFull, keep);
-                if (keep) E3[pos + __popc(ball & ((1u << lane) - 1u))] = ((ue >> 2) << 6) | ((ue & 3u) << 4);
+                if (keep) E3[pos + __popc(ball & ((1u << lane) - 1u))] = (u << 6) | ((ue & 3u) << 4);
                 pos += __popc(ball);
             }
             __syncwarp();
             const uint32_t pm[3] = {(uint32_t)v, w1, w2};
             if (COUNT)
-                count_leaves<K>(g, sink, E3, pos, 0, pos, true, pm, pcode, (uint32_t)v, (e2 & 3u) != 0u, sc.gcnt,
+                count_leaves<K, HASH>(g, sink, E3, pos, 0, pos, true, pm, pcode, (uint32_t)v, (e2 & 3u) != 0u, sc.gcnt,
                                 sc.ring, lane);
             else leaves<K>(g, sink, E3, pos, 0, (pos + 1) / 2, pm, pcode, (uint32_t)v, lane);
             __syncwarp();
@@ -1019,7 +1063,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
 // (phase 1: the unit loop, work estimates and queueing; phase 2: the queue),
 // and per kind of set (SET: several graphs, each seen through its offsets;
 // otherwise one graph read through the kernel's own arrays).
-template <int K, bool COUNT, int PHASE, bool SET>
+template <int K, bool COUNT, int PHASE, bool SET, bool HASH>
 __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? (SET ? ACC_MINB34S : ACC_MINB34C) : ACC_MINB34))
     k_enum(EnumArgs a) {
     using L = Layout<K>;
@@ -1102,11 +1146,11 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? (SET ?
                     const int gi = a.gs.graph_of(vg);
                     const GMeta mt = a.gs.meta(gi);
                     sink.switch_graph(gi, lane);
-                    process_unit<K, COUNT>(a, view_of(a, mt), sink, sc, (uint32_t)u, vg - mt.voff, vg, 0,
-                                           0x7FFFFFFF, true, D, wmax, lane);
+                    process_unit<K, COUNT, HASH>(a, view_of(a, mt), sink, sc, (uint32_t)u, vg - mt.voff, vg, 0,
+                                                 0x7FFFFFFF, true, D, wmax, lane);
                 } else {
-                    process_unit<K, COUNT>(a, view_single(a), sink, sc, (uint32_t)u, vg, vg, 0, 0x7FFFFFFF, true, D,
-                                           wmax, lane);
+                    process_unit<K, COUNT, HASH>(a, view_single(a), sink, sc, (uint32_t)u, vg, vg, 0, 0x7FFFFFFF,
+                                                 true, D, wmax, lane);
                 }
             }
         }
@@ -1123,11 +1167,11 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? (SET ?
                 const int gi = a.gs.graph_of(vg);
                 const GMeta mt = a.gs.meta(gi);
                 sink.switch_graph(gi, lane);
-                process_unit<K, COUNT>(a, view_of(a, mt), sink, sc, it.x, vg - mt.voff, vg, (int)it.y, (int)it.z,
-                                       false, D, wmax, lane);
+                process_unit<K, COUNT, HASH>(a, view_of(a, mt), sink, sc, it.x, vg - mt.voff, vg, (int)it.y,
+                                             (int)it.z, false, D, wmax, lane);
             } else {
-                process_unit<K, COUNT>(a, view_single(a), sink, sc, it.x, vg, vg, (int)it.y, (int)it.z, false, D,
-                                       wmax, lane);
+                process_unit<K, COUNT, HASH>(a, view_single(a), sink, sc, it.x, vg, vg, (int)it.y, (int)it.z, false,
+                                             D, wmax, lane);
             }
         }
     }
@@ -1157,15 +1201,15 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? (SET ?
     }
 }
 
-template <int K, bool COUNT, int PHASE, bool SET>
+template <int K, bool COUNT, int PHASE, bool SET, bool HASH>
 int blocks_per_sm() {
     static int cached = 0;
     if (cached) return cached;
-    if (cudaFuncSetAttribute(k_enum<K, COUNT, PHASE, SET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_enum<K, COUNT, PHASE, SET, HASH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Layout<K>::total) != cudaSuccess)
         return -1;
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_enum<K, COUNT, PHASE, SET>, kThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_enum<K, COUNT, PHASE, SET, HASH>, kThreads,
                                                       Layout<K>::total) != cudaSuccess ||
         b < 1)
         return -1;
@@ -1173,34 +1217,47 @@ int blocks_per_sm() {
     return b;
 }
 
-template <int K, bool COUNT, int PHASE, bool SET>
+template <int K, bool COUNT, int PHASE, bool SET, bool HASH>
 int launch_phase(const EnumArgs &a, int num_sms, cudaStream_t s, int grid_num, int grid_den) {
-    const int bps = blocks_per_sm<K, COUNT, PHASE, SET>();
+    const int bps = blocks_per_sm<K, COUNT, PHASE, SET, HASH>();
     if (bps < 1) return ACC_ERR_CUDA;
     int grid = (int)((long long)num_sms * bps * grid_num / grid_den);
     if (grid < num_sms) grid = num_sms;
     if (grid > num_sms * bps) grid = num_sms * bps;
-    k_enum<K, COUNT, PHASE, SET><<<grid, kThreads, Layout<K>::total, s>>>(a);
+    k_enum<K, COUNT, PHASE, SET, HASH><<<grid, kThreads, Layout<K>::total, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
 
+template <int K, bool COUNT, bool SET, bool HASH>
+int launch_ph(const EnumArgs &a, int num_sms, int phase, cudaStream_t s, int grid_num, int grid_den) {
+    return phase == 1 ? launch_phase<K, COUNT, 1, SET, HASH>(a, num_sms, s, grid_num, grid_den)
+                      : launch_phase<K, COUNT, 2, SET, HASH>(a, num_sms, s, grid_num, grid_den);
+}
+
+// Hashed adjacency is read by the count mode only (the enumerate mode probes
+// pairs of list members, for which the dense block is kept).
 template <int K, bool COUNT>
 int launch_k(const EnumArgs &a, int num_sms, int phase, cudaStream_t s, int grid_num, int grid_den) {
-    if (a.gs.B > 1)
-        return phase == 1 ? launch_phase<K, COUNT, 1, true>(a, num_sms, s, grid_num, grid_den)
-                          : launch_phase<K, COUNT, 2, true>(a, num_sms, s, grid_num, grid_den);
-    return phase == 1 ? launch_phase<K, COUNT, 1, false>(a, num_sms, s, grid_num, grid_den)
-                      : launch_phase<K, COUNT, 2, false>(a, num_sms, s, grid_num, grid_den);
+    const bool set = a.gs.B > 1;
+    if constexpr (COUNT) {
+        if (a.nh)
+            return set ? launch_ph<K, true, true, true>(a, num_sms, phase, s, grid_num, grid_den)
+                       : launch_ph<K, true, false, true>(a, num_sms, phase, s, grid_num, grid_den);
+    }
+    return set ? launch_ph<K, COUNT, true, false>(a, num_sms, phase, s, grid_num, grid_den)
+               : launch_ph<K, COUNT, false, false>(a, num_sms, phase, s, grid_num, grid_den);
 }
 
 // Most resident blocks per SM of any instantiation for k (sizes the per-warp
 // overflow lists).
 template <int K>
 int bps_max() {
-    const int b[8] = {blocks_per_sm<K, false, 1, false>(), blocks_per_sm<K, false, 2, false>(),
-                      blocks_per_sm<K, true, 1, false>(),  blocks_per_sm<K, true, 2, false>(),
-                      blocks_per_sm<K, false, 1, true>(),  blocks_per_sm<K, false, 2, true>(),
-                      blocks_per_sm<K, true, 1, true>(),   blocks_per_sm<K, true, 2, true>()};
+    const int b[12] = {blocks_per_sm<K, false, 1, false, false>(), blocks_per_sm<K, false, 2, false, false>(),
+                       blocks_per_sm<K, true, 1, false, false>(),  blocks_per_sm<K, true, 2, false, false>(),
+                       blocks_per_sm<K, false, 1, true, false>(),  blocks_per_sm<K, false, 2, true, false>(),
+                       blocks_per_sm<K, true, 1, true, false>(),   blocks_per_sm<K, true, 2, true, false>(),
+                       blocks_per_sm<K, true, 1, false, true>(),   blocks_per_sm<K, true, 2, false, true>(),
+                       blocks_per_sm<K, true, 1, true, true>(),    blocks_per_sm<K, true, 2, true, true>()};
     int m = 0;
     for (int x : b) {
         if (x < 1) return -1;

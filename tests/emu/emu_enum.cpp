@@ -3,7 +3,8 @@
 // relayout.inc) on the host over the G* build of a set of B graphs given as
 // input, the way the library launches them: phase 1 (light units whole,
 // heavy units queued), then phase 2 (the queue drained).  Input (int64
-// unless noted): k B mode light target blocks queue_cap, then n pitch nnz of
+// unless noted): k B mode (0 count, 1 enumerate, 2 count on hashed adjacency)
+// light target blocks queue_cap, then n pitch nnz of
 // each graph, then the set's arrays: state (the graphs' blocks one after
 // another), nptr[NV + 1] (positions over the whole set), deg[NV], lo[NV]
 // (int32), nbr (uint32, local ids) and the canonical code -> class table
@@ -31,13 +32,26 @@ template <class T> static bool rd(FILE *f, T *p, size_t n) { return fread(p, siz
 template <int K, bool COUNT>
 static void run(EnumArgs a, int blocks) {
     static_assert(acc::en::Layout<K>::total <= sizeof(emu_smem));
-    // the instantiation the library launches: one graph, or a set of several
+    // the instantiation the library launches: one graph or a set of several,
+    // dense or hashed adjacency (count mode)
+    if constexpr (COUNT) {
+        if (a.nh) {
+            if (a.gs.B > 1) {
+                run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 1, true, true>(a); });
+                run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 2, true, true>(a); });
+            } else {
+                run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 1, false, true>(a); });
+                run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 2, false, true>(a); });
+            }
+            return;
+        }
+    }
     if (a.gs.B > 1) {
-        run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 1, true>(a); });
-        run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 2, true>(a); });
+        run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 1, true, false>(a); });
+        run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 2, true, false>(a); });
     } else {
-        run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 1, false>(a); });
-        run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 2, false>(a); });
+        run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 1, false, false>(a); });
+        run_warps(blocks, 32, [&] { acc::en::k_enum<K, COUNT, 2, false, false>(a); });
     }
 }
 
@@ -108,8 +122,30 @@ int main(int argc, char **argv) {
         for (long long p = nptr[v]; p < nptr[v + 1]; p++)
             src[p] = (uint32_t)v | (p - nptr[v] < lo[v] ? 0x80000000u : 0u);
 
+    // mode 2: the count mode probing hashed adjacency tables, filled here the
+    // way the device build fills them (bucket of the neighbour's hash, or the
+    // next one with a free slot)
+    std::vector<uint32_t> nh;
+    if (mode == 2) {
+        nh.assign((size_t)acc::kNhWords * (size_t)nnz + 8, 0u);
+        for (long long v = 0; v < NV; v++) {
+            const uint32_t lg = acc::nh_lg(deg[v]), mask = (1u << lg) - 1u;
+            uint32_t *tab = nh.data() + (size_t)acc::kNhWords * (size_t)nptr[v];
+            for (long long p = nptr[v]; p < nptr[v + 1]; p++) {
+                uint32_t b = acc::nh_bucket(nbr[p] >> 2, lg);
+                for (bool done = false; !done; b = (b + 1u) & mask)
+                    for (int j = 0; j < 4 && !done; j++)
+                        if (tab[4 * b + j] == 0u) {
+                            tab[4 * b + j] = nbr[p];
+                            done = true;
+                        }
+            }
+        }
+    }
+
     EnumArgs a{};
     a.src = src.data();
+    a.nh = mode == 2 ? reinterpret_cast<const uint4 *>(nh.data()) : nullptr;
     a.state = st.data();
     a.deg = deg.data();
     a.lo = lo.data();
@@ -128,12 +164,12 @@ int main(int argc, char **argv) {
     a.queue_cap = (unsigned long long)h[6];
     a.scratch = scratch.data();
     a.scratch_per_warp = spw;
-    a.mode = (int)mode;
+    a.mode = mode == 2 ? 0 : (int)mode;
     a.light = h[3];
     a.target = h[4];
     a.counts = counts.data();
     a.status = &status;
-    const bool count = mode == 0;
+    const bool count = mode != 1;
     if (NV > 0) {
         if (k == 3) count ? run<3, true>(a, blocks) : run<3, false>(a, blocks);
         else if (k == 4) count ? run<4, true>(a, blocks) : run<4, false>(a, blocks);

@@ -105,6 +105,19 @@ def scenario_modes(lib):
                 # plain ESU walk (below 1024 vertices nothing is renumbered)
                 if mode == acc.ACC_MODE_COUNT and c.stats()[6] != esu_scanned_entries(n, s, d, k):
                     raise AssertionError(f"k {k} n {n}: {c.stats()[6]} entries scanned")
+    # the count mode probing the hashed adjacency tables (built on the device
+    # after the neighbour lists: one more kernel), then the dense block again
+    ok(lib.acc_ctx_set_mode(c.h, acc.ACC_MODE_COUNT), "acc_ctx_set_mode")
+    for adj in (acc.ACC_ADJ_HASH, acc.ACC_ADJ_DENSE, acc.ACC_ADJ_HASH):
+        ok(lib.acc_ctx_set_adjacency(c.h, adj), "acc_ctx_set_adjacency")
+        for k, gs in cases.items():
+            for n, s, d in gs:
+                rp, cl = csr(n, s, d)
+                rc, st, got = c.count(rp, cl, n, k)
+                if rc or st or got.tolist() != oracle.count(n, s, d, k).tolist():
+                    raise AssertionError(f"adjacency {adj} k {k} n {n}: rc {rc} status {st}")
+    if lib.acc_ctx_set_adjacency(c.h, 3) != acc.ACC_ERR_ARG:
+        raise AssertionError("an unknown adjacency choice is accepted")
     c.close()
 
 

@@ -285,6 +285,10 @@ inline int atomicMax(int *p, int v) {
     }
     return old;
 }
+inline unsigned atomicCAS(unsigned *p, unsigned c, unsigned v) {
+    std::atomic_ref<unsigned>(*p).compare_exchange_strong(c, v);
+    return c;
+}
 inline int atomicCAS(int *p, int c, int v) {
     std::atomic_ref<int>(*p).compare_exchange_strong(c, v);
     return c;

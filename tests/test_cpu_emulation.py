@@ -108,7 +108,7 @@ def emu_bins(tmp_path_factory):
         _function(graph, "__device__ __forceinline__ int warp_excl_scan") + "\n" +
         _function(graph, "__global__ void k_fill("))
     en = open(os.path.join(CSRC, "enum.cu")).read()
-    region = _region(en, "// Tuning knobs", "template <int K, bool COUNT, int PHASE, bool SET>\nint blocks_per_sm")
+    region = _region(en, "// Tuning knobs", "template <int K, bool COUNT, int PHASE, bool SET, bool HASH>\nint blocks_per_sm")
     # the kernels' dynamic shared memory becomes a static host buffer; the
     # histogram drain threshold becomes a compile-time parameter
     for old, new in (("extern __shared__ __align__(16) unsigned char smem[];", "unsigned char *smem = emu_smem;"),
@@ -375,7 +375,7 @@ SCHEDULES = {"light": (1 << 30, 1 << 30, 1 << 16), "heavy": (0, 1, 1 << 16), "qu
 
 
 @pytest.mark.parametrize("k", [3, 4, 5])
-@pytest.mark.parametrize("mode", [0, 1], ids=["count", "enumerate"])
+@pytest.mark.parametrize("mode", [0, 1, 2], ids=["count", "enumerate", "count_hashed"])
 @pytest.mark.parametrize("sched", list(SCHEDULES))
 def test_enumeration_kernels_equal_oracle(emu_bins, k, mode, sched):
     light, target, qcap = SCHEDULES[sched]
@@ -415,7 +415,7 @@ def _by_degree(n, s, d):
 
 
 @pytest.mark.parametrize("k", [3, 4, 5])
-@pytest.mark.parametrize("mode", [0, 1], ids=["count", "enumerate"])
+@pytest.mark.parametrize("mode", [0, 1, 2], ids=["count", "enumerate", "count_hashed"])
 def test_enumeration_overflow_lists_and_drain(emu_bins, k, mode):
     """Shared-memory lists of 16 entries (8 for k = 5) and a histogram drained
     every 256 increments: hub graphs send the extension lists to the per-warp
@@ -439,7 +439,7 @@ def test_enumeration_overflow_lists_and_drain(emu_bins, k, mode):
 
 
 @pytest.mark.parametrize("k", [3, 4, 5])
-@pytest.mark.parametrize("mode", [0, 1], ids=["count", "enumerate"])
+@pytest.mark.parametrize("mode", [0, 1, 2], ids=["count", "enumerate", "count_hashed"])
 def test_enumeration_kernels_on_graph_sets(emu_bins, k, mode):
     """Several graphs in one launch pair (the batched form): units of every
     graph interleave in the warps' grabs, each graph's counts stay apart."""
