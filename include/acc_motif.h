@@ -63,8 +63,11 @@ extern "C" {
 
 /* Largest vertex count the dense n x n pair-state matrix is built for
  * (n^2/4 bytes: 64 GiB at this limit, within one GB300's memory; the
- * per-warp overflow lists add 8(n + 64) bytes per resident warp). */
+ * per-warp overflow lists add 8(n + 64) bytes per resident warp).  Larger
+ * graphs, up to ACC_MAX_N_SPARSE vertices, are counted in ACC_MODE_COUNT
+ * only, built without the dense matrix (ACC_ADJ_SPARSE below). */
 #define ACC_MAX_N 524288
+#define ACC_MAX_N_SPARSE 67108864
 
 typedef struct acc_ctx acc_ctx;
 
@@ -108,7 +111,8 @@ ACC_API int acc_motif_prepare(acc_ctx *ctx, int k, void *stream);
  *            v -> u.  Any order within a row; repeated arcs count once
  *            (E is a set).  A self-loop or a target outside [0, n) is an
  *            input error.
- *  n, m      vertex and arc counts, 0 <= n <= ACC_MAX_N, 0 <= m < 2^31.
+ *  n, m      vertex and arc counts, 0 <= n <= ACC_MAX_N (ACC_MAX_N_SPARSE in
+ *            ACC_MODE_COUNT), 0 <= m < 2^31.
  *  k         3, 4 or 5.
  *  stream    cudaStream_t (void*), see above.
  *  d_counts  device int64[acc_motif_num_classes(k)], overwritten.
@@ -408,16 +412,25 @@ ACC_API int acc_ctx_set_mode(acc_ctx *ctx, int mode);
  *  ACC_ADJ_HASH: per-vertex open-addressing tables of the neighbour entries
  *   (32 bytes per entry of the G* neighbour lists, built on the device after
  *   the lists), one 16-byte load per probe in the common case.
- *  ACC_ADJ_AUTO (default): hashed when the largest graph of the count or
- *   batch has at least 32768 vertices for k = 5, 131072 for k = 3, 4 (where
- *   the dense probes, out of L2, get slower than the hashed ones); dense
- *   otherwise.
- * The dense block is built in every case (it also deduplicates the arcs).
- * All choices give identical counts.  Errors: ACC_ERR_ARG.
+ *  ACC_ADJ_SPARSE: the same hashed tables, and the neighbour lists built
+ *   without the dense block: every arc puts a raw entry in both endpoints'
+ *   rows, each row is sorted (one warp in shared memory up to 2048 raw
+ *   entries, one block in global memory above) and its repeated neighbours
+ *   merged.  Memory O(n + m); the call waits once for the build (the
+ *   per-warp overflow lists are sized by the largest degree it finds), so it
+ *   is never replayed from a launch graph.
+ *  ACC_ADJ_AUTO (default): sparse above ACC_MAX_N vertices; hashed when the
+ *   largest graph of the count or batch has at least 32768 vertices for
+ *   k = 5, 131072 for k = 3, 4 (where the dense probes, out of L2, get slower
+ *   than the hashed ones); dense otherwise.
+ * Except for ACC_ADJ_SPARSE the dense block is built in every case (it also
+ * deduplicates the arcs).  All choices give identical counts.  Errors:
+ * ACC_ERR_ARG.
  */
 #define ACC_ADJ_AUTO 0
 #define ACC_ADJ_DENSE 1
 #define ACC_ADJ_HASH 2
+#define ACC_ADJ_SPARSE 3
 ACC_API int acc_ctx_set_adjacency(acc_ctx *ctx, int adjacency);
 
 /*

@@ -77,8 +77,17 @@ def _load():
                                           ctypes.POINTER(ctypes.c_int32)]
     lib.oracle_swap_randomise.restype = ctypes.c_int64
     lib.oracle_zscores.restype = None
+    lib.oracle_set_dense_max.argtypes = [ctypes.c_int32]
+    lib.oracle_set_dense_max.restype = None
     _lib = lib
     return lib
+
+
+def set_dense_max(n: int) -> None:
+    """Graphs of at most n vertices keep the arc test in a dense bit matrix,
+    larger ones in sorted out-neighbour lists (default 65536; the counts are
+    the same either way)."""
+    _load().oracle_set_dense_max(n)
 
 
 def _p(a: np.ndarray, ct):

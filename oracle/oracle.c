@@ -157,10 +157,18 @@ int oracle_build_table(int k, int32_t *class_of_code, uint32_t *class_code, int 
 /* Graph: dense out-arc bit matrix plus sorted undirected neighbour lists */
 /* ------------------------------------------------------------------ */
 
+/* Graphs of at most this many vertices keep the arc test in a dense bit
+   matrix (n^2 / 8 bytes); larger ones in sorted out-neighbour lists. */
+static int32_t dense_max = 65536;
+
+void oracle_set_dense_max(int32_t n) { dense_max = n; }
+
 typedef struct {
     int32_t n;
     uint64_t words; /* 64-bit words per bit-matrix row */
-    uint64_t *out;  /* bit (a, b) set iff arc a -> b */
+    uint64_t *out;  /* bit (a, b) set iff arc a -> b; NULL above dense_max */
+    int64_t *optr;  /* out-neighbours of a: oadj[optr[a] .. optr[a+1]), sorted, no repeats */
+    int32_t *oadj;
     int64_t *nptr;  /* neighbour lists of G*, sorted ascending */
     int32_t *nbr;
     int64_t maxdeg;
@@ -168,7 +176,14 @@ typedef struct {
 
 static int arc(const ograph *g, int32_t a, int32_t b)
 {
-    return (int)((g->out[(uint64_t)a * g->words + ((uint32_t)b >> 6)] >> (b & 63)) & 1u);
+    if (g->out) return (int)((g->out[(uint64_t)a * g->words + ((uint32_t)b >> 6)] >> (b & 63)) & 1u);
+    int64_t lo = g->optr[a], hi = g->optr[a + 1] - 1;  /* binary search for b */
+    while (lo <= hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (g->oadj[mid] == b) return 1;
+        if (g->oadj[mid] < b) lo = mid + 1; else hi = mid - 1;
+    }
+    return 0;
 }
 
 static int adjacent(const ograph *g, int32_t a, int32_t b) { return arc(g, a, b) || arc(g, b, a); }
@@ -185,14 +200,35 @@ static int ograph_build(ograph *g, int32_t n, int64_t m, const int32_t *src, con
     memset(g, 0, sizeof(*g));
     g->n = n;
     g->words = ((uint64_t)n + 63) / 64;
-    g->out = (uint64_t *)calloc((size_t)(g->words * (uint64_t)(n > 0 ? n : 1)), sizeof(uint64_t));
+    if (n <= dense_max) {
+        g->out = (uint64_t *)calloc((size_t)(g->words * (uint64_t)(n > 0 ? n : 1)), sizeof(uint64_t));
+        if (!g->out) return -1;
+    }
     g->nptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
-    if (!g->out || !g->nptr) return -1;
+    g->optr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!g->nptr || !g->optr) return -1;
     for (int64_t e = 0; e < m; e++) {
         int32_t a = src[e], b = dst[e];
         if (a < 0 || a >= n || b < 0 || b >= n || a == b) return -2;
-        g->out[(uint64_t)a * g->words + ((uint32_t)b >> 6)] |= 1ull << (b & 63);
+        if (g->out) g->out[(uint64_t)a * g->words + ((uint32_t)b >> 6)] |= 1ull << (b & 63);
+        g->optr[a + 1]++;
     }
+    /* out-neighbour lists: sorted, repeats dropped */
+    for (int32_t a = 0; a < n; a++) g->optr[a + 1] += g->optr[a];
+    g->oadj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    int64_t *ofill = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!g->oadj || !ofill) { free(ofill); return -1; }
+    for (int64_t e = 0; e < m; e++) g->oadj[g->optr[src[e]] + ofill[src[e]]++] = dst[e];
+    free(ofill);
+    int64_t ow = 0;
+    for (int32_t a = 0; a < n; a++) {
+        const int64_t lo = g->optr[a], hi = g->optr[a + 1];
+        qsort(g->oadj + lo, (size_t)(hi - lo), sizeof(int32_t), cmp_i32);
+        g->optr[a] = ow;
+        for (int64_t t = lo; t < hi; t++)
+            if (t == lo || g->oadj[t] != g->oadj[t - 1]) g->oadj[ow++] = g->oadj[t];
+    }
+    g->optr[n] = ow;
     /* neighbour lists of G*: b is listed under a (and a under b) for every
        arc a -> b; each list is then sorted and repeats are dropped */
     int64_t *fill = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
@@ -230,6 +266,8 @@ static void ograph_free(ograph *g)
     free(g->out);
     free(g->nptr);
     free(g->nbr);
+    free(g->optr);
+    free(g->oadj);
 }
 
 /* Adjacency code of the ordered tuple w[0..k-1] in g. */

@@ -27,6 +27,7 @@ ACC_ERR_ARG = -7
 ACC_ERR_TOO_LARGE = -8
 ACC_ERR_INTERNAL = -9
 ACC_MAX_N = 524288
+ACC_MAX_N_SPARSE = 67108864
 ACC_STATS_LEN = 7
 
 NUM_CLASSES = {3: 13, 4: 199, 5: 9364}
@@ -45,7 +46,7 @@ EXPORTS = (
 ACC_REQ_QUEUED, ACC_REQ_RUNNING, ACC_REQ_DONE = 0, 1, 2
 ACC_SERVE_FIFO, ACC_SERVE_SHORTEST = 0, 1
 ACC_MODE_COUNT, ACC_MODE_ENUMERATE, ACC_MODE_FORMULA = 0, 1, 2
-ACC_ADJ_AUTO, ACC_ADJ_DENSE, ACC_ADJ_HASH = 0, 1, 2
+ACC_ADJ_AUTO, ACC_ADJ_DENSE, ACC_ADJ_HASH, ACC_ADJ_SPARSE = 0, 1, 2, 3
 ACC_RAND_SWAP, ACC_RAND_MUTUAL = 0, 1
 
 
@@ -537,7 +538,7 @@ class Counter:
         self.mode = mode
 
     def set_adjacency(self, adjacency: int):
-        """ACC_ADJ_AUTO (default), ACC_ADJ_DENSE or ACC_ADJ_HASH; same counts."""
+        """ACC_ADJ_AUTO (default), ACC_ADJ_DENSE, ACC_ADJ_HASH or ACC_ADJ_SPARSE; same counts."""
         _check(acc_ctx_set_adjacency(self.ctx, adjacency), "acc_ctx_set_adjacency")
 
     def set_schedule(self, light: int = 0, target: int = 0):

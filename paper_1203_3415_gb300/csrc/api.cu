@@ -158,18 +158,45 @@ void release_luts(acc_ctx *c) {
 
 long long scratch_per_warp(int max_n) { return 2 * (((long long)max_n + 32 + 31) & ~31LL); }
 
+// The count mode builds the lists without the dense block (and probes
+// hashed tables) above the dense block's limit, or when asked to.
+bool sparse_build(const acc_ctx *c, int max_n) {
+    return c->mode == ACC_MODE_COUNT && (c->adjacency == ACC_ADJ_SPARSE || max_n > ACC_MAX_N);
+}
+
 bool uses_hash(const acc_ctx *c, int k, int max_n) {
     return c->mode == ACC_MODE_COUNT &&
-           (c->adjacency == ACC_ADJ_HASH || (c->adjacency == ACC_ADJ_AUTO && hash_auto(k, max_n)));
+           (c->adjacency == ACC_ADJ_HASH || c->adjacency == ACC_ADJ_SPARSE || max_n > ACC_MAX_N ||
+            (c->adjacency == ACC_ADJ_AUTO && hash_auto(k, max_n)));
 }
+
+// Size limit of one graph: the dense block's, or the sparse build's for the
+// count mode (local ids fill 26 bits of the extension-list entries).
+int size_check(const acc_ctx *c, long long n) {
+    if (n > ACC_MAX_N_SPARSE) return ACC_ERR_TOO_LARGE;
+    if (n > ACC_MAX_N && c->mode != ACC_MODE_COUNT) return ACC_ERR_TOO_LARGE;
+    return ACC_OK;
+}
+
+// Entries of one per-warp overflow list for the sparse build: an extension
+// list holds at most 3 maxdeg vertices (k = 5: the level-2 list after w2
+// and the neighbours of w2; k = 4: two neighbour lists; k = 3: one).
+long long sparse_list_entries(int maxdeg) { return (3LL * maxdeg + 64 + 31) & ~31LL; }
 
 // Workspace for a set of NV vertices in blocks of state_words words, with at
 // most `arcs` arcs and graphs of at most max_n vertices.
 int ensure_workspace(acc_ctx *c, long long NV, long long state_words, long long arcs, int max_n, int k) {
     int rc;
+    const bool sparse = sparse_build(c, max_n);
     if (uses_hash(c, k, max_n) && (rc = grow(&c->nh, &c->nh_cap, (size_t)kNhWords * (size_t)(2 * arcs) + 4)))
         return rc;
-    {
+    if (sparse) {
+        if ((rc = grow(&c->sp_raw, &c->sp_raw_cap, (size_t)(2 * arcs) + 1))) return rc;
+        if ((rc = grow(&c->sp_merged, &c->sp_merged_cap, (size_t)(2 * arcs) + 1))) return rc;
+        if ((rc = grow(&c->sp_roff, &c->sp_roff_cap, (size_t)NV + 1))) return rc;
+        if ((rc = grow(&c->sp_big, &c->sp_big_cap, (size_t)sparse_big_rows_cap(arcs)))) return rc;
+    }
+    if (!sparse) {
         // a reallocation (the capacity changes; the address may not) brings
         // memory that is not zero: the next build sweeps it
         const size_t cap_before = c->state_cap;
@@ -201,7 +228,7 @@ int ensure_workspace(acc_ctx *c, long long NV, long long state_words, long long 
     if ((rc = grow(&c->f5_pre, &c->f5_pre_cap, (size_t)NV + 1))) return rc;
     if ((rc = grow(&c->nbr, &c->nbr_cap, (size_t)(2 * arcs) + 1))) return rc;
     if ((rc = grow(&c->src, &c->src_cap, (size_t)(2 * arcs) + 1))) return rc;
-    if ((rc = grow(&c->occ, &c->occ_cap, (size_t)NV * (size_t)occ_words(max_n) + 1))) return rc;
+    if (!sparse && (rc = grow(&c->occ, &c->occ_cap, (size_t)NV * (size_t)occ_words(max_n) + 1))) return rc;
     if (!c->info) {
         if (!ok(cudaMalloc(&c->info, sizeof(GraphInfo)))) return ACC_ERR_NOMEM;
         if (!ok(cudaMemset(c->info, 0, sizeof(GraphInfo)))) return ACC_ERR_CUDA;
@@ -215,7 +242,11 @@ int ensure_workspace(acc_ctx *c, long long NV, long long state_words, long long 
     }
     const int warps = enum_grid_warps(k, c->num_sms);
     if (warps < 0) return warps;
-    if ((rc = grow(&c->scratch, &c->scratch_cap, (size_t)scratch_per_warp(max_n) * (size_t)warps))) return rc;
+    // the sparse build sizes the overflow lists by the largest degree, once
+    // it is known (run_set)
+    if (!sparse && (rc = grow(&c->scratch, &c->scratch_cap, (size_t)scratch_per_warp(max_n) * (size_t)warps)))
+        return rc;
+    if (!c->maxdeg_host && !ok(cudaMallocHost(&c->maxdeg_host, sizeof(int)))) return ACC_ERR_NOMEM;
     return ACC_OK;
 }
 
@@ -226,7 +257,8 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     c->timed_call = c->timing;
     if (c->timing && !ok(cudaEventRecord(c->ev[0], s))) return ACC_ERR_CUDA;
     const bool clean = c->state_clean;
-    c->state_clean = false;  // until the closing clear below is enqueued
+    const bool sparse = sparse_build(c, max_n);
+    if (!sparse) c->state_clean = false;  // until the closing clear below is enqueued
     // a buffer not known to be clean is swept whole (capacity, not just this
     // set's blocks): a later, larger set may use any part of it
     BuildBufs bb;
@@ -245,10 +277,28 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     bb.occ_w = occ_words(max_n);
     bb.info = c->info;
     bb.k = k;
-    int rc = launch_build_graph(gs, bb, max_n, status, reinterpret_cast<unsigned long long *>(counts),
+    int rc;
+    if (sparse) {
+        const SparseBufs sb = {c->sp_raw, c->sp_merged, c->sp_roff, c->sp_big};
+        rc = launch_build_graph_sparse(gs, bb, sb, max_n, status, reinterpret_cast<unsigned long long *>(counts),
+                                       (long long)gs.B * num_classes(k), relabel, c->num_sms, s);
+    } else {
+        rc = launch_build_graph(gs, bb, max_n, status, reinterpret_cast<unsigned long long *>(counts),
                                 (long long)gs.B * num_classes(k), relabel, c->num_sms, s);
+    }
     if (rc < 0) return rc;
     launches += rc;
+    long long spw = scratch_per_warp(max_n);
+    if (sparse) {
+        // overflow lists sized by the largest degree: wait for the build
+        if (!ok(cudaMemcpyAsync(c->maxdeg_host, &c->info->maxdeg, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+            !ok(cudaStreamSynchronize(s)))
+            return ACC_ERR_CUDA;
+        spw = 2 * sparse_list_entries(*c->maxdeg_host);
+        const int warps = enum_grid_warps(k, c->num_sms);
+        if (warps < 0) return warps;
+        if ((rc = grow(&c->scratch, &c->scratch_cap, (size_t)spw * (size_t)warps))) return rc;
+    }
     // count mode on a large set: probes read hashed tables, built from the
     // sorted neighbour lists
     const bool hash = gs.NV > 0 && uses_hash(c, k, max_n);
@@ -273,7 +323,7 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     a.queue = c->queue;
     a.queue_cap = c->queue_cap;
     a.scratch = c->scratch;
-    a.scratch_per_warp = scratch_per_warp(max_n);
+    a.scratch_per_warp = spw;
     a.mode = c->mode == ACC_MODE_ENUMERATE ? 1 : 0;
     a.light = c->sched_light > 0 ? c->sched_light : enum_default_light();
     a.target = c->sched_target > 0 ? c->sched_target : enum_default_target();
@@ -305,10 +355,12 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
         launches += rc;
     }
     if (c->timing && !ok(cudaEventRecord(c->ev[2], s))) return ACC_ERR_CUDA;
-    rc = launch_clear_graph(gs, c->state, c->occ, occ_words(max_n), c->num_sms, s);
-    if (rc < 0) return rc;
-    launches += rc;
-    c->state_clean = true;
+    if (!sparse) {
+        rc = launch_clear_graph(gs, c->state, c->occ, occ_words(max_n), c->num_sms, s);
+        if (rc < 0) return rc;
+        launches += rc;
+        c->state_clean = true;
+    }
     c->last_launches = launches;
     c->last_k = k;
     c->last_units = gs.NV;
@@ -330,12 +382,12 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
     if (!c || !rowptr || !counts || (m > 0 && !col)) return ACC_ERR_ARG;
     if (!valid_k(k)) return ACC_ERR_K;
     if (n < 0 || m < 0 || m >= (1ll << 31)) return ACC_ERR_INPUT;
-    if (n > ACC_MAX_N) return ACC_ERR_TOO_LARGE;
+    if (size_check(c, n)) return ACC_ERR_TOO_LARGE;
     if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
     int rc = ensure_lut(c, k, s);
     if (rc) return rc;
     const long long pitch = state_pitch(n);
-    if ((rc = ensure_workspace(c, n, (long long)n * pitch, m, n, k))) return rc;
+    if ((rc = ensure_workspace(c, n, sparse_build(c, n) ? 0 : (long long)n * pitch, m, n, k))) return rc;
     GSet gs = {};
     gs.one.rowptr = reinterpret_cast<const long long *>(rowptr);
     gs.one.col = col;
@@ -350,7 +402,7 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
     gs.M = m;
     int *status = status_user ? status_user : c->status_dev;
     const bool relabel = n >= kRelabelMinN;
-    if (c->graphs && !c->timing && c->state_clean && n > 0) {
+    if (c->graphs && !c->timing && c->state_clean && n > 0 && !sparse_build(c, n)) {
         // repeat counts replay one CUDA graph of the whole launch sequence;
         // it is captured (on the context's stream, not run) at the second
         // count with the same key, and only while the pair-state buffer is
@@ -426,9 +478,15 @@ long long ctx_footprint(const acc_ctx *c, long long n, long long m, int k) {
     const long long pitch = state_pitch((int)n);
     const long long warps = enum_grid_warps(k, c->num_sms);
     const long long hash_bytes = uses_hash(c, k, (int)n) ? 4LL * kNhWords * (2 * m + 1) : 0;
-    const long long bytes = n * pitch * 4 + 5 * 4 * (n + 1) + 8 * (n + 1) + 8 * (2 * m + 1) + hash_bytes +
-                            4 * n * occ_words((int)n) +
-                            (long long)kQueueCap * 16 + scratch_per_warp((int)n) * (warps > 0 ? warps : 0) * 4;
+    const bool sparse = sparse_build(c, (int)n);
+    // the sparse build keeps raw and merged rows (2 m words each) and row
+    // offsets instead of the dense block and its bitmap; its overflow lists
+    // are bounded by the largest degree, itself at most 2m and n
+    const long long list_n = sparse ? (2 * m < n ? 2 * m : n) : n;
+    const long long bytes = (sparse ? 16 * (m + 1) + 8 * (n + 1) : n * pitch * 4 + 4 * n * occ_words((int)n)) +
+                            5 * 4 * (n + 1) + 8 * (n + 1) + 8 * (2 * m + 1) + hash_bytes + (long long)kQueueCap * 16 +
+                            (sparse ? 2 * sparse_list_entries((int)list_n) : scratch_per_warp((int)n)) *
+                                (warps > 0 ? warps : 0) * 4;
     return bytes + bytes / 4;
 }
 
@@ -455,7 +513,7 @@ const char *acc_strerror(int code) {
     case ACC_ERR_OVERFLOW: return "a count or an index would not fit its type";
     case ACC_ERR_CUDA: return "a CUDA runtime call failed";
     case ACC_ERR_ARG: return "null pointer, bad handle or bad option";
-    case ACC_ERR_TOO_LARGE: return "n above ACC_MAX_N";
+    case ACC_ERR_TOO_LARGE: return "n above ACC_MAX_N (ACC_MAX_N_SPARSE in the count mode)";
     case ACC_ERR_INTERNAL: return "internal consistency check failed";
     default: return "unknown error";
     }
@@ -498,6 +556,11 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaFree(c->nbr);
     cudaFree(c->src);
     cudaFree(c->nh);
+    cudaFree(c->sp_raw);
+    cudaFree(c->sp_merged);
+    cudaFree(c->sp_roff);
+    cudaFree(c->sp_big);
+    if (c->maxdeg_host) cudaFreeHost(c->maxdeg_host);
     cudaFree(c->info);
     cudaFree(c->queue);
     cudaFree(c->scratch);
@@ -541,7 +604,7 @@ int acc_motif_count_host(acc_ctx *c, const int64_t *h_rowptr, const int32_t *h_c
     if (!c || !h_rowptr || !h_counts || (m > 0 && !h_col)) return ACC_ERR_ARG;
     if (!valid_k(k)) return ACC_ERR_K;
     if (n < 0 || m < 0 || m >= (1ll << 31)) return ACC_ERR_INPUT;
-    if (n > ACC_MAX_N) return ACC_ERR_TOO_LARGE;
+    if (size_check(c, n)) return ACC_ERR_TOO_LARGE;
     if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
     int rc;
     size_t cnt_cap = c->h2d_counts ? 9364 : 0;
@@ -577,7 +640,7 @@ int acc_motif_batch_prepare(acc_ctx *c, const acc_graph_desc *graphs, int32_t B,
         const acc_graph_desc &d = graphs[g];
         if (!d.rowptr || (d.m > 0 && !d.col)) return ACC_ERR_ARG;
         if (d.n < 0 || d.m < 0 || d.m >= (1ll << 31)) return ACC_ERR_INPUT;
-        if (d.n > ACC_MAX_N) return ACC_ERR_TOO_LARGE;
+        if (size_check(c, d.n)) return ACC_ERR_TOO_LARGE;
         GMeta &mt = metas[(size_t)g];
         mt.rowptr = reinterpret_cast<const long long *>(d.rowptr);
         mt.col = d.col;
@@ -599,7 +662,7 @@ int acc_motif_batch_prepare(acc_ctx *c, const acc_graph_desc *graphs, int32_t B,
     if (!ok(cudaStreamSynchronize(s))) return ACC_ERR_CUDA;
     int rc = ensure_lut(c, k, s);
     if (rc) return rc;
-    if ((rc = ensure_workspace(c, NV, words, arcs, max_n, k))) return rc;
+    if ((rc = ensure_workspace(c, NV, sparse_build(c, max_n) ? 0 : words, arcs, max_n, k))) return rc;
     if ((rc = grow(&c->meta_dev, &c->meta_cap, (size_t)B + 1))) return rc;
     if ((rc = grow(&c->gid, &c->gid_cap, (size_t)NV + 1))) return rc;
     if (B > 0 && !ok(cudaMemcpy(c->meta_dev, metas.data(), sizeof(GMeta) * (size_t)B, cudaMemcpyHostToDevice)))
@@ -798,7 +861,8 @@ int acc_motif_last_stats(acc_ctx *c, int64_t *h_stats) {
 }
 
 int acc_ctx_set_adjacency(acc_ctx *c, int adjacency) {
-    if (!c || (adjacency != ACC_ADJ_AUTO && adjacency != ACC_ADJ_DENSE && adjacency != ACC_ADJ_HASH))
+    if (!c || (adjacency != ACC_ADJ_AUTO && adjacency != ACC_ADJ_DENSE && adjacency != ACC_ADJ_HASH &&
+               adjacency != ACC_ADJ_SPARSE))
         return ACC_ERR_ARG;
     c->adjacency = adjacency;
     return ACC_OK;

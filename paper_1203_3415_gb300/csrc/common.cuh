@@ -46,6 +46,8 @@ struct GraphInfo {
     unsigned long long unit_ctr;    // base units taken by phase 1
     unsigned long long chunks_pushed;
     unsigned long long scanned;     // count mode: neighbour entries the last two levels scanned
+    unsigned big_rows;              // sparse build: rows listed for the block sort
+    unsigned big_head;              // sparse build: listed rows taken
     float bound[3];                 // degree sums of the count bound (count_bound_terms)
 };
 
@@ -199,6 +201,20 @@ struct BuildBufs {
 };
 int launch_build_graph(const GSet &gs, const BuildBufs &b, int max_n, int *status, unsigned long long *counts,
                        long long ncounts, bool relabel, int num_sms, cudaStream_t s);
+// The sparse build: the same lists, degrees, renumbering, status and count
+// bound from sorted rows of raw entries, without the dense block (b.state,
+// b.occ unused).  Buffers: raw and merged 2 M words each, roff NV + 1, big
+// sparse_big_rows_cap(M) ints.
+struct SparseBufs {
+    uint32_t *raw;
+    uint32_t *merged;
+    long long *roff;
+    int *big;
+};
+int sparse_big_rows_cap(long long arcs);
+int launch_build_graph_sparse(const GSet &gs, const BuildBufs &b, const SparseBufs &sb, int max_n, int *status,
+                              unsigned long long *counts, long long ncounts, bool relabel, int num_sms,
+                              cudaStream_t s);
 // Hashed adjacency of a built set: nh (kNhWords * max_entries words) is
 // cleared and every neighbour entry inserted; max_entries bounds the set's
 // 2 |E*| (the exact count is read on the device).

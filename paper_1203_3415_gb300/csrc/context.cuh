@@ -42,6 +42,14 @@ struct acc_ctx {
     uint32_t *nh = nullptr;   // hashed adjacency tables
     size_t nh_cap = 0;
     int adjacency = ACC_ADJ_AUTO;
+    // sparse build: raw and merged rows, row offsets, rows for the block sort
+    uint32_t *sp_raw = nullptr, *sp_merged = nullptr;
+    size_t sp_raw_cap = 0, sp_merged_cap = 0;
+    long long *sp_roff = nullptr;
+    size_t sp_roff_cap = 0;
+    int *sp_big = nullptr;
+    size_t sp_big_cap = 0;
+    int *maxdeg_host = nullptr;  // pinned
     uint32_t *occ = nullptr;  // pair-state row occupancy bitmaps
     size_t occ_cap = 0;
     size_t nbr_cap = 0;

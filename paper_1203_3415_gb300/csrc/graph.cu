@@ -124,8 +124,9 @@ __global__ void k_arc_degrees(GSet gs, int *deg_io) {
 // neighbours of block vertex a; lo (if non-null) those below a.  The atomic
 // that finds a state word empty marks the word's 32-word chunk in its row's
 // occupancy bitmap.
-__global__ void k_ingest(GSet gs, uint32_t *state, const int *__restrict__ label, int *status, int *deg, int *lo,
-                         uint32_t *occ, int occ_w) {
+// Row checks of the input CSRs (grid-stride): rowptr non-decreasing within
+// [0, m], rowptr[0] = 0, rowptr[n] = m; no arcs in a graph without vertices.
+__device__ __forceinline__ void validate_rows(const GSet &gs, int *status) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < gs.NV; v += stride) {
         const GMeta mt = gs.meta(gs.graph_of((int)v));
@@ -138,6 +139,11 @@ __global__ void k_ingest(GSet gs, uint32_t *state, const int *__restrict__ label
         const GMeta mt = gs.meta((int)g);  // arcs of a graph without vertices
         if (mt.n == 0 && mt.m != 0) set_status(status, ACC_ERR_INPUT);
     }
+}
+
+__global__ void k_ingest(GSet gs, uint32_t *state, const int *__restrict__ label, int *status, int *deg, int *lo,
+                         uint32_t *occ, int occ_w) {
+    validate_rows(gs, status);
     for_each_arc(gs, [&](int v, const GMeta &mt, int lv, long long p) {
         const int u0 = mt.col[p];
         if (u0 < 0 || u0 >= mt.n || u0 == lv) {
@@ -340,6 +346,8 @@ __global__ void __launch_bounds__(1024) k_scan_degrees(const int *__restrict__ d
             if (count_bound(k, max_n, warp_max[0], tb) > kCountLimit) set_status(status, ACC_ERR_OVERFLOW);
         }
         info->maxdeg = warp_max[0];
+        info->big_rows = 0;
+        info->big_head = 0;
         info->queue_tail = 0;
         info->queue_head = 0;
         info->unit_ctr = 0;
@@ -440,6 +448,8 @@ __global__ void __launch_bounds__(1024) k_scan_top(long long *tile_sum, int ntil
     }
     if (t == 0) {
         if (k && count_bound(k, max_n, info->maxdeg, info->bound) > kCountLimit) set_status(status, ACC_ERR_OVERFLOW);
+        info->big_rows = 0;
+        info->big_head = 0;
         info->queue_tail = 0;
         info->queue_head = 0;
         info->unit_ctr = 0;
@@ -591,6 +601,190 @@ __global__ void k_fill(GSet gs, const uint32_t *__restrict__ state, const uint32
             const int in_round = __shfl_sync(kFull, ex + cnt, last) - __shfl_sync(kFull, ex, last_first);
             carry = (last_owner == carry_row ? carry : 0) + in_round;
             carry_row = last_owner;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sparse build: the same G* neighbour lists without the dense pair-state
+// block (for graphs above its size limit, or on request).  Each arc puts one
+// raw entry (u << 2) | state bit into each endpoint's row (bit 0 at the
+// tail's row: arc a -> u; bit 1 at the head's row); each row is then sorted
+// and the entries of one neighbour merged (their state bits OR'd, so repeated
+// arcs count once and a mutual pair becomes state 3), and the merged rows are
+// compacted into the lists.
+// ---------------------------------------------------------------------------
+
+constexpr int kSortSmall = 2048;  // raw entries of a row one warp sorts in shared memory
+constexpr int kSortWarps = 4;     // warps per block of the small-row sort
+
+// Raw entries per row (cnt[v], both directions of each arc), after the row
+// checks of the input; arcs with a bad target or self-loops are reported
+// and not counted.
+__global__ void k_sp_count(GSet gs, const int *__restrict__ label, int *status, int *cnt) {
+    validate_rows(gs, status);
+    for_each_arc(gs, [&](int v, const GMeta &mt, int lv, long long p) {
+        const int u0 = mt.col[p];
+        if (u0 < 0 || u0 >= mt.n || u0 == lv) {
+            set_status(status, ACC_ERR_INPUT);
+            return;
+        }
+        const int a = label ? label[v] - mt.voff : lv;
+        const int u = label ? label[mt.voff + u0] - mt.voff : u0;
+        atomicAdd(&cnt[mt.voff + a], 1);
+        atomicAdd(&cnt[mt.voff + u], 1);
+    });
+}
+
+// The raw entries into their rows (row v from roff[v]; cur[v] counts the
+// entries placed, in any order).
+__global__ void k_sp_scatter(GSet gs, const int *__restrict__ label, const long long *__restrict__ roff, int *cur,
+                             uint32_t *raw) {
+    for_each_arc(gs, [&](int v, const GMeta &mt, int lv, long long p) {
+        const int u0 = mt.col[p];
+        if (u0 < 0 || u0 >= mt.n || u0 == lv) return;
+        const int a = label ? label[v] - mt.voff : lv;
+        const int u = label ? label[mt.voff + u0] - mt.voff : u0;
+        raw[roff[mt.voff + a] + atomicAdd(&cur[mt.voff + a], 1)] = ((uint32_t)u << 2) | 1u;
+        raw[roff[mt.voff + u] + atomicAdd(&cur[mt.voff + u], 1)] = ((uint32_t)a << 2) | 2u;
+    });
+}
+
+// Ascending sort of x[0..n) by compare-exchanges that always put the smaller
+// value at the lower index (the bitonic network in its flipped form: each
+// merge of size k first compares i with its mirror i ^ (k - 1), then i with
+// i ^ j); the comparators reaching past n meet virtual maxima that never
+// move, so any n works without padding.  Thread t of nt runs indexes t, t +
+// nt, ...; sync() separates the stages.
+template <typename Sync>
+__device__ __forceinline__ void flip_sort(uint32_t *x, int n, int t, int nt, Sync sync) {
+    for (int k = 2; (k >> 1) < n; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = t; i < n; i += nt) {
+                const int l = j == (k >> 1) ? (i ^ (k - 1)) : (i ^ j);
+                if (l > i && l < n) {
+                    const uint32_t a = x[i], b = x[l];
+                    if (a > b) {
+                        x[i] = b;
+                        x[l] = a;
+                    }
+                }
+            }
+            sync();
+        }
+    }
+}
+
+// Warp per row of at most kSortSmall raw entries (longer rows are listed in
+// big[] for k_sp_sort_big): sort in the warp's shared buffer, then OR every
+// entry into merged[roff[v] + (its neighbour's rank in the row)] (merged is
+// zero beforehand); deg[v], lo[v] = neighbours of v, those below v.
+__global__ void __launch_bounds__(kSortWarps * kWarp) k_sp_sort_small(GSet gs, const long long *__restrict__ roff,
+                                                                   const uint32_t *__restrict__ raw,
+                                                                   uint32_t *merged, int *deg, int *lo, int *big,
+                                                                   GraphInfo *info) {
+    __shared__ uint32_t buf[kSortWarps][kSortSmall];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *x = buf[wib];
+    const long long nw = (long long)gridDim.x * kSortWarps;
+    for (long long v = blockIdx.x * (long long)kSortWarps + wib; v < gs.NV; v += nw) {
+        const long long r0 = roff[v];
+        const int R = (int)(roff[v + 1] - r0);
+        if (R > kSortSmall) {
+            if (lane == 0) big[atomicAdd(&info->big_rows, 1u)] = (int)v;
+            continue;
+        }
+        for (int i = lane; i < R; i += kWarp) x[i] = raw[r0 + i];
+        __syncwarp();
+        flip_sort(x, R, lane, kWarp, [] { __syncwarp(); });
+        const uint32_t vloc = (uint32_t)((int)v - gs.meta(gs.graph_of((int)v)).voff);
+        int runs = 0, below = 0;
+        for (int c0 = 0; c0 < R; c0 += kWarp) {
+            const int i = c0 + lane;
+            const uint32_t e = i < R ? x[i] : 0u;
+            const bool start = i < R && (i == 0 || (x[i - 1] >> 2) != (e >> 2));
+            const unsigned ball = __ballot_sync(kFull, start);
+            if (i < R) atomicOr(&merged[r0 + runs + __popc(ball & (0xFFFFFFFFu >> (31 - lane))) - 1], e);
+            below += __popc(__ballot_sync(kFull, start && (e >> 2) < vloc));
+            runs += __popc(ball);
+        }
+        if (lane == 0) {
+            deg[v] = runs;
+            lo[v] = below;
+        }
+        __syncwarp();
+    }
+}
+
+// Block per listed long row (taken one at a time through info->big_head):
+// the same sort in place in raw (global memory), then the same merge.
+__global__ void k_sp_sort_big(GSet gs, const long long *__restrict__ roff, uint32_t *raw, uint32_t *merged, int *deg,
+                              int *lo, const int *__restrict__ big, GraphInfo *info) {
+    __shared__ int row, warp_cnt[32], warp_below[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nwarps = blockDim.x >> 5;
+    for (;;) {
+        if (t == 0) {
+            const unsigned i = atomicAdd(&info->big_head, 1u);
+            row = i < info->big_rows ? big[i] : -1;
+        }
+        __syncthreads();
+        const int v = row;
+        if (v < 0) return;
+        const long long r0 = roff[v];
+        const int R = (int)(roff[v + 1] - r0);
+        uint32_t *x = raw + r0;
+        flip_sort(x, R, t, (int)blockDim.x, [] {
+            __threadfence_block();
+            __syncthreads();
+        });
+        const uint32_t vloc = (uint32_t)(v - gs.meta(gs.graph_of(v)).voff);
+        int runs = 0, below = 0;
+        for (int c0 = 0; c0 < R; c0 += (int)blockDim.x) {
+            const int i = c0 + t;
+            const uint32_t e = i < R ? x[i] : 0u;
+            const bool start = i < R && (i == 0 || (x[i - 1] >> 2) != (e >> 2));
+            const unsigned ball = __ballot_sync(kFull, start);
+            const unsigned bbelow = __ballot_sync(kFull, start && (e >> 2) < vloc);
+            if (lane == 0) {
+                warp_cnt[wid] = __popc(ball);
+                warp_below[wid] = __popc(bbelow);
+            }
+            __syncthreads();
+            int before = 0, total = 0, tb = 0;
+            for (int w = 0; w < nwarps; w++) {
+                if (w < wid) before += warp_cnt[w];
+                total += warp_cnt[w];
+                tb += warp_below[w];
+            }
+            if (i < R) atomicOr(&merged[r0 + runs + before + __popc(ball & (0xFFFFFFFFu >> (31 - lane))) - 1], e);
+            runs += total;
+            below += tb;
+            __syncthreads();
+        }
+        if (t == 0) {
+            deg[v] = runs;
+            lo[v] = below;
+        }
+        __syncthreads();
+    }
+}
+
+// Warp per row: the merged row into the neighbour lists at nptr (the scan of
+// the final degrees), and each entry's row into src (bit 31: a neighbour
+// below the row's vertex).
+__global__ void k_sp_compact(GSet gs, const long long *__restrict__ roff, const uint32_t *__restrict__ merged,
+                             const int *__restrict__ deg, const long long *__restrict__ nptr, uint32_t *nbr,
+                             uint32_t *src) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; v < gs.NV; v += nw) {
+        const long long r0 = roff[v], b = nptr[v];
+        const int d = deg[v];
+        const uint32_t vloc = (uint32_t)((int)v - gs.meta(gs.graph_of((int)v)).voff);
+        for (int i = lane; i < d; i += kWarp) {
+            const uint32_t e = merged[r0 + i];
+            nbr[b + i] = e;
+            src[b + i] = (uint32_t)v | ((e >> 2) < vloc ? 0x80000000u : 0u);
         }
     }
 }
@@ -784,6 +978,94 @@ int launch_build_graph(const GSet &gs, const BuildBufs &bb, int max_n, int *stat
                                                                               bb.nptr, bb.nbr, bb.src, rw);
     launches++;
     return cudaGetLastError() == cudaSuccess ? launches : ACC_ERR_CUDA;
+}
+
+int sparse_big_rows_cap(long long arcs) { return (int)(2 * arcs / kSortSmall + 2); }
+
+int launch_build_graph_sparse(const GSet &gs, const BuildBufs &bb, const SparseBufs &sb, int max_n, int *status,
+                              unsigned long long *counts, long long ncounts, bool relabel, int num_sms,
+                              cudaStream_t s) {
+    static bool smem_opt_in = false;
+    if (!smem_opt_in) {
+        if (cudaFuncSetAttribute(k_scan_degrees, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kScanSingleMax * 4)) != cudaSuccess ||
+            cudaFuncSetAttribute(k_relabel_graph, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kRelabelSmemMax * 4) != cudaSuccess)
+            return ACC_ERR_CUDA;
+        smem_opt_in = true;
+    }
+    int launches = 0;
+    const long long NV = gs.NV;
+    const int arcs_grid = grid_for(max(gs.M, NV), 256, num_sms);
+    int *cnt = bb.lo, *cur = bb.deg;  // raw entries per row, then the final neighbours below each vertex
+    {
+        IntRanges r = {{bb.deg, bb.lo, bb.deg_in, nullptr}, {NV, NV, relabel ? NV : 0, 0}};
+        const long long items = max(NV, ncounts) > 0 ? max(NV, ncounts) : 1;
+        k_zero<<<grid_for(items, 256 * 4, num_sms), 256, 0, s>>>(nullptr, 0, nullptr, 0, status, counts, ncounts, r);
+        if (!launch_ok()) return ACC_ERR_CUDA;
+        launches++;
+    }
+    if (relabel) {
+        k_arc_degrees<<<arcs_grid, 256, 0, s>>>(gs, bb.deg_in);
+        if (!launch_ok()) return ACC_ERR_CUDA;
+        launches++;
+        if (max_n <= kRelabelSmemMax) {
+            k_relabel_graph<<<gs.B, 1024, (size_t)max_n * 4, s>>>(gs, bb.deg_in, bb.label);
+            if (!launch_ok()) return ACC_ERR_CUDA;
+            launches++;
+        } else {
+            int *dhist = bb.deg;  // zeroed above, zeroed again by k_desc_scatter
+            int *start = reinterpret_cast<int *>(bb.nptr);
+            k_dhist<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, bb.deg_in, dhist);
+            if (!launch_ok()) return ACC_ERR_CUDA;
+            k_desc_starts<<<gs.B, 1024, 0, s>>>(gs, dhist, start);
+            if (!launch_ok()) return ACC_ERR_CUDA;
+            k_desc_scatter<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, bb.deg_in, start, bb.label, dhist);
+            if (!launch_ok()) return ACC_ERR_CUDA;
+            launches += 3;
+        }
+    }
+    k_sp_count<<<arcs_grid, 256, 0, s>>>(gs, relabel ? bb.label : nullptr, status, cnt);
+    if (!launch_ok()) return ACC_ERR_CUDA;
+    launches++;
+    // degree scans: the raw counts into the row offsets (no count bound), and
+    // after the sort the final degrees into nptr (with it)
+    auto scan = [&](const int *d, long long *out, int k) -> int {
+        if (NV <= kScanSingleMax) {
+            k_scan_degrees<<<1, 1024, (size_t)(NV > 0 ? NV : 1) * 4, s>>>(d, (int)NV, out, bb.info, k, max_n, status);
+            return launch_ok() ? 1 : ACC_ERR_CUDA;
+        }
+        const int ntiles = (int)scan_tiles_needed(NV);
+        k_reset_maxdeg<<<1, 1, 0, s>>>(bb.info);
+        if (!launch_ok()) return ACC_ERR_CUDA;
+        k_scan_tiles<<<ntiles, 1024, 0, s>>>(d, (int)NV, bb.tiles, bb.info, k);
+        if (!launch_ok()) return ACC_ERR_CUDA;
+        k_scan_top<<<1, 1024, 0, s>>>(bb.tiles, ntiles, out, (int)NV, bb.info, k, max_n, status);
+        if (!launch_ok()) return ACC_ERR_CUDA;
+        k_scan_apply<<<ntiles, 1024, 0, s>>>(d, (int)NV, bb.tiles, out);
+        return launch_ok() ? 4 : ACC_ERR_CUDA;
+    };
+    int rc = scan(cnt, sb.roff, 0);
+    if (rc < 0) return rc;
+    launches += rc;
+    k_sp_scatter<<<arcs_grid, 256, 0, s>>>(gs, relabel ? bb.label : nullptr, sb.roff, cur, sb.raw);
+    if (!launch_ok()) return ACC_ERR_CUDA;
+    launches++;
+    if (gs.M > 0 && cudaMemsetAsync(sb.merged, 0, (size_t)(2 * gs.M) * sizeof(uint32_t), s) != cudaSuccess)
+        return ACC_ERR_CUDA;
+    k_sp_sort_small<<<grid_for((NV + kSortWarps - 1) / kSortWarps, 1, num_sms), kSortWarps * kWarp, 0, s>>>(
+        gs, sb.roff, sb.raw, sb.merged, bb.deg, bb.lo, sb.big, bb.info);
+    if (!launch_ok()) return ACC_ERR_CUDA;
+    k_sp_sort_big<<<num_sms, 256, 0, s>>>(gs, sb.roff, sb.raw, sb.merged, bb.deg, bb.lo, sb.big, bb.info);
+    if (!launch_ok()) return ACC_ERR_CUDA;
+    launches += 2;
+    if ((rc = scan(bb.deg, bb.nptr, bb.k)) < 0) return rc;
+    launches += rc;
+    k_sp_compact<<<grid_for(NV * kWarp, 256, num_sms), 256, 0, s>>>(gs, sb.roff, sb.merged, bb.deg, bb.nptr, bb.nbr,
+                                                                   bb.src);
+    if (!launch_ok()) return ACC_ERR_CUDA;
+    launches++;
+    return launches;
 }
 
 int launch_clear_graph(const GSet &gs, uint32_t *state, const uint32_t *occ, int occ_w, int num_sms, cudaStream_t s) {

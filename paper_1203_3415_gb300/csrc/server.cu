@@ -262,7 +262,7 @@ int acc_server_add_graph(acc_server *sv, const int64_t *d_rowptr, const int32_t 
                          int32_t *graph_id) {
     if (!sv || !d_rowptr || !graph_id || (m > 0 && !d_col)) return ACC_ERR_ARG;
     if (n < 0 || m < 0 || m >= (1ll << 31)) return ACC_ERR_INPUT;
-    if (n > ACC_MAX_N) return ACC_ERR_TOO_LARGE;
+    if (n > ACC_MAX_N_SPARSE) return ACC_ERR_TOO_LARGE;  // requests are counted in the count mode
     Graph g{d_rowptr, d_col, n, m, {0.0, 0.0, 0.0}};
     if (!ok(cudaSetDevice(sv->device))) return ACC_ERR_CUDA;
     const int rc = estimate_work(g);

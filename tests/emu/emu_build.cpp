@@ -1,15 +1,16 @@
 // Runs the graph builder (csrc/graph.cu, kernels and host launcher, with each
 // launch turned into emu_launch; source in graph_kernels.inc) on the host
-// over a set of B graphs given as input CSRs: relabel + 256 k num_sms B
-// (int64; k > 0 turns on the count-bound check for that k), then
+// over a set of B graphs given as input CSRs: relabel + 2 sparse + 256 k
+// num_sms B (int64; sparse: the build without the dense block; k > 0 turns
+// on the count-bound check for that k), then
 // n m of each graph (int64), then each graph's rowptr[n + 1] (int64) and
 // col[m] (int32).  The set is built twice: first over a pair-state buffer
 // full of garbage (swept by the build's zeroing), then, after the builder's
 // own clear, over the buffer it left clean.  Output per build, as records of
 // int64 (length, values): status, launches, nnz, maxdeg and whether the
 // counts were zeroed; label[NV]; deg[NV]; lo[NV]; nptr[NV + 1]; nbr[nnz];
-// the state words; the occupancy words; after the clear, whether the state
-// buffer is all zero.
+// the state words; the occupancy words (both empty for the sparse build);
+// after the clear, whether the state buffer is all zero; src[nnz].
 #include "shim.h"
 #include "common.cuh"
 thread_local dim threadIdx, blockIdx;
@@ -36,6 +37,7 @@ int main(int argc, char **argv) {
     long long h[3];
     if (!rd(f, h, 3)) return 2;
     const bool relabel = (h[0] & 1) != 0;
+    const bool sparse = (h[0] & 2) != 0;
     const int guard_k = (int)(h[0] >> 8);
     const int num_sms = (int)h[1];
     const long long B = h[2];
@@ -74,6 +76,9 @@ int main(int argc, char **argv) {
     std::vector<int> deg(NV + 1), lo(NV + 1), label(NV + 1), deg_in(NV + 1), gid(NV + 1);
     std::vector<long long> nptr(NV + 1), tiles(acc::scan_tiles_needed(NV) + 1);
     std::vector<uint32_t> nbr(2 * M + 1), occ(NV * occ_w + 1);
+    std::vector<uint32_t> src(2 * M + 1), raw(2 * M + 1), merged(2 * M + 1);
+    std::vector<long long> roff(NV + 1);
+    std::vector<int> big(acc::sparse_big_rows_cap(M));
     acc::GraphInfo info{};
     std::vector<unsigned long long> counts(7, 123);
     int status = -7;
@@ -102,10 +107,15 @@ int main(int argc, char **argv) {
     bb.occ_w = occ_w;
     bb.info = &info;
     bb.k = guard_k;
+    bb.src = src.data();
+    const acc::SparseBufs sb = {raw.data(), merged.data(), roff.data(), big.data()};
     for (int pass = 0; pass < 2; pass++) {
         std::fill(counts.begin(), counts.end(), 123ull);
-        const int launches = acc::launch_build_graph(gs, bb, max_n, &status, counts.data(), (long long)counts.size(),
-                                                     relabel, num_sms, nullptr);
+        const int launches =
+            sparse ? acc::launch_build_graph_sparse(gs, bb, sb, max_n, &status, counts.data(),
+                                                    (long long)counts.size(), relabel, num_sms, nullptr)
+                   : acc::launch_build_graph(gs, bb, max_n, &status, counts.data(), (long long)counts.size(), relabel,
+                                             num_sms, nullptr);
         bool zeroed = true;
         for (auto c : counts) zeroed = zeroed && c == 0;
         const long long nnz = status == 0 ? info.nnz : 0;
@@ -116,12 +126,13 @@ int main(int argc, char **argv) {
         put(lo.data(), NV);
         put(nptr.data(), NV + 1);
         put(nbr.data(), (size_t)nnz);
-        put(state.data(), words);
-        put(occ.data(), NV * occ_w);
-        if (acc::launch_clear_graph(gs, state.data(), occ.data(), occ_w, num_sms, nullptr) < 0) return 4;
+        put(state.data(), sparse ? 0 : words);
+        put(occ.data(), sparse ? 0 : NV * occ_w);
+        if (!sparse && acc::launch_clear_graph(gs, state.data(), occ.data(), occ_w, num_sms, nullptr) < 0) return 4;
         long long clean = 1;
-        for (long long i = 0; i < words; i++) clean = clean && state[i] == 0;
+        for (long long i = 0; i < words; i++) clean = clean && (sparse || state[i] == 0);
         put(&clean, 1);
+        put(src.data(), (size_t)nnz);
         bb.state_clean = true;
     }
     fclose(out);

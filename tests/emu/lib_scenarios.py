@@ -106,9 +106,10 @@ def scenario_modes(lib):
                 if mode == acc.ACC_MODE_COUNT and c.stats()[6] != esu_scanned_entries(n, s, d, k):
                     raise AssertionError(f"k {k} n {n}: {c.stats()[6]} entries scanned")
     # the count mode probing the hashed adjacency tables (built on the device
-    # after the neighbour lists: one more kernel), then the dense block again
+    # after the neighbour lists: one more kernel), with the lists built with
+    # and without the dense block, and the dense block again
     ok(lib.acc_ctx_set_mode(c.h, acc.ACC_MODE_COUNT), "acc_ctx_set_mode")
-    for adj in (acc.ACC_ADJ_HASH, acc.ACC_ADJ_DENSE, acc.ACC_ADJ_HASH):
+    for adj in (acc.ACC_ADJ_HASH, acc.ACC_ADJ_SPARSE, acc.ACC_ADJ_DENSE, acc.ACC_ADJ_SPARSE, acc.ACC_ADJ_HASH):
         ok(lib.acc_ctx_set_adjacency(c.h, adj), "acc_ctx_set_adjacency")
         for k, gs in cases.items():
             for n, s, d in gs:
@@ -116,7 +117,7 @@ def scenario_modes(lib):
                 rc, st, got = c.count(rp, cl, n, k)
                 if rc or st or got.tolist() != oracle.count(n, s, d, k).tolist():
                     raise AssertionError(f"adjacency {adj} k {k} n {n}: rc {rc} status {st}")
-    if lib.acc_ctx_set_adjacency(c.h, 3) != acc.ACC_ERR_ARG:
+    if lib.acc_ctx_set_adjacency(c.h, 4) != acc.ACC_ERR_ARG:
         raise AssertionError("an unknown adjacency choice is accepted")
     c.close()
 
@@ -203,9 +204,17 @@ def scenario_host_and_errors(lib):
         raise AssertionError("k = 6 accepted")
     if lib.acc_motif_count(c.h, None, P(cl), n, len(cl), 3, None, P(out), None) != acc.ACC_ERR_ARG:
         raise AssertionError("null rowptr accepted")
+    # above the size limits (the count mode takes graphs above the dense
+    # block's limit, up to ACC_MAX_N_SPARSE): refused on the host, before the
+    # undersized arrays passed here could be read
+    if lib.acc_motif_count(c.h, P(rp), P(cl), acc.ACC_MAX_N_SPARSE + 1, len(cl), 3, None, P(out), None) != \
+            acc.ACC_ERR_TOO_LARGE:
+        raise AssertionError("n above the sparse limit accepted")
+    ok(lib.acc_ctx_set_mode(c.h, acc.ACC_MODE_ENUMERATE), "acc_ctx_set_mode")
     if lib.acc_motif_count(c.h, P(rp), P(cl), acc.ACC_MAX_N + 1, len(cl), 3, None, P(out), None) != \
             acc.ACC_ERR_TOO_LARGE:
-        raise AssertionError("n above the limit accepted")
+        raise AssertionError("n above the dense limit accepted outside the count mode")
+    ok(lib.acc_ctx_set_mode(c.h, acc.ACC_MODE_COUNT), "acc_ctx_set_mode")
     # an empty graph counts nothing
     e_rp = np.zeros(5, np.int64)
     rc = lib.acc_motif_count(c.h, P(e_rp), P(np.zeros(1, np.int32)), 4, 0, 3, None, P(out), None)

@@ -5,7 +5,7 @@ Calls only the CPU oracle (``oracle/``) and the seeded generators
 the workload, the SHA-256 of the generated arc list (so a test can tell that
 it regenerated the same graph), N_k and every nonzero class count.
 
-    python tests/golden/make_golden.py [--threads T] [--only NAME ...] [--batch] [--serving]
+    python tests/golden/make_golden.py [--threads T] [--only NAME ...] [--batch] [--serving] [--million]
 """
 import argparse
 import hashlib
@@ -104,19 +104,46 @@ def make_serving_pool_golden(path, threads):
                 print(f"serving graph {gi} k={k}: N_k = {int(counts.sum())} in {time.time() - t:.1f} s", flush=True)
 
 
+def million_vertex_graph():
+    """Sparse directed Chung-Lu graph above the dense block's size limit:
+    10^6 vertices, 3 * 10^6 arcs, exponent 2.3, degree cap 100, 10%
+    reciprocal, seed 3600."""
+    return synth.chung_lu(1_000_000, 3_000_000, 2.3, 100, 10, 3600)
+
+
+def make_million_golden(path, threads):
+    """The million-vertex graph at k = 3 and 4: graph digest, N_k and the
+    digest of its int64 counts."""
+    g = million_vertex_graph()
+    with open(path, "w") as f:
+        f.write("# sparse directed Chung-Lu graph, n = 10^6, m = 3 10^6 (exponent 2.3, cap 100, 10% reciprocal,"
+                " seed 3600)\n")
+        f.write(f"# oracle ESU, {threads} threads; one line per k:\n")
+        f.write("# k n m graph_sha256 total counts_sha256\n")
+        for k in (3, 4):
+            t = time.time()
+            counts = oracle.count(g.n, g.src, g.dst, k, threads=threads)
+            f.write(f"{k} {g.n} {g.m} {synth.graph_digest(g)} {int(counts.sum())} {counts_digest(counts)}\n")
+            f.flush()
+            print(f"million-vertex graph k={k}: N_k = {int(counts.sum())} in {time.time() - t:.1f} s", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--threads", type=int, default=oracle.max_threads())
     ap.add_argument("--only", nargs="*")
     ap.add_argument("--batch", action="store_true", help="also write the batched k=4 expectations")
     ap.add_argument("--serving", action="store_true", help="also write the serving test pool's expectations")
+    ap.add_argument("--million", action="store_true", help="also write the million-vertex graph's expectations")
     args = ap.parse_args()
+    if args.million:
+        make_million_golden(os.path.join(HERE, "million_vertices.txt"), args.threads)
     if args.batch:
         make_batch_golden(os.path.join(HERE, "batch_k4.txt"), args.threads)
     if args.serving:
         make_serving_pool_golden(os.path.join(HERE, "serving_pool.txt"), args.threads)
-        if args.only is not None and not args.only:
-            return
+    if args.only is not None and not args.only:
+        return
     for name, (make, k) in WORKLOADS.items():
         if args.only and name not in args.only:
             continue

@@ -460,17 +460,17 @@ def _err_input():
     return int(re.search(r"#define\s+ACC_ERR_INPUT\s+\(?(-?\d+)\)?", hdr).group(1))
 
 
-def _build_many(bins, jobs, binary="emu_build", guard_k=0):
+def _build_many(bins, jobs, binary="emu_build", guard_k=0, sparse=False):
     """Run the graph builder over [(graphs, relabel, num_sms)], graphs a list
     of (n, rowptr, col): per job, the two builds' records."""
     inps = []
     for graphs, relabel, num_sms in jobs:
-        buf = struct.pack("<3q", int(relabel) + 256 * guard_k, num_sms, len(graphs))
+        buf = struct.pack("<3q", int(relabel) + 2 * int(sparse) + 256 * guard_k, num_sms, len(graphs))
         buf += b"".join(struct.pack("<2q", n, len(cl)) for n, _, cl in graphs)
         for n, rp, cl in graphs:
             buf += np.asarray(rp, "<i8").tobytes() + np.asarray(cl, "<i4").tobytes()
         inps.append(buf)
-    names = ("head", "label", "deg", "lo", "nptr", "nbr", "state", "occ", "clean")
+    names = ("head", "label", "deg", "lo", "nptr", "nbr", "state", "occ", "clean", "src")
     res = []
     for o in _run_many(bins[binary], inps, True, bins["dir"]):
         raw = np.frombuffer(o, "<i8")
@@ -483,12 +483,13 @@ def _build_many(bins, jobs, binary="emu_build", guard_k=0):
     return res
 
 
-def _check_build(r, graphs, relabel):
+def _check_build(r, graphs, relabel, sparse=False):
     """The builder's records against a plain construction: per graph, the
     renumbering orders vertices by descending (clamped) out- plus in-degree
     and is a permutation; the pair states, degrees, below-counts, neighbour
-    lists (positions over the whole set) and occupancy bits are those of the
-    renumbered graph."""
+    lists (positions over the whole set), each entry's row (bit 31: a
+    neighbour below the row's vertex) and occupancy bits are those of the
+    renumbered graph (the sparse build keeps no pair states or bits)."""
     status, _, nnz, maxdeg, zeroed = r["head"].tolist()
     assert status == 0 and zeroed == 1 and r["clean"][0] == 1
     voff, base = 0, 0
@@ -521,11 +522,24 @@ def _check_build(r, graphs, relabel):
         occ_all.append(occ)
         voff += n
     cat = lambda xs: np.concatenate(xs).astype(np.int64) if xs else np.zeros(0, np.int64)  # noqa: E731
-    assert np.array_equal(r["state"], cat(st_all))
+    if sparse:
+        assert len(r["state"]) == 0 and len(r["occ"]) == 0
+    else:
+        assert np.array_equal(r["state"], cat(st_all))
+        assert np.array_equal(r["occ"], cat(occ_all))
     assert np.array_equal(r["deg"], cat(deg_all)) and np.array_equal(r["lo"], cat(lo_all))
     assert np.array_equal(r["nptr"], cat(nptr_all)) and np.array_equal(r["nbr"], cat(nbr_all))
-    assert np.array_equal(r["occ"], cat(occ_all))
     assert nnz == base and maxdeg == (int(max(d.max(initial=0) for d in deg_all)) if deg_all else 0)
+    # row of each entry: global vertex, bit 31 for a neighbour below it
+    nptr_cat, nbr_cat = cat(nptr_all), cat(nbr_all)
+    want_src = np.zeros(len(nbr_cat), np.int64)
+    voff = 0
+    for n, _, _ in graphs:
+        for v in range(n):
+            b, e = nptr_cat[voff + v], nptr_cat[voff + v + 1]
+            want_src[b:e] = (voff + v) | np.where((nbr_cat[b:e] >> 2) < v, 1 << 31, 0)
+        voff += n
+    assert np.array_equal(r["src"], want_src)
 
 
 def _raw_csr(n, s, d, rng):
@@ -537,8 +551,9 @@ def _raw_csr(n, s, d, rng):
     return n, rp, d[order].astype(np.int32)
 
 
+@pytest.mark.parametrize("sparse", [False, True], ids=["dense", "sparse"])
 @pytest.mark.parametrize("relabel", [False, True], ids=["as_given", "renumbered"])
-def test_graph_builder_equals_plain_construction(emu_bins, relabel):
+def test_graph_builder_equals_plain_construction(emu_bins, relabel, sparse):
     """The whole builder (zeroing, renumbering, ingest, degree scan, fill,
     then the clear) on the host, built with 2048-vertex single-block limits:
     one small graph (one-block scan, shared-memory renumbering), and a set
@@ -557,9 +572,18 @@ def test_graph_builder_equals_plain_construction(emu_bins, relabel):
             s, d = np.concatenate([s, s[k]]), np.concatenate([d, d[k]])
         big.append(_raw_csr(n, s, d, rng))
     jobs = [(small, relabel, 1), (big, relabel, 2)]
-    for (graphs, _, _), builds in zip(jobs, _build_many(emu_bins, jobs)):
+    if sparse:
+        # rows longer than the warp sort's 2048 raw entries take the block
+        # sort: a hub with 3000 out-arcs, 600 of them repeated, and 500 in-arcs
+        rng2 = np.random.default_rng(950 + relabel)
+        n = 4000
+        outs = rng2.permutation(np.arange(1, n))[:3000]
+        s = np.concatenate([np.zeros(3000 + 600, np.int64), rng2.permutation(np.arange(1, n))[:500]])
+        d = np.concatenate([outs, outs[:600], np.zeros(500, np.int64)])
+        jobs.append(([_raw_csr(n, s, d, rng)], relabel, 2))
+    for (graphs, _, _), builds in zip(jobs, _build_many(emu_bins, jobs, sparse=sparse)):
         for r in builds:
-            _check_build(r, graphs, relabel)
+            _check_build(r, graphs, relabel, sparse)
 
 
 def test_graph_builder_reports_malformed_input(emu_bins):
@@ -583,13 +607,14 @@ def test_graph_builder_reports_malformed_input(emu_bins):
     jobs.append(([(3, ok_rp, ok_col), empty_with_arcs], False, 1))
     good = [(3, ok_rp, ok_col)]
     jobs.append((good, True, 1))
-    res = _build_many(emu_bins, jobs)
-    for (graphs, _, _), builds in zip(jobs[:-1], res[:-1]):
-        for r in builds:
-            assert r["head"][0] == err, graphs
-            assert r["clean"][0] == 1
-    for r in res[-1]:
-        _check_build(r, good, True)
+    for sparse in (False, True):
+        res = _build_many(emu_bins, jobs, sparse=sparse)
+        for (graphs, _, _), builds in zip(jobs[:-1], res[:-1]):
+            for r in builds:
+                assert r["head"][0] == err, graphs
+                assert r["clean"][0] == 1
+        for r in res[-1]:
+            _check_build(r, good, True, sparse)
 
 
 def test_count_bound_guard(emu_bins):

@@ -244,7 +244,11 @@ def test_malformed_input(counter):
     rr = torch.from_numpy(good_r).cuda()
     cc = torch.from_numpy(good_c).cuda()
     assert p.acc_motif_count(counter.ctx, rr.data_ptr(), cc.data_ptr(), 5, 3, 6, 0, rr.data_ptr(), None) == p.ACC_ERR_K
-    assert p.acc_motif_count(counter.ctx, rr.data_ptr(), cc.data_ptr(), p.ACC_MAX_N + 1, 3, 3, 0, rr.data_ptr(),
+    # above the size limit (the count mode builds graphs above the dense
+    # block's limit without it, up to ACC_MAX_N_SPARSE vertices): refused on
+    # the host, before the undersized arrays passed here could be read
+    too_many = p.ACC_MAX_N_SPARSE + 1 if counter.mode == p.ACC_MODE_COUNT else p.ACC_MAX_N + 1
+    assert p.acc_motif_count(counter.ctx, rr.data_ptr(), cc.data_ptr(), too_many, 3, 3, 0, rr.data_ptr(),
                              None) == p.ACC_ERR_TOO_LARGE
     assert p.acc_motif_count(counter.ctx, 0, cc.data_ptr(), 5, 3, 3, 0, rr.data_ptr(), None) == p.ACC_ERR_ARG
     # a good graph after the errors still counts

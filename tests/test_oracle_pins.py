@@ -375,3 +375,32 @@ def test_zscores_closed_form(orc):
     rand = np.array([[10], [20]], dtype=np.int64)
     assert orc.zscores(np.array([15]), rand)[0] == 0.0
     assert orc.zscores(np.array([25]), rand)[0] == 2.0
+
+
+def test_sorted_list_arc_test_equals_bit_matrix(orc):
+    """The oracle's two arc tests (dense bit matrix; binary search in sorted
+    out-lists, used above 65536 vertices) give the same counts: on random
+    digraphs with repeated arcs, on the closed forms, and on the brute force
+    over all k-subsets."""
+    rng = np.random.default_rng(4400)
+    try:
+        cases = []
+        for _ in range(40):
+            n = int(rng.integers(1, 22))
+            s, d = random_digraph(rng, n, p=float(rng.random()), recip=float(rng.random()))
+            if len(s):  # repeated arcs
+                j = rng.integers(0, len(s), size=len(s) // 3 + 1)
+                s, d = np.concatenate([s, s[j]]), np.concatenate([d, d[j]])
+            cases.append((n, s, d))
+        dense = [[orc.count(n, s, d, k).tolist() for k in (3, 4, 5)] for n, s, d in cases]
+        orc.set_dense_max(0)
+        for (n, s, d), want in zip(cases, dense):
+            assert [orc.count(n, s, d, k).tolist() for k in (3, 4, 5)] == want
+            if n <= 12:
+                assert orc.count(n, s, d, 4).tolist() == orc.count_bruteforce(n, s, d, 4).tolist()
+        s, d = complete_bidirected(9)
+        assert int(orc.count(9, s, d, 5).sum()) == math.comb(9, 5)
+        s, d = directed_path(30)
+        assert int(orc.count(30, s, d, 4).sum()) == 27
+    finally:
+        orc.set_dense_max(65536)
