@@ -319,6 +319,28 @@ def issue_peak_gops(env):
     return props.multi_processor_count * 4 * 32 * sm_max * 1e6 / 1e9, src
 
 
+def table_build_ms(env, k, stream):
+    """Device time of one build of the code -> class table for k (canonical
+    labelling of all 2^(k(k-1)) codes and the class ranks), median of three
+    builds after one untimed build, through the allocation-free entry point
+    (so no allocation sits between the events)."""
+    torch, acc, dev = env.torch, env.acc, env.dev
+    table = torch.empty(1 << (k * (k - 1)), dtype=torch.int16, device=dev)
+    codes = torch.empty(acc.NUM_CLASSES[k], dtype=torch.int32, device=dev)
+    times = []
+    for i in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = acc.acc_motif_build_table_static(k, stream.cuda_stream, table.data_ptr(), codes.data_ptr())
+        e1.record(stream)
+        if rc < 0:
+            raise RuntimeError(f"table build failed: {acc.acc_strerror(rc)}")
+        torch.cuda.synchronize(dev)
+        if i:
+            times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
+
+
 def measure_single(env, workload, steps, warmup, mode="count", schedule="", cpu_baseline=True):
     """One graph counted per step through acc_motif_count, inputs resident in
     HBM, L2 flushed between steps; then the same through the host-buffer
@@ -419,6 +441,7 @@ def measure_single(env, workload, steps, warmup, mode="count", schedule="", cpu_
     e2e_max = reduce_max(dist, e2e_t, dev)
     e2e_units = reduce_sum(dist, float(n_k) * e2e_steps, dev)
     counter.close()
+    table_ms = table_build_ms(env, k, stream)
     if env.rank != 0:
         return None
 
@@ -472,6 +495,8 @@ def measure_single(env, workload, steps, warmup, mode="count", schedule="", cpu_
                       "enumerate_phase1": statistics.mean(p1_ms), "enumerate_phase2": statistics.mean(p2_ms),
                       "step_median": statistics.median(step_ms)},
         "parity_vs_stored_oracle_counts": parity,
+        # once per k per device, outside the timed steps
+        "table_build_ms": table_ms,
         "work": {"chunks": stats["chunks"], "undirected_edges": stats["undirected_edges"],
                  "max_degree": stats["max_degree"], "blocks": stats["blocks"]},
     }

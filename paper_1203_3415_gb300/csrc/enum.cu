@@ -40,6 +40,8 @@
 // (a second launch) drains the queue.
 #include <math.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace acc {
@@ -115,10 +117,14 @@ struct Layout {
     static constexpr int SH_ROW = 2 * (K - 1);   // field of slot k-2
     static constexpr size_t lut = SMEM_LUT ? (((size_t(1) << NB) * 2 + 15) & ~size_t(15)) : 0;
     static constexpr size_t pending = 16;
-    static constexpr size_t hist = (K == 5 ? size_t(NCLS) * 4 : size_t(kWarpsPerBlock) * NCLS * 4 + 15) & ~size_t(15);
+    // histogram words per warp (k <= 4) or block (k = 5): the classes, then a
+    // trap bin that takes any add of a code without a class (never expected;
+    // non-zero at the end means an internal error)
+    static constexpr int HSTRIDE = NCLS + 1;
+    static constexpr size_t hist = ((K == 5 ? size_t(1) : size_t(kWarpsPerBlock)) * HSTRIDE * 4 + 15) & ~size_t(15);
     static constexpr size_t ebuf = size_t(kWarpsPerBlock) * LISTS * CAP * 4;
     static constexpr int G = 1 << (2 * (K - 2));  // state vectors to the prefix: 4, 16, 64
-    static constexpr size_t groups = size_t(kWarpsPerBlock) * 3 * G * 4;  // count mode: sizes + list
+    static constexpr size_t groups = size_t(kWarpsPerBlock) * 2 * G * 4;  // count mode: sizes + list
     // count mode: rows staged for the flat scan (a batch of 32 is staged
     // only while the ring has room for it)
     static constexpr int WIN = K == 5 ? ACC_CWIN5 : ACC_CWIN;
@@ -282,26 +288,25 @@ struct Sink {
     // are read as signed 32-bit when drained; a delta too large for them goes
     // straight to the int64 counts.
     __device__ __forceinline__ void add(int cls, long long delta) {
-        if (cls < 0) {
-            set_status(status, ACC_ERR_INTERNAL);
-            return;
-        }
         if (direct || delta >= (1ll << 28) || delta <= -(1ll << 28)) {
-            atomicAdd(&counts[cls], (unsigned long long)delta);
+            if (cls < 0) set_status(status, ACC_ERR_INTERNAL);
+            else atomicAdd(&counts[cls], (unsigned long long)delta);
             return;
         }
-        atomicAdd(&hist[cls], (uint32_t)(int32_t)delta);
+        atomicAdd(&hist[min((uint32_t)cls, (uint32_t)Layout<K>::NCLS)], (uint32_t)(int32_t)delta);
         moved += (unsigned long long)(delta < 0 ? -delta : delta);
     }
 
     // Count mode: add +1 or -1 to class cls (the scan's leaves and moves).
+    // A code without a class (cls < 0) lands in the shared trap bin, checked
+    // at the end of the kernel, so the hot loop carries no branch for it.
     __device__ __forceinline__ void add1(int cls, int delta) {
-        if (cls < 0) {
-            set_status(status, ACC_ERR_INTERNAL);
-            return;
+        if (direct) {
+            if (cls < 0) set_status(status, ACC_ERR_INTERNAL);
+            else atomicAdd(&counts[cls], (unsigned long long)(long long)delta);
+        } else {
+            atomicAdd(&hist[min((uint32_t)cls, (uint32_t)Layout<K>::NCLS)], (uint32_t)delta);
         }
-        if (direct) atomicAdd(&counts[cls], (unsigned long long)(long long)delta);
-        else atomicAdd(&hist[cls], (uint32_t)delta);
     }
 
     __device__ __forceinline__ int cls_of(uint32_t code) const {
@@ -341,7 +346,7 @@ struct Sink {
     // `code` (into its run, added to the histogram when the class changes).
     __device__ __forceinline__ void bump(uint32_t code, bool valid) {
         if (!valid) return;
-        const int cls = Layout<K>::SMEM_LUT ? (int)lut[code] : (int)__ldg(lut + code);
+        const int cls = cls_of(code);
         if (cls == run_cls) {
             ++run_len;
         } else {
@@ -552,10 +557,11 @@ __device__ __forceinline__ bool in_list(const uint32_t *s, uint32_t u, const uin
 template <int K, bool HASH>
 __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, const uint32_t *E, int B, int jlo,
                                              int jend, bool bulk, const uint32_t *pm, uint32_t pcode,
-                                             uint32_t root, bool w2_in_a, uint32_t *gcnt, uint32_t *ring, int lane) {
+                                             uint32_t root, bool w2_in_a, uint32_t *gcnt, uint32_t *ring,
+                                             int lane) {
     using L = Layout<K>;
     if (bulk) {
-        uint32_t *glist = gcnt + L::G;  // (group, count) pairs of the non-empty groups
+        uint32_t *glist = gcnt + L::G;  // (count << 6) | group of each non-empty group (a list has < 2^26 members)
         for (int i = lane; i < L::G; i += kWarp) gcnt[i] = 0;
         __syncwarp();
         for (int q = lane; q < B; q += kWarp) atomicAdd(&gcnt[e_sv(E[q])], 1u);
@@ -565,11 +571,7 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
             const int gi = b0 + lane;
             const uint32_t c = gi < L::G ? gcnt[gi] : 0u;
             const unsigned m = __ballot_sync(kFull, c > 0);
-            if (c > 0) {
-                const int pos = ng + __popc(m & ((1u << lane) - 1u));
-                glist[2 * pos] = (uint32_t)gi;
-                glist[2 * pos + 1] = c;
-            }
+            if (c > 0) glist[ng + __popc(m & ((1u << lane) - 1u))] = (c << 6) | (uint32_t)gi;
             ng += __popc(m);
         }
         __syncwarp();
@@ -584,8 +586,9 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
             if (ia * ng - ia * (ia - 1) / 2 > q) ia--;
             else if (ia + 1 < ng && (ia + 1) * ng - (ia + 1) * ia / 2 <= q) ia++;
             const int ib = ia + (q - (ia * ng - ia * (ia - 1) / 2));
-            const uint32_t ga = glist[2 * ia], ca = glist[2 * ia + 1];
-            const uint32_t gb = glist[2 * ib], cb = glist[2 * ib + 1];
+            const uint32_t ea = glist[ia], eb = glist[ib];
+            const uint32_t ga = ea & 63u, ca = ea >> 6;
+            const uint32_t gb = eb & 63u, cb = eb >> 6;
             const long long pairs = ib == ia ? (long long)ca * (ca - 1) / 2 : (long long)ca * cb;
             if (pairs) sink.add(sink.cls_of(pcode | (ga << L::SH_ROW) | gb), pairs);
         }
@@ -599,20 +602,21 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
     // offset, list entry), and a window finds each lane's row from the ring
     // rows that start inside it (one OR-reduction of their start bits and a
     // population count).  Flat positions wrap modulo 2^32; only differences
-    // below 2^31 are compared.
+    // below 2^31 are compared.  A step takes W windows.
     constexpr int W = L::WIN;
     constexpr int RM = L::RING - 1;
     uint32_t *rS = ring, *rO = ring + L::RING, *rE = ring + 2 * L::RING;
     PRow rowp[K - 2];  // adjacency of the prefix vertices
 #pragma unroll
     for (int k2 = 0; k2 < K - 2; k2++) rowp[k2] = prow<HASH>(g, pm[k2]);
-    uint32_t T = 0, C = 0;  // flat entries staged, consumed
-    int tail = 0, cur = -1;  // ring rows staged; last ring row starting before C
+    uint32_t T = 0;          // flat entries staged
+    uint32_t F = 0;          // flat entries consumed
+    int tail = 0, cur = -1;  // ring rows staged; last ring row starting before F
     int jb = jlo;
-    for (;;) {
-        // stage rows while fewer than W windows are pending and the ring has
-        // room for 32 more rows (the live rows are cur .. tail - 1)
-        while (jb < jend && T - C < 32u * W && tail - cur + kWarp <= L::RING) {
+    // stage rows while fewer than W windows are pending and the ring
+    // has room for 32 more rows (the live rows are cur .. tail - 1)
+    auto stage = [&]() {
+        while (jb < jend && T - F < 32u * W && tail - cur + kWarp <= L::RING) {
             const int j = jb + lane;
             uint32_t ej = 0, first = 0;
             int cnt = 0;
@@ -640,29 +644,30 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
             sink.scanned += (unsigned long long)tot;
             jb += kWarp;
         }
-        if (T == C) break;
-        __syncwarp();
-        const uint32_t pend = T - C;
-        uint32_t ue[W], er[W];
-        bool ok[W];
-#pragma unroll
-        for (int w = 0; w < W; w++) {
-            const uint32_t t0 = C + 32u * w;
-            // ring rows cur+1 .. cur+32 may start inside [t0, t0 + 32)
-            uint32_t bit = 0;
-            const int r = cur + 1 + lane;
-            if (r < tail) {
-                const uint32_t sd = rS[r & RM] - t0;
-                if (sd < 32u) bit = 1u << sd;
-            }
-            const uint32_t starts = __reduce_or_sync(kFull, bit);
-            const int row = cur + __popc(starts & (0xFFFFFFFFu >> (31 - lane)));
-            cur += __popc(starts);
-            ok[w] = 32u * w + lane < pend;
-            er[w] = rE[row & RM];
-            const uint32_t off = rO[row & RM];
-            ue[w] = ok[w] ? __ldg(g.nbr + (off + t0 + lane)) : 0u;
+    };
+    // the ring row of this lane's entry in the window starting at F + 32 w
+    // (whole warp; windows in order)
+    auto locate = [&](int w) -> int {
+        const uint32_t t0 = F + 32u * w;
+        // ring rows cur+1 .. cur+32 may start inside [t0, t0 + 32)
+        uint32_t bit = 0;
+        const int r = cur + 1 + lane;
+        if (r < tail) {
+            const uint32_t sd = rS[r & RM] - t0;
+            if (sd < 32u) bit = 1u << sd;
         }
+        const uint32_t starts = __reduce_or_sync(kFull, bit);
+        const int row = cur + __popc(starts & (0xFFFFFFFFu >> (31 - lane)));
+        cur += __popc(starts);
+        return row & RM;
+    };
+    // classes of one step's leaves: an exclusive leaf P + {x, u} (u adjacent
+    // to no prefix vertex) adds one to its class; an adjacent pair of list
+    // members {x, u} (each once, from its smaller vertex) moves one leaf from
+    // the non-adjacent class to its own.  Table reads of every window are
+    // issued before any histogram add, with no branch in between.
+    auto classify = [&](const auto &ue, const auto &er, const auto &ok) {
+        constexpr int W = std::extent<std::remove_reference_t<decltype(ue)>>::value;
         uint32_t sv[W][K - 2];
 #pragma unroll
         for (int w = 0; w < W; w++) {
@@ -670,12 +675,6 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
 #pragma unroll
             for (int k2 = 0; k2 < K - 2; k2++) sv[w][k2] = ok[w] ? pget<HASH>(rowp[k2], u) : 0u;
         }
-        // classes of the step's leaves: an exclusive leaf P + {x, u} (u
-        // adjacent to no prefix vertex) adds one to its class; an adjacent
-        // pair of list members {x, u} (each once, from its smaller vertex)
-        // moves one leaf from the non-adjacent class to its own.  Table reads
-        // of every window are issued before any histogram add, with no branch
-        // in between.
         int add_cls[W];
         bool add[W], adj[W];
         uint32_t base[W];
@@ -697,9 +696,48 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
 #pragma unroll
         for (int w = 0; w < W; w++)
             if (adj[w]) sink.add1(sink.cls_of(base[w]), -1);
-        const uint32_t used = pend < 32u * W ? pend : 32u * W;
-        C += used;
+    };
+    // one step of NW windows; FULL: all NW windows hold entries (no lane
+    // masks).  The last step of a list takes only the windows it fills.
+    auto step = [&](auto nw, auto full) {
+        constexpr int NW = decltype(nw)::value;
+        constexpr bool FULL = decltype(full)::value;
+        const uint32_t pend = T - F;
+        uint32_t ue[NW], er[NW];
+        bool ok[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+            const int row = locate(w);
+            ok[w] = FULL || 32u * w + lane < pend;
+            er[w] = rE[row];
+            const uint32_t off = rO[row];
+            ue[w] = ok[w] ? __ldg(g.nbr + (off + F + 32u * w + lane)) : 0u;
+        }
+        classify(ue, er, ok);
+        const uint32_t used = FULL || pend >= 32u * NW ? 32u * NW : pend;
+        F += used;
         sink.after_batch(2u * used, lane);  // each entry moves at most two counters by one
+    };
+    static_assert(W >= 1 && W <= 4, "windows per step");
+    for (;;) {
+        stage();
+        const uint32_t pend = T - F;
+        if (!pend) break;
+        __syncwarp();
+        if (pend >= 32u * W) {
+            step(std::integral_constant<int, W>{}, std::true_type{});
+        } else if (pend > 32u * (W - 1)) {
+            step(std::integral_constant<int, W>{}, std::false_type{});
+        } else if constexpr (W >= 4) {
+            if (pend > 64u) step(std::integral_constant<int, 3>{}, std::false_type{});
+            else if (pend > 32u) step(std::integral_constant<int, 2>{}, std::false_type{});
+            else step(std::integral_constant<int, 1>{}, std::false_type{});
+        } else if constexpr (W == 3) {
+            if (pend > 32u) step(std::integral_constant<int, 2>{}, std::false_type{});
+            else step(std::integral_constant<int, 1>{}, std::false_type{});
+        } else if constexpr (W == 2) {
+            step(std::integral_constant<int, 1>{}, std::false_type{});
+        }
     }
     __syncwarp();
 }
@@ -1086,13 +1124,13 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? (SET ?
 
     if (L::SMEM_LUT)
         for (int i = tid; i < (1 << L::NB); i += blockDim.x) lut_s[i] = a.lut[i];
-    const int hist_words = K == 5 ? L::NCLS : kWarpsPerBlock * L::NCLS;
+    const int hist_words = K == 5 ? L::HSTRIDE : kWarpsPerBlock * L::HSTRIDE;
     for (int i = tid; i < hist_words; i += blockDim.x) hist[i] = 0;
     if (tid == 0) *pending = 0;
     __syncthreads();
 
     Sink<K> sink;
-    sink.hist = K == 5 ? hist : hist + wib * L::NCLS;
+    sink.hist = K == 5 ? hist : hist + wib * L::HSTRIDE;
     sink.lut = L::SMEM_LUT ? lut_s : a.lut;
     sink.counts_base = a.counts;
     sink.counts = a.counts;
@@ -1111,7 +1149,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? (SET ?
     sc.ovf[0] = a.scratch + gw * a.scratch_per_warp;
     sc.ovf[1] = sc.ovf[0] + a.scratch_per_warp / 2;
     sc.cap = L::CAP;
-    sc.gcnt = groups + (size_t)wib * 3 * L::G;
+    sc.gcnt = groups + (size_t)wib * 2 * L::G;
     sc.ring = rings + (size_t)wib * 3 * L::RING;
     sink.moved = 0;
     sink.scanned = 0;
@@ -1178,6 +1216,9 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? (SET ?
 
     if (COUNT && lane == 0 && sink.scanned) atomicAdd(&a.info->scanned, sink.scanned);
     __syncthreads();
+    // an add that found no class (never expected) is an internal error
+    if (K <= 4 ? (lane == 0 && sink.hist[L::NCLS] != 0u) : (tid == 0 && hist[L::NCLS] != 0u))
+        set_status(a.status, ACC_ERR_INTERNAL);
     if (several) {
         // each warp drains its own histogram to the graph it ended on
         // (k = 5 with several graphs counted straight into int64)
@@ -1195,7 +1236,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? (SET ?
     } else {
         for (int c = tid; c < L::NCLS; c += blockDim.x) {
             long long s = 0;
-            for (int w = 0; w < kWarpsPerBlock; w++) s += (int32_t)hist[w * L::NCLS + c];
+            for (int w = 0; w < kWarpsPerBlock; w++) s += (int32_t)hist[w * L::HSTRIDE + c];
             if (s) atomicAdd(&a.counts[c], (unsigned long long)s);
         }
     }
