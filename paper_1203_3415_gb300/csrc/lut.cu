@@ -33,16 +33,22 @@ template <>
 struct Fact<0> { static constexpr int v = 1; };
 
 // Thread per code: weak connectivity, then the minimum code over all vertex
-// orders.  dest[p][b] is where order p sends code bit b.  Each block also
-// ranks the canonical codes among its own kRankBlock codes (rank_local) and
-// writes how many it holds (block_count); k_rank_scan turns the block counts
-// into offsets, so rank(c) = rank_local[c] + block_off[c / kRankBlock].
+// orders.  A code's bits for the arcs out of vertex i form one row of k-1
+// bits (bit i (k-1) + t for the arc to the t-th other vertex), so the image
+// of a code under order p is the OR over i of img[p][i][row i]: one table
+// load per vertex instead of one per set bit.  Each block builds img (dest
+// [p][b] is where order p sends code bit b) and also ranks the canonical
+// codes among its own kRankBlock codes (rank_local) and writes how many it
+// holds (block_count); k_rank_scan turns the block counts into offsets, so
+// rank(c) = rank_local[c] + block_off[c / kRankBlock].
 template <int K>
 __global__ void __launch_bounds__(kRankBlock) k_canon(uint32_t *canon, int *rank_local, int *block_count) {
     constexpr int NB = K * (K - 1);
     constexpr int NP = Fact<K>::v;
+    constexpr int R = 1 << (K - 1);  // values of one vertex's row
     constexpr uint32_t NCODES = 1u << NB;
     __shared__ uint8_t dest[NP][NB];
+    __shared__ uint32_t img[NP][K][R];
     __shared__ int warp_off[kRankBlock / 32];
     for (int p = threadIdx.x; p < NP; p += blockDim.x) {
         // decode order p from the factorial number system
@@ -61,6 +67,14 @@ __global__ void __launch_bounds__(kRankBlock) k_canon(uint32_t *canon, int *rank
         for (int i = 0; i < K; i++)
             for (int j = 0; j < K; j++)
                 if (i != j) dest[p][code_bit(K, i, j)] = (uint8_t)code_bit(K, pi[i], pi[j]);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < NP * K * R; e += blockDim.x) {
+        const int p = e / (K * R), i = (e / R) % K, row = e % R;
+        uint32_t out = 0;
+        for (int t = 0; t < K - 1; t++)
+            if ((row >> t) & 1) out |= 1u << dest[p][i * (K - 1) + t];
+        img[p][i][row] = out;
     }
     __syncthreads();
     const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -82,14 +96,14 @@ __global__ void __launch_bounds__(kRankBlock) k_canon(uint32_t *canon, int *rank
             reach = nxt;
         }
         if (reach == (1u << K) - 1u) {
+            int row[K];
+#pragma unroll
+            for (int i = 0; i < K; i++) row[i] = (int)((c >> (i * (K - 1))) & (R - 1u));
             best = c;
             for (int p = 0; p < NP; p++) {
-                uint32_t out = 0, rest = c;
-                while (rest) {
-                    const int b = __ffs(rest) - 1;
-                    out |= 1u << dest[p][b];
-                    rest &= rest - 1;
-                }
+                uint32_t out = 0;
+#pragma unroll
+                for (int i = 0; i < K; i++) out |= img[p][i][row[i]];
                 best = min(best, out);
             }
         }
