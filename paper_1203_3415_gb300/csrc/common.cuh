@@ -272,7 +272,7 @@ int launch_enumerate(int k, const EnumArgs &a, int num_sms, int phase, cudaStrea
                      int grid_den = 1);
 // Default schedule of the enumeration kernels (see EnumArgs::light, target).
 long long enum_default_light();
-long long enum_default_target();
+long long enum_default_target(int k, bool count_mode);
 int enum_grid_warps(int k, int num_sms);
 
 }  // namespace acc

@@ -67,6 +67,9 @@ namespace {
 #ifndef ACC_TARGET
 #define ACC_TARGET (1 << 12)
 #endif
+#ifndef ACC_TARGET5
+#define ACC_TARGET5 (1 << 14)  // k = 5: longer chunks, over which the shared level-2 rows are scanned once
+#endif
 #ifndef ACC_UNROLL
 #define ACC_UNROLL 4
 #endif
@@ -81,6 +84,12 @@ namespace {
 #endif
 #ifndef ACC_RING5
 #define ACC_RING5 64  // the same for k = 5 (its block histogram leaves less shared memory)
+#endif
+#ifndef ACC_SHARED5
+#define ACC_SHARED5 1  // k = 5 count mode: scan the level-2 rows shared by the level-3 lists once
+#endif
+#ifndef ACC_SHARED5_U
+#define ACC_SHARED5_U 2  // lists taken at a time by that scan
 #endif
 #ifndef ACC_CAP5
 #define ACC_CAP5 64  // per-warp shared-memory list entries (each of two lists), k = 5
@@ -129,7 +138,9 @@ struct Layout {
     // only while the ring has room for it)
     static constexpr int WIN = K == 5 ? ACC_CWIN5 : ACC_CWIN;
     static constexpr int RING = K == 5 ? ACC_RING5 : ACC_RING;
-    static constexpr size_t ring = size_t(kWarpsPerBlock) * RING * 3 * 4;
+    // (k = 5: a fourth array, each row's position in the level-2 list)
+    static constexpr int RING_ARRAYS = K == 5 ? 4 : 3;
+    static constexpr size_t ring = size_t(kWarpsPerBlock) * RING * RING_ARRAYS * 4;
     static constexpr size_t total = lut + pending + hist + ebuf + groups + ring;
 };
 
@@ -416,7 +427,7 @@ struct Scratch {
     uint32_t *ovf[2];  // global overflow lists of this warp
     int cap;
     uint32_t *gcnt;    // count mode: group sizes and the non-empty group list
-    uint32_t *ring;    // count mode: staged rows (flat start, entry offset, list entry), RING each
+    uint32_t *ring;    // count mode: staged rows (flat start, entry offset, list entry[, list position]), RING each
 };
 
 // The last two ESU levels over extension list E[0..B), virtual rows
@@ -738,6 +749,123 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
         } else if constexpr (W == 2) {
             step(std::integral_constant<int, 1>{}, std::false_type{});
         }
+    }
+    __syncwarp();
+}
+
+// k = 5, count mode: the rows that the level-3 lists of lists [r0, r1) of
+// one level-2 list E2 take over from E2.  The level-3 list of w2 = E2[j2]
+// starts with E2[j2+1 ..] (its part A), so row j of E2 (x = E2[j]) is a row
+// of every list j2 in [r0, min(j, r1)), with the same neighbour entries and
+// the same states to v and w1 each time.  Here each such row is scanned once:
+// rows j in (r0, B2) are staged into the ring as one flat sequence of
+// 32-entry windows (as in count_leaves, each row also recording j), a lane
+// takes one entry u of a window with its states to v and w1, and the warp
+// then walks the lists j2 (w2 = E2[j2], the same for every lane): a lane
+// whose row lies after j2 probes w2 against x and u and counts its leaf of
+// list j2 exactly as count_leaves would (an exclusive leaf, or the move of
+// an adjacent member pair).  The lists' group-pair counts and the rows of
+// their part B are left to count_leaves.
+template <bool HASH>
+__device__ __forceinline__ void count_shared_rows(const GView &g, Sink<5> &sink, const uint32_t *E2, int B2, int r0,
+                                                  int r1, uint32_t pc01, const PRow &row_v, const PRow &row_w1,
+                                                  uint32_t v, uint32_t w1, uint32_t *ring, int lane) {
+    using L = Layout<5>;
+    constexpr int RM = L::RING - 1;
+    uint32_t *rS = ring, *rO = ring + L::RING, *rE = ring + 2 * L::RING, *rJ = ring + 3 * L::RING;
+    uint32_t T = 0, F = 0;   // flat entries staged, consumed
+    int tail = 0, cur = -1;  // ring rows staged; last ring row starting before F
+    int jb = r0 + 1;
+    for (;;) {
+        while (jb < B2 && T - F < 32u && tail - cur + kWarp <= L::RING) {
+            const int j = jb + lane;
+            uint32_t ej = 0, first = 0;
+            int cnt = 0;
+            if (j < B2) {
+                ej = E2[j];
+                const uint32_t x = e_id(ej);
+                const long long nb = g.nptr[x];
+                const int d = g.deg[x];
+                const int st = first_above(g.nbr, nb, d, v);
+                first = (uint32_t)(nb + st);
+                cnt = d - st;
+            }
+            const unsigned nz = __ballot_sync(kFull, cnt > 0);
+            int tot;
+            const int pre = excl_scan(cnt, lane, &tot);
+            if (cnt > 0) {
+                const int slot = (tail + __popc(nz & ((1u << lane) - 1u))) & RM;
+                const uint32_t sflat = T + (uint32_t)pre;
+                rS[slot] = sflat;
+                rO[slot] = first - sflat;
+                rE[slot] = ej;
+                rJ[slot] = (uint32_t)j;
+            }
+            // entries scanned over all lists: cnt for each list the row is in
+            unsigned long long w = (unsigned long long)cnt * (unsigned long long)max(0, min(j, r1) - r0);
+#pragma unroll
+            for (int d = 16; d; d >>= 1) w += __shfl_xor_sync(kFull, w, d);
+            sink.scanned += w;
+            tail += __popc(nz);
+            T += (uint32_t)tot;
+            jb += kWarp;
+        }
+        const uint32_t pend = T - F;
+        if (!pend) break;
+        __syncwarp();
+        // this lane's row in the window [F, F + 32)
+        uint32_t bit = 0;
+        {
+            const int r = cur + 1 + lane;
+            if (r < tail) {
+                const uint32_t sd = rS[r & RM] - F;
+                if (sd < 32u) bit = 1u << sd;
+            }
+        }
+        const uint32_t starts = __reduce_or_sync(kFull, bit);
+        const int row = (cur + __popc(starts & (0xFFFFFFFFu >> (31 - lane)))) & RM;
+        cur += __popc(starts);
+        const bool ok = (uint32_t)lane < pend;
+        const uint32_t er = rE[row];
+        const int jrow = ok ? (int)rJ[row] : r0;  // lists j2 < jrow take this entry
+        const uint32_t ue = ok ? __ldg(g.nbr + (rO[row] + F + (uint32_t)lane)) : 0u;
+        const uint32_t u = ue >> 2, su = ue & 3u, x = e_id(er);
+        const uint32_t s01u = ok ? pget<HASH>(row_v, u) | (pget<HASH>(row_w1, u) << 2) : 0u;
+        const uint32_t sv01x = er & 15u;
+        const int jmax = __reduce_max_sync(kFull, min(jrow, r1));
+        // lists taken U at a time: their probes and table reads are issued
+        // before any histogram add
+        constexpr int U = ACC_SHARED5_U;
+        for (int j0 = r0; j0 < jmax; j0 += U) {
+            int ca[U], cm[U];
+            bool add[U], adj[U];
+#pragma unroll
+            for (int i = 0; i < U; i++) {
+                const int j2 = j0 + i;
+                const bool act = j2 < jrow && j2 < jmax;
+                const uint32_t e2 = j2 < jmax ? E2[j2] : 0u;
+                const uint32_t w2 = e_id(e2);
+                const PRow row_w2 = prow<HASH>(g, w2);
+                const uint32_t sx = act ? pget<HASH>(row_w2, x) : 0u;
+                const uint32_t sw = act ? pget<HASH>(row_w2, u) : 0u;
+                const uint32_t cr = pc01 | ((e2 & 15u) << 14) | ((sv01x | (sx << 4)) << L::SH_ROW);
+                const uint32_t mu = s01u | (sw << 4);
+                const uint32_t s3[3] = {s01u & 3u, s01u >> 2, sw};
+                const uint32_t pm[3] = {v, w1, w2};
+                adj[i] = act && mu != 0u && u > x && in_list<5>(s3, u, pm, (e2 & 3u) != 0u);
+                add[i] = (act && mu == 0u) || adj[i];
+                ca[i] = sink.cls_of(cr | mu | (su << L::SH_PAIR));
+                cm[i] = sink.cls_of(cr | mu);
+            }
+#pragma unroll
+            for (int i = 0; i < U; i++)
+                if (add[i]) sink.add1(ca[i], 1);
+#pragma unroll
+            for (int i = 0; i < U; i++)
+                if (adj[i]) sink.add1(cm[i], -1);
+            sink.after_batch(2u * U * kWarp, lane);  // each lane moves at most two counters by one per list
+        }
+        F += pend < 32u ? pend : 32u;
     }
     __syncwarp();
 }
@@ -1085,12 +1213,17 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
             }
             __syncwarp();
             const uint32_t pm[3] = {(uint32_t)v, w1, w2};
+            // count mode: the group pairs of the whole list, the rows of its
+            // part B (the rows of part A follow for all lists at once)
             if (COUNT)
-                count_leaves<K, HASH>(g, sink, E3, pos, 0, pos, true, pm, pcode, (uint32_t)v, (e2 & 3u) != 0u, sc.gcnt,
-                                sc.ring, lane);
+                count_leaves<K, HASH>(g, sink, E3, pos, ACC_SHARED5 ? A3 : 0, pos, true, pm, pcode, (uint32_t)v,
+                                      (e2 & 3u) != 0u, sc.gcnt, sc.ring, lane);
             else leaves<K>(g, sink, E3, pos, 0, (pos + 1) / 2, pm, pcode, (uint32_t)v, lane);
             __syncwarp();
         }
+        if constexpr (K == 5 && COUNT && ACC_SHARED5)
+            if (r1 > r0)
+                count_shared_rows<HASH>(g, sink, E2, B2, r0, r1, pc01, row_v, row_w1, (uint32_t)v, w1, sc.ring, lane);
         if (rest >= B2) break;
     }
     sink.flush();
@@ -1150,7 +1283,7 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? (SET ?
     sc.ovf[1] = sc.ovf[0] + a.scratch_per_warp / 2;
     sc.cap = L::CAP;
     sc.gcnt = groups + (size_t)wib * 2 * L::G;
-    sc.ring = rings + (size_t)wib * 3 * L::RING;
+    sc.ring = rings + (size_t)wib * L::RING_ARRAYS * L::RING;
     sink.moved = 0;
     sink.scanned = 0;
     const long long nnz = a.info->nnz;
@@ -1310,7 +1443,7 @@ int bps_max() {
 }  // namespace
 
 long long enum_default_light() { return ACC_LIGHT; }
-long long enum_default_target() { return ACC_TARGET; }
+long long enum_default_target(int k, bool count_mode) { return k == 5 && count_mode ? ACC_TARGET5 : ACC_TARGET; }
 
 int enum_grid_warps(int k, int num_sms) {
     const int bps = k == 3 ? bps_max<3>() : (k == 4 ? bps_max<4>() : bps_max<5>());
