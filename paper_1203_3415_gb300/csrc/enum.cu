@@ -85,11 +85,8 @@ namespace {
 #ifndef ACC_RING5
 #define ACC_RING5 64  // the same for k = 5 (its block histogram leaves less shared memory)
 #endif
-#ifndef ACC_SHARED5
-#define ACC_SHARED5 1  // k = 5 count mode: scan the level-2 rows shared by the level-3 lists once
-#endif
-#ifndef ACC_SHARED5_U
-#define ACC_SHARED5_U 2  // lists taken at a time by that scan
+#ifndef ACC_SHARED_U
+#define ACC_SHARED_U 2  // lists taken at a time by the shared-row scan (k = 5 count mode)
 #endif
 #ifndef ACC_CAP5
 #define ACC_CAP5 64  // per-warp shared-memory list entries (each of two lists), k = 5
@@ -138,7 +135,7 @@ struct Layout {
     // only while the ring has room for it)
     static constexpr int WIN = K == 5 ? ACC_CWIN5 : ACC_CWIN;
     static constexpr int RING = K == 5 ? ACC_RING5 : ACC_RING;
-    // (k = 5: a fourth array, each row's position in the level-2 list)
+    // (k = 5: a fourth array, each row's position in its list)
     static constexpr int RING_ARRAYS = K == 5 ? 4 : 3;
     static constexpr size_t ring = size_t(kWarpsPerBlock) * RING * RING_ARRAYS * 4;
     static constexpr size_t total = lut + pending + hist + ebuf + groups + ring;
@@ -753,36 +750,48 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
     __syncwarp();
 }
 
-// k = 5, count mode: the rows that the level-3 lists of lists [r0, r1) of
-// one level-2 list E2 take over from E2.  The level-3 list of w2 = E2[j2]
-// starts with E2[j2+1 ..] (its part A), so row j of E2 (x = E2[j]) is a row
-// of every list j2 in [r0, min(j, r1)), with the same neighbour entries and
-// the same states to v and w1 each time.  Here each such row is scanned once:
-// rows j in (r0, B2) are staged into the ring as one flat sequence of
-// 32-entry windows (as in count_leaves, each row also recording j), a lane
-// takes one entry u of a window with its states to v and w1, and the warp
-// then walks the lists j2 (w2 = E2[j2], the same for every lane): a lane
-// whose row lies after j2 probes w2 against x and u and counts its leaf of
-// list j2 exactly as count_leaves would (an exclusive leaf, or the move of
-// an adjacent member pair).  The lists' group-pair counts and the rows of
-// their part B are left to count_leaves.
-template <bool HASH>
-__device__ __forceinline__ void count_shared_rows(const GView &g, Sink<5> &sink, const uint32_t *E2, int B2, int r0,
-                                                  int r1, uint32_t pc01, const PRow &row_v, const PRow &row_w1,
-                                                  uint32_t v, uint32_t w1, uint32_t *ring, int lane) {
-    using L = Layout<5>;
+// Count mode, k = 5: the last list level before the leaves.  EL (BL
+// members) is the extension list of a fixed prefix P0 of k-3 vertices
+// ({v, w1}: EL is the level-2 list of unit (v, w1)), entries (x << 6) |
+// states of x to P0.  Member
+// wl = EL[jl] extends P0 to the prefix P0 + {wl} of the two leaf levels,
+// whose list EN(jl) is EL after jl (part A, with each member's state to wl
+// added) followed by the neighbours of wl above v adjacent to no vertex of P0
+// (part B).  Rows [r0, r1) of EL are taken here.
+//
+// Row j of EL (x = EL[j]) is a part-A row of every list EN(jl), jl in
+// [r0, min(j, r1)), with the same neighbour entries and the same states to P0
+// each time.  So each list EN(jl) is built, its group pairs counted and its
+// part-B rows scanned by count_leaves, and then the shared rows are scanned
+// once for all the lists: rows j in (r0, BL) are staged into the ring as one
+// flat sequence of 32-entry windows (as in count_leaves, each row also
+// recording j), a lane takes one entry u of a window with its states to P0,
+// and the warp then walks the lists jl (wl the same for every lane): a lane
+// whose row lies after jl probes wl against x and u and counts its leaf of
+// list EN(jl) exactly as count_leaves would (an exclusive leaf, or the move
+// of an adjacent member pair).  (For k = 4 the same sharing would need units
+// of whole roots, whose level-2 lists could then no longer be split across
+// warps; measured slower there, so k = 4 keeps one list per unit.)
+template <int K, bool HASH>
+__device__ __forceinline__ void count_shared_rows(const GView &g, Sink<K> &sink, const uint32_t *EL, int BL, int r0,
+                                                  int r1, uint32_t pc0, const uint32_t *p0, const PRow *rows0,
+                                                  uint32_t *ring, int lane) {
+    using L = Layout<K>;
     constexpr int RM = L::RING - 1;
+    constexpr int SB = 2 * (K - 3);         // bits of the states to P0
+    constexpr int SHL = L::SH_ROW + 2 * (K - 2);  // field of slot k-3 (wl's states to P0)
+    const uint32_t v = p0[0];
     uint32_t *rS = ring, *rO = ring + L::RING, *rE = ring + 2 * L::RING, *rJ = ring + 3 * L::RING;
     uint32_t T = 0, F = 0;   // flat entries staged, consumed
     int tail = 0, cur = -1;  // ring rows staged; last ring row starting before F
     int jb = r0 + 1;
     for (;;) {
-        while (jb < B2 && T - F < 32u && tail - cur + kWarp <= L::RING) {
+        while (jb < BL && T - F < 32u && tail - cur + kWarp <= L::RING) {
             const int j = jb + lane;
             uint32_t ej = 0, first = 0;
             int cnt = 0;
-            if (j < B2) {
-                ej = E2[j];
+            if (j < BL) {
+                ej = EL[j];
                 const uint32_t x = e_id(ej);
                 const long long nb = g.nptr[x];
                 const int d = g.deg[x];
@@ -827,32 +836,40 @@ __device__ __forceinline__ void count_shared_rows(const GView &g, Sink<5> &sink,
         cur += __popc(starts);
         const bool ok = (uint32_t)lane < pend;
         const uint32_t er = rE[row];
-        const int jrow = ok ? (int)rJ[row] : r0;  // lists j2 < jrow take this entry
+        const int jrow = ok ? (int)rJ[row] : r0;  // lists jl < jrow take this entry
         const uint32_t ue = ok ? __ldg(g.nbr + (rO[row] + F + (uint32_t)lane)) : 0u;
         const uint32_t u = ue >> 2, su = ue & 3u, x = e_id(er);
-        const uint32_t s01u = ok ? pget<HASH>(row_v, u) | (pget<HASH>(row_w1, u) << 2) : 0u;
-        const uint32_t sv01x = er & 15u;
+        uint32_t s0u = 0;  // u's states to P0
+#pragma unroll
+        for (int k2 = 0; k2 < K - 3; k2++) s0u |= (ok ? pget<HASH>(rows0[k2], u) : 0u) << (2 * k2);
+        const uint32_t s0x = er & ((1u << SB) - 1u);
         const int jmax = __reduce_max_sync(kFull, min(jrow, r1));
         // lists taken U at a time: their probes and table reads are issued
         // before any histogram add
-        constexpr int U = ACC_SHARED5_U;
+        constexpr int U = ACC_SHARED_U;
         for (int j0 = r0; j0 < jmax; j0 += U) {
             int ca[U], cm[U];
             bool add[U], adj[U];
 #pragma unroll
             for (int i = 0; i < U; i++) {
-                const int j2 = j0 + i;
-                const bool act = j2 < jrow && j2 < jmax;
-                const uint32_t e2 = j2 < jmax ? E2[j2] : 0u;
-                const uint32_t w2 = e_id(e2);
-                const PRow row_w2 = prow<HASH>(g, w2);
-                const uint32_t sx = act ? pget<HASH>(row_w2, x) : 0u;
-                const uint32_t sw = act ? pget<HASH>(row_w2, u) : 0u;
-                const uint32_t cr = pc01 | ((e2 & 15u) << 14) | ((sv01x | (sx << 4)) << L::SH_ROW);
-                const uint32_t mu = s01u | (sw << 4);
-                const uint32_t s3[3] = {s01u & 3u, s01u >> 2, sw};
-                const uint32_t pm[3] = {v, w1, w2};
-                adj[i] = act && mu != 0u && u > x && in_list<5>(s3, u, pm, (e2 & 3u) != 0u);
+                const int jl = j0 + i;
+                const bool act = jl < jrow && jl < jmax;
+                const uint32_t el = jl < jmax ? EL[jl] : 0u;
+                const uint32_t wl = e_id(el);
+                const PRow row_l = prow<HASH>(g, wl);
+                const uint32_t sx = act ? pget<HASH>(row_l, x) : 0u;
+                const uint32_t sw = act ? pget<HASH>(row_l, u) : 0u;
+                const uint32_t cr = pc0 | ((el & ((1u << SB) - 1u)) << SHL) | ((s0x | (sx << SB)) << L::SH_ROW);
+                const uint32_t mu = s0u | (sw << SB);
+                uint32_t s[K - 2], pm[K - 2];
+#pragma unroll
+                for (int k2 = 0; k2 < K - 3; k2++) {
+                    s[k2] = (s0u >> (2 * k2)) & 3u;
+                    pm[k2] = p0[k2];
+                }
+                s[K - 3] = sw;
+                pm[K - 3] = wl;
+                adj[i] = act && mu != 0u && u > x && in_list<K>(s, u, pm, (el & 3u) != 0u);
                 add[i] = (act && mu == 0u) || adj[i];
                 ca[i] = sink.cls_of(cr | mu | (su << L::SH_PAIR));
                 cm[i] = sink.cls_of(cr | mu);
@@ -868,6 +885,65 @@ __device__ __forceinline__ void count_shared_rows(const GView &g, Sink<5> &sink,
         F += pend < 32u ? pend : 32u;
     }
     __syncwarp();
+}
+
+// Count mode, k = 5: rows [r0, r1) of the last list level EL (see
+// count_shared_rows): each member's leaf list built, its group pairs and
+// part-B rows counted by count_leaves, then the shared part-A rows.
+template <int K, bool HASH>
+__device__ __forceinline__ void count_last_lists(const GView &g, Sink<K> &sink, const Scratch &sc, const uint32_t *EL,
+                                                 int BL, int r0, int r1, uint32_t pc0, const uint32_t *p0,
+                                                 const PRow *rows0, int lane) {
+    using L = Layout<K>;
+    constexpr int SB = 2 * (K - 3);
+    constexpr int SHL = L::SH_ROW + 2 * (K - 2);
+    const uint32_t v = p0[0];
+    for (int jl = r0; jl < r1; jl++) {
+        const uint32_t el = EL[jl];
+        const uint32_t wl = e_id(el);
+        const uint32_t pcode = pc0 | ((el & ((1u << SB) - 1u)) << SHL);
+        const int A = BL - 1 - jl;
+        const int dw = g.deg[wl];
+        const long long ub = (long long)A + dw;
+        // (EL sits in buf[0] or ovf[0])
+        uint32_t *EN = ub <= sc.cap ? sc.buf[1] : sc.ovf[1];
+        // the list: EL after wl (with wl's states), then the neighbours of
+        // wl above v adjacent to no vertex of P0, both read in one pass (the
+        // neighbours at or below v skipped by their ids)
+        const PRow row_l = prow<HASH>(g, wl);
+        const long long wb = g.nptr[wl];
+        const int nq = max(A, dw);
+        int pos = A;
+        for (int q0 = 0; q0 < nq; q0 += kWarp) {
+            const int q = q0 + lane;
+            const bool in_a = q < A;
+            uint32_t xe = 0, ue = 0;
+            if (in_a) xe = EL[jl + 1 + q];
+            if (q < dw) ue = __ldg(g.nbr + wb + q);
+            const uint32_t x = e_id(xe), u = ue >> 2;
+            uint32_t sa = 0;
+            bool keep = false;
+            if (in_a) sa = pget<HASH>(row_l, x);
+            if (q < dw && u > v) {
+                keep = true;
+#pragma unroll
+                for (int k2 = 0; k2 < K - 3; k2++) keep = keep && pget<HASH>(rows0[k2], u) == 0u;
+            }
+            if (in_a) EN[q] = (x << 6) | (xe & ((1u << SB) - 1u)) | (sa << SB);
+            const unsigned ball = __ballot_sync(kFull, keep);
+            if (keep) EN[pos + __popc(ball & ((1u << lane) - 1u))] = (u << 6) | ((ue & 3u) << SB);
+            pos += __popc(ball);
+        }
+        __syncwarp();
+        uint32_t pm[K - 2];
+#pragma unroll
+        for (int k2 = 0; k2 < K - 3; k2++) pm[k2] = p0[k2];
+        pm[K - 3] = wl;
+        // the group pairs of the whole list, the rows of its part B
+        count_leaves<K, HASH>(g, sink, EN, pos, A, pos, true, pm, pcode, v, (el & 3u) != 0u, sc.gcnt, sc.ring, lane);
+        __syncwarp();
+    }
+    count_shared_rows<K, HASH>(g, sink, EL, BL, r0, r1, pc0, p0, rows0, sc.ring, lane);
 }
 
 // Level-2 extension list of unit (v, w1), w1 at position p of N*(v): part A
@@ -1176,6 +1252,14 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
     // to v and w1)
     const uint32_t pc01 = s01 << 18;
     const PRow row_v = prow<HASH>(g, (uint32_t)v), row_w1 = prow<HASH>(g, w1);
+    if constexpr (K == 5 && COUNT) {
+        const uint32_t p0[2] = {(uint32_t)v, w1};
+        const PRow rows0[2] = {row_v, row_w1};
+        if (hi > jlo) count_last_lists<K, HASH>(g, sink, sc, E2, B2, jlo, hi, pc01, p0, rows0, lane);
+        if (rest < B2) count_last_lists<K, HASH>(g, sink, sc, E2, B2, rest, B2, pc01, p0, rows0, lane);
+        __syncwarp();
+        return;
+    }
     for (int pass = 0; pass < 2; pass++) {
         const int r0 = pass == 0 ? jlo : rest;
         const int r1 = pass == 0 ? hi : B2;
@@ -1213,17 +1297,9 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
             }
             __syncwarp();
             const uint32_t pm[3] = {(uint32_t)v, w1, w2};
-            // count mode: the group pairs of the whole list, the rows of its
-            // part B (the rows of part A follow for all lists at once)
-            if (COUNT)
-                count_leaves<K, HASH>(g, sink, E3, pos, ACC_SHARED5 ? A3 : 0, pos, true, pm, pcode, (uint32_t)v,
-                                      (e2 & 3u) != 0u, sc.gcnt, sc.ring, lane);
-            else leaves<K>(g, sink, E3, pos, 0, (pos + 1) / 2, pm, pcode, (uint32_t)v, lane);
+            leaves<K>(g, sink, E3, pos, 0, (pos + 1) / 2, pm, pcode, (uint32_t)v, lane);
             __syncwarp();
         }
-        if constexpr (K == 5 && COUNT && ACC_SHARED5)
-            if (r1 > r0)
-                count_shared_rows<HASH>(g, sink, E2, B2, r0, r1, pc01, row_v, row_w1, (uint32_t)v, w1, sc.ring, lane);
         if (rest >= B2) break;
     }
     sink.flush();
@@ -1292,21 +1368,23 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? (SET ?
     const long long wmax = (long long)a.info->maxdeg + kRowCost;  // largest work of one list row
 
     if constexpr (PHASE == 1) {
-        const long long nunits = K == 3 ? NV : nnz;
-        const int grab = a.gs.B > 1 ? ACC_GRAB_SET : (K == 4 ? ACC_GRAB4 : kGrab);
+        // units: roots (k = 3) or G* arc positions (v, w1) with w1 > v
+        constexpr bool ROOTS = K == 3;
+        const long long nunits = ROOTS ? NV : nnz;
+        const int grab = a.gs.B > 1 ? ACC_GRAB_SET : (K == 4 && !ROOTS ? ACC_GRAB4 : kGrab);
         for (;;) {
             unsigned long long u0 = 0;
             if (lane == 0) u0 = atomicAdd(&a.info->unit_ctr, (unsigned long long)grab);
             u0 = __shfl_sync(kFull, u0, 0);
             if ((long long)u0 >= nunits) break;
             const long long u1 = min((long long)u0 + grab, nunits);
-            // k = 4, 5: each grabbed position's row vertex (bit 31: a
+            // arc units: each grabbed position's row vertex (bit 31: a
             // neighbour below the row's vertex, not a unit), one per lane
             uint32_t rows = 0;
-            if (K != 3 && u0 + lane < (unsigned long long)u1) rows = __ldg(a.src + u0 + lane);
+            if (!ROOTS && u0 + lane < (unsigned long long)u1) rows = __ldg(a.src + u0 + lane);
             for (long long u = (long long)u0; u < u1; u++) {
                 int vg;
-                if (K == 3) {
+                if (ROOTS) {
                     vg = (int)u;
                 } else {
                     const uint32_t r = __shfl_sync(kFull, rows, (int)(u - (long long)u0));
