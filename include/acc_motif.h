@@ -295,8 +295,9 @@ ACC_API int acc_ctx_set_randomise_memory(acc_ctx *ctx, int64_t bytes);
  * policy (acc_server_set_policy; a request that cannot fit even with every
  * slot idle fails with ACC_ERR_NOMEM).  Each slot has its own
  * context and CUDA stream, so admitted requests overlap on the device; a
- * request's enumeration grid is capped (1/8 of the GPU for graphs of at most
- * 4096 vertices, 5/8 above) so that one large request cannot hold every SM.
+ * request on a graph of at most 4096 vertices takes 1/8 of the GPU's
+ * enumeration grid (its few work units cannot fill more) and so runs beside
+ * the others, a larger one takes the whole grid.
  * Results are the same as acc_motif_count's for the same graph and k.  The
  * server does its host work only inside these calls (no threads), so call
  * acc_server_progress or acc_server_poll regularly.  A server is not

@@ -6,10 +6,13 @@
 // GPU start without waiting for a batch boundary and overlap on the device.
 // Each slot owns a context (workspace) and a CUDA stream; completion is
 // detected with CUDA events, results are copied to pinned host memory in
-// stream order.  The enumeration grid of a request is capped (a small graph
-// takes 1/8 of the GPU's persistent grid, a large one 5/8) so that one large
-// request cannot lock every SM while small requests wait.  Admission takes
-// the queued request with the smallest aged work estimate (or FIFO order).
+// stream order.  A small graph (at most 4096 vertices) takes 1/8 of the GPU's
+// persistent enumeration grid, which its few units cannot fill anyway, so
+// that it runs beside a large request instead of behind it; a large graph
+// takes the whole grid (capping it at 5/8 to make room for small requests
+// measured slower in throughput and in tail latency at saturation).
+// Admission takes the queued request with the smallest aged work estimate (or
+// FIFO order).
 // Host work happens only inside the caller's calls (no threads).
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -24,6 +27,7 @@
 namespace {
 
 constexpr int kSmallGraph = 4096;  // vertices; smaller graphs get the small grid share
+constexpr int kSmallShare = 1, kBigShare = 8;  // eighths of the persistent grid a request takes
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -181,7 +185,7 @@ int progress(acc_server *sv) {
         }
         Slot &sl = sv->slots[(size_t)best];
         sl.footprint = best_fp;
-        sl.ctx->grid_num = g.n <= kSmallGraph ? 1 : 5;
+        sl.ctx->grid_num = g.n <= kSmallGraph ? kSmallShare : kBigShare;
         sl.ctx->grid_den = 8;
         r.t_start = now_s();
         const int rc = acc_motif_count(sl.ctx, g.rowptr, g.col, g.n, g.m, r.k, sl.s, sl.d_counts, sl.d_status);
