@@ -441,10 +441,11 @@ ACC_API int acc_ctx_set_adjacency(acc_ctx *ctx, int adjacency);
  * cut into row tiles of about `target` work that any warp may take.  Work is
  * counted in scanned neighbour entries (count mode) or leaves (enumerate
  * mode).  0 selects the built-in default: light 2048 and target 4096, except
- * target 16384 for k = 5 in the count mode (whose tiles share one scan of the
- * level-2 rows, so longer tiles save work).  Values above 2^40 or negative
- * are ACC_ERR_ARG.  The schedule changes speed only, never the counts.
- * acc_ctx_get_schedule reports the values in effect for k = 3 and 4.
+ * in the count mode light 6144 for k = 4 and target 16384 for k = 5 (whose
+ * tiles share one scan of the level-2 rows, so longer tiles save work).
+ * Values above 2^40 or negative are ACC_ERR_ARG.  The schedule changes speed
+ * only, never the counts.  acc_ctx_get_schedule reports the values in effect
+ * for k = 3.
  */
 ACC_API int acc_ctx_set_schedule(acc_ctx *ctx, int64_t light, int64_t target);
 ACC_API int acc_ctx_get_schedule(acc_ctx *ctx, int64_t *light, int64_t *target);

@@ -325,7 +325,7 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     a.scratch = c->scratch;
     a.scratch_per_warp = spw;
     a.mode = c->mode == ACC_MODE_ENUMERATE ? 1 : 0;
-    a.light = c->sched_light > 0 ? c->sched_light : enum_default_light();
+    a.light = c->sched_light > 0 ? c->sched_light : enum_default_light(k, a.mode == 0);
     a.target = c->sched_target > 0 ? c->sched_target : enum_default_target(k, a.mode == 0);
     a.counts = reinterpret_cast<unsigned long long *>(counts);
     a.status = status;
@@ -884,8 +884,8 @@ int acc_ctx_set_schedule(acc_ctx *c, int64_t light, int64_t target) {
 
 int acc_ctx_get_schedule(acc_ctx *c, int64_t *light, int64_t *target) {
     if (!c || !light || !target) return ACC_ERR_ARG;
-    *light = c->sched_light > 0 ? c->sched_light : enum_default_light();
-    *target = c->sched_target > 0 ? c->sched_target : enum_default_target(4, true);
+    *light = c->sched_light > 0 ? c->sched_light : enum_default_light(3, true);
+    *target = c->sched_target > 0 ? c->sched_target : enum_default_target(3, true);
     return ACC_OK;
 }
 
@@ -905,7 +905,7 @@ int acc_motif_batch_autotune(acc_ctx *c, void *stream, int64_t *h_light, int64_t
     long long best_l = 0, best_t = 0;
     float best = -1.0f;
     if (B == 0) {
-        best_l = enum_default_light();
+        best_l = enum_default_light(c->batch_k, c->mode != ACC_MODE_ENUMERATE);
         best_t = enum_default_target(c->batch_k, c->mode != ACC_MODE_ENUMERATE);
         best = 0.0f;
         goto done;

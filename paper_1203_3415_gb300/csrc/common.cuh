@@ -271,7 +271,7 @@ int launch_zscores(const long long *counts, int groups, int group_size, int K, d
 int launch_enumerate(int k, const EnumArgs &a, int num_sms, int phase, cudaStream_t s, int grid_num = 1,
                      int grid_den = 1);
 // Default schedule of the enumeration kernels (see EnumArgs::light, target).
-long long enum_default_light();
+long long enum_default_light(int k, bool count_mode);
 long long enum_default_target(int k, bool count_mode);
 int enum_grid_warps(int k, int num_sms);
 

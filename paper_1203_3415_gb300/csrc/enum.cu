@@ -64,6 +64,9 @@ namespace {
 #ifndef ACC_LIGHT
 #define ACC_LIGHT (1 << 11)
 #endif
+#ifndef ACC_LIGHT4
+#define ACC_LIGHT4 6144  // k = 4 count mode (tuned on the Chung-Lu k = 4 workload)
+#endif
 #ifndef ACC_TARGET
 #define ACC_TARGET (1 << 12)
 #endif
@@ -1520,7 +1523,7 @@ int bps_max() {
 
 }  // namespace
 
-long long enum_default_light() { return ACC_LIGHT; }
+long long enum_default_light(int k, bool count_mode) { return k == 4 && count_mode ? ACC_LIGHT4 : ACC_LIGHT; }
 long long enum_default_target(int k, bool count_mode) { return k == 5 && count_mode ? ACC_TARGET5 : ACC_TARGET; }
 
 int enum_grid_warps(int k, int num_sms) {
