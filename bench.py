@@ -341,7 +341,7 @@ def table_build_ms(env, k, stream):
     return statistics.median(times)
 
 
-def measure_single(env, workload, steps, warmup, mode="count", schedule="", cpu_baseline=True):
+def measure_single(env, workload, steps, warmup, mode="count", schedule="", cpu_baseline=True, adjacency="auto"):
     """One graph counted per step through acc_motif_count, inputs resident in
     HBM, L2 flushed between steps; then the same through the host-buffer
     entry point.  Returns the bench line (without the run-wide keys)."""
@@ -357,6 +357,8 @@ def measure_single(env, workload, steps, warmup, mode="count", schedule="", cpu_
     counter.set_mode({"count": acc.ACC_MODE_COUNT, "enumerate": acc.ACC_MODE_ENUMERATE,
                       "formula": acc.ACC_MODE_FORMULA}[mode])
     counter.prepare(k)
+    counter.set_adjacency({"auto": acc.ACC_ADJ_AUTO, "dense": acc.ACC_ADJ_DENSE, "hash": acc.ACC_ADJ_HASH,
+                           "sparse": acc.ACC_ADJ_SPARSE}[adjacency])
     if schedule:
         light, target = (int(x) for x in schedule.split(","))
         counter.set_schedule(light, target)
@@ -458,7 +460,8 @@ def measure_single(env, workload, steps, warmup, mode="count", schedule="", cpu_
         units, per_unit = n_k, ops_per_subgraph(k)
         unit_name = "classified subgraphs"
     achieved = per_unit * units / enum_s / 1e9
-    traffic, counters = profiled_counters(workload, mode)
+    # the profiles were taken with the default probe structure
+    traffic, counters = profiled_counters(workload, mode) if adjacency == "auto" else (None, None)
 
     # CPU baseline: the oracle on this host's cores, the whole workload
     cpu = None
@@ -471,7 +474,7 @@ def measure_single(env, workload, steps, warmup, mode="count", schedule="", cpu_
         "value": value, "unit": UNIT, "steps": steps, "warmup": warmup,
         "ms_per_step": 1000.0 * max_s / steps,
         "config": {"workload": workload, "k": k, "n": g.n, "m": g.m, "subgraphs_per_step": n_k,
-                   "mode": mode,
+                   "mode": mode, "adjacency": adjacency,
                    "l2": "flushed between timed steps (256 MiB device write)",
                    "parallelism": f"replicas{env.world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
@@ -514,7 +517,7 @@ def bench_line(env, rec, steps, warmup):
 def run_ours(args):
     env = GpuEnv()
     rec = measure_single(env, args.workload, args.steps, args.warmup, args.mode, args.schedule,
-                         not args.no_cpu_baseline)
+                         not args.no_cpu_baseline, adjacency=args.adjacency)
     subs = None
     if args.workload == DEFAULT_WORKLOAD and not args.headline_only:
         # every other workload of the benchmark set, each under its own
@@ -1044,6 +1047,9 @@ def main():
     ap.add_argument("--serve-policy", choices=["shortest", "fifo"], default="shortest",
                     help="serving admission order: smallest aged work estimate first, or submission order")
     ap.add_argument("--serve-aging-s", type=float, default=1.0)
+    ap.add_argument("--adjacency", choices=["auto", "dense", "hash", "sparse"], default="auto",
+                    help="count mode: pair-state probes on the dense block, hashed tables, or hashed tables over "
+                         "lists built without the block (same counts)")
     ap.add_argument("--schedule", default="",
                     help="enumeration schedule LIGHT,TARGET for the single-graph workloads (default: the kernels')")
     ap.add_argument("--rand-mode", choices=["swap", "mutual"], default="swap",
