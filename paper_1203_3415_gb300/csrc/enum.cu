@@ -850,14 +850,19 @@ __device__ __forceinline__ void count_shared_rows(const GView &g, Sink<K> &sink,
         // lists taken U at a time: their probes and table reads are issued
         // before any histogram add
         constexpr int U = ACC_SHARED_U;
+        static_assert(kWarp % U == 0, "lists per step divide the warp");
+        // the lists' entries, 32 at a time, one per lane, handed out by
+        // shuffles (no dependent load of EL on each list's path)
+        uint32_t elv = 0;
         for (int j0 = r0; j0 < jmax; j0 += U) {
+            if (((j0 - r0) & (kWarp - 1)) == 0) elv = j0 + lane < jmax ? EL[j0 + lane] : 0u;
             int ca[U], cm[U];
             bool add[U], adj[U];
 #pragma unroll
             for (int i = 0; i < U; i++) {
                 const int jl = j0 + i;
                 const bool act = jl < jrow && jl < jmax;
-                const uint32_t el = jl < jmax ? EL[jl] : 0u;
+                const uint32_t el = __shfl_sync(kFull, elv, (jl - r0) & (kWarp - 1));
                 const uint32_t wl = e_id(el);
                 const PRow row_l = prow<HASH>(g, wl);
                 const uint32_t sx = act ? pget<HASH>(row_l, x) : 0u;
