@@ -156,7 +156,9 @@ void release_luts(acc_ctx *c) {
     }
 }
 
-long long scratch_per_warp(int max_n) { return 2 * (((long long)max_n + 32 + 31) & ~31LL); }
+// per warp: two overflow lists of up to max_n entries, then the k = 5 count
+// mode's collected part-B rows
+long long scratch_per_warp(int max_n) { return 2 * (((long long)max_n + 32 + 31) & ~31LL) + 2 * kPartBRows; }
 
 // The count mode builds the lists without the dense block (and probes
 // hashed tables) above the dense block's limit, or when asked to.
@@ -294,7 +296,7 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
         if (!ok(cudaMemcpyAsync(c->maxdeg_host, &c->info->maxdeg, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
             !ok(cudaStreamSynchronize(s)))
             return ACC_ERR_CUDA;
-        spw = 2 * sparse_list_entries(*c->maxdeg_host);
+        spw = 2 * sparse_list_entries(*c->maxdeg_host) + 2 * kPartBRows;
         const int warps = enum_grid_warps(k, c->num_sms);
         if (warps < 0) return warps;
         if ((rc = grow(&c->scratch, &c->scratch_cap, (size_t)spw * (size_t)warps))) return rc;
@@ -485,7 +487,7 @@ long long ctx_footprint(const acc_ctx *c, long long n, long long m, int k) {
     const long long list_n = sparse ? (2 * m < n ? 2 * m : n) : n;
     const long long bytes = (sparse ? 16 * (m + 1) + 8 * (n + 1) : n * pitch * 4 + 4 * n * occ_words((int)n)) +
                             5 * 4 * (n + 1) + 8 * (n + 1) + 8 * (2 * m + 1) + hash_bytes + (long long)kQueueCap * 16 +
-                            (sparse ? 2 * sparse_list_entries((int)list_n) : scratch_per_warp((int)n)) *
+                            (sparse ? 2 * sparse_list_entries((int)list_n) + 2 * kPartBRows : scratch_per_warp((int)n)) *
                                 (warps > 0 ? warps : 0) * 4;
     return bytes + bytes / 4;
 }

@@ -34,6 +34,12 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // Block shape of the enumeration kernels.
 constexpr int kWarpsPerBlock = 8;
+#ifndef ACC_PARTB_ROWS
+#define ACC_PARTB_ROWS 1024
+#endif
+// k = 5 count mode: part-B rows of a tile's level-3 lists a warp collects (two
+// words each, at the end of its scratch) before scanning them in one pass
+constexpr int kPartBRows = ACC_PARTB_ROWS;
 constexpr int kThreads = kWarpsPerBlock * kWarp;
 
 // Per-call scalars the builder leaves on the device.

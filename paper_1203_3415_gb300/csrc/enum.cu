@@ -88,6 +88,9 @@ namespace {
 #ifndef ACC_RING5
 #define ACC_RING5 64  // the same for k = 5 (its block histogram leaves less shared memory)
 #endif
+#ifndef ACC_COLLECT_B
+#define ACC_COLLECT_B 1  // k = 5 count mode: scan the part-B rows of a tile's lists together
+#endif
 #ifndef ACC_SHARED_U
 #define ACC_SHARED_U 2  // lists taken at a time by the shared-row scan (k = 5 count mode)
 #endif
@@ -428,6 +431,7 @@ struct Scratch {
     int cap;
     uint32_t *gcnt;    // count mode: group sizes and the non-empty group list
     uint32_t *ring;    // count mode: staged rows (flat start, entry offset, list entry[, list position]), RING each
+    uint32_t *pb;      // k = 5 count mode: collected part-B rows (entries, then their lists' entries), global
 };
 
 // The last two ESU levels over extension list E[0..B), virtual rows
@@ -563,15 +567,13 @@ __device__ __forceinline__ bool in_list(const uint32_t *s, uint32_t u, const uin
 // Adjacent pairs are then moved to their own classes one by one, found in
 // the neighbour lists of the list members (the paper's m / m' corrections),
 // and the same scan yields the exclusive leaves P + {x, u}.  `bulk` (set for
-// exactly one chunk of a list) adds the group-pair counts.  w2_in_a (k = 5)
-// says whether w2 lies in part A of the level-2 list.
-template <int K, bool HASH>
-__device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, const uint32_t *E, int B, int jlo,
-                                             int jend, bool bulk, const uint32_t *pm, uint32_t pcode,
-                                             uint32_t root, bool w2_in_a, uint32_t *gcnt, uint32_t *ring,
-                                             int lane) {
+// exactly one chunk of a list) adds the group-pair counts (count_group_pairs).
+// w2_in_a (k = 5) says whether w2 lies in part A of the level-2 list.
+template <int K>
+__device__ __forceinline__ void count_group_pairs(Sink<K> &sink, const uint32_t *E, int B, uint32_t pcode,
+                                                  uint32_t *gcnt, int lane) {
     using L = Layout<K>;
-    if (bulk) {
+    {
         uint32_t *glist = gcnt + L::G;  // (count << 6) | group of each non-empty group (a list has < 2^26 members)
         for (int i = lane; i < L::G; i += kWarp) gcnt[i] = 0;
         __syncwarp();
@@ -605,6 +607,15 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
         }
         account_moved(sink, lane);
     }
+}
+
+template <int K, bool HASH>
+__device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, const uint32_t *E, int B, int jlo,
+                                             int jend, bool bulk, const uint32_t *pm, uint32_t pcode,
+                                             uint32_t root, bool w2_in_a, uint32_t *gcnt, uint32_t *ring,
+                                             int lane) {
+    using L = Layout<K>;
+    if (bulk) count_group_pairs<K>(sink, E, B, pcode, gcnt, lane);
     // neighbour scan of rows [jlo, jend): adjacent member pairs (each once,
     // from its smaller vertex) and exclusive neighbours.  The rows' entries
     // above the root form one flat sequence, cut into 32-entry windows with
@@ -895,6 +906,129 @@ __device__ __forceinline__ void count_shared_rows(const GView &g, Sink<K> &sink,
     __syncwarp();
 }
 
+// Count mode, k = 5: the part-B rows that count_last_lists collected from
+// several level-3 lists (pbE: the list entry of row i, (x << 6) | x's states
+// to v, w1 and its list's w2; pbL: the entry EL[jl] of that list's w2), in
+// one flat scan as count_leaves does for one list, with each row's own w2:
+// a lane takes its row's w2 from the ring and probes it beside v and w1.
+template <bool HASH>
+__device__ __forceinline__ void count_partb_rows(const GView &g, Sink<5> &sink, const uint32_t *pbE,
+                                                 const uint32_t *pbL, int nrows, uint32_t pc0, const uint32_t *p0,
+                                                 const PRow *rows0, uint32_t *ring, int lane) {
+    using L = Layout<5>;
+    constexpr int W = L::WIN;
+    constexpr int RM = L::RING - 1;
+    const uint32_t v = p0[0];
+    uint32_t *rS = ring, *rO = ring + L::RING, *rE = ring + 2 * L::RING, *rL = ring + 3 * L::RING;
+    uint32_t T = 0, F = 0;   // flat entries staged, consumed
+    int tail = 0, cur = -1;  // ring rows staged; last ring row starting before F
+    int jb = 0;
+    auto stage = [&]() {
+        while (jb < nrows && T - F < 32u * W && tail - cur + kWarp <= L::RING) {
+            const int j = jb + lane;
+            uint32_t ej = 0, el = 0, first = 0;
+            int cnt = 0;
+            if (j < nrows) {
+                ej = pbE[j];
+                el = pbL[j];
+                const uint32_t x = e_id(ej);
+                const long long nb = g.nptr[x];
+                const int d = g.deg[x];
+                const int st = first_above(g.nbr, nb, d, v);
+                first = (uint32_t)(nb + st);
+                cnt = d - st;
+            }
+            const unsigned nz = __ballot_sync(kFull, cnt > 0);
+            int tot;
+            const int pre = excl_scan(cnt, lane, &tot);
+            if (cnt > 0) {
+                const int slot = (tail + __popc(nz & ((1u << lane) - 1u))) & RM;
+                const uint32_t sflat = T + (uint32_t)pre;
+                rS[slot] = sflat;
+                rO[slot] = first - sflat;
+                rE[slot] = ej;
+                rL[slot] = el;
+            }
+            tail += __popc(nz);
+            T += (uint32_t)tot;
+            sink.scanned += (unsigned long long)tot;
+            jb += kWarp;
+        }
+    };
+    auto locate = [&](int w) -> int {
+        const uint32_t t0 = F + 32u * w;
+        uint32_t bit = 0;
+        const int r = cur + 1 + lane;
+        if (r < tail) {
+            const uint32_t sd = rS[r & RM] - t0;
+            if (sd < 32u) bit = 1u << sd;
+        }
+        const uint32_t starts = __reduce_or_sync(kFull, bit);
+        const int row = cur + __popc(starts & (0xFFFFFFFFu >> (31 - lane)));
+        cur += __popc(starts);
+        return row & RM;
+    };
+    auto step = [&](auto nw, auto full) {
+        constexpr int NW = decltype(nw)::value;
+        constexpr bool FULL = decltype(full)::value;
+        const uint32_t pend = T - F;
+        uint32_t ue[NW], er[NW], el[NW];
+        bool ok[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+            const int row = locate(w);
+            ok[w] = FULL || 32u * w + lane < pend;
+            er[w] = rE[row];
+            el[w] = rL[row];
+            const uint32_t off = rO[row];
+            ue[w] = ok[w] ? __ldg(g.nbr + (off + F + 32u * w + lane)) : 0u;
+        }
+        uint32_t sv[NW][3];
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+            const uint32_t u = ue[w] >> 2;
+            const PRow row_l = prow<HASH>(g, e_id(el[w]));
+            sv[w][0] = ok[w] ? pget<HASH>(rows0[0], u) : 0u;
+            sv[w][1] = ok[w] ? pget<HASH>(rows0[1], u) : 0u;
+            sv[w][2] = ok[w] ? pget<HASH>(row_l, u) : 0u;
+        }
+        int add_cls[NW];
+        bool add[NW], adj[NW];
+        uint32_t base[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+            const uint32_t u = ue[w] >> 2, su = ue[w] & 3u;
+            const uint32_t cr = pc0 | ((el[w] & 15u) << 14) | (e_sv(er[w]) << L::SH_ROW);
+            const uint32_t mu = sv[w][0] | (sv[w][1] << 2) | (sv[w][2] << 4);
+            const uint32_t pm[3] = {v, p0[1], e_id(el[w])};
+            adj[w] = ok[w] && mu != 0u && u > e_id(er[w]) && in_list<5>(sv[w], u, pm, (el[w] & 3u) != 0u);
+            add[w] = (ok[w] && mu == 0u) || adj[w];
+            base[w] = cr | mu;
+            add_cls[w] = sink.cls_of(base[w] | (su << L::SH_PAIR));
+        }
+#pragma unroll
+        for (int w = 0; w < NW; w++)
+            if (add[w]) sink.add1(add_cls[w], 1);
+#pragma unroll
+        for (int w = 0; w < NW; w++)
+            if (adj[w]) sink.add1(sink.cls_of(base[w]), -1);
+        const uint32_t used = FULL || pend >= 32u * NW ? 32u * NW : pend;
+        F += used;
+        sink.after_batch(2u * used, lane);  // each entry moves at most two counters by one
+    };
+    static_assert(W >= 1 && W <= 2, "windows per step of the part-B scan");
+    for (;;) {
+        stage();
+        const uint32_t pend = T - F;
+        if (!pend) break;
+        __syncwarp();
+        if (pend >= 32u * W) step(std::integral_constant<int, W>{}, std::true_type{});
+        else if (pend > 32u * (W - 1)) step(std::integral_constant<int, W>{}, std::false_type{});
+        else step(std::integral_constant<int, 1>{}, std::false_type{});
+    }
+    __syncwarp();
+}
+
 // Count mode, k = 5: rows [r0, r1) of the last list level EL (see
 // count_shared_rows): each member's leaf list built, its group pairs and
 // part-B rows counted by count_leaves, then the shared part-A rows.
@@ -906,6 +1040,7 @@ __device__ __forceinline__ void count_last_lists(const GView &g, Sink<K> &sink, 
     constexpr int SB = 2 * (K - 3);
     constexpr int SHL = L::SH_ROW + 2 * (K - 2);
     const uint32_t v = p0[0];
+    int nb = 0;  // part-B rows collected in sc.pb
     for (int jl = r0; jl < r1; jl++) {
         const uint32_t el = EL[jl];
         const uint32_t wl = e_id(el);
@@ -943,14 +1078,32 @@ __device__ __forceinline__ void count_last_lists(const GView &g, Sink<K> &sink, 
             pos += __popc(ball);
         }
         __syncwarp();
-        uint32_t pm[K - 2];
+        // the group pairs of the whole list; its part-B rows are collected
+        // (with the list's w2) and scanned together with those of the next
+        // lists, or on their own when they alone overflow the collection
+        const int nB = pos - A;
+        if (!ACC_COLLECT_B || nB > kPartBRows) {
+            uint32_t pm[K - 2];
 #pragma unroll
-        for (int k2 = 0; k2 < K - 3; k2++) pm[k2] = p0[k2];
-        pm[K - 3] = wl;
-        // the group pairs of the whole list, the rows of its part B
-        count_leaves<K, HASH>(g, sink, EN, pos, A, pos, true, pm, pcode, v, (el & 3u) != 0u, sc.gcnt, sc.ring, lane);
+            for (int k2 = 0; k2 < K - 3; k2++) pm[k2] = p0[k2];
+            pm[K - 3] = wl;
+            count_leaves<K, HASH>(g, sink, EN, pos, A, pos, true, pm, pcode, v, (el & 3u) != 0u, sc.gcnt, sc.ring,
+                                  lane);
+        } else {
+            count_group_pairs<K>(sink, EN, pos, pcode, sc.gcnt, lane);
+            if (nb + nB > kPartBRows) {
+                count_partb_rows<HASH>(g, sink, sc.pb, sc.pb + kPartBRows, nb, pc0, p0, rows0, sc.ring, lane);
+                nb = 0;
+            }
+            for (int q = lane; q < nB; q += kWarp) {
+                sc.pb[nb + q] = EN[A + q];
+                sc.pb[kPartBRows + nb + q] = el;
+            }
+            nb += nB;
+        }
         __syncwarp();
     }
+    if (nb) count_partb_rows<HASH>(g, sink, sc.pb, sc.pb + kPartBRows, nb, pc0, p0, rows0, sc.ring, lane);
     count_shared_rows<K, HASH>(g, sink, EL, BL, r0, r1, pc0, p0, rows0, sc.ring, lane);
 }
 
@@ -1363,8 +1516,10 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? (SET ?
     const long long gw = (long long)blockIdx.x * kWarpsPerBlock + wib;
     sc.buf[0] = ebuf + (size_t)wib * L::LISTS * L::CAP;
     sc.buf[1] = sc.buf[0] + L::CAP;
+    // per-warp scratch: two overflow lists, then the collected part-B rows
     sc.ovf[0] = a.scratch + gw * a.scratch_per_warp;
-    sc.ovf[1] = sc.ovf[0] + a.scratch_per_warp / 2;
+    sc.ovf[1] = sc.ovf[0] + (a.scratch_per_warp - 2 * kPartBRows) / 2;
+    sc.pb = sc.ovf[0] + (a.scratch_per_warp - 2 * kPartBRows);
     sc.cap = L::CAP;
     sc.gcnt = groups + (size_t)wib * 2 * L::G;
     sc.ring = rings + (size_t)wib * L::RING_ARRAYS * L::RING;

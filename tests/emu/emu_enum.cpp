@@ -108,8 +108,9 @@ int main(int argc, char **argv) {
     info.nnz = nnz;
     info.maxdeg = 0;
     for (long long v = 0; v < NV; v++) info.maxdeg = std::max(info.maxdeg, deg[v]);
-    // per-warp overflow lists as the host sizes them: 2 (max_n + 32) rounded up
-    const long long spw = 2 * ((max_n + 32 + 31) & ~31LL);
+    // per-warp scratch as the host sizes it: two overflow lists of max_n + 32
+    // entries rounded up, then the k = 5 count mode's collected part-B rows
+    const long long spw = 2 * ((max_n + 32 + 31) & ~31LL) + 2 * acc::kPartBRows;
     std::vector<uint32_t> scratch((size_t)spw * blocks * acc::kWarpsPerBlock + 1);
     std::vector<uint4> queue((size_t)h[6] + 1);
     std::vector<unsigned long long> counts((size_t)B * ncls, 0);

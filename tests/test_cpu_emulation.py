@@ -152,7 +152,8 @@ def emu_bins(tmp_path_factory):
     targets = [(n, n, []) for n in ("emu_rand", "emu_f4", "emu_fill")]
     targets += [("emu_f3", "emu_f35", ["-DEMU_K=3"]), ("emu_f5", "emu_f35", ["-DEMU_K=5"])]
     targets += [("emu_enum", "emu_enum", ["-DEMU_DRAIN_AT=(1u<<30)"]),
-                ("emu_enum_small", "emu_enum", ["-DEMU_DRAIN_AT=256u", "-DACC_CAP34=16", "-DACC_CAP5=8"]),
+                ("emu_enum_small", "emu_enum", ["-DEMU_DRAIN_AT=256u", "-DACC_CAP34=16", "-DACC_CAP5=8",
+                                                    "-DACC_PARTB_ROWS=8"]),
                 ("emu_build", "emu_build", ["-I", str(bdir), "-fsanitize=address", "-DEMU_LANE_STACK=65536"]),
                 ("emu_build_guard", "emu_build", ["-I", str(gdir), "-DEMU_LANE_STACK=65536"]),
                 ("emu_lut", "emu_lut", ["-O2"]),
