@@ -50,7 +50,7 @@ namespace {
 
 // Tuning knobs (compile-time; -D overrides for sweeps).
 #ifndef ACC_CAP34
-#define ACC_CAP34 512
+#define ACC_CAP34 256
 #endif
 #ifndef ACC_GRAB4
 #define ACC_GRAB4 2  // base units per atomic grab for k = 4 (lighter units, one hot counter)
@@ -1421,47 +1421,49 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
         __syncwarp();
         return;
     }
-    for (int pass = 0; pass < 2; pass++) {
-        const int r0 = pass == 0 ? jlo : rest;
-        const int r1 = pass == 0 ? hi : B2;
-        for (int j2 = r0; j2 < r1; j2++) {
-            const uint32_t e2 = E2[j2];
-            const uint32_t w2 = e_id(e2);
-            const uint32_t pcode = pc01 | ((e2 & 15u) << 14);
-            const int A3 = B2 - 1 - j2;
-            const int dw = g.deg[w2];
-            const long long ub = (long long)A3 + dw;
-            uint32_t *E3 = ub <= sc.cap ? sc.buf[1] : sc.ovf[1];
-            // level-3 list: the level-2 list after w2 (with w2's states),
-            // then the neighbours of w2 above v adjacent to neither v nor w1,
-            // both read in one pass (the neighbours at or below v skipped by
-            // their ids)
-            const PRow row_w2 = prow<HASH>(g, w2);
-            const long long wb = g.nptr[w2];
-            const int nq = max(A3, dw);
-            int pos = A3;
-            for (int q0 = 0; q0 < nq; q0 += kWarp) {
-                const int q = q0 + lane;
-                const bool in_a = q < A3;
-                uint32_t xe = 0, ue = 0;
-                if (in_a) xe = E2[j2 + 1 + q];
-                if (q < dw) ue = __ldg(g.nbr + wb + q);
-                const uint32_t x = e_id(xe), u = ue >> 2;
-                uint32_t sa = 0;
-                bool keep = false;
-                if (in_a) sa = pget<HASH>(row_w2, x);
-                if (q < dw && u > (uint32_t)v) keep = pget<HASH>(row_v, u) == 0u && pget<HASH>(row_w1, u) == 0u;
-                if (in_a) E3[q] = (x << 6) | (xe & 15u) | (sa << 4);
-                const unsigned ball = __ballot_sync(kFull, keep);
-                if (keep) E3[pos + __popc(ball & ((1u << lane) - 1u))] = (u << 6) | ((ue & 3u) << 4);
-                pos += __popc(ball);
+    if constexpr (!COUNT) {
+        for (int pass = 0; pass < 2; pass++) {
+            const int r0 = pass == 0 ? jlo : rest;
+            const int r1 = pass == 0 ? hi : B2;
+            for (int j2 = r0; j2 < r1; j2++) {
+                const uint32_t e2 = E2[j2];
+                const uint32_t w2 = e_id(e2);
+                const uint32_t pcode = pc01 | ((e2 & 15u) << 14);
+                const int A3 = B2 - 1 - j2;
+                const int dw = g.deg[w2];
+                const long long ub = (long long)A3 + dw;
+                uint32_t *E3 = ub <= sc.cap ? sc.buf[1] : sc.ovf[1];
+                // level-3 list: the level-2 list after w2 (with w2's states),
+                // then the neighbours of w2 above v adjacent to neither v nor w1,
+                // both read in one pass (the neighbours at or below v skipped by
+                // their ids)
+                const PRow row_w2 = prow<HASH>(g, w2);
+                const long long wb = g.nptr[w2];
+                const int nq = max(A3, dw);
+                int pos = A3;
+                for (int q0 = 0; q0 < nq; q0 += kWarp) {
+                    const int q = q0 + lane;
+                    const bool in_a = q < A3;
+                    uint32_t xe = 0, ue = 0;
+                    if (in_a) xe = E2[j2 + 1 + q];
+                    if (q < dw) ue = __ldg(g.nbr + wb + q);
+                    const uint32_t x = e_id(xe), u = ue >> 2;
+                    uint32_t sa = 0;
+                    bool keep = false;
+                    if (in_a) sa = pget<HASH>(row_w2, x);
+                    if (q < dw && u > (uint32_t)v) keep = pget<HASH>(row_v, u) == 0u && pget<HASH>(row_w1, u) == 0u;
+                    if (in_a) E3[q] = (x << 6) | (xe & 15u) | (sa << 4);
+                    const unsigned ball = __ballot_sync(kFull, keep);
+                    if (keep) E3[pos + __popc(ball & ((1u << lane) - 1u))] = (u << 6) | ((ue & 3u) << 4);
+                    pos += __popc(ball);
+                }
+                __syncwarp();
+                const uint32_t pm[3] = {(uint32_t)v, w1, w2};
+                leaves<K>(g, sink, E3, pos, 0, (pos + 1) / 2, pm, pcode, (uint32_t)v, lane);
+                __syncwarp();
             }
-            __syncwarp();
-            const uint32_t pm[3] = {(uint32_t)v, w1, w2};
-            leaves<K>(g, sink, E3, pos, 0, (pos + 1) / 2, pm, pcode, (uint32_t)v, lane);
-            __syncwarp();
+            if (rest >= B2) break;
         }
-        if (rest >= B2) break;
     }
     sink.flush();
     __syncwarp();
