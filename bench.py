@@ -355,7 +355,9 @@ def measure_single(env, workload, steps, warmup, mode="count", schedule="", cpu_
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     counter = acc.Counter(env.local)
     counter.set_mode({"count": acc.ACC_MODE_COUNT, "enumerate": acc.ACC_MODE_ENUMERATE,
-                      "formula": acc.ACC_MODE_FORMULA}[mode])
+                      "formula": acc.ACC_MODE_FORMULA, "auto": acc.ACC_MODE_AUTO}[mode])
+    # the path the automatic mode takes (formula for k = 3 on the dense block)
+    eff = mode if mode != "auto" else ("formula" if k == 3 and adjacency in ("auto", "dense") else "count")
     counter.prepare(k)
     counter.set_adjacency({"auto": acc.ACC_ADJ_AUTO, "dense": acc.ACC_ADJ_DENSE, "hash": acc.ACC_ADJ_HASH,
                            "sparse": acc.ACC_ADJ_SPARSE}[adjacency])
@@ -450,10 +452,10 @@ def measure_single(env, workload, steps, warmup, mode="count", schedule="", cpu_
     peak_gops, peak_src = issue_peak_gops(env)
     enum_s = statistics.mean(enum_ms) / 1000.0
     leaf_achieved = ops_per_subgraph(k) * n_k / enum_s / 1e9
-    if mode == "count":
+    if eff == "count":
         units, per_unit = int(stats["scanned_entries"]), ops_per_scanned_entry(k)
         unit_name = "neighbour entries scanned by the last two levels"
-    elif mode == "formula" and k == 3:
+    elif eff == "formula" and k == 3:
         units, per_unit = n_k, ops_per_subgraph(k)
         unit_name = "classified subgraphs (leaf-equivalent: the formula path visits none)"
     else:
@@ -461,7 +463,7 @@ def measure_single(env, workload, steps, warmup, mode="count", schedule="", cpu_
         unit_name = "classified subgraphs"
     achieved = per_unit * units / enum_s / 1e9
     # the profiles were taken with the default probe structure
-    traffic, counters = profiled_counters(workload, mode) if adjacency == "auto" else (None, None)
+    traffic, counters = profiled_counters(workload, eff) if adjacency == "auto" else (None, None)
 
     # CPU baseline: the oracle on this host's cores, the whole workload
     cpu = None
@@ -474,12 +476,12 @@ def measure_single(env, workload, steps, warmup, mode="count", schedule="", cpu_
         "value": value, "unit": UNIT, "steps": steps, "warmup": warmup,
         "ms_per_step": 1000.0 * max_s / steps,
         "config": {"workload": workload, "k": k, "n": g.n, "m": g.m, "subgraphs_per_step": n_k,
-                   "mode": mode, "adjacency": adjacency,
+                   "mode": mode if mode == eff else f"{mode} ({eff} path)", "adjacency": adjacency,
                    "l2": "flushed between timed steps (256 MiB device write)",
                    "parallelism": f"replicas{env.world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved / peak_gops, "traffic": traffic,
-                     "kernel": f"k_enum<{k}> (phase 1 + phase 2)",
+                     "kernel": "k_formula3" if eff == "formula" and k == 3 else f"k_enum<{k}> (phase 1 + phase 2)",
                      "work_unit": unit_name, "units_per_launch": units, "ops_per_unit": per_unit,
                      "peak_source": peak_src,
                      # what a kernel visiting every leaf would have to sustain for this rate
@@ -524,7 +526,7 @@ def run_ours(args):
         # clock samples, in the same run
         subs = {}
         for w in ("er_n1000_m5000_k3", "regulatory_n5000_m15000_k5"):
-            r = measure_single(env, w, args.steps, args.warmup, "count", "", not args.no_cpu_baseline)
+            r = measure_single(env, w, args.steps, args.warmup, args.mode, "", not args.no_cpu_baseline)
             if r is not None:
                 subs[w] = r
         r = measure_batch(env, max(3, min(args.steps, 10)), args.warmup, not args.no_cpu_baseline, cpu_budget_s=5.0)
@@ -1054,9 +1056,10 @@ def main():
                     help="enumeration schedule LIGHT,TARGET for the single-graph workloads (default: the kernels')")
     ap.add_argument("--rand-mode", choices=["swap", "mutual"], default="swap",
                     help="significance workload: double-edge swaps, or swaps that keep mutual arcs mutual")
-    ap.add_argument("--mode", choices=["count", "enumerate", "formula"], default="count",
-                    help="last two levels counted by state-vector groups, every leaf enumerated, or (k=3) the "
-                         "per-vertex formulas")
+    ap.add_argument("--mode", choices=["count", "enumerate", "formula", "auto"], default="auto",
+                    help="last two levels counted by state-vector groups, every leaf enumerated, the paper's "
+                         "formulas, or the library's automatic choice (formulas for k=3 up to 16384 vertices, "
+                         "else the count mode)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

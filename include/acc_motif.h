@@ -397,11 +397,18 @@ ACC_API int acc_motif_last_stats(acc_ctx *ctx, int64_t *h_stats);
  *   it counted per pair of its 63 neighbour sets, linked pairs moved to their
  *   own class, each class divided by the number of connected 3-sets that
  *   reach its pattern.
+ *  ACC_MODE_AUTO: ACC_MODE_FORMULA for k = 3 on graphs of at most 16384
+ *   vertices (where the per-vertex formulas measured faster than the count
+ *   mode; above, hubs make their triangle listing the longer scan),
+ *   ACC_MODE_COUNT otherwise (for k = 4, 5 the count mode scans fewer
+ *   neighbour entries than the per-edge and per-triple formulas on every
+ *   graph measured, dense ones included).
  * All modes give identical counts.  Errors: ACC_ERR_ARG.
  */
 #define ACC_MODE_COUNT 0
 #define ACC_MODE_ENUMERATE 1
 #define ACC_MODE_FORMULA 2
+#define ACC_MODE_AUTO 3
 ACC_API int acc_ctx_set_mode(acc_ctx *ctx, int mode);
 
 /*

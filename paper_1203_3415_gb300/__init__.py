@@ -45,7 +45,7 @@ EXPORTS = (
 )
 ACC_REQ_QUEUED, ACC_REQ_RUNNING, ACC_REQ_DONE = 0, 1, 2
 ACC_SERVE_FIFO, ACC_SERVE_SHORTEST = 0, 1
-ACC_MODE_COUNT, ACC_MODE_ENUMERATE, ACC_MODE_FORMULA = 0, 1, 2
+ACC_MODE_COUNT, ACC_MODE_ENUMERATE, ACC_MODE_FORMULA, ACC_MODE_AUTO = 0, 1, 2, 3
 ACC_ADJ_AUTO, ACC_ADJ_DENSE, ACC_ADJ_HASH, ACC_ADJ_SPARSE = 0, 1, 2, 3
 ACC_RAND_SWAP, ACC_RAND_MUTUAL = 0, 1
 

@@ -58,7 +58,7 @@ struct acc_ctx {
     unsigned long long queue_cap = 0;
     uint32_t *scratch = nullptr;
     size_t scratch_cap = 0;
-    int mode = 0;             // ACC_MODE_COUNT or ACC_MODE_ENUMERATE
+    int mode = 0;             // ACC_MODE_COUNT, _ENUMERATE, _FORMULA or _AUTO
     long long sched_light = 0;   // enumeration schedule (0: the kernels' default)
     long long sched_target = 0;
     int *status_dev = nullptr;

@@ -92,7 +92,7 @@ def scenario_modes(lib):
     cases = {3: graphs(1, 3, 40), 4: graphs(2, 3, 22), 5: graphs(3, 2, 12)}
     g = synth.chung_lu(60, 200, 2.1, 30, 20, 4)
     cases[4].append((g.n, g.src, g.dst))
-    for mode in (acc.ACC_MODE_COUNT, acc.ACC_MODE_ENUMERATE, acc.ACC_MODE_FORMULA):
+    for mode in (acc.ACC_MODE_COUNT, acc.ACC_MODE_ENUMERATE, acc.ACC_MODE_FORMULA, acc.ACC_MODE_AUTO):
         ok(lib.acc_ctx_set_mode(c.h, mode), "acc_ctx_set_mode")
         for k, gs in cases.items():
             for n, s, d in gs:
@@ -102,9 +102,14 @@ def scenario_modes(lib):
                 if rc or st or got.tolist() != want.tolist():
                     raise AssertionError(f"mode {mode} k {k} n {n}: rc {rc} status {st}")
                 # the count mode's work figure equals the same sum over a
-                # plain ESU walk (below 1024 vertices nothing is renumbered)
-                if mode == acc.ACC_MODE_COUNT and c.stats()[6] != esu_scanned_entries(n, s, d, k):
-                    raise AssertionError(f"k {k} n {n}: {c.stats()[6]} entries scanned")
+                # plain ESU walk (below 1024 vertices nothing is renumbered);
+                # the automatic mode takes the count mode for k = 4, 5 and the
+                # formula path (no scan) for k = 3 on these small graphs
+                counted = mode == acc.ACC_MODE_COUNT or (mode == acc.ACC_MODE_AUTO and k > 3)
+                if counted and c.stats()[6] != esu_scanned_entries(n, s, d, k):
+                    raise AssertionError(f"mode {mode} k {k} n {n}: {c.stats()[6]} entries scanned")
+                if mode == acc.ACC_MODE_AUTO and k == 3 and n > 0 and c.stats()[6] != 0:
+                    raise AssertionError(f"automatic mode, k 3, n {n}: not the formula path")
     # the count mode probing the hashed adjacency tables (built on the device
     # after the neighbour lists: one more kernel), with the lists built with
     # and without the dense block, and the dense block again
@@ -119,6 +124,8 @@ def scenario_modes(lib):
                     raise AssertionError(f"adjacency {adj} k {k} n {n}: rc {rc} status {st}")
     if lib.acc_ctx_set_adjacency(c.h, 4) != acc.ACC_ERR_ARG:
         raise AssertionError("an unknown adjacency choice is accepted")
+    if lib.acc_ctx_set_mode(c.h, 4) != acc.ACC_ERR_ARG:
+        raise AssertionError("an unknown mode is accepted")
     c.close()
 
 

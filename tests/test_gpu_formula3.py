@@ -88,4 +88,31 @@ def test_batch_and_mode_agreement(counter):
     assert gpu_count(counter, h.n, h.src, h.dst, 5).tolist() == \
         oracle.count(h.n, h.src, h.dst, 5, threads=oracle.max_threads()).tolist()
     with pytest.raises(p.MotifError):
-        counter.set_mode(3)
+        counter.set_mode(4)  # no such mode (3 is the automatic one)
+
+
+def test_automatic_mode_takes_both_paths():
+    """ACC_MODE_AUTO: k = 3 on graphs of at most 16384 vertices runs the
+    formula path (no neighbour entries scanned), larger k = 3 graphs and
+    every k = 4 count run the count mode (entries scanned); the counts equal
+    the oracle's in both branches."""
+    from paper_1203_3415_gb300 import build
+    build.build()
+    import paper_1203_3415_gb300 as p
+    c = p.Counter(0)
+    c.set_mode(p.ACC_MODE_AUTO)
+    try:
+        small = synth.chung_lu(4000, 24000, 2.2, 200, 10, 21)
+        assert gpu_count(c, small.n, small.src, small.dst, 3).tolist() == \
+            oracle.count(small.n, small.src, small.dst, 3).tolist()
+        assert c.last_stats()["scanned_entries"] == 0
+        big = synth.chung_lu(20000, 80000, 2.2, 300, 10, 22)
+        assert gpu_count(c, big.n, big.src, big.dst, 3).tolist() == \
+            oracle.count(big.n, big.src, big.dst, 3, threads=oracle.max_threads()).tolist()
+        assert c.last_stats()["scanned_entries"] > 0
+        h = synth.chung_lu(1500, 6000, 2.2, 100, 10, 23)
+        assert gpu_count(c, h.n, h.src, h.dst, 4).tolist() == \
+            oracle.count(h.n, h.src, h.dst, 4, threads=oracle.max_threads()).tolist()
+        assert c.last_stats()["scanned_entries"] > 0
+    finally:
+        c.close()
