@@ -36,8 +36,11 @@
 //
 // Work units: k=3 one unit per root v; k=4 and k=5 one unit per arc position
 // of the G* CSR, i.e. per (v, w1) with w1 > v.  Phase 1 runs every light unit
-// and queues the heavy ones as row ranges of their extension list; phase 2
-// (a second launch) drains the queue.
+// and queues the heavy ones as row ranges of their extension list (k = 5:
+// of the level-2 list, one level-3 list per row); phase 2 (a second launch)
+// drains the queue.  k = 5 in the count mode scans the level-2 rows that a
+// range's level-3 lists share once for all of them (count_shared_rows) and
+// the lists' own rows together (count_partb_rows).
 #include <math.h>
 
 #include <type_traits>
