@@ -172,6 +172,33 @@ __host__ __device__ inline uint32_t nh_bucket(uint32_t u, uint32_t lg) {
     return lg ? (u * 0x9E3779B1u) >> (32u - lg) : 0u;  // multiplicative hash, top lg bits
 }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may have
+// its blocks scheduled while the previous kernel of the stream finishes; it
+// waits in grid_dep_wait(), its first statement, until that kernel has
+// completed and its writes are visible (a no-op after a plain launch).
+__device__ __forceinline__ void grid_dep_wait() {
+#ifdef __CUDA_ARCH__
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+#ifdef __CUDACC__
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+#endif
+
 // First-error-wins status update.
 __device__ inline void set_status(int *status, int err) {
     if (status) atomicCAS(status, 0, err);

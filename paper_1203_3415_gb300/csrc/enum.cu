@@ -1479,6 +1479,7 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
 template <int K, bool COUNT, int PHASE, bool SET, bool HASH>
 __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? (SET ? ACC_MINB34S : ACC_MINB34C) : ACC_MINB34))
     k_enum(EnumArgs a) {
+    grid_dep_wait();
     using L = Layout<K>;
     extern __shared__ __align__(16) unsigned char smem[];
     int16_t *lut_s = reinterpret_cast<int16_t *>(smem);
@@ -1644,7 +1645,7 @@ int launch_phase(const EnumArgs &a, int num_sms, cudaStream_t s, int grid_num, i
     int grid = (int)((long long)num_sms * bps * grid_num / grid_den);
     if (grid < num_sms) grid = num_sms;
     if (grid > num_sms * bps) grid = num_sms * bps;
-    k_enum<K, COUNT, PHASE, SET, HASH><<<grid, kThreads, Layout<K>::total, s>>>(a);
+    launch_pdl(k_enum<K, COUNT, PHASE, SET, HASH>, grid, kThreads, Layout<K>::total, s, a);
     return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
 

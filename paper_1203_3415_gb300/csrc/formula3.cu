@@ -38,6 +38,7 @@ __device__ __forceinline__ uint32_t probe3(const uint32_t *__restrict__ st, long
 __global__ void k_formula3(GSet gs, const uint32_t *__restrict__ state, const long long *__restrict__ nptr,
                            const int *__restrict__ deg, const int *__restrict__ lo, const uint32_t *__restrict__ nbr,
                            const int16_t *__restrict__ lut, unsigned long long *counts, int *status) {
+    grid_dep_wait();
     __shared__ unsigned long long hist[kF3Classes];
     const bool several = gs.B > 1;  // several graphs: straight to each graph's counts
     for (int i = threadIdx.x; i < kF3Classes; i += blockDim.x) hist[i] = 0;
@@ -112,7 +113,7 @@ int launch_formula3(const GSet &gs, const uint32_t *state, const long long *nptr
     if (gs.NV == 0) return 0;
     long long blocks = (gs.NV * kWarp + 255) / 256;
     if (blocks > (long long)num_sms * 8) blocks = (long long)num_sms * 8;
-    k_formula3<<<(int)blocks, 256, 0, s>>>(gs, state, nptr, deg, lo, nbr, lut, counts, status);
+    launch_pdl(k_formula3, (int)blocks, 256, 0, s, gs, state, nptr, deg, lo, nbr, lut, counts, status);
     return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
 

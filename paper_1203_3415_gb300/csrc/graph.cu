@@ -56,6 +56,7 @@ struct IntRanges {
 
 __global__ void k_zero(uint4 *p, size_t n16, unsigned char *tail, size_t ntail, int *status,
                        unsigned long long *counts, long long ncounts, IntRanges ints) {
+    grid_dep_wait();
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t j = i; j < n16; j += stride) p[j] = make_uint4(0, 0, 0, 0);
@@ -108,6 +109,7 @@ __device__ __forceinline__ void for_each_arc(const GSet &gs, F f) {
 // both arcs of a mutual pair counted), the key of the renumbering.  Arcs
 // with a bad target are skipped here (k_ingest reports them).
 __global__ void k_arc_degrees(GSet gs, int *deg_io) {
+    grid_dep_wait();
     for_each_arc(gs, [&](int v, const GMeta &mt, int lv, long long p) {
         const int u0 = mt.col[p];
         if (u0 < 0 || u0 >= mt.n || u0 == lv) return;
@@ -143,6 +145,7 @@ __device__ __forceinline__ void validate_rows(const GSet &gs, int *status) {
 
 __global__ void k_ingest(GSet gs, uint32_t *state, const int *__restrict__ label, int *status, int *deg, int *lo,
                          uint32_t *occ, int occ_w) {
+    grid_dep_wait();
     validate_rows(gs, status);
     for_each_arc(gs, [&](int v, const GMeta &mt, int lv, long long p) {
         const int u0 = mt.col[p];
@@ -173,6 +176,7 @@ __global__ void k_ingest(GSet gs, uint32_t *state, const int *__restrict__ label
 // bitmap marks (every word the ingest set lies in one), lane j taking the
 // j-th marked chunk of a bitmap word.  The buffer is all zero afterwards.
 __global__ void k_clear_chunks(GSet gs, uint32_t *state, const uint32_t *__restrict__ occ, int occ_w) {
+    grid_dep_wait();
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -195,6 +199,7 @@ __global__ void k_clear_chunks(GSet gs, uint32_t *state, const uint32_t *__restr
 // Per-graph histogram dhist[voff + key] of the renumbering keys (clamped to
 // n - 1: the out- plus in-degree can exceed it).
 __global__ void k_dhist(GSet gs, const int *__restrict__ key, int *dhist) {
+    grid_dep_wait();
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < gs.NV;
          v += (long long)gridDim.x * blockDim.x) {
         const GMeta mt = gs.meta(gs.graph_of((int)v));
@@ -204,6 +209,7 @@ __global__ void k_dhist(GSet gs, const int *__restrict__ key, int *dhist) {
 
 // Block per graph: start[voff + d] = vertices of the graph with degree above d.
 __global__ void __launch_bounds__(1024) k_desc_starts(GSet gs, const int *__restrict__ dhist, int *start) {
+    grid_dep_wait();
     __shared__ int warp_sum[32];
     const GMeta mt = gs.meta(blockIdx.x);
     const int n = mt.n;
@@ -245,6 +251,7 @@ __global__ void __launch_bounds__(1024) k_desc_starts(GSet gs, const int *__rest
 // label[v] = voff + the next free position of v's key class in its graph
 // (ties in any order); also zeroes dhist (dead once the starts exist).
 __global__ void k_desc_scatter(GSet gs, const int *__restrict__ key, int *start, int *label, int *dhist) {
+    grid_dep_wait();
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < gs.NV;
          v += (long long)gridDim.x * blockDim.x) {
         const GMeta mt = gs.meta(gs.graph_of((int)v));
@@ -258,6 +265,7 @@ __global__ void k_desc_scatter(GSet gs, const int *__restrict__ key, int *start,
 // shared memory by coalesced loads (n ints of dynamic shared memory).
 __global__ void __launch_bounds__(1024) k_scan_degrees(const int *__restrict__ deg_g, int n, long long *nptr, GraphInfo *info,
                                                        int k, int max_n, int *status) {
+    grid_dep_wait();
     extern __shared__ int deg[];
     __shared__ long long warp_sum[32];
     __shared__ int warp_max[32];
@@ -363,6 +371,7 @@ constexpr int kScanTile = 4096;
 
 __global__ void __launch_bounds__(1024) k_scan_tiles(const int *__restrict__ deg, int n, long long *tile_sum, GraphInfo *info,
                                                      int k) {
+    grid_dep_wait();
     __shared__ long long ws[32];
     __shared__ int wm[32];
     __shared__ float wb[32][3];
@@ -410,6 +419,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(const int *__restrict__ deg
 
 __global__ void __launch_bounds__(1024) k_scan_top(long long *tile_sum, int ntiles, long long *nptr, int n, GraphInfo *info,
                                                    int k, int max_n, int *status) {
+    grid_dep_wait();
     __shared__ long long warp_sum[32];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int chunk = (ntiles + blockDim.x - 1) / blockDim.x;
@@ -460,6 +470,7 @@ __global__ void __launch_bounds__(1024) k_scan_top(long long *tile_sum, int ntil
 
 __global__ void __launch_bounds__(1024) k_scan_apply(const int *__restrict__ deg, int n, const long long *__restrict__ tile_off,
                              long long *nptr) {
+    grid_dep_wait();
     __shared__ long long warp_sum[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int per = kScanTile / 1024;  // elements per thread (blockDim 1024)
@@ -512,6 +523,7 @@ __global__ void __launch_bounds__(1024) k_scan_apply(const int *__restrict__ deg
 // (the enumeration's phase 1 reads a work unit's vertex from it).
 __global__ void k_fill(GSet gs, const uint32_t *__restrict__ state, const uint32_t *__restrict__ occ, int occ_w,
                        const long long *__restrict__ nptr, uint32_t *nbr, uint32_t *src, int rw) {
+    grid_dep_wait();
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -622,6 +634,7 @@ constexpr int kSortWarps = 4;     // warps per block of the small-row sort
 // checks of the input; arcs with a bad target or self-loops are reported
 // and not counted.
 __global__ void k_sp_count(GSet gs, const int *__restrict__ label, int *status, int *cnt) {
+    grid_dep_wait();
     validate_rows(gs, status);
     for_each_arc(gs, [&](int v, const GMeta &mt, int lv, long long p) {
         const int u0 = mt.col[p];
@@ -640,6 +653,7 @@ __global__ void k_sp_count(GSet gs, const int *__restrict__ label, int *status, 
 // entries placed, in any order).
 __global__ void k_sp_scatter(GSet gs, const int *__restrict__ label, const long long *__restrict__ roff, int *cur,
                              uint32_t *raw) {
+    grid_dep_wait();
     for_each_arc(gs, [&](int v, const GMeta &mt, int lv, long long p) {
         const int u0 = mt.col[p];
         if (u0 < 0 || u0 >= mt.n || u0 == lv) return;
@@ -683,6 +697,7 @@ __global__ void __launch_bounds__(kSortWarps * kWarp) k_sp_sort_small(GSet gs, c
                                                                    const uint32_t *__restrict__ raw,
                                                                    uint32_t *merged, int *deg, int *lo, int *big,
                                                                    GraphInfo *info) {
+    grid_dep_wait();
     __shared__ uint32_t buf[kSortWarps][kSortSmall];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t *x = buf[wib];
@@ -720,6 +735,7 @@ __global__ void __launch_bounds__(kSortWarps * kWarp) k_sp_sort_small(GSet gs, c
 // the same sort in place in raw (global memory), then the same merge.
 __global__ void k_sp_sort_big(GSet gs, const long long *__restrict__ roff, uint32_t *raw, uint32_t *merged, int *deg,
                               int *lo, const int *__restrict__ big, GraphInfo *info) {
+    grid_dep_wait();
     __shared__ int row, warp_cnt[32], warp_below[32];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nwarps = blockDim.x >> 5;
     for (;;) {
@@ -775,6 +791,7 @@ __global__ void k_sp_sort_big(GSet gs, const long long *__restrict__ roff, uint3
 __global__ void k_sp_compact(GSet gs, const long long *__restrict__ roff, const uint32_t *__restrict__ merged,
                              const int *__restrict__ deg, const long long *__restrict__ nptr, uint32_t *nbr,
                              uint32_t *src) {
+    grid_dep_wait();
     const int lane = threadIdx.x & 31;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; v < gs.NV; v += nw) {
@@ -793,6 +810,7 @@ __global__ void k_sp_compact(GSet gs, const long long *__restrict__ roff, const 
 // vertices): renumber the graph's vertices by descending key, ties in any
 // order, with the key histogram and its starts in shared memory.
 __global__ void __launch_bounds__(1024) k_relabel_graph(GSet gs, const int *__restrict__ key, int *label) {
+    grid_dep_wait();
     extern __shared__ int h[];
     __shared__ int warp_sum[32];
     const GMeta mt = gs.meta(blockIdx.x);
@@ -853,11 +871,13 @@ __global__ void __launch_bounds__(1024) k_relabel_graph(GSet gs, const int *__re
 
 // gid[v] = graph of global vertex v (block per graph).
 __global__ void k_graph_ids(GSet gs, int *gid) {
+    grid_dep_wait();
     const GMeta mt = gs.meta(blockIdx.x);
     for (int i = threadIdx.x; i < mt.n; i += blockDim.x) gid[mt.voff + i] = blockIdx.x;
 }
 
 __global__ void k_reset_maxdeg(GraphInfo *info) {
+    grid_dep_wait();
     info->maxdeg = 0;
     info->bound[0] = info->bound[1] = info->bound[2] = 0.0f;
 }
@@ -886,14 +906,14 @@ int launch_zero(void *p, size_t bytes, int num_sms, cudaStream_t s, int *status,
     IntRanges r = {{ints, nullptr, nullptr, nullptr}, {ints ? nints : 0, 0, 0, 0}};
     const size_t n16 = bytes / 16, ntail = bytes % 16;
     const int grid = grid_for((long long)(n16 > 0 ? n16 : 1), 256 * 4, num_sms);
-    k_zero<<<grid, 256, 0, s>>>(reinterpret_cast<uint4 *>(p), n16,
+    launch_pdl(k_zero, grid, 256, 0, s, reinterpret_cast<uint4 *>(p), n16,
                                 reinterpret_cast<unsigned char *>(p) + n16 * 16, ntail, status, counts, ncounts, r);
     return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
 
 int launch_graph_ids(const GSet &gs, int *gid, cudaStream_t s) {
     if (gs.B <= 1) return 0;
-    k_graph_ids<<<gs.B, 256, 0, s>>>(gs, gid);
+    launch_pdl(k_graph_ids, gs.B, 256, 0, s, gs, gid);
     return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
 
@@ -922,7 +942,7 @@ int launch_build_graph(const GSet &gs, const BuildBufs &bb, int max_n, int *stat
                        {NV, NV, relabel ? NV : 0, nocc}};
         const size_t n16 = bytes / 16, ntail = bytes % 16;
         const long long items = (long long)max((size_t)1, max(n16, (size_t)max(max(NV, ncounts), nocc)));
-        k_zero<<<grid_for(items, 256 * 4, num_sms), 256, 0, s>>>(reinterpret_cast<uint4 *>(bb.state), n16,
+        launch_pdl(k_zero, grid_for(items, 256 * 4, num_sms), 256, 0, s, reinterpret_cast<uint4 *>(bb.state), n16,
                                                                  reinterpret_cast<unsigned char *>(bb.state) + n16 * 16,
                                                                  ntail, status, counts, ncounts, r);
         if (!launch_ok()) return ACC_ERR_CUDA;
@@ -931,50 +951,50 @@ int launch_build_graph(const GSet &gs, const BuildBufs &bb, int max_n, int *stat
     if (relabel) {
         // each graph's vertices renumbered by descending out- plus in-degree,
         // then the block built under the new ids
-        k_arc_degrees<<<arcs_grid, 256, 0, s>>>(gs, bb.deg_in);
+        launch_pdl(k_arc_degrees, arcs_grid, 256, 0, s, gs, bb.deg_in);
         if (!launch_ok()) return ACC_ERR_CUDA;
         launches++;
         if (max_n <= kRelabelSmemMax) {
-            k_relabel_graph<<<gs.B, 1024, (size_t)max_n * 4, s>>>(gs, bb.deg_in, bb.label);
+            launch_pdl(k_relabel_graph, gs.B, 1024, (size_t)max_n * 4, s, gs, bb.deg_in, bb.label);
             if (!launch_ok()) return ACC_ERR_CUDA;
             launches++;
         } else {
             int *dhist = bb.deg;  // zeroed above, zeroed again by k_desc_scatter
             int *start = reinterpret_cast<int *>(bb.nptr);
-            k_dhist<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, bb.deg_in, dhist);
+            launch_pdl(k_dhist, grid_for(NV, 256, num_sms), 256, 0, s, gs, bb.deg_in, dhist);
             if (!launch_ok()) return ACC_ERR_CUDA;
-            k_desc_starts<<<gs.B, 1024, 0, s>>>(gs, dhist, start);
+            launch_pdl(k_desc_starts, gs.B, 1024, 0, s, gs, dhist, start);
             if (!launch_ok()) return ACC_ERR_CUDA;
-            k_desc_scatter<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, bb.deg_in, start, bb.label, dhist);
+            launch_pdl(k_desc_scatter, grid_for(NV, 256, num_sms), 256, 0, s, gs, bb.deg_in, start, bb.label, dhist);
             if (!launch_ok()) return ACC_ERR_CUDA;
             launches += 3;
         }
     }
-    k_ingest<<<arcs_grid, 256, 0, s>>>(gs, bb.state, relabel ? bb.label : nullptr, status, bb.deg, bb.lo, bb.occ,
+    launch_pdl(k_ingest, arcs_grid, 256, 0, s, gs, bb.state, relabel ? bb.label : nullptr, status, bb.deg, bb.lo, bb.occ,
                                        bb.occ_w);
     if (!launch_ok()) return ACC_ERR_CUDA;
     launches++;
     if (NV <= kScanSingleMax) {
-        k_scan_degrees<<<1, 1024, (size_t)(NV > 0 ? NV : 1) * 4, s>>>(bb.deg, (int)NV, bb.nptr, bb.info, bb.k, max_n,
+        launch_pdl(k_scan_degrees, 1, 1024, (size_t)(NV > 0 ? NV : 1) * 4, s, bb.deg, (int)NV, bb.nptr, bb.info, bb.k, max_n,
                                                                       status);
         if (!launch_ok()) return ACC_ERR_CUDA;
         launches++;
     } else {
         const int ntiles = (int)scan_tiles_needed(NV);
-        k_reset_maxdeg<<<1, 1, 0, s>>>(bb.info);
+        launch_pdl(k_reset_maxdeg, 1, 1, 0, s, bb.info);
         if (!launch_ok()) return ACC_ERR_CUDA;
-        k_scan_tiles<<<ntiles, 1024, 0, s>>>(bb.deg, (int)NV, bb.tiles, bb.info, bb.k);
+        launch_pdl(k_scan_tiles, ntiles, 1024, 0, s, bb.deg, (int)NV, bb.tiles, bb.info, bb.k);
         if (!launch_ok()) return ACC_ERR_CUDA;
-        k_scan_top<<<1, 1024, 0, s>>>(bb.tiles, ntiles, bb.nptr, (int)NV, bb.info, bb.k, max_n, status);
+        launch_pdl(k_scan_top, 1, 1024, 0, s, bb.tiles, ntiles, bb.nptr, (int)NV, bb.info, bb.k, max_n, status);
         if (!launch_ok()) return ACC_ERR_CUDA;
-        k_scan_apply<<<ntiles, 1024, 0, s>>>(bb.deg, (int)NV, bb.tiles, bb.nptr);
+        launch_pdl(k_scan_apply, ntiles, 1024, 0, s, bb.deg, (int)NV, bb.tiles, bb.nptr);
         if (!launch_ok()) return ACC_ERR_CUDA;
         launches += 4;
     }
     // rows per warp: enough warps to fill the GPU (64 per SM) first
     int rw = 1;
     while (rw < kWarp && (long long)rw * 2 * num_sms * 64 <= NV) rw *= 2;
-    k_fill<<<grid_for((NV + rw - 1) / rw * kWarp, 256, num_sms), 256, 0, s>>>(gs, bb.state, bb.occ, bb.occ_w,
+    launch_pdl(k_fill, grid_for((NV + rw - 1) / rw * kWarp, 256, num_sms), 256, 0, s, gs, bb.state, bb.occ, bb.occ_w,
                                                                               bb.nptr, bb.nbr, bb.src, rw);
     launches++;
     return cudaGetLastError() == cudaSuccess ? launches : ACC_ERR_CUDA;
@@ -1001,67 +1021,67 @@ int launch_build_graph_sparse(const GSet &gs, const BuildBufs &bb, const SparseB
     {
         IntRanges r = {{bb.deg, bb.lo, bb.deg_in, nullptr}, {NV, NV, relabel ? NV : 0, 0}};
         const long long items = max(NV, ncounts) > 0 ? max(NV, ncounts) : 1;
-        k_zero<<<grid_for(items, 256 * 4, num_sms), 256, 0, s>>>(nullptr, 0, nullptr, 0, status, counts, ncounts, r);
+        launch_pdl(k_zero, grid_for(items, 256 * 4, num_sms), 256, 0, s, nullptr, 0, nullptr, 0, status, counts, ncounts, r);
         if (!launch_ok()) return ACC_ERR_CUDA;
         launches++;
     }
     if (relabel) {
-        k_arc_degrees<<<arcs_grid, 256, 0, s>>>(gs, bb.deg_in);
+        launch_pdl(k_arc_degrees, arcs_grid, 256, 0, s, gs, bb.deg_in);
         if (!launch_ok()) return ACC_ERR_CUDA;
         launches++;
         if (max_n <= kRelabelSmemMax) {
-            k_relabel_graph<<<gs.B, 1024, (size_t)max_n * 4, s>>>(gs, bb.deg_in, bb.label);
+            launch_pdl(k_relabel_graph, gs.B, 1024, (size_t)max_n * 4, s, gs, bb.deg_in, bb.label);
             if (!launch_ok()) return ACC_ERR_CUDA;
             launches++;
         } else {
             int *dhist = bb.deg;  // zeroed above, zeroed again by k_desc_scatter
             int *start = reinterpret_cast<int *>(bb.nptr);
-            k_dhist<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, bb.deg_in, dhist);
+            launch_pdl(k_dhist, grid_for(NV, 256, num_sms), 256, 0, s, gs, bb.deg_in, dhist);
             if (!launch_ok()) return ACC_ERR_CUDA;
-            k_desc_starts<<<gs.B, 1024, 0, s>>>(gs, dhist, start);
+            launch_pdl(k_desc_starts, gs.B, 1024, 0, s, gs, dhist, start);
             if (!launch_ok()) return ACC_ERR_CUDA;
-            k_desc_scatter<<<grid_for(NV, 256, num_sms), 256, 0, s>>>(gs, bb.deg_in, start, bb.label, dhist);
+            launch_pdl(k_desc_scatter, grid_for(NV, 256, num_sms), 256, 0, s, gs, bb.deg_in, start, bb.label, dhist);
             if (!launch_ok()) return ACC_ERR_CUDA;
             launches += 3;
         }
     }
-    k_sp_count<<<arcs_grid, 256, 0, s>>>(gs, relabel ? bb.label : nullptr, status, cnt);
+    launch_pdl(k_sp_count, arcs_grid, 256, 0, s, gs, relabel ? bb.label : nullptr, status, cnt);
     if (!launch_ok()) return ACC_ERR_CUDA;
     launches++;
     // degree scans: the raw counts into the row offsets (no count bound), and
     // after the sort the final degrees into nptr (with it)
     auto scan = [&](const int *d, long long *out, int k) -> int {
         if (NV <= kScanSingleMax) {
-            k_scan_degrees<<<1, 1024, (size_t)(NV > 0 ? NV : 1) * 4, s>>>(d, (int)NV, out, bb.info, k, max_n, status);
+            launch_pdl(k_scan_degrees, 1, 1024, (size_t)(NV > 0 ? NV : 1) * 4, s, d, (int)NV, out, bb.info, k, max_n, status);
             return launch_ok() ? 1 : ACC_ERR_CUDA;
         }
         const int ntiles = (int)scan_tiles_needed(NV);
-        k_reset_maxdeg<<<1, 1, 0, s>>>(bb.info);
+        launch_pdl(k_reset_maxdeg, 1, 1, 0, s, bb.info);
         if (!launch_ok()) return ACC_ERR_CUDA;
-        k_scan_tiles<<<ntiles, 1024, 0, s>>>(d, (int)NV, bb.tiles, bb.info, k);
+        launch_pdl(k_scan_tiles, ntiles, 1024, 0, s, d, (int)NV, bb.tiles, bb.info, k);
         if (!launch_ok()) return ACC_ERR_CUDA;
-        k_scan_top<<<1, 1024, 0, s>>>(bb.tiles, ntiles, out, (int)NV, bb.info, k, max_n, status);
+        launch_pdl(k_scan_top, 1, 1024, 0, s, bb.tiles, ntiles, out, (int)NV, bb.info, k, max_n, status);
         if (!launch_ok()) return ACC_ERR_CUDA;
-        k_scan_apply<<<ntiles, 1024, 0, s>>>(d, (int)NV, bb.tiles, out);
+        launch_pdl(k_scan_apply, ntiles, 1024, 0, s, d, (int)NV, bb.tiles, out);
         return launch_ok() ? 4 : ACC_ERR_CUDA;
     };
     int rc = scan(cnt, sb.roff, 0);
     if (rc < 0) return rc;
     launches += rc;
-    k_sp_scatter<<<arcs_grid, 256, 0, s>>>(gs, relabel ? bb.label : nullptr, sb.roff, cur, sb.raw);
+    launch_pdl(k_sp_scatter, arcs_grid, 256, 0, s, gs, relabel ? bb.label : nullptr, sb.roff, cur, sb.raw);
     if (!launch_ok()) return ACC_ERR_CUDA;
     launches++;
     if (gs.M > 0 && cudaMemsetAsync(sb.merged, 0, (size_t)(2 * gs.M) * sizeof(uint32_t), s) != cudaSuccess)
         return ACC_ERR_CUDA;
-    k_sp_sort_small<<<grid_for((NV + kSortWarps - 1) / kSortWarps, 1, num_sms), kSortWarps * kWarp, 0, s>>>(
+    launch_pdl(k_sp_sort_small, grid_for((NV + kSortWarps - 1) / kSortWarps, 1, num_sms), kSortWarps * kWarp, 0, s, 
         gs, sb.roff, sb.raw, sb.merged, bb.deg, bb.lo, sb.big, bb.info);
     if (!launch_ok()) return ACC_ERR_CUDA;
-    k_sp_sort_big<<<num_sms, 256, 0, s>>>(gs, sb.roff, sb.raw, sb.merged, bb.deg, bb.lo, sb.big, bb.info);
+    launch_pdl(k_sp_sort_big, num_sms, 256, 0, s, gs, sb.roff, sb.raw, sb.merged, bb.deg, bb.lo, sb.big, bb.info);
     if (!launch_ok()) return ACC_ERR_CUDA;
     launches += 2;
     if ((rc = scan(bb.deg, bb.nptr, bb.k)) < 0) return rc;
     launches += rc;
-    k_sp_compact<<<grid_for(NV * kWarp, 256, num_sms), 256, 0, s>>>(gs, sb.roff, sb.merged, bb.deg, bb.nptr, bb.nbr,
+    launch_pdl(k_sp_compact, grid_for(NV * kWarp, 256, num_sms), 256, 0, s, gs, sb.roff, sb.merged, bb.deg, bb.nptr, bb.nbr,
                                                                    bb.src);
     if (!launch_ok()) return ACC_ERR_CUDA;
     launches++;
@@ -1070,7 +1090,7 @@ int launch_build_graph_sparse(const GSet &gs, const BuildBufs &bb, const SparseB
 
 int launch_clear_graph(const GSet &gs, uint32_t *state, const uint32_t *occ, int occ_w, int num_sms, cudaStream_t s) {
     if (gs.NV == 0) return 0;
-    k_clear_chunks<<<grid_for(gs.NV * kWarp, 256, num_sms), 256, 0, s>>>(gs, state, occ, occ_w);
+    launch_pdl(k_clear_chunks, grid_for(gs.NV * kWarp, 256, num_sms), 256, 0, s, gs, state, occ, occ_w);
     return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
 

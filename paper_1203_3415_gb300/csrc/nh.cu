@@ -20,6 +20,7 @@ namespace {
 __global__ void k_nh_fill(const long long *__restrict__ nptr, const int *__restrict__ deg,
                           const uint32_t *__restrict__ nbr, const uint32_t *__restrict__ src,
                           const GraphInfo *__restrict__ info, uint32_t *nh) {
+    grid_dep_wait();
     const long long nnz = info->nnz;
     for (long long pos = blockIdx.x * (long long)blockDim.x + threadIdx.x; pos < nnz;
          pos += (long long)gridDim.x * blockDim.x) {
@@ -46,7 +47,7 @@ int launch_nh_build(const long long *nptr, const int *deg, const uint32_t *nbr, 
         return ACC_ERR_CUDA;
     long long grid = (max_entries + 255) / 256;
     if (grid > (long long)num_sms * 16) grid = (long long)num_sms * 16;
-    k_nh_fill<<<(int)grid, 256, 0, s>>>(nptr, deg, nbr, src, info, nh);
+    launch_pdl(k_nh_fill, (int)grid, 256, 0, s, nptr, deg, nbr, src, info, nh);
     return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
 

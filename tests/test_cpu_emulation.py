@@ -86,6 +86,46 @@ def _launches_to_calls(src):
         i = c
     out.append(src[i:])
     src = "".join(out)
+    # the same for launch_pdl(kernel, grid, block, smem, stream, args...)
+    out, i = [], 0
+    while True:
+        a = src.find("launch_pdl(", i)
+        if a < 0:
+            break
+        j = a + len("launch_pdl(")
+        k = j
+        while src[k].isalnum() or src[k] == "_":
+            k += 1
+        if src[k] == "<":  # template arguments of the kernel
+            depth = 0
+            while True:
+                depth += {"<": 1, ">": -1}.get(src[k], 0)
+                k += 1
+                if depth == 0:
+                    break
+        kernel = src[j:k]
+        parts, depth, start, c = [], 0, k + 1, k + 1
+        assert src[k] == ",", src[a:k + 20]
+        while True:
+            ch = src[c]
+            if ch in "([{":
+                depth += 1
+            elif ch in ")]}":
+                if depth == 0:
+                    parts.append(src[start:c])
+                    break
+                depth -= 1
+            elif ch == "," and depth == 0:
+                parts.append(src[start:c])
+                start = c + 1
+            c += 1
+        assert src[c + 1] == ";", src[a:c + 2]
+        cfg, args = parts[:4], parts[4:]
+        out.append(src[i:a])
+        out.append("emu_launch(%s, [=] { %s(%s); })" % (",".join(cfg), kernel, ",".join(args)))
+        i = c + 1
+    out.append(src[i:])
+    src = "".join(out)
     src = re.sub(r"extern __shared__ (?:__align__\(\d+\) )?([\w ]+?) (\w+)\[\];",
                  r"\1 *\2 = reinterpret_cast<\1 *>(emu_dyn_smem);", src)
     assert "extern __shared__" not in src
