@@ -1041,7 +1041,7 @@ def main():
                     help="serving window of the default run's serving sub-records (200 and 50 requests/s)")
     ap.add_argument("--headline-only", action="store_true",
                     help="default workload: print the headline line without the other workloads' sub-records")
-    ap.add_argument("--slots", type=int, default=4, help="serving: concurrent requests")
+    ap.add_argument("--slots", type=int, default=8, help="serving: concurrent requests")
     ap.add_argument("--mem-budget-gb", type=float, default=96.0, help="serving: workspace budget")
     ap.add_argument("--reference-roots", type=int, default=0,
                     help="reference arm: ESU roots per step (0: all roots, the whole workload)")
