@@ -428,7 +428,7 @@ ACC_API int acc_ctx_set_mode(acc_ctx *ctx, int mode);
  *   per-warp overflow lists are sized by the largest degree it finds), so it
  *   is never replayed from a launch graph.
  *  ACC_ADJ_AUTO (default): sparse above ACC_MAX_N vertices; hashed when the
- *   largest graph of the count or batch has at least 32768 vertices for
+ *   largest graph of the count or batch has at least 49152 vertices for
  *   k = 5, 131072 for k = 3, 4 (where the dense probes, out of L2, get slower
  *   than the hashed ones); dense otherwise.
  * Except for ACC_ADJ_SPARSE the dense block is built in every case (it also

@@ -22,7 +22,7 @@ constexpr unsigned long long kQueueCap = 1ull << 22;
 // block's probes (n^2/4 bytes, out of L2) get slower than the hashed ones
 // (measured on GB300: k = 5 dense/hashed 82/87 scanned entries per ns at
 // n = 40000, 53/87 at 80000; k = 4 149/107 at 40000, 122/108 at 80000).
-constexpr int kHashMinN5 = 32768;
+constexpr int kHashMinN5 = 49152;
 constexpr int kHashMinN34 = 131072;
 bool hash_auto(int k, int max_n) { return max_n >= (k == 5 ? kHashMinN5 : kHashMinN34); }
 // Below this many vertices the renumbering pass costs more than it saves.

@@ -92,11 +92,11 @@ def test_full_size_workloads(counter, name, make, k):
 
 
 def test_automatic_choice_by_size():
-    """By default a 33000-vertex graph is counted at k = 5 with hashed tables
+    """By default a 50000-vertex graph is counted at k = 5 with hashed tables
     (one more kernel than the dense run) and at k = 4 with the dense block;
     the counts are the dense block's either way."""
     import paper_1203_3415_gb300 as p
-    g = synth.chung_lu(33000, 66000, 2.2, 60, 10, 3400)
+    g = synth.chung_lu(50000, 100000, 2.2, 60, 10, 3400)
     auto, dense = p.Counter(0), p.Counter(0)
     dense.set_adjacency(p.ACC_ADJ_DENSE)
     for k, extra in ((5, 1), (4, 0)):
