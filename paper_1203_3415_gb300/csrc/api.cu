@@ -178,6 +178,14 @@ bool uses_hash(const acc_ctx *c, int k, int max_n) {
             (c->adjacency == ACC_ADJ_AUTO && hash_auto(k, max_n)));
 }
 
+// The count mode's scans stage the list rows that are neighbours of the
+// root from the reverse positions of the root's entries (ACC_REV=0 at build
+// time: by binary search, as for every other row).
+#ifndef ACC_REV
+#define ACC_REV 1
+#endif
+bool uses_rev(const acc_ctx *c, int) { return ACC_REV && count_family(c); }
+
 // Size limit of one graph: the dense block's, or the sparse build's for the
 // count mode (local ids fill 26 bits of the extension-list entries).
 int size_check(const acc_ctx *c, long long n) {
@@ -236,6 +244,7 @@ int ensure_workspace(acc_ctx *c, long long NV, long long state_words, long long 
     if ((rc = grow(&c->f5_pre, &c->f5_pre_cap, (size_t)NV + 1))) return rc;
     if ((rc = grow(&c->nbr, &c->nbr_cap, (size_t)(2 * arcs) + 1))) return rc;
     if ((rc = grow(&c->src, &c->src_cap, (size_t)(2 * arcs) + 1))) return rc;
+    if (uses_rev(c, k) && (rc = grow(&c->rev, &c->rev_cap, (size_t)(2 * arcs) + 1))) return rc;
     if (!sparse && (rc = grow(&c->occ, &c->occ_cap, (size_t)NV * (size_t)occ_words(max_n) + 1))) return rc;
     if (!c->info) {
         if (!ok(cudaMalloc(&c->info, sizeof(GraphInfo)))) return ACC_ERR_NOMEM;
@@ -310,8 +319,21 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     // count mode on a large set: probes read hashed tables, built from the
     // sorted neighbour lists
     const bool hash = gs.NV > 0 && uses_hash(c, k, max_n);
+    // the automatic mode takes the k = 3 formula path on graphs of up to
+    // kAutoFormulaMaxN vertices (measured faster there: 0.028 against 0.034 ms
+    // at 1000 vertices, 0.065 against 0.100 at 5000; slower at 20000 with
+    // hubs of degree 470, 0.208 against 0.181)
     if (hash) {
         rc = launch_nh_build(c->nptr, c->deg, c->nbr, c->src, c->info, 2 * gs.M, c->nh, c->num_sms, s);
+        if (rc < 0) return rc;
+        launches += rc;
+    }
+    const bool formula = c->mode == ACC_MODE_FORMULA ||
+                         (c->mode == ACC_MODE_AUTO && k == 3 && max_n <= kAutoFormulaMaxN && !sparse &&
+                          !uses_hash(c, k, max_n));
+    const bool rev = gs.NV > 0 && !formula && uses_rev(c, k);
+    if (rev) {
+        rc = launch_rev_build(gs, c->nptr, c->deg, c->nbr, c->src, c->info, 2 * gs.M, c->rev, c->num_sms, s);
         if (rc < 0) return rc;
         launches += rc;
     }
@@ -324,6 +346,7 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     a.nbr = c->nbr;
     a.src = c->src;
     a.nh = hash ? reinterpret_cast<const uint4 *>(c->nh) : nullptr;
+    a.rev = rev ? c->rev : nullptr;
     a.lut = c->lut_sv[k];
     a.gs = gs;
     a.max_n = max_n;
@@ -338,13 +361,6 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     a.counts = reinterpret_cast<unsigned long long *>(counts);
     a.status = status;
     const bool any = gs.NV > 0;
-    // the automatic mode takes the k = 3 formula path on graphs of up to
-    // kAutoFormulaMaxN vertices (measured faster there: 0.028 against 0.034 ms
-    // at 1000 vertices, 0.065 against 0.100 at 5000; slower at 20000 with
-    // hubs of degree 470, 0.208 against 0.181)
-    const bool formula = c->mode == ACC_MODE_FORMULA ||
-                         (c->mode == ACC_MODE_AUTO && k == 3 && max_n <= kAutoFormulaMaxN && !sparse_build(c, max_n) &&
-                          !uses_hash(c, k, max_n));
     if (any && formula) {
         if (k == 3)
             rc = launch_formula3(gs, c->state, c->nptr, c->deg, c->lo, c->nbr, c->lut[3],
@@ -436,9 +452,9 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
         key.grid_num = c->grid_num;
         key.grid_den = c->grid_den;
         key.adjacency = c->adjacency;
-        const void *ws[20] = {c->state, c->deg, c->lo, c->label, c->deg_in, c->nptr, c->tiles, c->nbr, c->occ,
+        const void *ws[21] = {c->state, c->deg, c->lo, c->label, c->deg_in, c->nptr, c->tiles, c->nbr, c->occ,
                               c->info, c->queue, c->scratch, c->lut[k], c->lut_sv[k], c->class_code_dev[k],
-                              c->f5_pre, c->status_dev, c->src, c->nh, nullptr};
+                              c->f5_pre, c->status_dev, c->src, c->nh, c->rev, nullptr};
         memcpy(key.ws, ws, sizeof(ws));
         bool have = c->cg_exec && memcmp(&key, &c->cg_key, sizeof(key)) == 0;
         // capture only when a count repeats: a one-off count runs one by one
@@ -498,7 +514,8 @@ long long ctx_footprint(const acc_ctx *c, long long n, long long m, int k) {
     // are bounded by the largest degree, itself at most 2m and n
     const long long list_n = sparse ? (2 * m < n ? 2 * m : n) : n;
     const long long bytes = (sparse ? 16 * (m + 1) + 8 * (n + 1) : n * pitch * 4 + 4 * n * occ_words((int)n)) +
-                            5 * 4 * (n + 1) + 8 * (n + 1) + 8 * (2 * m + 1) + hash_bytes + (long long)kQueueCap * 16 +
+                            5 * 4 * (n + 1) + 8 * (n + 1) + (uses_rev(c, k) ? 16 : 8) * (2 * m + 1) + hash_bytes +
+                            (long long)kQueueCap * 16 +
                             (sparse ? 2 * sparse_list_entries((int)list_n) + 2 * kPartBRows : scratch_per_warp((int)n)) *
                                 (warps > 0 ? warps : 0) * 4;
     return bytes + bytes / 4;
@@ -569,6 +586,7 @@ void acc_ctx_destroy(acc_ctx *c) {
     cudaFree(c->occ);
     cudaFree(c->nbr);
     cudaFree(c->src);
+    cudaFree(c->rev);
     cudaFree(c->nh);
     cudaFree(c->sp_raw);
     cudaFree(c->sp_merged);

@@ -253,6 +253,13 @@ int launch_build_graph_sparse(const GSet &gs, const BuildBufs &b, const SparseBu
 // 2 |E*| (the exact count is read on the device).
 int launch_nh_build(const long long *nptr, const int *deg, const uint32_t *nbr, const uint32_t *src,
                     const GraphInfo *info, long long max_entries, uint32_t *nh, int num_sms, cudaStream_t s);
+// Reverse positions of a built set: for the entry p of row a holding x,
+// the part of N*(x) above a (each list holds the other end of every edge,
+// sorted by local id), as rev[p] = (first position, length).  The count mode
+// stages a list row x that is a neighbour of the root v from rev(v -> x)
+// instead of searching N*(x).  max_entries bounds 2 |E*|.
+int launch_rev_build(const GSet &gs, const long long *nptr, const int *deg, const uint32_t *nbr, const uint32_t *src,
+                     const GraphInfo *info, long long max_entries, uint2 *rev, int num_sms, cudaStream_t s);
 // Zero the pair-state chunks a build set (by its occupancy bitmap), leaving
 // the buffer all zero.
 int launch_clear_graph(const GSet &gs, uint32_t *state, const uint32_t *occ, int occ_w, int num_sms, cudaStream_t s);
@@ -281,6 +288,7 @@ struct EnumArgs {
     const uint32_t *nbr;        // entries hold local ids
     const uint32_t *src;        // global row vertex of each entry, bit 31: neighbour below it
     const uint4 *nh;            // hashed adjacency (count mode), or NULL: probes read the dense block
+    const uint2 *rev;           // count mode: reverse positions (launch_rev_build), or NULL
     const int16_t *lut;         // class table in the state-vector layout
     GSet gs;
     int max_n;                  // largest graph of the set

@@ -39,6 +39,8 @@ struct acc_ctx {
     uint32_t *nbr = nullptr;
     uint32_t *src = nullptr;  // row of each neighbour entry
     size_t src_cap = 0;
+    uint2 *rev = nullptr;     // count mode: reverse position of each neighbour entry
+    size_t rev_cap = 0;
     uint32_t *nh = nullptr;   // hashed adjacency tables
     size_t nh_cap = 0;
     int adjacency = ACC_ADJ_AUTO;
@@ -104,7 +106,7 @@ struct acc_ctx {
         const void *rowptr, *col, *counts, *status;
         long long m, light, target;
         int n, k, mode, grid_num, grid_den, adjacency;
-        const void *ws[20];
+        const void *ws[21];
     } cg_key = {}, cg_seen = {};  // the captured graph's key; the last key counted one by one
     int cg_launches = 0;
     long long cg_units = 0;

@@ -168,6 +168,7 @@ struct GView {
     const int *lo;
     const uint32_t *nbr;
     const uint32_t *nh;     // hashed adjacency (tables at kNhWords * nptr), or NULL
+    const uint2 *rev;       // reverse positions (by global position), or NULL
     int n;
 };
 
@@ -217,6 +218,7 @@ __device__ __forceinline__ GView view_single(const EnumArgs &a) {
     g.lo = a.lo;
     g.nbr = a.nbr;
     g.nh = reinterpret_cast<const uint32_t *>(a.nh);
+    g.rev = a.rev;
     g.n = a.gs.one.n;
     return g;
 }
@@ -230,6 +232,7 @@ __device__ __forceinline__ GView view_of(const EnumArgs &a, const GMeta &mt) {
     g.lo = a.lo + mt.voff;
     g.nbr = a.nbr;
     g.nh = reinterpret_cast<const uint32_t *>(a.nh);
+    g.rev = a.rev;
     g.n = mt.n;
     return g;
 }
@@ -237,8 +240,7 @@ __device__ __forceinline__ GView view_of(const EnumArgs &a, const GMeta &mt) {
 // First position of N*(x) (entries (u << 2) | s, sorted) with u > root.
 __device__ __forceinline__ int first_above(const uint32_t *__restrict__ nbr, long long base, int d, uint32_t root) {
     const uint32_t key = (root + 1u) << 2;
-    // under the degree-descending numbering most lists lie wholly above
-    // the root: one load settles them
+    // a list wholly above the root is settled by one load
     if (d == 0 || __ldg(nbr + base) >= key) return 0;
     int lo = 1, hi = d;
     while (lo < hi) {
@@ -612,11 +614,14 @@ __device__ __forceinline__ void count_group_pairs(Sink<K> &sink, const uint32_t 
     }
 }
 
+// Rows j < A are neighbours of the root, E[j] the entry at position j of
+// revA (the reverse positions of the root's list from that entry on): the
+// part of N*(x) above the root is read there, with no search.
 template <int K, bool HASH>
 __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, const uint32_t *E, int B, int jlo,
                                              int jend, bool bulk, const uint32_t *pm, uint32_t pcode,
                                              uint32_t root, bool w2_in_a, uint32_t *gcnt, uint32_t *ring,
-                                             int lane) {
+                                             const uint2 *revA, int A, int lane) {
     using L = Layout<K>;
     if (bulk) count_group_pairs<K>(sink, E, B, pcode, gcnt, lane);
     // neighbour scan of rows [jlo, jend): adjacent member pairs (each once,
@@ -638,6 +643,7 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
     uint32_t F = 0;          // flat entries consumed
     int tail = 0, cur = -1;  // ring rows staged; last ring row starting before F
     int jb = jlo;
+    const int Ae = min(A, jend);  // rows read from revA
     // stage rows while fewer than W windows are pending and the ring
     // has room for 32 more rows (the live rows are cur .. tail - 1)
     auto stage = [&]() {
@@ -645,7 +651,12 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
             const int j = jb + lane;
             uint32_t ej = 0, first = 0;
             int cnt = 0;
-            if (j < jend) {
+            if (j < Ae) {
+                ej = E[j];
+                const uint2 r = __ldg(revA + j);
+                first = r.x;
+                cnt = (int)r.y;
+            } else if (j < jend) {
                 ej = E[j];
                 const uint32_t x = e_id(ej);
                 const long long nb = g.nptr[x];
@@ -792,7 +803,7 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
 template <int K, bool HASH>
 __device__ __forceinline__ void count_shared_rows(const GView &g, Sink<K> &sink, const uint32_t *EL, int BL, int r0,
                                                   int r1, uint32_t pc0, const uint32_t *p0, const PRow *rows0,
-                                                  uint32_t *ring, int lane) {
+                                                  uint32_t *ring, const uint2 *revA, int A, int lane) {
     using L = Layout<K>;
     constexpr int RM = L::RING - 1;
     constexpr int SB = 2 * (K - 3);         // bits of the states to P0
@@ -802,12 +813,18 @@ __device__ __forceinline__ void count_shared_rows(const GView &g, Sink<K> &sink,
     uint32_t T = 0, F = 0;   // flat entries staged, consumed
     int tail = 0, cur = -1;  // ring rows staged; last ring row starting before F
     int jb = r0 + 1;
+    const int Ae = min(A, BL);  // rows read from revA (neighbours of v, as in count_leaves)
     for (;;) {
         while (jb < BL && T - F < 32u && tail - cur + kWarp <= L::RING) {
             const int j = jb + lane;
             uint32_t ej = 0, first = 0;
             int cnt = 0;
-            if (j < BL) {
+            if (j < Ae) {
+                ej = EL[j];
+                const uint2 r = __ldg(revA + j);
+                first = r.x;
+                cnt = (int)r.y;
+            } else if (j < BL) {
                 ej = EL[j];
                 const uint32_t x = e_id(ej);
                 const long long nb = g.nptr[x];
@@ -1034,11 +1051,13 @@ __device__ __forceinline__ void count_partb_rows(const GView &g, Sink<5> &sink, 
 
 // Count mode, k = 5: rows [r0, r1) of the last list level EL (see
 // count_shared_rows): each member's leaf list built, its group pairs and
-// part-B rows counted by count_leaves, then the shared part-A rows.
+// part-B rows counted by count_leaves, then the shared part-A rows.  The
+// first A_el rows of EL are neighbours of v whose reverse positions start
+// at revA (as for count_leaves).
 template <int K, bool HASH>
 __device__ __forceinline__ void count_last_lists(const GView &g, Sink<K> &sink, const Scratch &sc, const uint32_t *EL,
                                                  int BL, int r0, int r1, uint32_t pc0, const uint32_t *p0,
-                                                 const PRow *rows0, int lane) {
+                                                 const PRow *rows0, const uint2 *revA, int A_el, int lane) {
     using L = Layout<K>;
     constexpr int SB = 2 * (K - 3);
     constexpr int SHL = L::SH_ROW + 2 * (K - 2);
@@ -1091,7 +1110,7 @@ __device__ __forceinline__ void count_last_lists(const GView &g, Sink<K> &sink, 
             for (int k2 = 0; k2 < K - 3; k2++) pm[k2] = p0[k2];
             pm[K - 3] = wl;
             count_leaves<K, HASH>(g, sink, EN, pos, A, pos, true, pm, pcode, v, (el & 3u) != 0u, sc.gcnt, sc.ring,
-                                  lane);
+                                  nullptr, 0, lane);
         } else {
             count_group_pairs<K>(sink, EN, pos, pcode, sc.gcnt, lane);
             if (nb + nB > kPartBRows) {
@@ -1107,7 +1126,7 @@ __device__ __forceinline__ void count_last_lists(const GView &g, Sink<K> &sink, 
         __syncwarp();
     }
     if (nb) count_partb_rows<HASH>(g, sink, sc.pb, sc.pb + kPartBRows, nb, pc0, p0, rows0, sc.ring, lane);
-    count_shared_rows<K, HASH>(g, sink, EL, BL, r0, r1, pc0, p0, rows0, sc.ring, lane);
+    count_shared_rows<K, HASH>(g, sink, EL, BL, r0, r1, pc0, p0, rows0, sc.ring, revA, A_el, lane);
 }
 
 // Level-2 extension list of unit (v, w1), w1 at position p of N*(v): part A
@@ -1301,10 +1320,15 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
             }
         }
         const uint32_t pm[1] = {(uint32_t)v};
+        // every row is a neighbour of the root, at position rb + j
+        const uint2 *revA = g.rev ? g.rev + rb : nullptr;
+        const int A = g.rev ? B : 0;
         if (hi > jlo)
-            count_leaves<K, HASH>(g, sink, E, B, jlo, hi, jlo == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, sc.ring, lane);
+            count_leaves<K, HASH>(g, sink, E, B, jlo, hi, jlo == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, sc.ring, revA,
+                                  A, lane);
         if (rest < B)
-            count_leaves<K, HASH>(g, sink, E, B, rest, B, rest == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, sc.ring, lane);
+            count_leaves<K, HASH>(g, sink, E, B, rest, B, rest == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, sc.ring,
+                                  revA, A, lane);
         __syncwarp();
         return;
     }
@@ -1363,12 +1387,16 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
         }
         const uint32_t pm[2] = {(uint32_t)v, w1};
         const uint32_t pcode = s01 << (L::SH_ROW + 4);
+        // part A of the list (the neighbours of v after w1) sits at
+        // positions unit + 1 + j of v's list
+        const uint2 *revA = g.rev ? g.rev + unit + 1 : nullptr;
+        const int A = g.rev ? g.deg[v] - t - 1 : 0;
         if (hi > jlo)
             count_leaves<K, HASH>(g, sink, E2, B2, jlo, hi, jlo == 0, pm, pcode, (uint32_t)v, false, sc.gcnt, sc.ring,
-                            lane);
+                                  revA, A, lane);
         if (rest < B2)
-            count_leaves<K, HASH>(g, sink, E2, B2, rest, B2, rest == 0, pm, pcode, (uint32_t)v, false, sc.gcnt, sc.ring,
-                            lane);
+            count_leaves<K, HASH>(g, sink, E2, B2, rest, B2, rest == 0, pm, pcode, (uint32_t)v, false, sc.gcnt,
+                                  sc.ring, revA, A, lane);
         __syncwarp();
         return;
     }
@@ -1419,8 +1447,11 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
     if constexpr (K == 5 && COUNT) {
         const uint32_t p0[2] = {(uint32_t)v, w1};
         const PRow rows0[2] = {row_v, row_w1};
-        if (hi > jlo) count_last_lists<K, HASH>(g, sink, sc, E2, B2, jlo, hi, pc01, p0, rows0, lane);
-        if (rest < B2) count_last_lists<K, HASH>(g, sink, sc, E2, B2, rest, B2, pc01, p0, rows0, lane);
+        // part A of E2 (the neighbours of v after w1) at positions unit + 1 + j
+        const uint2 *revA = g.rev ? g.rev + unit + 1 : nullptr;
+        const int A2 = g.rev ? g.deg[v] - t - 1 : 0;
+        if (hi > jlo) count_last_lists<K, HASH>(g, sink, sc, E2, B2, jlo, hi, pc01, p0, rows0, revA, A2, lane);
+        if (rest < B2) count_last_lists<K, HASH>(g, sink, sc, E2, B2, rest, B2, pc01, p0, rows0, revA, A2, lane);
         __syncwarp();
         return;
     }

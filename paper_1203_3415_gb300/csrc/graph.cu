@@ -869,6 +869,33 @@ __global__ void __launch_bounds__(1024) k_relabel_graph(GSet gs, const int *__re
     }
 }
 
+// Thread per neighbour entry p (row vertex a = src[p], neighbour x): the
+// index i of a in N*(x), found by binary search of x's sorted list (a is
+// there: the lists are symmetric), stored as the part of N*(x) above a:
+// its first position nptr[x] + i + 1 and its length deg(x) - i - 1.
+__global__ void k_rev(GSet gs, const long long *__restrict__ nptr, const int *__restrict__ deg,
+                      const uint32_t *__restrict__ nbr, const uint32_t *__restrict__ src,
+                      const GraphInfo *__restrict__ info, uint2 *rev) {
+    grid_dep_wait();
+    const long long nnz = info->nnz;
+    for (long long pos = blockIdx.x * (long long)blockDim.x + threadIdx.x; pos < nnz;
+         pos += (long long)gridDim.x * blockDim.x) {
+        const uint32_t a = src[pos] & 0x7FFFFFFFu;  // global
+        const int voff = gs.meta(gs.graph_of((int)a)).voff;
+        const uint32_t x = (uint32_t)voff + (nbr[pos] >> 2);
+        const uint32_t key = (a - (uint32_t)voff) << 2;
+        const long long base = nptr[x];
+        const int d = deg[x];
+        int lo = 0, hi = d;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (nbr[base + mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        rev[pos] = make_uint2((uint32_t)(base + lo + 1), (uint32_t)(d - lo - 1));
+    }
+}
+
 // gid[v] = graph of global vertex v (block per graph).
 __global__ void k_graph_ids(GSet gs, int *gid) {
     grid_dep_wait();
@@ -1086,6 +1113,13 @@ int launch_build_graph_sparse(const GSet &gs, const BuildBufs &bb, const SparseB
     if (!launch_ok()) return ACC_ERR_CUDA;
     launches++;
     return launches;
+}
+
+int launch_rev_build(const GSet &gs, const long long *nptr, const int *deg, const uint32_t *nbr, const uint32_t *src,
+                     const GraphInfo *info, long long max_entries, uint2 *rev, int num_sms, cudaStream_t s) {
+    if (max_entries <= 0) return 0;
+    launch_pdl(k_rev, grid_for(max_entries, 256, num_sms), 256, 0, s, gs, nptr, deg, nbr, src, info, rev);
+    return cudaGetLastError() == cudaSuccess ? 1 : ACC_ERR_CUDA;
 }
 
 int launch_clear_graph(const GSet &gs, uint32_t *state, const uint32_t *occ, int occ_w, int num_sms, cudaStream_t s) {

@@ -144,8 +144,24 @@ int main(int argc, char **argv) {
         }
     }
 
+    // count mode: the reverse position of each entry (the part of the
+    // neighbour's sorted list above the row's vertex: first position,
+    // length), as the library's build computes it
+    std::vector<uint2> rev(nnz + 1);
+    for (long long v = 0; v < NV; v++) {
+        const int voff = meta[gid[v]].voff;
+        const uint32_t key = (uint32_t)(v - voff) << 2;
+        for (long long p = nptr[v]; p < nptr[v + 1]; p++) {
+            const long long x = voff + (nbr[p] >> 2);
+            const long long i =
+                std::lower_bound(nbr.begin() + nptr[x], nbr.begin() + nptr[x] + deg[x], key) - (nbr.begin() + nptr[x]);
+            rev[p] = make_uint2((uint32_t)(nptr[x] + i + 1), (uint32_t)(deg[x] - i - 1));
+        }
+    }
+
     EnumArgs a{};
     a.src = src.data();
+    a.rev = mode != 1 ? rev.data() : nullptr;
     a.nh = mode == 2 ? reinterpret_cast<const uint4 *>(nh.data()) : nullptr;
     a.state = st.data();
     a.deg = deg.data();

@@ -39,7 +39,9 @@ using std::max;
 using std::min;
 
 struct int4 { int x, y, z, w; };
+struct uint2 { unsigned x, y; };
 struct uint4 { unsigned x, y, z, w; };
+inline uint2 make_uint2(unsigned a, unsigned b) { return {a, b}; }
 inline int4 make_int4(int a, int b, int c, int d) { return {a, b, c, d}; }
 inline uint4 make_uint4(unsigned a, unsigned b, unsigned c, unsigned d) { return {a, b, c, d}; }
 struct dim { unsigned x; };

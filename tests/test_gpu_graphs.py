@@ -40,7 +40,7 @@ def test_repeats_equal_one_by_one(acc):
         out.zero_()
         cnt.count(r, c, g.n, 4, counts=out)
         assert out.cpu().numpy().tolist() == want.tolist()
-        assert cnt.last_stats()["launches"] == 9
+        assert cnt.last_stats()["launches"] == 10
     cnt.set_launch_graphs(False)
     out.zero_()
     cnt.count(r, c, g.n, 4, counts=out)
