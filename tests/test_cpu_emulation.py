@@ -782,7 +782,8 @@ def emu_lib_results(tmp_path_factory):
         if os.path.isabs(asan) and os.path.exists(asan) else []
     procs = []
     for i, u in enumerate(units):
-        cmd = ["g++", "-std=c++20", "-O1", "-fPIC", "-pthread", "-w", *san, "-I", EMU, "-I",
+        # (every count-mode set builds the reverse positions, however small)
+        cmd = ["g++", "-std=c++20", "-O1", "-fPIC", "-pthread", "-w", *san, "-DACC_REV_MIN_ARCS=0", "-I", EMU, "-I",
                os.path.join(EMU, "fake"), "-I", CSRC, "-c", u, "-o", str(out / ("u%d.o" % i))]
         procs.append(subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
     for pr in procs:
