@@ -82,6 +82,9 @@ namespace {
 #ifndef ACC_CWIN
 #define ACC_CWIN 3  // count mode: 32-entry windows of the flat row scan per step (entries in flight per lane), k = 3, 4
 #endif
+#ifndef ACC_CWIN_P2
+#define ACC_CWIN_P2 4  // the same in phase 2, whose queued chunks of heavy units run longer scans
+#endif
 #ifndef ACC_CWIN5
 #define ACC_CWIN5 2  // the same for k = 5
 #endif
@@ -149,6 +152,10 @@ struct Layout {
     static constexpr size_t ring = size_t(kWarpsPerBlock) * RING * RING_ARRAYS * 4;
     static constexpr size_t total = lut + pending + hist + ebuf + groups + ring;
 };
+
+// Windows per step of the phase-2 scans (the queued chunks of heavy units).
+template <int K>
+constexpr int kWinP2 = K == 5 ? Layout<K>::WIN : ACC_CWIN_P2;
 
 __device__ __forceinline__ uint32_t probe(const uint32_t *__restrict__ st, long long pitch, uint32_t a, uint32_t b) {
     return (__ldg(st + (long long)a * pitch + (b >> 4)) >> ((b & 15u) << 1)) & 3u;
@@ -617,7 +624,7 @@ __device__ __forceinline__ void count_group_pairs(Sink<K> &sink, const uint32_t 
 // Rows j < A are neighbours of the root, E[j] the entry at position j of
 // revA (the reverse positions of the root's list from that entry on): the
 // part of N*(x) above the root is read there, with no search.
-template <int K, bool HASH>
+template <int K, bool HASH, int WN = Layout<K>::WIN>
 __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, const uint32_t *E, int B, int jlo,
                                              int jend, bool bulk, const uint32_t *pm, uint32_t pcode,
                                              uint32_t root, bool w2_in_a, uint32_t *gcnt, uint32_t *ring,
@@ -633,7 +640,7 @@ __device__ __forceinline__ void count_leaves(const GView &g, Sink<K> &sink, cons
     // rows that start inside it (one OR-reduction of their start bits and a
     // population count).  Flat positions wrap modulo 2^32; only differences
     // below 2^31 are compared.  A step takes W windows.
-    constexpr int W = L::WIN;
+    constexpr int W = WN;
     constexpr int RM = L::RING - 1;
     uint32_t *rS = ring, *rO = ring + L::RING, *rE = ring + 2 * L::RING;
     PRow rowp[K - 2];  // adjacency of the prefix vertices
@@ -1289,7 +1296,7 @@ __device__ __forceinline__ long long total_work(int B, WorkFn work, int lane) {
 // instead.  D is the per-row allowance for exclusive neighbours (mean degree
 // + 1); wmax bounds the count mode's work of one row (largest degree + row
 // cost), so a short list skips summing its rows' work.
-template <int K, bool COUNT, bool HASH>
+template <int K, bool COUNT, bool HASH, int WN = Layout<K>::WIN>
 __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, const Scratch &sc, uint32_t unit,
                              int v, int vglob, int jlo, int jhi, bool phase1, long long D, long long wmax, int lane) {
     using L = Layout<K>;
@@ -1324,10 +1331,10 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
         const uint2 *revA = g.rev ? g.rev + rb : nullptr;
         const int A = g.rev ? B : 0;
         if (hi > jlo)
-            count_leaves<K, HASH>(g, sink, E, B, jlo, hi, jlo == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, sc.ring, revA,
+            count_leaves<K, HASH, WN>(g, sink, E, B, jlo, hi, jlo == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, sc.ring, revA,
                                   A, lane);
         if (rest < B)
-            count_leaves<K, HASH>(g, sink, E, B, rest, B, rest == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, sc.ring,
+            count_leaves<K, HASH, WN>(g, sink, E, B, rest, B, rest == 0, pm, 0u, (uint32_t)v, false, sc.gcnt, sc.ring,
                                   revA, A, lane);
         __syncwarp();
         return;
@@ -1392,10 +1399,10 @@ __device__ void process_unit(const EnumArgs &a, const GView &g, Sink<K> &sink, c
         const uint2 *revA = g.rev ? g.rev + unit + 1 : nullptr;
         const int A = g.rev ? g.deg[v] - t - 1 : 0;
         if (hi > jlo)
-            count_leaves<K, HASH>(g, sink, E2, B2, jlo, hi, jlo == 0, pm, pcode, (uint32_t)v, false, sc.gcnt, sc.ring,
+            count_leaves<K, HASH, WN>(g, sink, E2, B2, jlo, hi, jlo == 0, pm, pcode, (uint32_t)v, false, sc.gcnt, sc.ring,
                                   revA, A, lane);
         if (rest < B2)
-            count_leaves<K, HASH>(g, sink, E2, B2, rest, B2, rest == 0, pm, pcode, (uint32_t)v, false, sc.gcnt,
+            count_leaves<K, HASH, WN>(g, sink, E2, B2, rest, B2, rest == 0, pm, pcode, (uint32_t)v, false, sc.gcnt,
                                   sc.ring, revA, A, lane);
         __syncwarp();
         return;
@@ -1616,11 +1623,11 @@ __global__ void __launch_bounds__(kThreads, K == 5 ? ACC_MINB5 : (COUNT ? (SET ?
                 const int gi = a.gs.graph_of(vg);
                 const GMeta mt = a.gs.meta(gi);
                 sink.switch_graph(gi, lane);
-                process_unit<K, COUNT, HASH>(a, view_of(a, mt), sink, sc, it.x, vg - mt.voff, vg, (int)it.y,
-                                             (int)it.z, false, D, wmax, lane);
+                process_unit<K, COUNT, HASH, kWinP2<K>>(a, view_of(a, mt), sink, sc, it.x, vg - mt.voff, vg,
+                                                        (int)it.y, (int)it.z, false, D, wmax, lane);
             } else {
-                process_unit<K, COUNT, HASH>(a, view_single(a), sink, sc, it.x, vg, vg, (int)it.y, (int)it.z, false,
-                                             D, wmax, lane);
+                process_unit<K, COUNT, HASH, kWinP2<K>>(a, view_single(a), sink, sc, it.x, vg, vg, (int)it.y,
+                                                        (int)it.z, false, D, wmax, lane);
             }
         }
     }
