@@ -10,7 +10,8 @@
 // int64 (length, values): status, launches, nnz, maxdeg and whether the
 // counts were zeroed; label[NV]; deg[NV]; lo[NV]; nptr[NV + 1]; nbr[nnz];
 // the state words; the occupancy words (both empty for the sparse build);
-// after the clear, whether the state buffer is all zero; src[nnz].
+// after the clear, whether the state buffer is all zero; src[nnz]; the
+// reverse positions (launch_rev_build) as first, length pairs[2 nnz].
 #include "shim.h"
 #include "common.cuh"
 thread_local dim threadIdx, blockIdx;
@@ -77,6 +78,7 @@ int main(int argc, char **argv) {
     std::vector<long long> nptr(NV + 1), tiles(acc::scan_tiles_needed(NV) + 1);
     std::vector<uint32_t> nbr(2 * M + 1), occ(NV * occ_w + 1);
     std::vector<uint32_t> src(2 * M + 1), raw(2 * M + 1), merged(2 * M + 1);
+    std::vector<uint2> rev(2 * M + 1);
     std::vector<long long> roff(NV + 1);
     std::vector<int> big(acc::sparse_big_rows_cap(M));
     acc::GraphInfo info{};
@@ -133,6 +135,15 @@ int main(int argc, char **argv) {
         for (long long i = 0; i < words; i++) clean = clean && (sparse || state[i] == 0);
         put(&clean, 1);
         put(src.data(), (size_t)nnz);
+        std::vector<uint32_t> rv;
+        if (status == 0 && acc::launch_rev_build(gs, nptr.data(), deg.data(), nbr.data(), src.data(), &info, 2 * M,
+                                                 rev.data(), num_sms, nullptr) < 0)
+            return 4;
+        for (long long p = 0; p < nnz; p++) {
+            rv.push_back(rev[p].x);
+            rv.push_back(rev[p].y);
+        }
+        put(rv.data(), rv.size());
         bb.state_clean = true;
     }
     fclose(out);

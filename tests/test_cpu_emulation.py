@@ -511,7 +511,7 @@ def _build_many(bins, jobs, binary="emu_build", guard_k=0, sparse=False):
         for n, rp, cl in graphs:
             buf += np.asarray(rp, "<i8").tobytes() + np.asarray(cl, "<i4").tobytes()
         inps.append(buf)
-    names = ("head", "label", "deg", "lo", "nptr", "nbr", "state", "occ", "clean", "src")
+    names = ("head", "label", "deg", "lo", "nptr", "nbr", "state", "occ", "clean", "src", "rev")
     res = []
     for o in _run_many(bins[binary], inps, True, bins["dir"]):
         raw = np.frombuffer(o, "<i8")
@@ -530,7 +530,9 @@ def _check_build(r, graphs, relabel, sparse=False):
     and is a permutation; the pair states, degrees, below-counts, neighbour
     lists (positions over the whole set), each entry's row (bit 31: a
     neighbour below the row's vertex) and occupancy bits are those of the
-    renumbered graph (the sparse build keeps no pair states or bits)."""
+    renumbered graph (the sparse build keeps no pair states or bits); the
+    reverse positions give, for the entry v -> x, the part of x's list above
+    v (first position, length)."""
     status, _, nnz, maxdeg, zeroed = r["head"].tolist()
     assert status == 0 and zeroed == 1 and r["clean"][0] == 1
     voff, base = 0, 0
@@ -581,6 +583,17 @@ def _check_build(r, graphs, relabel, sparse=False):
             want_src[b:e] = (voff + v) | np.where((nbr_cat[b:e] >> 2) < v, 1 << 31, 0)
         voff += n
     assert np.array_equal(r["src"], want_src)
+    want_rev = np.zeros((len(nbr_cat), 2), np.int64)
+    voff = 0
+    for n, _, _ in graphs:
+        for v in range(n):
+            for p in range(nptr_cat[voff + v], nptr_cat[voff + v + 1]):
+                x = voff + (int(nbr_cat[p]) >> 2)
+                row = (nbr_cat[nptr_cat[x]:nptr_cat[x + 1]] >> 2).tolist()
+                i = row.index(v)  # the lists are symmetric
+                want_rev[p] = (nptr_cat[x] + i + 1, len(row) - i - 1)
+        voff += n
+    assert np.array_equal(r["rev"], want_rev.reshape(-1))
 
 
 def _raw_csr(n, s, d, rng):
