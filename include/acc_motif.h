@@ -188,7 +188,10 @@ ACC_API int acc_motif_batch_prepare(acc_ctx *ctx, const acc_graph_desc *h_graphs
  * acc_motif_count (the overflow guard bounds every graph of the batch by
  * the degree sums of all of them, and by C(largest n, k)).  With d_status non-NULL the call only enqueues kernels
  * (no allocation, no copy, no wait), so it can be captured into a CUDA graph
- * and replayed.  A captured run stays valid until the next
+ * and replayed; only a run after acc_ctx_set_mode or acc_ctx_set_adjacency
+ * changed the context since the prepare may first grow the workspace for
+ * the new path (ACC_ERR_TOO_LARGE if the new mode cannot take the batch's
+ * largest graph).  A captured run stays valid until the next
  * acc_motif_batch_prepare on the context (which rewrites the descriptors the
  * capture reads; the batch's sizes are baked into the captured launches) or
  * until a later call on the context grows its workspace; capture again after

@@ -191,7 +191,7 @@ bool uses_hash(const acc_ctx *c, int k, int max_n) {
 #ifndef ACC_REV_MIN_ARCS
 #define ACC_REV_MIN_ARCS 8192
 #endif
-bool uses_rev(const acc_ctx *c, int) { return ACC_REV && count_family(c); }
+bool uses_rev(const acc_ctx *c, long long arcs) { return ACC_REV && count_family(c) && arcs >= ACC_REV_MIN_ARCS; }
 
 // Size limit of one graph: the dense block's, or the sparse build's for the
 // count mode (local ids fill 26 bits of the extension-list entries).
@@ -251,7 +251,7 @@ int ensure_workspace(acc_ctx *c, long long NV, long long state_words, long long 
     if ((rc = grow(&c->f5_pre, &c->f5_pre_cap, (size_t)NV + 1))) return rc;
     if ((rc = grow(&c->nbr, &c->nbr_cap, (size_t)(2 * arcs) + 1))) return rc;
     if ((rc = grow(&c->src, &c->src_cap, (size_t)(2 * arcs) + 1))) return rc;
-    if (uses_rev(c, k) && (rc = grow(&c->rev, &c->rev_cap, (size_t)(2 * arcs) + 1))) return rc;
+    if (uses_rev(c, arcs) && (rc = grow(&c->rev, &c->rev_cap, (size_t)(2 * arcs) + 1))) return rc;
     if (!sparse && (rc = grow(&c->occ, &c->occ_cap, (size_t)NV * (size_t)occ_words(max_n) + 1))) return rc;
     if (!c->info) {
         if (!ok(cudaMalloc(&c->info, sizeof(GraphInfo)))) return ACC_ERR_NOMEM;
@@ -338,7 +338,7 @@ int run_set(acc_ctx *c, const GSet &gs, int max_n, int k, bool relabel, cudaStre
     const bool formula = c->mode == ACC_MODE_FORMULA ||
                          (c->mode == ACC_MODE_AUTO && k == 3 && max_n <= kAutoFormulaMaxN && !sparse &&
                           !uses_hash(c, k, max_n));
-    const bool rev = gs.NV > 0 && gs.M >= ACC_REV_MIN_ARCS && !formula && uses_rev(c, k);
+    const bool rev = gs.NV > 0 && !formula && uses_rev(c, gs.M);
     if (rev) {
         rc = launch_rev_build(gs, c->nptr, c->deg, c->nbr, c->src, c->info, 2 * gs.M, c->rev, c->num_sms, s);
         if (rc < 0) return rc;
@@ -507,6 +507,16 @@ int count_impl(acc_ctx *c, const int64_t *rowptr, const int32_t *col, int32_t n,
     return finish(c, s, status_user);
 }
 
+// The workspace a run of the prepared batch needs under the context's
+// current mode and adjacency choice, which may differ from those at the
+// prepare (the count mode's reverse positions, hashed tables or sparse
+// build): grows nothing when they are the same.
+int batch_workspace(acc_ctx *c) {
+    if (size_check(c, c->batch_max_n)) return ACC_ERR_TOO_LARGE;
+    return ensure_workspace(c, c->batch_set.NV, sparse_build(c, c->batch_max_n) ? 0 : c->batch_words, c->batch_arcs,
+                            c->batch_max_n, c->batch_k);
+}
+
 }  // namespace
 
 namespace acc {
@@ -521,7 +531,7 @@ long long ctx_footprint(const acc_ctx *c, long long n, long long m, int k) {
     // are bounded by the largest degree, itself at most 2m and n
     const long long list_n = sparse ? (2 * m < n ? 2 * m : n) : n;
     const long long bytes = (sparse ? 16 * (m + 1) + 8 * (n + 1) : n * pitch * 4 + 4 * n * occ_words((int)n)) +
-                            5 * 4 * (n + 1) + 8 * (n + 1) + (uses_rev(c, k) ? 16 : 8) * (2 * m + 1) + hash_bytes +
+                            5 * 4 * (n + 1) + 8 * (n + 1) + (uses_rev(c, m) ? 16 : 8) * (2 * m + 1) + hash_bytes +
                             (long long)kQueueCap * 16 +
                             (sparse ? 2 * sparse_list_entries((int)list_n) + 2 * kPartBRows : scratch_per_warp((int)n)) *
                                 (warps > 0 ? warps : 0) * 4;
@@ -729,8 +739,10 @@ int acc_motif_batch_run(acc_ctx *c, void *stream, int64_t *d_counts, int32_t *d_
     if (!ok(cudaSetDevice(c->device))) return ACC_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     if (c->batch_set.B == 0) return ACC_OK;
+    int rc = batch_workspace(c);
+    if (rc) return rc;
     int *status = d_status ? d_status : c->status_dev;
-    const int rc = run_set(c, c->batch_set, c->batch_max_n, c->batch_k, true, s, d_counts, status);
+    rc = run_set(c, c->batch_set, c->batch_max_n, c->batch_k, true, s, d_counts, status);
     if (rc) return rc;
     return finish(c, s, d_status);
 }
@@ -951,6 +963,7 @@ int acc_motif_batch_autotune(acc_ctx *c, void *stream, int64_t *h_light, int64_t
         best = 0.0f;
         goto done;
     }
+    if ((rc = batch_workspace(c))) return rc;
     if (!ok(cudaMalloc(&counts, (size_t)B * num_classes(c->batch_k) * sizeof(int64_t)))) return ACC_ERR_NOMEM;
     if (!ok(cudaEventCreate(&e0)) || !ok(cudaEventCreate(&e1))) {
         rc = ACC_ERR_CUDA;

@@ -244,17 +244,21 @@ def _descs(gs):
 
 def scenario_batch(lib):
     """A batch of graphs prepared once and run several times in every mode,
-    then the autotuner, for k = 3, 4 and 5."""
+    then the autotuner, for k = 3, 4 and 5; each k prepared in another mode
+    (a run in a mode that needs more workspace than the prepare's grows it
+    first)."""
     c = Ctx(lib)
-    for k, nmax in ((3, 30), (4, 18), (5, 10)):
+    for k, nmax, prep_mode in ((3, 30, acc.ACC_MODE_ENUMERATE), (4, 18, acc.ACC_MODE_COUNT),
+                               (5, 10, acc.ACC_MODE_FORMULA)):
         gs = graphs(20 + k, 6, nmax)
         gs.insert(2, (5, np.zeros(0, np.int64), np.zeros(0, np.int64)))
         descs, keep = _descs(gs)
+        ok(lib.acc_ctx_set_mode(c.h, prep_mode), "set_mode before prepare")
         ok(lib.acc_motif_batch_prepare(c.h, descs, len(gs), k, None), "batch_prepare")
         want = [oracle.count(n, s, d, k).tolist() for n, s, d in gs]
         # every mode on the same prepared batch (graph sets take each mode's
         # per-graph counting branch)
-        for mode in (acc.ACC_MODE_ENUMERATE, acc.ACC_MODE_FORMULA, acc.ACC_MODE_COUNT):
+        for mode in (acc.ACC_MODE_COUNT, acc.ACC_MODE_ENUMERATE, acc.ACC_MODE_FORMULA, acc.ACC_MODE_COUNT):
             ok(lib.acc_ctx_set_mode(c.h, mode), "set_mode")
             for rep in range(2):
                 out = np.full(len(gs) * NCLS[k], -1, np.int64)

@@ -207,3 +207,29 @@ def test_prepare_waits_for_an_enqueued_run(counter):
         assert ca[i].cpu().numpy().tolist() == oracle.count(g.n, g.src, g.dst, 4, threads=oracle.max_threads()).tolist(), i
     for i, g in enumerate(gb):
         assert cb[i].cpu().numpy().tolist() == oracle.count(g.n, g.src, g.dst, 4).tolist(), i
+
+
+def test_mode_changed_between_prepare_and_run():
+    """A batch prepared in the enumerate mode and run in the count mode (and
+    back): the run first grows the workspace the count mode needs (its
+    reverse positions, for a set of at least 8192 arcs), and every mode gives
+    the oracle's counts."""
+    from paper_1203_3415_gb300 import build
+    build.build()
+    import paper_1203_3415_gb300 as p
+    graphs = []
+    for seed in (91, 92, 93):
+        g = synth.chung_lu(2000, 8000, 2.2, 120, 10, seed)
+        graphs.append((g.n, g.src, g.dst))
+    want = [oracle.count(n, s, d, 4, threads=oracle.max_threads()).tolist() for n, s, d in graphs]
+    c = p.Counter(0)
+    try:
+        c.set_mode(p.ACC_MODE_ENUMERATE)
+        dev = to_device(graphs)
+        c.prepare_batch(dev, 4)
+        for mode in (p.ACC_MODE_COUNT, p.ACC_MODE_ENUMERATE, p.ACC_MODE_FORMULA, p.ACC_MODE_AUTO):
+            c.set_mode(mode)
+            got = c.run_batch().cpu().numpy()
+            assert got.tolist() == want, mode
+    finally:
+        c.close()
