@@ -62,6 +62,9 @@ def test_contents_change_between_repeats(acc):
         c.copy_(torch.from_numpy(cc))
         cnt.count(r, c, n, 4, counts=out)
         assert out.cpu().numpy().tolist() == oracle.count(n, g.src, g.dst, 4).tolist(), seed
+        # fewer than 8192 arcs: no reverse positions, so one launch fewer
+        # than the 12000-arc graph of the test above
+        assert cnt.last_stats()["launches"] == 9
     cnt.close()
 
 
