@@ -384,7 +384,10 @@ ACC_API int acc_motif_last_stats(acc_ctx *ctx, int64_t *h_stats);
  *   are not adjacent are counted per pair of state-vector groups (their class
  *   depends only on the two members' states to the prefix), the adjacent
  *   pairs are corrected one by one from the members' neighbour lists, as the
- *   paper's Table starb counts patterns from set sizes minus edges.
+ *   paper's Table starb counts patterns from set sizes minus edges.  For a
+ *   set of at least 8192 arcs the build also stores, per neighbour entry
+ *   v -> x, where x's list passes v (8 bytes per entry), so the scans of
+ *   the root's neighbours' lists start without a search.
  *  ACC_MODE_ENUMERATE: every k-subset is visited and classified on its own.
  *  ACC_MODE_FORMULA: for k = 3, the paper's per-vertex formulas (Thm teo3,
  *   Algorithm s3, Table starb): open triples from the sizes of each vertex's
